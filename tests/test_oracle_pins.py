@@ -1,0 +1,382 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by the mathematics.
+
+Every test here checks the oracle against something other than itself:
+exact many-body (Fock-space) dynamics, brute-force 8-index sums, explicit
+Kronecker-product matrices, closed forms, conservation laws, the Hubbard
+specialisations the paper prints, and the memory-integral HF-GKBA the
+G1-G2 scheme is derived from.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+from oracle import g1g2_oracle as O
+from oracle.hfgkba import propagate_hfgkba
+from paper_2002_12717_gb300 import inputs
+
+from . import fock
+
+
+def sym_w(nb, rng, real=False):
+    """Random w with w_ijkl = w_jilk and w_ijkl = conj(w_klij) (Eqs. wsymm_a/b)."""
+    x = rng.standard_normal((nb,) * 4)
+    if not real:
+        x = x + 1j * rng.standard_normal((nb,) * 4)
+    x = x + x.transpose(1, 0, 3, 2)
+    x = x + x.transpose(2, 3, 0, 1).conj()
+    return x * 0.25
+
+
+def random_fock_state(nb, npart, rng):
+    dim = 1 << nb
+    v = np.zeros(dim, dtype=np.complex128)
+    for b in range(dim):
+        if bin(b).count("1") == npart:
+            v[b] = rng.standard_normal() + 1j * rng.standard_normal()
+    return v / np.linalg.norm(v)
+
+
+# ---------------------------------------------------------------------------
+# Exact many-body pins (Fock space, nb = 5 spin-orbitals)
+# ---------------------------------------------------------------------------
+
+def test_g1_equation_is_exact_first_hierarchy_equation():
+    """Eq. (eom_gone) with I of Eq. (definition_D) is exact for any state.
+
+    Pins h^HF (Eq. h_HF incl. the exchange term), the collision integral and
+    its index order 𝒢_lpjk, and the sign conventions of Eq. (g-glsymm).
+    """
+    rng = np.random.default_rng(11)
+    nb = 5
+    h = inputs.random_hermitian(nb, rng)
+    w = sym_w(nb, rng)
+    H = fock.hamiltonian(h, w)
+    psi = random_fock_state(nb, 2, rng)
+    n, n2 = fock.rdms(psi, nb)
+    g2 = fock.correlated_g2(n, n2)
+    exact = fock.time_derivative(H, psi, lambda v: fock.rdms(v, nb)[0])
+    hhf = O.hf_hamiltonian(h, w, n)
+    got = O.g1_rhs(hhf, n, O.collision_integral(w, g2))
+    assert np.abs(got - exact).max() < 1e-8
+
+
+def test_source_term_is_exact_initial_slope_from_slater_determinant():
+    """From an uncorrelated state the exact d𝒢/dt equals -iΨ^- (Eq. dgdt-a).
+
+    Pins the source term of Eq. (psi-pm-def): signs, index placement and the
+    antisymmetrised w^- of the SOA.
+    """
+    rng = np.random.default_rng(12)
+    nb = 5
+    h = inputs.random_hermitian(nb, rng)
+    w = sym_w(nb, rng)
+    H = fock.hamiltonian(h, w)
+    orb = np.linalg.qr(rng.standard_normal((nb, 2)) + 1j * rng.standard_normal((nb, 2)))[0]
+    psi = fock.slater(orb, nb)
+    n, n2 = fock.rdms(psi, nb)
+    assert np.abs(fock.correlated_g2(n, n2)).max() < 1e-12
+    exact = fock.time_derivative(H, psi, lambda v: fock.correlated_g2(*fock.rdms(v, nb)))
+    got = -1j * O.psi_source(O.w_antisym(w), n)
+    assert np.abs(got - exact).max() < 1e-8
+    # the plain-w source (GW reading) is a different function
+    assert np.abs(-1j * O.psi_source(w, n) - exact).max() > 1e-3
+
+
+def test_commutator_is_exact_for_noninteracting_dynamics():
+    """With w = 0 the exact correlated part obeys i d𝒢/dt = [h^(2), 𝒢] (Eq. result_eom_soa)."""
+    rng = np.random.default_rng(13)
+    nb = 5
+    h = inputs.random_hermitian(nb, rng)
+    H = fock.hamiltonian(h, np.zeros((nb,) * 4))
+    psi = random_fock_state(nb, 2, rng)
+    n, n2 = fock.rdms(psi, nb)
+    g2 = fock.correlated_g2(n, n2)
+    assert np.abs(g2).max() > 1e-2
+    exact = fock.time_derivative(H, psi, lambda v: fock.correlated_g2(*fock.rdms(v, nb)))
+    got = -1j * O.two_particle_commutator(h, g2)
+    assert np.abs(got - exact).max() < 1e-8
+
+
+def test_energy_equals_many_body_expectation():
+    """E9 from the two-particle density matrix of Eq. (ini-g2) equals <ψ|H|ψ>."""
+    rng = np.random.default_rng(14)
+    nb = 5
+    h = inputs.random_hermitian(nb, rng)
+    w = sym_w(nb, rng)
+    H = fock.hamiltonian(h, w)
+    psi = random_fock_state(nb, 3, rng)
+    n, n2 = fock.rdms(psi, nb)
+    g2 = fock.correlated_g2(n, n2)
+    e = O.energies(O.Problem(h, w), 0.0, n, g2)
+    assert abs(e["e_total"] - (psi.conj() @ H @ psi).real) < 1e-10
+    assert abs(e["n_particles"] - 3.0) < 1e-12
+
+
+def test_double_occupancy_equals_many_body_expectation():
+    rng = np.random.default_rng(15)
+    L = 2
+    nb = 2 * L
+    h = inputs.spin_orbital_h(inputs.chain_hopping(L))
+    w = inputs.spin_orbital_hubbard_w(L, 2.0)
+    psi = random_fock_state(nb, 2, rng)
+    n, n2 = fock.rdms(psi, nb)
+    g2 = fock.correlated_g2(n, n2)
+    c = fock.annihilators(nb)
+    for s in range(L):
+        nu = c[2 * s].T @ c[2 * s]
+        nd = c[2 * s + 1].T @ c[2 * s + 1]
+        exact = (psi.conj() @ nu @ nd @ psi).real
+        assert abs(O.double_occupancy(n, g2, L)[s] - exact) < 1e-12
+    # E_corr of the Hubbard w is -U Σ_i 𝒢_{i↑i↓i↑i↓}-type terms; check E against <H>
+    H = fock.hamiltonian(h, w)
+    e = O.energies(O.Problem(h, w), 0.0, n, g2)
+    assert abs(e["e_total"] - (psi.conj() @ H @ psi).real) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Brute force and explicit matrices
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nb", [3, 4])
+def test_psi_successive_contractions_equal_literal_phi_sum(nb):
+    """Eq. (soa-skalierung) equals the literal Eq. (psi-pm-def) with Φ built from 𝒢^H."""
+    rng = np.random.default_rng(20 + nb)
+    n = inputs.random_hermitian(nb, rng) * 0.3 + 0.4 * np.eye(nb)
+    w = sym_w(nb, rng)
+    gl = 1j * n
+    gg = gl - 1j * np.eye(nb)
+    gh = lambda a: np.einsum("ip,jq->ijpq", a, a)          # 𝒢^H_ijpq = G_ip G_jq (Eq. g2h-def)
+    # Φ^{ijkl}_{pqrs} = (iħ)^4 [𝒢^H,>_ijpq 𝒢^H,<_klrs - 𝒢^H,<_ijpq 𝒢^H,>_klrs]
+    phi = (1j ** 4) * (np.einsum("ijpq,klrs->ijklpqrs", gh(gg), gh(gl))
+                       - np.einsum("ijpq,klrs->ijklpqrs", gh(gl), gh(gg)))
+    for wt in (w, O.w_antisym(w)):
+        # Ψ_ijkl = (iħ)^-2 Σ_pqrs w_pqrs Φ^{ijrs}_{pqkl}
+        literal = np.einsum("pqrs,ijrspqkl->ijkl", wt, phi) / (1j ** 2)
+        assert np.abs(O.psi_source(wt, n) - literal).max() < 1e-12
+
+
+def test_commutator_equals_kronecker_matrix_commutator():
+    """Eq. (twopart_hamiltonian): h2 = 1⊗h + h⊗1 as an nb^2 x nb^2 matrix."""
+    rng = np.random.default_rng(30)
+    nb = 4
+    h = inputs.random_hermitian(nb, rng)
+    g2 = rng.standard_normal((nb,) * 4) + 1j * rng.standard_normal((nb,) * 4)
+    eye = np.eye(nb)
+    h2 = np.einsum("jl,ik->ijkl", eye, h) + np.einsum("ik,jl->ijkl", eye, h)
+    m = g2.reshape(nb * nb, nb * nb)
+    hm = h2.reshape(nb * nb, nb * nb)
+    want = (hm @ m - m @ hm).reshape((nb,) * 4)
+    assert np.abs(O.two_particle_commutator(h, g2) - want).max() < 1e-12
+
+
+def test_hf_hamiltonian_is_energy_gradient():
+    """h^HF - h = ∂E_HF/∂n^T for both bases (consistency of Eq. h_HF with E9)."""
+    rng = np.random.default_rng(31)
+    nb = 4
+    h = inputs.random_hermitian(nb, rng)
+    w = sym_w(nb, rng, real=True)
+    n = inputs.random_hermitian(nb, rng) * 0.2 + 0.5 * np.eye(nb)
+    for restricted in (False, True):
+        prob = O.Problem(h, w, restricted=restricted)
+        hhf = O.hf_hamiltonian(h, w, n, restricted)
+        s = 2.0 if restricted else 1.0
+        eps = 1e-6
+        grad = np.zeros((nb, nb), dtype=np.complex128)
+        for a in range(nb):
+            for b in range(nb):
+                for part, unit in ((0, 1.0), (1, 1j)):
+                    dn = np.zeros((nb, nb), dtype=np.complex128)
+                    dn[b, a] += unit * eps
+                    ep = O.energies(prob, 0, n + dn, 0 * w)["e_hf"]
+                    em = O.energies(prob, 0, n - dn, 0 * w)["e_hf"]
+                    d = (ep - em) / (2 * eps)
+                    grad[a, b] += d if part == 0 else -1j * d
+        # E_HF(n + dn) - E_HF(n) = Re Σ (h^HF - h)_ab dn_ba * s  (dn Hermitian-free probe)
+        assert np.abs(grad - s * (hhf - h)).max() < 1e-6
+
+
+def test_gw_hcorr_matches_delta_reduction():
+    """Eq. (gwhcorr) with Eq. (g2f-def): the G^>G^< - G^<G^> difference is δ-terms of n."""
+    rng = np.random.default_rng(32)
+    nb = 4
+    w = sym_w(nb, rng)
+    n = inputs.random_hermitian(nb, rng) * 0.2 + 0.5 * np.eye(nb)
+    eye = np.eye(nb)
+    # G^>_jq G^<_pl - G^<_jq G^>_pl = δ_jq n_pl - n_jq δ_pl  (brute force over all indices)
+    want = np.zeros((nb,) * 4, dtype=np.complex128)
+    for i in range(nb):
+        for j in range(nb):
+            for k in range(nb):
+                for l in range(nb):
+                    acc = 0
+                    for p in range(nb):
+                        for q in range(nb):
+                            acc += w[q, i, p, k] * (eye[j, q] * n[p, l] - n[j, q] * eye[p, l])
+                    want[i, j, k, l] = acc
+    assert np.abs(O.gw_hcorr(w, n) - want).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Hubbard specialisations printed in the paper
+# ---------------------------------------------------------------------------
+
+def test_hubbard_soa_source_matches_phi_hubbard():
+    """Eq. (g2-hubbard) with Φ of Eq. (phi-hubbard) equals the restricted-mode Ψ."""
+    rng = np.random.default_rng(40)
+    L, U = 4, 1.7
+    n = inputs.random_hermitian(L, rng) * 0.2 + 0.5 * np.eye(L)
+    gl = 1j * n
+    gg = gl - 1j * np.eye(L)
+    phi = (1j ** 4) * (np.einsum("ip,jp,pk,pl->ijkl", gg, gg, gl, gl)
+                       - np.einsum("ip,jp,pk,pl->ijkl", gl, gl, gg, gg))
+    want = U * phi / (1j ** 2)
+    got = O.psi_source(inputs.onsite_w_restricted(L, U).astype(complex), n)
+    assert np.abs(got - want).max() < 1e-12
+
+
+def test_hubbard_gw_polarisation_matches_pihubbardtrans():
+    """Eq. (pihubbardtrans): the general Π with the spin-orbital Hubbard w, ↑↓↑↓ block."""
+    rng = np.random.default_rng(41)
+    L, U = 3, 1.3
+    nb = 2 * L
+    w = inputs.spin_orbital_hubbard_w(L, U).astype(complex)
+    ns = inputs.random_hermitian(L, rng) * 0.2 + 0.5 * np.eye(L)
+    n = np.kron(ns, np.eye(2))
+    _, g2 = inputs.random_state(nb, rng, soa=False)
+    pi = O.gw_polarisation(O.gw_hcorr(w, n), g2)
+    g_uuuu = g2[0::2, 0::2, 0::2, 0::2]
+    gl = 1j * ns
+    gg = gl - 1j * np.eye(L)
+    # Π^{↑↓↑↓}_ijkl = -(iħ)^2 U Σ_p [G^>_jp G^<_pl - G^<_jp G^>_pl] 𝒢^{↑↑↑↑}_ipkp
+    want = np.zeros((L,) * 4, dtype=complex)
+    for i in range(L):
+        for j in range(L):
+            for k in range(L):
+                for l in range(L):
+                    for p in range(L):
+                        want[i, j, k, l] += -(1j ** 2) * U * (gg[j, p] * gl[p, l] - gl[j, p] * gg[p, l]) \
+                            * g_uuuu[i, p, k, p]
+    got = pi[0::2, 1::2, 0::2, 1::2]
+    assert np.abs(got - want).max() < 1e-12
+    assert np.abs(want).max() > 1e-3
+
+
+def test_restricted_mode_equals_spin_orbital_hubbard():
+    """Restricted chain of L sites == spin-orbital chain of 2L orbitals (SOA, Sec. III.D)."""
+    L, U = 3, 1.0
+    hs = inputs.chain_hopping(L)
+    hs[0, 0] += 2.0
+    n_site = inputs.lowest_projector(inputs.chain_hopping(L), 1) * 0 + np.diag([0.7, 0.4, 0.4]).astype(complex)
+    pr = O.Problem(hs, inputs.onsite_w_restricted(L, U), restricted=True)
+    ps = O.Problem(inputs.spin_orbital_h(hs), inputs.spin_orbital_hubbard_w(L, U))
+    nr, gr, _, obr = O.propagate(pr, n_site, np.zeros((L,) * 4), 0.02, 50)
+    nso, gso, _, obs = O.propagate(ps, np.kron(n_site, np.eye(2)), np.zeros((2 * L,) * 4), 0.02, 50)
+    assert np.abs(nso[0::2, 0::2] - nr).max() < 1e-12
+    assert np.abs(gso[0::2, 1::2, 0::2, 1::2] - gr).max() < 1e-12
+    assert abs(obr[-1]["e_total"] - obs[-1]["e_total"]) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Closed forms and conservation laws
+# ---------------------------------------------------------------------------
+
+def test_noninteracting_closed_form():
+    """w = 0: 𝒢 stays 0 and n(t) = e^{-iht} n0 e^{iht} (Eq. eom_gone-2 with I = 0)."""
+    rng = np.random.default_rng(50)
+    nb = 5
+    h = inputs.random_hermitian(nb, rng)
+    n0 = inputs.lowest_projector(inputs.random_hermitian(nb, rng), 2)
+    prob = O.Problem(h, np.zeros((nb,) * 4))
+    errs = []
+    for dt in (0.02, 0.01):
+        n, g2, t, _ = O.propagate(prob, n0, np.zeros((nb,) * 4), dt, int(round(2.0 / dt)))
+        u = expm(-1j * h * t)
+        errs.append(np.abs(n - u @ n0 @ u.conj().T).max())
+        assert np.abs(g2).max() == 0.0
+    assert errs[1] < 1e-8 and 12 < errs[0] / errs[1] < 20      # RK4: O(dt^4)
+
+
+def test_hubbard_chain_initial_state_closed_form():
+    """Open 8-site chain at half filling: HF ground state energies in closed form."""
+    d = inputs.hubbard_chain_restricted()
+    prob = O.Problem(inputs.chain_hopping(8), d["w"], restricted=True)
+    e = O.energies(prob, 0.0, d["n0"], np.zeros((8,) * 4))
+    e_tb = 2 * sum(-2 * math.cos(math.pi * k / 9) for k in range(1, 5))
+    assert abs(e["e_one"] - e_tb) < 1e-12
+    assert abs(e["e_hf"] - 8 * 0.25 * 1.0) < 1e-12          # U Σ_i n_ii^2 with n_ii = 1/2
+    assert np.abs(np.diag(d["n0"]).real - 0.5).max() < 1e-12
+    # the state is self-consistent: [h^HF(n0), n0] = 0
+    hhf = O.hf_hamiltonian(inputs.chain_hopping(8), d["w"], d["n0"], True)
+    assert np.abs(hhf @ d["n0"] - d["n0"] @ hhf).max() < 1e-12
+
+
+@pytest.mark.parametrize("se", ["HF", "SOA", "GW"])
+def test_conservation_laws(se):
+    """Particle number to round-off; energy to O(dt^4) (Sec. VIII: energy conserving)."""
+    L = 3
+    nb = 2 * L
+    hs = inputs.chain_hopping(L)
+    hs[0, 0] += 2.0
+    prob = O.Problem(inputs.spin_orbital_h(hs), inputs.spin_orbital_hubbard_w(L, 1.0), selfenergy=se)
+    n0 = np.kron(inputs.lowest_projector(inputs.chain_hopping(L), 2) * 0 + np.diag([0.8, 0.5, 0.2]), np.eye(2))
+    drifts = []
+    for dt in (0.04, 0.02):
+        steps = int(round(2.0 / dt))
+        n, g2, _, obs = O.propagate(prob, n0.astype(complex), np.zeros((nb,) * 4), dt, steps, obs_every=steps)
+        assert abs(obs[-1]["n_particles"] - obs[0]["n_particles"]) < 1e-12
+        drifts.append(abs(obs[-1]["e_total"] - obs[0]["e_total"]))
+        # 𝒢 symmetries of Eqs. (Gsymm_a/b)
+        assert np.abs(g2 - g2.transpose(1, 0, 3, 2)).max() < 1e-14
+        assert np.abs(g2 - g2.transpose(2, 3, 0, 1).conj()).max() < 1e-14
+        if se == "SOA":
+            assert np.abs(g2 + g2.transpose(0, 1, 3, 2)).max() < 1e-14
+    if se == "HF":
+        assert drifts[1] < 1e-8
+    else:
+        assert drifts[0] > 0 and 10 < drifts[0] / drifts[1] < 24   # ~2^4
+
+
+def test_energy_balance_with_drive():
+    """E(T) - E(0) equals the drive work ∫ f'(t) <D> dt to O(dt^4)."""
+    rng = np.random.default_rng(60)
+    nb = 4
+    h = inputs.random_hermitian(nb, rng)
+    w = sym_w(nb, rng, real=True)
+    D = np.diag(rng.standard_normal(nb)).astype(complex)
+    drv = inputs.GaussSine(A=0.5, omega=1.5, t0=1.0, sigma=0.5)
+    n0 = inputs.lowest_projector(h, 2)
+    res = []
+    for se in ("SOA", "GW"):
+        prob = O.Problem(h, w, selfenergy=se, D=D, drive=drv.f)
+        errs = []
+        for dt in (0.04, 0.02):
+            steps = int(round(2.0 / dt))
+            _, _, _, obs = O.propagate(prob, n0, np.zeros((nb,) * 4), dt, steps, obs_every=steps,
+                                       dfdt=drv.dfdt)
+            errs.append(abs(obs[-1]["e_total"] - obs[0]["e_total"] - obs[-1]["pulse_work"]))
+        assert abs(obs[-1]["pulse_work"]) > 1e-3
+        assert errs[1] < 1e-6 and errs[0] / errs[1] > 8
+        res.append(errs)
+
+
+def test_g1g2_equals_memory_integral_hfgkba():
+    """The G1-G2 SOA equations reproduce the non-Markovian HF-GKBA (Sec. III.C, Fig. densities).
+
+    Hubbard dimer (4 spin-orbitals), U = J, half filling, uncorrelated start, quench.
+    The memory-integral solution converges to the G1-G2 one at second order.
+    """
+    L = 2
+    hs = inputs.chain_hopping(L)
+    hs[0, 0] += 1.0
+    prob = O.Problem(inputs.spin_orbital_h(hs), inputs.spin_orbital_hubbard_w(L, 1.0))
+    n0 = np.kron(inputs.lowest_projector(inputs.chain_hopping(L), 1), np.eye(2))
+    T = 2.0
+    n_ref, _, _, _ = O.propagate(prob, n0, np.zeros((4,) * 4), 0.005, int(T / 0.005))
+    errs = []
+    for dt in (0.1, 0.05):
+        ns = propagate_hfgkba(prob, n0, dt, int(round(T / dt)))
+        errs.append(np.abs(ns[-1] - n_ref).max())
+    assert errs[1] < 2e-3
+    assert 3.0 < errs[0] / errs[1] < 5.0
