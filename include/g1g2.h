@@ -1,0 +1,155 @@
+/*
+ * g1g2.h -- C ABI of libg1g2, a GB300 (sm_103a) implementation of the time-local
+ * G1-G2 scheme of Joost, Schluenzen and Bonitz (arXiv:2002.12717).
+ *
+ * The library propagates the one-particle density matrix n (called G1 here,
+ * n_ij = <c_j^dagger c_i>, Sec. II.B Eq. g-glsymm) and the correlated
+ * two-particle Green function G2 (the nb^4 tensor of Eq. gscor-def) with
+ * classical RK4.  The right-hand side is
+ *   G1:  Eq. (eom_gone-2) with the collision integral of Eq. (eom_gone-I)
+ *   G2:  Eq. (result_eom_soa) for SOA (source term Psi^-, Eq. psi-pm-def),
+ *        Eq. (g2-eq-gw-pi) for GW (plain-w Psi plus the polarisation term
+ *        of Eq. gwpi), nothing for HF (time-dependent Hartree-Fock).
+ * Conventions: fermions, hbar = 1, h(t) = h + f(t) D.
+ *
+ * Layout of every complex array: row-major, interleaved (re, im) doubles.
+ *   h, D, G1 : nb x nb            element (i, j) at 2*(i*nb + j)
+ *   w, G2    : nb x nb x nb x nb  element (i, j, k, l) at 2*(((i*nb + j)*nb + k)*nb + l)
+ * w is the pair interaction of Eq. (h): H = sum h_ij c_i^+ c_j
+ *   + 1/2 sum w_ijkl c_i^+ c_j^+ c_l c_k.  With g1g2_options.w_is_real != 0,
+ *   w is passed as nb^4 real doubles instead.
+ *
+ * Ownership: init, set_drive, set_state and get_state take HOST pointers and
+ * copy; the caller keeps its buffers.  g1g2_rhs takes DEVICE pointers owned
+ * by the caller.  The context owns all of its device memory until
+ * g1g2_destroy.  All device work is issued on the stream given in
+ * g1g2_options.cuda_stream (NULL = the legacy default stream).
+ *
+ * Errors: every int-returning call returns G1G2_OK (0) or a negative code;
+ * nothing aborts or throws across the ABI.  g1g2_strerror gives the message,
+ * g1g2_last_error_detail the detail of the last failure on this thread.
+ */
+#ifndef G1G2_H
+#define G1G2_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define G1G2_OK            0
+#define G1G2_EINVAL       -1  /* bad size, NULL pointer, bad enum, unsupported combination */
+#define G1G2_ESYMM        -2  /* w, G1_0 or G2_0 violates the symmetries of Sec. II (Eqs. Gsymm, wsymm) */
+#define G1G2_ENOMEM       -3  /* device allocation failed */
+#define G1G2_ECUDA        -4  /* a CUDA runtime call or kernel launch failed */
+#define G1G2_ENONFINITE   -5  /* the state contains NaN or Inf */
+#define G1G2_ETIMEOUT     -6  /* a bounded device wait gave up */
+#define G1G2_EUNSUPPORTED -7  /* valid request that this build does not implement */
+
+typedef struct g1g2_ctx g1g2_ctx;  /* opaque */
+
+/* Selfenergy of the G2 equation. */
+typedef enum {
+  G1G2_HF = 0,   /* I = 0, G2 frozen: time-dependent Hartree-Fock (Eq. eom_gone-2 without I) */
+  G1G2_SOA = 1,  /* second-order Born, Sec. III.C, Eq. (result_eom_soa) */
+  G1G2_GW = 2    /* GW, Sec. IV.C, Eq. (g2-eq-gw-pi) */
+} g1g2_selfenergy;
+
+/* Arithmetic of the contractions. The RK4 state update, the Hartree-Fock
+ * build and the observables are FP64 in every mode. */
+typedef enum {
+  G1G2_FP64 = 0,   /* every contraction in FP64 on the CUDA cores: the reference form */
+  G1G2_TF32X3 = 1  /* split-precision tensor-core contractions: hi/lo TF32 operands, FP32 accumulation */
+} g1g2_precision;
+
+/* Basis. SPIN_RESTRICTED: the index runs over spatial orbitals, w is an
+ * opposite-spin interaction and n_up = n_down (the Hubbard equations of
+ * Sec. III.D: no exchange term in h^HF and Psi, spin factors in the energies).
+ * Only SOA and HF are defined in this basis. */
+typedef enum { G1G2_SPIN_ORBITAL = 0, G1G2_SPIN_RESTRICTED = 1 } g1g2_basis;
+
+typedef struct {
+  int precision;      /* g1g2_precision */
+  int basis;          /* g1g2_basis */
+  int w_is_real;      /* nonzero: w is nb^4 real doubles */
+  double sym_tol;     /* absolute symmetry tolerance for w, G1_0, G2_0 (scaled by max|x|); <0 skips */
+  void *cuda_stream;  /* cudaStream_t used for every launch; NULL = default stream */
+} g1g2_options;
+
+typedef struct {
+  double t;
+  double n_particles;  /* Re Tr n (x2 spin-restricted) */
+  double e_one;        /* Re Tr(h(t) n) (x2 spin-restricted) */
+  double e_hf;         /* 1/2 Re sum w^-_ijkl n_ki n_lj (spin-restricted: Re sum w_ijkl n_ki n_lj) */
+  double e_corr;       /* -1/2 Re sum w_ijkl G2_klij (spin-restricted: -Re sum w_ijkl G2_klij) */
+  double e_total;      /* e_one + e_hf + e_corr */
+  double pulse_work;   /* W(t) = int f'(t) Re Tr(D n) dt, RK4-weighted over the stages */
+} g1g2_obs;
+
+/* Default options: FP64, spin-orbital, complex w, sym_tol 1e-10, default stream. */
+void g1g2_default_options(g1g2_options *opt);
+
+/* Create a propagation context (Sec. III.F: the initial values n^0 and G2^0).
+ *   nb         basis size, 1 <= nb <= 128
+ *   h          nb*nb complex, Hermitian (host)
+ *   w          nb^4 complex, or real if opt->w_is_real (host); must satisfy
+ *              w_ijkl = w_jilk and w_ijkl = conj(w_klij) (Eqs. wsymm_a/b)
+ *   G1_0       nb*nb complex, Hermitian (host)
+ *   G2_0       nb^4 complex with Eqs. (Gsymm_a/b) (host), or NULL for G2_0 = 0
+ *   se         g1g2_selfenergy
+ *   opt        options, or NULL for the defaults
+ * Returns G1G2_EINVAL for nb out of range, NULL arrays, bad enums, or GW in
+ * the spin-restricted basis; G1G2_ESYMM when a symmetry is violated beyond
+ * sym_tol; G1G2_ENOMEM / G1G2_ECUDA on device failure. t starts at 0. */
+int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const double *G1_0,
+              const double *G2_0, int se, const g1g2_options *opt);
+
+/* Time-dependent one-body term h(t) = h + f(t) D (the excitations of the
+ * workloads; the paper's Eq. (h) allows any h(t)).
+ *   D       nb*nb complex Hermitian (host), copied
+ *   kind    0 none; 1 gauss-sine f = A sin(w t) exp(-(t-t0)^2/(2 s^2)) with
+ *           params = {A, w, t0, s}; 2 piecewise linear through M equidistant
+ *           values on [ta, tb], params = {ta, tb, v_0 .. v_{M-1}} (M >= 2),
+ *           constant beyond the ends.
+ * Returns G1G2_EINVAL on a bad kind or parameter count. */
+int g1g2_set_drive(g1g2_ctx *c, const double *D, int kind, const double *params, int nparams);
+
+/* One evaluation of the right-hand side at time t (device pointers, caller-owned,
+ * interleaved complex, same layouts as above):
+ *   n_dev, G2_dev  input state; G2_dev must be Hermitian as an nb^2 x nb^2
+ *                  matrix (Eq. Gsymm_b), which the tensor-core form relies on
+ *   dn_dev, dG2_dev  outputs dn/dt and dG2/dt (dG2 is zero for HF)
+ * Runs on the context's stream; returns after the launches are queued. */
+int g1g2_rhs(g1g2_ctx *c, double t, const double *n_dev, const double *G2_dev, double *dn_dev,
+             double *dG2_dev);
+
+/* One classical RK4 step of size dt on the context's state (no host sync). */
+int g1g2_step(g1g2_ctx *c, double dt);
+
+/* nsteps RK4 steps. When obs is non-NULL it receives 1 + nsteps/obs_every
+ * records (t = start and after every obs_every-th step); when density is
+ * non-NULL it receives nb doubles per record (n_ii, x2 spin-restricted).
+ * Synchronises the stream at the end; checks the state for NaN/Inf at every
+ * record (G1G2_ENONFINITE). */
+int g1g2_propagate(g1g2_ctx *c, double dt, int nsteps, int obs_every, g1g2_obs *obs, double *density);
+
+/* Observables of the current state (synchronous). density: nb doubles or NULL.
+ * double_occ: nb/2 doubles or NULL, spin-orbital basis with index 2*site+spin only
+ * (E10: d_i = n_{i+,i+} n_{i-,i-} - |n_{i+,i-}|^2 - G2_{i+ i- i+ i-}). */
+int g1g2_observables(g1g2_ctx *c, g1g2_obs *out, double *density, double *double_occ);
+
+/* Copy the state to / from host memory (G2 may be NULL on get; NULL on set means 0). */
+int g1g2_get_state(g1g2_ctx *c, double *t, double *G1, double *G2);
+int g1g2_set_state(g1g2_ctx *c, double t, const double *G1, const double *G2);
+
+/* Number of kernel launches issued by this context since creation. */
+long long g1g2_launch_count(const g1g2_ctx *c);
+
+const char *g1g2_strerror(int code);
+const char *g1g2_last_error_detail(void);
+void g1g2_destroy(g1g2_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* G1G2_H */

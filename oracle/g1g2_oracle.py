@@ -36,7 +36,13 @@ Readings of the paper used here (each is listed in the design doc as well):
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
+
+# every einsum below is one contraction step; optimize=True lets numpy hand a
+# two-operand contraction to BLAS (tensordot) instead of its generic loop
+einsum = functools.partial(np.einsum, optimize=True)
 
 SOA = "SOA"
 GW = "GW"
@@ -70,12 +76,12 @@ def hf_hamiltonian(h, w, n, restricted=False):
     Hubbard basis).
     """
     wt = w if restricted else w_antisym(w)
-    return h - 1j * np.einsum("ikjl,lk->ij", wt, g_less(n))
+    return h - 1j * einsum("ikjl,lk->ij", wt, g_less(n))
 
 
 def collision_integral(w, G2):
     """Eq. (definition_D) / (eom_gone-I), lower sign: I_ij = -i Σ_klp w_iklp 𝒢_lpjk."""
-    return -1j * np.einsum("iklp,lpjk->ij", w, G2)
+    return -1j * einsum("iklp,lpjk->ij", w, G2)
 
 
 def g1_rhs(hhf, n, I):
@@ -99,10 +105,10 @@ def two_particle_commutator(hhf, G2):
     the Kronecker deltas is carried out, leaving the four single sums
     (the same form the paper writes for the Hubbard basis in Sec. VII.A).
     """
-    return (np.einsum("ip,pjkl->ijkl", hhf, G2)
-            + np.einsum("jp,ipkl->ijkl", hhf, G2)
-            - np.einsum("ijpl,pk->ijkl", G2, hhf)
-            - np.einsum("ijkp,pl->ijkl", G2, hhf))
+    return (einsum("ip,pjkl->ijkl", hhf, G2)
+            + einsum("jp,ipkl->ijkl", hhf, G2)
+            - einsum("ijpl,pk->ijkl", G2, hhf)
+            - einsum("ijkp,pl->ijkl", G2, hhf))
 
 
 def psi_source(wt, n):
@@ -116,10 +122,10 @@ def psi_source(wt, n):
     gl, gg = g_less(n), g_greater(n)
 
     def chain(a, b, c, d):
-        x = np.einsum("pqrs,sl->pqrl", wt, d)      # Σ_s w_pqrs d_sl
-        x = np.einsum("rk,pqrl->pqkl", c, x)       # Σ_r c_rk (...)
-        x = np.einsum("jq,pqkl->pjkl", b, x)       # Σ_q b_jq (...)
-        return np.einsum("ip,pjkl->ijkl", a, x)    # Σ_p a_ip (...)
+        x = einsum("pqrs,sl->pqrl", wt, d)      # Σ_s w_pqrs d_sl
+        x = einsum("rk,pqrl->pqkl", c, x)       # Σ_r c_rk (...)
+        x = einsum("jq,pqkl->pjkl", b, x)       # Σ_q b_jq (...)
+        return einsum("ip,pjkl->ijkl", a, x)    # Σ_p a_ip (...)
 
     return (1j ** 2) * (chain(gg, gg, gl, gl) - chain(gl, gl, gg, gg))
 
@@ -130,7 +136,7 @@ def psi_source(wt, n):
 
 def g2_exchange(gx, gy):
     """Eq. (g2f-def) on the time diagonal: 𝒢^F_ijkl = G^x_il G^y_jk."""
-    return np.einsum("il,jk->ijkl", gx, gy)
+    return einsum("il,jk->ijkl", gx, gy)
 
 
 def gw_hcorr(w, n):
@@ -140,12 +146,12 @@ def gw_hcorr(w, n):
     """
     gl, gg = g_less(n), g_greater(n)
     fdiff = g2_exchange(gg, gl) - g2_exchange(gl, gg)
-    return -(1j ** 2) * np.einsum("qipk,jplq->ijkl", w, fdiff)
+    return -(1j ** 2) * einsum("qipk,jplq->ijkl", w, fdiff)
 
 
 def gw_polarisation(hcorr, G2):
     """Eq. (gwpi): Π_ijkl = Σ_pq 𝔥_qjpl 𝒢_ipkq."""
-    return np.einsum("qjpl,ipkq->ijkl", hcorr, G2)
+    return einsum("qjpl,ipkq->ijkl", hcorr, G2)
 
 
 # ---------------------------------------------------------------------------
@@ -222,14 +228,14 @@ def energies(prob: Problem, t, n, G2):
     """
     h = prob.h_of_t(t)
     if prob.restricted:
-        e1 = 2.0 * np.einsum("ij,ji->", h, n).real
-        ehf = np.einsum("ijkl,ki,lj->", prob.w, n, n).real
-        ecorr = -np.einsum("ijkl,klij->", prob.w, G2).real if prob.selfenergy != HF else 0.0
+        e1 = 2.0 * einsum("ij,ji->", h, n).real
+        ehf = einsum("ijkl,ki,lj->", prob.w, n, n).real
+        ecorr = -einsum("ijkl,klij->", prob.w, G2).real if prob.selfenergy != HF else 0.0
         npart = 2.0 * np.trace(n).real
     else:
-        e1 = np.einsum("ij,ji->", h, n).real
-        ehf = 0.5 * np.einsum("ijkl,ki,lj->", w_antisym(prob.w), n, n).real
-        ecorr = -0.5 * np.einsum("ijkl,klij->", prob.w, G2).real if prob.selfenergy != HF else 0.0
+        e1 = einsum("ij,ji->", h, n).real
+        ehf = 0.5 * einsum("ijkl,ki,lj->", w_antisym(prob.w), n, n).real
+        ecorr = -0.5 * einsum("ijkl,klij->", prob.w, G2).real if prob.selfenergy != HF else 0.0
         npart = np.trace(n).real
     return {"e_one": e1, "e_hf": ehf, "e_corr": ecorr,
             "e_total": e1 + ehf + ecorr, "n_particles": npart}
@@ -244,7 +250,7 @@ def drive_power(prob: Problem, t, n):
     if prob.D is None:
         return 0.0
     s = 2.0 if prob.restricted else 1.0
-    return s * np.einsum("ij,ji->", prob.D, n).real
+    return s * einsum("ij,ji->", prob.D, n).real
 
 
 def double_occupancy(n, G2, nsites):

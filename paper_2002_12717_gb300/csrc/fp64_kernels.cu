@@ -1,0 +1,551 @@
+// Plain FP64 kernels of libg1g2: the reference form of every contraction
+// (CUDA-core DFMA), the Hartree-Fock build, the G1 right-hand side, the G2
+// assembly with the fused RK4 update, and the FP64 observables.
+#include "g1g2_internal.h"
+
+#include <algorithm>
+
+namespace g1g2 {
+
+namespace {
+
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ cplx cfma(cplx a, cplx b, cplx c) {
+  return {fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y))};
+}
+__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ cplx csub(cplx a, cplx b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ cplx cconj(cplx a) { return {a.x, -a.y}; }
+__device__ __forceinline__ cplx cscale(cplx a, double s) { return {a.x * s, a.y * s}; }
+// -i * z
+__device__ __forceinline__ cplx mul_minus_i(cplx z) { return {z.y, -z.x}; }
+
+// ---------------------------------------------------------------------------
+// Strided batched complex GEMM (FP64 CUDA cores).
+// Tile 32x32x16, 64 threads, each thread a 4x4 micro-tile strided by 8.
+// ---------------------------------------------------------------------------
+constexpr int GBM = 32, GBN = 32, GBK = 16, GTM = 4, GTN = 4;
+constexpr int GNT = (GBM / GTM) * (GBN / GTN);  // 64
+
+struct ZGemmDev {
+  int M, N, K, batch;
+  const cplx *A; long long sa_b, sa_m, sa_k;
+  const cplx *B; long long sb_b, sb_k, sb_n;
+  cplx *C; long long sc_b, sc_m, sc_n;
+  cplx alpha; double beta;
+  int conjA, conjB;
+};
+
+__global__ void __launch_bounds__(GNT) zgemm_kernel(ZGemmDev g, int reduce, int per_split, cplx *partial) {
+  __shared__ cplx As[GBK][GBM + 1];
+  __shared__ cplx Bs[GBK][GBN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % (GBN / GTN), ty = tid / (GBN / GTN);
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+
+  long long b_begin, b_end, b_step;
+  if (reduce) {
+    b_begin = (long long)blockIdx.z * per_split;
+    b_end = min((long long)g.batch, b_begin + per_split);
+    b_step = 1;
+  } else {
+    b_begin = blockIdx.z;
+    b_end = g.batch;
+    b_step = gridDim.z;
+  }
+  for (long long b0 = b_begin; b0 < b_end; b0 += (reduce ? (b_end - b_begin) : b_step)) {
+    cplx acc[GTM][GTN];
+#pragma unroll
+    for (int i = 0; i < GTM; ++i)
+#pragma unroll
+      for (int j = 0; j < GTN; ++j) acc[i][j] = {0.0, 0.0};
+    const long long bl = reduce ? b_end : b0 + 1;
+    for (long long b = b0; b < bl; ++b) {
+      const cplx *A = g.A + b * g.sa_b;
+      const cplx *B = g.B + b * g.sb_b;
+      for (int k0 = 0; k0 < g.K; k0 += GBK) {
+        for (int idx = tid; idx < GBM * GBK; idx += GNT) {
+          int m, k;
+          if (g.sa_k == 1) { m = idx / GBK; k = idx % GBK; } else { k = idx / GBM; m = idx % GBM; }
+          cplx v = {0.0, 0.0};
+          if (m0 + m < g.M && k0 + k < g.K) v = A[(long long)(m0 + m) * g.sa_m + (long long)(k0 + k) * g.sa_k];
+          if (g.conjA) v.y = -v.y;
+          As[k][m] = v;
+        }
+        for (int idx = tid; idx < GBN * GBK; idx += GNT) {
+          int n, k;
+          if (g.sb_n == 1) { k = idx / GBN; n = idx % GBN; } else { n = idx / GBK; k = idx % GBK; }
+          cplx v = {0.0, 0.0};
+          if (n0 + n < g.N && k0 + k < g.K) v = B[(long long)(k0 + k) * g.sb_k + (long long)(n0 + n) * g.sb_n];
+          if (g.conjB) v.y = -v.y;
+          Bs[k][n] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < GBK; ++kk) {
+          cplx a[GTM], bb[GTN];
+#pragma unroll
+          for (int i = 0; i < GTM; ++i) a[i] = As[kk][ty + i * (GBM / GTM)];
+#pragma unroll
+          for (int j = 0; j < GTN; ++j) bb[j] = Bs[kk][tx + j * (GBN / GTN)];
+#pragma unroll
+          for (int i = 0; i < GTM; ++i)
+#pragma unroll
+            for (int j = 0; j < GTN; ++j) acc[i][j] = cfma(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+    }
+    // epilogue
+#pragma unroll
+    for (int i = 0; i < GTM; ++i) {
+      const int m = m0 + ty + i * (GBM / GTM);
+      if (m >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < GTN; ++j) {
+        const int n = n0 + tx + j * (GBN / GTN);
+        if (n >= g.N) continue;
+        if (reduce) {
+          partial[((long long)blockIdx.z * g.M + m) * g.N + n] = acc[i][j];
+        } else {
+          cplx *c = g.C + b0 * g.sc_b + (long long)m * g.sc_m + (long long)n * g.sc_n;
+          cplx r = cmul(g.alpha, acc[i][j]);
+          if (g.beta != 0.0) r = cadd(r, cscale(*c, g.beta));
+          *c = r;
+        }
+      }
+    }
+    if (reduce) break;
+  }
+}
+
+__global__ void zgemm_reduce_kernel(ZGemmDev g, int splits, const cplx *partial) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)g.M * g.N) return;
+  const int m = (int)(idx / g.N), n = (int)(idx % g.N);
+  cplx s = {0.0, 0.0};
+  for (int z = 0; z < splits; ++z) s = cadd(s, partial[(long long)z * g.M * g.N + idx]);
+  cplx *c = g.C + (long long)m * g.sc_m + (long long)n * g.sc_n;
+  cplx r = cmul(g.alpha, s);
+  if (g.beta != 0.0) r = cadd(r, cscale(*c, g.beta));
+  *c = r;
+}
+
+ZGemmDev to_dev(const ZGemm &g) {
+  ZGemmDev d;
+  d.M = g.M; d.N = g.N; d.K = g.K; d.batch = g.batch;
+  d.A = g.A; d.sa_b = g.sa_b; d.sa_m = g.sa_m; d.sa_k = g.sa_k;
+  d.B = g.B; d.sb_b = g.sb_b; d.sb_k = g.sb_k; d.sb_n = g.sb_n;
+  d.C = g.C; d.sc_b = g.sc_b; d.sc_m = g.sc_m; d.sc_n = g.sc_n;
+  d.alpha = g.alpha; d.beta = g.beta;
+  d.conjA = g.conjA; d.conjB = g.conjB;
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// 4-index permutation, tiled over the innermost input and output axes.
+// ---------------------------------------------------------------------------
+constexpr int PT = 32;
+
+__global__ void permute4_kernel(int nb, const cplx *__restrict__ in, cplx *__restrict__ out, int p0, int p1,
+                                int p2, int p3, cplx alpha, double beta, int conj) {
+  // out axis 3 is innermost in memory; input innermost axis is out-axis p3.
+  __shared__ cplx tile[PT][PT + 1];
+  const int ntile = (nb + PT - 1) / PT;
+  const int tA = blockIdx.x % ntile;   // tile along out axis 3
+  const int tB = blockIdx.x / ntile;   // tile along out axis p3 (when p3 != 3)
+  // the two remaining out axes
+  int rest[2], r = 0;
+  for (int d = 0; d < 3; ++d)
+    if (d != p3) rest[r++] = d;
+  // when p3 == 3 the tiles run over out axis 3 only and 'rest' holds axes 0..2 minus p3 -> handle below
+  const long long nb2 = (long long)nb * nb;
+  const int pidx[4] = {p0, p1, p2, p3};
+  if (p3 == 3) {
+    // both innermost: plain gather with a 2D grid: blockIdx.y = (a0, a1), x-tiles over (a2, a3)
+    const long long a01 = blockIdx.y;
+    const int a0 = (int)(a01 / nb), a1 = (int)(a01 % nb);
+    for (int e = threadIdx.y * blockDim.x + threadIdx.x; e < nb * nb; e += blockDim.x * blockDim.y) {
+      const int a2 = e / nb, a3 = e % nb;
+      const int a[4] = {a0, a1, a2, a3};
+      const long long src = (((long long)a[pidx[0]] * nb + a[pidx[1]]) * nb + a[pidx[2]]) * nb + a[pidx[3]];
+      const long long dst = (((long long)a0 * nb + a1) * nb + a2) * nb + a3;
+      cplx v = in[src];
+      if (conj) v.y = -v.y;
+      cplx res = cmul(alpha, v);
+      if (beta != 0.0) res = cadd(res, cscale(out[dst], beta));
+      out[dst] = res;
+    }
+    return;
+  }
+  const long long ab = blockIdx.y;   // the two remaining out axes, flattened
+  int a[4];
+  a[rest[0]] = (int)(ab / nb);
+  a[rest[1]] = (int)(ab % nb);
+  // load: threadIdx.x runs over out axis p3 (input-contiguous), threadIdx.y over out axis 3
+  for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
+    const int x3 = tA * PT + yy;
+    const int xp = tB * PT + threadIdx.x;
+    if (x3 < nb && xp < nb) {
+      a[3] = x3;
+      a[p3] = xp;
+      const long long src = (((long long)a[pidx[0]] * nb + a[pidx[1]]) * nb + a[pidx[2]]) * nb + a[pidx[3]];
+      tile[yy][threadIdx.x] = in[src];
+    }
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
+    const int xp = tB * PT + yy;
+    const int x3 = tA * PT + threadIdx.x;
+    if (x3 < nb && xp < nb) {
+      int b[4] = {a[0], a[1], a[2], a[3]};
+      b[3] = x3;
+      b[p3] = xp;
+      const long long dst = (((long long)b[0] * nb + b[1]) * nb + b[2]) * nb + b[3];
+      cplx v = tile[threadIdx.x][yy];
+      if (conj) v.y = -v.y;
+      cplx res = cmul(alpha, v);
+      if (beta != 0.0) res = cadd(res, cscale(out[dst], beta));
+      out[dst] = res;
+    }
+  }
+  (void)nb2;
+}
+
+// ---------------------------------------------------------------------------
+// Hartree-Fock build: one warp per (i, j).
+// ---------------------------------------------------------------------------
+template <bool REAL>
+__global__ void hf_build_kernel(int nb, const void *__restrict__ Wm_, const cplx *__restrict__ h,
+                                const cplx *__restrict__ D, double f, const cplx *__restrict__ n,
+                                cplx *__restrict__ hhf) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nb2 = nb * nb;
+  if (warp >= nb2) return;
+  cplx acc = {0.0, 0.0};
+  if (REAL) {
+    const double *Wm = static_cast<const double *>(Wm_) + (long long)warp * nb2;
+    for (int c = lane; c < nb2; c += 32) {
+      const double wv = Wm[c];
+      acc.x = fma(wv, n[c].x, acc.x);
+      acc.y = fma(wv, n[c].y, acc.y);
+    }
+  } else {
+    const cplx *Wm = static_cast<const cplx *>(Wm_) + (long long)warp * nb2;
+    for (int c = lane; c < nb2; c += 32) acc = cfma(Wm[c], n[c], acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) {
+    cplx r = cadd(h[warp], acc);
+    if (D) r = cadd(r, cscale(D[warp], f));
+    hhf[warp] = r;
+  }
+}
+
+__global__ void one_minus_kernel(int nb, const cplx *n, cplx *nbar) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nb * nb) return;
+  const int i = idx / nb, j = idx % nb;
+  cplx v = n[idx];
+  nbar[idx] = {(i == j ? 1.0 : 0.0) - v.x, -v.y};
+}
+
+// RK4 bookkeeping for one element with derivative k.
+__device__ __forceinline__ void rk4_apply(long long e, cplx k, int stage, double dt, cplx *y, cplx *ys, cplx *acc,
+                                          cplx *kout) {
+  if (stage < 0) {
+    kout[e] = k;
+    return;
+  }
+  const cplx y0 = y[e];
+  if (stage == 0) {
+    acc[e] = k;
+    ys[e] = {fma(0.5 * dt, k.x, y0.x), fma(0.5 * dt, k.y, y0.y)};
+  } else if (stage == 1) {
+    const cplx a = acc[e];
+    acc[e] = {fma(2.0, k.x, a.x), fma(2.0, k.y, a.y)};
+    ys[e] = {fma(0.5 * dt, k.x, y0.x), fma(0.5 * dt, k.y, y0.y)};
+  } else if (stage == 2) {
+    const cplx a = acc[e];
+    acc[e] = {fma(2.0, k.x, a.x), fma(2.0, k.y, a.y)};
+    ys[e] = {fma(dt, k.x, y0.x), fma(dt, k.y, y0.y)};
+  } else {
+    const cplx a = acc[e];
+    y[e] = {fma(dt / 6.0, a.x + k.x, y0.x), fma(dt / 6.0, a.y + k.y, y0.y)};
+  }
+}
+
+// dn = -i[hHF, n] - (I + I^dag): one thread per element, explicit sums over p.
+__global__ void g1_update_kernel(int nb, const cplx *__restrict__ hhf, const cplx *__restrict__ n,
+                                 const cplx *__restrict__ I, int stage, double dt, cplx *y, cplx *ys, cplx *acc,
+                                 cplx *kout) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nb * nb) return;
+  const int i = idx / nb, j = idx % nb;
+  cplx comm = {0.0, 0.0};
+  for (int p = 0; p < nb; ++p) {
+    comm = cfma(hhf[i * nb + p], n[p * nb + j], comm);
+    const cplx np_ = n[i * nb + p];
+    const cplx hp = hhf[p * nb + j];
+    comm = csub(comm, cmul(np_, hp));
+  }
+  cplx k = mul_minus_i(comm);
+  if (I) {
+    const cplx a = I[i * nb + j];
+    const cplx b = cconj(I[j * nb + i]);
+    k = csub(k, cadd(a, b));
+  }
+  rk4_apply(idx, k, stage, dt, y, ys, acc, kout);
+}
+
+// dG = -i (Cb - Ab + conj(Ab^T)): 32x32 tiles of the (ij),(kl) matrix view.
+__global__ void g2_assemble_kernel(int nb, const cplx *__restrict__ Cb, const cplx *__restrict__ Ab, int stage,
+                                   double dt, cplx *y, cplx *ys, cplx *acc, cplx *kout) {
+  __shared__ cplx tile[PT][PT + 1];
+  const long long M = (long long)nb * nb;
+  const long long r0 = (long long)blockIdx.y * PT, c0 = (long long)blockIdx.x * PT;
+  // load the transposed tile Ab[(c0..), (r0..)]
+  for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
+    const long long rr = c0 + yy, cc = r0 + threadIdx.x;
+    if (rr < M && cc < M) tile[yy][threadIdx.x] = Ab[rr * M + cc];
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
+    const long long r = r0 + yy, c = c0 + threadIdx.x;
+    if (r < M && c < M) {
+      const long long e = r * M + c;
+      const cplx at = cconj(tile[threadIdx.x][yy]);
+      const cplx v = cadd(csub(Cb[e], Ab[e]), at);
+      rk4_apply(e, mul_minus_i(v), stage, dt, y, ys, acc, kout);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Observables
+// ---------------------------------------------------------------------------
+__global__ void obs_one_body_kernel(int nb, const cplx *h, const cplx *D, double f, const cplx *hhf, const cplx *n,
+                                    double *red) {
+  // single block
+  __shared__ double s[4][256];
+  double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx / nb, j = idx % nb;
+    const cplx nji = n[j * nb + i];
+    cplx hij = h[idx];
+    if (D) hij = cadd(hij, cscale(D[idx], f));
+    a0 += hij.x * nji.x - hij.y * nji.y;
+    const cplx dh = csub(hhf[idx], hij);
+    a1 += dh.x * nji.x - dh.y * nji.y;
+    if (i == j) a2 += nji.x;
+    if (D) a3 += D[idx].x * nji.x - D[idx].y * nji.y;
+  }
+  s[0][threadIdx.x] = a0; s[1][threadIdx.x] = a1; s[2][threadIdx.x] = a2; s[3][threadIdx.x] = a3;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int q = 0; q < 4; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) red[threadIdx.x] = s[threadIdx.x][0];
+}
+
+// per-block partial sums of Re W[(ij),(kl)] G[(kl),(ij)] and of the non-finite count
+__global__ void obs_two_body_kernel(int nb, const cplx *__restrict__ W, const cplx *__restrict__ G,
+                                    double *partials) {
+  __shared__ cplx tile[PT][PT + 1];
+  __shared__ double s0[PT * 8], s1[PT * 8];
+  const long long M = (long long)nb * nb;
+  const long long r0 = (long long)blockIdx.y * PT, c0 = (long long)blockIdx.x * PT;
+  const int tid = threadIdx.y * PT + threadIdx.x;
+  for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
+    const long long rr = c0 + yy, cc = r0 + threadIdx.x;
+    if (rr < M && cc < M) tile[yy][threadIdx.x] = G[rr * M + cc];
+  }
+  __syncthreads();
+  double acc = 0.0, bad = 0.0;
+  for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
+    const long long r = r0 + yy, c = c0 + threadIdx.x;
+    if (r < M && c < M) {
+      const cplx w = W[r * M + c];
+      const cplx g = tile[threadIdx.x][yy];   // G[(c),(r)]
+      acc += w.x * g.x - w.y * g.y;
+      const cplx gd = G[r * M + c];
+      if (!isfinite(gd.x) || !isfinite(gd.y)) bad += 1.0;
+    }
+  }
+  s0[tid] = acc;
+  s1[tid] = bad;
+  __syncthreads();
+  for (int o = (PT * 8) / 2; o > 0; o >>= 1) {
+    if (tid < o) { s0[tid] += s0[tid + o]; s1[tid] += s1[tid + o]; }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    partials[2 * b] = s0[0];
+    partials[2 * b + 1] = s1[0];
+  }
+}
+
+__global__ void sum_pairs_kernel(const double *partials, long long nblk, double *red) {
+  __shared__ double s0[256], s1[256];
+  double a = 0, b = 0;
+  for (long long i = threadIdx.x; i < nblk; i += blockDim.x) { a += partials[2 * i]; b += partials[2 * i + 1]; }
+  s0[threadIdx.x] = a; s1[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) { s0[threadIdx.x] += s0[threadIdx.x + o]; s1[threadIdx.x] += s1[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { red[0] = s0[0]; red[1] = s1[0]; }
+}
+
+__global__ void accumulate_work_kernel(int nb, const cplx *D, const cplx *n, double coeff, double *W) {
+  __shared__ double s[256];
+  double a = 0;
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx / nb, j = idx % nb;
+    const cplx nji = n[j * nb + i];
+    a += D[idx].x * nji.x - D[idx].y * nji.y;
+  }
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *W += coeff * s[0];
+}
+
+__global__ void double_occ_kernel(int nb, const cplx *n, const cplx *G, double *out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nb / 2) return;
+  const int u = 2 * s, d = 2 * s + 1;
+  const long long nb_ = nb;
+  const cplx nuu = n[u * nb + u], ndd = n[d * nb + d], nud = n[u * nb + d], ndu = n[d * nb + u];
+  const cplx g = G[((u * nb_ + d) * nb_ + u) * nb_ + d];
+  const cplx prod = csub(cmul(nuu, ndd), cmul(nud, ndu));
+  out[s] = prod.x - g.x;
+}
+
+__global__ void count_nonfinite_kernel(const cplx *x, long long len, double *cnt) {
+  __shared__ double s[256];
+  double a = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[i].x) || !isfinite(x[i].y)) a += 1.0;
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && s[0] != 0.0) atomicAdd(cnt, s[0]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+void zgemm(Launcher &L, const ZGemm &g) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, std::min(g.batch, 65535));
+  zgemm_kernel<<<grid, GNT, 0, L.stream>>>(to_dev(g), 0, 1, nullptr);
+  L.after_launch();
+}
+
+void zgemm_reduce(Launcher &L, const ZGemm &g, cplx *partial, int splits) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  splits = std::max(1, std::min(splits, g.batch));
+  const int per = (g.batch + splits - 1) / splits;
+  splits = (g.batch + per - 1) / per;
+  dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, splits);
+  zgemm_kernel<<<grid, GNT, 0, L.stream>>>(to_dev(g), 1, per, partial);
+  L.after_launch();
+  const long long mn = (long long)g.M * g.N;
+  zgemm_reduce_kernel<<<(unsigned)((mn + 255) / 256), 256, 0, L.stream>>>(to_dev(g), splits, partial);
+  L.after_launch();
+}
+
+void permute4(Launcher &L, int nb, const cplx *in, cplx *out, const int p[4], cplx alpha, double beta, bool conj) {
+  const int nt = (nb + PT - 1) / PT;
+  dim3 block(PT, 8);
+  if (p[3] == 3) {
+    dim3 grid(1, (unsigned)((long long)nb * nb));
+    permute4_kernel<<<grid, block, 0, L.stream>>>(nb, in, out, p[0], p[1], p[2], p[3], alpha, beta, conj);
+  } else {
+    dim3 grid(nt * nt, (unsigned)((long long)nb * nb));
+    permute4_kernel<<<grid, block, 0, L.stream>>>(nb, in, out, p[0], p[1], p[2], p[3], alpha, beta, conj);
+  }
+  L.after_launch();
+}
+
+void hf_build(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *h, const cplx *D, double f,
+              const cplx *n, cplx *hhf) {
+  const int warps = nb * nb;
+  const int threads = 256;
+  const int blocks = (warps * 32 + threads - 1) / threads;
+  if (wm_real)
+    hf_build_kernel<true><<<blocks, threads, 0, L.stream>>>(nb, Wm, h, D, f, n, hhf);
+  else
+    hf_build_kernel<false><<<blocks, threads, 0, L.stream>>>(nb, Wm, h, D, f, n, hhf);
+  L.after_launch();
+}
+
+void one_minus(Launcher &L, int nb, const cplx *n, cplx *nbar) {
+  one_minus_kernel<<<(nb * nb + 255) / 256, 256, 0, L.stream>>>(nb, n, nbar);
+  L.after_launch();
+}
+
+void g1_update(Launcher &L, int nb, const cplx *hhf, const cplx *n, const cplx *I, Rk4Stage st, cplx *y, cplx *ys,
+               cplx *acc, cplx *kout) {
+  g1_update_kernel<<<(nb * nb + 127) / 128, 128, 0, L.stream>>>(nb, hhf, n, I, st.stage, st.dt, y, ys, acc, kout);
+  L.after_launch();
+}
+
+void g2_assemble(Launcher &L, int nb, const cplx *Cb, const cplx *Ab, Rk4Stage st, cplx *y, cplx *ys, cplx *acc,
+                 cplx *kout) {
+  const long long M = (long long)nb * nb;
+  const unsigned t = (unsigned)((M + PT - 1) / PT);
+  g2_assemble_kernel<<<dim3(t, t), dim3(PT, 8), 0, L.stream>>>(nb, Cb, Ab, st.stage, st.dt, y, ys, acc, kout);
+  L.after_launch();
+}
+
+void obs_one_body(Launcher &L, int nb, const cplx *h, const cplx *D, double f, const cplx *hhf, const cplx *n,
+                  double *red) {
+  obs_one_body_kernel<<<1, 256, 0, L.stream>>>(nb, h, D, f, hhf, n, red);
+  L.after_launch();
+}
+
+void obs_two_body(Launcher &L, int nb, const cplx *W, const cplx *G, double *partials, double *red) {
+  const long long M = (long long)nb * nb;
+  const unsigned t = (unsigned)((M + PT - 1) / PT);
+  obs_two_body_kernel<<<dim3(t, t), dim3(PT, 8), 0, L.stream>>>(nb, W, G, partials);
+  L.after_launch();
+  sum_pairs_kernel<<<1, 256, 0, L.stream>>>(partials, (long long)t * t, red);
+  L.after_launch();
+}
+
+void accumulate_work(Launcher &L, int nb, const cplx *D, const cplx *n, double coeff, double *W_acc) {
+  accumulate_work_kernel<<<1, 256, 0, L.stream>>>(nb, D, n, coeff, W_acc);
+  L.after_launch();
+}
+
+void double_occ(Launcher &L, int nb, const cplx *n, const cplx *G, double *out) {
+  double_occ_kernel<<<(nb / 2 + 63) / 64, 64, 0, L.stream>>>(nb, n, G, out);
+  L.after_launch();
+}
+
+void count_nonfinite(Launcher &L, const cplx *x, long long len, double *cnt) {
+  const unsigned blocks = (unsigned)std::min<long long>((len + 255) / 256, 4096);
+  count_nonfinite_kernel<<<blocks, 256, 0, L.stream>>>(x, len, cnt);
+  L.after_launch();
+}
+
+}  // namespace g1g2

@@ -1,0 +1,81 @@
+// Internal declarations of libg1g2 (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/g1g2.h"
+
+namespace g1g2 {
+
+using cplx = double2;  // interleaved (re, im), the layout of the ABI
+
+// ---------------------------------------------------------------------------
+// Launch bookkeeping: every kernel launch goes through one of these so that a
+// failed launch is turned into G1G2_ECUDA and counted.
+// ---------------------------------------------------------------------------
+struct Launcher {
+  cudaStream_t stream = nullptr;
+  long long *counter = nullptr;
+  cudaError_t err = cudaSuccess;
+  void after_launch() {
+    if (counter) ++*counter;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+  }
+};
+
+// Generic strided complex FP64 GEMM, batched:
+//   C_b[m][n] = alpha * sum_k opA(A_b[m][k]) * opB(B_b[k][n]) + beta * C_b[m][n]
+// (reduce = false), or C[m][n] = alpha * sum_b sum_k ... + beta * C (reduce = true).
+struct ZGemm {
+  int M = 0, N = 0, K = 0, batch = 1;
+  const cplx *A = nullptr; long long sa_b = 0, sa_m = 0, sa_k = 0;
+  const cplx *B = nullptr; long long sb_b = 0, sb_k = 0, sb_n = 0;
+  cplx *C = nullptr;       long long sc_b = 0, sc_m = 0, sc_n = 0;
+  cplx alpha{1.0, 0.0};
+  double beta = 0.0;
+  bool conjA = false, conjB = false;
+};
+void zgemm(Launcher &L, const ZGemm &g);
+void zgemm_reduce(Launcher &L, const ZGemm &g, cplx *partial, int splits);
+
+// out(a0,a1,a2,a3) = beta*out + alpha*op(in(a_p0, a_p1, a_p2, a_p3)), op = conj if conj.
+void permute4(Launcher &L, int nb, const cplx *in, cplx *out, const int p[4], cplx alpha, double beta,
+              bool conj);
+
+// hHF = h + f D + Wm * vec(n), Wm[(ij),(lk)] (real or complex), Eq. (h_HF).
+void hf_build(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *h, const cplx *D, double f,
+              const cplx *n, cplx *hhf);
+// nbar = 1 - n
+void one_minus(Launcher &L, int nb, const cplx *n, cplx *nbar);
+
+// RK4 stage bookkeeping shared by the G1 and G2 updates.
+struct Rk4Stage {
+  int stage = -1;      // -1: write k to kout; 0..3: classical RK4 stage
+  double dt = 0.0;
+};
+// dn = -i[hHF, n] - (I + I^dag) (I may be null); then the RK4 update of (y, ys, acc)
+// or a plain write of dn to kout.
+void g1_update(Launcher &L, int nb, const cplx *hhf, const cplx *n, const cplx *I, Rk4Stage st,
+               cplx *y, cplx *ys, cplx *acc, cplx *kout);
+// dG = -i (Cb - Ab + conj(Ab^T)) with ^T the (ij)<->(kl) transpose; RK4 update or write k.
+void g2_assemble(Launcher &L, int nb, const cplx *Cb, const cplx *Ab, Rk4Stage st, cplx *y, cplx *ys,
+                 cplx *acc, cplx *kout);
+
+// Observables.
+// red[0..] = {Re Tr(h n), Re Tr((hHF-h(t)) n), Re Tr n, Re Tr(D n)} for state n;
+void obs_one_body(Launcher &L, int nb, const cplx *h, const cplx *D, double f, const cplx *hhf,
+                  const cplx *n, double *red);
+// red[0] = Re sum W[(ij),(kl)] G[(kl),(ij)], red[1] = count of non-finite entries of G.
+void obs_two_body(Launcher &L, int nb, const cplx *W, const cplx *G, double *partials, double *red);
+// W_acc += coeff * Re Tr(D n)
+void accumulate_work(Launcher &L, int nb, const cplx *D, const cplx *n, double coeff, double *W_acc);
+// out[s] = double occupancy of site s (spin-orbital index 2 s + spin).
+void double_occ(Launcher &L, int nb, const cplx *n, const cplx *G, double *out);
+// count non-finite entries of x (length len) into *cnt (double, accumulated)
+void count_nonfinite(Launcher &L, const cplx *x, long long len, double *cnt);
+
+}  // namespace g1g2

@@ -1,0 +1,21 @@
+// Split-precision tensor-core form of the G1-G2 right-hand side (internal).
+#pragma once
+
+#include "g1g2_internal.h"
+
+namespace g1g2 {
+
+struct TcPath;
+
+// Build the tensor-core path for one context. hw: w (complex, [(ij),(kl)]),
+// hsrc: source-term interaction (w^- for SOA in a spin-orbital basis, else w).
+int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, const cplx *hsrc,
+              cudaStream_t stream);
+void tc_destroy(TcPath *p);
+
+// One right-hand side (hhf already built from n_in): collision integral and
+// G1 update, then the G2 contractions and the assembly with the RK4 update.
+void tc_rhs(TcPath *p, Launcher &L, const cplx *n_in, const cplx *G_in, const cplx *hhf, Rk4Stage st,
+            cplx *ny, cplx *nys, cplx *nacc, cplx *nk, cplx *Gy, cplx *Gys, cplx *Gacc, cplx *Gk);
+
+}  // namespace g1g2

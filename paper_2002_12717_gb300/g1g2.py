@@ -1,0 +1,209 @@
+"""Thin ctypes binding of libg1g2 (include/g1g2.h): argument marshalling only.
+
+Every step of the propagation runs in the CUDA library; nothing here computes
+any part of the G1-G2 equations.  Host arrays are numpy (complex128, or
+float64 for a real w); device arrays for `rhs` are torch CUDA tensors of
+dtype complex128 (interleaved re/im doubles, the ABI layout).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libg1g2.so")
+
+OK, EINVAL, ESYMM, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+SELFENERGY = {"HF": 0, "SOA": 1, "GW": 2}
+PRECISION = {"fp64": 0, "tf32x3": 1}
+
+
+class G1G2Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(msg)
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("basis", ctypes.c_int), ("w_is_real", ctypes.c_int),
+                ("sym_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("n_particles", ctypes.c_double), ("e_one", ctypes.c_double),
+                ("e_hf", ctypes.c_double), ("e_corr", ctypes.c_double), ("e_total", ctypes.c_double),
+                ("pulse_work", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def load():
+    """Load libg1g2.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libg1g2.so not found at {LIB_PATH}: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    sig = {
+        "g1g2_default_options": (None, [ctypes.POINTER(Options)]),
+        "g1g2_init": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int,
+                                     ctypes.POINTER(Options)]),
+        "g1g2_set_drive": (ctypes.c_int, [vp, _dp, ctypes.c_int, _dp, ctypes.c_int]),
+        "g1g2_rhs": (ctypes.c_int, [vp, ctypes.c_double, vp, vp, vp, vp]),
+        "g1g2_step": (ctypes.c_int, [vp, ctypes.c_double]),
+        "g1g2_propagate": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Obs), _dp]),
+        "g1g2_observables": (ctypes.c_int, [vp, ctypes.POINTER(Obs), _dp, _dp]),
+        "g1g2_get_state": (ctypes.c_int, [vp, _dp, _dp, _dp]),
+        "g1g2_set_state": (ctypes.c_int, [vp, ctypes.c_double, _dp, _dp]),
+        "g1g2_launch_count": (ctypes.c_longlong, [vp]),
+        "g1g2_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "g1g2_last_error_detail": (ctypes.c_char_p, []),
+        "g1g2_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != OK:
+        lib = load()
+        raise G1G2Error(rc, f"{lib.g1g2_strerror(rc).decode()}: {lib.g1g2_last_error_detail().decode()}")
+
+
+def _cptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+class Propagator:
+    """One g1g2_ctx: state (G1 = n, G2), RK4 stepping, observables."""
+
+    def __init__(self, h, w, n0, G2_0=None, selfenergy="SOA", precision="fp64", restricted=False,
+                 sym_tol=1e-10, stream=None):
+        lib = load()
+        self.nb = int(np.asarray(h).shape[0])
+        self.restricted = restricted
+        self.selfenergy = selfenergy
+        opt = Options()
+        lib.g1g2_default_options(ctypes.byref(opt))
+        opt.precision = PRECISION[precision]
+        opt.basis = 1 if restricted else 0
+        opt.sym_tol = sym_tol
+        opt.cuda_stream = stream
+        w = np.asarray(w)
+        if np.isrealobj(w):
+            wbuf = np.ascontiguousarray(w, dtype=np.float64)
+            opt.w_is_real = 1
+        else:
+            wbuf = _c128(w)
+        hb, nbuf = _c128(h), _c128(n0)
+        gbuf = None if G2_0 is None else _c128(G2_0)
+        ctx = ctypes.c_void_p()
+        rc = lib.g1g2_init(ctypes.byref(ctx), self.nb, _cptr(hb), _cptr(wbuf), _cptr(nbuf),
+                           None if gbuf is None else _cptr(gbuf), SELFENERGY[selfenergy], ctypes.byref(opt))
+        _check(rc)
+        self._ctx = ctx
+        self._lib = lib
+
+    # -- lifecycle -------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.g1g2_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls -----------------------------------------------------------
+    def set_drive(self, D, drive):
+        """h(t) = h + f(t) D; `drive` has .kind (1 gauss-sine, 2 piecewise linear) and .params."""
+        if drive is None or D is None:
+            _check(self._lib.g1g2_set_drive(self._ctx, None, 0, None, 0))
+            return
+        db = _c128(D)
+        params = np.ascontiguousarray(drive.params, dtype=np.float64)
+        _check(self._lib.g1g2_set_drive(self._ctx, _cptr(db), int(drive.kind), _cptr(params), len(params)))
+
+    def rhs(self, t, n_dev, G2_dev, dn_dev, dG2_dev):
+        """dn/dt and dG2/dt at (t, n, G2) into caller-owned device tensors (complex128, contiguous)."""
+        for x in (n_dev, G2_dev, dn_dev, dG2_dev):
+            if x is not None and not x.is_contiguous():
+                raise ValueError("device tensors must be contiguous")
+        ptr = lambda x: None if x is None else ctypes.c_void_p(x.data_ptr())
+        _check(self._lib.g1g2_rhs(self._ctx, float(t), ptr(n_dev), ptr(G2_dev), ptr(dn_dev), ptr(dG2_dev)))
+
+    def step(self, dt):
+        _check(self._lib.g1g2_step(self._ctx, float(dt)))
+
+    def propagate(self, dt, nsteps, obs_every=0):
+        """Run nsteps RK4 steps; returns (list of observable dicts, density array) when obs_every > 0."""
+        if obs_every <= 0:
+            _check(self._lib.g1g2_propagate(self._ctx, float(dt), int(nsteps), 0, None, None))
+            return [], None
+        nrec = 1 + nsteps // obs_every
+        obs = (Obs * nrec)()
+        dens = np.zeros((nrec, self.nb))
+        _check(self._lib.g1g2_propagate(self._ctx, float(dt), int(nsteps), int(obs_every), obs, _cptr(dens)))
+        return [o.as_dict() for o in obs], dens
+
+    def observables(self, double_occ=False):
+        o = Obs()
+        dens = np.zeros(self.nb)
+        docc = np.zeros(self.nb // 2) if double_occ else None
+        _check(self._lib.g1g2_observables(self._ctx, ctypes.byref(o), _cptr(dens),
+                                          None if docc is None else _cptr(docc)))
+        d = o.as_dict()
+        d["density"] = dens
+        if double_occ:
+            d["double_occ"] = docc
+        return d
+
+    def get_state(self, with_g2=True):
+        t = ctypes.c_double()
+        n = np.zeros((self.nb, self.nb), dtype=np.complex128)
+        g = np.zeros((self.nb,) * 4, dtype=np.complex128) if with_g2 else None
+        _check(self._lib.g1g2_get_state(self._ctx, ctypes.byref(t), _cptr(n), None if g is None else _cptr(g)))
+        return t.value, n, g
+
+    def set_state(self, t, n, G2=None):
+        nb_ = _c128(n)
+        gb = None if G2 is None else _c128(G2)
+        _check(self._lib.g1g2_set_state(self._ctx, float(t), _cptr(nb_), None if gb is None else _cptr(gb)))
+
+    @property
+    def launch_count(self):
+        return int(self._lib.g1g2_launch_count(self._ctx))
+
+
+def from_workload(d, precision="fp64", stream=None):
+    """Propagator for a workload dict of paper_2002_12717_gb300.inputs."""
+    p = Propagator(d["h"], d["w"], d["n0"], d.get("G2_0"), selfenergy=d["selfenergy"], precision=precision,
+                   restricted=d["restricted"], stream=stream)
+    if d.get("D") is not None:
+        p.set_drive(d["D"], d["drive"])
+    return p

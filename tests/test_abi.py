@@ -1,0 +1,115 @@
+"""The C-ABI library: it loads, exports every symbol include/g1g2.h declares, and
+rejects bad arguments before touching a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2002_12717_gb300 import g1g2, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "g1g2.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(g1g2_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(g1g2.LIB_PATH):
+        from paper_2002_12717_gb300 import build
+        build.build()
+    return g1g2.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_strerror_and_defaults(lib):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert lib.g1g2_strerror(code)
+    assert b"unknown" in lib.g1g2_strerror(42)
+    opt = g1g2.Options()
+    lib.g1g2_default_options(ctypes.byref(opt))
+    assert opt.precision == 0 and opt.basis == 0 and opt.sym_tol == pytest.approx(1e-10)
+
+
+def _init(lib, nb, h, w, n0, se=1, opt=None, g2=None):
+    ctx = ctypes.c_void_p()
+    o = g1g2.Options()
+    lib.g1g2_default_options(ctypes.byref(o))
+    if opt:
+        for k, v in opt.items():
+            setattr(o, k, v)
+    ptr = lambda a: None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return lib.g1g2_init(ctypes.byref(ctx), nb, ptr(h), ptr(w), ptr(n0), ptr(g2), se, ctypes.byref(o))
+
+
+def _valid(nb):
+    rng = np.random.default_rng(0)
+    h = inputs.random_hermitian(nb, rng)
+    w = inputs.factor_w(nb, 3, rng).astype(np.complex128)
+    n0 = inputs.lowest_projector(h, 1)
+    return h, w, n0
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    h, w, n0 = _valid(3)
+    assert _init(lib, 0, h, w, n0) == g1g2.EINVAL
+    assert _init(lib, 129, h, w, n0) == g1g2.EINVAL
+    assert _init(lib, 3, None, w, n0) == g1g2.EINVAL
+    assert _init(lib, 3, h, None, n0) == g1g2.EINVAL
+    assert _init(lib, 3, h, w, None) == g1g2.EINVAL
+    assert _init(lib, 3, h, w, n0, se=7) == g1g2.EINVAL
+    assert _init(lib, 3, h, w, n0, opt={"precision": 9}) == g1g2.EINVAL
+    assert _init(lib, 3, h, w, n0, opt={"basis": 5}) == g1g2.EINVAL
+    assert _init(lib, 3, h, w, n0, se=2, opt={"basis": 1}) == g1g2.EINVAL   # GW has no restricted form
+    assert b"restricted" in lib.g1g2_last_error_detail()
+
+
+def test_symmetry_violations_rejected_on_host(lib):
+    h, w, n0 = _valid(3)
+    bad = w.copy()
+    bad[0, 1, 2, 0] += 0.1                       # breaks w_ijkl = w_jilk
+    assert _init(lib, 3, h, bad, n0) == g1g2.ESYMM
+    bad = w.copy()
+    bad[0, 1, 0, 2] += 0.1j                      # breaks w_ijkl = conj(w_klij)
+    bad[1, 0, 2, 0] += 0.1j
+    assert _init(lib, 3, h, bad, n0) == g1g2.ESYMM
+    hb = h.copy()
+    hb[0, 1] += 0.3
+    assert _init(lib, 3, hb, w, n0) == g1g2.ESYMM
+    nb_ = n0.copy()
+    nb_[0, 2] += 0.3j
+    assert _init(lib, 3, h, w, nb_) == g1g2.ESYMM
+    g2 = np.zeros((3,) * 4, dtype=np.complex128)
+    g2[0, 1, 2, 2] = 0.5
+    assert _init(lib, 3, h, w, n0, g2=g2) == g1g2.ESYMM
+
+
+def test_null_context_calls(lib):
+    assert lib.g1g2_step(None, 0.1) == g1g2.EINVAL
+    assert lib.g1g2_rhs(None, 0.0, None, None, None, None) == g1g2.EINVAL
+    assert lib.g1g2_propagate(None, 0.1, 1, 1, None, None) == g1g2.EINVAL
+    assert lib.g1g2_observables(None, None, None, None) == g1g2.EINVAL
+    assert lib.g1g2_get_state(None, None, None, None) == g1g2.EINVAL
+    assert lib.g1g2_set_state(None, 0.0, None, None) == g1g2.EINVAL
+    assert lib.g1g2_set_drive(None, None, 1, None, 0) == g1g2.EINVAL
+    assert lib.g1g2_launch_count(None) == -1
+    lib.g1g2_destroy(None)
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(g1g2, "_lib", None)
+    monkeypatch.setattr(g1g2, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not found"):
+        g1g2.load()

@@ -1,0 +1,121 @@
+"""Parity of the plain FP64 GPU form with the CPU oracle, element by element."""
+import numpy as np
+import pytest
+
+from oracle import g1g2_oracle as O
+from paper_2002_12717_gb300 import inputs
+
+from .helpers import problem, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-12   # FP64 contractions of length <= nb^2 on O(1) data
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
+
+
+def run_rhs(prop, t, n, g2):
+    nb = n.shape[0]
+    dn = torch.zeros((nb, nb), dtype=torch.complex128, device="cuda")
+    dg = torch.zeros((nb,) * 4, dtype=torch.complex128, device="cuda")
+    prop.rhs(t, gpu(n), gpu(g2), dn, dg)
+    torch.cuda.synchronize()
+    return dn.cpu().numpy(), dg.cpu().numpy()
+
+
+CASES = [
+    ("HF", 5, False, False), ("SOA", 1, False, False), ("SOA", 2, False, False), ("SOA", 5, False, True),
+    ("SOA", 17, False, False), ("SOA", 33, False, False), ("SOA", 8, True, False), ("SOA", 13, True, False),
+    ("GW", 2, False, False), ("GW", 7, False, True), ("GW", 17, False, False), ("GW", 33, False, False),
+]
+
+
+@pytest.mark.parametrize("se,nb,restricted,complex_w", CASES)
+def test_rhs_parity(se, nb, restricted, complex_w):
+    from paper_2002_12717_gb300.g1g2 import Propagator
+    h, w, n, g2, D, drv = problem(nb, se, restricted, complex_w, seed=nb)
+    prob = O.Problem(h, w, se, restricted, D, drv.f)
+    t = 0.7
+    dn_ref, dg_ref = O.rhs(prob, t, n, g2)
+    with Propagator(h, w, n, None, se, "fp64", restricted) as p:
+        p.set_drive(D, drv)
+        dn, dg = run_rhs(p, t, n, g2)
+    assert rel_err(dn, dn_ref) < TOL_FP64
+    if se == "HF":
+        assert np.abs(dg).max() == 0.0
+    else:
+        assert rel_err(dg, dg_ref) < TOL_FP64
+
+
+def test_hubbard_chain_full_run_matches_oracle():
+    """8-site restricted Hubbard chain, quench, 500 RK4 steps, observables every step."""
+    from paper_2002_12717_gb300.g1g2 import from_workload
+    d = inputs.workload("hubbard-chain-nb8")
+    prob = O.Problem(d["h"], d["w"], "SOA", True)
+    _, _, _, obs_ref = O.propagate(prob, d["n0"], np.zeros((8,) * 4), d["dt"], d["nsteps"])
+    with from_workload(d) as p:
+        obs, dens = p.propagate(d["dt"], d["nsteps"], 1)
+    e_ref = np.array([o["e_total"] for o in obs_ref])
+    e = np.array([o["e_total"] for o in obs])
+    d_ref = np.array([o["density"] for o in obs_ref])
+    assert np.abs(dens - d_ref).max() < 1e-11
+    assert np.abs(e - e_ref).max() < 1e-11
+    assert abs(e[-1] - e[0]) < 1e-6                     # energy conserved after the quench
+    assert np.abs(np.array([o["n_particles"] for o in obs]) - 8.0).max() < 1e-12
+
+
+@pytest.mark.parametrize("se", ["SOA", "GW"])
+def test_propagation_with_pulse_matches_oracle(se):
+    """General basis nb=12 with the gauss-sine pulse: state, energies and drive work."""
+    from paper_2002_12717_gb300.g1g2 import Propagator
+    nb = 12
+    d = inputs.general_basis(nb, 24, 6, seed=9, selfenergy=se, pulse=True)
+    d["drive"] = inputs.GaussSine(A=0.5, omega=1.5, t0=0.3, sigma=0.2)
+    prob = O.Problem(d["h"], d["w"], se, False, d["D"], d["drive"].f)
+    dt, steps = 0.01, 60
+    n_ref, g_ref, _, obs_ref = O.propagate(prob, d["n0"], np.zeros((nb,) * 4), dt, steps, obs_every=20,
+                                           dfdt=d["drive"].dfdt)
+    with Propagator(d["h"], d["w"], d["n0"], None, se) as p:
+        p.set_drive(d["D"], d["drive"])
+        obs, dens = p.propagate(dt, steps, 20)
+        _, n, g = p.get_state()
+    assert rel_err(n, n_ref) < 1e-11
+    assert rel_err(g, g_ref) < 1e-10
+    for a, b in zip(obs, obs_ref):
+        for k in ("e_one", "e_hf", "e_corr", "e_total", "n_particles", "pulse_work"):
+            assert abs(a[k] - b[k]) < 1e-11, k
+    assert abs(obs[-1]["pulse_work"]) > 1e-4
+
+
+def test_double_occupancy_and_energies_spin_orbital():
+    from paper_2002_12717_gb300.g1g2 import Propagator
+    L = 3
+    nb = 2 * L
+    rng = np.random.default_rng(4)
+    h = inputs.spin_orbital_h(inputs.chain_hopping(L))
+    w = inputs.spin_orbital_hubbard_w(L, 2.0)
+    n, g2 = inputs.random_state(nb, rng, soa=True)
+    with Propagator(h, w, n, g2, "SOA") as p:
+        o = p.observables(double_occ=True)
+    ref = O.energies(O.Problem(h, w), 0.0, n, g2)
+    for k in ("e_one", "e_hf", "e_corr", "e_total", "n_particles"):
+        assert abs(o[k] - ref[k]) < 1e-12
+    assert np.abs(o["double_occ"] - O.double_occupancy(n, g2, L)).max() < 1e-12
+
+
+def test_state_roundtrip_and_launch_count():
+    from paper_2002_12717_gb300.g1g2 import Propagator
+    h, w, n, g2, _, _ = problem(6, "SOA", seed=3, drive=False)
+    with Propagator(h, w, n, g2, "SOA") as p:
+        t, n1, g1 = p.get_state()
+        assert t == 0.0 and np.array_equal(n1, n) and np.array_equal(g1, g2)
+        c0 = p.launch_count
+        p.step(0.01)
+        torch.cuda.synchronize()
+        assert p.launch_count > c0
+        p.set_state(2.5, n, None)
+        t, n2, gz = p.get_state()
+        assert t == 2.5 and np.abs(gz).max() == 0.0
