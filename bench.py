@@ -1,0 +1,346 @@
+"""Throughput of the G1-G2 RK4 propagation on GB300.
+
+One bench "step" is one RK4 step of each of the two workloads the metric names,
+back to back: the general-basis SOA system at nb = 96 and the general-basis GW
+system at nb = 64 (seeded h, w = Σ_P L^P ⊗ L^P, gauss-sine pulse; the
+`inputs` module).  Together they run every stage of the right-hand side (HF
+build, collision integral, two-particle commutator, source term, GW
+quasi-Hamiltonian and polarisation, assembly + RK4, observables).
+value = bench steps per second = 1 / (t_SOA96 + t_GW64).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32x3|fp64]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+With N > 1 (torchrun) every rank runs an independent replica of the same
+propagation on its own GPU (the method has no data-parallel split without an
+exchange step that is not built); value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2002_12717_gb300 import inputs  # noqa: E402
+
+METRIC = "G1-G2 RK4 steps/s (one step = SOA nb=96 + GW nb=64)"
+WORKLOADS = ("general-soa-nb96", "general-gw-nb64")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 (DFMA) throughput of one GB300, measured with a dependent-free DFMA loop over
+# all SMs (profiles/fp64_dfma_peak.md); used as the ALU roofline of the FP64 form.
+FP64_PEAK_TFLOPS = 1.200
+FP64_PEAK_NOTE = "profiles/fp64_dfma_peak.md"
+# nominal dense tensor ratio TF32 / BF16 (1.1 / 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def load_peaks():
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per launch of each kernel family (8 real flops per complex MAC)
+# ---------------------------------------------------------------------------
+
+def algorithmic_flops(nb, se, stage_launches):
+    """Complex MACs of the contraction launches of one RK4 step, by kernel tag.
+
+    Per right-hand side: collision integral nb^5, commutator 4 nb^5, source term
+    4 nb^5 (two fused-free mode products each side), GW: quasi-Hamiltonian 2 nb^5
+    and polarisation nb^6.
+    """
+    n5 = nb ** 5
+    per_rhs = 9 * n5 + (2 * n5 + nb ** 6 if se == "GW" else 0)
+    return 8.0 * per_rhs * 4
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2002_12717_gb300.g1g2 import from_workload
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    peaks, peak_kind = load_peaks()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    per = {}
+    prof_all = {}
+    launches_total = 0
+    clocks = ClockSampler(dev)
+    for name in args.workloads:
+        d = inputs.workload(name)
+        prop = from_workload(d, precision=args.precision)
+        dt = d["dt"]
+        prop.propagate(dt, args.warmup)          # warm-up steps (untimed)
+        torch.cuda.synchronize()
+        barrier()
+        prop.profile(True)
+        c0 = prop.launch_count
+        if not per:
+            clocks.start()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record()
+        for _ in range(args.steps):
+            prop.step(dt)
+        end.record()
+        torch.cuda.synchronize()
+        ms = start.elapsed_time(end) / args.steps
+        launches = prop.launch_count - c0
+        launches_total += launches
+        rep = prop.profile_report()
+        prop.profile(False)
+        for k, (n_l, t_ms) in rep.items():
+            a = prof_all.setdefault(k, [0, 0.0, 0.0])
+            a[0] += n_l
+            a[1] += t_ms
+        # algorithmic flops of the contraction kernels of this workload
+        per[name] = {"nb": d["nb"], "selfenergy": d["selfenergy"], "ms_per_step": ms, "launches": launches,
+                     "flops_per_step": algorithmic_flops(d["nb"], d["selfenergy"], None), "dt": dt}
+        # end-to-end through the public API: state from pinned host memory, K steps,
+        # observables (energies + density) copied back after every step
+        n0 = torch.from_numpy(np.ascontiguousarray(d["n0"])).pin_memory().numpy()
+        g0 = torch.zeros((d["nb"],) * 4, dtype=torch.complex128).pin_memory().numpy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prop.set_state(0.0, n0, g0)
+        obs, _ = prop.propagate(dt, args.steps, 1)
+        e2e_s = time.perf_counter() - t0
+        per[name]["e2e_ms_per_step"] = 1e3 * e2e_s / args.steps
+        per[name]["h2d_bytes"] = n0.nbytes + g0.nbytes
+        per[name]["d2h_bytes_per_step"] = 56 + 16 * d["nb"]
+        per[name]["energy_drift_rel"] = abs(obs[-1]["e_total"] - obs[0]["e_total"] - obs[-1]["pulse_work"]) / abs(
+            obs[0]["e_total"])
+        prop.close()
+        del prop
+        torch.cuda.empty_cache()
+        barrier()
+    clk = clocks.stop()
+
+    step_ms = sum(p["ms_per_step"] for p in per.values())
+    if dist is not None:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = world * 1e3 / step_ms
+    e2e_ms = sum(p["e2e_ms_per_step"] for p in per.values())
+    e2e_value = world * 1e3 / e2e_ms
+
+    # roofline of the dominant kernel (largest share of device time)
+    dom = max(prof_all.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_launches, dom_ms, _) = dom
+    total_flops = sum(p["flops_per_step"] * args.steps for p in per.values())
+    contraction_tags = [k for k in prof_all if "zgemm" in k or k.startswith("tc_")]
+    contraction_ms = sum(prof_all[k][1] for k in contraction_tags)
+    if args.precision == "fp64":
+        achieved = total_flops / (contraction_ms * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if peak else None, "traffic": None,
+                "kernel": "fp64_zgemm (+ fp64_zgemm_splitk): all complex contractions",
+                "peak_source": FP64_PEAK_NOTE, "kernel_share": contraction_ms / sum(v[1] for v in prof_all.values())}
+    else:
+        achieved = total_flops / (contraction_ms * 1e-3) / 1e12
+        peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": ",".join(sorted(contraction_tags)),
+                "peak_source": f"{peak_kind} bf16 sustained x TF32/BF16 nominal ratio"}
+    roof["dominant_kernel"] = dom_name
+    roof["dominant_share"] = dom_ms / sum(v[1] for v in prof_all.values())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "tf32x3+f64",
+        "data": "synthetic (seeded general basis: h Hermitian Gaussian, w = sum_P L^P x L^P, gauss-sine pulse)",
+        "config": {"workload": "+".join(args.workloads), "precision": args.precision,
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "inputs larger than L2 (G2 state 1.36 GB at nb=96, 268 MB at nb=64)",
+                   "parts": {k: {kk: vv for kk, vv in v.items()} for k, v in per.items()}},
+        "e2e": {"value": e2e_value, "unit": "steps/s",
+                "h2d_bytes_per_step": sum(p["h2d_bytes"] for p in per.values()) / args.steps,
+                "d2h_bytes_per_step": sum(p["d2h_bytes_per_step"] for p in per.values()),
+                "how": "g1g2_set_state from pinned host + g1g2_propagate(K, observables every step)"},
+        "gpu_launches": launches_total,
+        "roofline": roof,
+        "clocks": clk,
+        "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1][1])},
+    }
+    return line
+
+
+def cpu_baseline(args):
+    """The CPU oracle as it stands, one right-hand side of each workload (bounded sample)."""
+    from oracle import g1g2_oracle as O
+
+    times = {}
+    for name in args.workloads:
+        d = inputs.workload(name)
+        prob = O.Problem(d["h"], d["w"], d["selfenergy"], d["restricted"], d["D"], d["drive"].f)
+        g0 = np.zeros((d["nb"],) * 4, dtype=np.complex128)
+        t0 = time.perf_counter()
+        O.rhs(prob, 0.0, d["n0"], g0)
+        times[name] = time.perf_counter() - t0
+    step_s = 4 * sum(times.values())   # an RK4 step is four right-hand sides
+    return {"value": 1.0 / step_s, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one right-hand side per workload (" + ", ".join(f"{k}: {v:.1f} s" for k, v in times.items())
+                      + "); RK4 step = 4 x the sum"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, alternating one RHS of each workload per step."""
+    from oracle import g1g2_oracle as O
+
+    probs = []
+    for name in args.workloads:
+        d = inputs.workload(name)
+        probs.append((name, O.Problem(d["h"], d["w"], d["selfenergy"], d["restricted"], d["D"], d["drive"].f),
+                      d["n0"], np.zeros((d["nb"],) * 4, dtype=np.complex128)))
+    times = {name: [] for name, *_ in probs}
+    warm = min(args.warmup, 1)   # the oracle has no caches to warm; one untimed call
+    for i in range(warm + args.steps):
+        name, prob, n0, g0 = probs[i % len(probs)]
+        t0 = time.perf_counter()
+        O.rhs(prob, 0.0, n0, g0)
+        if i >= warm:
+            times[name].append(time.perf_counter() - t0)
+    for name, *_ in probs:
+        if not times[name]:   # K too small to visit every workload: time one call
+            _, prob, n0, g0 = next(p for p in probs if p[0] == name)
+            t0 = time.perf_counter()
+            O.rhs(prob, 0.0, n0, g0)
+            times[name].append(time.perf_counter() - t0)
+    step_s = 4 * sum(statistics.mean(v) for v in times.values())
+    value = 1.0 / step_s
+    sample = "per bench step one oracle right-hand side, alternating " + " / ".join(times) + \
+             "; RK4 step = 4 x (mean RHS time of each workload)"
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "+".join(args.workloads), "precision": "fp64-oracle"},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "tf32x3"])
+    ap.add_argument("--workloads", default=",".join(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.workloads = args.workloads.split(",")
+    if args.precision is None:
+        args.precision = os.environ.get("G1G2_BENCH_PRECISION", "fp64")
+    if args.steps is None:
+        args.steps = 3 if args.precision == "fp64" else 20
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    line = run_ours(args, rank, world, dist)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -144,6 +144,20 @@ int g1g2_set_state(g1g2_ctx *c, double t, const double *G1, const double *G2);
 /* Number of kernel launches issued by this context since creation. */
 long long g1g2_launch_count(const g1g2_ctx *c);
 
+/* Per-kernel device time, for roofline accounting (not part of the paper's
+ * method).  g1g2_profile(c, 1) clears the records and brackets every later
+ * launch of the context with CUDA events on its stream; g1g2_profile(c, 0)
+ * stops recording.  g1g2_profile_report synchronises the stream and writes at
+ * most max_entries aggregates (one per kernel name, launches and summed
+ * milliseconds) to out, their number to *n_entries; the records are kept. */
+typedef struct {
+  char name[48];
+  long long launches;
+  double total_ms;
+} g1g2_kernel_stat;
+int g1g2_profile(g1g2_ctx *c, int enable);
+int g1g2_profile_report(g1g2_ctx *c, g1g2_kernel_stat *out, int max_entries, int *n_entries);
+
 const char *g1g2_strerror(int code);
 const char *g1g2_last_error_detail(void);
 void g1g2_destroy(g1g2_ctx *c);

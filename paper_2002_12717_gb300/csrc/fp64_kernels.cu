@@ -456,6 +456,7 @@ __global__ void count_nonfinite_kernel(const cplx *x, long long len, double *cnt
 void zgemm(Launcher &L, const ZGemm &g) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, std::min(g.batch, 65535));
+  L.before("fp64_zgemm");
   zgemm_kernel<<<grid, GNT, 0, L.stream>>>(to_dev(g), 0, 1, nullptr);
   L.after_launch();
 }
@@ -466,9 +467,11 @@ void zgemm_reduce(Launcher &L, const ZGemm &g, cplx *partial, int splits) {
   const int per = (g.batch + splits - 1) / splits;
   splits = (g.batch + per - 1) / per;
   dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, splits);
+  L.before("fp64_zgemm_splitk");
   zgemm_kernel<<<grid, GNT, 0, L.stream>>>(to_dev(g), 1, per, partial);
   L.after_launch();
   const long long mn = (long long)g.M * g.N;
+  L.before("fp64_splitk_reduce");
   zgemm_reduce_kernel<<<(unsigned)((mn + 255) / 256), 256, 0, L.stream>>>(to_dev(g), splits, partial);
   L.after_launch();
 }
@@ -476,6 +479,7 @@ void zgemm_reduce(Launcher &L, const ZGemm &g, cplx *partial, int splits) {
 void permute4(Launcher &L, int nb, const cplx *in, cplx *out, const int p[4], cplx alpha, double beta, bool conj) {
   const int nt = (nb + PT - 1) / PT;
   dim3 block(PT, 8);
+  L.before("permute4");
   if (p[3] == 3) {
     dim3 grid(1, (unsigned)((long long)nb * nb));
     permute4_kernel<<<grid, block, 0, L.stream>>>(nb, in, out, p[0], p[1], p[2], p[3], alpha, beta, conj);
@@ -491,6 +495,7 @@ void hf_build(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *h, 
   const int warps = nb * nb;
   const int threads = 256;
   const int blocks = (warps * 32 + threads - 1) / threads;
+  L.before("hf_build");
   if (wm_real)
     hf_build_kernel<true><<<blocks, threads, 0, L.stream>>>(nb, Wm, h, D, f, n, hhf);
   else
@@ -499,12 +504,14 @@ void hf_build(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *h, 
 }
 
 void one_minus(Launcher &L, int nb, const cplx *n, cplx *nbar) {
+  L.before("one_minus");
   one_minus_kernel<<<(nb * nb + 255) / 256, 256, 0, L.stream>>>(nb, n, nbar);
   L.after_launch();
 }
 
 void g1_update(Launcher &L, int nb, const cplx *hhf, const cplx *n, const cplx *I, Rk4Stage st, cplx *y, cplx *ys,
                cplx *acc, cplx *kout) {
+  L.before("g1_update");
   g1_update_kernel<<<(nb * nb + 127) / 128, 128, 0, L.stream>>>(nb, hhf, n, I, st.stage, st.dt, y, ys, acc, kout);
   L.after_launch();
 }
@@ -513,12 +520,14 @@ void g2_assemble(Launcher &L, int nb, const cplx *Cb, const cplx *Ab, Rk4Stage s
                  cplx *kout) {
   const long long M = (long long)nb * nb;
   const unsigned t = (unsigned)((M + PT - 1) / PT);
+  L.before("fp64_g2_assemble_rk4");
   g2_assemble_kernel<<<dim3(t, t), dim3(PT, 8), 0, L.stream>>>(nb, Cb, Ab, st.stage, st.dt, y, ys, acc, kout);
   L.after_launch();
 }
 
 void obs_one_body(Launcher &L, int nb, const cplx *h, const cplx *D, double f, const cplx *hhf, const cplx *n,
                   double *red) {
+  L.before("obs_one_body");
   obs_one_body_kernel<<<1, 256, 0, L.stream>>>(nb, h, D, f, hhf, n, red);
   L.after_launch();
 }
@@ -526,24 +535,29 @@ void obs_one_body(Launcher &L, int nb, const cplx *h, const cplx *D, double f, c
 void obs_two_body(Launcher &L, int nb, const cplx *W, const cplx *G, double *partials, double *red) {
   const long long M = (long long)nb * nb;
   const unsigned t = (unsigned)((M + PT - 1) / PT);
+  L.before("obs_two_body");
   obs_two_body_kernel<<<dim3(t, t), dim3(PT, 8), 0, L.stream>>>(nb, W, G, partials);
   L.after_launch();
+  L.before("obs_sum");
   sum_pairs_kernel<<<1, 256, 0, L.stream>>>(partials, (long long)t * t, red);
   L.after_launch();
 }
 
 void accumulate_work(Launcher &L, int nb, const cplx *D, const cplx *n, double coeff, double *W_acc) {
+  L.before("drive_work");
   accumulate_work_kernel<<<1, 256, 0, L.stream>>>(nb, D, n, coeff, W_acc);
   L.after_launch();
 }
 
 void double_occ(Launcher &L, int nb, const cplx *n, const cplx *G, double *out) {
+  L.before("double_occ");
   double_occ_kernel<<<(nb / 2 + 63) / 64, 64, 0, L.stream>>>(nb, n, G, out);
   L.after_launch();
 }
 
 void count_nonfinite(Launcher &L, const cplx *x, long long len, double *cnt) {
   const unsigned blocks = (unsigned)std::min<long long>((len + 255) / 256, 4096);
+  L.before("nonfinite_check");
   count_nonfinite_kernel<<<blocks, 256, 0, L.stream>>>(x, len, cnt);
   L.after_launch();
 }

@@ -54,11 +54,13 @@ struct g1g2_ctx {
   double *W_dev = nullptr;          // accumulated drive work
   std::vector<void *> allocs;
   TcPath *tc = nullptr;             // split-precision tensor-core path (precision != FP64)
+  Profiler prof;
 
   Launcher launcher() {
     Launcher L;
     L.stream = stream;
     L.counter = &launches;
+    L.prof = &prof;
     return L;
   }
 };
@@ -381,6 +383,43 @@ const char *g1g2_strerror(int code) {
 const char *g1g2_last_error_detail(void) { return g_detail.c_str(); }
 
 long long g1g2_launch_count(const g1g2_ctx *c) { return c ? c->launches : -1; }
+
+int g1g2_profile(g1g2_ctx *c, int enable) {
+  if (!c) return fail(G1G2_EINVAL, "ctx is NULL");
+  int rc = cuda_check(cudaStreamSynchronize(c->stream), "profile sync");
+  if (rc) return rc;
+  c->prof.clear();
+  c->prof.on = enable != 0;
+  return G1G2_OK;
+}
+
+int g1g2_profile_report(g1g2_ctx *c, g1g2_kernel_stat *out, int max_entries, int *n_entries) {
+  if (!c || !n_entries || (max_entries > 0 && !out)) return fail(G1G2_EINVAL, "NULL argument");
+  int rc = cuda_check(cudaStreamSynchronize(c->stream), "profile sync");
+  if (rc) return rc;
+  std::vector<std::string> names;
+  std::vector<long long> counts;
+  std::vector<double> ms;
+  for (const Profiler::Rec &r : c->prof.recs) {
+    float t = 0.f;
+    if ((rc = cuda_check(cudaEventElapsedTime(&t, c->prof.pool[r.start], c->prof.pool[r.stop]), "event time")))
+      return rc;
+    size_t k = 0;
+    while (k < names.size() && names[k] != r.tag) ++k;
+    if (k == names.size()) { names.push_back(r.tag); counts.push_back(0); ms.push_back(0.0); }
+    ++counts[k];
+    ms[k] += t;
+  }
+  const int n = (int)names.size();
+  for (int k = 0; k < n && k < max_entries; ++k) {
+    std::memset(out[k].name, 0, sizeof(out[k].name));
+    std::strncpy(out[k].name, names[k].c_str(), sizeof(out[k].name) - 1);
+    out[k].launches = counts[k];
+    out[k].total_ms = ms[k];
+  }
+  *n_entries = n < max_entries ? n : max_entries;
+  return G1G2_OK;
+}
 
 void g1g2_destroy(g1g2_ctx *c) {
   if (!c) return;

@@ -16,14 +16,46 @@ using cplx = double2;  // interleaved (re, im), the layout of the ABI
 // Launch bookkeeping: every kernel launch goes through one of these so that a
 // failed launch is turned into G1G2_ECUDA and counted.
 // ---------------------------------------------------------------------------
+// Optional per-kernel timing with CUDA events on the launch stream (g1g2_profile).
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Rec { const char *tag; int start, stop; };
+  std::vector<Rec> recs;
+  int record(cudaStream_t s) {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      pool.push_back(e);
+    }
+    cudaEventRecord(pool[used], s);
+    return (int)used++;
+  }
+  void clear() { used = 0; recs.clear(); }
+  ~Profiler() { for (cudaEvent_t e : pool) cudaEventDestroy(e); }
+};
+
 struct Launcher {
   cudaStream_t stream = nullptr;
   long long *counter = nullptr;
+  Profiler *prof = nullptr;
   cudaError_t err = cudaSuccess;
+  const char *tag = nullptr;
+  int ev_start = -1;
+  void before(const char *t) {
+    tag = t;
+    ev_start = (prof && prof->on) ? prof->record(stream) : -1;
+  }
   void after_launch() {
     if (counter) ++*counter;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess && err == cudaSuccess) err = e;
+    if (prof && prof->on && ev_start >= 0) {
+      const int stop = prof->record(stream);
+      if (stop >= 0) prof->recs.push_back({tag ? tag : "kernel", ev_start, stop});
+    }
+    ev_start = -1;
   }
 };
 

@@ -40,6 +40,10 @@ class Obs(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
+
+
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -65,6 +69,9 @@ def load():
         "g1g2_get_state": (ctypes.c_int, [vp, _dp, _dp, _dp]),
         "g1g2_set_state": (ctypes.c_int, [vp, ctypes.c_double, _dp, _dp]),
         "g1g2_launch_count": (ctypes.c_longlong, [vp]),
+        "g1g2_profile": (ctypes.c_int, [vp, ctypes.c_int]),
+        "g1g2_profile_report": (ctypes.c_int, [vp, ctypes.POINTER(KernelStat), ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int)]),
         "g1g2_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "g1g2_last_error_detail": (ctypes.c_char_p, []),
         "g1g2_destroy": (None, [vp]),
@@ -194,6 +201,17 @@ class Propagator:
         nb_ = _c128(n)
         gb = None if G2 is None else _c128(G2)
         _check(self._lib.g1g2_set_state(self._ctx, float(t), _cptr(nb_), None if gb is None else _cptr(gb)))
+
+    def profile(self, enable=True):
+        """Start (clearing old records) or stop per-kernel CUDA-event timing."""
+        _check(self._lib.g1g2_profile(self._ctx, 1 if enable else 0))
+
+    def profile_report(self):
+        """{kernel name: (launches, total ms)} of the recorded launches (synchronises)."""
+        stats = (KernelStat * 64)()
+        n = ctypes.c_int()
+        _check(self._lib.g1g2_profile_report(self._ctx, stats, 64, ctypes.byref(n)))
+        return {stats[i].name.decode(): (stats[i].launches, stats[i].total_ms) for i in range(n.value)}
 
     @property
     def launch_count(self):
