@@ -158,6 +158,33 @@ typedef struct {
 int g1g2_profile(g1g2_ctx *c, int enable);
 int g1g2_profile_report(g1g2_ctx *c, g1g2_kernel_stat *out, int max_entries, int *n_entries);
 
+/* G1 right-hand side without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- for example code whose device memory is owned by another
+ * allocator (a framework's caching pool, a fixed arena set up at start-up),
+ * or loops that must not risk the latency or failure of an allocation
+ * between steps.  It returns dn/dt of Eq. (eom_gone-2), with h^HF from
+ * Eq. (h_HF) and I from Eq. (eom_gone-I), the same quantity as the dn output
+ * of g1g2_rhs, for one state:
+ *   nb          1 <= nb <= 64 (larger nb returns G1G2_EINVAL with a detail)
+ *   restricted  nonzero: spin-restricted basis (no exchange term in h^HF)
+ *   h_dev       nb*nb complex one-body Hamiltonian h(t) (device)
+ *   w_dev       nb^4 complex interaction in the ABI layout (device)
+ *   n_dev       nb*nb complex density matrix G1 (device)
+ *   G2_dev      nb^4 complex G2 (device)
+ *   dn_dev      nb*nb complex output (device)
+ *   cuda_stream stream for the launches (NULL = default stream)
+ * All arrays are caller-owned.  Scratch (split-K partial sums, h^HF, I,
+ * about 2.2 MB) is one static device array per GPU, kept until the process
+ * exits and shared by every call on that GPU: calls whose kernels overlap on
+ * the GPU (different streams, or threads without ordering) race on it.  The
+ * first call on a device looks the array's address up (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Nothing in the scratch needs clearing between calls: each call writes every
+ * scratch element it reads. */
+int g1g2_g1_rhs_noalloc(int nb, int restricted, const double *h_dev, const double *w_dev, const double *n_dev,
+                        const double *G2_dev, double *dn_dev, void *cuda_stream);
+
 const char *g1g2_strerror(int code);
 const char *g1g2_last_error_detail(void);
 void g1g2_destroy(g1g2_ctx *c);

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libg1g2.so")
-SOURCES = ["g1g2_api.cu", "fp64_kernels.cu", "tc_kernels.cu"]
+SOURCES = ["g1g2_api.cu", "fp64_kernels.cu", "tc_kernels.cu", "g1g2_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

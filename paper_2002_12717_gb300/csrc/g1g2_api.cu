@@ -26,6 +26,8 @@ int fail(int code, const std::string &what) {
 
 }  // namespace
 
+void g1g2::set_error_detail(const std::string &what) { g_detail = what; }
+
 struct g1g2_ctx {
   int nb = 0, se = 0, prec = 0, basis = 0;
   bool w_real = false;

@@ -110,4 +110,7 @@ void double_occ(Launcher &L, int nb, const cplx *n, const cplx *G, double *out);
 // count non-finite entries of x (length len) into *cnt (double, accumulated)
 void count_nonfinite(Launcher &L, const cplx *x, long long len, double *cnt);
 
+// Text returned by g1g2_last_error_detail on this thread.
+void set_error_detail(const std::string &what);
+
 }  // namespace g1g2
