@@ -281,7 +281,7 @@ void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *
 
 void rhs_dispatch(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *G_in, Rk4Stage st,
                   const StageOut &o) {
-  if (c->prec == G1G2_FP64) {
+  if (c->prec == G1G2_FP64 || c->se == G1G2_HF) {
     rhs_fp64(c, L, t, n_in, G_in, st, o);
   } else {
     const double f = drive_f(c, t);
@@ -340,6 +340,7 @@ int observables_impl(g1g2_ctx *c, g1g2_obs *out, double *density, double *nonfin
       return rc;
   }
   if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "obs sync"))) return rc;
+  if (c->tc && (rc = tc_error(c->tc, c->stream))) return rc;
   const bool restricted = c->basis == G1G2_SPIN_RESTRICTED;
   const double s = restricted ? 2.0 : 1.0;
   out->t = c->t;
@@ -557,8 +558,6 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
           (rc = dalloc(c, &c->Pp, N4)))
         return bail(rc);
     }
-  } else if (correlated) {
-    if ((rc = dalloc(c, &c->Gs, N4)) || (rc = dalloc(c, &c->Gacc, N4))) return bail(rc);
   }
   // uploads
   auto up = [&](void *dst, const void *src, size_t bytes) {
@@ -580,9 +579,13 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
     if ((rc = up(c->wP, hP.data(), N4 * sizeof(cplx)))) return bail(rc);
   }
   if (correlated && c->prec != G1G2_FP64) {
+    if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "init sync"))) return bail(rc);
+    g_detail.clear();
     rc = tc_create(&c->tc, nb, se, restricted, hw.data(), hsrc.data(), c->stream);
-    if (rc) return bail(rc == G1G2_EUNSUPPORTED ? fail(rc, g_detail.empty() ? "tensor-core form unavailable" : g_detail)
-                                                : rc);
+    if (rc) return bail(rc);
+    Launcher L = c->launcher();
+    tc_load_state(c->tc, L, c->G);
+    if ((rc = launch_status(L, "tensor-core state"))) return bail(rc);
   }
   if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "init sync"))) return bail(rc);
   *out = c;
@@ -671,7 +674,8 @@ int g1g2_propagate(g1g2_ctx *c, double dt, int nsteps, int obs_every, g1g2_obs *
     if ((rc = rk4_step(c, dt))) return rc;
     if (recording && (s + 1) % obs_every == 0 && (rc = record())) return rc;
   }
-  return cuda_check(cudaStreamSynchronize(c->stream), "propagate sync");
+  if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "propagate sync"))) return rc;
+  return c->tc ? tc_error(c->tc, c->stream) : G1G2_OK;
 }
 
 int g1g2_get_state(g1g2_ctx *c, double *t, double *G1, double *G2) {
@@ -696,6 +700,11 @@ int g1g2_set_state(g1g2_ctx *c, double t, const double *G1, const double *G2) {
   else rc = cuda_check(cudaMemsetAsync(c->G, 0, N4 * sizeof(cplx), c->stream), "set");
   if (rc) return rc;
   c->t = t;
+  if (c->tc) {
+    Launcher L = c->launcher();
+    tc_load_state(c->tc, L, c->G);
+    if ((rc = launch_status(L, "tensor-core state"))) return rc;
+  }
   if ((rc = cuda_check(cudaMemsetAsync(c->W_dev, 0, sizeof(double), c->stream), "memset"))) return rc;
   return cuda_check(cudaStreamSynchronize(c->stream), "set sync");
 }

@@ -1,0 +1,326 @@
+// Persistent tcgen05 GEMM with split-precision TF32 operands for the G1-G2
+// contractions.
+//
+//   D[m][n] = sum_k A[m][k] B[n][k]        (both operands K-major)
+//
+// A is a big FP32 tensor streamed by TMA (128-row tiles, 32-float K blocks,
+// 128-byte swizzle); two converter warps split each landed A tile into a
+// round-to-nearest TF32 "hi" part (in place) and a TF32 "lo" remainder.  B is
+// small and arrives pre-split (hi and lo arrays).  Each K step issues three
+// MMAs, A_hi B_hi + A_lo B_hi + A_hi B_lo, into an FP32 accumulator in TMEM,
+// which carries about 21 significant bits of every product.  The accumulator
+// is double-buffered (2 x 256 TMEM columns) so the epilogue of one tile
+// overlaps the main loop of the next.
+//
+// Warp roles (256 threads): warp 0 TMA producer, warp 1 TMEM owner and MMA
+// issuer, warps 2-3 converters, warps 4-7 epilogue (TMEM lanes 0..127).
+#pragma once
+
+#include "tc_ptx.cuh"
+
+namespace g1g2 {
+namespace tc {
+
+constexpr int kTileM = 128;
+constexpr int kBlockK = 32;                        // floats per K block (128 B)
+constexpr uint32_t kABytes = kTileM * kBlockK * 4; // 16 KB
+constexpr int kAccCols = 256;                      // TMEM columns per accumulator buffer
+
+enum ARows : int {
+  AR_LINEAR = 0,   // A viewed as [plane][row][k]; tile = 128 consecutive rows
+  AR_GATHER4 = 1,  // A = T[plane][a][b][c][k]; tile = rows (a: 4, b: 32) at fixed c
+  AR_SPLITK = 2,   // A = G[plane][j][c]; tile = (plane, K split), rows j
+};
+
+enum Epi : int {
+  EP_DIRECT = 0,        // out[v][row][l]
+  EP_EXCH_T = 1,        // row (p,q,r), col l -> out[v][q][p][l][r]
+  EP_GATHER_TCONJ = 2,  // row (a,b,c), col d -> out[v][c][d][a][b], imaginary plane negated
+  EP_PARTIAL = 3,       // split-K partial sums: partial[split][plane][row][col]
+};
+
+struct GemmParams {
+  int nb;             // basis size N
+  int a_rows;         // ARows
+  int epi;            // Epi
+  int tiles;          // work items
+  int kb_per_plane;   // K blocks per A plane
+  int a_planes;       // 1 (real A) or 2 (complex A, planar)
+  int nout;           // MMA N (multiple of 16, <= 256)
+  int n_valid;        // output columns that are stored
+  long long rows;     // AR_LINEAR: valid rows
+  int g_na, g_nb;     // AR_GATHER4: number of a-blocks (4) and b-blocks (32)
+  int splits;         // AR_SPLITK: K splits per plane
+  int kb_per_split;   //            K blocks per split
+  int kb_all;         //            K blocks in total
+  int kb_chunks;      // AR_SPLITK: each K block is its own TMEM accumulation, summed in FP64 smem
+  double *out64;      //            FP64 partial sums [split][plane][row][col]
+  float *out;
+  long long out_plane;
+  int *err;
+};
+
+__device__ __forceinline__ int tile_kblocks(const GemmParams &p, int tile) {
+  if (p.a_rows == AR_SPLITK) {
+    const int split = tile % p.splits;
+    const int b0 = split * p.kb_per_split;
+    const int n = p.kb_all - b0;
+    return n < p.kb_per_split ? (n > 0 ? n : 0) : p.kb_per_split;
+  }
+  return p.kb_per_plane * p.a_planes;
+}
+
+__global__ void __launch_bounds__(256, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
+                   const __grid_constant__ CUtensorMap tmBlo, const GemmParams p, const int stages) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t b_bytes = (uint32_t)p.nout * kBlockK * 4;
+  const uint32_t stage_bytes = 2 * kABytes + 2 * b_bytes;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stage_bytes);
+  uint64_t *full = bars;
+  uint64_t *conv = bars + stages;
+  uint64_t *empty = bars + 2 * stages;
+  uint64_t *tfull = bars + 3 * stages;
+  uint64_t *tempty = tfull + 2;
+  uint64_t *fin = tempty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
+  double *acc64 = reinterpret_cast<double *>(smem + (size_t)stages * stage_bytes + 256);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 64);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
+    mbar_init(fin, 1);
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, 2 * kAccCols);
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int N = p.nb;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
+        const int nkb = tile_kblocks(p, tile);
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
+          uint8_t *st = smem + (size_t)s * stage_bytes;
+          mbar_arrive_expect_tx(&full[s], kABytes + 2 * b_bytes);
+          int bk;  // K coordinate (floats) of this block in B
+          if (p.a_rows == AR_LINEAR) {
+            const int u = kb / p.kb_per_plane, pb = kb % p.kb_per_plane;
+            tma_load_3d(st, &tmA, &full[s], pb * kBlockK, tile * kTileM, u);
+            bk = kb * kBlockK;
+          } else if (p.a_rows == AR_GATHER4) {
+            const int u = kb / p.kb_per_plane, pb = kb % p.kb_per_plane;
+            const int bB = tile % p.g_nb, aB = (tile / p.g_nb) % p.g_na, c = tile / (p.g_nb * p.g_na);
+            tma_load_5d(st, &tmA, &full[s], pb * kBlockK, c, bB * 32, aB * 4, u);
+            bk = kb * kBlockK;
+          } else {
+            const int u = tile / p.splits, split = tile % p.splits;
+            const int kglob = (split * p.kb_per_split + kb) * kBlockK;
+            tma_load_3d(st, &tmA, &full[s], kglob, 0, u);
+            bk = kglob;
+          }
+          tma_load_3d(st + 2 * kABytes, &tmBhi, &full[s], bk, 0, 0);
+          tma_load_3d(st + 2 * kABytes + b_bytes, &tmBlo, &full[s], bk, 0, 0);
+          if (++s == stages) { s = 0; ph ^= 1u; }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(kTileM, p.nout);
+      int s = 0, acc = 0;
+      uint32_t ph = 0, acc_ph = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
+        const int nkb = tile_kblocks(p, tile);
+        if (!p.kb_chunks) {
+          if (!mbar_wait(&tempty[acc], acc_ph ^ 1u, p.err)) break;
+          tc_fence_after();
+        }
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (p.kb_chunks) {
+            if (!mbar_wait(&tempty[acc], acc_ph ^ 1u, p.err)) { ok = false; break; }
+            tc_fence_after();
+          }
+          const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kAccCols);
+          const uint32_t first = p.kb_chunks ? 0u : (uint32_t)kb;
+          if (!mbar_wait(&conv[s], ph, p.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
+          const uint32_t sal = sa + kABytes, sbh = sa + 2 * kABytes, sbl = sbh + b_bytes;
+#pragma unroll
+          for (int k = 0; k < kBlockK / 8; ++k) {
+            const uint64_t ah = smem_desc_sw128(sa + 32 * k), al = smem_desc_sw128(sal + 32 * k);
+            const uint64_t bh = smem_desc_sw128(sbh + 32 * k), bl = smem_desc_sw128(sbl + 32 * k);
+            mma_tf32(d_tmem, ah, bh, idesc, (first | (uint32_t)k) ? 1u : 0u);
+            mma_tf32(d_tmem, al, bh, idesc, 1u);
+            mma_tf32(d_tmem, ah, bl, idesc, 1u);
+          }
+          mma_commit(&empty[s]);
+          if (++s == stages) { s = 0; ph ^= 1u; }
+          if (p.kb_chunks) {
+            mma_commit(&tfull[acc]);
+            if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
+          }
+        }
+        if (!ok) break;
+        if (!p.kb_chunks) {
+          mma_commit(&tfull[acc]);
+          if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
+        }
+      }
+      // every MMA issued by this thread has completed before TMEM is released
+      mma_commit(fin);
+      mbar_wait(fin, 0, p.err);
+    }
+  } else if (warp < 4) {
+    // ------------------------------------------------------------ converters
+    const int ct = threadIdx.x - 64;
+    int s = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
+      const int nkb = tile_kblocks(p, tile);
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (!mbar_wait(&full[s], ph, p.err)) { ok = false; break; }
+        float4 *a = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes);
+        float4 *lo = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes + kABytes);
+#pragma unroll 4
+        for (int i = ct; i < (int)(kABytes / 16); i += 64) {
+          const float4 x = a[i];
+          float4 h, l;
+          h.x = to_tf32(x.x); l.x = to_tf32(x.x - h.x);
+          h.y = to_tf32(x.y); l.y = to_tf32(x.y - h.y);
+          h.z = to_tf32(x.z); l.z = to_tf32(x.z - h.z);
+          h.w = to_tf32(x.w); l.w = to_tf32(x.w - h.w);
+          a[i] = h;
+          lo[i] = l;
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(&conv[s]);
+        if (++s == stages) { s = 0; ph ^= 1u; }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int r = threadIdx.x - 128;                  // TMEM lane == tile row
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    int acc = 0;
+    uint32_t acc_ph = 0;
+    const long long NN = N;
+    if (p.kb_chunks) {
+      // split-K with FP64 accumulation: every K block arrives as its own FP32 tile
+      const int nv = p.n_valid;
+      const int ld = nv + 1;  // odd row stride in doubles: no shared-memory bank conflicts across rows
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
+        const int nkb = tile_kblocks(p, tile);
+        const int u = tile / p.splits, split = tile % p.splits;
+        if (r < N)
+          for (int col = 0; col < nv; ++col) acc64[r * ld + col] = 0.0;
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(&tfull[acc], acc_ph, p.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t tbase = tmem_base + lane_base + (uint32_t)(acc * kAccCols);
+          for (int c0 = 0; c0 < p.nout; c0 += 32) {
+            float v[32];
+            tmem_ld32(tbase + (uint32_t)c0, v);
+            if (r < N) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (c0 + j < nv) acc64[r * ld + c0 + j] += (double)v[j];
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(&tempty[acc]);
+          if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
+        }
+        if (!ok) break;
+        if (r < N)
+          for (int col = 0; col < nv; ++col)
+            p.out64[(((long long)split * 2 + u) * NN + r) * nv + col] = acc64[r * ld + col];
+      }
+    } else
+    for (int tile = blockIdx.x; tile < p.tiles; tile += gridDim.x) {
+      if (!mbar_wait(&tfull[acc], acc_ph, p.err)) break;
+      tc_fence_after();
+      // the row this thread owns
+      bool valid = false;
+      long long i0 = 0, i1 = 0, i2 = 0, grow = 0;
+      int u = 0, split = 0;
+      if (p.a_rows == AR_LINEAR) {
+        grow = (long long)tile * kTileM + r;
+        valid = grow < p.rows;
+        i2 = grow % NN;
+        i1 = (grow / NN) % NN;
+        i0 = grow / (NN * NN);
+      } else if (p.a_rows == AR_GATHER4) {
+        const int bB = tile % p.g_nb, aB = (tile / p.g_nb) % p.g_na, c = tile / (p.g_nb * p.g_na);
+        i0 = aB * 4 + r / 32;   // a
+        i1 = bB * 32 + r % 32;  // b
+        i2 = c;
+        valid = i0 < NN && i1 < NN;
+      } else {
+        u = tile / p.splits;
+        split = tile % p.splits;
+        valid = r < N;
+      }
+      const uint32_t tbase = tmem_base + lane_base + (uint32_t)(acc * kAccCols);
+      for (int c0 = 0; c0 < p.nout; c0 += 32) {
+        float v[32];
+        tmem_ld32(tbase + (uint32_t)c0, v);
+        if (!valid) continue;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = c0 + j;
+          if (col >= p.n_valid) continue;
+          if (p.epi == EP_PARTIAL) {
+            p.out[(((long long)split * 2 + u) * NN + r) * p.n_valid + col] = v[j];
+            continue;
+          }
+          const int vv = col / N;
+          const long long l = col % N;
+          float x = v[j];
+          long long idx;
+          if (p.epi == EP_DIRECT) {
+            idx = grow * NN + l;
+          } else if (p.epi == EP_EXCH_T) {
+            idx = ((i1 * NN + i0) * NN + l) * NN + i2;
+          } else {
+            idx = ((i2 * NN + l) * NN + i0) * NN + i1;
+            if (vv) x = -x;
+          }
+          p.out[vv * p.out_plane + idx] = x;
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[acc]);
+      if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 2 * kAccCols);
+  }
+}
+
+}  // namespace tc
+}  // namespace g1g2

@@ -1,20 +1,592 @@
-// Split-precision tensor-core form (placeholder until the tcgen05 kernels land).
+// Split-precision tensor-core form of the G1-G2 right-hand side (sm_103a).
+//
+// The nb^5 contractions run on tcgen05 (tc_gemm.cuh); the Hartree-Fock build,
+// the G1 update, the RK4 state of G2 and the observables stay FP64.  Every
+// contraction is written as a right multiplication of a big tensor by a small
+// nb x nb matrix over its last index, using the symmetries the exact dynamics
+// keep (Eqs. Gsymm_a/b for G2, Eqs. wsymm_a/b for w):
+//
+//   commutator (Eqs. twopart_hamiltonian, result_eom_soa): with M = G2 as an
+//     nb^2 x nb^2 Hermitian matrix, [h2, M] = U^dag - U, U = M h2, and the
+//     mode-3 half of U is the exchange image of the mode-4 half:
+//     U_ijkl = Z_ijkl + Z_jilk,  Z = G2 x_4 hHF                      (1 pass)
+//   source term (Eqs. psi-pm-def, soa-skalierung): A = (nbar (x) nbar) w~ (n (x) n),
+//     Psi = A^dag - A; the chain is evaluated as
+//       B1 = w~ x_4 n            stored exchange-permuted
+//       B  = B1~ x_4 n           rows gathered, stored as B^dag (transposed, conj)
+//       T2 = B^dag x_4 nbar      stored exchange-permuted
+//       A^dag = T2~ x_4 nbar                                          (4 passes)
+//   collision integral (Eq. eom_gone-I): I_ij = -i sum_c w_ic conj(G2_jc) with
+//     c = (k,l,p), both operands row-contiguous; split-K over c.
+//   assembly: P = U - (Q + Q~)/2 with Q = A^dag, dG2 = -i (P^dag - P), read as
+//     the orbit {X, exch X, trans X, exch trans X} of 8^4 blocks so every
+//     input block is read once; the RK4 stage update is fused.
 #include "tc_path.h"
+#include "tc_gemm.cuh"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
 
 namespace g1g2 {
 
-struct TcPath {
-  int nb;
-};
+using namespace tc;
 
-int tc_create(TcPath **out, int, int, bool, const cplx *, const cplx *, cudaStream_t) {
-  *out = nullptr;
-  return G1G2_EUNSUPPORTED;
+namespace {
+
+constexpr int BSZ = 8;                      // assembly block edge
+constexpr int BEL = BSZ * BSZ * BSZ * BSZ;  // elements per block
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ------------------------------------------------------------------ small kernels
+// B operand of "X x_4 S" for a complex (planar) X: rows (v, l), K' = (u, p):
+// (a_re, a_im) * S_pl as a real 2x2 block [[S_re, S_im], [-S_im, S_re]].
+// Real X: rows (v, l), K' = p: S_v[p][l].  hi = TF32(x), lo = TF32(x - hi).
+__global__ void realify_kernel(int nb, int nout, int kpad, int complex_a, int shift, const cplx *__restrict__ S,
+                               float *hi, float *lo) {
+  const int kt = complex_a ? 2 * kpad : kpad;
+  const int total = nout * kt;
+  // optional shift S -> S - mu 1 with mu = Re Tr S / nb (the commutator does not see it)
+  double mu = 0.0;
+  if (shift)
+    for (int i = 0; i < nb; ++i) mu += S[i * nb + i].x;
+  mu /= nb;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int row = e / kt, col = e % kt;
+    double x = 0.0;
+    if (row < 2 * nb) {
+      const int v = row / nb, l = row % nb;
+      const int u = complex_a ? col / kpad : 0;
+      const int pp = complex_a ? col % kpad : col;
+      if (pp < nb) {
+        cplx s = S[pp * nb + l];
+        if (pp == l) s.x -= mu;
+        if (!complex_a) x = v ? s.y : s.x;
+        else if (u == 0) x = v ? s.y : s.x;
+        else x = v ? s.x : -s.y;
+      }
+    }
+    const float h = to_tf32((float)x);
+    hi[e] = h;
+    lo[e] = to_tf32((float)(x - (double)h));
+  }
 }
 
-void tc_destroy(TcPath *p) { delete p; }
+// w (real part of the FP64 interleaved tensor) -> hi/lo TF32 arrays [i][c].
+__global__ void split_real_kernel(long long n, const cplx *__restrict__ w, float *hi, float *lo) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double x = w[e].x;
+    const float h = to_tf32((float)x);
+    hi[e] = h;
+    lo[e] = to_tf32((float)(x - (double)h));
+  }
+}
 
-void tc_rhs(TcPath *, Launcher &, const cplx *, const cplx *, const cplx *, Rk4Stage, cplx *, cplx *, cplx *,
-            cplx *, cplx *, cplx *, cplx *, cplx *) {}
+// interleaved FP64 -> planar FP32 (re plane, im plane)
+__global__ void to_planar_f32_kernel(long long n, const cplx *__restrict__ x, float *out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const cplx v = x[e];
+    out[e] = (float)v.x;
+    out[n + e] = (float)v.y;
+  }
+}
+
+// I_ij = -D1[j][i] - i D0[j][i], summed over the K splits in FP64.
+__global__ void collision_reduce_kernel(int nb, int splits, const double *__restrict__ partial, cplx *I) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nb * nb) return;
+  const int i = e / nb, j = e % nb;
+  double d0 = 0.0, d1 = 0.0;
+  for (int s = 0; s < splits; ++s) {
+    d0 += partial[(((long long)s * 2 + 0) * nb + j) * nb + i];
+    d1 += partial[(((long long)s * 2 + 1) * nb + j) * nb + i];
+  }
+  I[e] = {-d1, -d0};
+}
+
+struct AsmParams {
+  int nb, nblk;
+  const int4 *blocks;
+  const float *Z, *Q, *Pi;     // planar FP32 (plane stride P)
+  long long P;
+  cplx *y;                     // FP64 state (interleaved)
+  float *acc;                  // planar FP32
+  float *ys;                   // planar FP32 stage input of the next stage
+  float *y32;                  // planar FP32 copy of y (stage 3)
+  cplx *kout;                  // write-k mode
+  int stage;
+  double dt;
+};
+
+__device__ __forceinline__ int bidx(int a, int b, int c, int d) { return ((a * BSZ + b) * BSZ + c) * BSZ + d; }
+
+__device__ __forceinline__ void load_blocks(const AsmParams &p, const float *src, const int (&X)[4][4], float2 *sm) {
+  const long long N = p.nb;
+  for (int m = 0; m < 4; ++m) {
+    for (int e = threadIdx.x; e < BEL; e += blockDim.x) {
+      const int a = e >> 9, b = (e >> 6) & 7, c = (e >> 3) & 7, d = e & 7;
+      const long long g0 = X[m][0] * BSZ + a, g1 = X[m][1] * BSZ + b, g2 = X[m][2] * BSZ + c, g3 = X[m][3] * BSZ + d;
+      float2 v = {0.f, 0.f};
+      if (g0 < N && g1 < N && g2 < N && g3 < N) {
+        const long long g = ((g0 * N + g1) * N + g2) * N + g3;
+        v.x = src[g];
+        v.y = src[p.P + g];
+      }
+      sm[m * BEL + e] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) orbit_assemble_kernel(const AsmParams p) {
+  extern __shared__ float2 sm[];  // 4 blocks of BEL complex values
+  const int4 base = p.blocks[blockIdx.x];
+  const int X[4][4] = {{base.x, base.y, base.z, base.w},
+                       {base.y, base.x, base.w, base.z},
+                       {base.z, base.w, base.x, base.y},
+                       {base.w, base.z, base.y, base.x}};
+  constexpr int PER = BEL / 256;
+  float2 kx[PER], ky[PER];
+
+  load_blocks(p, p.Z, X, sm);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int e = threadIdx.x + 256 * t;
+    const int a = e >> 9, b = (e >> 6) & 7, c = (e >> 3) & 7, d = e & 7;
+    const float2 z0 = sm[0 * BEL + bidx(a, b, c, d)], z1 = sm[1 * BEL + bidx(b, a, d, c)];
+    const float2 z2 = sm[2 * BEL + bidx(c, d, a, b)], z3 = sm[3 * BEL + bidx(d, c, b, a)];
+    kx[t] = {z0.x + z1.x, z0.y + z1.y};
+    ky[t] = {z2.x + z3.x, z2.y + z3.y};
+  }
+  __syncthreads();
+  load_blocks(p, p.Q, X, sm);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int e = threadIdx.x + 256 * t;
+    const int a = e >> 9, b = (e >> 6) & 7, c = (e >> 3) & 7, d = e & 7;
+    const float2 q0 = sm[0 * BEL + bidx(a, b, c, d)], q1 = sm[1 * BEL + bidx(b, a, d, c)];
+    const float2 q2 = sm[2 * BEL + bidx(c, d, a, b)], q3 = sm[3 * BEL + bidx(d, c, b, a)];
+    const float2 P0 = {kx[t].x - 0.5f * (q0.x + q1.x), kx[t].y - 0.5f * (q0.y + q1.y)};
+    const float2 P2 = {ky[t].x - 0.5f * (q2.x + q3.x), ky[t].y - 0.5f * (q2.y + q3.y)};
+    // k0 = -i (conj(P2) - P0),  k2 = -i (conj(P0) - P2)
+    const float2 D = {P2.x - P0.x, -P2.y - P0.y};
+    const float2 E = {P0.x - P2.x, -P0.y - P2.y};
+    kx[t] = {D.y, -D.x};
+    ky[t] = {E.y, -E.x};
+  }
+  if (p.Pi) {
+    __syncthreads();
+    load_blocks(p, p.Pi, X, sm);
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int e = threadIdx.x + 256 * t;
+      const int a = e >> 9, b = (e >> 6) & 7, c = (e >> 3) & 7, d = e & 7;
+      const float2 p0 = sm[0 * BEL + bidx(a, b, c, d)], p1 = sm[1 * BEL + bidx(b, a, d, c)];
+      const float2 p2 = sm[2 * BEL + bidx(c, d, a, b)], p3 = sm[3 * BEL + bidx(d, c, b, a)];
+      // R = Pi_ijkl - conj(Pi_lkji) on the four members, symmetrised over exchange
+      const float2 s01 = {0.5f * ((p0.x - p3.x) + (p1.x - p2.x)), 0.5f * ((p0.y + p3.y) + (p1.y + p2.y))};
+      const float2 s23 = {0.5f * ((p2.x - p1.x) + (p3.x - p0.x)), 0.5f * ((p2.y + p1.y) + (p3.y + p0.y))};
+      kx[t] = {kx[t].x + s01.y, kx[t].y - s01.x};
+      ky[t] = {ky[t].x + s23.y, ky[t].y - s23.x};
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int e = threadIdx.x + 256 * t;
+    const int a = e >> 9, b = (e >> 6) & 7, c = (e >> 3) & 7, d = e & 7;
+    sm[0 * BEL + bidx(a, b, c, d)] = kx[t];
+    sm[1 * BEL + bidx(b, a, d, c)] = kx[t];
+    sm[2 * BEL + bidx(c, d, a, b)] = ky[t];
+    sm[3 * BEL + bidx(d, c, b, a)] = ky[t];
+  }
+  __syncthreads();
+  // RK4 update of each distinct member block, in natural (coalesced) order
+  const long long N = p.nb;
+  for (int m = 0; m < 4; ++m) {
+    bool dup = false;
+    for (int q = 0; q < m; ++q)
+      dup |= (X[q][0] == X[m][0] && X[q][1] == X[m][1] && X[q][2] == X[m][2] && X[q][3] == X[m][3]);
+    if (dup) continue;
+    for (int e = threadIdx.x; e < BEL; e += blockDim.x) {
+      const int a = e >> 9, b = (e >> 6) & 7, c = (e >> 3) & 7, d = e & 7;
+      const long long g0 = X[m][0] * BSZ + a, g1 = X[m][1] * BSZ + b, g2 = X[m][2] * BSZ + c, g3 = X[m][3] * BSZ + d;
+      if (g0 >= N || g1 >= N || g2 >= N || g3 >= N) continue;
+      const long long g = ((g0 * N + g1) * N + g2) * N + g3;
+      const float2 k = sm[m * BEL + e];
+      if (p.stage < 0) {
+        p.kout[g] = {(double)k.x, (double)k.y};
+        continue;
+      }
+      const cplx y0 = p.y[g];
+      const double dt = p.dt;
+      if (p.stage == 0) {
+        p.acc[g] = k.x;
+        p.acc[p.P + g] = k.y;
+        p.ys[g] = (float)(y0.x + 0.5 * dt * k.x);
+        p.ys[p.P + g] = (float)(y0.y + 0.5 * dt * k.y);
+      } else if (p.stage < 3) {
+        p.acc[g] += 2.f * k.x;
+        p.acc[p.P + g] += 2.f * k.y;
+        const double h = (p.stage == 1) ? 0.5 * dt : dt;
+        p.ys[g] = (float)(y0.x + h * k.x);
+        p.ys[p.P + g] = (float)(y0.y + h * k.y);
+      } else {
+        const double nx = y0.x + dt / 6.0 * ((double)p.acc[g] + (double)k.x);
+        const double ny = y0.y + dt / 6.0 * ((double)p.acc[p.P + g] + (double)k.y);
+        p.y[g] = {nx, ny};
+        p.y32[g] = (float)nx;
+        p.y32[p.P + g] = (float)ny;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ tensor maps
+int encode_map(CUtensorMap *m, const void *base, int rank, const cuuint64_t *dims, const cuuint64_t *strides,
+               const cuuint32_t *box) {
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = cuTensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void *>(base), dims,
+                                      strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? G1G2_OK : G1G2_ECUDA;
+}
+
+// A viewed as [planes][rows][K]
+int map_linear(CUtensorMap *m, const float *base, int K, long long rows, int planes) {
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t str[2] = {(cuuint64_t)K * 4, (cuuint64_t)K * 4 * rows};
+  cuuint32_t box[3] = {(cuuint32_t)kBlockK, (cuuint32_t)kTileM, 1};
+  return encode_map(m, base, 3, dims, str, box);
+}
+// A = T[plane][a][b][c][s], box (s 32, c 1, b 32, a 4)
+int map_gather(CUtensorMap *m, const float *base, int N) {
+  const cuuint64_t n = N;
+  cuuint64_t dims[5] = {n, n, n, n, 2};
+  cuuint64_t str[4] = {n * 4, n * n * 4, n * n * n * 4, n * n * n * n * 4};
+  cuuint32_t box[5] = {(cuuint32_t)kBlockK, 1, 32, 4, 1};
+  return encode_map(m, base, 5, dims, str, box);
+}
+// small pre-split B operand [rows][kt]
+int map_b(CUtensorMap *m, const float *base, int kt, int rows, int box_rows) {
+  cuuint64_t dims[3] = {(cuuint64_t)kt, (cuuint64_t)rows, 1};
+  cuuint64_t str[2] = {(cuuint64_t)kt * 4, (cuuint64_t)kt * 4 * rows};
+  cuuint32_t box[3] = {(cuuint32_t)kBlockK, (cuuint32_t)box_rows, 1};
+  return encode_map(m, base, 3, dims, str, box);
+}
+
+}  // namespace
+
+struct TcPath {
+  int nb = 0, se = 0, kpad = 0, nout2 = 0, nout1 = 0, sms = 0;
+  bool restricted = false;
+  long long N4 = 0;
+  std::vector<void *> allocs;
+  // FP32 planar tensors [2][nb^4]
+  float *y32 = nullptr, *ys32 = nullptr, *acc = nullptr, *Z = nullptr, *buf1 = nullptr, *buf2 = nullptr;
+  float *W32 = nullptr;                 // source interaction (real) [nb^4]
+  float *w_hi = nullptr, *w_lo = nullptr;  // w (real) split [i][c]
+  // small pre-split B operands
+  float *bh_hi = nullptr, *bh_lo = nullptr;   // hHF, complex A
+  float *bnr_hi = nullptr, *bnr_lo = nullptr; // n, real A
+  float *bnc_hi = nullptr, *bnc_lo = nullptr; // n, complex A
+  float *bnb_hi = nullptr, *bnb_lo = nullptr; // nbar, complex A
+  double *partial = nullptr;
+  cplx *nbar = nullptr, *I = nullptr;
+  int4 *blocks = nullptr;
+  int nblocks = 0;
+  int *err = nullptr;
+  int splits = 0, kb_all_coll = 0, kb_per_split = 0;
+  // tensor maps
+  CUtensorMap mZin_y32, mZin_ys32, mCol_y32, mCol_ys32, mW32, mBuf1Gather, mBuf2Lin, mBuf1Lin;
+  CUtensorMap mBh_hi, mBh_lo, mBnr_hi, mBnr_lo, mBnc_hi, mBnc_lo, mBnb_hi, mBnb_lo, mW_hi, mW_lo;
+};
+
+namespace {
+
+template <class T>
+int talloc(TcPath *p, T **ptr, size_t count) {
+  void *q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return G1G2_ENOMEM;
+  }
+  p->allocs.push_back(q);
+  *ptr = static_cast<T *>(q);
+  return G1G2_OK;
+}
+
+// dynamic shared memory of one GEMM CTA; acc64_bytes > 0 adds the FP64 split-K accumulator
+size_t gemm_smem(int nout, int *stages, size_t acc64_bytes = 0) {
+  const size_t stage = 2 * (size_t)kABytes + 2 * (size_t)nout * kBlockK * 4;
+  const size_t budget = 220 * 1024 - acc64_bytes;
+  int s = (int)std::min<size_t>(4, budget / stage);
+  if (s < 2) s = 2;
+  *stages = s;
+  return 1024 + s * stage + 256 + acc64_bytes;
+}
+
+void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, const CUtensorMap &Bh,
+                 const CUtensorMap &Bl, GemmParams gp) {
+  gp.err = t->err;
+  int stages = 0;
+  const size_t acc64 = gp.kb_chunks ? (size_t)gp.nb * (gp.n_valid + 1) * sizeof(double) : 0;
+  const size_t smem = gemm_smem(gp.nout, &stages, acc64);
+  const int grid = std::max(1, std::min(gp.tiles, t->sms));
+  L.before(tag);
+  tc_gemm_kernel<<<grid, 256, smem, L.stream>>>(A, Bh, Bl, gp, stages);
+  L.after_launch();
+}
+
+GemmParams linear_params(const TcPath *t, long long rows, int planes, int epi, float *out) {
+  GemmParams g{};
+  g.nb = t->nb;
+  g.a_rows = AR_LINEAR;
+  g.epi = epi;
+  g.rows = rows;
+  g.tiles = (int)((rows + kTileM - 1) / kTileM);
+  g.kb_per_plane = t->kpad / kBlockK;
+  g.a_planes = planes;
+  g.nout = t->nout2;
+  g.n_valid = 2 * t->nb;
+  g.out = out;
+  g.out_plane = t->N4;
+  return g;
+}
+
+}  // namespace
+
+int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, const cplx *hsrc, cudaStream_t stream) {
+  *out = nullptr;
+  if (nb % 4 != 0) {
+    set_error_detail("the tensor-core form needs nb divisible by 4 (TMA row pitch)");
+    return G1G2_EUNSUPPORTED;
+  }
+  if (se == G1G2_GW) {
+    set_error_detail("the tensor-core form of GW is not built yet");
+    return G1G2_EUNSUPPORTED;
+  }
+  const long long N = nb, N4 = N * N * N * N;
+  for (long long e = 0; e < N4; ++e)
+    if (hw[e].y != 0.0) {
+      set_error_detail("the tensor-core form takes a real interaction w");
+      return G1G2_EUNSUPPORTED;
+    }
+  TcPath *t = new TcPath;
+  t->nb = nb;
+  t->se = se;
+  t->restricted = restricted;
+  t->N4 = N4;
+  t->kpad = round_up(nb, kBlockK);
+  t->nout2 = round_up(2 * nb, 16);
+  t->nout1 = round_up(nb, 16);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, dev);
+  int rc = G1G2_OK;
+  auto bail = [&](int code) {
+    tc_destroy(t);
+    return code;
+  };
+  const int kt_c = 2 * t->kpad, kt_r = t->kpad;
+  if ((rc = talloc(t, &t->y32, 2 * N4)) || (rc = talloc(t, &t->ys32, 2 * N4)) || (rc = talloc(t, &t->acc, 2 * N4)) ||
+      (rc = talloc(t, &t->Z, 2 * N4)) || (rc = talloc(t, &t->buf1, 2 * N4)) || (rc = talloc(t, &t->buf2, 2 * N4)) ||
+      (rc = talloc(t, &t->W32, N4)) || (rc = talloc(t, &t->w_hi, N4)) || (rc = talloc(t, &t->w_lo, N4)) ||
+      (rc = talloc(t, &t->bh_hi, (size_t)t->nout2 * kt_c)) || (rc = talloc(t, &t->bh_lo, (size_t)t->nout2 * kt_c)) ||
+      (rc = talloc(t, &t->bnr_hi, (size_t)t->nout2 * kt_r)) || (rc = talloc(t, &t->bnr_lo, (size_t)t->nout2 * kt_r)) ||
+      (rc = talloc(t, &t->bnc_hi, (size_t)t->nout2 * kt_c)) || (rc = talloc(t, &t->bnc_lo, (size_t)t->nout2 * kt_c)) ||
+      (rc = talloc(t, &t->bnb_hi, (size_t)t->nout2 * kt_c)) || (rc = talloc(t, &t->bnb_lo, (size_t)t->nout2 * kt_c)) ||
+      (rc = talloc(t, &t->nbar, N * N)) || (rc = talloc(t, &t->I, N * N)) || (rc = talloc(t, &t->err, 1)))
+    return bail(rc);
+  // collision split-K geometry: K = nb^3 floats, both planes
+  t->kb_all_coll = (int)((N * N * N + kBlockK - 1) / kBlockK);
+  t->splits = std::max(1, std::min(t->kb_all_coll, t->sms));
+  t->kb_per_split = (t->kb_all_coll + t->splits - 1) / t->splits;
+  t->splits = (t->kb_all_coll + t->kb_per_split - 1) / t->kb_per_split;
+  if ((rc = talloc(t, &t->partial, (size_t)t->splits * 2 * N * N))) return bail(rc);
+  // canonical blocks of the assembly orbits
+  {
+    const int nB = (nb + BSZ - 1) / BSZ;
+    std::vector<int4> blk;
+    for (int a = 0; a < nB; ++a)
+      for (int b = 0; b < nB; ++b)
+        for (int c = 0; c < nB; ++c)
+          for (int d = 0; d < nB; ++d) {
+            const int m[4][4] = {{a, b, c, d}, {b, a, d, c}, {c, d, a, b}, {d, c, b, a}};
+            bool canon = true;
+            for (int q = 1; q < 4 && canon; ++q) {
+              for (int z = 0; z < 4; ++z) {
+                if (m[q][z] < m[0][z]) { canon = false; break; }
+                if (m[q][z] > m[0][z]) break;
+              }
+            }
+            if (canon) blk.push_back(make_int4(a, b, c, d));
+          }
+    t->nblocks = (int)blk.size();
+    if ((rc = talloc(t, &t->blocks, blk.size()))) return bail(rc);
+    if (cudaMemcpy(t->blocks, blk.data(), blk.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(G1G2_ECUDA);
+  }
+  // fixed operands: W32 = source interaction (real), w hi/lo for the collision integral
+  {
+    std::vector<float> w32(N4);
+    for (long long e = 0; e < N4; ++e) w32[e] = (float)hsrc[e].x;
+    if (cudaMemcpy(t->W32, w32.data(), N4 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(G1G2_ECUDA);
+    cplx *wd = nullptr;
+    if (cudaMalloc(&wd, N4 * sizeof(cplx)) != cudaSuccess) return bail(G1G2_ENOMEM);
+    cudaMemcpy(wd, hw, N4 * sizeof(cplx), cudaMemcpyHostToDevice);
+    split_real_kernel<<<1024, 256, 0, stream>>>(N4, wd, t->w_hi, t->w_lo);
+    cudaStreamSynchronize(stream);
+    cudaFree(wd);
+    if (cudaGetLastError() != cudaSuccess) return bail(G1G2_ECUDA);
+  }
+  if (cudaMemset(t->err, 0, sizeof(int)) != cudaSuccess) return bail(G1G2_ECUDA);
+  // tensor maps
+  const long long N3 = N * N * N;
+  if ((rc = map_linear(&t->mZin_y32, t->y32, nb, N3, 2)) || (rc = map_linear(&t->mZin_ys32, t->ys32, nb, N3, 2)) ||
+      (rc = map_linear(&t->mCol_y32, t->y32, (int)N3, N, 2)) ||
+      (rc = map_linear(&t->mCol_ys32, t->ys32, (int)N3, N, 2)) || (rc = map_linear(&t->mW32, t->W32, nb, N3, 1)) ||
+      (rc = map_gather(&t->mBuf1Gather, t->buf1, nb)) || (rc = map_linear(&t->mBuf2Lin, t->buf2, nb, N3, 2)) ||
+      (rc = map_linear(&t->mBuf1Lin, t->buf1, nb, N3, 2)) ||
+      (rc = map_b(&t->mBh_hi, t->bh_hi, kt_c, t->nout2, t->nout2)) ||
+      (rc = map_b(&t->mBh_lo, t->bh_lo, kt_c, t->nout2, t->nout2)) ||
+      (rc = map_b(&t->mBnr_hi, t->bnr_hi, kt_r, t->nout2, t->nout2)) ||
+      (rc = map_b(&t->mBnr_lo, t->bnr_lo, kt_r, t->nout2, t->nout2)) ||
+      (rc = map_b(&t->mBnc_hi, t->bnc_hi, kt_c, t->nout2, t->nout2)) ||
+      (rc = map_b(&t->mBnc_lo, t->bnc_lo, kt_c, t->nout2, t->nout2)) ||
+      (rc = map_b(&t->mBnb_hi, t->bnb_hi, kt_c, t->nout2, t->nout2)) ||
+      (rc = map_b(&t->mBnb_lo, t->bnb_lo, kt_c, t->nout2, t->nout2)) ||
+      (rc = map_b(&t->mW_hi, t->w_hi, (int)N3, nb, t->nout1)) ||
+      (rc = map_b(&t->mW_lo, t->w_lo, (int)N3, nb, t->nout1))) {
+    set_error_detail("cuTensorMapEncodeTiled failed");
+    return bail(rc);
+  }
+  int st = 0;
+  const size_t smax = std::max(gemm_smem(t->nout2, &st), gemm_smem(t->nout1, &st, (size_t)nb * (nb + 1) * sizeof(double)));
+  if (smax > 227 * 1024) {
+    set_error_detail("basis too large for the FP64 split-K accumulator of the tensor-core collision integral");
+    return bail(G1G2_EUNSUPPORTED);
+  }
+  if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax) != cudaSuccess ||
+      cudaFuncSetAttribute(orbit_assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(4 * BEL * sizeof(float2))) != cudaSuccess) {
+    set_error_detail("cannot raise the shared-memory limit of the tensor-core kernels");
+    return bail(G1G2_ECUDA);
+  }
+  *out = t;
+  return G1G2_OK;
+}
+
+void tc_destroy(TcPath *p) {
+  if (!p) return;
+  for (void *q : p->allocs) cudaFree(q);
+  delete p;
+}
+
+int tc_error(TcPath *p, cudaStream_t stream) {
+  int e = 0;
+  if (cudaMemcpyAsync(&e, p->err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess) return G1G2_ECUDA;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return G1G2_ECUDA;
+  if (e) {
+    set_error_detail("a tensor-core kernel gave up waiting on a barrier");
+    return G1G2_ETIMEOUT;
+  }
+  return G1G2_OK;
+}
+
+void tc_load_state(TcPath *p, Launcher &L, const cplx *G) {
+  L.before("tc_to_planar");
+  to_planar_f32_kernel<<<2048, 256, 0, L.stream>>>(p->N4, G, p->y32);
+  L.after_launch();
+}
+
+void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cplx *hhf, Rk4Stage st, cplx *ny,
+            cplx *nys, cplx *nacc, cplx *nk, cplx *Gy, cplx *Gys, cplx *Gacc, cplx *Gk) {
+  (void)Gys;
+  (void)Gacc;
+  const int nb = t->nb;
+  const long long N = nb, N3 = N * N * N;
+  // stage input of G2 in FP32 planar
+  const bool from_y = (st.stage == 0);
+  if (st.stage < 0) {
+    L.before("tc_to_planar");
+    to_planar_f32_kernel<<<2048, 256, 0, L.stream>>>(t->N4, G_in, t->ys32);
+    L.after_launch();
+  }
+  const CUtensorMap &mZin = from_y ? t->mZin_y32 : t->mZin_ys32;
+  const CUtensorMap &mCol = from_y ? t->mCol_y32 : t->mCol_ys32;
+  // small operands
+  one_minus(L, nb, n_in, t->nbar);
+  {
+    struct { const cplx *S; int complex_a, shift; float *hi, *lo; } ops[4] = {
+        {hhf, 1, 1, t->bh_hi, t->bh_lo}, {n_in, 0, 0, t->bnr_hi, t->bnr_lo},
+        {n_in, 1, 0, t->bnc_hi, t->bnc_lo}, {t->nbar, 1, 0, t->bnb_hi, t->bnb_lo}};
+    for (auto &o : ops) {
+      L.before("tc_realify");
+      realify_kernel<<<64, 256, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.S, o.hi, o.lo);
+      L.after_launch();
+    }
+  }
+  // a2: collision integral, split-K over c = (k,l,p)
+  {
+    GemmParams g{};
+    g.nb = nb;
+    g.a_rows = AR_SPLITK;
+    g.epi = EP_PARTIAL;
+    g.splits = t->splits;
+    g.kb_per_split = t->kb_per_split;
+    g.kb_all = t->kb_all_coll;
+    g.tiles = 2 * t->splits;
+    g.kb_per_plane = t->kb_per_split;
+    g.a_planes = 1;
+    g.nout = t->nout1;
+    g.n_valid = nb;
+    g.kb_chunks = 1;
+    g.out64 = t->partial;
+    launch_gemm(t, L, "tc_gemm_collision", mCol, t->mW_hi, t->mW_lo, g);
+    L.before("tc_collision_reduce");
+    collision_reduce_kernel<<<(nb * nb + 127) / 128, 128, 0, L.stream>>>(nb, t->splits, t->partial, t->I);
+    L.after_launch();
+  }
+  g1_update(L, nb, hhf, n_in, t->I, st, ny, nys, nacc, nk);
+  // a3: Z = G2 x_4 hHF
+  launch_gemm(t, L, "tc_gemm_commutator", mZin, t->mBh_hi, t->mBh_lo, linear_params(t, N3, 2, EP_DIRECT, t->Z));
+  // a4: the source-term chain
+  launch_gemm(t, L, "tc_gemm_psi1", t->mW32, t->mBnr_hi, t->mBnr_lo, linear_params(t, N3, 1, EP_EXCH_T, t->buf1));
+  {
+    GemmParams g = linear_params(t, N3, 2, EP_GATHER_TCONJ, t->buf2);
+    g.a_rows = AR_GATHER4;
+    g.g_na = (nb + 3) / 4;
+    g.g_nb = (nb + 31) / 32;
+    g.tiles = nb * g.g_na * g.g_nb;
+    launch_gemm(t, L, "tc_gemm_psi2", t->mBuf1Gather, t->mBnc_hi, t->mBnc_lo, g);
+  }
+  launch_gemm(t, L, "tc_gemm_psi3", t->mBuf2Lin, t->mBnb_hi, t->mBnb_lo, linear_params(t, N3, 2, EP_EXCH_T, t->buf1));
+  launch_gemm(t, L, "tc_gemm_psi4", t->mBuf1Lin, t->mBnb_hi, t->mBnb_lo, linear_params(t, N3, 2, EP_DIRECT, t->buf2));
+  // a7: orbit assembly + RK4
+  AsmParams a{};
+  a.nb = nb;
+  a.nblk = t->nblocks;
+  a.blocks = t->blocks;
+  a.Z = t->Z;
+  a.Q = t->buf2;
+  a.Pi = nullptr;
+  a.P = t->N4;
+  a.y = Gy;
+  a.acc = t->acc;
+  a.ys = t->ys32;
+  a.y32 = t->y32;
+  a.kout = Gk;
+  a.stage = st.stage;
+  a.dt = st.dt;
+  L.before("tc_orbit_assemble_rk4");
+  orbit_assemble_kernel<<<t->nblocks, 256, 4 * BEL * sizeof(float2), L.stream>>>(a);
+  L.after_launch();
+}
 
 }  // namespace g1g2

@@ -13,6 +13,11 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, con
               cudaStream_t stream);
 void tc_destroy(TcPath *p);
 
+// Refresh the FP32 copy of the G2 state (after init / set_state).
+void tc_load_state(TcPath *p, Launcher &L, const cplx *G);
+// G1G2_ETIMEOUT when a tensor-core kernel gave up on a barrier (synchronises the stream).
+int tc_error(TcPath *p, cudaStream_t stream);
+
 // One right-hand side (hhf already built from n_in): collision integral and
 // G1 update, then the G2 contractions and the assembly with the RK4 update.
 void tc_rhs(TcPath *p, Launcher &L, const cplx *n_in, const cplx *G_in, const cplx *hhf, Rk4Stage st,
