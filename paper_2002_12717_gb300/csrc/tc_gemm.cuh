@@ -30,13 +30,17 @@ enum ARows : int {
   AR_LINEAR = 0,   // A viewed as [plane][row][k]; tile = 128 consecutive rows
   AR_GATHER4 = 1,  // A = T[plane][a][b][c][k]; tile = rows (a: 4, b: 32) at fixed c
   AR_SPLITK = 2,   // A = G[plane][j][c]; tile = (plane, K split), rows j
+  AR_PI = 3,       // A = G[plane][i][p][k][q]; tile rows (i: 4, k: 32), K blocks over (plane, p, q)
 };
 
+// Output index maps.  In every map the fastest-varying output index is the
+// tile row, so the 32 lanes of a warp store 32 consecutive floats per column.
 enum Epi : int {
-  EP_DIRECT = 0,        // out[v][row][l]
+  EP_SWAP34 = 0,        // row (i,j,k), col l -> out[v][i][j][l][k]
   EP_EXCH_T = 1,        // row (p,q,r), col l -> out[v][q][p][l][r]
   EP_GATHER_TCONJ = 2,  // row (a,b,c), col d -> out[v][c][d][a][b], imaginary plane negated
-  EP_PARTIAL = 3,       // split-K partial sums: partial[split][plane][row][col]
+  EP_PARTIAL = 3,       // split-K sums: partial[split][plane][row][col] (FP64 from a compensated FP32 sum)
+  EP_PI = 4,            // row (i,k), col (j,l,v) interleaved -> out[v][i][j][l][k]
 };
 
 struct GemmParams {
@@ -53,10 +57,17 @@ struct GemmParams {
   int splits;         // AR_SPLITK: K splits per plane
   int kb_per_split;   //            K blocks per split
   int kb_all;         //            K blocks in total
-  int kb_chunks;      // AR_SPLITK: each K block is its own TMEM accumulation, summed in FP64 smem
+  int kb_chunks;      // AR_SPLITK: K blocks per TMEM accumulation (0: one accumulation per tile),
+                      //            chunks summed in shared memory
   double *out64;      //            FP64 partial sums [split][plane][row][col]
   float *out;
   long long out_plane;
+  int kb_first;       // AR_LINEAR with two A tensors: K blocks [0, kb_first) read tmA,
+                      // [kb_first, kb_total) read tmA2 (same rows); 0 = one A tensor
+  int n_tiles;        // output column tiles of width nout (B rows n_tile*nout ...); 1 for most passes
+  int pi_mk, pi_kq;   // AR_PI: number of k-blocks (32) per i-block; q-blocks (32) per p
+  int pi_mtiles;      // AR_PI: row tiles; tile = n_tile * pi_mtiles + m_tile (column-tile outer,
+                      //        so concurrent CTAs share the B column tile in L2)
   int *err;
 };
 
@@ -67,12 +78,14 @@ __device__ __forceinline__ int tile_kblocks(const GemmParams &p, int tile) {
     const int n = p.kb_all - b0;
     return n < p.kb_per_split ? (n > 0 ? n : 0) : p.kb_per_split;
   }
-  return p.kb_per_plane * p.a_planes;
+  if (p.a_rows == AR_PI) return 2 * p.nb * p.pi_kq;
+  return p.kb_per_plane * p.a_planes * (p.kb_first ? 2 : 1);
 }
 
 __global__ void __launch_bounds__(256, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
-                   const __grid_constant__ CUtensorMap tmBlo, const GemmParams p, const int stages) {
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
+                   const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
+                   const GemmParams p, const int stages) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t b_bytes = (uint32_t)p.nout * kBlockK * 4;
@@ -85,7 +98,7 @@ __global__ void __launch_bounds__(256, 1)
   uint64_t *tempty = tfull + 2;
   uint64_t *fin = tempty + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
-  double *acc64 = reinterpret_cast<double *>(smem + (size_t)stages * stage_bytes + 256);
+  float2 *acc2 = reinterpret_cast<float2 *>(smem + (size_t)stages * stage_bytes + 256);  // (sum, error) pairs
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -121,13 +134,22 @@ __global__ void __launch_bounds__(256, 1)
           mbar_arrive_expect_tx(&full[s], kABytes + 2 * b_bytes);
           int bk;  // K coordinate (floats) of this block in B
           if (p.a_rows == AR_LINEAR) {
-            const int u = kb / p.kb_per_plane, pb = kb % p.kb_per_plane;
-            tma_load_3d(st, &tmA, &full[s], pb * kBlockK, tile * kTileM, u);
+            const bool second = p.kb_first && kb >= p.kb_first;
+            const int kl = second ? kb - p.kb_first : kb;
+            const int u = kl / p.kb_per_plane, pb = kl % p.kb_per_plane;
+            tma_load_3d(st, second ? &tmA2 : &tmA, &full[s], pb * kBlockK, tile * kTileM, u);
             bk = kb * kBlockK;
           } else if (p.a_rows == AR_GATHER4) {
             const int u = kb / p.kb_per_plane, pb = kb % p.kb_per_plane;
             const int bB = tile % p.g_nb, aB = (tile / p.g_nb) % p.g_na, c = tile / (p.g_nb * p.g_na);
             tma_load_5d(st, &tmA, &full[s], pb * kBlockK, c, bB * 32, aB * 4, u);
+            bk = kb * kBlockK;
+          } else if (p.a_rows == AR_PI) {
+            const int mt = tile % p.pi_mtiles;
+            const int kB = mt % p.pi_mk, iB = mt / p.pi_mk;
+            const int qb = kb % p.pi_kq, rest = kb / p.pi_kq;
+            const int pp = rest % N, u = rest / N;
+            tma_load_5d(st, &tmA, &full[s], qb * kBlockK, kB * 32, pp, iB * 4, u);
             bk = kb * kBlockK;
           } else {
             const int u = tile / p.splits, split = tile % p.splits;
@@ -135,8 +157,9 @@ __global__ void __launch_bounds__(256, 1)
             tma_load_3d(st, &tmA, &full[s], kglob, 0, u);
             bk = kglob;
           }
-          tma_load_3d(st + 2 * kABytes, &tmBhi, &full[s], bk, 0, 0);
-          tma_load_3d(st + 2 * kABytes + b_bytes, &tmBlo, &full[s], bk, 0, 0);
+          const int brow = (p.a_rows == AR_PI) ? (tile / p.pi_mtiles) * p.nout : 0;
+          tma_load_3d(st + 2 * kABytes, &tmBhi, &full[s], bk, brow, 0);
+          tma_load_3d(st + 2 * kABytes + b_bytes, &tmBlo, &full[s], bk, brow, 0);
           if (++s == stages) { s = 0; ph ^= 1u; }
         }
       }
@@ -155,12 +178,14 @@ __global__ void __launch_bounds__(256, 1)
           tc_fence_after();
         }
         for (int kb = 0; kb < nkb; ++kb) {
-          if (p.kb_chunks) {
+          const bool chunk_start = p.kb_chunks && (kb % p.kb_chunks == 0);
+          const bool chunk_end = p.kb_chunks && (kb % p.kb_chunks == p.kb_chunks - 1 || kb == nkb - 1);
+          if (chunk_start) {
             if (!mbar_wait(&tempty[acc], acc_ph ^ 1u, p.err)) { ok = false; break; }
             tc_fence_after();
           }
           const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kAccCols);
-          const uint32_t first = p.kb_chunks ? 0u : (uint32_t)kb;
+          const uint32_t first = p.kb_chunks ? (uint32_t)(kb % p.kb_chunks) : (uint32_t)kb;
           if (!mbar_wait(&conv[s], ph, p.err)) { ok = false; break; }
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
@@ -175,7 +200,7 @@ __global__ void __launch_bounds__(256, 1)
           }
           mma_commit(&empty[s]);
           if (++s == stages) { s = 0; ph ^= 1u; }
-          if (p.kb_chunks) {
+          if (chunk_end) {
             mma_commit(&tfull[acc]);
             if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
           }
@@ -226,16 +251,19 @@ __global__ void __launch_bounds__(256, 1)
     uint32_t acc_ph = 0;
     const long long NN = N;
     if (p.kb_chunks) {
-      // split-K with FP64 accumulation: every K block arrives as its own FP32 tile
+      // split-K: every K block arrives as its own FP32 tile and is added to a
+      // compensated (sum, error) FP32 pair per output (Knuth's TwoSum), which
+      // keeps about twice the FP32 precision at FP32 speed
       const int nv = p.n_valid;
-      const int ld = nv + 1;  // odd row stride in doubles: no shared-memory bank conflicts across rows
+      const int ld = nv + 1;  // odd row stride: no shared-memory bank conflicts across rows
       bool ok = true;
       for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
         const int nkb = tile_kblocks(p, tile);
         const int u = tile / p.splits, split = tile % p.splits;
         if (r < N)
-          for (int col = 0; col < nv; ++col) acc64[r * ld + col] = 0.0;
-        for (int kb = 0; kb < nkb; ++kb) {
+          for (int col = 0; col < nv; ++col) acc2[r * ld + col] = make_float2(0.f, 0.f);
+        const int nchunks = (nkb + p.kb_chunks - 1) / p.kb_chunks;
+        for (int ch = 0; ch < nchunks; ++ch) {
           if (!mbar_wait(&tfull[acc], acc_ph, p.err)) { ok = false; break; }
           tc_fence_after();
           const uint32_t tbase = tmem_base + lane_base + (uint32_t)(acc * kAccCols);
@@ -244,8 +272,17 @@ __global__ void __launch_bounds__(256, 1)
             tmem_ld32(tbase + (uint32_t)c0, v);
             if (r < N) {
 #pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (c0 + j < nv) acc64[r * ld + c0 + j] += (double)v[j];
+              for (int j = 0; j < 32; ++j) {
+                if (c0 + j < nv) {
+                  float2 a = acc2[r * ld + c0 + j];
+                  const float sum = a.x + v[j];
+                  const float bp = sum - a.x;
+                  const float err = (a.x - (sum - bp)) + (v[j] - bp);
+                  a.x = sum;
+                  a.y += err;
+                  acc2[r * ld + c0 + j] = a;
+                }
+              }
             }
           }
           tc_fence_before();
@@ -254,8 +291,10 @@ __global__ void __launch_bounds__(256, 1)
         }
         if (!ok) break;
         if (r < N)
-          for (int col = 0; col < nv; ++col)
-            p.out64[(((long long)split * 2 + u) * NN + r) * nv + col] = acc64[r * ld + col];
+          for (int col = 0; col < nv; ++col) {
+            const float2 a = acc2[r * ld + col];
+            p.out64[(((long long)split * 2 + u) * NN + r) * nv + col] = (double)a.x + (double)a.y;
+          }
       }
     } else
     for (int tile = blockIdx.x; tile < p.tiles; tile += gridDim.x) {
@@ -277,6 +316,13 @@ __global__ void __launch_bounds__(256, 1)
         i1 = bB * 32 + r % 32;  // b
         i2 = c;
         valid = i0 < NN && i1 < NN;
+      } else if (p.a_rows == AR_PI) {
+        const int mt = tile % p.pi_mtiles;
+        const int kB = mt % p.pi_mk, iB = mt / p.pi_mk;
+        i0 = iB * 4 + r / 32;   // i
+        i2 = kB * 32 + r % 32;  // k
+        grow = (long long)(tile / p.pi_mtiles) * p.nout;  // first global output column of the tile
+        valid = i0 < NN && i2 < NN;
       } else {
         u = tile / p.splits;
         split = tile % p.splits;
@@ -295,12 +341,20 @@ __global__ void __launch_bounds__(256, 1)
             p.out[(((long long)split * 2 + u) * NN + r) * p.n_valid + col] = v[j];
             continue;
           }
-          const int vv = col / N;
-          const long long l = col % N;
+          const int vv = col >= N ? 1 : 0;
+          const long long l = col - vv * N;
           float x = v[j];
           long long idx;
-          if (p.epi == EP_DIRECT) {
-            idx = grow * NN + l;
+          if (p.epi == EP_PI) {
+            const long long cg = grow + col;  // (j, l, v) interleaved
+            if (cg >= p.rows) continue;
+            const long long jl = cg >> 1;
+            const long long jj = jl / NN, ll = jl - jj * NN;
+            p.out[(cg & 1) * p.out_plane + ((i0 * NN + jj) * NN + ll) * NN + i2] = x;
+            continue;
+          }
+          if (p.epi == EP_SWAP34) {
+            idx = ((i0 * NN + i1) * NN + l) * NN + i2;
           } else if (p.epi == EP_EXCH_T) {
             idx = ((i1 * NN + i0) * NN + l) * NN + i2;
           } else {

@@ -18,7 +18,7 @@
 //       A^dag = T2~ x_4 nbar                                          (4 passes)
 //   collision integral (Eq. eom_gone-I): I_ij = -i sum_c w_ic conj(G2_jc) with
 //     c = (k,l,p), both operands row-contiguous; split-K over c.
-//   assembly: P = U - (Q + Q~)/2 with Q = A^dag, dG2 = -i (P^dag - P), read as
+//   assembly: P = U - (Q + exch Q)/2 with Q = A^dag and dG2 = -i (P^dag - P), read as
 //     the orbit {X, exch X, trans X, exch trans X} of 8^4 blocks so every
 //     input block is read once; the RK4 stage update is fused.
 #include "tc_path.h"
@@ -44,8 +44,8 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // B operand of "X x_4 S" for a complex (planar) X: rows (v, l), K' = (u, p):
 // (a_re, a_im) * S_pl as a real 2x2 block [[S_re, S_im], [-S_im, S_re]].
 // Real X: rows (v, l), K' = p: S_v[p][l].  hi = TF32(x), lo = TF32(x - hi).
-__global__ void realify_kernel(int nb, int nout, int kpad, int complex_a, int shift, const cplx *__restrict__ S,
-                               float *hi, float *lo) {
+__global__ void realify_kernel(int nb, int nout, int kpad, int complex_a, int shift, double scale, int ld, int col0,
+                               int transpose, const cplx *__restrict__ S, float *hi, float *lo) {
   const int kt = complex_a ? 2 * kpad : kpad;
   const int total = nout * kt;
   // optional shift S -> S - mu 1 with mu = Re Tr S / nb (the commutator does not see it)
@@ -61,16 +61,17 @@ __global__ void realify_kernel(int nb, int nout, int kpad, int complex_a, int sh
       const int u = complex_a ? col / kpad : 0;
       const int pp = complex_a ? col % kpad : col;
       if (pp < nb) {
-        cplx s = S[pp * nb + l];
+        cplx s = transpose ? S[l * nb + pp] : S[pp * nb + l];
         if (pp == l) s.x -= mu;
         if (!complex_a) x = v ? s.y : s.x;
         else if (u == 0) x = v ? s.y : s.x;
         else x = v ? s.x : -s.y;
       }
     }
+    x *= scale;
     const float h = to_tf32((float)x);
-    hi[e] = h;
-    lo[e] = to_tf32((float)(x - (double)h));
+    hi[row * ld + col0 + col] = h;
+    lo[row * ld + col0 + col] = to_tf32((float)(x - (double)h));
   }
 }
 
@@ -106,10 +107,54 @@ __global__ void collision_reduce_kernel(int nb, int splits, const double *__rest
   I[e] = {-d1, -d0};
 }
 
+// B operand of the polarisation GEMM: rows (j,l,v) interleaved as 2 (j nb + l) + v,
+// K = (u, p, q) as (u nb + p) kpad + q, value R(hcorr_qjpl)[u][v] split into TF32
+// hi/lo, with hcorr_qjpl = Y1_qjpl - Y2_plqj (Y1 = w x_4 n, Y2 = w x_4 n^T, both
+// in the swapped layout [a][b][d][c]).  One CTA per (j,l) and 32x32 (p,q) tile.
+__global__ void realify_pi_kernel(int nb, int kpad, const float *__restrict__ Y1s, const float *__restrict__ Y2s,
+                                  long long P, float *hi, float *lo, long long ldb) {
+  __shared__ float2 t1[32][33];
+  const long long N = nb;
+  const long long jl = blockIdx.y;
+  const long long j = jl / N, l = jl % N;
+  const int ntq = kpad / 32;
+  const int p0 = (blockIdx.x / ntq) * 32, q0 = (blockIdx.x % ntq) * 32;
+  const int tx = threadIdx.x, ty0 = threadIdx.y;
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int q = q0 + ty, pp = p0 + tx;
+    float2 v = make_float2(0.f, 0.f);
+    if (q < nb && pp < nb) {
+      const long long g = ((q * N + j) * N + l) * N + pp;   // Y1_{q j p l} at [q][j][l][p]
+      v = make_float2(Y1s[g], Y1s[P + g]);
+    }
+    t1[ty][tx] = v;
+  }
+  __syncthreads();
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int pp = p0 + ty, q = q0 + tx;
+    if (pp >= nb) continue;
+    float2 h = make_float2(0.f, 0.f);
+    if (q < nb) {
+      const long long g = ((pp * N + l) * N + j) * N + q;   // Y2_{p l q j} at [p][l][j][q]
+      const float2 a = t1[tx][ty];
+      h = make_float2(a.x - Y2s[g], a.y - Y2s[P + g]);
+    }
+    for (int u = 0; u < 2; ++u)
+      for (int v = 0; v < 2; ++v) {
+        const float x = (u == 0) ? (v ? h.y : h.x) : (v ? h.x : -h.y);
+        const long long row = 2 * jl + v;
+        const long long col = ((long long)u * N + pp) * kpad + q;
+        const float hh = to_tf32(x);
+        hi[row * ldb + col] = hh;
+        lo[row * ldb + col] = to_tf32(x - hh);
+      }
+  }
+}
+
 struct AsmParams {
   int nb, nblk;
   const int4 *blocks;
-  const float *Z, *Q, *Pi;     // planar FP32 (plane stride P)
+  const float *Z, *Q, *Pi;     // planar FP32 (plane stride P); Z, Q in the swapped layout
   long long P;
   cplx *y;                     // FP64 state (interleaved)
   float *acc;                  // planar FP32
@@ -121,126 +166,173 @@ struct AsmParams {
 };
 
 __device__ __forceinline__ int bidx(int a, int b, int c, int d) { return ((a * BSZ + b) * BSZ + c) * BSZ + d; }
+// Shared-memory slot of block element (a,b,c,d): the last coordinate is XOR-swizzled
+// with the other three so that the four orbit permutations hit (nearly) distinct banks.
+__device__ __forceinline__ int sidx(int a, int b, int c, int d) { return bidx(a, b, c, d ^ ((a ^ b ^ c) & 7)); }
 
-__device__ __forceinline__ void load_blocks(const AsmParams &p, const float *src, const int (&X)[4][4], float2 *sm) {
-  const long long N = p.nb;
-  for (int m = 0; m < 4; ++m) {
-    for (int e = threadIdx.x; e < BEL; e += blockDim.x) {
-      const int a = e >> 9, b = (e >> 6) & 7, c = (e >> 3) & 7, d = e & 7;
-      const long long g0 = X[m][0] * BSZ + a, g1 = X[m][1] * BSZ + b, g2 = X[m][2] * BSZ + c, g3 = X[m][3] * BSZ + d;
-      float2 v = {0.f, 0.f};
-      if (g0 < N && g1 < N && g2 < N && g3 < N) {
-        const long long g = ((g0 * N + g1) * N + g2) * N + g3;
-        v.x = src[g];
-        v.y = src[p.P + g];
-      }
-      sm[m * BEL + e] = v;
-    }
-  }
+constexpr int ATHREADS = 1024;              // assembly threads per CTA
+constexpr int APER = BEL / ATHREADS;        // element orbits per thread
+
+__device__ __forceinline__ void elem(int e, int &a, int &b, int &c, int &d) {
+  a = e >> 9; b = (e >> 6) & 7; c = (e >> 3) & 7; d = e & 7;
 }
 
-__global__ void __launch_bounds__(256) orbit_assemble_kernel(const AsmParams p) {
-  extern __shared__ float2 sm[];  // 4 blocks of BEL complex values
+// Load the four member blocks of src into sm.  With swap34 the tensor is stored
+// with its last two indices exchanged (the GEMM epilogue layout), so block
+// (B0,B1,B2,B3) is read as the stored block (B0,B1,B3,B2); its element for the
+// natural index (a,b,c,d) then sits at bidx(a,b,d,c).
+__device__ __forceinline__ void load_blocks(const AsmParams &p, const float *src, const int (&X)[4][4], float2 *sm,
+                                            bool swap34) {
+  const long long N = p.nb;
+  float2 v[4][APER];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int B2 = swap34 ? X[m][3] : X[m][2], B3 = swap34 ? X[m][2] : X[m][3];
+#pragma unroll
+    for (int t = 0; t < APER; ++t) {
+      int a, b, c, d;
+      elem(threadIdx.x + ATHREADS * t, a, b, c, d);
+      const long long g0 = X[m][0] * BSZ + a, g1 = X[m][1] * BSZ + b, g2 = B2 * BSZ + c, g3 = B3 * BSZ + d;
+      v[m][t] = make_float2(0.f, 0.f);
+      if (g0 < N && g1 < N && g2 < N && g3 < N) {
+        const long long g = ((g0 * N + g1) * N + g2) * N + g3;
+        v[m][t].x = src[g];
+        v[m][t].y = src[p.P + g];
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int t = 0; t < APER; ++t) {
+      int a, b, c, d;
+      elem(threadIdx.x + ATHREADS * t, a, b, c, d);
+      sm[m * BEL + sidx(a, b, c, d)] = v[m][t];
+    }
+}
+
+__device__ __forceinline__ float2 sval(const float2 *sm, int m, int a, int b, int c, int d, bool swap34) {
+  return sm[m * BEL + (swap34 ? sidx(a, b, d, c) : sidx(a, b, c, d))];
+}
+
+// One CTA per orbit {X, exch X, trans X, exch trans X} of 8^4 blocks, each
+// thread APER element orbits.  Z and Q arrive in the swapped layout.
+__global__ void __launch_bounds__(ATHREADS) orbit_assemble_kernel(const AsmParams p) {
+  extern __shared__ float2 sm[];  // 4 * BEL
   const int4 base = p.blocks[blockIdx.x];
   const int X[4][4] = {{base.x, base.y, base.z, base.w},
                        {base.y, base.x, base.w, base.z},
                        {base.z, base.w, base.x, base.y},
                        {base.w, base.z, base.y, base.x}};
-  constexpr int PER = BEL / 256;
-  float2 kx[PER], ky[PER];
+  float2 kx[APER], ky[APER];
 
-  load_blocks(p, p.Z, X, sm);
+  load_blocks(p, p.Z, X, sm, true);
   __syncthreads();
 #pragma unroll
-  for (int t = 0; t < PER; ++t) {
-    const int e = threadIdx.x + 256 * t;
-    const int a = e >> 9, b = (e >> 6) & 7, c = (e >> 3) & 7, d = e & 7;
-    const float2 z0 = sm[0 * BEL + bidx(a, b, c, d)], z1 = sm[1 * BEL + bidx(b, a, d, c)];
-    const float2 z2 = sm[2 * BEL + bidx(c, d, a, b)], z3 = sm[3 * BEL + bidx(d, c, b, a)];
-    kx[t] = {z0.x + z1.x, z0.y + z1.y};
-    ky[t] = {z2.x + z3.x, z2.y + z3.y};
+  for (int t = 0; t < APER; ++t) {
+    int a, b, c, d;
+    elem(threadIdx.x + ATHREADS * t, a, b, c, d);
+    const float2 z0 = sval(sm, 0, a, b, c, d, true), z1 = sval(sm, 1, b, a, d, c, true);
+    const float2 z2 = sval(sm, 2, c, d, a, b, true), z3 = sval(sm, 3, d, c, b, a, true);
+    kx[t] = make_float2(z0.x + z1.x, z0.y + z1.y);
+    ky[t] = make_float2(z2.x + z3.x, z2.y + z3.y);
   }
   __syncthreads();
-  load_blocks(p, p.Q, X, sm);
+  load_blocks(p, p.Q, X, sm, true);
   __syncthreads();
 #pragma unroll
-  for (int t = 0; t < PER; ++t) {
-    const int e = threadIdx.x + 256 * t;
-    const int a = e >> 9, b = (e >> 6) & 7, c = (e >> 3) & 7, d = e & 7;
-    const float2 q0 = sm[0 * BEL + bidx(a, b, c, d)], q1 = sm[1 * BEL + bidx(b, a, d, c)];
-    const float2 q2 = sm[2 * BEL + bidx(c, d, a, b)], q3 = sm[3 * BEL + bidx(d, c, b, a)];
-    const float2 P0 = {kx[t].x - 0.5f * (q0.x + q1.x), kx[t].y - 0.5f * (q0.y + q1.y)};
-    const float2 P2 = {ky[t].x - 0.5f * (q2.x + q3.x), ky[t].y - 0.5f * (q2.y + q3.y)};
+  for (int t = 0; t < APER; ++t) {
+    int a, b, c, d;
+    elem(threadIdx.x + ATHREADS * t, a, b, c, d);
+    // P = U - (Q + exch Q)/2 on the two exchange pairs of the orbit
+    const float2 q0 = sval(sm, 0, a, b, c, d, true), q1 = sval(sm, 1, b, a, d, c, true);
+    const float2 q2 = sval(sm, 2, c, d, a, b, true), q3 = sval(sm, 3, d, c, b, a, true);
+    const float2 P0 = make_float2(kx[t].x - 0.5f * (q0.x + q1.x), kx[t].y - 0.5f * (q0.y + q1.y));
+    const float2 P2 = make_float2(ky[t].x - 0.5f * (q2.x + q3.x), ky[t].y - 0.5f * (q2.y + q3.y));
     // k0 = -i (conj(P2) - P0),  k2 = -i (conj(P0) - P2)
-    const float2 D = {P2.x - P0.x, -P2.y - P0.y};
-    const float2 E = {P0.x - P2.x, -P0.y - P2.y};
-    kx[t] = {D.y, -D.x};
-    ky[t] = {E.y, -E.x};
+    const float2 D = make_float2(P2.x - P0.x, -P2.y - P0.y);
+    const float2 E = make_float2(P0.x - P2.x, -P0.y - P2.y);
+    kx[t] = make_float2(D.y, -D.x);
+    ky[t] = make_float2(E.y, -E.x);
   }
   if (p.Pi) {
     __syncthreads();
-    load_blocks(p, p.Pi, X, sm);
+    load_blocks(p, p.Pi, X, sm, true);
     __syncthreads();
 #pragma unroll
-    for (int t = 0; t < PER; ++t) {
-      const int e = threadIdx.x + 256 * t;
-      const int a = e >> 9, b = (e >> 6) & 7, c = (e >> 3) & 7, d = e & 7;
-      const float2 p0 = sm[0 * BEL + bidx(a, b, c, d)], p1 = sm[1 * BEL + bidx(b, a, d, c)];
-      const float2 p2 = sm[2 * BEL + bidx(c, d, a, b)], p3 = sm[3 * BEL + bidx(d, c, b, a)];
+    for (int t = 0; t < APER; ++t) {
+      int a, b, c, d;
+      elem(threadIdx.x + ATHREADS * t, a, b, c, d);
+      const float2 p0 = sval(sm, 0, a, b, c, d, true), p1 = sval(sm, 1, b, a, d, c, true);
+      const float2 p2 = sval(sm, 2, c, d, a, b, true), p3 = sval(sm, 3, d, c, b, a, true);
       // R = Pi_ijkl - conj(Pi_lkji) on the four members, symmetrised over exchange
-      const float2 s01 = {0.5f * ((p0.x - p3.x) + (p1.x - p2.x)), 0.5f * ((p0.y + p3.y) + (p1.y + p2.y))};
-      const float2 s23 = {0.5f * ((p2.x - p1.x) + (p3.x - p0.x)), 0.5f * ((p2.y + p1.y) + (p3.y + p0.y))};
-      kx[t] = {kx[t].x + s01.y, kx[t].y - s01.x};
-      ky[t] = {ky[t].x + s23.y, ky[t].y - s23.x};
+      const float2 s01 = make_float2(0.5f * ((p0.x - p3.x) + (p1.x - p2.x)), 0.5f * ((p0.y + p3.y) + (p1.y + p2.y)));
+      const float2 s23 = make_float2(0.5f * ((p2.x - p1.x) + (p3.x - p0.x)), 0.5f * ((p2.y + p1.y) + (p3.y + p0.y)));
+      kx[t] = make_float2(kx[t].x + s01.y, kx[t].y - s01.x);
+      ky[t] = make_float2(ky[t].x + s23.y, ky[t].y - s23.x);
     }
   }
   __syncthreads();
 #pragma unroll
-  for (int t = 0; t < PER; ++t) {
-    const int e = threadIdx.x + 256 * t;
-    const int a = e >> 9, b = (e >> 6) & 7, c = (e >> 3) & 7, d = e & 7;
-    sm[0 * BEL + bidx(a, b, c, d)] = kx[t];
-    sm[1 * BEL + bidx(b, a, d, c)] = kx[t];
-    sm[2 * BEL + bidx(c, d, a, b)] = ky[t];
-    sm[3 * BEL + bidx(d, c, b, a)] = ky[t];
+  for (int t = 0; t < APER; ++t) {
+    int a, b, c, d;
+    elem(threadIdx.x + ATHREADS * t, a, b, c, d);
+    sm[0 * BEL + sidx(a, b, c, d)] = kx[t];
+    sm[1 * BEL + sidx(b, a, d, c)] = kx[t];
+    sm[2 * BEL + sidx(c, d, a, b)] = ky[t];
+    sm[3 * BEL + sidx(d, c, b, a)] = ky[t];
   }
   __syncthreads();
-  // RK4 update of each distinct member block, in natural (coalesced) order
+  // RK4 update of each distinct member block, in natural (coalesced) order;
+  // all loads of a member are issued before its stores
   const long long N = p.nb;
+  cplx *__restrict__ yv = p.y;
+  float *__restrict__ accv = p.acc;
+  float *__restrict__ ysv = p.ys;
+  float *__restrict__ y32v = p.y32;
+  const long long P = p.P;
+  const double dt = p.dt;
   for (int m = 0; m < 4; ++m) {
     bool dup = false;
     for (int q = 0; q < m; ++q)
       dup |= (X[q][0] == X[m][0] && X[q][1] == X[m][1] && X[q][2] == X[m][2] && X[q][3] == X[m][3]);
     if (dup) continue;
-    for (int e = threadIdx.x; e < BEL; e += blockDim.x) {
-      const int a = e >> 9, b = (e >> 6) & 7, c = (e >> 3) & 7, d = e & 7;
+    long long g[APER];
+    bool in[APER];
+    float2 k[APER];
+    cplx y0[APER];
+    float2 ac[APER];
+#pragma unroll
+    for (int t = 0; t < APER; ++t) {
+      int a, b, c, d;
+      elem(threadIdx.x + ATHREADS * t, a, b, c, d);
       const long long g0 = X[m][0] * BSZ + a, g1 = X[m][1] * BSZ + b, g2 = X[m][2] * BSZ + c, g3 = X[m][3] * BSZ + d;
-      if (g0 >= N || g1 >= N || g2 >= N || g3 >= N) continue;
-      const long long g = ((g0 * N + g1) * N + g2) * N + g3;
-      const float2 k = sm[m * BEL + e];
-      if (p.stage < 0) {
-        p.kout[g] = {(double)k.x, (double)k.y};
-        continue;
+      in[t] = g0 < N && g1 < N && g2 < N && g3 < N;
+      g[t] = ((g0 * N + g1) * N + g2) * N + g3;
+      k[t] = sm[m * BEL + sidx(a, b, c, d)];
+      if (in[t] && p.stage >= 0) {
+        y0[t] = yv[g[t]];
+        ac[t] = (p.stage > 0) ? make_float2(accv[g[t]], accv[P + g[t]]) : make_float2(0.f, 0.f);
       }
-      const cplx y0 = p.y[g];
-      const double dt = p.dt;
-      if (p.stage == 0) {
-        p.acc[g] = k.x;
-        p.acc[p.P + g] = k.y;
-        p.ys[g] = (float)(y0.x + 0.5 * dt * k.x);
-        p.ys[p.P + g] = (float)(y0.y + 0.5 * dt * k.y);
+    }
+#pragma unroll
+    for (int t = 0; t < APER; ++t) {
+      if (!in[t]) continue;
+      if (p.stage < 0) {
+        p.kout[g[t]] = make_double2((double)k[t].x, (double)k[t].y);
       } else if (p.stage < 3) {
-        p.acc[g] += 2.f * k.x;
-        p.acc[p.P + g] += 2.f * k.y;
-        const double h = (p.stage == 1) ? 0.5 * dt : dt;
-        p.ys[g] = (float)(y0.x + h * k.x);
-        p.ys[p.P + g] = (float)(y0.y + h * k.y);
+        const double h = (p.stage == 2) ? dt : 0.5 * dt;
+        const float w = (p.stage == 0) ? 1.f : 2.f;
+        accv[g[t]] = ac[t].x + w * k[t].x;
+        accv[P + g[t]] = ac[t].y + w * k[t].y;
+        ysv[g[t]] = (float)(y0[t].x + h * k[t].x);
+        ysv[P + g[t]] = (float)(y0[t].y + h * k[t].y);
       } else {
-        const double nx = y0.x + dt / 6.0 * ((double)p.acc[g] + (double)k.x);
-        const double ny = y0.y + dt / 6.0 * ((double)p.acc[p.P + g] + (double)k.y);
-        p.y[g] = {nx, ny};
-        p.y32[g] = (float)nx;
-        p.y32[p.P + g] = (float)ny;
+        const double nx = y0[t].x + dt / 6.0 * ((double)ac[t].x + (double)k[t].x);
+        const double ny = y0[t].y + dt / 6.0 * ((double)ac[t].y + (double)k[t].y);
+        yv[g[t]] = make_double2(nx, ny);
+        y32v[g[t]] = (float)nx;
+        y32v[P + g[t]] = (float)ny;
       }
     }
   }
@@ -264,11 +356,11 @@ int map_linear(CUtensorMap *m, const float *base, int K, long long rows, int pla
   return encode_map(m, base, 3, dims, str, box);
 }
 // A = T[plane][a][b][c][s], box (s 32, c 1, b 32, a 4)
-int map_gather(CUtensorMap *m, const float *base, int N) {
+int map_gather(CUtensorMap *m, const float *base, int N, cuuint32_t b1 = 1, cuuint32_t b2 = 32, cuuint32_t b3 = 4) {
   const cuuint64_t n = N;
   cuuint64_t dims[5] = {n, n, n, n, 2};
   cuuint64_t str[4] = {n * 4, n * n * 4, n * n * n * 4, n * n * n * n * 4};
-  cuuint32_t box[5] = {(cuuint32_t)kBlockK, 1, 32, 4, 1};
+  cuuint32_t box[5] = {(cuuint32_t)kBlockK, b1, b2, b3, 1};
   return encode_map(m, base, 5, dims, str, box);
 }
 // small pre-split B operand [rows][kt]
@@ -297,6 +389,11 @@ struct TcPath {
   float *bnb_hi = nullptr, *bnb_lo = nullptr; // nbar, complex A
   double *partial = nullptr;
   cplx *nbar = nullptr, *I = nullptr;
+  // GW: Y1 = w x_4 n, Y2 = w x_4 n^T, polarisation Pi, its B operand
+  float *Y1 = nullptr, *Y2 = nullptr, *Pi = nullptr, *bpi_hi = nullptr, *bpi_lo = nullptr;
+  float *bnt_hi = nullptr, *bnt_lo = nullptr;   // n^T, real A
+  int pi_nout = 0, pi_ntiles = 0, pi_mtiles = 0;
+  long long pi_ldb = 0;
   int4 *blocks = nullptr;
   int nblocks = 0;
   int *err = nullptr;
@@ -304,6 +401,7 @@ struct TcPath {
   // tensor maps
   CUtensorMap mZin_y32, mZin_ys32, mCol_y32, mCol_ys32, mW32, mBuf1Gather, mBuf2Lin, mBuf1Lin;
   CUtensorMap mBh_hi, mBh_lo, mBnr_hi, mBnr_lo, mBnc_hi, mBnc_lo, mBnb_hi, mBnb_lo, mW_hi, mW_lo;
+  CUtensorMap mPi_y32, mPi_ys32, mBpi_hi, mBpi_lo, mBnt_hi, mBnt_lo;
 };
 
 namespace {
@@ -331,14 +429,14 @@ size_t gemm_smem(int nout, int *stages, size_t acc64_bytes = 0) {
 }
 
 void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, const CUtensorMap &Bh,
-                 const CUtensorMap &Bl, GemmParams gp) {
+                 const CUtensorMap &Bl, GemmParams gp, const CUtensorMap *A2 = nullptr) {
   gp.err = t->err;
   int stages = 0;
-  const size_t acc64 = gp.kb_chunks ? (size_t)gp.nb * (gp.n_valid + 1) * sizeof(double) : 0;
+  const size_t acc64 = gp.kb_chunks ? (size_t)gp.nb * (gp.n_valid + 1) * sizeof(float2) : 0;
   const size_t smem = gemm_smem(gp.nout, &stages, acc64);
   const int grid = std::max(1, std::min(gp.tiles, t->sms));
   L.before(tag);
-  tc_gemm_kernel<<<grid, 256, smem, L.stream>>>(A, Bh, Bl, gp, stages);
+  tc_gemm_kernel<<<grid, 256, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
   L.after_launch();
 }
 
@@ -364,10 +462,6 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, con
   *out = nullptr;
   if (nb % 4 != 0) {
     set_error_detail("the tensor-core form needs nb divisible by 4 (TMA row pitch)");
-    return G1G2_EUNSUPPORTED;
-  }
-  if (se == G1G2_GW) {
-    set_error_detail("the tensor-core form of GW is not built yet");
     return G1G2_EUNSUPPORTED;
   }
   const long long N = nb, N4 = N * N * N * N;
@@ -396,12 +490,28 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, con
   if ((rc = talloc(t, &t->y32, 2 * N4)) || (rc = talloc(t, &t->ys32, 2 * N4)) || (rc = talloc(t, &t->acc, 2 * N4)) ||
       (rc = talloc(t, &t->Z, 2 * N4)) || (rc = talloc(t, &t->buf1, 2 * N4)) || (rc = talloc(t, &t->buf2, 2 * N4)) ||
       (rc = talloc(t, &t->W32, N4)) || (rc = talloc(t, &t->w_hi, N4)) || (rc = talloc(t, &t->w_lo, N4)) ||
-      (rc = talloc(t, &t->bh_hi, (size_t)t->nout2 * kt_c)) || (rc = talloc(t, &t->bh_lo, (size_t)t->nout2 * kt_c)) ||
+      (rc = talloc(t, &t->bh_hi, (size_t)t->nout2 * 2 * kt_c)) ||
+      (rc = talloc(t, &t->bh_lo, (size_t)t->nout2 * 2 * kt_c)) ||
       (rc = talloc(t, &t->bnr_hi, (size_t)t->nout2 * kt_r)) || (rc = talloc(t, &t->bnr_lo, (size_t)t->nout2 * kt_r)) ||
       (rc = talloc(t, &t->bnc_hi, (size_t)t->nout2 * kt_c)) || (rc = talloc(t, &t->bnc_lo, (size_t)t->nout2 * kt_c)) ||
       (rc = talloc(t, &t->bnb_hi, (size_t)t->nout2 * kt_c)) || (rc = talloc(t, &t->bnb_lo, (size_t)t->nout2 * kt_c)) ||
       (rc = talloc(t, &t->nbar, N * N)) || (rc = talloc(t, &t->I, N * N)) || (rc = talloc(t, &t->err, 1)))
     return bail(rc);
+  if (se == G1G2_GW) {
+    const long long ncol = 2 * N * N;  // output columns (j, l, v)
+    t->pi_nout = (int)std::min<long long>(256, ((ncol + 15) / 16) * 16);
+    t->pi_ntiles = (int)((ncol + t->pi_nout - 1) / t->pi_nout);
+    t->pi_mtiles = ((nb + 3) / 4) * ((nb + 31) / 32);
+    t->pi_ldb = 2 * N * t->kpad;
+    const size_t brows = (size_t)t->pi_ntiles * t->pi_nout;
+    if ((rc = talloc(t, &t->Y1, 2 * N4)) || (rc = talloc(t, &t->Y2, 2 * N4)) || (rc = talloc(t, &t->Pi, 2 * N4)) ||
+        (rc = talloc(t, &t->bpi_hi, brows * t->pi_ldb)) || (rc = talloc(t, &t->bpi_lo, brows * t->pi_ldb)) ||
+        (rc = talloc(t, &t->bnt_hi, (size_t)t->nout2 * kt_r)) || (rc = talloc(t, &t->bnt_lo, (size_t)t->nout2 * kt_r)))
+      return bail(rc);
+    if (cudaMemset(t->bpi_hi, 0, brows * t->pi_ldb * sizeof(float)) != cudaSuccess ||
+        cudaMemset(t->bpi_lo, 0, brows * t->pi_ldb * sizeof(float)) != cudaSuccess)
+      return bail(G1G2_ECUDA);
+  }
   // collision split-K geometry: K = nb^3 floats, both planes
   t->kb_all_coll = (int)((N * N * N + kBlockK - 1) / kBlockK);
   t->splits = std::max(1, std::min(t->kb_all_coll, t->sms));
@@ -462,12 +572,19 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, con
       (rc = map_b(&t->mBnb_hi, t->bnb_hi, kt_c, t->nout2, t->nout2)) ||
       (rc = map_b(&t->mBnb_lo, t->bnb_lo, kt_c, t->nout2, t->nout2)) ||
       (rc = map_b(&t->mW_hi, t->w_hi, (int)N3, nb, t->nout1)) ||
-      (rc = map_b(&t->mW_lo, t->w_lo, (int)N3, nb, t->nout1))) {
+      (rc = map_b(&t->mW_lo, t->w_lo, (int)N3, nb, t->nout1)) ||
+      (se == G1G2_GW &&
+       ((rc = map_gather(&t->mPi_y32, t->y32, nb, 32, 1, 4)) || (rc = map_gather(&t->mPi_ys32, t->ys32, nb, 32, 1, 4)) ||
+        (rc = map_b(&t->mBpi_hi, t->bpi_hi, (int)t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
+        (rc = map_b(&t->mBpi_lo, t->bpi_lo, (int)t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
+        (rc = map_b(&t->mBnt_hi, t->bnt_hi, kt_r, t->nout2, t->nout2)) ||
+        (rc = map_b(&t->mBnt_lo, t->bnt_lo, kt_r, t->nout2, t->nout2))))) {
     set_error_detail("cuTensorMapEncodeTiled failed");
     return bail(rc);
   }
   int st = 0;
-  const size_t smax = std::max(gemm_smem(t->nout2, &st), gemm_smem(t->nout1, &st, (size_t)nb * (nb + 1) * sizeof(double)));
+  size_t smax = std::max(gemm_smem(t->nout2, &st), gemm_smem(t->nout1, &st, (size_t)nb * (nb + 1) * sizeof(float2)));
+  if (se == G1G2_GW) smax = std::max(smax, gemm_smem(t->pi_nout, &st));
   if (smax > 227 * 1024) {
     set_error_detail("basis too large for the FP64 split-K accumulator of the tensor-core collision integral");
     return bail(G1G2_EUNSUPPORTED);
@@ -523,12 +640,19 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   // small operands
   one_minus(L, nb, n_in, t->nbar);
   {
-    struct { const cplx *S; int complex_a, shift; float *hi, *lo; } ops[4] = {
-        {hhf, 1, 1, t->bh_hi, t->bh_lo}, {n_in, 0, 0, t->bnr_hi, t->bnr_lo},
-        {n_in, 1, 0, t->bnc_hi, t->bnc_lo}, {t->nbar, 1, 0, t->bnb_hi, t->bnb_lo}};
-    for (auto &o : ops) {
+    const int kc = 2 * t->kpad;
+    struct { const cplx *S; int complex_a, shift; double scale; int ld, col0, transpose; float *hi, *lo; } ops[5] = {
+        {hhf, 1, 1, 1.0, kc, 0, 0, t->bh_hi, t->bh_lo},
+        {n_in, 0, 0, 1.0, t->kpad, 0, 0, t->bnr_hi, t->bnr_lo},
+        {n_in, 1, 0, 1.0, kc, 0, 0, t->bnc_hi, t->bnc_lo},
+        {t->nbar, 1, 0, 1.0, kc, 0, 0, t->bnb_hi, t->bnb_lo},
+        {n_in, 0, 0, 1.0, t->kpad, 0, 1, t->bnt_hi, t->bnt_lo}};
+    const int nops = (t->se == G1G2_GW) ? 5 : 4;
+    for (int q = 0; q < nops; ++q) {
+      const auto &o = ops[q];
       L.before("tc_realify");
-      realify_kernel<<<64, 256, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.S, o.hi, o.lo);
+      realify_kernel<<<64, 256, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.scale, o.ld, o.col0,
+                                               o.transpose, o.S, o.hi, o.lo);
       L.after_launch();
     }
   }
@@ -546,7 +670,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     g.a_planes = 1;
     g.nout = t->nout1;
     g.n_valid = nb;
-    g.kb_chunks = 1;
+    g.kb_chunks = 4;
     g.out64 = t->partial;
     launch_gemm(t, L, "tc_gemm_collision", mCol, t->mW_hi, t->mW_lo, g);
     L.before("tc_collision_reduce");
@@ -554,8 +678,6 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     L.after_launch();
   }
   g1_update(L, nb, hhf, n_in, t->I, st, ny, nys, nacc, nk);
-  // a3: Z = G2 x_4 hHF
-  launch_gemm(t, L, "tc_gemm_commutator", mZin, t->mBh_hi, t->mBh_lo, linear_params(t, N3, 2, EP_DIRECT, t->Z));
   // a4: the source-term chain
   launch_gemm(t, L, "tc_gemm_psi1", t->mW32, t->mBnr_hi, t->mBnr_lo, linear_params(t, N3, 1, EP_EXCH_T, t->buf1));
   {
@@ -567,7 +689,34 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     launch_gemm(t, L, "tc_gemm_psi2", t->mBuf1Gather, t->mBnc_hi, t->mBnc_lo, g);
   }
   launch_gemm(t, L, "tc_gemm_psi3", t->mBuf2Lin, t->mBnb_hi, t->mBnb_lo, linear_params(t, N3, 2, EP_EXCH_T, t->buf1));
-  launch_gemm(t, L, "tc_gemm_psi4", t->mBuf1Lin, t->mBnb_hi, t->mBnb_lo, linear_params(t, N3, 2, EP_DIRECT, t->buf2));
+  // a3: Z = G2 x_4 (hHF - mu); last a4 pass: Q = T2~ x_4 nbar = A^dag (both in the swapped layout)
+  launch_gemm(t, L, "tc_gemm_commutator", mZin, t->mBh_hi, t->mBh_lo, linear_params(t, N3, 2, EP_SWAP34, t->Z));
+  launch_gemm(t, L, "tc_gemm_psi4", t->mBuf1Lin, t->mBnb_hi, t->mBnb_lo, linear_params(t, N3, 2, EP_SWAP34, t->buf2));
+  if (t->se == G1G2_GW) {
+    // a5: Y1 = w x_4 n, Y2 = w x_4 n^T (hcorr_ijkl = Y1_ijkl - Y2_klij), swapped layout
+    launch_gemm(t, L, "tc_gemm_hcorr", t->mW32, t->mBnr_hi, t->mBnr_lo, linear_params(t, N3, 1, EP_SWAP34, t->Y1));
+    launch_gemm(t, L, "tc_gemm_hcorr", t->mW32, t->mBnt_hi, t->mBnt_lo, linear_params(t, N3, 1, EP_SWAP34, t->Y2));
+    L.before("tc_realify_pi");
+    realify_pi_kernel<<<dim3((unsigned)(((nb + 31) / 32) * (t->kpad / 32)), (unsigned)(N * N)), dim3(32, 8), 0,
+                        L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, t->bpi_hi, t->bpi_lo, t->pi_ldb);
+    L.after_launch();
+    // a6: Pi_(ik),(jl) = sum_(pq) G_ipkq hcorr_qjpl, one GEMM with M = N' = K = nb^2
+    GemmParams g{};
+    g.nb = nb;
+    g.a_rows = AR_PI;
+    g.epi = EP_PI;
+    g.n_tiles = t->pi_ntiles;
+    g.pi_mk = (nb + 31) / 32;
+    g.pi_kq = t->kpad / kBlockK;
+    g.pi_mtiles = t->pi_mtiles;
+    g.tiles = t->pi_mtiles * t->pi_ntiles;
+    g.nout = t->pi_nout;
+    g.n_valid = t->pi_nout;
+    g.rows = 2 * N * N;
+    g.out = t->Pi;
+    g.out_plane = t->N4;
+    launch_gemm(t, L, "tc_gemm_pi", from_y ? t->mPi_y32 : t->mPi_ys32, t->mBpi_hi, t->mBpi_lo, g);
+  }
   // a7: orbit assembly + RK4
   AsmParams a{};
   a.nb = nb;
@@ -575,7 +724,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   a.blocks = t->blocks;
   a.Z = t->Z;
   a.Q = t->buf2;
-  a.Pi = nullptr;
+  a.Pi = (t->se == G1G2_GW) ? t->Pi : nullptr;
   a.P = t->N4;
   a.y = Gy;
   a.acc = t->acc;
@@ -585,7 +734,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   a.stage = st.stage;
   a.dt = st.dt;
   L.before("tc_orbit_assemble_rk4");
-  orbit_assemble_kernel<<<t->nblocks, 256, 4 * BEL * sizeof(float2), L.stream>>>(a);
+  orbit_assemble_kernel<<<t->nblocks, ATHREADS, 4 * BEL * sizeof(float2), L.stream>>>(a);
   L.after_launch();
 }
 

@@ -250,6 +250,9 @@ def workload(name):
     elif name == "general-soa-nb96":
         d = general_basis(96, 192, 48, seed=4, pulse=True)
         d.update(dt=0.01, nsteps=1000)
+    elif name == "general-soa-nb64":
+        d = general_basis(64, 128, 32, seed=6, pulse=True)
+        d.update(dt=0.01, nsteps=500)
     elif name == "general-gw-nb64":
         d = general_basis(64, 128, 32, seed=5, selfenergy="GW", pulse=True)
         d.update(dt=0.01, nsteps=500)
@@ -259,7 +262,7 @@ def workload(name):
 
 
 WORKLOADS = ("hubbard-chain-nb8", "general-soa-nb32", "general-gw-nb48", "hubbard-2d-4x4",
-             "general-soa-nb96", "general-gw-nb64")
+             "general-soa-nb96", "general-gw-nb64", "general-soa-nb64")
 
 
 def random_state(nb, rng, g2_scale=1e-2, soa=True):
