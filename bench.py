@@ -43,6 +43,9 @@ FP64_PEAK_TFLOPS = 1.200
 FP64_PEAK_NOTE = "profiles/fp64_dfma_peak.md"
 # nominal dense tensor ratio TF32 / BF16 (1.1 / 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
+# DRAM bytes (read + write) per launch from ncu captures of the current kernels,
+# keyed by (kernel tag, workload); see profiles/.  Missing entries report null.
+TRAFFIC = {}
 
 
 def load_peaks():
@@ -54,19 +57,46 @@ def load_peaks():
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per launch of each kernel family (8 real flops per complex MAC)
+# algorithmic work per launch of each kernel family
 # ---------------------------------------------------------------------------
 
-def algorithmic_flops(nb, se, stage_launches):
-    """Complex MACs of the contraction launches of one RK4 step, by kernel tag.
+def algorithmic_flops(nb, se, stage_launches=None):
+    """Paper-level work of one RK4 step: 8 real flops per complex MAC.
 
-    Per right-hand side: collision integral nb^5, commutator 4 nb^5, source term
-    4 nb^5 (two fused-free mode products each side), GW: quasi-Hamiltonian 2 nb^5
-    and polarisation nb^6.
+    Per right-hand side: collision integral nb^5, commutator 4 nb^5, source
+    term 4 nb^5 (successive contractions), GW: quasi-Hamiltonian 2 nb^5 and
+    polarisation nb^6.  Four right-hand sides per step.
     """
     n5 = nb ** 5
     per_rhs = 9 * n5 + (2 * n5 + nb ** 6 if se == "GW" else 0)
     return 8.0 * per_rhs * 4
+
+
+def kernel_work(tag, nb, se):
+    """(bound, work per launch) of the dominant-kernel candidates.
+
+    Tensor kernels count the real flops of the split-precision products the
+    kernel must issue (three TF32 products per real multiply-add, 2 flops
+    each) on the unpadded problem; the assembly counts its algorithmic HBM
+    bytes (FP32 intermediates, FP64 state, FP32 RK4 accumulator and stage
+    input), averaged over the four RK4 stages.
+    """
+    n = float(nb)
+    split = 3 * 2
+    if tag == "tc_gemm_pi":
+        return "tensor", split * n * n * (2 * n * n) * (2 * n * n)
+    if tag in ("tc_gemm_commutator", "tc_gemm_psi2", "tc_gemm_psi3", "tc_gemm_psi4"):
+        return "tensor", split * n ** 3 * (2 * n) * (2 * n)
+    if tag in ("tc_gemm_psi1", "tc_gemm_hcorr"):
+        return "tensor", split * n ** 3 * (2 * n) * n
+    if tag == "tc_gemm_collision":
+        return "tensor", split * (2 * n) * n * n ** 3
+    if tag == "tc_orbit_assemble_rk4":
+        per_elem = 8 + 8 + 16 + 0.75 * 8 + 18 + (8 if se == "GW" else 0)
+        return "hbm", per_elem * n ** 4
+    if tag in ("fp64_zgemm", "fp64_zgemm_splitk"):
+        return "alu", None
+    return None, None
 
 
 class ClockSampler:
@@ -141,6 +171,7 @@ def run_ours(args, rank, world, dist):
 
     per = {}
     prof_all = {}
+    per_kernel = {}
     launches_total = 0
     clocks = ClockSampler(dev)
     for name in args.workloads:
@@ -170,6 +201,7 @@ def run_ours(args, rank, world, dist):
             a = prof_all.setdefault(k, [0, 0.0, 0.0])
             a[0] += n_l
             a[1] += t_ms
+        per_kernel[name] = rep
         # algorithmic flops of the contraction kernels of this workload
         per[name] = {"nb": d["nb"], "selfenergy": d["selfenergy"], "ms_per_step": ms, "launches": launches,
                      "flops_per_step": algorithmic_flops(d["nb"], d["selfenergy"], None), "dt": dt}
@@ -187,6 +219,29 @@ def run_ours(args, rank, world, dist):
         per[name]["d2h_bytes_per_step"] = 56 + 16 * d["nb"]
         per[name]["energy_drift_rel"] = abs(obs[-1]["e_total"] - obs[0]["e_total"] - obs[-1]["pulse_work"]) / abs(
             obs[0]["e_total"])
+        if args.compare_steps > 0 and args.precision != "fp64":
+            # same steps from the same initial state in the FP64 form: speed-up and error
+            c = args.compare_steps
+            prop.set_state(0.0, d["n0"], None)
+            obs_m, _ = prop.propagate(dt, c, c)
+            _, n_m, g_m = prop.get_state()
+            ref = from_workload(d, precision="fp64")
+            ref.propagate(dt, 1)
+            ref.set_state(0.0, d["n0"], None)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            obs_r, _ = ref.propagate(dt, c, c)
+            e1.record()
+            torch.cuda.synchronize()
+            _, n_r, g_r = ref.get_state()
+            ref.close()
+            del ref
+            per[name]["fp64_ms_per_step"] = e0.elapsed_time(e1) / c
+            per[name]["vs_fp64"] = {
+                "steps": c, "max_abs_dG1": float(np.abs(n_m - n_r).max()),
+                "max_abs_dG2": float(np.abs(g_m - g_r).max()),
+                "rel_dE": abs(obs_m[-1]["e_total"] - obs_r[-1]["e_total"]) / abs(obs_r[-1]["e_total"])}
         prop.close()
         del prop
         torch.cuda.empty_cache()
@@ -202,27 +257,36 @@ def run_ours(args, rank, world, dist):
     e2e_ms = sum(p["e2e_ms_per_step"] for p in per.values())
     e2e_value = world * 1e3 / e2e_ms
 
-    # roofline of the dominant kernel (largest share of device time)
-    dom = max(prof_all.items(), key=lambda kv: kv[1][1])
-    dom_name, (dom_launches, dom_ms, _) = dom
-    total_flops = sum(p["flops_per_step"] * args.steps for p in per.values())
-    contraction_tags = [k for k in prof_all if "zgemm" in k or k.startswith("tc_")]
-    contraction_ms = sum(prof_all[k][1] for k in contraction_tags)
-    if args.precision == "fp64":
-        achieved = total_flops / (contraction_ms * 1e-3) / 1e12
-        peak = FP64_PEAK_TFLOPS
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if peak else None, "traffic": None,
-                "kernel": "fp64_zgemm (+ fp64_zgemm_splitk): all complex contractions",
-                "peak_source": FP64_PEAK_NOTE, "kernel_share": contraction_ms / sum(v[1] for v in prof_all.values())}
-    else:
-        achieved = total_flops / (contraction_ms * 1e-3) / 1e12
+    # roofline of the dominant kernel: the (kernel, workload) pair with the largest device time
+    total_ms = sum(v[1] for v in prof_all.values())
+    cands = [(t_ms, tag, name, n_l) for name, rep in per_kernel.items() for tag, (n_l, t_ms) in rep.items()
+             if kernel_work(tag, per[name]["nb"], per[name]["selfenergy"])[0] is not None]
+    cands.sort(reverse=True)
+    if not cands:
+        cands = [(0.0, "none", next(iter(per)), 1)]
+    t_ms, dom_tag, dom_wl, dom_n = cands[0]
+    d_nb, d_se = per[dom_wl]["nb"], per[dom_wl]["selfenergy"]
+    bound, work = kernel_work(dom_tag, d_nb, d_se)
+    avg_s = t_ms * 1e-3 / dom_n
+    if bound == "tensor":
         peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": ",".join(sorted(contraction_tags)),
-                "peak_source": f"{peak_kind} bf16 sustained x TF32/BF16 nominal ratio"}
-    roof["dominant_kernel"] = dom_name
-    roof["dominant_share"] = dom_ms / sum(v[1] for v in prof_all.values())
+        achieved = work / avg_s / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} bf16 sustained x TF32/BF16 nominal ratio (1.1/2.25), of {peak_kind}"}
+    elif bound == "hbm":
+        peak = peaks["hbm_gbs"]
+        achieved = work / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} copy bandwidth, of {peak_kind}"}
+    else:
+        fl = sum(p["flops_per_step"] * args.steps for p in per.values())
+        zg = sum(v[1] for k, v in prof_all.items() if "zgemm" in k)
+        achieved = fl / (zg * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_NOTE + " (measured DFMA)"}
+        dom_tag = "fp64_zgemm (+ split-K): every complex contraction"
+    roof.update({"traffic": TRAFFIC.get((dom_tag, dom_wl)), "kernel": dom_tag, "workload": dom_wl,
+                 "avg_launch_ms": avg_s * 1e3, "launches": dom_n, "share": t_ms / total_ms})
 
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -238,6 +302,11 @@ def run_ours(args, rank, world, dist):
                 "d2h_bytes_per_step": sum(p["d2h_bytes_per_step"] for p in per.values()),
                 "how": "g1g2_set_state from pinned host + g1g2_propagate(K, observables every step)"},
         "gpu_launches": launches_total,
+        "fp64_form": ({"ms_per_step": sum(p["fp64_ms_per_step"] for p in per.values()),
+                       "steps_per_s": 1e3 / sum(p["fp64_ms_per_step"] for p in per.values()),
+                       "speedup_of_value": value / world / (1e3 / sum(p["fp64_ms_per_step"] for p in per.values())),
+                       "vs_fp64_error": {k: p["vs_fp64"] for k, p in per.items()}}
+                      if all("fp64_ms_per_step" in p for p in per.values()) else None),
         "roofline": roof,
         "clocks": clk,
         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1][1])},
@@ -310,10 +379,12 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp64", "tf32x3"])
     ap.add_argument("--workloads", default=",".join(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare-steps", type=int, default=3,
+                    help="steps run in both forms from the initial state (speed-up and error vs FP64)")
     args = ap.parse_args()
     args.workloads = args.workloads.split(",")
     if args.precision is None:
-        args.precision = os.environ.get("G1G2_BENCH_PRECISION", "fp64")
+        args.precision = os.environ.get("G1G2_BENCH_PRECISION", "tf32x3")
     if args.steps is None:
         args.steps = 3 if args.precision == "fp64" else 20
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup

@@ -250,6 +250,9 @@ def workload(name):
     elif name == "general-soa-nb96":
         d = general_basis(96, 192, 48, seed=4, pulse=True)
         d.update(dt=0.01, nsteps=1000)
+    elif name == "general-soa-nb48":
+        d = general_basis(48, 96, 24, seed=7, pulse=True)
+        d.update(dt=0.01, nsteps=1000)
     elif name == "general-soa-nb64":
         d = general_basis(64, 128, 32, seed=6, pulse=True)
         d.update(dt=0.01, nsteps=500)
