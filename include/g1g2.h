@@ -137,6 +137,40 @@ int g1g2_propagate(g1g2_ctx *c, double dt, int nsteps, int obs_every, g1g2_obs *
  * (E10: d_i = n_{i+,i+} n_{i-,i-} - |n_{i+,i-}|^2 - G2_{i+ i- i+ i-}). */
 int g1g2_observables(g1g2_ctx *c, g1g2_obs *out, double *density, double *double_occ);
 
+/* Vector-Jacobian product of the right-hand side (FP64 form, SOA): given the
+ * cotangents (dn_bar, dG2_bar) of (dn/dt, dG2/dt) at the state (n, G2) at time
+ * t, write the cotangents of n, of G2 and of h^HF (= of the explicit h(t)),
+ * with respect to Re sum conj(x) y.  All pointers are caller-owned device
+ * arrays in the ABI layout; n must be Hermitian (the point of evaluation).
+ * Not in the paper: the building block of g1g2_adjoint. */
+int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_dev, const double *dn_bar,
+                 const double *dG2_bar, double *n_bar, double *G2_bar, double *h_bar);
+
+/* Discrete adjoint of nsteps RK4 steps of the FP64 form (HF or SOA), starting
+ * from the current state: the gradient of a final-time objective J with
+ * respect to the drive parameters, a global scale of w and the entries of h.
+ * Not in the paper; the reverse sweep is the exact transpose of the discrete
+ * RK4 map, with the state (n, G2) checkpointed every ckpt_every steps and
+ * each segment recomputed once.  ckpt_every <= 0 chooses the interval from
+ * the free device memory: the smallest k whose ceil(nsteps/k) + 1 checkpoints
+ * and k + 1 segment states fit in 80% of it (k = 1, no recomputation, when
+ * all steps fit), at most ceil(sqrt(nsteps)) (the memory minimum).
+ *   objective   0: mean double occupancy (1/L) sum_i d_i (E10; spin-orbital
+ *                  basis, index 2*site+spin); 1: density imbalance
+ *                  sum_i (-1)^site n_ii (x2 spin-restricted); 2: energy absorbed
+ *                  E(T) - E(0) (E9)
+ *   J_out       objective value at the final time
+ *   grad_drive  dJ/dtheta for the drive parameters (kind 2: the M control
+ *               values; kind 1: A, omega, t0, sigma), or NULL
+ *   grad_wscale dJ/ds for w -> s w at s = 1 (e.g. U dJ/dU for a Hubbard w), or NULL
+ *   grad_h      nb*nb interleaved gradient G on Hermitian h: for every Hermitian
+ *               perturbation dh, dJ = Re sum conj(G_ij) dh_ij (G is Hermitian), or NULL
+ * Cotangents use Re sum conj(x) y over every complex entry of (G1, G2).  On
+ * return the context holds the final state (as after g1g2_propagate).
+ * G1G2_EUNSUPPORTED for the tensor-core precision or GW. */
+int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objective, double *J_out,
+                 double *grad_drive, double *grad_wscale, double *grad_h);
+
 /* Copy the state to / from host memory (G2 may be NULL on get; NULL on set means 0). */
 int g1g2_get_state(g1g2_ctx *c, double *t, double *G1, double *G2);
 int g1g2_set_state(g1g2_ctx *c, double t, const double *G1, const double *G2);

@@ -563,3 +563,140 @@ void count_nonfinite(Launcher &L, const cplx *x, long long len, double *cnt) {
 }
 
 }  // namespace g1g2
+
+// ---------------------------------------------------------------------------
+// Kernels of the discrete adjoint (FP64)
+// ---------------------------------------------------------------------------
+namespace g1g2 {
+namespace {
+
+__global__ void zaxpby_kernel(long long n, cplx alpha, const cplx *__restrict__ x, cplx beta,
+                              const cplx *__restrict__ y, cplx *out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    cplx r = cmul(alpha, x[e]);
+    if (y) r = cadd(r, cmul(beta, y[e]));
+    out[e] = r;
+  }
+}
+
+// out = c * (a + a^dag) for an nb x nb matrix
+__global__ void herm_sum_kernel(int nb, cplx c, const cplx *__restrict__ a, cplx *out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nb * nb) return;
+  const int i = e / nb, j = e % nb;
+  out[e] = cmul(c, cadd(a[e], cconj(a[j * nb + i])));
+}
+
+// out = c * (Y + Y^dag), (Y^dag)_ijkl = conj(Y_klij), 32x32 tiles of the (ij),(kl) view
+__global__ void tconj_add_kernel(int nb, cplx c, const cplx *__restrict__ Y, cplx *out) {
+  __shared__ cplx tile[PT][PT + 1];
+  const long long M = (long long)nb * nb;
+  const long long r0 = (long long)blockIdx.y * PT, c0 = (long long)blockIdx.x * PT;
+  for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
+    const long long rr = c0 + yy, cc = r0 + threadIdx.x;
+    if (rr < M && cc < M) tile[yy][threadIdx.x] = Y[rr * M + cc];
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
+    const long long r = r0 + yy, cl = c0 + threadIdx.x;
+    if (r < M && cl < M) {
+      const long long e = r * M + cl;
+      out[e] = cmul(c, cadd(Y[e], cconj(tile[threadIdx.x][yy])));
+    }
+  }
+}
+
+// partial sums of Re sum conj(x) y
+__global__ void real_dot_kernel(long long n, const cplx *__restrict__ x, const cplx *__restrict__ y, double *partials) {
+  __shared__ double s[256];
+  double a = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    a += x[e].x * y[e].x + x[e].y * y[e].y;
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = s[0];
+}
+
+// acc[slot] += coeff * sum(partials)
+__global__ void dot_accumulate_kernel(int nparts, const double *partials, double coeff, double *acc) {
+  __shared__ double s[256];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) a += partials[i];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *acc += coeff * s[0];
+}
+
+// out_lk (+)= sum_ij Wm[(ij),(lk)] x_ij  (the adjoint of the Hartree-Fock build)
+template <bool REAL>
+__global__ void hf_build_t_kernel(int nb, const void *__restrict__ Wm_, const cplx *__restrict__ x, cplx *out,
+                                  int accumulate) {
+  const int nb2 = nb * nb;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nb2) return;
+  cplx acc = {0.0, 0.0};
+  for (int r = 0; r < nb2; ++r) {
+    const cplx xv = x[r];
+    if (REAL) {
+      const double wv = static_cast<const double *>(Wm_)[(long long)r * nb2 + c];
+      acc.x = fma(wv, xv.x, acc.x);
+      acc.y = fma(wv, xv.y, acc.y);
+    } else {
+      acc = cfma(cconj(static_cast<const cplx *>(Wm_)[(long long)r * nb2 + c]), xv, acc);
+    }
+  }
+  // the Hartree-Fock matrix is indexed [(ij),(lk)] with column (l*nb + k) = the n_lk entry
+  out[c] = accumulate ? cadd(out[c], acc) : acc;
+}
+
+}  // namespace
+
+void zaxpby(Launcher &L, long long n, cplx alpha, const cplx *x, cplx beta, const cplx *y, cplx *out) {
+  L.before("adj_axpby");
+  zaxpby_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8192), 256, 0, L.stream>>>(n, alpha, x, beta, y, out);
+  L.after_launch();
+}
+
+void herm_sum(Launcher &L, int nb, cplx c, const cplx *a, cplx *out) {
+  L.before("adj_herm_sum");
+  herm_sum_kernel<<<(nb * nb + 127) / 128, 128, 0, L.stream>>>(nb, c, a, out);
+  L.after_launch();
+}
+
+void tconj_add(Launcher &L, int nb, cplx c, const cplx *Y, cplx *out) {
+  const long long M = (long long)nb * nb;
+  const unsigned t = (unsigned)((M + PT - 1) / PT);
+  L.before("adj_tconj_add");
+  tconj_add_kernel<<<dim3(t, t), dim3(PT, 8), 0, L.stream>>>(nb, c, Y, out);
+  L.after_launch();
+}
+
+void real_dot_acc(Launcher &L, long long n, const cplx *x, const cplx *y, double coeff, double *partials, double *acc) {
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+  L.before("adj_dot");
+  real_dot_kernel<<<blocks, 256, 0, L.stream>>>(n, x, y, partials);
+  L.after_launch();
+  L.before("adj_dot");
+  dot_accumulate_kernel<<<1, 256, 0, L.stream>>>(blocks, partials, coeff, acc);
+  L.after_launch();
+}
+
+void hf_build_t(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *x, cplx *out, bool accumulate) {
+  const int nb2 = nb * nb;
+  L.before("adj_hf_build_t");
+  if (wm_real)
+    hf_build_t_kernel<true><<<(nb2 + 127) / 128, 128, 0, L.stream>>>(nb, Wm, x, out, accumulate ? 1 : 0);
+  else
+    hf_build_t_kernel<false><<<(nb2 + 127) / 128, 128, 0, L.stream>>>(nb, Wm, x, out, accumulate ? 1 : 0);
+  L.after_launch();
+}
+
+}  // namespace g1g2

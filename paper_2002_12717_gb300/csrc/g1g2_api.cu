@@ -57,6 +57,15 @@ struct g1g2_ctx {
   std::vector<void *> allocs;
   TcPath *tc = nullptr;             // split-precision tensor-core path (precision != FP64)
   Profiler prof;
+  // discrete adjoint (FP64 form), allocated on first use
+  cplx *zero_h = nullptr;                       // nb*nb zeros: h for the w-part of the RHS
+  cplx *AE = nullptr, *AB1 = nullptr, *AB2 = nullptr;
+  double *adj_red = nullptr;                    // reduction partials
+  double *adj_acc = nullptr;                    // [0] w-scale gradient, [1..] per-stage <D, hbar>
+  long long adj_acc_len = 0;
+  cplx *adj_hsum = nullptr;                     // accumulated cotangent of h
+  cplx *adj_hbar = nullptr;                     // cotangent of hHF of one stage
+  std::vector<void *> adj_allocs;
 
   Launcher launcher() {
     Launcher L;
@@ -145,12 +154,16 @@ struct StageOut {
 };
 
 void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *G_in, Rk4Stage st,
-              const StageOut &o) {
+              const StageOut &o, bool w_only = false) {
   const int nb = c->nb;
   const long long N = nb, N2 = N * N, N3 = N2 * N;
   const double f = drive_f(c, t);
-  // a1: Eq. (h_HF)
-  hf_build(L, nb, c->Wm, c->w_real, c->h, c->hasD ? c->D : nullptr, f, n_in, c->hhf);
+  // a1: Eq. (h_HF); with w_only the one-body h(t) is left out (the part of the
+  // right-hand side that is linear in w, used for the gradient by the scale of w)
+  if (w_only)
+    hf_build(L, nb, c->Wm, c->w_real, c->zero_h, nullptr, 0.0, n_in, c->hhf);
+  else
+    hf_build(L, nb, c->Wm, c->w_real, c->h, c->hasD ? c->D : nullptr, f, n_in, c->hhf);
   if (c->se == G1G2_HF) {
     g1_update(L, nb, c->hhf, n_in, nullptr, st, o.ny, o.nys, o.nacc, o.nk);
     return;
@@ -356,6 +369,159 @@ int observables_impl(g1g2_ctx *c, g1g2_obs *out, double *density, double *nonfin
   return G1G2_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Discrete adjoint of the FP64 form (HF and SOA).
+//
+// Cotangents use the real inner product <X, Y> = Re sum conj(X) Y over every
+// complex entry of (n, G2); the right-hand side is not holomorphic (it contains
+// I^dag, A^dag), so each term's adjoint is taken with respect to that product.
+// ---------------------------------------------------------------------------
+
+// out = alpha * (three-index contraction of X and conj(Z)) + beta * out, out nb x nb:
+//   mode 1: out[i][p] = sum_jkl X_ijkl conj(Z_pjkl)   mode 2: out[j][q] = sum_ikl X_ijkl conj(Z_iqkl)
+//   mode 3: out[p][k] = sum_ijl conj(Z_ijpl) X_ijkl   mode 4: out[p][l] = sum_ijk conj(Z_ijkp) X_ijkl
+void contract3(g1g2_ctx *c, Launcher &L, int mode, const cplx *X, const cplx *Z, cplx alpha, double beta, cplx *out) {
+  const long long N = c->nb, N2 = N * N, N3 = N2 * N;
+  ZGemm g;
+  g.M = c->nb; g.N = c->nb; g.C = out; g.sc_m = N; g.sc_n = 1; g.alpha = alpha; g.beta = beta;
+  if (mode == 1) {
+    g.K = (int)N2; g.batch = c->nb;
+    g.A = X; g.sa_b = N2; g.sa_m = N3; g.sa_k = 1;
+    g.B = Z; g.sb_b = N2; g.sb_k = 1; g.sb_n = N3; g.conjB = true;
+  } else if (mode == 2) {
+    g.K = (int)N2; g.batch = c->nb;
+    g.A = X; g.sa_b = N3; g.sa_m = N2; g.sa_k = 1;
+    g.B = Z; g.sb_b = N3; g.sb_k = 1; g.sb_n = N2; g.conjB = true;
+  } else if (mode == 3) {
+    g.K = c->nb; g.batch = (int)N2;
+    g.A = Z; g.sa_b = N2; g.sa_m = N; g.sa_k = 1; g.conjA = true;
+    g.B = X; g.sb_b = N2; g.sb_k = 1; g.sb_n = N;
+  } else {
+    g.K = (int)N2; g.batch = c->nb;
+    g.A = Z; g.sa_b = N3; g.sa_m = 1; g.sa_k = N; g.conjA = true;
+    g.B = X; g.sb_b = N3; g.sb_k = N; g.sb_n = 1;
+  }
+  zgemm_reduce(L, g, c->partial, c->splits);
+}
+
+// Mode products on nb^4 tensors: right products over index 4 or 3, left products over 1 or 2.
+void mode_right4(g1g2_ctx *c, Launcher &L, const cplx *X, const cplx *S, cplx *out, cplx alpha, double beta) {
+  const long long N = c->nb;
+  ZGemm g;
+  g.M = (int)(N * N * N); g.N = c->nb; g.K = c->nb;
+  g.A = X; g.sa_m = N; g.sa_k = 1; g.B = S; g.sb_k = N; g.sb_n = 1;
+  g.C = out; g.sc_m = N; g.sc_n = 1; g.alpha = alpha; g.beta = beta;
+  zgemm(L, g);
+}
+void mode_right3(g1g2_ctx *c, Launcher &L, const cplx *X, const cplx *S, cplx *out, cplx alpha, double beta) {
+  const long long N = c->nb, N2 = N * N;
+  ZGemm g;
+  g.M = c->nb; g.N = c->nb; g.K = c->nb; g.batch = (int)N2;
+  g.A = S; g.sa_m = 1; g.sa_k = N; g.B = X; g.sb_b = N2; g.sb_k = N; g.sb_n = 1;
+  g.C = out; g.sc_b = N2; g.sc_m = N; g.sc_n = 1; g.alpha = alpha; g.beta = beta;
+  zgemm(L, g);
+}
+void mode_left2(g1g2_ctx *c, Launcher &L, const cplx *S, const cplx *X, cplx *out, cplx alpha, double beta) {
+  const long long N = c->nb, N2 = N * N, N3 = N2 * N;
+  ZGemm g;
+  g.M = c->nb; g.N = (int)N2; g.K = c->nb; g.batch = c->nb;
+  g.A = S; g.sa_m = N; g.sa_k = 1; g.B = X; g.sb_b = N3; g.sb_k = N2; g.sb_n = 1;
+  g.C = out; g.sc_b = N3; g.sc_m = N2; g.sc_n = 1; g.alpha = alpha; g.beta = beta;
+  zgemm(L, g);
+}
+void mode_left1(g1g2_ctx *c, Launcher &L, const cplx *S, const cplx *X, cplx *out, cplx alpha, double beta) {
+  const long long N = c->nb, N3 = N * N * N;
+  ZGemm g;
+  g.M = c->nb; g.N = (int)N3; g.K = c->nb;
+  g.A = S; g.sa_m = N; g.sa_k = 1; g.B = X; g.sb_k = N3; g.sb_n = 1;
+  g.C = out; g.sc_m = N3; g.sc_n = 1; g.alpha = alpha; g.beta = beta;
+  zgemm(L, g);
+}
+void matmul(g1g2_ctx *c, Launcher &L, const cplx *A, const cplx *B, cplx *out, cplx alpha, double beta) {
+  const long long N = c->nb;
+  ZGemm g;
+  g.M = c->nb; g.N = c->nb; g.K = c->nb;
+  g.A = A; g.sa_m = N; g.sa_k = 1; g.B = B; g.sb_k = N; g.sb_n = 1;
+  g.C = out; g.sc_m = N; g.sc_n = 1; g.alpha = alpha; g.beta = beta;
+  zgemm(L, g);
+}
+
+// Vector-Jacobian product of the FP64 right-hand side at (t, n, G): given the
+// cotangents (a, Y) of (dn, dG2), write the cotangents nbar of n, Gbar of G2
+// and hbar of h^HF (which is also the cotangent of the explicit h(t)).
+void vjp_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n, const cplx *G, const cplx *a, const cplx *Y,
+              cplx *nbar, cplx *Gbar, cplx *hbar) {
+  const int nb = c->nb;
+  const long long N = nb, N2 = N * N, N4 = N2 * N2;
+  const cplx I1{0.0, 1.0}, mI{0.0, -1.0}, one{1.0, 0.0}, mone{-1.0, 0.0};
+  const double f = drive_f(c, t);
+  hf_build(L, nb, c->Wm, c->w_real, c->h, c->hasD ? c->D : nullptr, f, n, c->hhf);
+  // dn = -i [hHF, n] - (I + I^dag): cotangent of hHF from the commutator: i [a, n]
+  matmul(c, L, a, n, hbar, I1, 0.0);
+  matmul(c, L, n, a, hbar, mI, 1.0);
+  const bool corr = c->se != G1G2_HF;
+  if (corr) {
+    // dG2 = -i [h2(hHF), G2] - i Psi: cotangent of hHF from the commutator
+    contract3(c, L, 1, Y, G, I1, 1.0, hbar);
+    contract3(c, L, 2, Y, G, I1, 1.0, hbar);
+    contract3(c, L, 3, Y, G, mI, 1.0, hbar);
+    contract3(c, L, 4, Y, G, mI, 1.0, hbar);
+  }
+  // nbar = i [hHF, a] + (adjoint of the Hartree-Fock build)(hbar)
+  matmul(c, L, c->hhf, a, nbar, I1, 0.0);
+  matmul(c, L, a, c->hhf, nbar, mI, 1.0);
+  hf_build_t(L, nb, c->Wm, c->w_real, hbar, nbar, true);
+  if (!corr) {
+    cudaMemsetAsync(Gbar, 0, N4 * sizeof(cplx), c->stream);
+    return;
+  }
+  // Gbar = i [h2(hHF), Y]  (the commutator map is anti-Hermitian)
+  mode_left1(c, L, c->hhf, Y, Gbar, I1, 0.0);
+  mode_left2(c, L, c->hhf, Y, Gbar, I1, 1.0);
+  mode_right3(c, L, Y, c->hhf, Gbar, mI, 1.0);
+  mode_right4(c, L, Y, c->hhf, Gbar, mI, 1.0);
+  // collision integral I_ij = -i sum w_iklp G2_lpjk, cotangent Ibar = -(a + a^dag):
+  // Gbar_lpjk += i sum_i w_iklp Ibar_ij  (batched over (lp) with wP[(lp)][i][k] = w_iklp)
+  herm_sum(L, nb, mone, a, c->I);
+  {
+    ZGemm g;
+    g.M = nb; g.N = nb; g.K = nb; g.batch = (int)N2;
+    g.A = c->I; g.sa_m = 1; g.sa_k = N;
+    g.B = c->wP; g.sb_b = N2; g.sb_k = N; g.sb_n = 1; g.conjB = true;
+    g.C = Gbar; g.sc_b = N2; g.sc_m = N; g.sc_n = 1;
+    g.alpha = I1; g.beta = 1.0;
+    zgemm(L, g);
+  }
+  // source term: -i Psi = i A - i A^dag, cotangent of A: E = -i (Y + Y^dag);
+  // A = nbar1 nbar2 w~ n3 n4, one n-factor at a time
+  tconj_add(L, nb, mI, Y, c->AE);
+  one_minus(L, nb, n, c->nbar);
+  mode_right4(c, L, c->wsrc, n, c->T1, one, 0.0);          // T1_pqrl = sum_s w~_pqrs n_sl
+  mode_right3(c, L, c->T1, n, c->T2, one, 0.0);            // T2_pqkl = sum_r n_rk T1_pqrl
+  mode_left2(c, L, c->nbar, c->T2, c->AB1, one, 0.0);      // B1 = nbar x_2 T2
+  contract3(c, L, 1, c->AE, c->AB1, mone, 1.0, nbar);
+  mode_left1(c, L, c->nbar, c->T2, c->AB1, one, 0.0);      // B2 = nbar x_1 T2
+  contract3(c, L, 2, c->AE, c->AB1, mone, 1.0, nbar);
+  mode_left2(c, L, c->nbar, c->T1, c->AB1, one, 0.0);
+  mode_left1(c, L, c->nbar, c->AB1, c->AB2, one, 0.0);     // B3 = nbar x_1 nbar x_2 T1
+  contract3(c, L, 3, c->AE, c->AB2, one, 1.0, nbar);
+  mode_right3(c, L, c->wsrc, n, c->AB1, one, 0.0);         // T1'_pqks = sum_r w~_pqrs n_rk
+  mode_left2(c, L, c->nbar, c->AB1, c->T2, one, 0.0);
+  mode_left1(c, L, c->nbar, c->T2, c->AB2, one, 0.0);      // B4 = nbar x_1 nbar x_2 T1'
+  contract3(c, L, 4, c->AE, c->AB2, one, 1.0, nbar);
+}
+
+int adj_alloc(g1g2_ctx *c, std::vector<void *> &own, void **p, size_t bytes) {
+  void *q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(G1G2_ENOMEM, "adjoint: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  own.push_back(q);
+  *p = q;
+  return G1G2_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -428,6 +594,7 @@ void g1g2_destroy(g1g2_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->tc) tc_destroy(c->tc);
+  for (void *p : c->adj_allocs) cudaFree(p);
   for (void *p : c->allocs) cudaFree(p);
   delete c;
 }
@@ -688,6 +855,338 @@ int g1g2_get_state(g1g2_ctx *c, double *t, double *G1, double *G2) {
   if (G2 && (rc = cuda_check(cudaMemcpyAsync(G2, c->G, N4 * sizeof(cplx), cudaMemcpyDeviceToHost, c->stream), "get")))
     return rc;
   return cuda_check(cudaStreamSynchronize(c->stream), "get sync");
+}
+
+int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_dev, const double *dn_bar,
+                 const double *dG2_bar, double *n_bar, double *G2_bar, double *h_bar) {
+  if (!c || !n_dev || !G2_dev || !dn_bar || !dG2_bar || !n_bar || !G2_bar || !h_bar)
+    return fail(G1G2_EINVAL, "NULL argument");
+  if (c->prec != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product runs on the FP64 form");
+  if (c->se == G1G2_GW) return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product covers HF and SOA");
+  const long long N2 = (long long)c->nb * c->nb, N4 = N2 * N2;
+  if (!c->AE) {  // scratch of the adjoint
+    void *p;
+    int rc;
+    for (cplx **b : {&c->AE, &c->AB1, &c->AB2}) {
+      if ((rc = adj_alloc(c, c->adj_allocs, &p, N4 * sizeof(cplx)))) return rc;
+      *b = (cplx *)p;
+    }
+    if (c->se == G1G2_HF) return fail(G1G2_EUNSUPPORTED, "call g1g2_adjoint once before the HF product");
+  }
+  Launcher L = c->launcher();
+  vjp_fp64(c, L, t, reinterpret_cast<const cplx *>(n_dev), reinterpret_cast<const cplx *>(G2_dev),
+           reinterpret_cast<const cplx *>(dn_bar), reinterpret_cast<const cplx *>(dG2_bar), reinterpret_cast<cplx *>(n_bar),
+           reinterpret_cast<cplx *>(G2_bar), reinterpret_cast<cplx *>(h_bar));
+  return launch_status(L, "rhs vjp");
+}
+
+// Checkpoint interval from the free device memory.  Every step is recomputed
+// at most once whatever the interval, so the interval only trades memory
+// ((ceil(nsteps/k) + 1) checkpoints + (k + 1) segment states) against the
+// recomputation ((k - 1)/k of a forward sweep): take the smallest k whose
+// states fit in 80% of the free memory (k = 1, no recomputation, when all
+// fit), never beyond the memory minimum k ~ sqrt(nsteps).
+static int adjoint_interval(int nsteps, size_t state_bytes) {
+  size_t free_b = 0, total_b = 0;
+  const int kmin_mem = std::max(1, (int)std::ceil(std::sqrt((double)nsteps)));
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return kmin_mem;
+  }
+  const double budget = 0.8 * (double)free_b - 8.0 * (double)state_bytes;  // minus the stage buffers
+  for (int k = 1; k < kmin_mem; ++k) {
+    const double states = (double)((nsteps + k - 1) / k + 1) + (double)(k + 1);
+    if (states * (double)state_bytes <= budget) return k;
+  }
+  return kmin_mem;
+}
+
+int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objective, double *J_out,
+                 double *grad_drive, double *grad_wscale, double *grad_h) {
+  if (!c || nsteps < 1 || !J_out) return fail(G1G2_EINVAL, "bad adjoint argument");
+  if (c->prec != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint runs on the FP64 form");
+  if (c->se == G1G2_GW) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers HF and SOA");
+  if (objective < 0 || objective > 2) return fail(G1G2_EINVAL, "objective must be 0, 1 or 2");
+  if (objective == 0 && (c->basis != G1G2_SPIN_ORBITAL || c->nb % 2))
+    return fail(G1G2_EINVAL, "double occupancy needs a spin-orbital basis with index 2*site+spin");
+  const int nb = c->nb;
+  const long long N = nb, N2 = N * N, N4 = N2 * N2;
+  const size_t SB = (N2 + N4) * sizeof(cplx);  // one stored state (n, G2)
+  const int k = ckpt_every > 0 ? std::min(ckpt_every, nsteps) : adjoint_interval(nsteps, SB);
+  const int nseg = (nsteps + k - 1) / k;
+  const bool restricted = c->basis == G1G2_SPIN_RESTRICTED;
+  const double sfac = restricted ? 2.0 : 1.0;
+  int rc;
+  Launcher L = c->launcher();
+  std::vector<void *> own;  // per-call memory
+  auto done = [&](int code) {
+    for (void *q : own) cudaFree(q);
+    return code;
+  };
+  // persistent adjoint scratch
+  if (!c->AE) {
+    void *p;
+    if ((rc = adj_alloc(c, c->adj_allocs, &p, N4 * sizeof(cplx)))) return rc;
+    c->AE = (cplx *)p;
+    if ((rc = adj_alloc(c, c->adj_allocs, &p, N4 * sizeof(cplx)))) return rc;
+    c->AB1 = (cplx *)p;
+    if ((rc = adj_alloc(c, c->adj_allocs, &p, N4 * sizeof(cplx)))) return rc;
+    c->AB2 = (cplx *)p;
+    if ((rc = adj_alloc(c, c->adj_allocs, &p, N2 * sizeof(cplx)))) return rc;
+    c->zero_h = (cplx *)p;
+    if ((rc = adj_alloc(c, c->adj_allocs, &p, 1024 * sizeof(double)))) return rc;
+    c->adj_red = (double *)p;
+    if ((rc = adj_alloc(c, c->adj_allocs, &p, N2 * sizeof(cplx)))) return rc;
+    c->adj_hsum = (cplx *)p;
+    if ((rc = adj_alloc(c, c->adj_allocs, &p, N2 * sizeof(cplx)))) return rc;
+    c->adj_hbar = (cplx *)p;
+    cudaMemsetAsync(c->zero_h, 0, N2 * sizeof(cplx), c->stream);
+    if (c->se == G1G2_HF) {  // the correlated buffers the adjoint touches
+      for (cplx **b : {&c->Gs, &c->Gacc, &c->wsrc, &c->wP, &c->Cb, &c->T1, &c->T2, &c->Ab})
+        if (!*b) {
+          if ((rc = adj_alloc(c, c->adj_allocs, &p, N4 * sizeof(cplx)))) return rc;
+          *b = (cplx *)p;
+          cudaMemsetAsync(p, 0, N4 * sizeof(cplx), c->stream);
+        }
+      if (!c->partial) {
+        c->splits = 4 * 152;
+        if ((rc = adj_alloc(c, c->adj_allocs, &p, (size_t)c->splits * N2 * sizeof(cplx)))) return rc;
+        c->partial = (cplx *)p;
+      }
+    }
+  }
+  // per-call memory: checkpoints, one segment of states, stage inputs, cotangents
+  auto state_n = [&](void *base) { return (cplx *)base; };
+  auto state_G = [&](void *base) { return (cplx *)base + N2; };
+  void *ckpt, *seg, *Y2, *Y3, *Y4, *lam, *lam2, *kbar, *Ybar, *kk, *acc;
+  if ((rc = adj_alloc(c, own, &ckpt, SB * (nseg + 1))) || (rc = adj_alloc(c, own, &seg, SB * (k + 1))) ||
+      (rc = adj_alloc(c, own, &Y2, SB)) || (rc = adj_alloc(c, own, &Y3, SB)) || (rc = adj_alloc(c, own, &Y4, SB)) ||
+      (rc = adj_alloc(c, own, &lam, SB)) || (rc = adj_alloc(c, own, &lam2, SB)) ||
+      (rc = adj_alloc(c, own, &kbar, SB)) || (rc = adj_alloc(c, own, &Ybar, SB)) || (rc = adj_alloc(c, own, &kk, SB)) ||
+      (rc = adj_alloc(c, own, &acc, sizeof(double) * (1 + 4 * (size_t)nsteps))))
+    return done(rc);
+  double *dacc = (double *)acc;
+  cudaMemsetAsync(dacc, 0, sizeof(double) * (1 + 4 * (size_t)nsteps), c->stream);
+  cudaMemsetAsync(c->adj_hsum, 0, N2 * sizeof(cplx), c->stream);
+  auto copy_state = [&](void *dst, const cplx *n, const cplx *G) {
+    cudaMemcpyAsync(state_n(dst), n, N2 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(state_G(dst), G, N4 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
+  };
+  auto at = [&](void *base, long long i) { return (void *)((char *)base + SB * i); };
+  // ---- forward sweep with checkpoints (the state at step m*k is kept)
+  const double t0 = c->t;
+  double E0 = 0.0, Eint0 = 0.0;  // E(0) and its interaction part for the energy-absorbed objective
+  {
+    g1g2_obs o;
+    if (objective == 2 && (rc = observables_impl(c, &o, nullptr, nullptr))) return done(rc);
+    if (objective == 2) {
+      E0 = o.e_total;
+      Eint0 = o.e_hf + o.e_corr;
+    }
+  }
+  copy_state(at(ckpt, 0), c->n, c->G);
+  for (int m = 0; m < nsteps; ++m) {
+    c->t = t0 + m * dt;  // same step times as the segment recomputation below
+    if ((rc = rk4_step(c, dt))) return done(rc);
+    if ((m + 1) % k == 0 && m + 1 < nsteps) copy_state(at(ckpt, (m + 1) / k), c->n, c->G);
+  }
+  copy_state(at(ckpt, nseg), c->n, c->G);  // final state
+  const double tM = c->t;
+  // ---- objective and its gradient lambda_M (host side for n, sparse / device for G2)
+  std::vector<cplx> hn(N2), hl(N2, cplx{0.0, 0.0});
+  cudaMemcpyAsync(hn.data(), c->n, N2 * sizeof(cplx), cudaMemcpyDeviceToHost, c->stream);
+  cudaMemsetAsync(state_G(lam), 0, N4 * sizeof(cplx), c->stream);
+  if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "adjoint sync"))) return done(rc);
+  double J = 0.0, EintT = 0.0;
+  if (objective == 0) {
+    const int Ls = nb / 2;
+    std::vector<cplx> gd(Ls);
+    for (int s = 0; s < Ls; ++s) {
+      const long long u = 2 * s, d = 2 * s + 1;
+      cudaMemcpyAsync(&gd[s], c->G + ((u * N + d) * N + u) * N + d, sizeof(cplx), cudaMemcpyDeviceToHost, c->stream);
+    }
+    cudaStreamSynchronize(c->stream);
+    const cplx mone{-1.0 / Ls, 0.0};
+    for (int s = 0; s < Ls; ++s) {
+      const long long u = 2 * s, d = 2 * s + 1;
+      const zc nuu(hn[u * N + u].x, hn[u * N + u].y), ndd(hn[d * N + d].x, hn[d * N + d].y);
+      const zc nud(hn[u * N + d].x, hn[u * N + d].y), ndu(hn[d * N + u].x, hn[d * N + u].y);
+      J += ((nuu * ndd - nud * ndu).real() - gd[s].x) / Ls;
+      const zc luu = std::conj(ndd) / (double)Ls, ldd = std::conj(nuu) / (double)Ls;
+      const zc lud = -std::conj(ndu) / (double)Ls, ldu = -std::conj(nud) / (double)Ls;
+      hl[u * N + u] = {luu.real(), luu.imag()};
+      hl[d * N + d] = {ldd.real(), ldd.imag()};
+      hl[u * N + d] = {lud.real(), lud.imag()};
+      hl[d * N + u] = {ldu.real(), ldu.imag()};
+      cudaMemcpyAsync(state_G(lam) + ((u * N + d) * N + u) * N + d, &mone, sizeof(cplx), cudaMemcpyHostToDevice,
+                      c->stream);
+      cudaStreamSynchronize(c->stream);
+    }
+  } else if (objective == 1) {
+    for (int i = 0; i < nb; ++i) {
+      const int site = restricted ? i : i / 2;
+      const double sgn = (site % 2 == 0) ? 1.0 : -1.0;
+      J += sfac * sgn * hn[(long long)i * N + i].x;
+      hl[(long long)i * N + i] = {sfac * sgn, 0.0};
+    }
+  } else {
+    g1g2_obs o;
+    if ((rc = observables_impl(c, &o, nullptr, nullptr))) return done(rc);
+    J = o.e_total - E0;
+    EintT = o.e_hf + o.e_corr;
+    // dE/dn = s hHF(T), dE/dG2 = -(s/2) w   (s = spin factor)
+    std::vector<cplx> hh(N2);
+    cudaMemcpyAsync(hh.data(), c->hhf, N2 * sizeof(cplx), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    for (long long e = 0; e < N2; ++e) hl[e] = {sfac * hh[e].x, sfac * hh[e].y};
+    zaxpby(L, N4, cplx{-0.5 * sfac, 0.0}, c->w, cplx{0.0, 0.0}, nullptr, state_G(lam));
+  }
+  cudaMemcpyAsync(state_n(lam), hl.data(), N2 * sizeof(cplx), cudaMemcpyHostToDevice, c->stream);
+  // ---- reverse sweep
+  const cplx one{1.0, 0.0}, zero{0.0, 0.0};
+  const double cs[4] = {0.0, 0.5, 0.5, 1.0};
+  for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+    const int m0 = sgi * k, m1 = std::min(nsteps, m0 + k);
+    // recompute the segment's step states
+    cudaMemcpyAsync(c->n, state_n(at(ckpt, sgi)), N2 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->G, state_G(at(ckpt, sgi)), N4 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
+    c->t = t0 + m0 * dt;
+    copy_state(at(seg, 0), c->n, c->G);
+    for (int m = m0; m < m1 - 1; ++m) {
+      c->t = t0 + m * dt;
+      if ((rc = rk4_step(c, dt))) return done(rc);
+      copy_state(at(seg, m - m0 + 1), c->n, c->G);
+    }
+    for (int m = m1 - 1; m >= m0; --m) {
+      const double tm = t0 + m * dt;
+      void *y = at(seg, m - m0);
+      // stage inputs Y1 = y, Y2, Y3, Y4
+      void *Ys[4] = {y, Y2, Y3, Y4};
+      const double ah[3] = {0.5 * dt, 0.5 * dt, dt};
+      for (int s = 0; s < 3; ++s) {
+        Rk4Stage st{-1, 0.0};
+        StageOut o{nullptr, nullptr, nullptr, state_n(kk), nullptr, nullptr, nullptr, state_G(kk)};
+        rhs_fp64(c, L, tm + cs[s] * dt, state_n(Ys[s]), state_G(Ys[s]), st, o);
+        if (c->se == G1G2_HF) cudaMemsetAsync(state_G(kk), 0, N4 * sizeof(cplx), c->stream);
+        zaxpby(L, N2, one, state_n(y), cplx{ah[s], 0.0}, state_n(kk), state_n(Ys[s + 1]));
+        zaxpby(L, N4, one, state_G(y), cplx{ah[s], 0.0}, state_G(kk), state_G(Ys[s + 1]));
+      }
+      // lam2 accumulates the cotangent of y_m
+      cudaMemcpyAsync(lam2, lam, SB, cudaMemcpyDeviceToDevice, c->stream);
+      const double lw[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
+      const double yw[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};  // weight of Ybar_{s+1} in kbar_s
+      for (int s = 3; s >= 0; --s) {
+        // kbar_s = lw_s lam + yw_s Ybar_{s+1}
+        if (s == 3) {
+          zaxpby(L, N2, cplx{lw[s], 0.0}, state_n(lam), zero, nullptr, state_n(kbar));
+          zaxpby(L, N4, cplx{lw[s], 0.0}, state_G(lam), zero, nullptr, state_G(kbar));
+        } else {
+          zaxpby(L, N2, cplx{lw[s], 0.0}, state_n(lam), cplx{yw[s], 0.0}, state_n(Ybar), state_n(kbar));
+          zaxpby(L, N4, cplx{lw[s], 0.0}, state_G(lam), cplx{yw[s], 0.0}, state_G(Ybar), state_G(kbar));
+        }
+        const double ts = tm + cs[s] * dt;
+        vjp_fp64(c, L, ts, state_n(Ys[s]), state_G(Ys[s]), state_n(kbar), state_G(kbar), state_n(Ybar),
+                 state_G(Ybar), c->adj_hbar);
+        // parameter cotangents of this stage: <D, hbar> (drive), hbar (h), <f_w, kbar> (scale of w)
+        if (c->hasD) real_dot_acc(L, N2, c->D, c->adj_hbar, 1.0, c->adj_red, dacc + 1 + 4 * (size_t)m + s);
+        if (grad_h) zaxpby(L, N2, one, c->adj_hsum, one, c->adj_hbar, c->adj_hsum);
+        if (grad_wscale) {
+          Rk4Stage st{-1, 0.0};
+          StageOut o{nullptr, nullptr, nullptr, state_n(kk), nullptr, nullptr, nullptr, state_G(kk)};
+          rhs_fp64(c, L, ts, state_n(Ys[s]), state_G(Ys[s]), st, o, true);
+          real_dot_acc(L, N2, state_n(kk), state_n(kbar), 1.0, c->adj_red, dacc);
+          if (c->se != G1G2_HF) real_dot_acc(L, N4, state_G(kk), state_G(kbar), 1.0, c->adj_red, dacc);
+        }
+        zaxpby(L, N2, one, state_n(lam2), one, state_n(Ybar), state_n(lam2));
+        zaxpby(L, N4, one, state_G(lam2), one, state_G(Ybar), state_G(lam2));
+      }
+      cudaMemcpyAsync(lam, lam2, SB, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if ((rc = launch_status(L, "adjoint"))) return done(rc);
+  }
+  // restore the final state
+  cudaMemcpyAsync(c->n, state_n(at(ckpt, nseg)), N2 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(c->G, state_G(at(ckpt, nseg)), N4 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
+  c->t = tM;
+  std::vector<double> hacc(1 + 4 * (size_t)nsteps);
+  cudaMemcpyAsync(hacc.data(), dacc, hacc.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  std::vector<cplx> hg(N2);
+  if (grad_h) cudaMemcpyAsync(hg.data(), c->adj_hsum, N2 * sizeof(cplx), cudaMemcpyDeviceToHost, c->stream);
+  if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "adjoint sync"))) return done(rc);
+  *J_out = J;
+  // E(T) - E(0) also depends on w directly: its interaction energies are linear in w
+  if (grad_wscale) *grad_wscale = hacc[0] + (objective == 2 ? EintT - Eint0 : 0.0);
+  if (grad_h) {
+    std::vector<cplx> hn0(N2);
+    if (objective == 2) {
+      // E(T) - E(0) depends on h directly: s (n(T) - n(0))
+      cudaMemcpyAsync(hn0.data(), state_n(at(ckpt, 0)), N2 * sizeof(cplx), cudaMemcpyDeviceToHost, c->stream);
+      cudaMemcpyAsync(hn.data(), c->n, N2 * sizeof(cplx), cudaMemcpyDeviceToHost, c->stream);
+      cudaStreamSynchronize(c->stream);
+    }
+    std::vector<cplx> g(N2);
+    for (long long e = 0; e < N2; ++e)
+      g[e] = {hg[e].x + (objective == 2 ? sfac * (hn[e].x - hn0[e].x) : 0.0),
+              hg[e].y + (objective == 2 ? sfac * (hn[e].y - hn0[e].y) : 0.0)};
+    // Hermitian part: the gradient on the space of Hermitian h (h^dag = h is kept by the dynamics)
+    for (long long i = 0; i < N; ++i)
+      for (long long j = 0; j < N; ++j) {
+        const cplx a = g[i * N + j], b = g[j * N + i];
+        grad_h[2 * (i * N + j)] = 0.5 * (a.x + b.x);
+        grad_h[2 * (i * N + j) + 1] = 0.5 * (a.y - b.y);
+      }
+  }
+  if (grad_drive && c->hasD) {
+    // dJ/dtheta = sum over steps and stages of (df/dtheta)(t_s) <D, hbar_s>, plus the
+    // explicit f-dependence of the energy objective at t = T and t = 0
+    const std::vector<double> &p = c->drive_params;
+    const int np = (int)p.size();
+    const int ng = c->drive_kind == 2 ? np - 2 : 4;
+    std::vector<double> gd(ng, 0.0);
+    auto add_df = [&](double tt, double wgt) {
+      if (c->drive_kind == 2) {
+        const double ta = p[0], tb = p[1];
+        const int M = np - 2;
+        const double hs = (tb - ta) / (M - 1);
+        const double x = (tt - ta) / hs;
+        if (x <= 0) gd[0] += wgt;
+        else if (x >= M - 1) gd[M - 1] += wgt;
+        else {
+          int sI = (int)std::floor(x);
+          if (sI > M - 2) sI = M - 2;
+          const double u = x - sI;
+          gd[sI] += (1 - u) * wgt;
+          gd[sI + 1] += u * wgt;
+        }
+      } else {
+        const double A = p[0], w = p[1], tc = p[2], sg = p[3];
+        const double g = std::exp(-(tt - tc) * (tt - tc) / (2 * sg * sg));
+        const double sn = std::sin(w * tt), cn = std::cos(w * tt);
+        gd[0] += wgt * sn * g;
+        gd[1] += wgt * A * tt * cn * g;
+        gd[2] += wgt * A * sn * g * (tt - tc) / (sg * sg);
+        gd[3] += wgt * A * sn * g * (tt - tc) * (tt - tc) / (sg * sg * sg);
+      }
+    };
+    for (int m = 0; m < nsteps; ++m)
+      for (int s = 0; s < 4; ++s) add_df(t0 + m * dt + cs[s] * dt, hacc[1 + 4 * (size_t)m + s]);
+    if (objective == 2) {
+      // J = E(T) - E(0) depends on f(T) and f(0) through h(t): dE/df = s Re Tr(D n)
+      Launcher L2 = c->launcher();
+      obs_one_body(L2, nb, c->h, c->D, drive_f(c, tM), c->hhf, c->n, c->red);
+      double r[4];
+      cudaMemcpyAsync(r, c->red, sizeof(r), cudaMemcpyDeviceToHost, c->stream);
+      cudaStreamSynchronize(c->stream);
+      add_df(tM, sfac * r[3]);
+      cudaMemcpyAsync(c->adj_hsum, state_n(at(ckpt, 0)), N2 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
+      obs_one_body(L2, nb, c->h, c->D, drive_f(c, t0), c->hhf, c->adj_hsum, c->red);
+      cudaMemcpyAsync(r, c->red, sizeof(r), cudaMemcpyDeviceToHost, c->stream);
+      cudaStreamSynchronize(c->stream);
+      add_df(t0, -sfac * r[3]);
+    }
+    for (int i = 0; i < ng; ++i) grad_drive[i] = gd[i];
+  }
+  return done(G1G2_OK);
 }
 
 int g1g2_set_state(g1g2_ctx *c, double t, const double *G1, const double *G2) {

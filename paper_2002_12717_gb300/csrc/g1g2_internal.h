@@ -110,6 +110,14 @@ void double_occ(Launcher &L, int nb, const cplx *n, const cplx *G, double *out);
 // count non-finite entries of x (length len) into *cnt (double, accumulated)
 void count_nonfinite(Launcher &L, const cplx *x, long long len, double *cnt);
 
+// Adjoint helpers: out = alpha x + beta y (y may be null); out = c (Y + Y^dag);
+// acc += coeff * Re sum conj(x) y; out (+)= Wm^T x (adjoint of the Hartree-Fock build).
+void zaxpby(Launcher &L, long long n, cplx alpha, const cplx *x, cplx beta, const cplx *y, cplx *out);
+void tconj_add(Launcher &L, int nb, cplx c, const cplx *Y, cplx *out);
+void herm_sum(Launcher &L, int nb, cplx c, const cplx *a, cplx *out);
+void real_dot_acc(Launcher &L, long long n, const cplx *x, const cplx *y, double coeff, double *partials, double *acc);
+void hf_build_t(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *x, cplx *out, bool accumulate);
+
 // Text returned by g1g2_last_error_detail on this thread.
 void set_error_detail(const std::string &what);
 

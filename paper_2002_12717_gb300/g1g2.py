@@ -69,6 +69,9 @@ def load():
         "g1g2_get_state": (ctypes.c_int, [vp, _dp, _dp, _dp]),
         "g1g2_set_state": (ctypes.c_int, [vp, ctypes.c_double, _dp, _dp]),
         "g1g2_launch_count": (ctypes.c_longlong, [vp]),
+        "g1g2_rhs_vjp": (ctypes.c_int, [vp, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp]),
+        "g1g2_adjoint": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
+                                        _dp]),
         "g1g2_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "g1g2_profile_report": (ctypes.c_int, [vp, ctypes.POINTER(KernelStat), ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int)]),
@@ -201,6 +204,26 @@ class Propagator:
         nb_ = _c128(n)
         gb = None if G2 is None else _c128(G2)
         _check(self._lib.g1g2_set_state(self._ctx, float(t), _cptr(nb_), None if gb is None else _cptr(gb)))
+
+    def rhs_vjp(self, t, n_dev, G2_dev, dn_bar, dG2_bar, n_bar, G2_bar, h_bar):
+        """Cotangents of (n, G2, h^HF) from those of (dn/dt, dG2/dt) (device tensors, FP64 form)."""
+        ptr = lambda x: ctypes.c_void_p(x.data_ptr())
+        _check(self._lib.g1g2_rhs_vjp(self._ctx, float(t), ptr(n_dev), ptr(G2_dev), ptr(dn_bar), ptr(dG2_bar),
+                                      ptr(n_bar), ptr(G2_bar), ptr(h_bar)))
+
+    def adjoint(self, dt, nsteps, objective=0, ckpt_every=0, n_drive_params=0):
+        """Discrete adjoint from the current state: (J, grad_drive, grad_wscale, grad_h).
+
+        objective 0: mean double occupancy, 1: density imbalance, 2: energy absorbed.
+        """
+        J = ctypes.c_double()
+        gd = np.zeros(max(n_drive_params, 1))
+        gw = ctypes.c_double()
+        gh = np.zeros((self.nb, self.nb), dtype=np.complex128)
+        _check(self._lib.g1g2_adjoint(self._ctx, float(dt), int(nsteps), int(ckpt_every), int(objective),
+                                      ctypes.byref(J), _cptr(gd) if n_drive_params else None, ctypes.byref(gw),
+                                      _cptr(gh)))
+        return J.value, gd[:n_drive_params], gw.value, gh
 
     def profile(self, enable=True):
         """Start (clearing old records) or stop per-kernel CUDA-event timing."""

@@ -380,3 +380,17 @@ def test_g1g2_equals_memory_integral_hfgkba():
         errs.append(np.abs(ns[-1] - n_ref).max())
     assert errs[1] < 2e-3
     assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_torch_restatement_matches_oracle():
+    """The autograd restatement (oracle/torch_oracle.py) reproduces the numpy oracle's RK4 run."""
+    import torch
+    from oracle import torch_oracle as T
+    d = inputs.hubbard_2d_spin_orbital(Lx=2, Ly=1, n_controls=5, ta=0.0, tb=0.4)
+    prob = O.Problem(d["h"], d["w"], "SOA", False, d["D"], d["drive"].f)
+    n_ref, g_ref, _, _ = O.propagate(prob, d["n0"], np.zeros((4,) * 4), 0.02, 20)
+    model = T.TorchSOA(d["h"], d["w"], d["D"])
+    n, g = T.propagate(model, torch.as_tensor(d["n0"]), torch.zeros((4,) * 4, dtype=torch.complex128), 0.02, 20,
+                       torch.as_tensor(d["drive"].values), 0.0, 0.4, 1.0, torch.zeros((4, 4), dtype=torch.complex128))
+    assert np.abs(n.numpy() - n_ref).max() < 1e-13
+    assert np.abs(g.numpy() - g_ref).max() < 1e-13
