@@ -58,7 +58,10 @@ typedef enum {
  * build and the observables are FP64 in every mode. */
 typedef enum {
   G1G2_FP64 = 0,   /* every contraction in FP64 on the CUDA cores: the reference form */
-  G1G2_TF32X3 = 1  /* split-precision tensor-core contractions: hi/lo TF32 operands, FP32 accumulation */
+  G1G2_TF32X3 = 1, /* split-precision tensor-core contractions: hi/lo TF32 operands, FP32 accumulation */
+  G1G2_BF16X4 = 2  /* tensor-core contractions on four BF16 slices per operand with one power-of-two
+                      scale per tensor; the leading slice product accumulates exactly in FP32, the
+                      lower-order products (2^-8 and below) in a second accumulator */
 } g1g2_precision;
 
 /* Basis. SPIN_RESTRICTED: the index runs over spatial orbitals, w is an

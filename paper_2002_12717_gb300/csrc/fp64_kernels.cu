@@ -36,7 +36,12 @@ struct ZGemmDev {
   int conjA, conjB;
 };
 
-__global__ void __launch_bounds__(GNT) zgemm_kernel(ZGemmDev g, int reduce, int per_split, cplx *partial) {
+// reduce != 0: split-K form.  The reduction runs over (batch, K); it is cut
+// into batch * kparts units (unit u: batch u / kparts, K range
+// [(u % kparts) * klen, ...)), and split z sums units [z * per_split, ...)
+// into partial[z].
+__global__ void __launch_bounds__(GNT) zgemm_kernel(ZGemmDev g, int reduce, int per_split, cplx *partial, int kparts,
+                                                     int klen) {
   __shared__ cplx As[GBK][GBM + 1];
   __shared__ cplx Bs[GBK][GBN + 1];
   const int tid = threadIdx.x;
@@ -46,7 +51,7 @@ __global__ void __launch_bounds__(GNT) zgemm_kernel(ZGemmDev g, int reduce, int 
   long long b_begin, b_end, b_step;
   if (reduce) {
     b_begin = (long long)blockIdx.z * per_split;
-    b_end = min((long long)g.batch, b_begin + per_split);
+    b_end = min((long long)g.batch * kparts, b_begin + per_split);
     b_step = 1;
   } else {
     b_begin = blockIdx.z;
@@ -60,15 +65,18 @@ __global__ void __launch_bounds__(GNT) zgemm_kernel(ZGemmDev g, int reduce, int 
 #pragma unroll
       for (int j = 0; j < GTN; ++j) acc[i][j] = {0.0, 0.0};
     const long long bl = reduce ? b_end : b0 + 1;
-    for (long long b = b0; b < bl; ++b) {
+    for (long long u = b0; u < bl; ++u) {
+      const long long b = reduce ? u / kparts : u;
+      const int kbeg = reduce ? (int)(u % kparts) * klen : 0;
+      const int kend = reduce ? min(g.K, kbeg + klen) : g.K;
       const cplx *A = g.A + b * g.sa_b;
       const cplx *B = g.B + b * g.sb_b;
-      for (int k0 = 0; k0 < g.K; k0 += GBK) {
+      for (int k0 = kbeg; k0 < kend; k0 += GBK) {
         for (int idx = tid; idx < GBM * GBK; idx += GNT) {
           int m, k;
           if (g.sa_k == 1) { m = idx / GBK; k = idx % GBK; } else { k = idx / GBM; m = idx % GBM; }
           cplx v = {0.0, 0.0};
-          if (m0 + m < g.M && k0 + k < g.K) v = A[(long long)(m0 + m) * g.sa_m + (long long)(k0 + k) * g.sa_k];
+          if (m0 + m < g.M && k0 + k < kend) v = A[(long long)(m0 + m) * g.sa_m + (long long)(k0 + k) * g.sa_k];
           if (g.conjA) v.y = -v.y;
           As[k][m] = v;
         }
@@ -76,7 +84,7 @@ __global__ void __launch_bounds__(GNT) zgemm_kernel(ZGemmDev g, int reduce, int 
           int n, k;
           if (g.sb_n == 1) { k = idx / GBN; n = idx % GBN; } else { n = idx / GBK; k = idx % GBK; }
           cplx v = {0.0, 0.0};
-          if (n0 + n < g.N && k0 + k < g.K) v = B[(long long)(k0 + k) * g.sb_k + (long long)(n0 + n) * g.sb_n];
+          if (n0 + n < g.N && k0 + k < kend) v = B[(long long)(k0 + k) * g.sb_k + (long long)(n0 + n) * g.sb_n];
           if (g.conjB) v.y = -v.y;
           Bs[k][n] = v;
         }
@@ -119,12 +127,20 @@ __global__ void __launch_bounds__(GNT) zgemm_kernel(ZGemmDev g, int reduce, int 
   }
 }
 
-__global__ void zgemm_reduce_kernel(ZGemmDev g, int splits, const cplx *partial) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)g.M * g.N) return;
-  const int m = (int)(idx / g.N), n = (int)(idx % g.N);
+// Block (32, 32): x = one of 32 consecutive outputs, y = a strided subset of the splits.
+__global__ void __launch_bounds__(1024) zgemm_reduce_kernel(ZGemmDev g, int splits, const cplx *partial) {
+  __shared__ cplx part[32][33];
+  const long long mn = (long long)g.M * g.N;
+  const long long idx = (long long)blockIdx.x * 32 + threadIdx.x;
   cplx s = {0.0, 0.0};
-  for (int z = 0; z < splits; ++z) s = cadd(s, partial[(long long)z * g.M * g.N + idx]);
+  if (idx < mn)
+    for (int z = threadIdx.y; z < splits; z += 32) s = cadd(s, partial[(long long)z * mn + idx]);
+  part[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y != 0 || idx >= mn) return;
+  s = {0.0, 0.0};
+  for (int y = 0; y < 32; ++y) s = cadd(s, part[y][threadIdx.x]);
+  const int m = (int)(idx / g.N), n = (int)(idx % g.N);
   cplx *c = g.C + (long long)m * g.sc_m + (long long)n * g.sc_n;
   cplx r = cmul(g.alpha, s);
   if (g.beta != 0.0) r = cadd(r, cscale(*c, g.beta));
@@ -457,22 +473,27 @@ void zgemm(Launcher &L, const ZGemm &g) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, std::min(g.batch, 65535));
   L.before("fp64_zgemm");
-  zgemm_kernel<<<grid, GNT, 0, L.stream>>>(to_dev(g), 0, 1, nullptr);
+  zgemm_kernel<<<grid, GNT, 0, L.stream>>>(to_dev(g), 0, 1, nullptr, 1, g.K);
   L.after_launch();
 }
 
 void zgemm_reduce(Launcher &L, const ZGemm &g, cplx *partial, int splits) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
-  splits = std::max(1, std::min(splits, g.batch));
-  const int per = (g.batch + splits - 1) / splits;
-  splits = (g.batch + per - 1) / per;
+  // cut K as well when the batch alone gives fewer units than splits
+  const int kblocks = (g.K + GBK - 1) / GBK;
+  const int kparts = std::max(1, std::min(kblocks, (splits + g.batch - 1) / g.batch));
+  const int klen = ((kblocks + kparts - 1) / kparts) * GBK;
+  const long long units = (long long)g.batch * kparts;
+  splits = (int)std::max(1LL, std::min((long long)splits, units));
+  const int per = (int)((units + splits - 1) / splits);
+  splits = (int)((units + per - 1) / per);
   dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, splits);
   L.before("fp64_zgemm_splitk");
-  zgemm_kernel<<<grid, GNT, 0, L.stream>>>(to_dev(g), 1, per, partial);
+  zgemm_kernel<<<grid, GNT, 0, L.stream>>>(to_dev(g), 1, per, partial, kparts, klen);
   L.after_launch();
   const long long mn = (long long)g.M * g.N;
   L.before("fp64_splitk_reduce");
-  zgemm_reduce_kernel<<<(unsigned)((mn + 255) / 256), 256, 0, L.stream>>>(to_dev(g), splits, partial);
+  zgemm_reduce_kernel<<<(unsigned)((mn + 31) / 32), dim3(32, 32), 0, L.stream>>>(to_dev(g), splits, partial);
   L.after_launch();
 }
 

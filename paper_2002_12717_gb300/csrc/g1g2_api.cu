@@ -609,7 +609,8 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   if (nb < 1 || nb > 128) return fail(G1G2_EINVAL, "nb must be in [1, 128]");
   if (!h || !w || !G1_0) return fail(G1G2_EINVAL, "h, w and G1_0 must be non-NULL");
   if (se < G1G2_HF || se > G1G2_GW) return fail(G1G2_EINVAL, "bad selfenergy");
-  if (opt.precision != G1G2_FP64 && opt.precision != G1G2_TF32X3) return fail(G1G2_EINVAL, "bad precision");
+  if (opt.precision != G1G2_FP64 && opt.precision != G1G2_TF32X3 && opt.precision != G1G2_BF16X4)
+    return fail(G1G2_EINVAL, "bad precision");
   if (opt.basis != G1G2_SPIN_ORBITAL && opt.basis != G1G2_SPIN_RESTRICTED) return fail(G1G2_EINVAL, "bad basis");
   if (opt.basis == G1G2_SPIN_RESTRICTED && se == G1G2_GW)
     return fail(G1G2_EINVAL, "GW couples same-spin components and has no spin-restricted form");
@@ -748,7 +749,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   if (correlated && c->prec != G1G2_FP64) {
     if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "init sync"))) return bail(rc);
     g_detail.clear();
-    rc = tc_create(&c->tc, nb, se, restricted, hw.data(), hsrc.data(), c->stream);
+    rc = tc_create(&c->tc, nb, se, restricted, c->prec == G1G2_BF16X4, hw.data(), hsrc.data(), c->stream);
     if (rc) return bail(rc);
     Launcher L = c->launcher();
     tc_load_state(c->tc, L, c->G);

@@ -12,6 +12,16 @@
 // is double-buffered (2 x 256 TMEM columns) so the epilogue of one tile
 // overlaps the main loop of the next.
 //
+// Sliced form (kSliced): the converters cut each A element, scaled by one
+// power of two per tensor (from its largest magnitude), into four
+// integer-valued BF16 slices (8 bits each, Ozaki-style), and B arrives as four
+// such slices.  The leading product A_0 B_0 is a sum of integers below 2^24
+// times one common scale, so its FP32 accumulation in TMEM is exact whatever
+// rounding the tensor core applies; the nine lower-order products (2^-8 and
+// smaller) go to a second accumulator.  This removes the systematic
+// round-toward-zero drift of long FP32 tensor-core accumulations, at 20 BF16
+// MMAs per 32-element K block instead of 12 TF32 ones.
+//
 // Warp roles (256 threads): warp 0 TMA producer, warp 1 TMEM owner and MMA
 // issuer, warps 2-3 converters, warps 4-7 epilogue (TMEM lanes 0..127).
 #pragma once
@@ -25,6 +35,15 @@ constexpr int kTileM = 128;
 constexpr int kBlockK = 32;                        // floats per K block (128 B)
 constexpr uint32_t kABytes = kTileM * kBlockK * 4; // 16 KB
 constexpr int kAccCols = 256;                      // TMEM columns per accumulator buffer
+constexpr int kSlices = 4;                         // BF16 slices per operand (sliced form)
+constexpr uint32_t kASliceBytes = kTileM * kBlockK * 2;  // 8 KB: one slice of an A tile, 64-byte rows
+constexpr uint32_t kSlicedBOff = kABytes + kSlices * kASliceBytes;  // 48 KB: B slices within a stage
+
+// shared memory of one pipeline stage
+__host__ __device__ constexpr uint32_t stage_bytes_for(bool sliced, int nout) {
+  return sliced ? kSlicedBOff + (uint32_t)kSlices * (uint32_t)nout * kBlockK * 2
+                : 2 * kABytes + 2 * (uint32_t)nout * kBlockK * 4;
+}
 
 enum ARows : int {
   AR_LINEAR = 0,   // A viewed as [plane][row][k]; tile = 128 consecutive rows
@@ -69,6 +88,12 @@ struct GemmParams {
   int pi_mtiles;      // AR_PI: row tiles; tile = n_tile * pi_mtiles + m_tile (column-tile outer,
                       //        so concurrent CTAs share the B column tile in L2)
   int *err;
+  const int *a_amax;  // sliced form: FP32 bit pattern of max |A| (the A slice scale)
+  int slice_lead;     // sliced form: leading-slice width L (slice_lead_for(K)); 0 means 7
+  int acc3;           // sliced form: order-1 products in their own exact accumulator (nout <= 128,
+                      // L = slice_lead_order1(K)); for long K, where the lower-order accumulator
+                      // would collect a visible truncation bias
+  int *out_amax;      // sliced form, optional: atomic max of |stored outputs| (FP32 bits)
 };
 
 __device__ __forceinline__ int tile_kblocks(const GemmParams &p, int tile) {
@@ -82,14 +107,24 @@ __device__ __forceinline__ int tile_kblocks(const GemmParams &p, int tile) {
   return p.kb_per_plane * p.a_planes * (p.kb_first ? 2 : 1);
 }
 
+// tmBhi/tmBlo: TF32 hi and lo parts of B; in the sliced form tmBhi holds the
+// four BF16 slices of B as [slice][row][k] (tmBlo unused).
+template <bool kSliced>
 __global__ void __launch_bounds__(256, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
                    const GemmParams p, const int stages) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t b_bytes = (uint32_t)p.nout * kBlockK * 4;
-  const uint32_t stage_bytes = 2 * kABytes + 2 * b_bytes;
+  const uint32_t b_bytes = kSliced ? (uint32_t)p.nout * kBlockK * 2 : (uint32_t)p.nout * kBlockK * 4;
+  const uint32_t stage_bytes = stage_bytes_for(kSliced, p.nout);
+  // accumulator buffers: TF32 form two (double-buffered); sliced form a pair
+  // (exact leading product, lower-order products) per buffer, two buffers when they fit
+  // acc3: three accumulators D0 (order 0), D1 (order 1), D2 (orders 2-3) at columns 0, 128, 256
+  const bool acc3 = kSliced && p.acc3;
+  const int nbuf = (!kSliced || (!acc3 && p.nout <= 128)) ? 2 : 1;
+  const uint32_t dlo_off = (nbuf == 2) ? 128u : 256u;
+  const uint32_t d1_off = acc3 ? 128u : dlo_off, d2_off = acc3 ? 256u : dlo_off;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stage_bytes);
   uint64_t *full = bars;
   uint64_t *conv = bars + stages;
@@ -131,7 +166,7 @@ __global__ void __launch_bounds__(256, 1)
         for (int kb = 0; kb < nkb; ++kb) {
           if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
           uint8_t *st = smem + (size_t)s * stage_bytes;
-          mbar_arrive_expect_tx(&full[s], kABytes + 2 * b_bytes);
+          mbar_arrive_expect_tx(&full[s], kABytes + (kSliced ? kSlices : 2) * b_bytes);
           int bk;  // K coordinate (floats) of this block in B
           if (p.a_rows == AR_LINEAR) {
             const bool second = p.kb_first && kb >= p.kb_first;
@@ -158,8 +193,12 @@ __global__ void __launch_bounds__(256, 1)
             bk = kglob;
           }
           const int brow = (p.a_rows == AR_PI) ? (tile / p.pi_mtiles) * p.nout : 0;
-          tma_load_3d(st + 2 * kABytes, &tmBhi, &full[s], bk, brow, 0);
-          tma_load_3d(st + 2 * kABytes + b_bytes, &tmBlo, &full[s], bk, brow, 0);
+          if (kSliced) {
+            tma_load_3d(st + kSlicedBOff, &tmBhi, &full[s], bk, brow, 0);  // all four slices
+          } else {
+            tma_load_3d(st + 2 * kABytes, &tmBhi, &full[s], bk, brow, 0);
+            tma_load_3d(st + 2 * kABytes + b_bytes, &tmBlo, &full[s], bk, brow, 0);
+          }
           if (++s == stages) { s = 0; ph ^= 1u; }
         }
       }
@@ -167,7 +206,7 @@ __global__ void __launch_bounds__(256, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = idesc_tf32(kTileM, p.nout);
+      const uint32_t idesc = kSliced ? idesc_bf16(kTileM, p.nout) : idesc_tf32(kTileM, p.nout);
       int s = 0, acc = 0;
       uint32_t ph = 0, acc_ph = 0;
       bool ok = true;
@@ -189,26 +228,51 @@ __global__ void __launch_bounds__(256, 1)
           if (!mbar_wait(&conv[s], ph, p.err)) { ok = false; break; }
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
-          const uint32_t sal = sa + kABytes, sbh = sa + 2 * kABytes, sbl = sbh + b_bytes;
+          if (kSliced) {
+            // slice s of A at sa + kABytes + s * kASliceBytes, of B at sa + kSlicedBOff + s * b_bytes
+            const uint32_t as0 = sa + kABytes, bs0 = sa + kSlicedBOff;
 #pragma unroll
-          for (int k = 0; k < kBlockK / 8; ++k) {
-            const uint64_t ah = smem_desc_sw128(sa + 32 * k), al = smem_desc_sw128(sal + 32 * k);
-            const uint64_t bh = smem_desc_sw128(sbh + 32 * k), bl = smem_desc_sw128(sbl + 32 * k);
-            mma_tf32(d_tmem, ah, bh, idesc, (first | (uint32_t)k) ? 1u : 0u);
-            mma_tf32(d_tmem, al, bh, idesc, 1u);
-            mma_tf32(d_tmem, ah, bl, idesc, 1u);
+            for (int k = 0; k < kBlockK / 16; ++k) {
+              uint64_t ad[kSlices], bd[kSlices];
+#pragma unroll
+              for (int q = 0; q < kSlices; ++q) {
+                ad[q] = smem_desc_sw64(as0 + q * kASliceBytes + 32 * k);
+                bd[q] = smem_desc_sw64(bs0 + q * b_bytes + 32 * k);
+              }
+              const uint32_t acc_in = (first | (uint32_t)k) ? 1u : 0u;
+              mma_bf16(d_tmem, ad[0], bd[0], idesc, acc_in);               // exact: integers < 2^24
+              mma_bf16(d_tmem + d1_off, ad[0], bd[1], idesc, acc_in);      // order 1 ...
+              mma_bf16(d_tmem + d1_off, ad[1], bd[0], idesc, 1u);
+              mma_bf16(d_tmem + d2_off, ad[0], bd[2], idesc, acc3 ? acc_in : 1u);  // order 2
+              mma_bf16(d_tmem + d2_off, ad[1], bd[1], idesc, 1u);
+              mma_bf16(d_tmem + d2_off, ad[2], bd[0], idesc, 1u);
+              mma_bf16(d_tmem + d2_off, ad[0], bd[3], idesc, 1u);          // order 3
+              mma_bf16(d_tmem + d2_off, ad[1], bd[2], idesc, 1u);
+              mma_bf16(d_tmem + d2_off, ad[2], bd[1], idesc, 1u);
+              mma_bf16(d_tmem + d2_off, ad[3], bd[0], idesc, 1u);
+            }
+          } else {
+            const uint32_t sal = sa + kABytes, sbh = sa + 2 * kABytes, sbl = sbh + b_bytes;
+#pragma unroll
+            for (int k = 0; k < kBlockK / 8; ++k) {
+              const uint64_t ah = smem_desc_sw128(sa + 32 * k), al = smem_desc_sw128(sal + 32 * k);
+              const uint64_t bh = smem_desc_sw128(sbh + 32 * k), bl = smem_desc_sw128(sbl + 32 * k);
+              mma_tf32(d_tmem, ah, bh, idesc, (first | (uint32_t)k) ? 1u : 0u);
+              mma_tf32(d_tmem, al, bh, idesc, 1u);
+              mma_tf32(d_tmem, ah, bl, idesc, 1u);
+            }
           }
           mma_commit(&empty[s]);
           if (++s == stages) { s = 0; ph ^= 1u; }
           if (chunk_end) {
             mma_commit(&tfull[acc]);
-            if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
+            if (++acc == nbuf) { acc = 0; acc_ph ^= 1u; }
           }
         }
         if (!ok) break;
         if (!p.kb_chunks) {
           mma_commit(&tfull[acc]);
-          if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
+          if (++acc == nbuf) { acc = 0; acc_ph ^= 1u; }
         }
       }
       // every MMA issued by this thread has completed before TMEM is released
@@ -221,22 +285,60 @@ __global__ void __launch_bounds__(256, 1)
     int s = 0;
     uint32_t ph = 0;
     bool ok = true;
+    // sliced form: xs = x 2^-E, slice q scaled back by 2^(E-7-8q)
+    float inv = 1.f, sc[kSlices] = {0.f, 0.f, 0.f, 0.f}, mul[kSlices] = {0.f, 0.f, 0.f, 0.f},
+          imul[kSlices] = {0.f, 0.f, 0.f, 0.f};
+    if (kSliced) {
+      const int E = slice_exponent(p.a_amax ? *p.a_amax : 0);
+      const int Ld = p.slice_lead ? p.slice_lead : 7;
+      inv = ldexpf(1.f, -E);
+#pragma unroll
+      for (int q = 0; q < kSlices; ++q) {
+        sc[q] = ldexpf(1.f, E - Ld - 8 * q);
+        mul[q] = ldexpf(1.f, Ld + 8 * q);
+        imul[q] = ldexpf(1.f, -(Ld + 8 * q));
+      }
+    }
     for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
       const int nkb = tile_kblocks(p, tile);
       for (int kb = 0; kb < nkb; ++kb) {
         if (!mbar_wait(&full[s], ph, p.err)) { ok = false; break; }
         float4 *a = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes);
-        float4 *lo = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes + kABytes);
+        if (kSliced) {
+          uint8_t *sl = smem + (size_t)s * stage_bytes + kABytes;
+#pragma unroll 2
+          for (int i = ct; i < (int)(kABytes / 16); i += 64) {
+            // 16-byte chunk i of the 128-byte-swizzled FP32 tile: row r, logical floats k0..k0+3
+            const int r = i >> 3, k0 = ((i & 7) ^ (r & 7)) << 2;
+            const float4 x = a[i];
+            float q0[kSlices], q1[kSlices], q2[kSlices], q3[kSlices];
+            slice4(x.x * inv, q0, mul, imul);
+            slice4(x.y * inv, q1, mul, imul);
+            slice4(x.z * inv, q2, mul, imul);
+            slice4(x.w * inv, q3, mul, imul);
+            // the same four elements in the 64-byte-swizzled BF16 slice tile
+            const uint32_t off = (uint32_t)r * 64u + ((uint32_t)((k0 >> 3) ^ ((r >> 1) & 3)) << 4) + (uint32_t)(k0 & 7) * 2u;
+#pragma unroll
+            for (int q = 0; q < kSlices; ++q) {
+              uint2 v;
+              v.x = pack_bf16(q0[q] * sc[q], q1[q] * sc[q]);
+              v.y = pack_bf16(q2[q] * sc[q], q3[q] * sc[q]);
+              *reinterpret_cast<uint2 *>(sl + q * kASliceBytes + off) = v;
+            }
+          }
+        } else {
+          float4 *lo = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes + kABytes);
 #pragma unroll 4
-        for (int i = ct; i < (int)(kABytes / 16); i += 64) {
-          const float4 x = a[i];
-          float4 h, l;
-          h.x = to_tf32(x.x); l.x = to_tf32(x.x - h.x);
-          h.y = to_tf32(x.y); l.y = to_tf32(x.y - h.y);
-          h.z = to_tf32(x.z); l.z = to_tf32(x.z - h.z);
-          h.w = to_tf32(x.w); l.w = to_tf32(x.w - h.w);
-          a[i] = h;
-          lo[i] = l;
+          for (int i = ct; i < (int)(kABytes / 16); i += 64) {
+            const float4 x = a[i];
+            float4 h, l;
+            h.x = to_tf32(x.x); l.x = to_tf32(x.x - h.x);
+            h.y = to_tf32(x.y); l.y = to_tf32(x.y - h.y);
+            h.z = to_tf32(x.z); l.z = to_tf32(x.z - h.z);
+            h.w = to_tf32(x.w); l.w = to_tf32(x.w - h.w);
+            a[i] = h;
+            lo[i] = l;
+          }
         }
         fence_proxy_async_smem();
         mbar_arrive(&conv[s]);
@@ -270,6 +372,18 @@ __global__ void __launch_bounds__(256, 1)
           for (int c0 = 0; c0 < p.nout; c0 += 32) {
             float v[32];
             tmem_ld32(tbase + (uint32_t)c0, v);
+            if (kSliced) {
+              float vl[32];
+              tmem_ld32(tbase + d1_off + (uint32_t)c0, vl);
+              if (acc3) {
+                float v2[32];
+                tmem_ld32(tbase + d2_off + (uint32_t)c0, v2);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) vl[j] += v2[j];
+              }
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v[j] += vl[j];
+            }
             if (r < N) {
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
@@ -287,7 +401,7 @@ __global__ void __launch_bounds__(256, 1)
           }
           tc_fence_before();
           mbar_arrive(&tempty[acc]);
-          if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
+          if (++acc == nbuf) { acc = 0; acc_ph ^= 1u; }
         }
         if (!ok) break;
         if (r < N)
@@ -296,9 +410,11 @@ __global__ void __launch_bounds__(256, 1)
             p.out64[(((long long)split * 2 + u) * NN + r) * nv + col] = (double)a.x + (double)a.y;
           }
       }
-    } else
+    } else {
+    float mx = 0.f;  // largest |stored value| of this thread (sliced form, out_amax)
     for (int tile = blockIdx.x; tile < p.tiles; tile += gridDim.x) {
-      if (!mbar_wait(&tfull[acc], acc_ph, p.err)) break;
+      // warp-uniform: the TMEM loads below are .sync.aligned
+      if (!__all_sync(0xffffffffu, mbar_wait(&tfull[acc], acc_ph, p.err))) break;
       tc_fence_after();
       // the row this thread owns
       bool valid = false;
@@ -332,6 +448,18 @@ __global__ void __launch_bounds__(256, 1)
       for (int c0 = 0; c0 < p.nout; c0 += 32) {
         float v[32];
         tmem_ld32(tbase + (uint32_t)c0, v);
+        if (kSliced) {
+          float vl[32];
+          tmem_ld32(tbase + d1_off + (uint32_t)c0, vl);
+          if (acc3) {
+            float v2[32];
+            tmem_ld32(tbase + d2_off + (uint32_t)c0, v2);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) vl[j] += v2[j];
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += vl[j];
+        }
         if (!valid) continue;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -362,11 +490,18 @@ __global__ void __launch_bounds__(256, 1)
             if (vv) x = -x;
           }
           p.out[vv * p.out_plane + idx] = x;
+          if (kSliced) mx = fmaxf(mx, fabsf(x));
         }
       }
       tc_fence_before();
       mbar_arrive(&tempty[acc]);
-      if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
+      if (++acc == nbuf) { acc = 0; acc_ph ^= 1u; }
+    }
+    if (kSliced && p.out_amax) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) atomicMax(p.out_amax, __float_as_int(mx));
+    }
     }
   }
   __syncthreads();

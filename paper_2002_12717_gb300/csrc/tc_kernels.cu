@@ -21,12 +21,23 @@
 //   assembly: P = U - (Q + exch Q)/2 with Q = A^dag and dG2 = -i (P^dag - P), read as
 //     the orbit {X, exch X, trans X, exch trans X} of 8^4 blocks so every
 //     input block is read once; the RK4 stage update is fused.
+//
+// Two operand forms: TF32 hi/lo (three TF32 products) and four BF16 slices
+// with an exact leading product (tc_gemm.cuh).  The sliced form needs the
+// largest magnitude of every A tensor before it is read; each producer (the
+// assembly, the FP32 copy of the state, the source-term passes) folds it into
+// a slot of amax with an atomic maximum.  The polarisation GEMM accumulates
+// K = 2 nb^2 products in TMEM; there the order-1 products get an exact
+// accumulator of their own and the leading slice is narrowed
+// (slice_lead_order1) so that both exact sums stay below 2^24.
 #include "tc_path.h"
 #include "tc_gemm.cuh"
 
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -87,13 +98,91 @@ __global__ void split_real_kernel(long long n, const cplx *__restrict__ w, float
   }
 }
 
-// interleaved FP64 -> planar FP32 (re plane, im plane)
-__global__ void to_planar_f32_kernel(long long n, const cplx *__restrict__ x, float *out) {
+// block-wide maximum of v folded into *slot (FP32 bit patterns of non-negative values order as ints)
+__device__ __forceinline__ void block_amax(float v, int *slot) {
+  __shared__ int smx;
+  if (threadIdx.x == 0) smx = 0;
+  __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&smx, __float_as_int(v));
+  __syncthreads();
+  if (threadIdx.x == 0) atomicMax(slot, smx);
+}
+
+// interleaved FP64 -> planar FP32 (re plane, im plane); amax (optional): max |out|
+__global__ void to_planar_f32_kernel(long long n, const cplx *__restrict__ x, float *out, int *amax) {
+  float mx = 0.f;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const cplx v = x[e];
-    out[e] = (float)v.x;
-    out[n + e] = (float)v.y;
+    const float re = (float)v.x, im = (float)v.y;
+    out[e] = re;
+    out[n + e] = im;
+    mx = fmaxf(mx, fmaxf(fabsf(re), fabsf(im)));
   }
+  if (amax) block_amax(mx, amax);
+}
+
+// value of the real B operand of realify_kernel at (row, col) (no scale)
+__device__ __forceinline__ double realified(int nb, int kpad, int complex_a, int transpose, double mu,
+                                            const cplx *__restrict__ S, int row, int col) {
+  if (row >= 2 * nb) return 0.0;
+  const int v = row / nb, l = row % nb;
+  const int u = complex_a ? col / kpad : 0;
+  const int pp = complex_a ? col % kpad : col;
+  if (pp >= nb) return 0.0;
+  cplx s = transpose ? S[l * nb + pp] : S[pp * nb + l];
+  if (pp == l) s.x -= mu;
+  if (!complex_a || u == 0) return v ? s.y : s.x;
+  return v ? s.x : -s.y;
+}
+
+// Four BF16 slices of x (|x| < 2^E): slice q = q_q 2^(E-L-8q), integer |q_0| <= 2^L, |q_q| <= 128.
+__device__ __forceinline__ void slice4_f64(double x, int E, int L, __nv_bfloat16 *out, long long stride) {
+  double r = ldexp(x, -E);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double sh = ldexp(1.0, L + 8 * q);
+    const double qq = rint(r * sh);
+    r -= qq / sh;
+    out[q * stride] = __float2bfloat16_rn((float)ldexp(qq, E - L - 8 * q));
+  }
+}
+
+// Sliced form of realify_kernel (one CTA): the same real matrix, one power-of-two
+// scale from its largest magnitude, written as slices [q][row][ld].
+__global__ void __launch_bounds__(1024) slice_b_kernel(int nb, int nout, int kpad, int complex_a, int shift, int ld,
+                                                       int transpose, const cplx *__restrict__ S,
+                                                       __nv_bfloat16 *out, long long slice_stride) {
+  __shared__ double red[32];
+  const int kt = complex_a ? 2 * kpad : kpad;
+  const int total = nout * kt;
+  double mu = 0.0;
+  if (shift)
+    for (int i = 0; i < nb; ++i) mu += S[i * nb + i].x;
+  mu /= nb;
+  double mx = 0.0;
+  for (int e = threadIdx.x; e < total; e += blockDim.x)
+    mx = fmax(mx, fabs(realified(nb, kpad, complex_a, transpose, mu, S, e / kt, e % kt)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+  int E = 0;
+  if (mx > 0.0) frexp(mx, &E);  // mx < 2^E
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int row = e / kt, col = e % kt;
+    slice4_f64(realified(nb, kpad, complex_a, transpose, mu, S, row, col), E, 7, out + (long long)row * ld + col,
+               slice_stride);
+  }
+}
+
+// real part of w -> four BF16 slices [q][i][c] with the common exponent E
+__global__ void slice_w_kernel(long long n, const cplx *__restrict__ w, int E, __nv_bfloat16 *out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    slice4_f64(w[e].x, E, 7, out + e, n);
 }
 
 // I_ij = -D1[j][i] - i D0[j][i], summed over the K splits in FP64.
@@ -153,6 +242,53 @@ __global__ void realify_pi_kernel(int nb, int kpad, const float *__restrict__ Y1
   }
 }
 
+// Sliced form of realify_pi_kernel: the same B values, as four BF16 slices
+// [q][row][ldb] with leading width L and the exponent of max|Y1| + max|Y2|
+// (a bound on max|hcorr|; amax holds the FP32 bit patterns of both maxima).
+__global__ void realify_pi_sliced_kernel(int nb, int kpad, const float *__restrict__ Y1s,
+                                         const float *__restrict__ Y2s, long long P, const int *amax, int L,
+                                         __nv_bfloat16 *out, long long ldb, long long slice_stride) {
+  __shared__ float2 t1[32][33];
+  const long long N = nb;
+  const long long jl = blockIdx.y;
+  const long long j = jl / N, l = jl % N;
+  const int ntq = kpad / 32;
+  const int p0 = (blockIdx.x / ntq) * 32, q0 = (blockIdx.x % ntq) * 32;
+  const int tx = threadIdx.x, ty0 = threadIdx.y;
+  int E = 0;
+  {
+    const double bound = (double)__int_as_float(amax[0]) + (double)__int_as_float(amax[1]);
+    if (bound > 0.0) frexp(bound, &E);
+  }
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int q = q0 + ty, pp = p0 + tx;
+    float2 v = make_float2(0.f, 0.f);
+    if (q < nb && pp < nb) {
+      const long long g = ((q * N + j) * N + l) * N + pp;   // Y1_{q j p l} at [q][j][l][p]
+      v = make_float2(Y1s[g], Y1s[P + g]);
+    }
+    t1[ty][tx] = v;
+  }
+  __syncthreads();
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int pp = p0 + ty, q = q0 + tx;
+    if (pp >= nb) continue;
+    float2 h = make_float2(0.f, 0.f);
+    if (q < nb) {
+      const long long g = ((pp * N + l) * N + j) * N + q;   // Y2_{p l q j} at [p][l][j][q]
+      const float2 a = t1[tx][ty];
+      h = make_float2(a.x - Y2s[g], a.y - Y2s[P + g]);
+    }
+    for (int u = 0; u < 2; ++u)
+      for (int v = 0; v < 2; ++v) {
+        const float x = (u == 0) ? (v ? h.y : h.x) : (v ? h.x : -h.y);
+        const long long row = 2 * jl + v;
+        const long long col = ((long long)u * N + pp) * kpad + q;
+        slice4_f64((double)x, E, L, out + row * ldb + col, slice_stride);
+      }
+  }
+}
+
 struct AsmParams {
   int nb, nblk;
   const int4 *blocks;
@@ -165,6 +301,7 @@ struct AsmParams {
   cplx *kout;                  // write-k mode
   int stage;
   double dt;
+  int *amax;                   // optional: max |written ys or y32| (sliced form)
 };
 
 __device__ __forceinline__ int bidx(int a, int b, int c, int d) { return ((a * BSZ + b) * BSZ + c) * BSZ + d; }
@@ -294,6 +431,7 @@ __global__ void __launch_bounds__(ATHREADS) orbit_assemble_kernel(const AsmParam
   float *__restrict__ y32v = p.y32;
   const long long P = p.P;
   const double dt = p.dt;
+  float mx = 0.f;
   for (int m = 0; m < 4; ++m) {
     bool dup = false;
     for (int q = 0; q < m; ++q)
@@ -327,17 +465,21 @@ __global__ void __launch_bounds__(ATHREADS) orbit_assemble_kernel(const AsmParam
         const float w = (p.stage == 0) ? 1.f : 2.f;
         accv[g[t]] = ac[t].x + w * k[t].x;
         accv[P + g[t]] = ac[t].y + w * k[t].y;
-        ysv[g[t]] = (float)(y0[t].x + h * k[t].x);
-        ysv[P + g[t]] = (float)(y0[t].y + h * k[t].y);
+        const float sx = (float)(y0[t].x + h * k[t].x), sy = (float)(y0[t].y + h * k[t].y);
+        ysv[g[t]] = sx;
+        ysv[P + g[t]] = sy;
+        mx = fmaxf(mx, fmaxf(fabsf(sx), fabsf(sy)));
       } else {
         const double nx = y0[t].x + dt / 6.0 * ((double)ac[t].x + (double)k[t].x);
         const double ny = y0[t].y + dt / 6.0 * ((double)ac[t].y + (double)k[t].y);
         yv[g[t]] = make_double2(nx, ny);
         y32v[g[t]] = (float)nx;
         y32v[P + g[t]] = (float)ny;
+        mx = fmaxf(mx, fmaxf(fabsf((float)nx), fabsf((float)ny)));
       }
     }
   }
+  if (p.amax) block_amax(mx, p.amax);
 }
 
 // ------------------------------------------------------------------ tensor maps
@@ -357,12 +499,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 int encode_map(CUtensorMap *m, const void *base, int rank, const cuuint64_t *dims, const cuuint64_t *strides,
-               const cuuint32_t *box) {
+               const cuuint32_t *box, bool bf16 = false) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return G1G2_ECUDA;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void *>(base), dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank,
+                   const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   bf16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? G1G2_OK : G1G2_ECUDA;
 }
@@ -388,6 +531,13 @@ int map_b(CUtensorMap *m, const float *base, int kt, int rows, int box_rows) {
   cuuint64_t str[2] = {(cuuint64_t)kt * 4, (cuuint64_t)kt * 4 * rows};
   cuuint32_t box[3] = {(cuuint32_t)kBlockK, (cuuint32_t)box_rows, 1};
   return encode_map(m, base, 3, dims, str, box);
+}
+// B as four BF16 slices [q][rows][kt]; one box carries all four
+int map_bs(CUtensorMap *m, const __nv_bfloat16 *base, long long kt, int rows, int box_rows) {
+  cuuint64_t dims[3] = {(cuuint64_t)kt, (cuuint64_t)rows, (cuuint64_t)kSlices};
+  cuuint64_t str[2] = {(cuuint64_t)kt * 2, (cuuint64_t)kt * 2 * rows};
+  cuuint32_t box[3] = {(cuuint32_t)kBlockK, (cuuint32_t)box_rows, (cuuint32_t)kSlices};
+  return encode_map(m, base, 3, dims, str, box, true);
 }
 
 }  // namespace
@@ -417,6 +567,13 @@ struct TcPath {
   int nblocks = 0;
   int *err = nullptr;
   int splits = 0, kb_all_coll = 0, kb_per_split = 0;
+  // sliced form: BF16 slices [4][rows][kt] of the B operands and of w; A maxima
+  bool sliced = false;
+  __nv_bfloat16 *bh_s = nullptr, *bnr_s = nullptr, *bnc_s = nullptr, *bnb_s = nullptr, *bnt_s = nullptr,
+                *w_s = nullptr, *bpi_s = nullptr;
+  int *amax = nullptr;  // slots: see kAmax*
+  int pi_lead = 7;      // leading-slice width of the polarisation GEMM (K = 2 nb kpad)
+  CUtensorMap mBh_s, mBnr_s, mBnc_s, mBnb_s, mBnt_s, mW_s, mBpi_s;
   // tensor maps
   CUtensorMap mZin_y32, mZin_ys32, mCol_y32, mCol_ys32, mW32, mBuf1Gather, mBuf2Lin, mBuf1Lin;
   CUtensorMap mBh_hi, mBh_lo, mBnr_hi, mBnr_lo, mBnc_hi, mBnc_lo, mBnb_hi, mBnb_lo, mW_hi, mW_lo;
@@ -424,6 +581,12 @@ struct TcPath {
 };
 
 namespace {
+
+// amax slots: FP32 bit patterns of the largest |A| of each A tensor of the sliced form
+enum : int {
+  kAmaxW = 0, kAmaxY = 1, kAmaxYs = 2, kAmaxP1 = 3, kAmaxP2 = 4, kAmaxP3 = 5, kAmaxH1 = 6, kAmaxH2 = 7,
+  kAmaxSlots = 8
+};
 
 template <class T>
 int talloc(TcPath *p, T **ptr, size_t count) {
@@ -438,24 +601,28 @@ int talloc(TcPath *p, T **ptr, size_t count) {
 }
 
 // dynamic shared memory of one GEMM CTA; acc64_bytes > 0 adds the FP64 split-K accumulator
-size_t gemm_smem(int nout, int *stages, size_t acc64_bytes = 0) {
-  const size_t stage = 2 * (size_t)kABytes + 2 * (size_t)nout * kBlockK * 4;
-  const size_t budget = 220 * 1024 - acc64_bytes;
+size_t gemm_smem(bool sliced, int nout, int *stages, size_t acc64_bytes = 0) {
+  const size_t stage = stage_bytes_for(sliced, nout);
+  const size_t budget = 224 * 1024 - acc64_bytes;
   int s = (int)std::min<size_t>(4, budget / stage);
   if (s < 2) s = 2;
   *stages = s;
   return 1024 + s * stage + 256 + acc64_bytes;
 }
 
+// sliced: the BF16-slice form (Bh = slices of B, Bl unused); otherwise TF32 hi/lo
 void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, const CUtensorMap &Bh,
-                 const CUtensorMap &Bl, GemmParams gp, const CUtensorMap *A2 = nullptr) {
+                 const CUtensorMap &Bl, GemmParams gp, bool sliced = false, const CUtensorMap *A2 = nullptr) {
   gp.err = t->err;
   int stages = 0;
   const size_t acc64 = gp.kb_chunks ? (size_t)gp.nb * (gp.n_valid + 1) * sizeof(float2) : 0;
-  const size_t smem = gemm_smem(gp.nout, &stages, acc64);
+  const size_t smem = gemm_smem(sliced, gp.nout, &stages, acc64);
   const int grid = std::max(1, std::min(gp.tiles, t->sms));
   L.before(tag);
-  tc_gemm_kernel<<<grid, 256, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
+  if (sliced)
+    tc_gemm_kernel<true><<<grid, 256, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
+  else
+    tc_gemm_kernel<false><<<grid, 256, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
   L.after_launch();
 }
 
@@ -477,7 +644,8 @@ GemmParams linear_params(const TcPath *t, long long rows, int planes, int epi, f
 
 }  // namespace
 
-int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, const cplx *hsrc, cudaStream_t stream) {
+int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const cplx *hw, const cplx *hsrc,
+              cudaStream_t stream) {
   *out = nullptr;
   if (nb % 4 != 0) {
     set_error_detail("the tensor-core form needs nb divisible by 4 (TMA row pitch)");
@@ -493,6 +661,7 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, con
   t->nb = nb;
   t->se = se;
   t->restricted = restricted;
+  t->sliced = sliced;
   t->N4 = N4;
   t->kpad = round_up(nb, kBlockK);
   t->nout2 = round_up(2 * nb, 16);
@@ -516,9 +685,18 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, con
       (rc = talloc(t, &t->bnb_hi, (size_t)t->nout2 * kt_c)) || (rc = talloc(t, &t->bnb_lo, (size_t)t->nout2 * kt_c)) ||
       (rc = talloc(t, &t->nbar, N * N)) || (rc = talloc(t, &t->I, N * N)) || (rc = talloc(t, &t->err, 1)))
     return bail(rc);
+  if (sliced) {
+    const size_t bs_c = (size_t)kSlices * t->nout2 * kt_c, bs_r = (size_t)kSlices * t->nout2 * kt_r;
+    if ((rc = talloc(t, &t->bh_s, bs_c)) || (rc = talloc(t, &t->bnr_s, bs_r)) || (rc = talloc(t, &t->bnc_s, bs_c)) ||
+        (rc = talloc(t, &t->bnb_s, bs_c)) || (rc = talloc(t, &t->bnt_s, bs_r)) ||
+        (rc = talloc(t, &t->w_s, (size_t)kSlices * N4)) || (rc = talloc(t, &t->amax, kAmaxSlots)))
+      return bail(rc);
+    if (cudaMemset(t->amax, 0, kAmaxSlots * sizeof(int)) != cudaSuccess) return bail(G1G2_ECUDA);
+  }
   if (se == G1G2_GW) {
     const long long ncol = 2 * N * N;  // output columns (j, l, v)
-    t->pi_nout = (int)std::min<long long>(256, ((ncol + 15) / 16) * 16);
+    // the sliced form keeps three accumulators of nout columns in TMEM (512 columns)
+    t->pi_nout = (int)std::min<long long>(sliced ? 128 : 256, ((ncol + 15) / 16) * 16);
     t->pi_ntiles = (int)((ncol + t->pi_nout - 1) / t->pi_nout);
     t->pi_mtiles = ((nb + 3) / 4) * ((nb + 31) / 32);
     t->pi_ldb = 2 * N * t->kpad;
@@ -530,6 +708,12 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, con
     if (cudaMemset(t->bpi_hi, 0, brows * t->pi_ldb * sizeof(float)) != cudaSuccess ||
         cudaMemset(t->bpi_lo, 0, brows * t->pi_ldb * sizeof(float)) != cudaSuccess)
       return bail(G1G2_ECUDA);
+    if (sliced) {
+      t->pi_lead = slice_lead_order1(2LL * N * t->kpad);
+      if ((rc = talloc(t, &t->bpi_s, (size_t)kSlices * brows * t->pi_ldb))) return bail(rc);
+      if (cudaMemset(t->bpi_s, 0, (size_t)kSlices * brows * t->pi_ldb * sizeof(__nv_bfloat16)) != cudaSuccess)
+        return bail(G1G2_ECUDA);
+    }
   }
   // collision split-K geometry: K = nb^3 floats, both planes
   t->kb_all_coll = (int)((N * N * N + kBlockK - 1) / kBlockK);
@@ -570,6 +754,20 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, con
     if (cudaMalloc(&wd, N4 * sizeof(cplx)) != cudaSuccess) return bail(G1G2_ENOMEM);
     cudaMemcpy(wd, hw, N4 * sizeof(cplx), cudaMemcpyHostToDevice);
     split_real_kernel<<<1024, 256, 0, stream>>>(N4, wd, t->w_hi, t->w_lo);
+    if (sliced) {
+      double wmax = 0.0;
+      float smax = 0.f;
+      for (long long e = 0; e < N4; ++e) {
+        wmax = std::max(wmax, std::fabs(hw[e].x));
+        smax = std::max(smax, std::fabs(w32[e]));
+      }
+      int E = 0;
+      if (wmax > 0.0) std::frexp(wmax, &E);
+      slice_w_kernel<<<1024, 256, 0, stream>>>(N4, wd, E, t->w_s);
+      int bits = 0;
+      std::memcpy(&bits, &smax, sizeof(bits));
+      cudaMemcpy(t->amax + kAmaxW, &bits, sizeof(int), cudaMemcpyHostToDevice);
+    }
     cudaStreamSynchronize(stream);
     cudaFree(wd);
     if (cudaGetLastError() != cudaSuccess) return bail(G1G2_ECUDA);
@@ -597,20 +795,39 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, con
         (rc = map_b(&t->mBpi_hi, t->bpi_hi, (int)t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
         (rc = map_b(&t->mBpi_lo, t->bpi_lo, (int)t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
         (rc = map_b(&t->mBnt_hi, t->bnt_hi, kt_r, t->nout2, t->nout2)) ||
-        (rc = map_b(&t->mBnt_lo, t->bnt_lo, kt_r, t->nout2, t->nout2))))) {
+        (rc = map_b(&t->mBnt_lo, t->bnt_lo, kt_r, t->nout2, t->nout2)))) ||
+      (sliced && ((rc = map_bs(&t->mBh_s, t->bh_s, kt_c, t->nout2, t->nout2)) ||
+                  (rc = map_bs(&t->mBnr_s, t->bnr_s, kt_r, t->nout2, t->nout2)) ||
+                  (rc = map_bs(&t->mBnc_s, t->bnc_s, kt_c, t->nout2, t->nout2)) ||
+                  (rc = map_bs(&t->mBnb_s, t->bnb_s, kt_c, t->nout2, t->nout2)) ||
+                  (rc = map_bs(&t->mBnt_s, t->bnt_s, kt_r, t->nout2, t->nout2)) ||
+                  (rc = map_bs(&t->mW_s, t->w_s, N3, nb, t->nout1)) ||
+                  (se == G1G2_GW &&
+                   (rc = map_bs(&t->mBpi_s, t->bpi_s, t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)))))) {
     set_error_detail("cuTensorMapEncodeTiled failed");
     return bail(rc);
   }
   int st = 0;
-  size_t smax = std::max(gemm_smem(t->nout2, &st), gemm_smem(t->nout1, &st, (size_t)nb * (nb + 1) * sizeof(float2)));
-  if (se == G1G2_GW) smax = std::max(smax, gemm_smem(t->pi_nout, &st));
+  const size_t acc64 = (size_t)nb * (nb + 1) * sizeof(float2);
+  size_t smax = std::max(gemm_smem(sliced, t->nout2, &st), gemm_smem(sliced, t->nout1, &st, acc64));
+  if (se == G1G2_GW) smax = std::max(smax, gemm_smem(sliced, t->pi_nout, &st));
   if (smax > 227 * 1024) {
     set_error_detail("basis too large for the FP64 split-K accumulator of the tensor-core collision integral");
     return bail(G1G2_EUNSUPPORTED);
   }
-  if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax) != cudaSuccess ||
-      cudaFuncSetAttribute(orbit_assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(4 * BEL * sizeof(float2))) != cudaSuccess) {
+  // The limit is a property of the kernel, shared by every context of the process:
+  // set it to the device maximum so that no context lowers it under another one.
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  auto raise_limit = [&](const void *fn, size_t need) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return false;
+    const int dyn = optin - (int)fa.sharedSizeBytes;  // static shared memory counts against the same limit
+    return dyn >= (int)need && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess;
+  };
+  if (!raise_limit((const void *)tc_gemm_kernel<false>, smax) || !raise_limit((const void *)tc_gemm_kernel<true>, smax) ||
+      !raise_limit((const void *)orbit_assemble_kernel, 4 * BEL * sizeof(float2))) {
+    cudaGetLastError();
     set_error_detail("cannot raise the shared-memory limit of the tensor-core kernels");
     return bail(G1G2_ECUDA);
   }
@@ -636,8 +853,10 @@ int tc_error(TcPath *p, cudaStream_t stream) {
 }
 
 void tc_load_state(TcPath *p, Launcher &L, const cplx *G) {
+  int *slot = p->sliced ? p->amax + kAmaxY : nullptr;
+  if (slot) cudaMemsetAsync(slot, 0, sizeof(int), L.stream);
   L.before("tc_to_planar");
-  to_planar_f32_kernel<<<2048, 256, 0, L.stream>>>(p->N4, G, p->y32);
+  to_planar_f32_kernel<<<2048, 256, 0, L.stream>>>(p->N4, G, p->y32, slot);
   L.after_launch();
 }
 
@@ -649,15 +868,37 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   const long long N = nb, N3 = N * N * N;
   // stage input of G2 in FP32 planar
   const bool from_y = (st.stage == 0);
+  const bool sl = t->sliced;
+  int *const amax = t->amax;
   if (st.stage < 0) {
+    if (sl) cudaMemsetAsync(amax + kAmaxYs, 0, sizeof(int), L.stream);
     L.before("tc_to_planar");
-    to_planar_f32_kernel<<<2048, 256, 0, L.stream>>>(t->N4, G_in, t->ys32);
+    to_planar_f32_kernel<<<2048, 256, 0, L.stream>>>(t->N4, G_in, t->ys32, sl ? amax + kAmaxYs : nullptr);
     L.after_launch();
   }
   const CUtensorMap &mZin = from_y ? t->mZin_y32 : t->mZin_ys32;
   const CUtensorMap &mCol = from_y ? t->mCol_y32 : t->mCol_ys32;
+  const int *g2_amax = sl ? amax + (from_y ? kAmaxY : kAmaxYs) : nullptr;
+  if (sl) cudaMemsetAsync(amax + kAmaxP1, 0, 3 * sizeof(int), L.stream);  // this call's source-term passes
   // small operands
   one_minus(L, nb, n_in, t->nbar);
+  if (sl) {
+    const int kc = 2 * t->kpad;
+    struct { const cplx *S; int complex_a, shift, ld, transpose; __nv_bfloat16 *out; } ops[5] = {
+        {hhf, 1, 1, kc, 0, t->bh_s},
+        {n_in, 0, 0, t->kpad, 0, t->bnr_s},
+        {n_in, 1, 0, kc, 0, t->bnc_s},
+        {t->nbar, 1, 0, kc, 0, t->bnb_s},
+        {n_in, 0, 0, t->kpad, 1, t->bnt_s}};
+    const int nops = (t->se == G1G2_GW) ? 5 : 4;
+    for (int q = 0; q < nops; ++q) {
+      const auto &o = ops[q];
+      L.before("tc_slice_b");
+      slice_b_kernel<<<1, 1024, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.ld, o.transpose, o.S,
+                                               o.out, (long long)t->nout2 * o.ld);
+      L.after_launch();
+    }
+  }
   {
     const int kc = 2 * t->kpad;
     struct { const cplx *S; int complex_a, shift; double scale; int ld, col0, transpose; float *hi, *lo; } ops[5] = {
@@ -666,7 +907,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
         {n_in, 1, 0, 1.0, kc, 0, 0, t->bnc_hi, t->bnc_lo},
         {t->nbar, 1, 0, 1.0, kc, 0, 0, t->bnb_hi, t->bnb_lo},
         {n_in, 0, 0, 1.0, t->kpad, 0, 1, t->bnt_hi, t->bnt_lo}};
-    const int nops = (t->se == G1G2_GW) ? 5 : 4;
+    const int nops = sl ? 0 : (t->se == G1G2_GW) ? 5 : 4;  // the sliced form slices these above
     for (int q = 0; q < nops; ++q) {
       const auto &o = ops[q];
       L.before("tc_realify");
@@ -691,33 +932,58 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     g.n_valid = nb;
     g.kb_chunks = 4;
     g.out64 = t->partial;
-    launch_gemm(t, L, "tc_gemm_collision", mCol, t->mW_hi, t->mW_lo, g);
+    g.a_amax = g2_amax;
+    launch_gemm(t, L, "tc_gemm_collision", mCol, sl ? t->mW_s : t->mW_hi, t->mW_lo, g, sl);
     L.before("tc_collision_reduce");
     collision_reduce_kernel<<<(nb * nb + 127) / 128, 128, 0, L.stream>>>(nb, t->splits, t->partial, t->I);
     L.after_launch();
   }
   g1_update(L, nb, hhf, n_in, t->I, st, ny, nys, nacc, nk);
   // a4: the source-term chain
-  launch_gemm(t, L, "tc_gemm_psi1", t->mW32, t->mBnr_hi, t->mBnr_lo, linear_params(t, N3, 1, EP_EXCH_T, t->buf1));
+  // sliced-form A scales and output maxima of each pass
+  auto lp = [&](long long rows, int planes, int epi, float *out, int a_slot, int out_slot) {
+    GemmParams g = linear_params(t, rows, planes, epi, out);
+    if (sl) {
+      g.a_amax = a_slot >= 0 ? amax + a_slot : g2_amax;
+      g.out_amax = out_slot >= 0 ? amax + out_slot : nullptr;
+    }
+    return g;
+  };
+  launch_gemm(t, L, "tc_gemm_psi1", t->mW32, sl ? t->mBnr_s : t->mBnr_hi, t->mBnr_lo,
+              lp(N3, 1, EP_EXCH_T, t->buf1, kAmaxW, kAmaxP1), sl);
   {
-    GemmParams g = linear_params(t, N3, 2, EP_GATHER_TCONJ, t->buf2);
+    GemmParams g = lp(N3, 2, EP_GATHER_TCONJ, t->buf2, kAmaxP1, kAmaxP2);
     g.a_rows = AR_GATHER4;
     g.g_na = (nb + 3) / 4;
     g.g_nb = (nb + 31) / 32;
     g.tiles = nb * g.g_na * g.g_nb;
-    launch_gemm(t, L, "tc_gemm_psi2", t->mBuf1Gather, t->mBnc_hi, t->mBnc_lo, g);
+    launch_gemm(t, L, "tc_gemm_psi2", t->mBuf1Gather, sl ? t->mBnc_s : t->mBnc_hi, t->mBnc_lo, g, sl);
   }
-  launch_gemm(t, L, "tc_gemm_psi3", t->mBuf2Lin, t->mBnb_hi, t->mBnb_lo, linear_params(t, N3, 2, EP_EXCH_T, t->buf1));
+  launch_gemm(t, L, "tc_gemm_psi3", t->mBuf2Lin, sl ? t->mBnb_s : t->mBnb_hi, t->mBnb_lo,
+              lp(N3, 2, EP_EXCH_T, t->buf1, kAmaxP2, kAmaxP3), sl);
   // a3: Z = G2 x_4 (hHF - mu); last a4 pass: Q = T2~ x_4 nbar = A^dag (both in the swapped layout)
-  launch_gemm(t, L, "tc_gemm_commutator", mZin, t->mBh_hi, t->mBh_lo, linear_params(t, N3, 2, EP_SWAP34, t->Z));
-  launch_gemm(t, L, "tc_gemm_psi4", t->mBuf1Lin, t->mBnb_hi, t->mBnb_lo, linear_params(t, N3, 2, EP_SWAP34, t->buf2));
+  launch_gemm(t, L, "tc_gemm_commutator", mZin, sl ? t->mBh_s : t->mBh_hi, t->mBh_lo,
+              lp(N3, 2, EP_SWAP34, t->Z, -1, -1), sl);
+  launch_gemm(t, L, "tc_gemm_psi4", t->mBuf1Lin, sl ? t->mBnb_s : t->mBnb_hi, t->mBnb_lo,
+              lp(N3, 2, EP_SWAP34, t->buf2, kAmaxP3, -1), sl);
   if (t->se == G1G2_GW) {
     // a5: Y1 = w x_4 n, Y2 = w x_4 n^T (hcorr_ijkl = Y1_ijkl - Y2_klij), swapped layout
-    launch_gemm(t, L, "tc_gemm_hcorr", t->mW32, t->mBnr_hi, t->mBnr_lo, linear_params(t, N3, 1, EP_SWAP34, t->Y1));
-    launch_gemm(t, L, "tc_gemm_hcorr", t->mW32, t->mBnt_hi, t->mBnt_lo, linear_params(t, N3, 1, EP_SWAP34, t->Y2));
+    if (sl) cudaMemsetAsync(amax + kAmaxH1, 0, 2 * sizeof(int), L.stream);
+    launch_gemm(t, L, "tc_gemm_hcorr", t->mW32, sl ? t->mBnr_s : t->mBnr_hi, t->mBnr_lo,
+                lp(N3, 1, EP_SWAP34, t->Y1, kAmaxW, kAmaxH1), sl);
+    launch_gemm(t, L, "tc_gemm_hcorr", t->mW32, sl ? t->mBnt_s : t->mBnt_hi, t->mBnt_lo,
+                lp(N3, 1, EP_SWAP34, t->Y2, kAmaxW, kAmaxH2), sl);
+    const dim3 pgrid((unsigned)(((nb + 31) / 32) * (t->kpad / 32)), (unsigned)(N * N));
     L.before("tc_realify_pi");
-    realify_pi_kernel<<<dim3((unsigned)(((nb + 31) / 32) * (t->kpad / 32)), (unsigned)(N * N)), dim3(32, 8), 0,
-                        L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, t->bpi_hi, t->bpi_lo, t->pi_ldb);
+    if (sl) {
+      const long long brows = (long long)t->pi_ntiles * t->pi_nout;
+      realify_pi_sliced_kernel<<<pgrid, dim3(32, 8), 0, L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4,
+                                                                    amax + kAmaxH1, t->pi_lead, t->bpi_s,
+                                                                    t->pi_ldb, brows * t->pi_ldb);
+    } else {
+      realify_pi_kernel<<<pgrid, dim3(32, 8), 0, L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, t->bpi_hi,
+                                                             t->bpi_lo, t->pi_ldb);
+    }
     L.after_launch();
     // a6: Pi_(ik),(jl) = sum_(pq) G_ipkq hcorr_qjpl, one GEMM with M = N' = K = nb^2
     GemmParams g{};
@@ -734,7 +1000,11 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     g.rows = 2 * N * N;
     g.out = t->Pi;
     g.out_plane = t->N4;
-    launch_gemm(t, L, "tc_gemm_pi", from_y ? t->mPi_y32 : t->mPi_ys32, t->mBpi_hi, t->mBpi_lo, g);
+    g.a_amax = g2_amax;
+    g.slice_lead = t->pi_lead;
+    g.acc3 = 1;
+    launch_gemm(t, L, "tc_gemm_pi", from_y ? t->mPi_y32 : t->mPi_ys32, sl ? t->mBpi_s : t->mBpi_hi, t->mBpi_lo, g,
+                sl);
   }
   // a7: orbit assembly + RK4
   AsmParams a{};
@@ -752,6 +1022,11 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   a.kout = Gk;
   a.stage = st.stage;
   a.dt = st.dt;
+  if (sl && st.stage >= 0) {
+    // the assembly writes the next stage input (ys) or, at the last stage, the new FP32 state (y32)
+    a.amax = amax + (st.stage < 3 ? kAmaxYs : kAmaxY);
+    cudaMemsetAsync(a.amax, 0, sizeof(int), L.stream);
+  }
   L.before("tc_orbit_assemble_rk4");
   orbit_assemble_kernel<<<t->nblocks, ATHREADS, 4 * BEL * sizeof(float2), L.stream>>>(a);
   L.after_launch();

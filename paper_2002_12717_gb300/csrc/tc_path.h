@@ -9,7 +9,8 @@ struct TcPath;
 
 // Build the tensor-core path for one context. hw: w (complex, [(ij),(kl)]),
 // hsrc: source-term interaction (w^- for SOA in a spin-orbital basis, else w).
-int tc_create(TcPath **out, int nb, int se, bool restricted, const cplx *hw, const cplx *hsrc,
+// sliced: BF16-slice operands with an exact leading product instead of TF32 hi/lo.
+int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const cplx *hw, const cplx *hsrc,
               cudaStream_t stream);
 void tc_destroy(TcPath *p);
 

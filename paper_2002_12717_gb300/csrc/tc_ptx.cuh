@@ -112,6 +112,37 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor: K-major operand tile with 64-byte rows and
+// 64-byte swizzling (8-row atoms 512 B apart), the layout of the bf16 slices.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+  d |= (uint64_t)1 << 16;                            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512u >> 4) << 32;                  // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                            // descriptor version
+  d |= (uint64_t)4 << 61;                            // 64-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::f16 with BF16 A and B, FP32 accumulator, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4)                       // D format: F32
+         | (1u << 7)                     // A format: BF16
+         | (1u << 10)                    // B format: BF16
+         | ((uint32_t)(N >> 3) << 17)    // N / 8
+         | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // Instruction descriptor: kind::tf32, FP32 accumulator, both operands K-major.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4)                       // D format: F32
@@ -150,6 +181,49 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Exponent E with |x| < 2^E for every x of a tensor whose largest magnitude has
+// the FP32 bit pattern mbits (0 for an all-zero tensor).
+__host__ __device__ __forceinline__ int slice_exponent(int mbits) {
+  return mbits > 0 ? ((mbits >> 23) & 255) - 126 : 0;
+}
+
+// Leading-slice width for an exact FP32 accumulation over K terms: with
+// |q_0| <= 2^L on both operands the K products sum below 2^24 when
+// K 2^(2L) < 2^24; L = 7 (8-bit slices) covers K <= 1024.
+__host__ __device__ constexpr int slice_lead_for(long long K) {
+  int L = 7;
+  while (L > 1 && K * (1LL << (2 * L)) >= (1LL << 24)) --L;
+  return L;
+}
+// ... and when the two order-1 products (|q_0 q_1| <= 2^(L+7)) must sum exactly too
+__host__ __device__ constexpr int slice_lead_order1(long long K) {
+  int L = slice_lead_for(K);
+  while (L > 1 && 2 * K * (1LL << (L + 7)) >= (1LL << 24)) --L;
+  return L;
+}
+
+// Four integer-valued slices of xs = x 2^-E (|xs| < 1): xs = sum_s q_s 2^(-L-8s)
+// + O(2^-(L+25)) with integers |q_0| <= 2^L, |q_s| <= 128 (round to nearest
+// even at each cut), so every slice is exact in BF16 once scaled back by
+// 2^(E-L-8s).  Each cut removes the leading bits exactly (the remainder is
+// representable in FP32).  mul[s] = 2^(L+8s), imul[s] = 2^-(L+8s).
+__device__ __forceinline__ void slice4(float xs, float (&q)[4], const float (&mul)[4], const float (&imul)[4]) {
+  q[0] = rintf(xs * mul[0]);
+  float r = fmaf(q[0], -imul[0], xs);
+  q[1] = rintf(r * mul[1]);
+  r = fmaf(q[1], -imul[1], r);
+  q[2] = rintf(r * mul[2]);
+  r = fmaf(q[2], -imul[2], r);
+  q[3] = rintf(r * mul[3]);
+}
+
+// two FP32 values -> packed BF16 pair (lo in the low half), round to nearest
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
 }
 
 // Round to the nearest TF32 value (10 explicit mantissa bits), kept in an FP32 container.

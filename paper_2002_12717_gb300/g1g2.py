@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libg1g2.so")
 
 OK, EINVAL, ESYMM, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 SELFENERGY = {"HF": 0, "SOA": 1, "GW": 2}
-PRECISION = {"fp64": 0, "tf32x3": 1}
+PRECISION = {"fp64": 0, "tf32x3": 1, "bf16x4": 2}
 
 
 class G1G2Error(RuntimeError):
