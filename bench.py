@@ -8,7 +8,7 @@ build, collision integral, two-particle commutator, source term, GW
 quasi-Hamiltonian and polarisation, assembly + RK4, observables).
 value = bench steps per second = 1 / (t_SOA96 + t_GW64).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32x3|fp64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x4|tf32x3|fp64]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
 
 With N > 1 (torchrun) every rank runs an independent replica of the same
@@ -72,17 +72,21 @@ def algorithmic_flops(nb, se, stage_launches=None):
     return 8.0 * per_rhs * 4
 
 
-def kernel_work(tag, nb, se):
+# tensor products issued per real multiply-add: TF32 hi/lo (3) or BF16 slices (10)
+SPLIT_PRODUCTS = {"tf32x3": 3, "bf16x4": 10}
+
+
+def kernel_work(tag, nb, se, precision="tf32x3"):
     """(bound, work per launch) of the dominant-kernel candidates.
 
     Tensor kernels count the real flops of the split-precision products the
-    kernel must issue (three TF32 products per real multiply-add, 2 flops
-    each) on the unpadded problem; the assembly counts its algorithmic HBM
-    bytes (FP32 intermediates, FP64 state, FP32 RK4 accumulator and stage
-    input), averaged over the four RK4 stages.
+    kernel must issue (three TF32 products, or ten BF16 slice products, per
+    real multiply-add, 2 flops each) on the unpadded problem; the assembly
+    counts its algorithmic HBM bytes (FP32 intermediates, FP64 state, FP32
+    RK4 accumulator and stage input), averaged over the four RK4 stages.
     """
     n = float(nb)
-    split = 3 * 2
+    split = SPLIT_PRODUCTS.get(precision, 3) * 2
     if tag == "tc_gemm_pi":
         return "tensor", split * n * n * (2 * n * n) * (2 * n * n)
     if tag in ("tc_gemm_commutator", "tc_gemm_psi2", "tc_gemm_psi3", "tc_gemm_psi4"):
@@ -260,15 +264,20 @@ def run_ours(args, rank, world, dist):
     # roofline of the dominant kernel: the (kernel, workload) pair with the largest device time
     total_ms = sum(v[1] for v in prof_all.values())
     cands = [(t_ms, tag, name, n_l) for name, rep in per_kernel.items() for tag, (n_l, t_ms) in rep.items()
-             if kernel_work(tag, per[name]["nb"], per[name]["selfenergy"])[0] is not None]
+             if kernel_work(tag, per[name]["nb"], per[name]["selfenergy"], args.precision)[0] is not None]
     cands.sort(reverse=True)
     if not cands:
         cands = [(0.0, "none", next(iter(per)), 1)]
     t_ms, dom_tag, dom_wl, dom_n = cands[0]
     d_nb, d_se = per[dom_wl]["nb"], per[dom_wl]["selfenergy"]
-    bound, work = kernel_work(dom_tag, d_nb, d_se)
+    bound, work = kernel_work(dom_tag, d_nb, d_se, args.precision)
     avg_s = t_ms * 1e-3 / dom_n
-    if bound == "tensor":
+    if bound == "tensor" and args.precision == "bf16x4":
+        peak = peaks["bf16_tflops_sustained"]
+        achieved = work / avg_s / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} bf16 sustained (cuBLAS loop), of {peak_kind}"}
+    elif bound == "tensor":
         peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
         achieved = work / avg_s / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -291,7 +300,7 @@ def run_ours(args, rank, world, dist):
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "tf32x3+f64",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else args.precision + "+f64",
         "data": "synthetic (seeded general basis: h Hermitian Gaussian, w = sum_P L^P x L^P, gauss-sine pulse)",
         "config": {"workload": "+".join(args.workloads), "precision": args.precision,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
@@ -312,6 +321,47 @@ def run_ours(args, rank, world, dist):
         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1][1])},
     }
     return line
+
+
+def adjoint_sample(args):
+    """Discrete adjoint on the 2D Hubbard cluster (4x4 sites, 32 spin-orbitals, 64 pulse
+    controls, dt = 0.01): gradient of the final double occupancy with respect to the
+    controls and U over the first `adjoint_steps` steps with checkpoints every 32 steps,
+    timed against the FP64 forward propagation of the same steps, with a central
+    finite-difference check (eps = 1e-5) of dJ/dU."""
+    from paper_2002_12717_gb300.g1g2 import Propagator
+
+    d = inputs.workload("hubbard-2d-4x4")
+    steps, dt, k = args.adjoint_steps, d["dt"], 32
+    M = len(d["drive"].values)
+
+    def make(w):
+        p = Propagator(d["h"], w, d["n0"], None, "SOA", "fp64")
+        p.set_drive(d["D"], d["drive"])
+        return p
+
+    def forward(w):
+        with make(w) as p:
+            t0 = time.perf_counter()
+            p.propagate(dt, steps)
+            J = float(p.observables(double_occ=True)["double_occ"].mean())
+            return J, time.perf_counter() - t0
+
+    forward(d["w"])  # warm-up
+    with make(d["w"]) as p:
+        t0 = time.perf_counter()
+        J, gd, gws, gh = p.adjoint(dt, steps, objective=0, ckpt_every=k, n_drive_params=M)
+        t_adj = time.perf_counter() - t0
+    J_f, t_fwd = forward(d["w"])
+    eps = 1e-5
+    fd = (forward(d["w"] * (1 + eps))[0] - forward(d["w"] * (1 - eps))[0]) / (2 * eps)
+    U = 2.0
+    return {"workload": f"hubbard-2d-4x4 (32 spin-orbitals, {M} controls), first {steps} of {d['nsteps']} steps",
+            "objective": "mean double occupancy at the final time", "ckpt_every": k, "precision": "fp64",
+            "ms_per_step": 1e3 * t_adj / steps, "forward_ms_per_step": 1e3 * t_fwd / steps,
+            "adjoint_over_forward": t_adj / t_fwd, "J": J, "J_forward": J_f,
+            "dJ_dU": gws / U, "fd_dJ_dU": fd / U, "rel_diff_dJ_dU": abs(gws - fd) / abs(fd),
+            "grad_controls_norm": float(np.linalg.norm(gd))}
 
 
 def cpu_baseline(args):
@@ -376,15 +426,17 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=None, choices=["fp64", "tf32x3"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "tf32x3", "bf16x4"])
     ap.add_argument("--workloads", default=",".join(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-steps", type=int, default=3,
                     help="steps run in both forms from the initial state (speed-up and error vs FP64)")
+    ap.add_argument("--adjoint-steps", type=int, default=100,
+                    help="steps of the discrete-adjoint sample on the 4x4 Hubbard cluster (0: skip)")
     args = ap.parse_args()
     args.workloads = args.workloads.split(",")
     if args.precision is None:
-        args.precision = os.environ.get("G1G2_BENCH_PRECISION", "tf32x3")
+        args.precision = os.environ.get("G1G2_BENCH_PRECISION", "bf16x4")
     if args.steps is None:
         args.steps = 3 if args.precision == "fp64" else 20
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
@@ -406,6 +458,8 @@ def main():
         dist = tdist
     line = run_ours(args, rank, world, dist)
     if rank == 0:
+        if args.adjoint_steps > 0:
+            line["adjoint"] = adjoint_sample(args)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)

@@ -22,8 +22,9 @@
 // round-toward-zero drift of long FP32 tensor-core accumulations, at 20 BF16
 // MMAs per 32-element K block instead of 12 TF32 ones.
 //
-// Warp roles (256 threads): warp 0 TMA producer, warp 1 TMEM owner and MMA
-// issuer, warps 2-3 converters, warps 4-7 epilogue (TMEM lanes 0..127).
+// Warp roles (384 threads): warp 0 TMA producer, warp 1 TMEM owner and MMA
+// issuer, warps 2-7 converters, warps 8-11 epilogue (TMEM lanes 0..127: a
+// warp reaches the lane quarter warp % 4).
 #pragma once
 
 #include "tc_ptx.cuh"
@@ -35,6 +36,9 @@ constexpr int kTileM = 128;
 constexpr int kBlockK = 32;                        // floats per K block (128 B)
 constexpr uint32_t kABytes = kTileM * kBlockK * 4; // 16 KB
 constexpr int kAccCols = 256;                      // TMEM columns per accumulator buffer
+constexpr int kGemmThreads = 384;
+constexpr int kConvThreads = 192;                  // warps 2-7
+constexpr int kEpiWarp0 = 8;                       // first epilogue warp
 constexpr int kSlices = 4;                         // BF16 slices per operand (sliced form)
 constexpr uint32_t kASliceBytes = kTileM * kBlockK * 2;  // 8 KB: one slice of an A tile, 64-byte rows
 constexpr uint32_t kSlicedBOff = kABytes + kSlices * kASliceBytes;  // 48 KB: B slices within a stage
@@ -110,7 +114,7 @@ __device__ __forceinline__ int tile_kblocks(const GemmParams &p, int tile) {
 // tmBhi/tmBlo: TF32 hi and lo parts of B; in the sliced form tmBhi holds the
 // four BF16 slices of B as [slice][row][k] (tmBlo unused).
 template <bool kSliced>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kGemmThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
                    const GemmParams p, const int stages) {
@@ -139,7 +143,7 @@ __global__ void __launch_bounds__(256, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 64);
+      mbar_init(&conv[s], kConvThreads);
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -279,25 +283,19 @@ __global__ void __launch_bounds__(256, 1)
       mma_commit(fin);
       mbar_wait(fin, 0, p.err);
     }
-  } else if (warp < 4) {
+  } else if (warp < kEpiWarp0) {
     // ------------------------------------------------------------ converters
     const int ct = threadIdx.x - 64;
     int s = 0;
     uint32_t ph = 0;
     bool ok = true;
-    // sliced form: xs = x 2^-E, slice q scaled back by 2^(E-7-8q)
-    float inv = 1.f, sc[kSlices] = {0.f, 0.f, 0.f, 0.f}, mul[kSlices] = {0.f, 0.f, 0.f, 0.f},
-          imul[kSlices] = {0.f, 0.f, 0.f, 0.f};
+    // sliced form: rounding constants c_q = 1.5 2^(23+E-L-8q) of the four cuts
+    float cut[kSlices] = {0.f, 0.f, 0.f, 0.f};
     if (kSliced) {
       const int E = slice_exponent(p.a_amax ? *p.a_amax : 0);
       const int Ld = p.slice_lead ? p.slice_lead : 7;
-      inv = ldexpf(1.f, -E);
 #pragma unroll
-      for (int q = 0; q < kSlices; ++q) {
-        sc[q] = ldexpf(1.f, E - Ld - 8 * q);
-        mul[q] = ldexpf(1.f, Ld + 8 * q);
-        imul[q] = ldexpf(1.f, -(Ld + 8 * q));
-      }
+      for (int q = 0; q < kSlices; ++q) cut[q] = ldexpf(1.5f, 23 + E - Ld - 8 * q);
     }
     for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
       const int nkb = tile_kblocks(p, tile);
@@ -307,29 +305,29 @@ __global__ void __launch_bounds__(256, 1)
         if (kSliced) {
           uint8_t *sl = smem + (size_t)s * stage_bytes + kABytes;
 #pragma unroll 2
-          for (int i = ct; i < (int)(kABytes / 16); i += 64) {
+          for (int i = ct; i < (int)(kABytes / 16); i += kConvThreads) {
             // 16-byte chunk i of the 128-byte-swizzled FP32 tile: row r, logical floats k0..k0+3
             const int r = i >> 3, k0 = ((i & 7) ^ (r & 7)) << 2;
             const float4 x = a[i];
             float q0[kSlices], q1[kSlices], q2[kSlices], q3[kSlices];
-            slice4(x.x * inv, q0, mul, imul);
-            slice4(x.y * inv, q1, mul, imul);
-            slice4(x.z * inv, q2, mul, imul);
-            slice4(x.w * inv, q3, mul, imul);
+            slice4(x.x, q0, cut);
+            slice4(x.y, q1, cut);
+            slice4(x.z, q2, cut);
+            slice4(x.w, q3, cut);
             // the same four elements in the 64-byte-swizzled BF16 slice tile
             const uint32_t off = (uint32_t)r * 64u + ((uint32_t)((k0 >> 3) ^ ((r >> 1) & 3)) << 4) + (uint32_t)(k0 & 7) * 2u;
 #pragma unroll
             for (int q = 0; q < kSlices; ++q) {
               uint2 v;
-              v.x = pack_bf16(q0[q] * sc[q], q1[q] * sc[q]);
-              v.y = pack_bf16(q2[q] * sc[q], q3[q] * sc[q]);
+              v.x = pack_bf16(q0[q], q1[q]);
+              v.y = pack_bf16(q2[q], q3[q]);
               *reinterpret_cast<uint2 *>(sl + q * kASliceBytes + off) = v;
             }
           }
         } else {
           float4 *lo = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes + kABytes);
 #pragma unroll 4
-          for (int i = ct; i < (int)(kABytes / 16); i += 64) {
+          for (int i = ct; i < (int)(kABytes / 16); i += kConvThreads) {
             const float4 x = a[i];
             float4 h, l;
             h.x = to_tf32(x.x); l.x = to_tf32(x.x - h.x);
@@ -347,7 +345,7 @@ __global__ void __launch_bounds__(256, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int r = threadIdx.x - 128;                  // TMEM lane == tile row
+    const int r = threadIdx.x - 32 * kEpiWarp0;       // TMEM lane == tile row
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     int acc = 0;
     uint32_t acc_ph = 0;

@@ -149,21 +149,31 @@ __device__ __forceinline__ void slice4_f64(double x, int E, int L, __nv_bfloat16
   }
 }
 
-// Sliced form of realify_kernel (one CTA): the same real matrix, one power-of-two
-// scale from its largest magnitude, written as slices [q][row][ld].
-__global__ void __launch_bounds__(1024) slice_b_kernel(int nb, int nout, int kpad, int complex_a, int shift, int ld,
-                                                       int transpose, const cplx *__restrict__ S,
-                                                       __nv_bfloat16 *out, long long slice_stride) {
-  __shared__ double red[32];
+// Sliced form of realify_kernel: the same real matrix, one power-of-two scale
+// from its largest magnitude, written as slices [q][row][ld].  The realified
+// matrix holds +-Re and +-Im of the (shifted) entries of S, so every CTA takes
+// the maximum over the nb^2 entries of S itself and slices its share.
+__global__ void __launch_bounds__(256) slice_b_kernel(int nb, int nout, int kpad, int complex_a, int shift, int ld,
+                                                      int transpose, const cplx *__restrict__ S,
+                                                      __nv_bfloat16 *out, long long slice_stride) {
+  __shared__ double red[8];
+  __shared__ double smu;
   const int kt = complex_a ? 2 * kpad : kpad;
   const int total = nout * kt;
-  double mu = 0.0;
-  if (shift)
-    for (int i = 0; i < nb; ++i) mu += S[i * nb + i].x;
-  mu /= nb;
+  if (threadIdx.x == 0) {
+    double mu = 0.0;
+    if (shift)
+      for (int i = 0; i < nb; ++i) mu += S[i * nb + i].x;
+    smu = mu / nb;
+  }
+  __syncthreads();
+  const double mu = smu;
   double mx = 0.0;
-  for (int e = threadIdx.x; e < total; e += blockDim.x)
-    mx = fmax(mx, fabs(realified(nb, kpad, complex_a, transpose, mu, S, e / kt, e % kt)));
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    cplx v = S[e];
+    if (e / nb == e % nb) v.x -= mu;
+    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
@@ -172,7 +182,7 @@ __global__ void __launch_bounds__(1024) slice_b_kernel(int nb, int nout, int kpa
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
   int E = 0;
   if (mx > 0.0) frexp(mx, &E);  // mx < 2^E
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int row = e / kt, col = e % kt;
     slice4_f64(realified(nb, kpad, complex_a, transpose, mu, S, row, col), E, 7, out + (long long)row * ld + col,
                slice_stride);
@@ -260,6 +270,9 @@ __global__ void realify_pi_sliced_kernel(int nb, int kpad, const float *__restri
     const double bound = (double)__int_as_float(amax[0]) + (double)__int_as_float(amax[1]);
     if (bound > 0.0) frexp(bound, &E);
   }
+  float cut[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) cut[q] = ldexpf(1.5f, 23 + E - L - 8 * q);
   for (int ty = ty0; ty < 32; ty += blockDim.y) {
     const int q = q0 + ty, pp = p0 + tx;
     float2 v = make_float2(0.f, 0.f);
@@ -284,7 +297,10 @@ __global__ void realify_pi_sliced_kernel(int nb, int kpad, const float *__restri
         const float x = (u == 0) ? (v ? h.y : h.x) : (v ? h.x : -h.y);
         const long long row = 2 * jl + v;
         const long long col = ((long long)u * N + pp) * kpad + q;
-        slice4_f64((double)x, E, L, out + row * ldb + col, slice_stride);
+        float sl[4];
+        slice4(x, sl, cut);
+#pragma unroll
+        for (int z = 0; z < 4; ++z) out[z * slice_stride + row * ldb + col] = __float2bfloat16_rn(sl[z]);
       }
   }
 }
@@ -620,9 +636,9 @@ void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, 
   const int grid = std::max(1, std::min(gp.tiles, t->sms));
   L.before(tag);
   if (sliced)
-    tc_gemm_kernel<true><<<grid, 256, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
+    tc_gemm_kernel<true><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
   else
-    tc_gemm_kernel<false><<<grid, 256, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
+    tc_gemm_kernel<false><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
   L.after_launch();
 }
 
@@ -894,7 +910,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     for (int q = 0; q < nops; ++q) {
       const auto &o = ops[q];
       L.before("tc_slice_b");
-      slice_b_kernel<<<1, 1024, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.ld, o.transpose, o.S,
+      slice_b_kernel<<<32, 256, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.ld, o.transpose, o.S,
                                                o.out, (long long)t->nout2 * o.ld);
       L.after_launch();
     }

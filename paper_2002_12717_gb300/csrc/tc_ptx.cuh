@@ -204,19 +204,19 @@ __host__ __device__ constexpr int slice_lead_order1(long long K) {
   return L;
 }
 
-// Four integer-valued slices of xs = x 2^-E (|xs| < 1): xs = sum_s q_s 2^(-L-8s)
-// + O(2^-(L+25)) with integers |q_0| <= 2^L, |q_s| <= 128 (round to nearest
-// even at each cut), so every slice is exact in BF16 once scaled back by
-// 2^(E-L-8s).  Each cut removes the leading bits exactly (the remainder is
-// representable in FP32).  mul[s] = 2^(L+8s), imul[s] = 2^-(L+8s).
-__device__ __forceinline__ void slice4(float xs, float (&q)[4], const float (&mul)[4], const float (&imul)[4]) {
-  q[0] = rintf(xs * mul[0]);
-  float r = fmaf(q[0], -imul[0], xs);
-  q[1] = rintf(r * mul[1]);
-  r = fmaf(q[1], -imul[1], r);
-  q[2] = rintf(r * mul[2]);
-  r = fmaf(q[2], -imul[2], r);
-  q[3] = rintf(r * mul[3]);
+// Four slices of x (|x| < 2^E): x = v_0 + v_1 + v_2 + v_3 + O(2^(E-L-25)), where
+// v_s is an integer multiple of 2^(E-L-8s) with |v_0| <= 2^E and
+// |v_s| <= 2^(E-L-8s+7) for s > 0, i.e. at most 8 significant bits: exact in
+// BF16.  Each cut rounds the running remainder to nearest-even on its grid by
+// adding and subtracting c_s = 1.5 2^(23+E-L-8s) (the sum's ulp is the grid
+// step), and the remainder r - v_s is exact in FP32.
+__device__ __forceinline__ void slice4(float x, float (&v)[4], const float (&c)[4]) {
+  float r = x;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    v[s] = __fsub_rn(__fadd_rn(r, c[s]), c[s]);
+    r = __fsub_rn(r, v[s]);
+  }
 }
 
 // two FP32 values -> packed BF16 pair (lo in the low half), round to nearest
