@@ -63,7 +63,7 @@ enum Epi : int {
   EP_EXCH_T = 1,        // row (p,q,r), col l -> out[v][q][p][l][r]
   EP_GATHER_TCONJ = 2,  // row (a,b,c), col d -> out[v][c][d][a][b], imaginary plane negated
   EP_PARTIAL = 3,       // split-K sums: partial[split][plane][row][col] (FP64 from a compensated FP32 sum)
-  EP_PI = 4,            // row (i,k), col (j,l,v) interleaved -> out[v][i][j][l][k]
+  EP_PI = 4,            // row (i,k), col (j,l,v) interleaved -> out[i][j][l][k] interleaved complex
 };
 
 struct GemmParams {
@@ -94,6 +94,8 @@ struct GemmParams {
   int *err;
   const int *a_amax;  // sliced form: FP32 bit pattern of max |A| (the A slice scale)
   int slice_lead;     // sliced form: leading-slice width L (slice_lead_for(K)); 0 means 7
+  int col_il;         // B rows (output columns) ordered 2 l + v instead of v nb + l
+  int out_il;         // EP_SWAP34 with col_il: interleaved complex FP32 output out[i][j][l][k]
   int acc3;           // sliced form: order-1 products in their own exact accumulator (nout <= 128,
                       // L = slice_lead_order1(K)); for long K, where the lower-order accumulator
                       // would collect a visible truncation bias
@@ -442,6 +444,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         split = tile % p.splits;
         valid = r < N;
       }
+      // Store map of this row: out[base + l cs (+ plane for the imaginary part)],
+      // with (l, v) decoded from the column (v nb + l, or 2 l + v with col_il).
+      long long base = 0;
+      int cs = 0;
+      bool neg_im = false;
+      if (p.epi == EP_SWAP34) {          // out[v][i][j][l][k], row (i,j,k)
+        base = (i0 * NN + i1) * NN * NN + i2;
+        cs = N;
+      } else if (p.epi == EP_EXCH_T) {   // out[v][q][p][l][r], row (p,q,r)
+        base = (i1 * NN + i0) * NN * NN + i2;
+        cs = N;
+      } else if (p.epi == EP_GATHER_TCONJ) {  // out[v][c][d][a][b], row (a,b,c), imaginary negated
+        base = i2 * NN * NN * NN + i0 * NN + i1;
+        cs = N * N;
+        neg_im = true;
+      }
       const uint32_t tbase = tmem_base + lane_base + (uint32_t)(acc * kAccCols);
       for (int c0 = 0; c0 < p.nout; c0 += 32) {
         float v[32];
@@ -459,36 +477,54 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           for (int j = 0; j < 32; ++j) v[j] += vl[j];
         }
         if (!valid) continue;
+        const int nv = min(32, p.n_valid - c0);  // columns of this chunk that are stored
+        if (p.epi == EP_PARTIAL) {
+          float *o = p.out + (((long long)split * 2 + u) * NN + r) * p.n_valid + c0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = c0 + j;
-          if (col >= p.n_valid) continue;
-          if (p.epi == EP_PARTIAL) {
-            p.out[(((long long)split * 2 + u) * NN + r) * p.n_valid + col] = v[j];
-            continue;
-          }
-          const int vv = col >= N ? 1 : 0;
-          const long long l = col - vv * N;
-          float x = v[j];
-          long long idx;
-          if (p.epi == EP_PI) {
-            const long long cg = grow + col;  // (j, l, v) interleaved
-            if (cg >= p.rows) continue;
+          for (int j = 0; j < 32; ++j)
+            if (j < nv) o[j] = v[j];
+        } else if (p.epi == EP_PI) {
+          // columns (j, l, v) interleaved from the even global column grow + c0: complex pairs
+          float2 *o = reinterpret_cast<float2 *>(p.out);
+          const long long cg0 = grow + c0;
+#pragma unroll
+          for (int j = 0; j < 32; j += 2) {
+            const long long cg = cg0 + j;
+            if (j >= nv || cg >= p.rows) break;
             const long long jl = cg >> 1;
             const long long jj = jl / NN, ll = jl - jj * NN;
-            p.out[(cg & 1) * p.out_plane + ((i0 * NN + jj) * NN + ll) * NN + i2] = x;
-            continue;
+            o[((i0 * NN + jj) * NN + ll) * NN + i2] = make_float2(v[j], v[j + 1]);
           }
-          if (p.epi == EP_SWAP34) {
-            idx = ((i0 * NN + i1) * NN + l) * NN + i2;
-          } else if (p.epi == EP_EXCH_T) {
-            idx = ((i1 * NN + i0) * NN + l) * NN + i2;
-          } else {
-            idx = ((i2 * NN + l) * NN + i0) * NN + i1;
-            if (vv) x = -x;
+        } else if (p.out_il) {
+          // col_il columns (2 l, 2 l + 1) -> one interleaved complex value
+          float2 *o = reinterpret_cast<float2 *>(p.out) + base;
+#pragma unroll
+          for (int j = 0; j < 32; j += 2) {
+            if (j >= nv) break;
+            const int l = (c0 + j) >> 1;
+            o[l * cs] = make_float2(v[j], v[j + 1]);
+            if (kSliced) mx = fmaxf(mx, fmaxf(fabsf(v[j]), fabsf(v[j + 1])));
           }
-          p.out[vv * p.out_plane + idx] = x;
-          if (kSliced) mx = fmaxf(mx, fabsf(x));
+        } else if (p.col_il) {
+          float *o = p.out + base;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (j >= nv) break;
+            const int col = c0 + j, vv = col & 1, l = col >> 1;
+            const float x = (neg_im && vv) ? -v[j] : v[j];
+            o[(long long)l * cs + (vv ? p.out_plane : 0)] = x;
+            if (kSliced) mx = fmaxf(mx, fabsf(x));
+          }
+        } else {
+          float *o = p.out + base;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (j >= nv) break;
+            const int col = c0 + j, vv = col >= N ? 1 : 0, l = col - (vv ? N : 0);
+            const float x = (neg_im && vv) ? -v[j] : v[j];
+            o[(long long)l * cs + (vv ? p.out_plane : 0)] = x;
+            if (kSliced) mx = fmaxf(mx, fabsf(x));
+          }
         }
       }
       tc_fence_before();

@@ -57,8 +57,10 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // B operand of "X x_4 S" for a complex (planar) X: rows (v, l), K' = (u, p):
 // (a_re, a_im) * S_pl as a real 2x2 block [[S_re, S_im], [-S_im, S_re]].
 // Real X: rows (v, l), K' = p: S_v[p][l].  hi = TF32(x), lo = TF32(x - hi).
+// Rows are ordered v nb + l, or 2 l + v with il (the real and imaginary part
+// of one output element then sit in adjacent accumulator columns).
 __global__ void realify_kernel(int nb, int nout, int kpad, int complex_a, int shift, double scale, int ld, int col0,
-                               int transpose, const cplx *__restrict__ S, float *hi, float *lo) {
+                               int transpose, int il, const cplx *__restrict__ S, float *hi, float *lo) {
   const int kt = complex_a ? 2 * kpad : kpad;
   const int total = nout * kt;
   // optional shift S -> S - mu 1 with mu = Re Tr S / nb (the commutator does not see it)
@@ -70,7 +72,7 @@ __global__ void realify_kernel(int nb, int nout, int kpad, int complex_a, int sh
     const int row = e / kt, col = e % kt;
     double x = 0.0;
     if (row < 2 * nb) {
-      const int v = row / nb, l = row % nb;
+      const int v = il ? (row & 1) : row / nb, l = il ? (row >> 1) : row % nb;
       const int u = complex_a ? col / kpad : 0;
       const int pp = complex_a ? col % kpad : col;
       if (pp < nb) {
@@ -124,10 +126,10 @@ __global__ void to_planar_f32_kernel(long long n, const cplx *__restrict__ x, fl
 }
 
 // value of the real B operand of realify_kernel at (row, col) (no scale)
-__device__ __forceinline__ double realified(int nb, int kpad, int complex_a, int transpose, double mu,
+__device__ __forceinline__ double realified(int nb, int kpad, int complex_a, int transpose, int il, double mu,
                                             const cplx *__restrict__ S, int row, int col) {
   if (row >= 2 * nb) return 0.0;
-  const int v = row / nb, l = row % nb;
+  const int v = il ? (row & 1) : row / nb, l = il ? (row >> 1) : row % nb;
   const int u = complex_a ? col / kpad : 0;
   const int pp = complex_a ? col % kpad : col;
   if (pp >= nb) return 0.0;
@@ -154,7 +156,7 @@ __device__ __forceinline__ void slice4_f64(double x, int E, int L, __nv_bfloat16
 // matrix holds +-Re and +-Im of the (shifted) entries of S, so every CTA takes
 // the maximum over the nb^2 entries of S itself and slices its share.
 __global__ void __launch_bounds__(256) slice_b_kernel(int nb, int nout, int kpad, int complex_a, int shift, int ld,
-                                                      int transpose, const cplx *__restrict__ S,
+                                                      int transpose, int il, const cplx *__restrict__ S,
                                                       __nv_bfloat16 *out, long long slice_stride) {
   __shared__ double red[8];
   __shared__ double smu;
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(256) slice_b_kernel(int nb, int nout, int kpad
   if (mx > 0.0) frexp(mx, &E);  // mx < 2^E
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int row = e / kt, col = e % kt;
-    slice4_f64(realified(nb, kpad, complex_a, transpose, mu, S, row, col), E, 7, out + (long long)row * ld + col,
+    slice4_f64(realified(nb, kpad, complex_a, transpose, il, mu, S, row, col), E, 7, out + (long long)row * ld + col,
                slice_stride);
   }
 }
@@ -308,10 +310,10 @@ __global__ void realify_pi_sliced_kernel(int nb, int kpad, const float *__restri
 struct AsmParams {
   int nb, nblk;
   const int4 *blocks;
-  const float *Z, *Q, *Pi;     // planar FP32 (plane stride P); Z, Q in the swapped layout
-  long long P;
+  const float *Z, *Q, *Pi;     // interleaved complex FP32, swapped layout
+  long long P;                 // plane stride of ys and y32
   cplx *y;                     // FP64 state (interleaved)
-  float *acc;                  // planar FP32
+  float *acc;                  // interleaved complex FP32
   float *ys;                   // planar FP32 stage input of the next stage
   float *y32;                  // planar FP32 copy of y (stage 3)
   cplx *kout;                  // write-k mode
@@ -332,10 +334,11 @@ __device__ __forceinline__ void elem(int e, int &a, int &b, int &c, int &d) {
   a = e >> 9; b = (e >> 6) & 7; c = (e >> 3) & 7; d = e & 7;
 }
 
-// Load the four member blocks of src into sm.  With swap34 the tensor is stored
-// with its last two indices exchanged (the GEMM epilogue layout), so block
-// (B0,B1,B2,B3) is read as the stored block (B0,B1,B3,B2); its element for the
-// natural index (a,b,c,d) then sits at bidx(a,b,d,c).
+// Load the four member blocks of src (interleaved complex FP32) into sm.  With
+// swap34 the tensor is stored with its last two indices exchanged (the GEMM
+// epilogue layout), so block (B0,B1,B2,B3) is read as the stored block
+// (B0,B1,B3,B2); its element for the natural index (a,b,c,d) then sits at
+// bidx(a,b,d,c).  A block row is 8 consecutive complex values (64 bytes).
 __device__ __forceinline__ void load_blocks(const AsmParams &p, const float *src, const int (&X)[4][4], float2 *sm,
                                             bool swap34) {
   const long long N = p.nb;
@@ -351,8 +354,7 @@ __device__ __forceinline__ void load_blocks(const AsmParams &p, const float *src
       v[m][t] = make_float2(0.f, 0.f);
       if (g0 < N && g1 < N && g2 < N && g3 < N) {
         const long long g = ((g0 * N + g1) * N + g2) * N + g3;
-        v[m][t].x = src[g];
-        v[m][t].y = src[p.P + g];
+        v[m][t] = reinterpret_cast<const float2 *>(src)[g];
       }
     }
   }
@@ -468,7 +470,7 @@ __global__ void __launch_bounds__(ATHREADS) orbit_assemble_kernel(const AsmParam
       k[t] = sm[m * BEL + sidx(a, b, c, d)];
       if (in[t] && p.stage >= 0) {
         y0[t] = yv[g[t]];
-        ac[t] = (p.stage > 0) ? make_float2(accv[g[t]], accv[P + g[t]]) : make_float2(0.f, 0.f);
+        ac[t] = (p.stage > 0) ? reinterpret_cast<const float2 *>(accv)[g[t]] : make_float2(0.f, 0.f);
       }
     }
 #pragma unroll
@@ -479,8 +481,7 @@ __global__ void __launch_bounds__(ATHREADS) orbit_assemble_kernel(const AsmParam
       } else if (p.stage < 3) {
         const double h = (p.stage == 2) ? dt : 0.5 * dt;
         const float w = (p.stage == 0) ? 1.f : 2.f;
-        accv[g[t]] = ac[t].x + w * k[t].x;
-        accv[P + g[t]] = ac[t].y + w * k[t].y;
+        reinterpret_cast<float2 *>(accv)[g[t]] = make_float2(ac[t].x + w * k[t].x, ac[t].y + w * k[t].y);
         const float sx = (float)(y0[t].x + h * k[t].x), sy = (float)(y0[t].y + h * k[t].y);
         ysv[g[t]] = sx;
         ysv[P + g[t]] = sy;
@@ -900,35 +901,35 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   one_minus(L, nb, n_in, t->nbar);
   if (sl) {
     const int kc = 2 * t->kpad;
-    struct { const cplx *S; int complex_a, shift, ld, transpose; __nv_bfloat16 *out; } ops[5] = {
-        {hhf, 1, 1, kc, 0, t->bh_s},
-        {n_in, 0, 0, t->kpad, 0, t->bnr_s},
-        {n_in, 1, 0, kc, 0, t->bnc_s},
-        {t->nbar, 1, 0, kc, 0, t->bnb_s},
-        {n_in, 0, 0, t->kpad, 1, t->bnt_s}};
+    struct { const cplx *S; int complex_a, shift, ld, transpose, il; __nv_bfloat16 *out; } ops[5] = {
+        {hhf, 1, 1, kc, 0, 1, t->bh_s},
+        {n_in, 0, 0, t->kpad, 0, 0, t->bnr_s},
+        {n_in, 1, 0, kc, 0, 0, t->bnc_s},
+        {t->nbar, 1, 0, kc, 0, 1, t->bnb_s},
+        {n_in, 0, 0, t->kpad, 1, 0, t->bnt_s}};
     const int nops = (t->se == G1G2_GW) ? 5 : 4;
     for (int q = 0; q < nops; ++q) {
       const auto &o = ops[q];
       L.before("tc_slice_b");
-      slice_b_kernel<<<32, 256, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.ld, o.transpose, o.S,
-                                               o.out, (long long)t->nout2 * o.ld);
+      slice_b_kernel<<<32, 256, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.ld, o.transpose, o.il,
+                                               o.S, o.out, (long long)t->nout2 * o.ld);
       L.after_launch();
     }
   }
   {
     const int kc = 2 * t->kpad;
-    struct { const cplx *S; int complex_a, shift; double scale; int ld, col0, transpose; float *hi, *lo; } ops[5] = {
-        {hhf, 1, 1, 1.0, kc, 0, 0, t->bh_hi, t->bh_lo},
-        {n_in, 0, 0, 1.0, t->kpad, 0, 0, t->bnr_hi, t->bnr_lo},
-        {n_in, 1, 0, 1.0, kc, 0, 0, t->bnc_hi, t->bnc_lo},
-        {t->nbar, 1, 0, 1.0, kc, 0, 0, t->bnb_hi, t->bnb_lo},
-        {n_in, 0, 0, 1.0, t->kpad, 0, 1, t->bnt_hi, t->bnt_lo}};
+    struct { const cplx *S; int complex_a, shift; double scale; int ld, col0, transpose, il; float *hi, *lo; } ops[5] = {
+        {hhf, 1, 1, 1.0, kc, 0, 0, 1, t->bh_hi, t->bh_lo},
+        {n_in, 0, 0, 1.0, t->kpad, 0, 0, 0, t->bnr_hi, t->bnr_lo},
+        {n_in, 1, 0, 1.0, kc, 0, 0, 0, t->bnc_hi, t->bnc_lo},
+        {t->nbar, 1, 0, 1.0, kc, 0, 0, 1, t->bnb_hi, t->bnb_lo},
+        {n_in, 0, 0, 1.0, t->kpad, 0, 1, 0, t->bnt_hi, t->bnt_lo}};
     const int nops = sl ? 0 : (t->se == G1G2_GW) ? 5 : 4;  // the sliced form slices these above
     for (int q = 0; q < nops; ++q) {
       const auto &o = ops[q];
       L.before("tc_realify");
       realify_kernel<<<64, 256, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.scale, o.ld, o.col0,
-                                               o.transpose, o.S, o.hi, o.lo);
+                                               o.transpose, o.il, o.S, o.hi, o.lo);
       L.after_launch();
     }
   }
@@ -975,13 +976,20 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     g.tiles = nb * g.g_na * g.g_nb;
     launch_gemm(t, L, "tc_gemm_psi2", t->mBuf1Gather, sl ? t->mBnc_s : t->mBnc_hi, t->mBnc_lo, g, sl);
   }
+  // B = nbar and B = hHF have interleaved rows (col_il); the passes feeding the
+  // assembly store interleaved complex FP32 (out_il)
+  auto il = [](GemmParams g, bool out_il) {
+    g.col_il = 1;
+    g.out_il = out_il ? 1 : 0;
+    return g;
+  };
   launch_gemm(t, L, "tc_gemm_psi3", t->mBuf2Lin, sl ? t->mBnb_s : t->mBnb_hi, t->mBnb_lo,
-              lp(N3, 2, EP_EXCH_T, t->buf1, kAmaxP2, kAmaxP3), sl);
+              il(lp(N3, 2, EP_EXCH_T, t->buf1, kAmaxP2, kAmaxP3), false), sl);
   // a3: Z = G2 x_4 (hHF - mu); last a4 pass: Q = T2~ x_4 nbar = A^dag (both in the swapped layout)
   launch_gemm(t, L, "tc_gemm_commutator", mZin, sl ? t->mBh_s : t->mBh_hi, t->mBh_lo,
-              lp(N3, 2, EP_SWAP34, t->Z, -1, -1), sl);
+              il(lp(N3, 2, EP_SWAP34, t->Z, -1, -1), true), sl);
   launch_gemm(t, L, "tc_gemm_psi4", t->mBuf1Lin, sl ? t->mBnb_s : t->mBnb_hi, t->mBnb_lo,
-              lp(N3, 2, EP_SWAP34, t->buf2, kAmaxP3, -1), sl);
+              il(lp(N3, 2, EP_SWAP34, t->buf2, kAmaxP3, -1), true), sl);
   if (t->se == G1G2_GW) {
     // a5: Y1 = w x_4 n, Y2 = w x_4 n^T (hcorr_ijkl = Y1_ijkl - Y2_klij), swapped layout
     if (sl) cudaMemsetAsync(amax + kAmaxH1, 0, 2 * sizeof(int), L.stream);
