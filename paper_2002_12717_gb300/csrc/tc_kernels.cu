@@ -49,6 +49,7 @@ using namespace tc;
 namespace {
 
 constexpr int BSZ = 8;                      // assembly block edge
+constexpr int kPiNoutSliced = 128;          // polarisation N tile of the sliced form (3 accumulators in TMEM)
 constexpr int BEL = BSZ * BSZ * BSZ * BSZ;  // elements per block
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -713,7 +714,7 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
   if (se == G1G2_GW) {
     const long long ncol = 2 * N * N;  // output columns (j, l, v)
     // the sliced form keeps three accumulators of nout columns in TMEM (512 columns)
-    t->pi_nout = (int)std::min<long long>(sliced ? 128 : 256, ((ncol + 15) / 16) * 16);
+    t->pi_nout = (int)std::min<long long>(sliced ? kPiNoutSliced : 256, ((ncol + 15) / 16) * 16);
     t->pi_ntiles = (int)((ncol + t->pi_nout - 1) / t->pi_nout);
     t->pi_mtiles = ((nb + 3) / 4) * ((nb + 31) / 32);
     t->pi_ldb = 2 * N * t->kpad;
