@@ -94,6 +94,10 @@ struct GemmParams {
   int *err;
   const int *a_amax;  // sliced form: FP32 bit pattern of max |A| (the A slice scale)
   int slice_lead;     // sliced form: leading-slice width L (slice_lead_for(K)); 0 means 7
+  int cluster2;       // sliced form, launched as CTA pairs whose tiles share the B column tile
+                      // (tile 2p and 2p+1): each CTA multicasts half of every B slice to both
+                      // (tmBhi then has a box of nout/2 rows x one slice), and a stage is free
+                      // once both CTAs' MMAs are done with it
   int col_il;         // B rows (output columns) ordered 2 l + v instead of v nb + l
   int out_il;         // EP_SWAP34 with col_il: interleaved complex FP32 output out[i][j][l][k]
   int acc3;           // sliced form: order-1 products in their own exact accumulator (nout <= 128,
@@ -142,11 +146,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   float2 *acc2 = reinterpret_cast<float2 *>(smem + (size_t)stages * stage_bytes + 256);  // (sum, error) pairs
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool pair = kSliced && p.cluster2;
+  const uint32_t crank = pair ? cluster_ctarank() : 0u;
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&conv[s], kConvThreads);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], pair ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -157,6 +163,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   }
   if (warp == 1) tmem_alloc(tmem_slot, 2 * kAccCols);
   __syncthreads();
+  if (pair) cluster_sync();  // the partner's barriers exist before anything is multicast to them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const int N = p.nb;
@@ -199,12 +206,27 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             bk = kglob;
           }
           const int brow = (p.a_rows == AR_PI) ? (tile / p.pi_mtiles) * p.nout : 0;
-          if (kSliced) {
+          if (pair) {
+            // this CTA's half of the rows of each slice, to both CTAs of the pair
+            const int half = p.nout / 2;
+#pragma unroll
+            for (int q = 0; q < kSlices; ++q)
+              tma_load_3d_mc(st + kSlicedBOff + q * b_bytes + crank * (b_bytes / 2), &tmBhi, &full[s], bk,
+                             brow + (int)crank * half, q, (uint16_t)0x3);
+          } else if (kSliced) {
             tma_load_3d(st + kSlicedBOff, &tmBhi, &full[s], bk, brow, 0);  // all four slices
           } else {
             tma_load_3d(st + 2 * kABytes, &tmBhi, &full[s], bk, brow, 0);
             tma_load_3d(st + 2 * kABytes + b_bytes, &tmBlo, &full[s], bk, brow, 0);
           }
+          if (++s == stages) { s = 0; ph ^= 1u; }
+        }
+      }
+      if (pair) {
+        // the partner's last MMA commits arrive on this CTA's empty barriers: wait for the
+        // final use of every stage before the pair may leave
+        for (int i = 0; i < stages; ++i) {
+          mbar_wait(&empty[s], ph ^ 1u, p.err);
           if (++s == stages) { s = 0; ph ^= 1u; }
         }
       }
@@ -268,7 +290,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
               mma_tf32(d_tmem, ah, bl, idesc, 1u);
             }
           }
-          mma_commit(&empty[s]);
+          if (pair)
+            mma_commit_mc(&empty[s], (uint16_t)0x3);  // both producers write into this stage
+          else
+            mma_commit(&empty[s]);
           if (++s == stages) { s = 0; ph ^= 1u; }
           if (chunk_end) {
             mma_commit(&tfull[acc]);
@@ -292,12 +317,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     uint32_t ph = 0;
     bool ok = true;
     // sliced form: rounding constants c_q = 1.5 2^(23+E-L-8q) of the four cuts
-    float cut[kSlices] = {0.f, 0.f, 0.f, 0.f};
+    uint64_t cut2[kSlices] = {0, 0, 0, 0};
     if (kSliced) {
       const int E = slice_exponent(p.a_amax ? *p.a_amax : 0);
       const int Ld = p.slice_lead ? p.slice_lead : 7;
 #pragma unroll
-      for (int q = 0; q < kSlices; ++q) cut[q] = ldexpf(1.5f, 23 + E - Ld - 8 * q);
+      for (int q = 0; q < kSlices; ++q) cut2[q] = splat_f32x2(ldexpf(1.5f, 23 + E - Ld - 8 * q));
     }
     for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
       const int nkb = tile_kblocks(p, tile);
@@ -311,18 +336,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             // 16-byte chunk i of the 128-byte-swizzled FP32 tile: row r, logical floats k0..k0+3
             const int r = i >> 3, k0 = ((i & 7) ^ (r & 7)) << 2;
             const float4 x = a[i];
-            float q0[kSlices], q1[kSlices], q2[kSlices], q3[kSlices];
-            slice4(x.x, q0, cut);
-            slice4(x.y, q1, cut);
-            slice4(x.z, q2, cut);
-            slice4(x.w, q3, cut);
+            float2 lo2[kSlices], hi2[kSlices];
+            slice4x2(make_float2(x.x, x.y), lo2, cut2);
+            slice4x2(make_float2(x.z, x.w), hi2, cut2);
             // the same four elements in the 64-byte-swizzled BF16 slice tile
             const uint32_t off = (uint32_t)r * 64u + ((uint32_t)((k0 >> 3) ^ ((r >> 1) & 3)) << 4) + (uint32_t)(k0 & 7) * 2u;
 #pragma unroll
             for (int q = 0; q < kSlices; ++q) {
               uint2 v;
-              v.x = pack_bf16(q0[q], q1[q]);
-              v.y = pack_bf16(q2[q], q3[q]);
+              v.x = pack_bf16(lo2[q].x, lo2[q].y);
+              v.y = pack_bf16(hi2[q].x, hi2[q].y);
               *reinterpret_cast<uint2 *>(sl + q * kASliceBytes + off) = v;
             }
           }
@@ -543,6 +566,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     tc_fence_after();
     tmem_dealloc(tmem_base, 2 * kAccCols);
   }
+  // neither CTA of a pair leaves while the other may still multicast into it
+  // or arrive on its barriers
+  if (pair) cluster_sync();
 }
 
 }  // namespace tc

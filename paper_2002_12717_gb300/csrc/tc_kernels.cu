@@ -550,11 +550,11 @@ int map_b(CUtensorMap *m, const float *base, int kt, int rows, int box_rows) {
   cuuint32_t box[3] = {(cuuint32_t)kBlockK, (cuuint32_t)box_rows, 1};
   return encode_map(m, base, 3, dims, str, box);
 }
-// B as four BF16 slices [q][rows][kt]; one box carries all four
-int map_bs(CUtensorMap *m, const __nv_bfloat16 *base, long long kt, int rows, int box_rows) {
+// B as four BF16 slices [q][rows][kt]; one box carries all four (box_slices = 4) or one
+int map_bs(CUtensorMap *m, const __nv_bfloat16 *base, long long kt, int rows, int box_rows, int box_slices = kSlices) {
   cuuint64_t dims[3] = {(cuuint64_t)kt, (cuuint64_t)rows, (cuuint64_t)kSlices};
   cuuint64_t str[2] = {(cuuint64_t)kt * 2, (cuuint64_t)kt * 2 * rows};
-  cuuint32_t box[3] = {(cuuint32_t)kBlockK, (cuuint32_t)box_rows, (cuuint32_t)kSlices};
+  cuuint32_t box[3] = {(cuuint32_t)kBlockK, (cuuint32_t)box_rows, (cuuint32_t)box_slices};
   return encode_map(m, base, 3, dims, str, box, true);
 }
 
@@ -591,7 +591,8 @@ struct TcPath {
                 *w_s = nullptr, *bpi_s = nullptr;
   int *amax = nullptr;  // slots: see kAmax*
   int pi_lead = 7;      // leading-slice width of the polarisation GEMM (K = 2 nb kpad)
-  CUtensorMap mBh_s, mBnr_s, mBnc_s, mBnb_s, mBnt_s, mW_s, mBpi_s;
+  CUtensorMap mBh_s, mBnr_s, mBnc_s, mBnb_s, mBnt_s, mW_s, mBpi_s, mBpi_s_half;
+  bool pi_pair = false;  // polarisation GEMM launched as CTA pairs sharing B (TMA multicast)
   // tensor maps
   CUtensorMap mZin_y32, mZin_ys32, mCol_y32, mCol_ys32, mW32, mBuf1Gather, mBuf2Lin, mBuf1Lin;
   CUtensorMap mBh_hi, mBh_lo, mBnr_hi, mBnr_lo, mBnc_hi, mBnc_lo, mBnb_hi, mBnb_lo, mW_hi, mW_lo;
@@ -635,12 +636,29 @@ void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, 
   int stages = 0;
   const size_t acc64 = gp.kb_chunks ? (size_t)gp.nb * (gp.n_valid + 1) * sizeof(float2) : 0;
   const size_t smem = gemm_smem(sliced, gp.nout, &stages, acc64);
-  const int grid = std::max(1, std::min(gp.tiles, t->sms));
+  int grid = std::max(1, std::min(gp.tiles, t->sms));
   L.before(tag);
-  if (sliced)
+  if (sliced && gp.cluster2) {
+    // CTA pairs (cluster of 2): even grid, even tile count (the caller checks the latter)
+    grid = std::max(2, grid & ~1);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kGemmThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, tc_gemm_kernel<true>, A, A2 ? *A2 : A, Bh, Bl, gp, stages);
+  } else if (sliced) {
     tc_gemm_kernel<true><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
-  else
+  } else {
     tc_gemm_kernel<false><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
+  }
   L.after_launch();
 }
 
@@ -728,6 +746,8 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
       return bail(G1G2_ECUDA);
     if (sliced) {
       t->pi_lead = slice_lead_order1(2LL * N * t->kpad);
+      // pairs need an even number of row tiles per column tile (both tiles of a pair share it)
+      t->pi_pair = (t->pi_mtiles % 2 == 0) && (t->pi_nout % 32 == 0);
       if ((rc = talloc(t, &t->bpi_s, (size_t)kSlices * brows * t->pi_ldb))) return bail(rc);
       if (cudaMemset(t->bpi_s, 0, (size_t)kSlices * brows * t->pi_ldb * sizeof(__nv_bfloat16)) != cudaSuccess)
         return bail(G1G2_ECUDA);
@@ -821,7 +841,9 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
                   (rc = map_bs(&t->mBnt_s, t->bnt_s, kt_r, t->nout2, t->nout2)) ||
                   (rc = map_bs(&t->mW_s, t->w_s, N3, nb, t->nout1)) ||
                   (se == G1G2_GW &&
-                   (rc = map_bs(&t->mBpi_s, t->bpi_s, t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)))))) {
+                   ((rc = map_bs(&t->mBpi_s, t->bpi_s, t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
+                    (rc = map_bs(&t->mBpi_s_half, t->bpi_s, t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout / 2,
+                                 1))))))) {
     set_error_detail("cuTensorMapEncodeTiled failed");
     return bail(rc);
   }
@@ -1028,8 +1050,9 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     g.a_amax = g2_amax;
     g.slice_lead = t->pi_lead;
     g.acc3 = 1;
-    launch_gemm(t, L, "tc_gemm_pi", from_y ? t->mPi_y32 : t->mPi_ys32, sl ? t->mBpi_s : t->mBpi_hi, t->mBpi_lo, g,
-                sl);
+    g.cluster2 = (sl && t->pi_pair) ? 1 : 0;
+    launch_gemm(t, L, "tc_gemm_pi", from_y ? t->mPi_y32 : t->mPi_ys32,
+                sl ? (g.cluster2 ? t->mBpi_s_half : t->mBpi_s) : t->mBpi_hi, t->mBpi_lo, g, sl);
   }
   // a7: orbit assembly + RK4
   AsmParams a{};

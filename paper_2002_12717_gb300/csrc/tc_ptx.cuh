@@ -79,6 +79,25 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
       : "memory");
 }
+// The same load delivered to every CTA of the cluster in cta_mask, at the same
+// shared-memory offsets, signalling each destination CTA's barrier at bar's offset.
+__device__ __forceinline__ void tma_load_3d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z,
+                                               uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "h"(cta_mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// every thread of every CTA of the cluster
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -161,6 +180,14 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// arrive on the barrier at bar's offset in every CTA of cta_mask once the issued MMAs complete
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(cta_mask)
+      : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -217,6 +244,26 @@ __device__ __forceinline__ void slice4(float x, float (&v)[4], const float (&c)[
     v[s] = __fsub_rn(__fadd_rn(r, c[s]), c[s]);
     r = __fsub_rn(r, v[s]);
   }
+}
+
+// slice4 on two values at once with packed FP32x2 adds (round to nearest per lane,
+// the same results as slice4 on each).  c2[s] holds c_s in both halves.
+__device__ __forceinline__ void slice4x2(float2 x, float2 (&v)[4], const uint64_t (&c2)[4]) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x.x), "f"(x.y));
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    uint64_t t, vs;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(r), "l"(c2[s]));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(vs) : "l"(t), "l"(c2[s]));
+    if (s < 3) asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(r), "l"(vs));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v[s].x), "=f"(v[s].y) : "l"(vs));
+  }
+}
+__device__ __forceinline__ uint64_t splat_f32x2(float c) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(c));
+  return r;
 }
 
 // two FP32 values -> packed BF16 pair (lo in the low half), round to nearest
