@@ -160,6 +160,22 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(values_ms, dist):
+    """Per-entry maximum over the ranks of per-rank times (the slowest replica sets the job's rate)."""
+    if dist is None:
+        return [float(v) for v in values_ms]
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values_ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_rate(world, ms_per_step):
+    """Whole-job steps/s of `world` independent replicas that each take at most ms_per_step per step."""
+    return world * 1e3 / ms_per_step
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -252,14 +268,10 @@ def run_ours(args, rank, world, dist):
         barrier()
     clk = clocks.stop()
 
-    step_ms = sum(p["ms_per_step"] for p in per.values())
-    if dist is not None:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = world * 1e3 / step_ms
-    e2e_ms = sum(p["e2e_ms_per_step"] for p in per.values())
-    e2e_value = world * 1e3 / e2e_ms
+    step_ms, e2e_ms = max_over_ranks([sum(p["ms_per_step"] for p in per.values()),
+                                      sum(p["e2e_ms_per_step"] for p in per.values())], dist)
+    value = job_rate(world, step_ms)
+    e2e_value = job_rate(world, e2e_ms)
 
     # roofline of the dominant kernel: the (kernel, workload) pair with the largest device time
     total_ms = sum(v[1] for v in prof_all.values())
