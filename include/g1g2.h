@@ -155,9 +155,9 @@ int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_de
  * Not in the paper; the reverse sweep is the exact transpose of the discrete
  * RK4 map, with the state (n, G2) checkpointed every ckpt_every steps and
  * each segment recomputed once.  ckpt_every <= 0 chooses the interval from
- * the free device memory: the smallest k whose ceil(nsteps/k) + 1 checkpoints
- * and k + 1 segment states fit in 80% of it (k = 1, no recomputation, when
- * all steps fit), at most ceil(sqrt(nsteps)) (the memory minimum).
+ * the free memory: the smallest k whose ceil(nsteps/k) + 1 checkpoints and
+ * k + 1 segment states fit (k = 1, no recomputation, when all steps fit; see
+ * g1g2_set_adjoint_checkpoints for device or pinned host checkpoints).
  *   objective   0: mean double occupancy (1/L) sum_i d_i (E10; spin-orbital
  *                  basis, index 2*site+spin); 1: density imbalance
  *                  sum_i (-1)^site n_ii (x2 spin-restricted); 2: energy absorbed
@@ -173,6 +173,29 @@ int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_de
  * G1G2_EUNSUPPORTED for the tensor-core precision or GW. */
 int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objective, double *J_out,
                  double *grad_drive, double *grad_wscale, double *grad_h);
+
+/* Where g1g2_adjoint keeps its checkpoints: G1G2_CKPT_AUTO (device memory when
+ * the checkpoints and one segment fit in 80% of the free device memory, else
+ * pinned host memory, at most half of the free host memory, with only the
+ * segment on the device), G1G2_CKPT_DEVICE or G1G2_CKPT_HOST.  The choice of
+ * the interval (ckpt_every <= 0) follows the location: the smallest interval
+ * that fits.  Results do not depend on it.  G1G2_EINVAL on another value.
+ * Not in the paper. */
+enum { G1G2_CKPT_AUTO = 0, G1G2_CKPT_DEVICE = 1, G1G2_CKPT_HOST = 2 };
+int g1g2_set_adjoint_checkpoints(g1g2_ctx *c, int where);
+
+/* Interval and location (G1G2_CKPT_DEVICE / G1G2_CKPT_HOST) the last
+ * g1g2_adjoint call used (0, 0 before the first). */
+int g1g2_adjoint_plan(const g1g2_ctx *c, int *ckpt_every, int *where);
+
+/* Failure-detection self-test (not in the paper): launches one CTA that waits
+ * on a barrier nothing arrives on, with the bounded wait the tensor-core
+ * kernels use but a limit of limit_us microseconds (1 .. 1e7).  Expected
+ * result: G1G2_ETIMEOUT (the wait gave up, reported through the error word,
+ * and the kernel returned; the CUDA context stays usable).  G1G2_EINVAL on a
+ * bad limit, G1G2_ECUDA on a launch failure.  Runs on the legacy default
+ * stream of the current device. */
+int g1g2_wait_selftest(int limit_us);
 
 /* Copy the state to / from host memory (G2 may be NULL on get; NULL on set means 0). */
 int g1g2_get_state(g1g2_ctx *c, double *t, double *G1, double *G2);

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <unistd.h>
 
 using namespace g1g2;
 
@@ -66,6 +67,8 @@ struct g1g2_ctx {
   cplx *adj_hsum = nullptr;                     // accumulated cotangent of h
   cplx *adj_hbar = nullptr;                     // cotangent of hHF of one stage
   std::vector<void *> adj_allocs;
+  int adj_where = G1G2_CKPT_AUTO;               // where the adjoint keeps its checkpoints
+  int adj_last_k = 0, adj_last_where = 0;       // plan of the last g1g2_adjoint call
 
   Launcher launcher() {
     Launcher L;
@@ -881,25 +884,64 @@ int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_de
   return launch_status(L, "rhs vjp");
 }
 
-// Checkpoint interval from the free device memory.  Every step is recomputed
-// at most once whatever the interval, so the interval only trades memory
-// ((ceil(nsteps/k) + 1) checkpoints + (k + 1) segment states) against the
-// recomputation ((k - 1)/k of a forward sweep): take the smallest k whose
-// states fit in 80% of the free memory (k = 1, no recomputation, when all
-// fit), never beyond the memory minimum k ~ sqrt(nsteps).
-static int adjoint_interval(int nsteps, size_t state_bytes) {
+// Checkpoint plan.  Every step is recomputed at most once whatever the
+// interval k, so k only trades memory ((ceil(M/k) + 1) checkpoints and k + 1
+// segment states) against recomputation ((k - 1)/k of a forward sweep).
+// Device plan: the smallest k whose states fit in 80% of the free device
+// memory (k = 1, no recomputation, when all fit), at most ceil(sqrt(M)) (the
+// memory minimum).  Host plan (requested, or when no device plan fits): the
+// checkpoints go to pinned host memory (at most half of the free host memory)
+// and only the segment stays on the device; the smallest k that fits both.
+struct AdjPlan {
+  int k, where;
+};
+static AdjPlan adjoint_plan(int nsteps, size_t SB, int ckpt_every, int where_req) {
+  const double sb = (double)SB;
+  auto ckpt_bytes = [&](int k) { return (double)((nsteps + k - 1) / k + 1) * sb; };
+  auto seg_bytes = [&](int k) { return (double)(k + 1) * sb; };
   size_t free_b = 0, total_b = 0;
-  const int kmin_mem = std::max(1, (int)std::ceil(std::sqrt((double)nsteps)));
-  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-    cudaGetLastError();
-    return kmin_mem;
+  double dev = 0.0;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) dev = 0.8 * (double)free_b - 8.0 * sb;  // minus stage buffers
+  else cudaGetLastError();
+  const long pages = sysconf(_SC_AVPHYS_PAGES), psz = sysconf(_SC_PAGESIZE);
+  const double host = (pages > 0 && psz > 0) ? 0.5 * (double)pages * (double)psz : 0.0;
+  const int kmem = std::max(1, (int)std::ceil(std::sqrt((double)nsteps)));
+  if (ckpt_every > 0) {
+    const int k = std::min(ckpt_every, nsteps);
+    int where = where_req;
+    if (where == G1G2_CKPT_AUTO) where = (ckpt_bytes(k) + seg_bytes(k) <= dev) ? G1G2_CKPT_DEVICE : G1G2_CKPT_HOST;
+    return {k, where};
   }
-  const double budget = 0.8 * (double)free_b - 8.0 * (double)state_bytes;  // minus the stage buffers
-  for (int k = 1; k < kmin_mem; ++k) {
-    const double states = (double)((nsteps + k - 1) / k + 1) + (double)(k + 1);
-    if (states * (double)state_bytes <= budget) return k;
+  if (where_req != G1G2_CKPT_HOST) {
+    for (int k = 1; k <= kmem; ++k)
+      if (ckpt_bytes(k) + seg_bytes(k) <= dev) return {k, G1G2_CKPT_DEVICE};
+    if (where_req == G1G2_CKPT_DEVICE) return {kmem, G1G2_CKPT_DEVICE};
   }
-  return kmin_mem;
+  for (int k = 1; k <= nsteps; ++k) {
+    if (seg_bytes(k) > dev && k > 1) break;
+    if (ckpt_bytes(k) <= host) return {k, G1G2_CKPT_HOST};
+  }
+  return {kmem, G1G2_CKPT_HOST};
+}
+
+int g1g2_wait_selftest(int limit_us) {
+  if (limit_us < 1 || limit_us > 10000000) return fail(G1G2_EINVAL, "limit must be 1 us .. 10 s");
+  return tc_wait_selftest(1000ull * (unsigned long long)limit_us, nullptr);
+}
+
+int g1g2_set_adjoint_checkpoints(g1g2_ctx *c, int where) {
+  if (!c) return fail(G1G2_EINVAL, "ctx is NULL");
+  if (where != G1G2_CKPT_AUTO && where != G1G2_CKPT_DEVICE && where != G1G2_CKPT_HOST)
+    return fail(G1G2_EINVAL, "checkpoint location must be AUTO, DEVICE or HOST");
+  c->adj_where = where;
+  return G1G2_OK;
+}
+
+int g1g2_adjoint_plan(const g1g2_ctx *c, int *ckpt_every, int *where) {
+  if (!c || !ckpt_every || !where) return fail(G1G2_EINVAL, "NULL argument");
+  *ckpt_every = c->adj_last_k;
+  *where = c->adj_last_where;
+  return G1G2_OK;
 }
 
 int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objective, double *J_out,
@@ -913,15 +955,22 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
   const int nb = c->nb;
   const long long N = nb, N2 = N * N, N4 = N2 * N2;
   const size_t SB = (N2 + N4) * sizeof(cplx);  // one stored state (n, G2)
-  const int k = ckpt_every > 0 ? std::min(ckpt_every, nsteps) : adjoint_interval(nsteps, SB);
+  const AdjPlan plan = adjoint_plan(nsteps, SB, ckpt_every, c->adj_where);
+  const int k = plan.k;
+  const bool host_ckpt = plan.where == G1G2_CKPT_HOST;
+  c->adj_last_k = k;
+  c->adj_last_where = plan.where;
   const int nseg = (nsteps + k - 1) / k;
   const bool restricted = c->basis == G1G2_SPIN_RESTRICTED;
   const double sfac = restricted ? 2.0 : 1.0;
   int rc;
   Launcher L = c->launcher();
   std::vector<void *> own;  // per-call memory
+  void *host_ckpt_mem = nullptr;
   auto done = [&](int code) {
+    cudaStreamSynchronize(c->stream);  // no copy may still read or write the checkpoints
     for (void *q : own) cudaFree(q);
+    if (host_ckpt_mem) cudaFreeHost(host_ckpt_mem);
     return code;
   };
   // persistent adjoint scratch
@@ -960,7 +1009,17 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
   auto state_n = [&](void *base) { return (cplx *)base; };
   auto state_G = [&](void *base) { return (cplx *)base + N2; };
   void *ckpt, *seg, *Y2, *Y3, *Y4, *lam, *lam2, *kbar, *Ybar, *kk, *acc;
-  if ((rc = adj_alloc(c, own, &ckpt, SB * (nseg + 1))) || (rc = adj_alloc(c, own, &seg, SB * (k + 1))) ||
+  if (host_ckpt) {
+    if (cudaHostAlloc(&host_ckpt_mem, SB * (nseg + 1), cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return done(fail(G1G2_ENOMEM, "adjoint: pinned host memory for " + std::to_string(nseg + 1) +
+                                        " checkpoints failed"));
+    }
+    ckpt = host_ckpt_mem;
+  } else if ((rc = adj_alloc(c, own, &ckpt, SB * (nseg + 1)))) {
+    return done(rc);
+  }
+  if ((rc = adj_alloc(c, own, &seg, SB * (k + 1))) ||
       (rc = adj_alloc(c, own, &Y2, SB)) || (rc = adj_alloc(c, own, &Y3, SB)) || (rc = adj_alloc(c, own, &Y4, SB)) ||
       (rc = adj_alloc(c, own, &lam, SB)) || (rc = adj_alloc(c, own, &lam2, SB)) ||
       (rc = adj_alloc(c, own, &kbar, SB)) || (rc = adj_alloc(c, own, &Ybar, SB)) || (rc = adj_alloc(c, own, &kk, SB)) ||
@@ -969,9 +1028,10 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
   double *dacc = (double *)acc;
   cudaMemsetAsync(dacc, 0, sizeof(double) * (1 + 4 * (size_t)nsteps), c->stream);
   cudaMemsetAsync(c->adj_hsum, 0, N2 * sizeof(cplx), c->stream);
+  // checkpoints may live in pinned host memory: copies use the unified address space
   auto copy_state = [&](void *dst, const cplx *n, const cplx *G) {
-    cudaMemcpyAsync(state_n(dst), n, N2 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
-    cudaMemcpyAsync(state_G(dst), G, N4 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(state_n(dst), n, N2 * sizeof(cplx), cudaMemcpyDefault, c->stream);
+    cudaMemcpyAsync(state_G(dst), G, N4 * sizeof(cplx), cudaMemcpyDefault, c->stream);
   };
   auto at = [&](void *base, long long i) { return (void *)((char *)base + SB * i); };
   // ---- forward sweep with checkpoints (the state at step m*k is kept)
@@ -1049,8 +1109,8 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
   for (int sgi = nseg - 1; sgi >= 0; --sgi) {
     const int m0 = sgi * k, m1 = std::min(nsteps, m0 + k);
     // recompute the segment's step states
-    cudaMemcpyAsync(c->n, state_n(at(ckpt, sgi)), N2 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
-    cudaMemcpyAsync(c->G, state_G(at(ckpt, sgi)), N4 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->n, state_n(at(ckpt, sgi)), N2 * sizeof(cplx), cudaMemcpyDefault, c->stream);
+    cudaMemcpyAsync(c->G, state_G(at(ckpt, sgi)), N4 * sizeof(cplx), cudaMemcpyDefault, c->stream);
     c->t = t0 + m0 * dt;
     copy_state(at(seg, 0), c->n, c->G);
     for (int m = m0; m < m1 - 1; ++m) {
@@ -1106,8 +1166,8 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
     if ((rc = launch_status(L, "adjoint"))) return done(rc);
   }
   // restore the final state
-  cudaMemcpyAsync(c->n, state_n(at(ckpt, nseg)), N2 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
-  cudaMemcpyAsync(c->G, state_G(at(ckpt, nseg)), N4 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(c->n, state_n(at(ckpt, nseg)), N2 * sizeof(cplx), cudaMemcpyDefault, c->stream);
+  cudaMemcpyAsync(c->G, state_G(at(ckpt, nseg)), N4 * sizeof(cplx), cudaMemcpyDefault, c->stream);
   c->t = tM;
   std::vector<double> hacc(1 + 4 * (size_t)nsteps);
   cudaMemcpyAsync(hacc.data(), dacc, hacc.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -1121,7 +1181,7 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
     std::vector<cplx> hn0(N2);
     if (objective == 2) {
       // E(T) - E(0) depends on h directly: s (n(T) - n(0))
-      cudaMemcpyAsync(hn0.data(), state_n(at(ckpt, 0)), N2 * sizeof(cplx), cudaMemcpyDeviceToHost, c->stream);
+      cudaMemcpyAsync(hn0.data(), state_n(at(ckpt, 0)), N2 * sizeof(cplx), cudaMemcpyDefault, c->stream);
       cudaMemcpyAsync(hn.data(), c->n, N2 * sizeof(cplx), cudaMemcpyDeviceToHost, c->stream);
       cudaStreamSynchronize(c->stream);
     }
@@ -1179,7 +1239,7 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
       cudaMemcpyAsync(r, c->red, sizeof(r), cudaMemcpyDeviceToHost, c->stream);
       cudaStreamSynchronize(c->stream);
       add_df(tM, sfac * r[3]);
-      cudaMemcpyAsync(c->adj_hsum, state_n(at(ckpt, 0)), N2 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
+      cudaMemcpyAsync(c->adj_hsum, state_n(at(ckpt, 0)), N2 * sizeof(cplx), cudaMemcpyDefault, c->stream);
       obs_one_body(L2, nb, c->h, c->D, drive_f(c, t0), c->hhf, c->adj_hsum, c->red);
       cudaMemcpyAsync(r, c->red, sizeof(r), cudaMemcpyDeviceToHost, c->stream);
       cudaStreamSynchronize(c->stream);

@@ -140,15 +140,20 @@ __device__ __forceinline__ double realified(int nb, int kpad, int complex_a, int
   return v ? s.x : -s.y;
 }
 
-// Four BF16 slices of x (|x| < 2^E): slice q = q_q 2^(E-L-8q), integer |q_0| <= 2^L, |q_q| <= 128.
-__device__ __forceinline__ void slice4_f64(double x, int E, int L, __nv_bfloat16 *out, long long stride) {
-  double r = ldexp(x, -E);
+// Four BF16 slices of x (|x| < 2^E), cut in FP64 as slice4 does in FP32: slice q
+// is x's remainder rounded to nearest-even on the grid 2^(E-L-8q) (add and
+// subtract of c[q] = 1.5 2^(52+E-L-8q)), at most 8 significant bits, exact in BF16.
+__device__ __forceinline__ void slice_cuts_f64(int E, int L, double (&c)[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) c[q] = ldexp(1.5, 52 + E - L - 8 * q);
+}
+__device__ __forceinline__ void slice4_f64(double x, const double (&c)[4], __nv_bfloat16 *out, long long stride) {
+  double r = x;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const double sh = ldexp(1.0, L + 8 * q);
-    const double qq = rint(r * sh);
-    r -= qq / sh;
-    out[q * stride] = __float2bfloat16_rn((float)ldexp(qq, E - L - 8 * q));
+    const double v = __dsub_rn(__dadd_rn(r, c[q]), c[q]);
+    r = __dsub_rn(r, v);
+    out[q * stride] = __float2bfloat16_rn((float)v);
   }
 }
 
@@ -185,30 +190,45 @@ __global__ void __launch_bounds__(256) slice_b_kernel(int nb, int nout, int kpad
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
   int E = 0;
   if (mx > 0.0) frexp(mx, &E);  // mx < 2^E
+  double c[4];
+  slice_cuts_f64(E, 7, c);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int row = e / kt, col = e % kt;
-    slice4_f64(realified(nb, kpad, complex_a, transpose, il, mu, S, row, col), E, 7, out + (long long)row * ld + col,
+    slice4_f64(realified(nb, kpad, complex_a, transpose, il, mu, S, row, col), c, out + (long long)row * ld + col,
                slice_stride);
   }
 }
 
 // real part of w -> four BF16 slices [q][i][c] with the common exponent E
 __global__ void slice_w_kernel(long long n, const cplx *__restrict__ w, int E, __nv_bfloat16 *out) {
+  double c[4];
+  slice_cuts_f64(E, 7, c);
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    slice4_f64(w[e].x, E, 7, out + e, n);
+    slice4_f64(w[e].x, c, out + e, n);
 }
 
-// I_ij = -D1[j][i] - i D0[j][i], summed over the K splits in FP64.
-__global__ void collision_reduce_kernel(int nb, int splits, const double *__restrict__ partial, cplx *I) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nb * nb) return;
-  const int i = e / nb, j = e % nb;
+// I_ij = -D1[j][i] - i D0[j][i], summed over the K splits in FP64.  Block (32, 8):
+// x runs over 32 consecutive (j, i) of the partial layout, y over the splits.
+__global__ void __launch_bounds__(256) collision_reduce_kernel(int nb, int splits, const double *__restrict__ partial,
+                                                              cplx *I) {
+  __shared__ double2 red[8][33];
+  const int e = blockIdx.x * 32 + threadIdx.x;  // j nb + i
+  const long long plane = (long long)nb * nb;
   double d0 = 0.0, d1 = 0.0;
-  for (int s = 0; s < splits; ++s) {
-    d0 += partial[(((long long)s * 2 + 0) * nb + j) * nb + i];
-    d1 += partial[(((long long)s * 2 + 1) * nb + j) * nb + i];
+  if (e < nb * nb)
+    for (int s = threadIdx.y; s < splits; s += 8) {
+      d0 += partial[(long long)s * 2 * plane + e];
+      d1 += partial[((long long)s * 2 + 1) * plane + e];
+    }
+  red[threadIdx.y][threadIdx.x] = make_double2(d0, d1);
+  __syncthreads();
+  if (threadIdx.y != 0 || e >= nb * nb) return;
+  for (int y = 1; y < 8; ++y) {
+    d0 += red[y][threadIdx.x].x;
+    d1 += red[y][threadIdx.x].y;
   }
-  I[e] = {-d1, -d0};
+  const int j = e / nb, i = e % nb;
+  I[i * nb + j] = {-d1, -d0};
 }
 
 // B operand of the polarisation GEMM: rows (j,l,v) interleaved as 2 (j nb + l) + v,
@@ -881,6 +901,45 @@ void tc_destroy(TcPath *p) {
   delete p;
 }
 
+namespace {
+// One CTA waits on an mbarrier that nothing arrives on: the bounded wait must
+// give up after limit_ns, set the error word and let the kernel return.
+__global__ void wait_selftest_kernel(unsigned long long limit_ns, int *err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(&bar, 0, err, limit_ns);
+  __syncthreads();
+}
+}  // namespace
+
+int tc_wait_selftest(unsigned long long limit_ns, cudaStream_t stream) {
+  int *err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return G1G2_ENOMEM;
+  }
+  int e = 0, rc = G1G2_OK;
+  if (cudaMemsetAsync(err, 0, sizeof(int), stream) != cudaSuccess) rc = G1G2_ECUDA;
+  if (!rc) {
+    wait_selftest_kernel<<<1, 32, 0, stream>>>(limit_ns, err);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      rc = G1G2_ECUDA;
+  }
+  cudaFree(err);
+  if (rc) return rc;
+  if (e) {
+    set_error_detail("self-test: the bounded barrier wait gave up as intended");
+    return G1G2_ETIMEOUT;
+  }
+  return G1G2_OK;
+}
+
 int tc_error(TcPath *p, cudaStream_t stream) {
   int e = 0;
   if (cudaMemcpyAsync(&e, p->err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess) return G1G2_ECUDA;
@@ -934,7 +993,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     for (int q = 0; q < nops; ++q) {
       const auto &o = ops[q];
       L.before("tc_slice_b");
-      slice_b_kernel<<<32, 256, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.ld, o.transpose, o.il,
+      slice_b_kernel<<<64, 256, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.ld, o.transpose, o.il,
                                                o.S, o.out, (long long)t->nout2 * o.ld);
       L.after_launch();
     }
@@ -975,7 +1034,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     g.a_amax = g2_amax;
     launch_gemm(t, L, "tc_gemm_collision", mCol, sl ? t->mW_s : t->mW_hi, t->mW_lo, g, sl);
     L.before("tc_collision_reduce");
-    collision_reduce_kernel<<<(nb * nb + 127) / 128, 128, 0, L.stream>>>(nb, t->splits, t->partial, t->I);
+    collision_reduce_kernel<<<(nb * nb + 31) / 32, dim3(32, 8), 0, L.stream>>>(nb, t->splits, t->partial, t->I);
     L.after_launch();
   }
   g1_update(L, nb, hhf, n_in, t->I, st, ny, nys, nacc, nk);

@@ -18,6 +18,9 @@ void tc_destroy(TcPath *p);
 void tc_load_state(TcPath *p, Launcher &L, const cplx *G);
 // G1G2_ETIMEOUT when a tensor-core kernel gave up on a barrier (synchronises the stream).
 int tc_error(TcPath *p, cudaStream_t stream);
+// Launch a wait on a barrier nothing arrives on, bounded by limit_ns:
+// G1G2_ETIMEOUT when the wait gave up and reported it (the expected result).
+int tc_wait_selftest(unsigned long long limit_ns, cudaStream_t stream);
 
 // One right-hand side (hhf already built from n_in): collision integral and
 // G1 update, then the G2 contractions and the assembly with the RK4 update.

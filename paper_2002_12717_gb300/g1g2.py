@@ -72,6 +72,9 @@ def load():
         "g1g2_rhs_vjp": (ctypes.c_int, [vp, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp]),
         "g1g2_adjoint": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
                                         _dp]),
+        "g1g2_wait_selftest": (ctypes.c_int, [ctypes.c_int]),
+        "g1g2_set_adjoint_checkpoints": (ctypes.c_int, [vp, ctypes.c_int]),
+        "g1g2_adjoint_plan": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "g1g2_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "g1g2_profile_report": (ctypes.c_int, [vp, ctypes.POINTER(KernelStat), ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int)]),
@@ -85,6 +88,11 @@ def load():
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def wait_selftest(limit_us=20000):
+    """Return code of the bounded-wait self-test (ETIMEOUT is the expected result)."""
+    return load().g1g2_wait_selftest(int(limit_us))
 
 
 def _check(rc):
@@ -224,6 +232,18 @@ class Propagator:
                                       ctypes.byref(J), _cptr(gd) if n_drive_params else None, ctypes.byref(gw),
                                       _cptr(gh)))
         return J.value, gd[:n_drive_params], gw.value, gh
+
+    CKPT = {"auto": 0, "device": 1, "host": 2}
+
+    def set_adjoint_checkpoints(self, where="auto"):
+        """Checkpoints of the adjoint in device memory, pinned host memory, or chosen by size ("auto")."""
+        _check(self._lib.g1g2_set_adjoint_checkpoints(self._ctx, self.CKPT[where]))
+
+    def adjoint_plan(self):
+        """(interval, "device" | "host") of the last adjoint call."""
+        k, w = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.g1g2_adjoint_plan(self._ctx, ctypes.byref(k), ctypes.byref(w)))
+        return k.value, {0: None, 1: "device", 2: "host"}[w.value]
 
     def profile(self, enable=True):
         """Start (clearing old records) or stop per-kernel CUDA-event timing."""

@@ -108,6 +108,15 @@ def test_null_context_calls(lib):
     lib.g1g2_destroy(None)
 
 
+def test_adjoint_and_selftest_arguments_rejected_on_host(lib):
+    k, w = ctypes.c_int(), ctypes.c_int()
+    assert lib.g1g2_set_adjoint_checkpoints(None, 0) == g1g2.EINVAL
+    assert lib.g1g2_adjoint_plan(None, ctypes.byref(k), ctypes.byref(w)) == g1g2.EINVAL
+    assert lib.g1g2_adjoint(None, 0.01, 10, 0, 0, None, None, None, None) == g1g2.EINVAL
+    assert lib.g1g2_wait_selftest(0) == g1g2.EINVAL
+    assert lib.g1g2_wait_selftest(20000000) == g1g2.EINVAL
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(g1g2, "_lib", None)
     monkeypatch.setattr(g1g2, "LIB_PATH", str(tmp_path / "missing.so"))

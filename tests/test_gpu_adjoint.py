@@ -196,3 +196,24 @@ def test_autograd_function_chain_rule():
     assert np.abs(got[1] - a.grad.numpy()).max() <= TOL_GRAD * np.abs(a.grad.numpy()).max()
     assert abs(got[2] - U.grad.item()) <= TOL_GRAD * abs(U.grad.item())
     assert abs(got[3] - tau.grad.item()) <= TOL_GRAD * abs(tau.grad.item())
+
+
+def test_host_checkpoints_give_identical_gradients():
+    """Checkpoints in pinned host memory: the same reverse sweep, bit for bit."""
+    from paper_2002_12717_gb300.g1g2 import Propagator
+    dt, nsteps, M = 0.02, 24, 4
+    d = _hubbard_case(M, nsteps, dt)
+    res = {}
+    for where in ("device", "host"):
+        with Propagator(d["h"], d["w"], d["n0"], None, "SOA", "fp64") as p:
+            p.set_drive(d["D"], d["drive"])
+            p.set_adjoint_checkpoints(where)
+            res[where] = p.adjoint(dt, nsteps, objective=0, ckpt_every=5, n_drive_params=M)
+            assert p.adjoint_plan() == (5, where)
+    a, b = res["device"], res["host"]
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and a[2] == b[2] and np.array_equal(a[3], b[3])
+    with Propagator(d["h"], d["w"], d["n0"], None, "SOA", "fp64") as p:
+        p.set_drive(d["D"], d["drive"])
+        p.adjoint(dt, nsteps, objective=0, n_drive_params=M)
+        k, where = p.adjoint_plan()
+        assert where == "device" and k == 1     # everything fits: no recomputation

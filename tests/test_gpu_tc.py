@@ -160,3 +160,17 @@ def test_contexts_of_different_forms_coexist():
             p.step(0.01)
         o1, o3 = p1.observables(), p3.observables()
     assert abs(o1["e_total"] - o3["e_total"]) < 1e-6 * abs(o1["e_total"])
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A barrier that nothing arrives on: the wait gives up after its limit, the
+    kernel returns ETIMEOUT through its error word, and later work still runs."""
+    import time
+    from paper_2002_12717_gb300 import g1g2
+    t0 = time.perf_counter()
+    assert g1g2.wait_selftest(20000) == g1g2.ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    d = inputs.general_basis(16, 32, 8, seed=3, pulse=False)
+    with g1g2.from_workload(d, precision="bf16x4") as p:
+        p.step(0.01)
+        assert np.isfinite(p.observables()["e_total"])
