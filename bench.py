@@ -376,6 +376,33 @@ def adjoint_sample(args):
             "grad_controls_norm": float(np.linalg.norm(gd))}
 
 
+def hubbard_scaling(sizes, steps=3):
+    """ms per RK4 step of the spin-restricted Hubbard chain (J = 1, U = 2, half filling,
+    quench) on the O(nb^4) Hubbard path and on the general O(nb^5) FP64 path."""
+    import torch
+
+    from paper_2002_12717_gb300.g1g2 import from_workload
+
+    out = []
+    for nb in sizes:
+        d = inputs.hubbard_chain_restricted(L=nb, U=2.0)
+        row = {"nb": nb}
+        for hub in (True, False):
+            with from_workload(d, precision="fp64") as p:
+                p.hubbard_path = hub
+                p.propagate(0.02, 2)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(steps):
+                    p.step(0.02)
+                e1.record()
+                torch.cuda.synchronize()
+                row["hubbard_ms" if hub else "general_ms"] = e0.elapsed_time(e1) / steps
+        out.append(row)
+    return out
+
+
 def cpu_baseline(args):
     """The CPU oracle as it stands, one right-hand side of each workload (bounded sample)."""
     from oracle import g1g2_oracle as O
@@ -443,6 +470,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-steps", type=int, default=3,
                     help="steps run in both forms from the initial state (speed-up and error vs FP64)")
+    ap.add_argument("--hubbard-scaling", default="",
+                    help="comma-separated nb: time the Hubbard O(nb^4) path against the general path and exit")
     ap.add_argument("--adjoint-steps", type=int, default=100,
                     help="steps of the discrete-adjoint sample on the 4x4 Hubbard cluster (0: skip)")
     args = ap.parse_args()
@@ -455,6 +484,11 @@ def main():
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.hubbard_scaling:
+        if rank == 0:
+            print(json.dumps({"hubbard_scaling": hubbard_scaling([int(x) for x in args.hubbard_scaling.split(",")])}),
+                  flush=True)
+        return
     if args.impl == "reference":
         if rank != 0:
             return

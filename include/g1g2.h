@@ -188,6 +188,20 @@ int g1g2_set_adjoint_checkpoints(g1g2_ctx *c, int where);
  * g1g2_adjoint call used (0, 0 before the first). */
 int g1g2_adjoint_plan(const g1g2_ctx *c, int *ckpt_every, int *where);
 
+/* O(nb^4) right-hand side for the Hubbard basis (Sec. VI: the commutator with
+ * the sparse h^HF as a stencil, and the source term with the products of four
+ * G^< cancelled, Eq. (soa-cubic-scheme); the collision integral reduces to
+ * I_ij = -i U_i G2_iiji).  Chosen automatically at g1g2_init when the basis is
+ * spin-restricted, the selfenergy SOA, the precision FP64 and w is on-site
+ * (w_ijkl = U_i when i = j = k = l, else 0); the commutator runs over the
+ * nonzero pattern of h, of D (set_drive) and of the diagonal.
+ *   g1g2_set_hubbard_path(c, 0) switches to the general O(nb^5) form,
+ *   g1g2_set_hubbard_path(c, 1) back (G1G2_EUNSUPPORTED if the structure does
+ *   not qualify); g1g2_hubbard_path returns 1 when it is in use, 0 when not,
+ *   G1G2_EINVAL for a NULL context. */
+int g1g2_set_hubbard_path(g1g2_ctx *c, int enable);
+int g1g2_hubbard_path(const g1g2_ctx *c);
+
 /* Failure-detection self-test (not in the paper): launches one CTA that waits
  * on a barrier nothing arrives on, with the bounded wait the tensor-core
  * kernels use but a limit of limit_us microseconds (1 .. 1e7).  Expected

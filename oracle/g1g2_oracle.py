@@ -21,7 +21,7 @@ G1 at the library boundary, n_ij = <c_j^dagger c_i>, Hermitian) and the
 correlated two-particle function G2 = 𝒢 of Eq. (gscor-def), an nb^4 tensor
 indexed [i, j, k, l].
 
-Readings of the paper used here (each is listed in the design doc as well):
+Readings of the paper used here, where it leaves a choice open:
   * fermions only; ħ = 1;
   * the integrator is classical RK4 on (n, 𝒢) jointly (the paper names none);
   * SOA uses Psi^- (w^- = w_pqrs - w_pqsr); GW uses the plain-w Psi

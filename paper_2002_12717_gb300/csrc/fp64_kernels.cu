@@ -325,21 +325,84 @@ __global__ void g2_assemble_kernel(int nb, const cplx *__restrict__ Cb, const cp
   __shared__ cplx tile[PT][PT + 1];
   const long long M = (long long)nb * nb;
   const long long r0 = (long long)blockIdx.y * PT, c0 = (long long)blockIdx.x * PT;
-  // load the transposed tile Ab[(c0..), (r0..)]
-  for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
-    const long long rr = c0 + yy, cc = r0 + threadIdx.x;
-    if (rr < M && cc < M) tile[yy][threadIdx.x] = Ab[rr * M + cc];
-  }
+  // load the transposed tile Ab[(c0..), (r0..)] (no Ab: dG = -i Cb)
+  if (Ab)
+    for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
+      const long long rr = c0 + yy, cc = r0 + threadIdx.x;
+      if (rr < M && cc < M) tile[yy][threadIdx.x] = Ab[rr * M + cc];
+    }
   __syncthreads();
   for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
     const long long r = r0 + yy, c = c0 + threadIdx.x;
     if (r < M && c < M) {
       const long long e = r * M + c;
-      const cplx at = cconj(tile[threadIdx.x][yy]);
-      const cplx v = cadd(csub(Cb[e], Ab[e]), at);
+      const cplx v = Ab ? cadd(csub(Cb[e], Ab[e]), cconj(tile[threadIdx.x][yy])) : Cb[e];
       rk4_apply(e, mul_minus_i(v), stage, dt, y, ys, acc, kout);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Hubbard basis, spin-restricted SOA: the O(nb^4) forms of the G2 right-hand
+// side.  With an on-site interaction w_ijkl = U_i d(i=j=k=l):
+//   * the commutator [h2, G] only needs the nonzeros of h^HF (h plus the
+//     diagonal Hartree term), a stencil over the sparsity pattern (CSR);
+//   * in the source term, writing G^> = G^< - i 1 cancels the products of
+//     four G^< (the reformulation of Sec. VI for the Hubbard basis) and
+//     leaves six terms, each with one or two Kronecker deltas; with
+//     G^< = i n they read Psi = -S,
+//       S_ijkl = - U_j n_ij n_jk n_jl - U_i n_ji n_ik n_il + d_ij U_i n_ik n_il
+//                + U_l n_il n_jl n_lk + U_k n_ik n_jk n_kl - d_kl U_k n_ik n_jk;
+//   * the collision integral is I_ij = -i U_i G_iiji.
+// ---------------------------------------------------------------------------
+__global__ void hubbard_c_kernel(int nb, const int *__restrict__ rp, const int *__restrict__ ci,
+                                 const cplx *__restrict__ hhf, const double *__restrict__ U,
+                                 const cplx *__restrict__ n, const cplx *__restrict__ G, cplx *C) {
+  // grid: y = i nb + j, x over (k, l); index arithmetic in 32 bits where it fits
+  const long long N = nb, N2 = N * N, N3 = N2 * N;
+  const int ij = blockIdx.y, i = ij / nb, j = ij - i * nb;
+  const int kl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (kl < nb * nb) {
+    const int k = kl / nb, l = kl - k * nb;
+    const long long e = (long long)ij * N2 + kl;
+    cplx acc = {0.0, 0.0};
+    // [h2, G]_ijkl = sum_p h_ip G_pjkl + h_jp G_ipkl - G_ijpl h_pk - G_ijkp h_pl
+    for (int q = rp[i]; q < rp[i + 1]; ++q) {
+      const int p = ci[q];
+      acc = cfma(hhf[i * N + p], G[p * N3 + j * N2 + kl], acc);
+    }
+    for (int q = rp[j]; q < rp[j + 1]; ++q) {
+      const int p = ci[q];
+      acc = cfma(hhf[j * N + p], G[i * N3 + p * N2 + k * N + l], acc);
+    }
+    for (int q = rp[k]; q < rp[k + 1]; ++q) {
+      const int p = ci[q];
+      acc = csub(acc, cmul(G[i * N3 + j * N2 + p * N + l], hhf[p * N + k]));
+    }
+    for (int q = rp[l]; q < rp[l + 1]; ++q) {
+      const int p = ci[q];
+      acc = csub(acc, cmul(G[e - l + p], hhf[p * N + l]));
+    }
+    // Psi = -S
+    const cplx nij = n[i * N + j], nji = n[j * N + i], nik = n[i * N + k], nil = n[i * N + l];
+    const cplx njk = n[j * N + k], njl = n[j * N + l], nlk = n[l * N + k], nkl = n[k * N + l];
+    cplx S = cscale(cmul(cmul(nij, njk), njl), -U[j]);
+    S = cadd(S, cscale(cmul(cmul(nji, nik), nil), -U[i]));
+    S = cadd(S, cscale(cmul(cmul(nil, njl), nlk), U[l]));
+    S = cadd(S, cscale(cmul(cmul(nik, njk), nkl), U[k]));
+    if (i == j) S = cadd(S, cscale(cmul(nik, nil), U[i]));
+    if (k == l) S = csub(S, cscale(cmul(nik, njk), U[k]));
+    C[e] = csub(acc, S);
+  }
+}
+
+__global__ void hubbard_collision_kernel(int nb, const double *__restrict__ U, const cplx *__restrict__ G, cplx *I) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nb * nb) return;
+  const long long N = nb;
+  const int i = e / nb, j = e % nb;
+  const cplx g = G[((i * N + i) * N + j) * N + i];  // G_iiji
+  I[e] = cscale(mul_minus_i(g), U[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -543,6 +606,19 @@ void g2_assemble(Launcher &L, int nb, const cplx *Cb, const cplx *Ab, Rk4Stage s
   const unsigned t = (unsigned)((M + PT - 1) / PT);
   L.before("fp64_g2_assemble_rk4");
   g2_assemble_kernel<<<dim3(t, t), dim3(PT, 8), 0, L.stream>>>(nb, Cb, Ab, st.stage, st.dt, y, ys, acc, kout);
+  L.after_launch();
+}
+
+void hubbard_c(Launcher &L, int nb, const int *rp, const int *ci, const cplx *hhf, const double *U, const cplx *n,
+               const cplx *G, cplx *C) {
+  L.before("hubbard_c");
+  hubbard_c_kernel<<<dim3((nb * nb + 127) / 128, nb * nb), 128, 0, L.stream>>>(nb, rp, ci, hhf, U, n, G, C);
+  L.after_launch();
+}
+
+void hubbard_collision(Launcher &L, int nb, const double *U, const cplx *G, cplx *I) {
+  L.before("hubbard_collision");
+  hubbard_collision_kernel<<<(nb * nb + 127) / 128, 128, 0, L.stream>>>(nb, U, G, I);
   L.after_launch();
 }
 

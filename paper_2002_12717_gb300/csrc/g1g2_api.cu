@@ -67,6 +67,11 @@ struct g1g2_ctx {
   cplx *adj_hsum = nullptr;                     // accumulated cotangent of h
   cplx *adj_hbar = nullptr;                     // cotangent of hHF of one stage
   std::vector<void *> adj_allocs;
+  // Hubbard basis (spin-restricted SOA, on-site w): O(nb^4) right-hand side
+  bool hub_ok = false, hub_on = false;
+  double *hub_U = nullptr;                      // U_i = w_iiii
+  int *hub_rp = nullptr, *hub_ci = nullptr;     // CSR pattern of h^HF (h, D, diagonal), symmetric
+  std::vector<unsigned char> hub_hpat;          // nonzero pattern of h (host)
   int adj_where = G1G2_CKPT_AUTO;               // where the adjoint keeps its checkpoints
   int adj_last_k = 0, adj_last_where = 0;       // plan of the last g1g2_adjoint call
 
@@ -169,6 +174,14 @@ void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *
     hf_build(L, nb, c->Wm, c->w_real, c->h, c->hasD ? c->D : nullptr, f, n_in, c->hhf);
   if (c->se == G1G2_HF) {
     g1_update(L, nb, c->hhf, n_in, nullptr, st, o.ny, o.nys, o.nacc, o.nk);
+    return;
+  }
+  if (c->hub_on) {
+    // Hubbard basis: I, then C = [h2, G] + Psi in O(nb^4); the assembly forms dG = -i C
+    hubbard_collision(L, nb, c->hub_U, G_in, c->I);
+    g1_update(L, nb, c->hhf, n_in, c->I, st, o.ny, o.nys, o.nacc, o.nk);
+    hubbard_c(L, nb, c->hub_rp, c->hub_ci, c->hhf, c->hub_U, n_in, G_in, c->Cb);
+    g2_assemble(L, nb, c->Cb, nullptr, st, o.Gy, o.Gys, o.Gacc, o.Gk);
     return;
   }
   // a2: I_ij = -i sum_(lp) sum_k wP[lp][i][k] G[lp][j][k]   (Eq. eom_gone-I)
@@ -514,6 +527,31 @@ void vjp_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n, const cplx *G, 
   contract3(c, L, 4, c->AE, c->AB2, one, 1.0, nbar);
 }
 
+// CSR pattern of h^HF for the Hubbard path: the nonzeros of h (and of D when a
+// drive is set), the diagonal, made symmetric.
+int hub_upload_pattern(g1g2_ctx *c, const std::vector<cplx> *D) {
+  const int N = c->nb;
+  std::vector<int> rp(N + 1, 0), ci;
+  for (int i = 0; i < N; ++i) {
+    for (int p = 0; p < N; ++p) {
+      const size_t a = (size_t)i * N + p, b = (size_t)p * N + i;
+      bool nz = i == p || c->hub_hpat[a] || c->hub_hpat[b];
+      if (D && !nz) nz = (*D)[a].x != 0.0 || (*D)[a].y != 0.0 || (*D)[b].x != 0.0 || (*D)[b].y != 0.0;
+      if (nz) ci.push_back(p);
+    }
+    rp[i + 1] = (int)ci.size();
+  }
+  if (cudaMemcpyAsync(c->hub_rp, rp.data(), rp.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c->hub_ci, ci.data(), ci.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(G1G2_ECUDA, "Hubbard pattern upload");
+  }
+  return G1G2_OK;
+}
+
 int adj_alloc(g1g2_ctx *c, std::vector<void *> &own, void **p, size_t bytes) {
   void *q = nullptr;
   if (cudaMalloc(&q, bytes) != cudaSuccess) {
@@ -749,6 +787,28 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
     if ((rc = up(c->wsrc, hsrc.data(), N4 * sizeof(cplx)))) return bail(rc);
     if ((rc = up(c->wP, hP.data(), N4 * sizeof(cplx)))) return bail(rc);
   }
+  // Hubbard basis: spin-restricted SOA with an on-site interaction w_ijkl = U_i d(i=j=k=l)
+  if (se == G1G2_SOA && restricted && c->prec == G1G2_FP64 && real) {
+    bool onsite = true;
+    std::vector<double> Ui(N);
+    for (size_t i = 0; i < N && onsite; ++i)
+      for (size_t j = 0; j < N && onsite; ++j)
+        for (size_t k = 0; k < N && onsite; ++k)
+          for (size_t l = 0; l < N; ++l) {
+            const double v = hw[at4(i, j, k, l)].x;
+            if (i == j && j == k && k == l) Ui[i] = v;
+            else if (v != 0.0) { onsite = false; break; }
+          }
+    if (onsite) {
+      c->hub_hpat.assign(N2, 0);
+      for (size_t e = 0; e < N2; ++e) c->hub_hpat[e] = (h[2 * e] != 0.0 || h[2 * e + 1] != 0.0);
+      if ((rc = dalloc(c, &c->hub_U, N)) || (rc = dalloc(c, &c->hub_rp, N + 1)) || (rc = dalloc(c, &c->hub_ci, N2)))
+        return bail(rc);
+      if ((rc = up(c->hub_U, Ui.data(), N * sizeof(double)))) return bail(rc);
+      if ((rc = hub_upload_pattern(c, nullptr))) return bail(rc);
+      c->hub_ok = c->hub_on = true;
+    }
+  }
   if (correlated && c->prec != G1G2_FP64) {
     if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "init sync"))) return bail(rc);
     g_detail.clear();
@@ -780,6 +840,11 @@ int g1g2_set_drive(g1g2_ctx *c, const double *D, int kind, const double *params,
   int rc = cuda_check(cudaMemcpyAsync(c->D, D, N2 * sizeof(cplx), cudaMemcpyHostToDevice, c->stream), "drive upload");
   if (rc) return rc;
   if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "drive sync"))) return rc;
+  if (c->hub_ok) {  // the drive's nonzeros join the pattern of h^HF
+    std::vector<cplx> Dh(N2);
+    for (size_t e = 0; e < N2; ++e) Dh[e] = {D[2 * e], D[2 * e + 1]};
+    if ((rc = hub_upload_pattern(c, &Dh))) return rc;
+  }
   c->drive_kind = kind;
   c->drive_params.assign(params, params + nparams);
   c->hasD = true;
@@ -923,6 +988,16 @@ static AdjPlan adjoint_plan(int nsteps, size_t SB, int ckpt_every, int where_req
   }
   return {kmem, G1G2_CKPT_HOST};
 }
+
+int g1g2_set_hubbard_path(g1g2_ctx *c, int enable) {
+  if (!c) return fail(G1G2_EINVAL, "ctx is NULL");
+  if (enable && !c->hub_ok)
+    return fail(G1G2_EUNSUPPORTED, "the O(nb^4) path needs spin-restricted SOA, the FP64 form and an on-site w");
+  c->hub_on = enable != 0;
+  return G1G2_OK;
+}
+
+int g1g2_hubbard_path(const g1g2_ctx *c) { return c ? (c->hub_on ? 1 : 0) : G1G2_EINVAL; }
 
 int g1g2_wait_selftest(int limit_us) {
   if (limit_us < 1 || limit_us > 10000000) return fail(G1G2_EINVAL, "limit must be 1 us .. 10 s");

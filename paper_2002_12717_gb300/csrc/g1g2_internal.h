@@ -93,12 +93,18 @@ struct Rk4Stage {
 // or a plain write of dn to kout.
 void g1_update(Launcher &L, int nb, const cplx *hhf, const cplx *n, const cplx *I, Rk4Stage st,
                cplx *y, cplx *ys, cplx *acc, cplx *kout);
-// dG = -i (Cb - Ab + conj(Ab^T)) with ^T the (ij)<->(kl) transpose; RK4 update or write k.
+// dG = -i (Cb - Ab + conj(Ab^T)) with ^T the (ij)<->(kl) transpose (dG = -i Cb when Ab is
+// null); RK4 update or write k.
 void g2_assemble(Launcher &L, int nb, const cplx *Cb, const cplx *Ab, Rk4Stage st, cplx *y, cplx *ys,
                  cplx *acc, cplx *kout);
 
 // Observables.
 // red[0..] = {Re Tr(h n), Re Tr((hHF-h(t)) n), Re Tr n, Re Tr(D n)} for state n;
+// Hubbard basis, spin-restricted SOA (on-site w_ijkl = U_i d(i=j=k=l)): C = [h2, G] + Psi
+// with the commutator over the CSR pattern (rp, ci) of h^HF, and I_ij = -i U_i G_iiji.
+void hubbard_c(Launcher &L, int nb, const int *rp, const int *ci, const cplx *hhf, const double *U, const cplx *n,
+               const cplx *G, cplx *C);
+void hubbard_collision(Launcher &L, int nb, const double *U, const cplx *G, cplx *I);
 void obs_one_body(Launcher &L, int nb, const cplx *h, const cplx *D, double f, const cplx *hhf,
                   const cplx *n, double *red);
 // red[0] = Re sum W[(ij),(kl)] G[(kl),(ij)], red[1] = count of non-finite entries of G.

@@ -73,6 +73,8 @@ def load():
         "g1g2_adjoint": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
                                         _dp]),
         "g1g2_wait_selftest": (ctypes.c_int, [ctypes.c_int]),
+        "g1g2_set_hubbard_path": (ctypes.c_int, [vp, ctypes.c_int]),
+        "g1g2_hubbard_path": (ctypes.c_int, [vp]),
         "g1g2_set_adjoint_checkpoints": (ctypes.c_int, [vp, ctypes.c_int]),
         "g1g2_adjoint_plan": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "g1g2_profile": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -232,6 +234,15 @@ class Propagator:
                                       ctypes.byref(J), _cptr(gd) if n_drive_params else None, ctypes.byref(gw),
                                       _cptr(gh)))
         return J.value, gd[:n_drive_params], gw.value, gh
+
+    @property
+    def hubbard_path(self):
+        """True when the O(nb^4) Hubbard-basis right-hand side is in use."""
+        return self._lib.g1g2_hubbard_path(self._ctx) == 1
+
+    @hubbard_path.setter
+    def hubbard_path(self, enable):
+        _check(self._lib.g1g2_set_hubbard_path(self._ctx, 1 if enable else 0))
 
     CKPT = {"auto": 0, "device": 1, "host": 2}
 
