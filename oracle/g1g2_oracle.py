@@ -46,6 +46,7 @@ einsum = functools.partial(np.einsum, optimize=True)
 
 SOA = "SOA"
 GW = "GW"
+GWX = "GWX"   # GW with the exchange source term Psi^± (end of Sec. IV.C)
 HF = "HF"
 
 
@@ -168,10 +169,11 @@ class Problem:
         self.restricted = restricted
         self.D = None if D is None else np.asarray(D, dtype=np.complex128)
         self.drive = drive  # callable f(t) -> float, or None
-        if restricted and selfenergy == GW:
+        if restricted and selfenergy in (GW, GWX):
             raise ValueError("GW couples same-spin components; no spin-restricted form")
-        # source-term interaction: Psi^- for SOA in a spin-orbital basis,
-        # plain w for GW (Sec. IV.C) and for the opposite-spin restricted mode
+        # source-term interaction: Psi^- for SOA in a spin-orbital basis and for
+        # GW with exchange (Psi replaced by Psi^±, end of Sec. IV.C), plain w for
+        # standard GW (Sec. IV.C) and for the opposite-spin restricted mode
         self.w_source = self.w if (restricted or selfenergy == GW) else w_antisym(self.w)
 
     def h_of_t(self, t):
@@ -186,6 +188,7 @@ def rhs(prob: Problem, t, n, G2):
     G1: Eq. (eom_gone-2) with I of Eq. (eom_gone-I).
     G2: SOA Eq. (result_eom_soa): i d𝒢/dt = [h2, 𝒢] + Psi^±;
         GW  Eq. (g2-eq-gw-pi):  i d𝒢/dt = [h2, 𝒢] + Psi + Π_ijkl - (Π_lkji)^*;
+        GWX: the same with Psi replaced by Psi^± (end of Sec. IV.C);
         HF: 𝒢 is not propagated (collision integral zero).
     """
     hhf = hf_hamiltonian(prob.h_of_t(t), prob.w, n, prob.restricted)
@@ -195,7 +198,7 @@ def rhs(prob: Problem, t, n, G2):
     I = collision_integral(prob.w, G2)
     dn = g1_rhs(hhf, n, I)
     rhs2 = two_particle_commutator(hhf, G2) + psi_source(prob.w_source, n)
-    if prob.selfenergy == GW:
+    if prob.selfenergy in (GW, GWX):
         pi = gw_polarisation(gw_hcorr(prob.w, n), G2)
         rhs2 = rhs2 + pi - pi.transpose(3, 2, 1, 0).conj()
     return dn, -1j * rhs2

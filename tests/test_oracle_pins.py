@@ -84,6 +84,27 @@ def test_source_term_is_exact_initial_slope_from_slater_determinant():
     assert np.abs(-1j * O.psi_source(w, n) - exact).max() > 1e-3
 
 
+def test_gw_with_exchange_has_the_exact_initial_slope():
+    """GW with Psi replaced by Psi^± (end of Sec. IV.C): from an uncorrelated state
+    (𝒢 = 0, so Π = 0) its full right-hand side is the exact d𝒢/dt, while standard
+    GW (plain-w source) is not.  Pins the exchange variant's source and that the
+    rest of its right-hand side vanishes at 𝒢 = 0."""
+    rng = np.random.default_rng(21)
+    nb = 5
+    h = inputs.random_hermitian(nb, rng)
+    w = sym_w(nb, rng)
+    H = fock.hamiltonian(h, w)
+    orb = np.linalg.qr(rng.standard_normal((nb, 3)) + 1j * rng.standard_normal((nb, 3)))[0]
+    psi = fock.slater(orb, nb)
+    n, n2 = fock.rdms(psi, nb)
+    g2 = fock.correlated_g2(n, n2)
+    exact = fock.time_derivative(H, psi, lambda v: fock.correlated_g2(*fock.rdms(v, nb)))
+    _, got = O.rhs(O.Problem(h, w, selfenergy=O.GWX), 0.0, n, g2)
+    assert np.abs(got - exact).max() < 1e-8
+    _, gw = O.rhs(O.Problem(h, w, selfenergy=O.GW), 0.0, n, g2)
+    assert np.abs(gw - exact).max() > 1e-3
+
+
 def test_commutator_is_exact_for_noninteracting_dynamics():
     """With w = 0 the exact correlated part obeys i d𝒢/dt = [h^(2), 𝒢] (Eq. result_eom_soa)."""
     rng = np.random.default_rng(13)
@@ -312,7 +333,7 @@ def test_hubbard_chain_initial_state_closed_form():
     assert np.abs(hhf @ d["n0"] - d["n0"] @ hhf).max() < 1e-12
 
 
-@pytest.mark.parametrize("se", ["HF", "SOA", "GW"])
+@pytest.mark.parametrize("se", ["HF", "SOA", "GW", "GWX"])
 def test_conservation_laws(se):
     """Particle number to round-off; energy to O(dt^4) (Sec. VIII: energy conserving)."""
     L = 3
