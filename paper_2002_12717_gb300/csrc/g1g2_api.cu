@@ -649,7 +649,10 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   if (opt_in) opt = *opt_in;
   if (nb < 1 || nb > 128) return fail(G1G2_EINVAL, "nb must be in [1, 128]");
   if (!h || !w || !G1_0) return fail(G1G2_EINVAL, "h, w and G1_0 must be non-NULL");
-  if (se < G1G2_HF || se > G1G2_GW) return fail(G1G2_EINVAL, "bad selfenergy");
+  if (se < G1G2_HF || se > G1G2_GW_EXCHANGE) return fail(G1G2_EINVAL, "bad selfenergy");
+  // GW with exchange is GW with the source term Psi^± (w^- in Psi)
+  const bool gw_exchange = se == G1G2_GW_EXCHANGE;
+  if (gw_exchange) se = G1G2_GW;
   if (opt.precision != G1G2_FP64 && opt.precision != G1G2_TF32X3 && opt.precision != G1G2_BF16X4)
     return fail(G1G2_EINVAL, "bad precision");
   if (opt.basis != G1G2_SPIN_ORBITAL && opt.basis != G1G2_SPIN_RESTRICTED) return fail(G1G2_EINVAL, "bad basis");
@@ -717,7 +720,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   }
   c->w_real = real;
   // source interaction: w^- (SOA, spin-orbital), else w
-  const bool use_minus = (se == G1G2_SOA && !restricted);
+  const bool use_minus = (se == G1G2_SOA || gw_exchange) && !restricted;
   for (size_t i = 0; i < N; ++i)
     for (size_t j = 0; j < N; ++j)
       for (size_t k = 0; k < N; ++k)

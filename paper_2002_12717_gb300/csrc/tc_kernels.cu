@@ -588,6 +588,7 @@ struct TcPath {
   // FP32 planar tensors [2][nb^4]
   float *y32 = nullptr, *ys32 = nullptr, *acc = nullptr, *Z = nullptr, *buf1 = nullptr, *buf2 = nullptr;
   float *W32 = nullptr;                 // source interaction (real) [nb^4]
+  float *Wh32 = nullptr;                // GW: w for the quasi-Hamiltonian (= W32 unless the source is w^-)
   float *w_hi = nullptr, *w_lo = nullptr;  // w (real) split [i][c]
   // small pre-split B operands
   float *bh_hi = nullptr, *bh_lo = nullptr;   // hHF, complex A
@@ -614,7 +615,7 @@ struct TcPath {
   CUtensorMap mBh_s, mBnr_s, mBnc_s, mBnb_s, mBnt_s, mW_s, mBpi_s, mBpi_s_half;
   bool pi_pair = false;  // polarisation GEMM launched as CTA pairs sharing B (TMA multicast)
   // tensor maps
-  CUtensorMap mZin_y32, mZin_ys32, mCol_y32, mCol_ys32, mW32, mBuf1Gather, mBuf2Lin, mBuf1Lin;
+  CUtensorMap mZin_y32, mZin_ys32, mCol_y32, mCol_ys32, mW32, mWh32, mBuf1Gather, mBuf2Lin, mBuf1Lin;
   CUtensorMap mBh_hi, mBh_lo, mBnr_hi, mBnr_lo, mBnc_hi, mBnc_lo, mBnb_hi, mBnb_lo, mW_hi, mW_lo;
   CUtensorMap mPi_y32, mPi_ys32, mBpi_hi, mBpi_lo, mBnt_hi, mBnt_lo;
 };
@@ -624,7 +625,7 @@ namespace {
 // amax slots: FP32 bit patterns of the largest |A| of each A tensor of the sliced form
 enum : int {
   kAmaxW = 0, kAmaxY = 1, kAmaxYs = 2, kAmaxP1 = 3, kAmaxP2 = 4, kAmaxP3 = 5, kAmaxH1 = 6, kAmaxH2 = 7,
-  kAmaxSlots = 8
+  kAmaxWh = 8, kAmaxSlots = 16
 };
 
 template <class T>
@@ -802,12 +803,34 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
     if (cudaMemcpy(t->blocks, blk.data(), blk.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(G1G2_ECUDA);
   }
-  // fixed operands: W32 = source interaction (real), w hi/lo for the collision integral
+  // fixed operands: W32 = source interaction (real), w hi/lo for the collision integral;
+  // GW with a w^- source (exchange) also needs plain w for the quasi-Hamiltonian (Wh32)
   {
     std::vector<float> w32(N4);
-    for (long long e = 0; e < N4; ++e) w32[e] = (float)hsrc[e].x;
+    bool src_is_w = true;
+    for (long long e = 0; e < N4; ++e) {
+      w32[e] = (float)hsrc[e].x;
+      if (hsrc[e].x != hw[e].x) src_is_w = false;
+    }
     if (cudaMemcpy(t->W32, w32.data(), N4 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(G1G2_ECUDA);
+    t->Wh32 = t->W32;
+    if (se == G1G2_GW && !src_is_w) {
+      std::vector<float> wh(N4);
+      float hmax = 0.f;
+      for (long long e = 0; e < N4; ++e) {
+        wh[e] = (float)hw[e].x;
+        hmax = std::max(hmax, std::fabs(wh[e]));
+      }
+      if ((rc = talloc(t, &t->Wh32, N4))) return bail(rc);
+      if (cudaMemcpy(t->Wh32, wh.data(), N4 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(G1G2_ECUDA);
+      if (sliced) {
+        int bits = 0;
+        std::memcpy(&bits, &hmax, sizeof(bits));
+        cudaMemcpy(t->amax + kAmaxWh, &bits, sizeof(int), cudaMemcpyHostToDevice);
+      }
+    }
     cplx *wd = nullptr;
     if (cudaMalloc(&wd, N4 * sizeof(cplx)) != cudaSuccess) return bail(G1G2_ENOMEM);
     cudaMemcpy(wd, hw, N4 * sizeof(cplx), cudaMemcpyHostToDevice);
@@ -836,6 +859,7 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
   if ((rc = map_linear(&t->mZin_y32, t->y32, nb, N3, 2)) || (rc = map_linear(&t->mZin_ys32, t->ys32, nb, N3, 2)) ||
       (rc = map_linear(&t->mCol_y32, t->y32, (int)N3, N, 2)) ||
       (rc = map_linear(&t->mCol_ys32, t->ys32, (int)N3, N, 2)) || (rc = map_linear(&t->mW32, t->W32, nb, N3, 1)) ||
+      (rc = map_linear(&t->mWh32, t->Wh32, nb, N3, 1)) ||
       (rc = map_gather(&t->mBuf1Gather, t->buf1, nb)) || (rc = map_linear(&t->mBuf2Lin, t->buf2, nb, N3, 2)) ||
       (rc = map_linear(&t->mBuf1Lin, t->buf1, nb, N3, 2)) ||
       (rc = map_b(&t->mBh_hi, t->bh_hi, kt_c, t->nout2, t->nout2)) ||
@@ -1075,10 +1099,11 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   if (t->se == G1G2_GW) {
     // a5: Y1 = w x_4 n, Y2 = w x_4 n^T (hcorr_ijkl = Y1_ijkl - Y2_klij), swapped layout
     if (sl) cudaMemsetAsync(amax + kAmaxH1, 0, 2 * sizeof(int), L.stream);
-    launch_gemm(t, L, "tc_gemm_hcorr", t->mW32, sl ? t->mBnr_s : t->mBnr_hi, t->mBnr_lo,
-                lp(N3, 1, EP_SWAP34, t->Y1, kAmaxW, kAmaxH1), sl);
-    launch_gemm(t, L, "tc_gemm_hcorr", t->mW32, sl ? t->mBnt_s : t->mBnt_hi, t->mBnt_lo,
-                lp(N3, 1, EP_SWAP34, t->Y2, kAmaxW, kAmaxH2), sl);
+    const int wh_slot = (t->Wh32 == t->W32) ? kAmaxW : kAmaxWh;
+    launch_gemm(t, L, "tc_gemm_hcorr", t->mWh32, sl ? t->mBnr_s : t->mBnr_hi, t->mBnr_lo,
+                lp(N3, 1, EP_SWAP34, t->Y1, wh_slot, kAmaxH1), sl);
+    launch_gemm(t, L, "tc_gemm_hcorr", t->mWh32, sl ? t->mBnt_s : t->mBnt_hi, t->mBnt_lo,
+                lp(N3, 1, EP_SWAP34, t->Y2, wh_slot, kAmaxH2), sl);
     const dim3 pgrid((unsigned)(((nb + 31) / 32) * (t->kpad / 32)), (unsigned)(N * N));
     L.before("tc_realify_pi");
     if (sl) {

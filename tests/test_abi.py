@@ -74,6 +74,9 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert _init(lib, 3, h, w, n0, opt={"basis": 5}) == g1g2.EINVAL
     assert _init(lib, 3, h, w, n0, se=2, opt={"basis": 1}) == g1g2.EINVAL   # GW has no restricted form
     assert b"restricted" in lib.g1g2_last_error_detail()
+    assert _init(lib, 3, h, w, n0, se=3, opt={"basis": 1}) == g1g2.EINVAL   # nor GW with exchange
+    assert b"restricted" in lib.g1g2_last_error_detail()
+    assert _init(lib, 3, h, w, n0, se=4) == g1g2.EINVAL
 
 
 def test_symmetry_violations_rejected_on_host(lib):

@@ -30,6 +30,7 @@ CASES = [
     ("HF", 5, False, False), ("SOA", 1, False, False), ("SOA", 2, False, False), ("SOA", 5, False, True),
     ("SOA", 17, False, False), ("SOA", 33, False, False), ("SOA", 8, True, False), ("SOA", 13, True, False),
     ("GW", 2, False, False), ("GW", 7, False, True), ("GW", 17, False, False), ("GW", 33, False, False),
+    ("GWX", 7, False, True), ("GWX", 17, False, False),
 ]
 
 

@@ -32,8 +32,8 @@ pytestmark = pytest.mark.gpu
 
 def tol_rhs(se, nb, prec="tf32x3"):
     if prec == "bf16x4":
-        return max(1e-6, 2 * 2.0 ** -24 * math.sqrt(2 * nb * nb)) if se == "GW" else 1e-6
-    kp = 2 * nb * nb if se == "GW" else 2 * nb
+        return max(1e-6, 2 * 2.0 ** -24 * math.sqrt(2 * nb * nb)) if se in ("GW", "GWX") else 1e-6
+    kp = 2 * nb * nb if se in ("GW", "GWX") else 2 * nb
     return max(2e-6, 8 * 2.0 ** -24 * math.sqrt(3 * kp / 8))
 
 
@@ -52,7 +52,8 @@ def run_rhs(prop, t, n, g2):
 
 CASES = [("SOA", 4, False), ("SOA", 8, False), ("SOA", 12, False), ("SOA", 20, False), ("SOA", 32, False),
          ("SOA", 36, False), ("SOA", 48, False), ("SOA", 8, True), ("SOA", 12, True), ("GW", 4, False),
-         ("GW", 8, False), ("GW", 12, False), ("GW", 20, False), ("GW", 32, False), ("GW", 36, False)]
+         ("GW", 8, False), ("GW", 12, False), ("GW", 20, False), ("GW", 32, False), ("GW", 36, False),
+         ("GWX", 12, False), ("GWX", 32, False)]
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x4"])
