@@ -43,9 +43,14 @@ FP64_PEAK_TFLOPS = 1.200
 FP64_PEAK_NOTE = "profiles/fp64_dfma_peak.md"
 # nominal dense tensor ratio TF32 / BF16 (1.1 / 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
-# DRAM bytes (read + write) per launch from ncu captures of the current kernels,
-# keyed by (kernel tag, workload); see profiles/.  Missing entries report null.
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the dominant kernel, keyed by (kernel tag,
+# workload), missing entries report null; from one ncu capture of
+# the current kernel: ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum
+# --clock-control none -k regex:tc_gemm_kernel -s 116 -c 1 on
+# `bench.py --workloads general-gw-nb64 --steps 1 --warmup 3` (the 117th GEMM launch
+# is the polarisation pass of the 13th right-hand side); bf16x4 form
+# (profiles/tc_gemm_pi_bf16x4_gw64.md).
+TRAFFIC = {("tc_gemm_pi", "general-gw-nb64"): 2497462784 + 132801536}
 
 
 def load_peaks():
@@ -306,7 +311,8 @@ def run_ours(args, rank, world, dist):
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_NOTE + " (measured DFMA)"}
         dom_tag = "fp64_zgemm (+ split-K): every complex contraction"
-    roof.update({"traffic": TRAFFIC.get((dom_tag, dom_wl)), "kernel": dom_tag, "workload": dom_wl,
+    roof.update({"traffic": TRAFFIC.get((dom_tag, dom_wl)) if args.precision == "bf16x4" else None,
+                 "kernel": dom_tag, "workload": dom_wl,
                  "avg_launch_ms": avg_s * 1e3, "launches": dom_n, "share": t_ms / total_ms})
 
     line = {
