@@ -47,6 +47,7 @@ einsum = functools.partial(np.einsum, optimize=True)
 SOA = "SOA"
 GW = "GW"
 GWX = "GWX"   # GW with the exchange source term Psi^± (end of Sec. IV.C)
+TPP = "TPP"   # particle-particle T matrix, Sec. IV.D, Eq. (g2-eq-tpp-lambda)
 HF = "HF"
 
 
@@ -156,6 +157,23 @@ def gw_polarisation(hcorr, G2):
 
 
 # ---------------------------------------------------------------------------
+# Sec. IV.D: particle-particle T matrix
+# ---------------------------------------------------------------------------
+
+def tpp_hcorr(w, n):
+    """Correlation part of the pp quasi-Hamiltonian, Eq. (HTPPcorr):
+    hcorr_ijkl = (iħ)^2 Σ_pq [G^{H,>}_ijpq - G^{H,<}_ijpq] w_pqkl, with the Hartree
+    product G^{H,≷}_ijpq = G^≷_ip G^≷_jq (Sec. II)."""
+    gl, gg = g_less(n), g_greater(n)
+    return (1j ** 2) * (einsum("ip,jq,pqkl->ijkl", gg, gg, w) - einsum("ip,jq,pqkl->ijkl", gl, gl, w))
+
+
+def tpp_ladder(hcorr, G2):
+    """Particle-particle ladder term, Eq. (lambdapp): Λ_ijkl = Σ_pq hcorr_ijpq 𝒢_pqkl."""
+    return einsum("ijpq,pqkl->ijkl", hcorr, G2)
+
+
+# ---------------------------------------------------------------------------
 # The closed systems: SOA (Sec. III.C), GW (Sec. IV.C), HF (I = 0)
 # ---------------------------------------------------------------------------
 
@@ -189,6 +207,7 @@ def rhs(prob: Problem, t, n, G2):
     G2: SOA Eq. (result_eom_soa): i d𝒢/dt = [h2, 𝒢] + Psi^±;
         GW  Eq. (g2-eq-gw-pi):  i d𝒢/dt = [h2, 𝒢] + Psi + Π_ijkl - (Π_lkji)^*;
         GWX: the same with Psi replaced by Psi^± (end of Sec. IV.C);
+        TPP Eq. (g2-eq-tpp-lambda): i d𝒢/dt = [h2, 𝒢] + Psi^± + Λ_ijkl - (Λ_klij)^*;
         HF: 𝒢 is not propagated (collision integral zero).
     """
     hhf = hf_hamiltonian(prob.h_of_t(t), prob.w, n, prob.restricted)
@@ -201,6 +220,9 @@ def rhs(prob: Problem, t, n, G2):
     if prob.selfenergy in (GW, GWX):
         pi = gw_polarisation(gw_hcorr(prob.w, n), G2)
         rhs2 = rhs2 + pi - pi.transpose(3, 2, 1, 0).conj()
+    elif prob.selfenergy == TPP:
+        lam = tpp_ladder(tpp_hcorr(prob.w, n), G2)
+        rhs2 = rhs2 + lam - lam.transpose(2, 3, 0, 1).conj()
     return dn, -1j * rhs2
 
 

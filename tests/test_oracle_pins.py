@@ -333,7 +333,48 @@ def test_hubbard_chain_initial_state_closed_form():
     assert np.abs(hhf @ d["n0"] - d["n0"] @ hhf).max() < 1e-12
 
 
-@pytest.mark.parametrize("se", ["HF", "SOA", "GW", "GWX"])
+def test_tpp_ladder_matches_lambdapp_hubbard():
+    """The general ladder term (Eqs. HTPPcorr, lambdapp) with the spin-restricted
+    on-site interaction equals the printed Hubbard form, Eq. (lambdapp_hubb):
+    Λ_ijkl = (iħ)^2 U Σ_p [G^>_ip G^>_jp - G^<_ip G^<_jp] 𝒢_ppkl.  Pins the sign,
+    the G^> / G^< order and the index placement of the quasi-Hamiltonian."""
+    rng = np.random.default_rng(31)
+    nb, U = 6, 1.7
+    w = inputs.onsite_w_restricted(nb, U).astype(np.complex128)
+    n = inputs.random_hermitian(nb, rng) * 0.3 + 0.5 * np.eye(nb)
+    g2 = rng.standard_normal((nb,) * 4) + 1j * rng.standard_normal((nb,) * 4)
+    got = O.tpp_ladder(O.tpp_hcorr(w, n), g2)
+    gl, gg = 1j * n, 1j * n - 1j * np.eye(nb)
+    printed = (1j ** 2) * U * np.einsum("ip,jp,ppkl->ijkl", gg, gg, g2) - \
+        (1j ** 2) * U * np.einsum("ip,jp,ppkl->ijkl", gl, gl, g2)
+    assert np.abs(got - printed).max() < 1e-13 * max(1.0, np.abs(printed).max())
+
+
+def test_tpp_separated_form_equals_full_quasi_hamiltonian_form():
+    """Eq. (g2-eq-tpp), written with the full pp quasi-Hamiltonian h^Ω = h^(2),HF + hcorr
+    (Eq. h-om-pp-def; hcorr here as a Kronecker matrix product) and conjugated 𝒢,
+    equals the separated form of Eq. (g2-eq-tpp-lambda) that the oracle evaluates
+    (complex w: pins the index order of w as well)."""
+    rng = np.random.default_rng(32)
+    nb = 5
+    h = inputs.random_hermitian(nb, rng)
+    w = sym_w(nb, rng)
+    n, g2 = inputs.random_state(nb, rng, soa=True)
+    prob = O.Problem(h, w, selfenergy=O.TPP)
+    _, got = O.rhs(prob, 0.0, n, g2)
+    hhf = O.hf_hamiltonian(h, w, n)
+    eye = np.eye(nb)
+    h2 = np.einsum("jl,ik->ijkl", eye, hhf) + np.einsum("ik,jl->ijkl", eye, hhf)   # Eq. (twopart_hamiltonian)
+    # hcorr as the nb^2 x nb^2 matrix (iħ)^2 (G^> ⊗ G^> - G^< ⊗ G^<) W, W_(pq),(kl) = w_pqkl
+    gl, gg = 1j * n, 1j * n - 1j * eye
+    hc = (1j ** 2) * (np.kron(gg, gg) - np.kron(gl, gl)) @ w.reshape(nb * nb, nb * nb)
+    hom = h2 + hc.reshape((nb,) * 4)
+    full = O.psi_source(O.w_antisym(w), n) + np.einsum("ijpq,klpq->ijkl", hom, g2.conj()) \
+        - np.einsum("ijpq,klpq->ijkl", g2, hom.conj())
+    assert np.abs(-1j * full - got).max() < 1e-12 * np.abs(got).max()
+
+
+@pytest.mark.parametrize("se", ["HF", "SOA", "GW", "GWX", "TPP"])
 def test_conservation_laws(se):
     """Particle number to round-off; energy to O(dt^4) (Sec. VIII: energy conserving)."""
     L = 3
@@ -351,7 +392,7 @@ def test_conservation_laws(se):
         # 𝒢 symmetries of Eqs. (Gsymm_a/b)
         assert np.abs(g2 - g2.transpose(1, 0, 3, 2)).max() < 1e-14
         assert np.abs(g2 - g2.transpose(2, 3, 0, 1).conj()).max() < 1e-14
-        if se == "SOA":
+        if se in ("SOA", "TPP"):
             assert np.abs(g2 + g2.transpose(0, 1, 3, 2)).max() < 1e-14
     if se == "HF":
         assert drifts[1] < 1e-8
