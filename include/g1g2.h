@@ -52,8 +52,11 @@ typedef enum {
   G1G2_HF = 0,   /* I = 0, G2 frozen: time-dependent Hartree-Fock (Eq. eom_gone-2 without I) */
   G1G2_SOA = 1,  /* second-order Born, Sec. III.C, Eq. (result_eom_soa) */
   G1G2_GW = 2,   /* GW, Sec. IV.C, Eq. (g2-eq-gw-pi) */
-  G1G2_GW_EXCHANGE = 3  /* GW with exchange: Psi replaced by Psi^± in Eq. (g2-eq-gw-pi)
+  G1G2_GW_EXCHANGE = 3, /* GW with exchange: Psi replaced by Psi^± in Eq. (g2-eq-gw-pi)
                            (end of Sec. IV.C); spin-orbital basis only */
+  G1G2_TPP = 4          /* particle-particle T matrix, Sec. IV.D, Eq. (g2-eq-tpp-lambda): the SOA
+                           equation plus the ladder term Lambda - (Lambda_klij)^*, Lambda = hcorr G2
+                           (Eqs. HTPPcorr, lambdapp); FP64 form only */
 } g1g2_selfenergy;
 
 /* Arithmetic of the contractions. The RK4 state update, the Hartree-Fock

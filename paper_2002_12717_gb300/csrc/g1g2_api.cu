@@ -161,6 +161,9 @@ struct StageOut {
   cplx *Gy, *Gys, *Gacc, *Gk;
 };
 
+void mode_left1(g1g2_ctx *c, Launcher &L, const cplx *S, const cplx *X, cplx *out, cplx alpha, double beta);
+void mode_left2(g1g2_ctx *c, Launcher &L, const cplx *S, const cplx *X, cplx *out, cplx alpha, double beta);
+
 void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *G_in, Rk4Stage st,
               const StageOut &o, bool w_only = false) {
   const int nb = c->nb;
@@ -264,6 +267,24 @@ void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *
     g.A = c->nbar; g.sa_m = N; g.sa_k = 1;
     g.B = c->T1; g.sb_k = N3; g.sb_n = 1;
     g.C = c->Ab; g.sc_m = N3; g.sc_n = 1;
+    zgemm(L, g);
+  }
+  if (c->se == G1G2_TPP) {
+    // Eq. (HTPPcorr) with G^> = -i nbar, G^< = i n: hcorr = (nbar (x) nbar - n (x) n) w
+    const cplx one{1.0, 0.0}, mone{-1.0, 0.0};
+    mode_left2(c, L, c->nbar, c->w, c->T1, one, 0.0);    // T1_ijkl = sum_q nbar_jq w_iqkl
+    mode_left1(c, L, c->nbar, c->T1, c->Hb, one, 0.0);   // Hb_ijkl = sum_p nbar_ip T1_pjkl
+    mode_left2(c, L, n_in, c->w, c->T1, one, 0.0);
+    mode_left1(c, L, n_in, c->T1, c->Hb, mone, 1.0);
+    // Eq. (lambdapp): Lambda = hcorr G2 as an (ij),(pq) x (pq),(kl) product.  The source term
+    // is Psi = -A + A^dag, so Psi + Lambda - Lambda^dag = -(A - Lambda) + (A - Lambda)^dag:
+    // subtract Lambda from A and let the assembly do the rest
+    ZGemm g;
+    g.M = (int)N2; g.N = (int)N2; g.K = (int)N2;
+    g.A = c->Hb; g.sa_m = N2; g.sa_k = 1;
+    g.B = G_in; g.sb_k = N2; g.sb_n = 1;
+    g.C = c->Ab; g.sc_m = N2; g.sc_n = 1;
+    g.alpha = mone; g.beta = 1.0;
     zgemm(L, g);
   }
   if (c->se == G1G2_GW) {
@@ -649,7 +670,9 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   if (opt_in) opt = *opt_in;
   if (nb < 1 || nb > 128) return fail(G1G2_EINVAL, "nb must be in [1, 128]");
   if (!h || !w || !G1_0) return fail(G1G2_EINVAL, "h, w and G1_0 must be non-NULL");
-  if (se < G1G2_HF || se > G1G2_GW_EXCHANGE) return fail(G1G2_EINVAL, "bad selfenergy");
+  if (se < G1G2_HF || se > G1G2_TPP) return fail(G1G2_EINVAL, "bad selfenergy");
+  if (se == G1G2_TPP && opt.precision != G1G2_FP64)
+    return fail(G1G2_EUNSUPPORTED, "the T-matrix ladder term runs on the FP64 form");
   // GW with exchange is GW with the source term Psi^± (w^- in Psi)
   const bool gw_exchange = se == G1G2_GW_EXCHANGE;
   if (gw_exchange) se = G1G2_GW;
@@ -720,7 +743,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   }
   c->w_real = real;
   // source interaction: w^- (SOA, spin-orbital), else w
-  const bool use_minus = (se == G1G2_SOA || gw_exchange) && !restricted;
+  const bool use_minus = (se == G1G2_SOA || se == G1G2_TPP || gw_exchange) && !restricted;
   for (size_t i = 0; i < N; ++i)
     for (size_t j = 0; j < N; ++j)
       for (size_t k = 0; k < N; ++k)
@@ -770,6 +793,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
           (rc = dalloc(c, &c->Pp, N4)))
         return bail(rc);
     }
+    if (se == G1G2_TPP && (rc = dalloc(c, &c->Hb, N4))) return bail(rc);
   }
   // uploads
   auto up = [&](void *dst, const void *src, size_t bytes) {
@@ -934,7 +958,8 @@ int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_de
   if (!c || !n_dev || !G2_dev || !dn_bar || !dG2_bar || !n_bar || !G2_bar || !h_bar)
     return fail(G1G2_EINVAL, "NULL argument");
   if (c->prec != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product runs on the FP64 form");
-  if (c->se == G1G2_GW) return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product covers HF and SOA");
+  if (c->se != G1G2_SOA && c->se != G1G2_HF)
+    return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product covers HF and SOA");
   const long long N2 = (long long)c->nb * c->nb, N4 = N2 * N2;
   if (!c->AE) {  // scratch of the adjoint
     void *p;
@@ -1026,7 +1051,7 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
                  double *grad_drive, double *grad_wscale, double *grad_h) {
   if (!c || nsteps < 1 || !J_out) return fail(G1G2_EINVAL, "bad adjoint argument");
   if (c->prec != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint runs on the FP64 form");
-  if (c->se == G1G2_GW) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers HF and SOA");
+  if (c->se != G1G2_SOA && c->se != G1G2_HF) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers HF and SOA");
   if (objective < 0 || objective > 2) return fail(G1G2_EINVAL, "objective must be 0, 1 or 2");
   if (objective == 0 && (c->basis != G1G2_SPIN_ORBITAL || c->nb % 2))
     return fail(G1G2_EINVAL, "double occupancy needs a spin-orbital basis with index 2*site+spin");

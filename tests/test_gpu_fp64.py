@@ -31,6 +31,7 @@ CASES = [
     ("SOA", 17, False, False), ("SOA", 33, False, False), ("SOA", 8, True, False), ("SOA", 13, True, False),
     ("GW", 2, False, False), ("GW", 7, False, True), ("GW", 17, False, False), ("GW", 33, False, False),
     ("GWX", 7, False, True), ("GWX", 17, False, False),
+    ("TPP", 6, False, True), ("TPP", 17, False, False), ("TPP", 9, True, False),
 ]
 
 
@@ -120,3 +121,21 @@ def test_state_roundtrip_and_launch_count():
         p.set_state(2.5, n, None)
         t, n2, gz = p.get_state()
         assert t == 2.5 and np.abs(gz).max() == 0.0
+
+
+def test_tpp_propagation_matches_oracle():
+    """Particle-particle T matrix: 3-site Hubbard chain in the spin-orbital basis,
+    100 RK4 steps on the GPU against the oracle (state and energy)."""
+    from paper_2002_12717_gb300.g1g2 import Propagator
+    L = 3
+    hs = inputs.chain_hopping(L)
+    hs[0, 0] += 2.0
+    h, w = inputs.spin_orbital_h(hs), inputs.spin_orbital_hubbard_w(L, 1.0)
+    n0 = np.kron(np.diag([0.8, 0.5, 0.2]), np.eye(2)).astype(np.complex128)
+    prob = O.Problem(h, w, "TPP")
+    n_ref, g_ref, _, obs_ref = O.propagate(prob, n0, np.zeros((2 * L,) * 4), 0.02, 100, obs_every=100)
+    with Propagator(h, w, n0, None, "TPP", "fp64") as p:
+        obs, _ = p.propagate(0.02, 100, 100)
+        _, n, g = p.get_state()
+    assert np.abs(n - n_ref).max() < 1e-12 and np.abs(g - g_ref).max() < 1e-12
+    assert abs(obs[-1]["e_total"] - obs_ref[-1]["e_total"]) < 1e-12
