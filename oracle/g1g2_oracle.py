@@ -48,6 +48,7 @@ SOA = "SOA"
 GW = "GW"
 GWX = "GWX"   # GW with the exchange source term Psi^± (end of Sec. IV.C)
 TPP = "TPP"   # particle-particle T matrix, Sec. IV.D, Eq. (g2-eq-tpp-lambda)
+TPH = "TPH"   # particle-hole T matrix, Sec. IV.E, Eq. (g2-eq-tph-lambda)
 HF = "HF"
 
 
@@ -173,6 +174,20 @@ def tpp_ladder(hcorr, G2):
     return einsum("ijpq,pqkl->ijkl", hcorr, G2)
 
 
+def tph_hcorr(w, n):
+    """Correlation part of the ph quasi-Hamiltonian, Eq. (HTPHcorr):
+    hcorr_ijkl = (iħ)^2 Σ_pq [G^{F,>}_iqlp - G^{F,<}_iqlp] w_pjkq, with the
+    equal-time exchange product of Eq. (g2f-def), G^{F,≷}_iqlp = G^≷_ip G^≶_ql
+    (the second factor is the opposite component)."""
+    gl, gg = g_less(n), g_greater(n)
+    return (1j ** 2) * (einsum("ip,ql,pjkq->ijkl", gg, gl, w) - einsum("ip,ql,pjkq->ijkl", gl, gg, w))
+
+
+def tph_ladder(hcorr, G2):
+    """Particle-hole ladder term, Eq. (lambdaph): Λ_ijkl = Σ_pq hcorr_ipql 𝒢_qjkp."""
+    return einsum("ipql,qjkp->ijkl", hcorr, G2)
+
+
 # ---------------------------------------------------------------------------
 # The closed systems: SOA (Sec. III.C), GW (Sec. IV.C), HF (I = 0)
 # ---------------------------------------------------------------------------
@@ -208,6 +223,7 @@ def rhs(prob: Problem, t, n, G2):
         GW  Eq. (g2-eq-gw-pi):  i d𝒢/dt = [h2, 𝒢] + Psi + Π_ijkl - (Π_lkji)^*;
         GWX: the same with Psi replaced by Psi^± (end of Sec. IV.C);
         TPP Eq. (g2-eq-tpp-lambda): i d𝒢/dt = [h2, 𝒢] + Psi^± + Λ_ijkl - (Λ_klij)^*;
+        TPH Eq. (g2-eq-tph-lambda): the same with the particle-hole ladder term;
         HF: 𝒢 is not propagated (collision integral zero).
     """
     hhf = hf_hamiltonian(prob.h_of_t(t), prob.w, n, prob.restricted)
@@ -220,8 +236,9 @@ def rhs(prob: Problem, t, n, G2):
     if prob.selfenergy in (GW, GWX):
         pi = gw_polarisation(gw_hcorr(prob.w, n), G2)
         rhs2 = rhs2 + pi - pi.transpose(3, 2, 1, 0).conj()
-    elif prob.selfenergy == TPP:
-        lam = tpp_ladder(tpp_hcorr(prob.w, n), G2)
+    elif prob.selfenergy in (TPP, TPH):
+        lam = tpp_ladder(tpp_hcorr(prob.w, n), G2) if prob.selfenergy == TPP else \
+            tph_ladder(tph_hcorr(prob.w, n), G2)
         rhs2 = rhs2 + lam - lam.transpose(2, 3, 0, 1).conj()
     return dn, -1j * rhs2
 

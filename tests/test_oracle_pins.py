@@ -374,7 +374,51 @@ def test_tpp_separated_form_equals_full_quasi_hamiltonian_form():
     assert np.abs(-1j * full - got).max() < 1e-12 * np.abs(got).max()
 
 
-@pytest.mark.parametrize("se", ["HF", "SOA", "GW", "GWX", "TPP"])
+def test_tph_ladder_matches_lambdaph_hubbard():
+    """The general particle-hole ladder term (Eqs. HTPHcorr, lambdaph) with the
+    spin-restricted on-site interaction equals the printed Hubbard form, Eq.
+    (lambdaph_hubb): Λ_ijkl = (iħ)^2 U Σ_p [G^>_ip G^<_pl - G^<_ip G^>_pl] 𝒢_pjkp.
+    Pins the mixed G^>/G^< exchange product and the index placement."""
+    rng = np.random.default_rng(41)
+    nb, U = 6, 1.3
+    w = inputs.onsite_w_restricted(nb, U).astype(np.complex128)
+    n = inputs.random_hermitian(nb, rng) * 0.3 + 0.5 * np.eye(nb)
+    g2 = rng.standard_normal((nb,) * 4) + 1j * rng.standard_normal((nb,) * 4)
+    got = O.tph_ladder(O.tph_hcorr(w, n), g2)
+    gl, gg = 1j * n, 1j * n - 1j * np.eye(nb)
+    printed = (1j ** 2) * U * (np.einsum("ip,pl,pjkp->ijkl", gg, gl, g2) - np.einsum("ip,pl,pjkp->ijkl", gl, gg, g2))
+    assert np.abs(got - printed).max() < 1e-13 * max(1.0, np.abs(printed).max())
+
+
+def test_tph_separated_form_equals_full_quasi_hamiltonian_form():
+    """Eq. (g2-eq-tph) with the full ph quasi-Hamiltonian (Eq. homph-def: the HF part
+    δ_jl h_ik - δ_ik h_jl plus hcorr, here summed over p, q in plain loops of the
+    printed index pattern) equals the separated form of Eq. (g2-eq-tph-lambda)."""
+    rng = np.random.default_rng(42)
+    nb = 4
+    h = inputs.random_hermitian(nb, rng)
+    w = sym_w(nb, rng)
+    n, g2 = inputs.random_state(nb, rng, soa=False)
+    _, got = O.rhs(O.Problem(h, w, selfenergy=O.TPH), 0.0, n, g2)
+    hhf = O.hf_hamiltonian(h, w, n)
+    gl, gg = 1j * n, 1j * n - 1j * np.eye(nb)
+    hom = np.zeros((nb,) * 4, dtype=np.complex128)
+    for i in range(nb):
+        for j in range(nb):
+            for k in range(nb):
+                for l in range(nb):
+                    v = (hhf[i, k] if j == l else 0) - (hhf[j, l] if i == k else 0)
+                    for p in range(nb):
+                        for q in range(nb):
+                            # G^{F,>}_iqlp - G^{F,<}_iqlp = G^>_ip G^<_ql - G^<_ip G^>_ql
+                            v += (1j ** 2) * (gg[i, p] * gl[q, l] - gl[i, p] * gg[q, l]) * w[p, j, k, q]
+                    hom[i, j, k, l] = v
+    full = O.psi_source(O.w_antisym(w), n) + np.einsum("ipql,kpqj->ijkl", hom, g2.conj()) \
+        - np.einsum("ipql,kpqj->ijkl", g2, hom.conj())
+    assert np.abs(-1j * full - got).max() < 1e-12 * np.abs(got).max()
+
+
+@pytest.mark.parametrize("se", ["HF", "SOA", "GW", "GWX", "TPP", "TPH"])
 def test_conservation_laws(se):
     """Particle number to round-off; energy to O(dt^4) (Sec. VIII: energy conserving)."""
     L = 3
