@@ -54,9 +54,12 @@ typedef enum {
   G1G2_GW = 2,   /* GW, Sec. IV.C, Eq. (g2-eq-gw-pi) */
   G1G2_GW_EXCHANGE = 3, /* GW with exchange: Psi replaced by Psi^± in Eq. (g2-eq-gw-pi)
                            (end of Sec. IV.C); spin-orbital basis only */
-  G1G2_TPP = 4          /* particle-particle T matrix, Sec. IV.D, Eq. (g2-eq-tpp-lambda): the SOA
+  G1G2_TPP = 4,         /* particle-particle T matrix, Sec. IV.D, Eq. (g2-eq-tpp-lambda): the SOA
                            equation plus the ladder term Lambda - (Lambda_klij)^*, Lambda = hcorr G2
                            (Eqs. HTPPcorr, lambdapp); FP64 form only */
+  G1G2_TPH = 5          /* particle-hole T matrix, Sec. IV.E, Eq. (g2-eq-tph-lambda): the same with
+                           Lambda_ijkl = sum_pq hcorr_ipql G2_qjkp (Eqs. HTPHcorr, lambdaph); FP64
+                           form only */
 } g1g2_selfenergy;
 
 /* Arithmetic of the contractions. The RK4 state update, the Hartree-Fock

@@ -163,6 +163,7 @@ struct StageOut {
 
 void mode_left1(g1g2_ctx *c, Launcher &L, const cplx *S, const cplx *X, cplx *out, cplx alpha, double beta);
 void mode_left2(g1g2_ctx *c, Launcher &L, const cplx *S, const cplx *X, cplx *out, cplx alpha, double beta);
+void mode_right4(g1g2_ctx *c, Launcher &L, const cplx *X, const cplx *S, cplx *out, cplx alpha, double beta);
 
 void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *G_in, Rk4Stage st,
               const StageOut &o, bool w_only = false) {
@@ -286,6 +287,30 @@ void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *
     g.C = c->Ab; g.sc_m = N2; g.sc_n = 1;
     g.alpha = mone; g.beta = 1.0;
     zgemm(L, g);
+  }
+  if (c->se == G1G2_TPH) {
+    // Eq. (HTPHcorr) with G^> = -i nbar, G^< = i n: hcorr_ijkl = sum_pq (n_ip nbar_ql - nbar_ip n_ql) w_pjkq
+    const cplx one{1.0, 0.0}, mone{-1.0, 0.0};
+    mode_left1(c, L, n_in, c->w, c->T1, one, 0.0);       // T1_ijkq = sum_p n_ip w_pjkq
+    mode_right4(c, L, c->T1, c->nbar, c->Hb, one, 0.0);  // Hb_ijkl = sum_q T1_ijkq nbar_ql
+    mode_left1(c, L, c->nbar, c->w, c->T1, one, 0.0);
+    mode_right4(c, L, c->T1, n_in, c->Hb, mone, 1.0);
+    // Eq. (lambdaph): Lambda_ijkl = sum_pq hcorr_ipql G2_qjkp as (il),(pq) x (pq),(jk)
+    const int pH[4] = {0, 2, 3, 1};  // Hp[i][l][p][q] = hcorr[i][p][q][l]
+    permute4(L, nb, c->Hb, c->Hp, pH, one, 0.0, false);
+    const int pG[4] = {1, 2, 3, 0};  // Gp[p][q][j][k] = G[q][j][k][p]
+    permute4(L, nb, G_in, c->Gp, pG, one, 0.0, false);
+    {
+      ZGemm g;
+      g.M = (int)N2; g.N = (int)N2; g.K = (int)N2;
+      g.A = c->Hp; g.sa_m = N2; g.sa_k = 1;
+      g.B = c->Gp; g.sb_k = N2; g.sb_n = 1;
+      g.C = c->Pp; g.sc_m = N2; g.sc_n = 1;
+      zgemm(L, g);
+    }
+    // A -= Lambda (as for the pp ladder term), Pp[i][l][j][k] = Lambda_ijkl
+    const int pL[4] = {0, 3, 1, 2};
+    permute4(L, nb, c->Pp, c->Ab, pL, mone, 1.0, false);
   }
   if (c->se == G1G2_GW) {
     // a5: hcorr_ijkl = sum_p w_ijkp n_pl - sum_q n_jq w_iqkl (Eq. gwhcorr with the exchange symmetry of w)
@@ -670,8 +695,8 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   if (opt_in) opt = *opt_in;
   if (nb < 1 || nb > 128) return fail(G1G2_EINVAL, "nb must be in [1, 128]");
   if (!h || !w || !G1_0) return fail(G1G2_EINVAL, "h, w and G1_0 must be non-NULL");
-  if (se < G1G2_HF || se > G1G2_TPP) return fail(G1G2_EINVAL, "bad selfenergy");
-  if (se == G1G2_TPP && opt.precision != G1G2_FP64)
+  if (se < G1G2_HF || se > G1G2_TPH) return fail(G1G2_EINVAL, "bad selfenergy");
+  if ((se == G1G2_TPP || se == G1G2_TPH) && opt.precision != G1G2_FP64)
     return fail(G1G2_EUNSUPPORTED, "the T-matrix ladder term runs on the FP64 form");
   // GW with exchange is GW with the source term Psi^± (w^- in Psi)
   const bool gw_exchange = se == G1G2_GW_EXCHANGE;
@@ -743,7 +768,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   }
   c->w_real = real;
   // source interaction: w^- (SOA, spin-orbital), else w
-  const bool use_minus = (se == G1G2_SOA || se == G1G2_TPP || gw_exchange) && !restricted;
+  const bool use_minus = (se == G1G2_SOA || se == G1G2_TPP || se == G1G2_TPH || gw_exchange) && !restricted;
   for (size_t i = 0; i < N; ++i)
     for (size_t j = 0; j < N; ++j)
       for (size_t k = 0; k < N; ++k)
@@ -788,7 +813,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
       return bail(rc);
     c->splits = 4 * 152;
     if ((rc = dalloc(c, &c->partial, (size_t)c->splits * N2))) return bail(rc);
-    if (se == G1G2_GW) {
+    if (se == G1G2_GW || se == G1G2_TPH) {
       if ((rc = dalloc(c, &c->Hb, N4)) || (rc = dalloc(c, &c->Gp, N4)) || (rc = dalloc(c, &c->Hp, N4)) ||
           (rc = dalloc(c, &c->Pp, N4)))
         return bail(rc);

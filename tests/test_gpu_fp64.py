@@ -32,6 +32,7 @@ CASES = [
     ("GW", 2, False, False), ("GW", 7, False, True), ("GW", 17, False, False), ("GW", 33, False, False),
     ("GWX", 7, False, True), ("GWX", 17, False, False),
     ("TPP", 6, False, True), ("TPP", 17, False, False), ("TPP", 9, True, False),
+    ("TPH", 6, False, True), ("TPH", 17, False, False), ("TPH", 9, True, False),
 ]
 
 
@@ -123,8 +124,9 @@ def test_state_roundtrip_and_launch_count():
         assert t == 2.5 and np.abs(gz).max() == 0.0
 
 
-def test_tpp_propagation_matches_oracle():
-    """Particle-particle T matrix: 3-site Hubbard chain in the spin-orbital basis,
+@pytest.mark.parametrize("se", ["TPP", "TPH"])
+def test_t_matrix_propagation_matches_oracle(se):
+    """T-matrix selfenergies: 3-site Hubbard chain in the spin-orbital basis,
     100 RK4 steps on the GPU against the oracle (state and energy)."""
     from paper_2002_12717_gb300.g1g2 import Propagator
     L = 3
@@ -132,9 +134,9 @@ def test_tpp_propagation_matches_oracle():
     hs[0, 0] += 2.0
     h, w = inputs.spin_orbital_h(hs), inputs.spin_orbital_hubbard_w(L, 1.0)
     n0 = np.kron(np.diag([0.8, 0.5, 0.2]), np.eye(2)).astype(np.complex128)
-    prob = O.Problem(h, w, "TPP")
+    prob = O.Problem(h, w, se)
     n_ref, g_ref, _, obs_ref = O.propagate(prob, n0, np.zeros((2 * L,) * 4), 0.02, 100, obs_every=100)
-    with Propagator(h, w, n0, None, "TPP", "fp64") as p:
+    with Propagator(h, w, n0, None, se, "fp64") as p:
         obs, _ = p.propagate(0.02, 100, 100)
         _, n, g = p.get_state()
     assert np.abs(n - n_ref).max() < 1e-12 and np.abs(g - g_ref).max() < 1e-12
