@@ -57,9 +57,12 @@ typedef enum {
   G1G2_TPP = 4,         /* particle-particle T matrix, Sec. IV.D, Eq. (g2-eq-tpp-lambda): the SOA
                            equation plus the ladder term Lambda - (Lambda_klij)^*, Lambda = hcorr G2
                            (Eqs. HTPPcorr, lambdapp); FP64 form only */
-  G1G2_TPH = 5          /* particle-hole T matrix, Sec. IV.E, Eq. (g2-eq-tph-lambda): the same with
+  G1G2_TPH = 5,         /* particle-hole T matrix, Sec. IV.E, Eq. (g2-eq-tph-lambda): the same with
                            Lambda_ijkl = sum_pq hcorr_ipql G2_qjkp (Eqs. HTPHcorr, lambdaph); FP64
                            form only */
+  G1G2_DSL = 6          /* dynamically screened ladder, Sec. V, Eq. (g2-dsl-equation-pi-lambda):
+                           Psi^± plus the GW term Pi - (Pi_lkji)^* plus the ladder term with
+                           Lambda = Lambda^pp + Lambda^ph; spin-orbital basis, FP64 form only */
 } g1g2_selfenergy;
 
 /* Arithmetic of the contractions. The RK4 state update, the Hartree-Fock

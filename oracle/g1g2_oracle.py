@@ -49,6 +49,7 @@ GW = "GW"
 GWX = "GWX"   # GW with the exchange source term Psi^± (end of Sec. IV.C)
 TPP = "TPP"   # particle-particle T matrix, Sec. IV.D, Eq. (g2-eq-tpp-lambda)
 TPH = "TPH"   # particle-hole T matrix, Sec. IV.E, Eq. (g2-eq-tph-lambda)
+DSL = "DSL"   # dynamically screened ladder, Sec. V, Eq. (g2-dsl-equation-pi-lambda)
 HF = "HF"
 
 
@@ -202,7 +203,7 @@ class Problem:
         self.restricted = restricted
         self.D = None if D is None else np.asarray(D, dtype=np.complex128)
         self.drive = drive  # callable f(t) -> float, or None
-        if restricted and selfenergy in (GW, GWX):
+        if restricted and selfenergy in (GW, GWX, DSL):
             raise ValueError("GW couples same-spin components; no spin-restricted form")
         # source-term interaction: Psi^- for SOA in a spin-orbital basis and for
         # GW with exchange (Psi replaced by Psi^±, end of Sec. IV.C), plain w for
@@ -224,6 +225,8 @@ def rhs(prob: Problem, t, n, G2):
         GWX: the same with Psi replaced by Psi^± (end of Sec. IV.C);
         TPP Eq. (g2-eq-tpp-lambda): i d𝒢/dt = [h2, 𝒢] + Psi^± + Λ_ijkl - (Λ_klij)^*;
         TPH Eq. (g2-eq-tph-lambda): the same with the particle-hole ladder term;
+        DSL Eq. (g2-dsl-equation-pi-lambda): Psi^± plus the GW polarisation term and
+            both ladder terms, each once;
         HF: 𝒢 is not propagated (collision integral zero).
     """
     hhf = hf_hamiltonian(prob.h_of_t(t), prob.w, n, prob.restricted)
@@ -233,12 +236,15 @@ def rhs(prob: Problem, t, n, G2):
     I = collision_integral(prob.w, G2)
     dn = g1_rhs(hhf, n, I)
     rhs2 = two_particle_commutator(hhf, G2) + psi_source(prob.w_source, n)
-    if prob.selfenergy in (GW, GWX):
+    if prob.selfenergy in (GW, GWX, DSL):
         pi = gw_polarisation(gw_hcorr(prob.w, n), G2)
         rhs2 = rhs2 + pi - pi.transpose(3, 2, 1, 0).conj()
-    elif prob.selfenergy in (TPP, TPH):
-        lam = tpp_ladder(tpp_hcorr(prob.w, n), G2) if prob.selfenergy == TPP else \
-            tph_ladder(tph_hcorr(prob.w, n), G2)
+    if prob.selfenergy in (TPP, TPH, DSL):
+        lam = np.zeros_like(G2)
+        if prob.selfenergy in (TPP, DSL):
+            lam = lam + tpp_ladder(tpp_hcorr(prob.w, n), G2)
+        if prob.selfenergy in (TPH, DSL):
+            lam = lam + tph_ladder(tph_hcorr(prob.w, n), G2)
         rhs2 = rhs2 + lam - lam.transpose(2, 3, 0, 1).conj()
     return dn, -1j * rhs2
 

@@ -270,7 +270,7 @@ void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *
     g.C = c->Ab; g.sc_m = N3; g.sc_n = 1;
     zgemm(L, g);
   }
-  if (c->se == G1G2_TPP) {
+  if (c->se == G1G2_TPP || c->se == G1G2_DSL) {
     // Eq. (HTPPcorr) with G^> = -i nbar, G^< = i n: hcorr = (nbar (x) nbar - n (x) n) w
     const cplx one{1.0, 0.0}, mone{-1.0, 0.0};
     mode_left2(c, L, c->nbar, c->w, c->T1, one, 0.0);    // T1_ijkl = sum_q nbar_jq w_iqkl
@@ -288,7 +288,7 @@ void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *
     g.alpha = mone; g.beta = 1.0;
     zgemm(L, g);
   }
-  if (c->se == G1G2_TPH) {
+  if (c->se == G1G2_TPH || c->se == G1G2_DSL) {
     // Eq. (HTPHcorr) with G^> = -i nbar, G^< = i n: hcorr_ijkl = sum_pq (n_ip nbar_ql - nbar_ip n_ql) w_pjkq
     const cplx one{1.0, 0.0}, mone{-1.0, 0.0};
     mode_left1(c, L, n_in, c->w, c->T1, one, 0.0);       // T1_ijkq = sum_p n_ip w_pjkq
@@ -312,7 +312,7 @@ void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *
     const int pL[4] = {0, 3, 1, 2};
     permute4(L, nb, c->Pp, c->Ab, pL, mone, 1.0, false);
   }
-  if (c->se == G1G2_GW) {
+  if (c->se == G1G2_GW || c->se == G1G2_DSL) {
     // a5: hcorr_ijkl = sum_p w_ijkp n_pl - sum_q n_jq w_iqkl (Eq. gwhcorr with the exchange symmetry of w)
     {
       ZGemm g;
@@ -695,8 +695,8 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   if (opt_in) opt = *opt_in;
   if (nb < 1 || nb > 128) return fail(G1G2_EINVAL, "nb must be in [1, 128]");
   if (!h || !w || !G1_0) return fail(G1G2_EINVAL, "h, w and G1_0 must be non-NULL");
-  if (se < G1G2_HF || se > G1G2_TPH) return fail(G1G2_EINVAL, "bad selfenergy");
-  if ((se == G1G2_TPP || se == G1G2_TPH) && opt.precision != G1G2_FP64)
+  if (se < G1G2_HF || se > G1G2_DSL) return fail(G1G2_EINVAL, "bad selfenergy");
+  if ((se == G1G2_TPP || se == G1G2_TPH || se == G1G2_DSL) && opt.precision != G1G2_FP64)
     return fail(G1G2_EUNSUPPORTED, "the T-matrix ladder term runs on the FP64 form");
   // GW with exchange is GW with the source term Psi^± (w^- in Psi)
   const bool gw_exchange = se == G1G2_GW_EXCHANGE;
@@ -704,7 +704,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   if (opt.precision != G1G2_FP64 && opt.precision != G1G2_TF32X3 && opt.precision != G1G2_BF16X4)
     return fail(G1G2_EINVAL, "bad precision");
   if (opt.basis != G1G2_SPIN_ORBITAL && opt.basis != G1G2_SPIN_RESTRICTED) return fail(G1G2_EINVAL, "bad basis");
-  if (opt.basis == G1G2_SPIN_RESTRICTED && se == G1G2_GW)
+  if (opt.basis == G1G2_SPIN_RESTRICTED && (se == G1G2_GW || se == G1G2_DSL))
     return fail(G1G2_EINVAL, "GW couples same-spin components and has no spin-restricted form");
 
   const size_t N = nb, N2 = N * N, N4 = N2 * N2;
@@ -768,7 +768,8 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   }
   c->w_real = real;
   // source interaction: w^- (SOA, spin-orbital), else w
-  const bool use_minus = (se == G1G2_SOA || se == G1G2_TPP || se == G1G2_TPH || gw_exchange) && !restricted;
+  const bool use_minus =
+      (se == G1G2_SOA || se == G1G2_TPP || se == G1G2_TPH || se == G1G2_DSL || gw_exchange) && !restricted;
   for (size_t i = 0; i < N; ++i)
     for (size_t j = 0; j < N; ++j)
       for (size_t k = 0; k < N; ++k)
@@ -813,7 +814,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
       return bail(rc);
     c->splits = 4 * 152;
     if ((rc = dalloc(c, &c->partial, (size_t)c->splits * N2))) return bail(rc);
-    if (se == G1G2_GW || se == G1G2_TPH) {
+    if (se == G1G2_GW || se == G1G2_TPH || se == G1G2_DSL) {
       if ((rc = dalloc(c, &c->Hb, N4)) || (rc = dalloc(c, &c->Gp, N4)) || (rc = dalloc(c, &c->Hp, N4)) ||
           (rc = dalloc(c, &c->Pp, N4)))
         return bail(rc);

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libg1g2.so")
 
 OK, EINVAL, ESYMM, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
-SELFENERGY = {"HF": 0, "SOA": 1, "GW": 2, "GWX": 3, "TPP": 4, "TPH": 5}
+SELFENERGY = {"HF": 0, "SOA": 1, "GW": 2, "GWX": 3, "TPP": 4, "TPH": 5, "DSL": 6}
 PRECISION = {"fp64": 0, "tf32x3": 1, "bf16x4": 2}
 
 

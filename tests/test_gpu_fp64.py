@@ -33,6 +33,7 @@ CASES = [
     ("GWX", 7, False, True), ("GWX", 17, False, False),
     ("TPP", 6, False, True), ("TPP", 17, False, False), ("TPP", 9, True, False),
     ("TPH", 6, False, True), ("TPH", 17, False, False), ("TPH", 9, True, False),
+    ("DSL", 1, False, False), ("DSL", 6, False, True), ("DSL", 17, False, False), ("DSL", 33, False, False),
 ]
 
 
@@ -124,9 +125,9 @@ def test_state_roundtrip_and_launch_count():
         assert t == 2.5 and np.abs(gz).max() == 0.0
 
 
-@pytest.mark.parametrize("se", ["TPP", "TPH"])
+@pytest.mark.parametrize("se", ["TPP", "TPH", "DSL"])
 def test_t_matrix_propagation_matches_oracle(se):
-    """T-matrix selfenergies: 3-site Hubbard chain in the spin-orbital basis,
+    """T-matrix and screened-ladder selfenergies: 3-site Hubbard chain in the spin-orbital basis,
     100 RK4 steps on the GPU against the oracle (state and energy)."""
     from paper_2002_12717_gb300.g1g2 import Propagator
     L = 3
@@ -141,3 +142,11 @@ def test_t_matrix_propagation_matches_oracle(se):
         _, n, g = p.get_state()
     assert np.abs(n - n_ref).max() < 1e-12 and np.abs(g - g_ref).max() < 1e-12
     assert abs(obs[-1]["e_total"] - obs_ref[-1]["e_total"]) < 1e-12
+
+
+def test_dsl_rejects_the_spin_restricted_basis_and_tensor_core_forms():
+    from paper_2002_12717_gb300.g1g2 import G1G2Error, Propagator
+    h, w, n, g2, _, _ = problem(6, "DSL", seed=2, drive=False)
+    for kw in (dict(restricted=True), dict(precision="bf16x4"), dict(precision="tf32x3")):
+        with pytest.raises(G1G2Error):
+            Propagator(h, w, n, g2, "DSL", **kw)

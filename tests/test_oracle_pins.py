@@ -418,7 +418,33 @@ def test_tph_separated_form_equals_full_quasi_hamiltonian_form():
     assert np.abs(-1j * full - got).max() < 1e-12 * np.abs(got).max()
 
 
-@pytest.mark.parametrize("se", ["HF", "SOA", "GW", "GWX", "TPP", "TPH"])
+def test_dsl_equals_printed_quasi_hamiltonian_form_and_is_additive():
+    """Eq. (g2-dsl-equation): Psi^± plus, for each of the GW, pp and ph quasi-Hamiltonians,
+    hcorr times conjugated 𝒢 minus its conjugate, in the index patterns printed there
+    (the third sum is over p, q), equals the Π/Λ form the oracle evaluates (Eq.
+    g2-dsl-equation-pi-lambda).  This also checks the GW polarisation term in its
+    conjugated form.  And each correlation term enters once: DSL - SOA is the sum of
+    (GWX - SOA), (TPP - SOA) and (TPH - SOA)."""
+    rng = np.random.default_rng(51)
+    nb = 4
+    h = inputs.random_hermitian(nb, rng)
+    w = sym_w(nb, rng)
+    n, g2 = inputs.random_state(nb, rng, soa=False)
+    _, got = O.rhs(O.Problem(h, w, selfenergy=O.DSL), 0.0, n, g2)
+    hhf = O.hf_hamiltonian(h, w, n)
+    he, hpp, hph = O.gw_hcorr(w, n), O.tpp_hcorr(w, n), O.tph_hcorr(w, n)
+    gc = g2.conj()
+    full = O.two_particle_commutator(hhf, g2) + O.psi_source(O.w_antisym(w), n)
+    full = full + np.einsum("qjpl,qkpi->ijkl", he, gc) - np.einsum("qjpl,qkpi->ijkl", g2, he.conj())
+    full = full + np.einsum("ijpq,klpq->ijkl", hpp, gc) - np.einsum("ijpq,klpq->ijkl", g2, hpp.conj())
+    full = full + np.einsum("ipql,kpqj->ijkl", hph, gc) - np.einsum("ipql,kpqj->ijkl", g2, hph.conj())
+    assert np.abs(-1j * full - got).max() < 1e-12 * np.abs(got).max()
+    parts = {se: O.rhs(O.Problem(h, w, selfenergy=se), 0.0, n, g2)[1] for se in (O.SOA, O.GWX, O.TPP, O.TPH)}
+    additive = parts[O.GWX] + parts[O.TPP] + parts[O.TPH] - 2 * parts[O.SOA]
+    assert np.abs(additive - got).max() < 1e-12 * np.abs(got).max()
+
+
+@pytest.mark.parametrize("se", ["HF", "SOA", "GW", "GWX", "TPP", "TPH", "DSL"])
 def test_conservation_laws(se):
     """Particle number to round-off; energy to O(dt^4) (Sec. VIII: energy conserving)."""
     L = 3
