@@ -9,7 +9,10 @@
  *   G1:  Eq. (eom_gone-2) with the collision integral of Eq. (eom_gone-I)
  *   G2:  Eq. (result_eom_soa) for SOA (source term Psi^-, Eq. psi-pm-def),
  *        Eq. (g2-eq-gw-pi) for GW (plain-w Psi plus the polarisation term
- *        of Eq. gwpi), nothing for HF (time-dependent Hartree-Fock).
+ *        of Eq. gwpi), the T-matrix ladder terms of Sec. IV.D/E and their
+ *        combination with GW (Sec. V), nothing for HF (time-dependent
+ *        Hartree-Fock).  g1g2_propagate_hfgkba runs the memory-integral
+ *        HF-GKBA the G1-G2 equations replace (Sec. III.B), for comparison.
  * Conventions: fermions, hbar = 1, h(t) = h + f(t) D.
  *
  * Layout of every complex array: row-major, interleaved (re, im) doubles.
@@ -31,6 +34,8 @@
  */
 #ifndef G1G2_H
 #define G1G2_H
+
+#include <stddef.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -145,6 +150,24 @@ int g1g2_step(g1g2_ctx *c, double dt);
  * Synchronises the stream at the end; checks the state for NaN/Inf at every
  * record (G1G2_ENONFINITE). */
 int g1g2_propagate(g1g2_ctx *c, double dt, int nsteps, int obs_every, g1g2_obs *obs, double *density);
+
+/* The original HF-GKBA in its memory-integral form (Sec. III.B), the scheme the
+ * G1-G2 equations replace: G2(t) = (i hbar)^3 int_{t0}^t dtb U2(t,tb) Psi(tb) U2(tb,t)
+ * (Eq. dtilde-solution-short, U2 = U (x) U by Eq. prop_two), with the Hartree-Fock
+ * propagators of the GKBA (Eqs. GKBA_propa/b), i hbar U(t,tb) = u(t) u(tb)^dag,
+ * i du/dt = hHF u.  Each evaluation of G2 sums over all earlier time steps (trapezoid
+ * rule), so nsteps steps cost O(nsteps^2) (Table I); n and u advance by Heun's method
+ * (second order), so the result converges to the G1-G2 one as dt^2.
+ *   c            SOA context in the FP64 form, nb <= 32, no drive (G1G2_EUNSUPPORTED
+ *                otherwise); its state must have G2 = 0 (uncorrelated start at the
+ *                context's time, G1G2_EINVAL otherwise)
+ *   G1_history   host, (nsteps+1)*nb*nb complex: n(t0 + m dt), m = 0..nsteps, or NULL
+ *   scratch_bytes  device memory for the batched history products (0: 256 MiB); the
+ *                history itself takes (nsteps+2) (nb^4 + 3 nb^2) complex doubles
+ * Allocates its scratch on each call (G1G2_ENOMEM when it does not fit) and frees it
+ * before returning.  On return the context holds n(T) and G2(T) from the memory
+ * integral and t = t0 + nsteps dt.  Synchronous. */
+int g1g2_propagate_hfgkba(g1g2_ctx *c, double dt, int nsteps, double *G1_history, size_t scratch_bytes);
 
 /* Observables of the current state (synchronous). density: nb doubles or NULL.
  * double_occ: nb/2 doubles or NULL, spin-orbital basis with index 2*site+spin only

@@ -797,3 +797,100 @@ void hf_build_t(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *x
 }
 
 }  // namespace g1g2
+
+// ---------------------------------------------------------------------------
+// Kernels of the memory-integral HF-GKBA (FP64)
+// ---------------------------------------------------------------------------
+namespace g1g2 {
+namespace {
+
+// out_b[m][i] = sum_p in_b[p][m] op(S_b[i][p]) with m = (q, r, s) running over the
+// trailing nb^3 entries: a mode-1 product whose new index i moves to the last place,
+// so four calls with S1..S4 apply S1 (x) S2 (x) S3 (x) S4 to the four indices and
+// return them in their original order.  One thread per (m, b); its nb inputs
+// in_b[p][m] are coalesced across the warp and held in registers.
+template <int NMAX>
+__global__ void __launch_bounds__(128) mode_rotate_kernel(int nb, const cplx *__restrict__ in,
+                                                          const cplx *__restrict__ S, int conjS,
+                                                          cplx *__restrict__ out) {
+  __shared__ cplx Ss[NMAX * NMAX];
+  const long long N3 = (long long)nb * nb * nb, N4 = N3 * nb;
+  const long long b = blockIdx.y;
+  const cplx *Sb = S + b * nb * nb;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    cplx v = Sb[e];
+    if (conjS) v.y = -v.y;
+    Ss[e] = v;
+  }
+  __syncthreads();
+  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= N3) return;
+  const cplx *ib = in + b * N4 + m;
+  cplx x[NMAX];
+#pragma unroll
+  for (int p = 0; p < NMAX; ++p) x[p] = (p < nb) ? ib[(long long)p * N3] : cplx{0.0, 0.0};
+  cplx *ob = out + b * N4 + m * nb;
+  for (int i = 0; i < nb; ++i) {
+    cplx acc = {0.0, 0.0};
+#pragma unroll
+    for (int p = 0; p < NMAX; ++p)
+      if (p < nb) acc = cfma(x[p], Ss[i * nb + p], acc);
+    ob[i] = acc;
+  }
+}
+
+__global__ void batch_sum_kernel(long long len, int nbatch, const cplx *__restrict__ x, double beta, cplx *out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
+    cplx s = (beta != 0.0) ? cscale(out[e], beta) : cplx{0.0, 0.0};
+    for (int b = 0; b < nbatch; ++b) s = cadd(s, x[(long long)b * len + e]);
+    out[e] = s;
+  }
+}
+
+__global__ void count_nonzero_kernel(const cplx *x, long long len, double *cnt) {
+  __shared__ double s[256];
+  double a = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    if (x[i].x != 0.0 || x[i].y != 0.0) a += 1.0;
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && s[0] != 0.0) atomicAdd(cnt, s[0]);
+}
+
+}  // namespace
+
+int mode_rotate_max_nb() { return 32; }
+
+void mode_rotate(Launcher &L, int nb, int batch, const cplx *in, const cplx *S, bool conjS, cplx *out) {
+  if (batch <= 0) return;
+  const long long N3 = (long long)nb * nb * nb;
+  dim3 grid((unsigned)((N3 + 127) / 128), (unsigned)batch);
+  L.before("hfgkba_mode_rotate");
+  if (nb <= 8)
+    mode_rotate_kernel<8><<<grid, 128, 0, L.stream>>>(nb, in, S, conjS ? 1 : 0, out);
+  else if (nb <= 16)
+    mode_rotate_kernel<16><<<grid, 128, 0, L.stream>>>(nb, in, S, conjS ? 1 : 0, out);
+  else
+    mode_rotate_kernel<32><<<grid, 128, 0, L.stream>>>(nb, in, S, conjS ? 1 : 0, out);
+  L.after_launch();
+}
+
+void batch_sum(Launcher &L, long long len, int nbatch, const cplx *x, double beta, cplx *out) {
+  L.before("hfgkba_batch_sum");
+  batch_sum_kernel<<<(unsigned)std::min<long long>((len + 255) / 256, 8192), 256, 0, L.stream>>>(len, nbatch, x, beta,
+                                                                                                 out);
+  L.after_launch();
+}
+
+void count_nonzero(Launcher &L, const cplx *x, long long len, double *cnt) {
+  const unsigned blocks = (unsigned)std::min<long long>((len + 255) / 256, 4096);
+  L.before("nonzero_count");
+  count_nonzero_kernel<<<blocks, 256, 0, L.stream>>>(x, len, cnt);
+  L.after_launch();
+}
+
+}  // namespace g1g2

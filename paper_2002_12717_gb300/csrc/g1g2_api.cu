@@ -165,6 +165,58 @@ void mode_left1(g1g2_ctx *c, Launcher &L, const cplx *S, const cplx *X, cplx *ou
 void mode_left2(g1g2_ctx *c, Launcher &L, const cplx *S, const cplx *X, cplx *out, cplx alpha, double beta);
 void mode_right4(g1g2_ctx *c, Launcher &L, const cplx *X, const cplx *S, cplx *out, cplx alpha, double beta);
 
+// a2: I_ij = -i sum_(lp) sum_k wP[lp][i][k] G[lp][j][k]   (Eq. eom_gone-I) into c->I
+void collision(g1g2_ctx *c, Launcher &L, const cplx *G_in) {
+  const long long N = c->nb, N2 = N * N;
+  ZGemm g;
+  g.M = (int)N; g.N = (int)N; g.K = (int)N; g.batch = (int)N2;
+  g.A = c->wP; g.sa_b = N2; g.sa_m = N; g.sa_k = 1;
+  g.B = G_in; g.sb_b = N2; g.sb_k = 1; g.sb_n = N;
+  g.C = c->I; g.sc_m = N; g.sc_n = 1;
+  g.alpha = {0.0, -1.0};
+  zgemm_reduce(L, g, c->partial, c->splits);
+}
+
+// a4: A_ijkl = sum nbar_ip nbar_jq wt_pqrs n_rk n_sl (Eq. psi-pm-def) by successive
+// contractions into c->Ab (nbar into c->nbar); the source term is Psi = -A + A^dag
+void source_A(g1g2_ctx *c, Launcher &L, const cplx *n_in) {
+  const int nb = c->nb;
+  const long long N = nb, N2 = N * N, N3 = N2 * N;
+  one_minus(L, nb, n_in, c->nbar);
+  {
+    ZGemm g;  // T1_pqrl = sum_s wt_pqrs n_sl
+    g.M = (int)N3; g.N = nb; g.K = nb;
+    g.A = c->wsrc; g.sa_m = N; g.sa_k = 1;
+    g.B = n_in; g.sb_k = N; g.sb_n = 1;
+    g.C = c->T1; g.sc_m = N; g.sc_n = 1;
+    zgemm(L, g);
+  }
+  {
+    ZGemm g;  // T2_pqkl = sum_r n_rk T1_pqrl  (batched over (pq)), A[k][r] = n_rk
+    g.M = nb; g.N = nb; g.K = nb; g.batch = (int)N2;
+    g.A = n_in; g.sa_m = 1; g.sa_k = N;
+    g.B = c->T1; g.sb_b = N2; g.sb_k = N; g.sb_n = 1;
+    g.C = c->T2; g.sc_b = N2; g.sc_m = N; g.sc_n = 1;
+    zgemm(L, g);
+  }
+  {
+    ZGemm g;  // T1_pjkl = sum_q nbar_jq T2_pqkl (batched over p)
+    g.M = nb; g.N = (int)N2; g.K = nb; g.batch = nb;
+    g.A = c->nbar; g.sa_m = N; g.sa_k = 1;
+    g.B = c->T2; g.sb_b = N3; g.sb_k = N2; g.sb_n = 1;
+    g.C = c->T1; g.sc_b = N3; g.sc_m = N2; g.sc_n = 1;
+    zgemm(L, g);
+  }
+  {
+    ZGemm g;  // Ab_ijkl = sum_p nbar_ip T1_pjkl
+    g.M = nb; g.N = (int)N3; g.K = nb;
+    g.A = c->nbar; g.sa_m = N; g.sa_k = 1;
+    g.B = c->T1; g.sb_k = N3; g.sb_n = 1;
+    g.C = c->Ab; g.sc_m = N3; g.sc_n = 1;
+    zgemm(L, g);
+  }
+}
+
 void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *G_in, Rk4Stage st,
               const StageOut &o, bool w_only = false) {
   const int nb = c->nb;
@@ -188,16 +240,8 @@ void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *
     g2_assemble(L, nb, c->Cb, nullptr, st, o.Gy, o.Gys, o.Gacc, o.Gk);
     return;
   }
-  // a2: I_ij = -i sum_(lp) sum_k wP[lp][i][k] G[lp][j][k]   (Eq. eom_gone-I)
-  {
-    ZGemm g;
-    g.M = nb; g.N = nb; g.K = nb; g.batch = (int)N2;
-    g.A = c->wP; g.sa_b = N2; g.sa_m = N; g.sa_k = 1;
-    g.B = G_in; g.sb_b = N2; g.sb_k = 1; g.sb_n = N;
-    g.C = c->I; g.sc_m = N; g.sc_n = 1;
-    g.alpha = {0.0, -1.0};
-    zgemm_reduce(L, g, c->partial, c->splits);
-  }
+  // a2: Eq. (eom_gone-I)
+  collision(c, L, G_in);
   g1_update(L, nb, c->hhf, n_in, c->I, st, o.ny, o.nys, o.nacc, o.nk);
 
   // a3: C = [h2, G] as four mode products (Eq. twopart_hamiltonian)
@@ -236,40 +280,8 @@ void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *
     g.alpha = {-1.0, 0.0}; g.beta = 1.0;
     zgemm(L, g);
   }
-  // a4: A = sum nbar_ip nbar_jq wt_pqrs n_rk n_sl by successive contractions; Psi = -A + A^dag
-  one_minus(L, nb, n_in, c->nbar);
-  {
-    ZGemm g;  // T1_pqrl = sum_s wt_pqrs n_sl
-    g.M = (int)N3; g.N = nb; g.K = nb;
-    g.A = c->wsrc; g.sa_m = N; g.sa_k = 1;
-    g.B = n_in; g.sb_k = N; g.sb_n = 1;
-    g.C = c->T1; g.sc_m = N; g.sc_n = 1;
-    zgemm(L, g);
-  }
-  {
-    ZGemm g;  // T2_pqkl = sum_r n_rk T1_pqrl  (batched over (pq)), A[k][r] = n_rk
-    g.M = nb; g.N = nb; g.K = nb; g.batch = (int)N2;
-    g.A = n_in; g.sa_m = 1; g.sa_k = N;
-    g.B = c->T1; g.sb_b = N2; g.sb_k = N; g.sb_n = 1;
-    g.C = c->T2; g.sc_b = N2; g.sc_m = N; g.sc_n = 1;
-    zgemm(L, g);
-  }
-  {
-    ZGemm g;  // T1_pjkl = sum_q nbar_jq T2_pqkl (batched over p)
-    g.M = nb; g.N = (int)N2; g.K = nb; g.batch = nb;
-    g.A = c->nbar; g.sa_m = N; g.sa_k = 1;
-    g.B = c->T2; g.sb_b = N3; g.sb_k = N2; g.sb_n = 1;
-    g.C = c->T1; g.sc_b = N3; g.sc_m = N2; g.sc_n = 1;
-    zgemm(L, g);
-  }
-  {
-    ZGemm g;  // Ab_ijkl = sum_p nbar_ip T1_pjkl
-    g.M = nb; g.N = (int)N3; g.K = nb;
-    g.A = c->nbar; g.sa_m = N; g.sa_k = 1;
-    g.B = c->T1; g.sb_k = N3; g.sb_n = 1;
-    g.C = c->Ab; g.sc_m = N3; g.sc_n = 1;
-    zgemm(L, g);
-  }
+  // a4: Eq. (psi-pm-def) by successive contractions into A; Psi = -A + A^dag in the assembly
+  source_A(c, L, n_in);
   if (c->se == G1G2_TPP || c->se == G1G2_DSL) {
     // Eq. (HTPPcorr) with G^> = -i nbar, G^< = i n: hcorr = (nbar (x) nbar - n (x) n) w
     const cplx one{1.0, 0.0}, mone{-1.0, 0.0};
@@ -607,6 +619,83 @@ int adj_alloc(g1g2_ctx *c, std::vector<void *> &own, void **p, size_t bytes) {
   own.push_back(q);
   *p = q;
   return G1G2_OK;
+}
+
+}  // namespace
+
+// Helpers of the memory-integral HF-GKBA (g1g2_propagate_hfgkba).
+namespace {
+
+struct DevScratch {
+  std::vector<void *> p;
+  ~DevScratch() { for (void *q : p) cudaFree(q); }
+  template <class T>
+  int get(T **out, size_t count) {
+    void *q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(G1G2_ENOMEM, "memory-integral scratch of " + std::to_string(count * sizeof(T)) + " bytes");
+    }
+    p.push_back(q);
+    *out = static_cast<T *>(q);
+    return G1G2_OK;
+  }
+};
+
+// dn = -i[hHF, n] - (I + I^dag) with I from G2, du = -i hHF u (Eqs. eom_gone-2, eom_gone-I)
+void gkba_derivs(g1g2_ctx *c, Launcher &L, const cplx *n, const cplx *u, const cplx *G2, cplx *dn, cplx *du) {
+  const int nb = c->nb;
+  hf_build(L, nb, c->Wm, c->w_real, c->h, nullptr, 0.0, n, c->hhf);
+  collision(c, L, G2);
+  g1_update(L, nb, c->hhf, n, c->I, Rk4Stage{-1, 0.0}, nullptr, nullptr, nullptr, dn);
+  ZGemm g;
+  g.M = nb; g.N = nb; g.K = nb;
+  g.A = c->hhf; g.sa_m = nb; g.sa_k = 1;
+  g.B = u; g.sb_k = nb; g.sb_n = 1;
+  g.C = du; g.sc_m = nb; g.sc_n = 1;
+  g.alpha = {0.0, -1.0};
+  zgemm(L, g);
+}
+
+// Q = -i Psi(n) = -i (-A + A^dag): the assembly with a zero commutator buffer (c->Cb)
+void gkba_source(g1g2_ctx *c, Launcher &L, const cplx *n, cplx *Q) {
+  source_A(c, L, n);
+  g2_assemble(L, c->nb, c->Cb, c->Ab, Rk4Stage{-1, 0.0}, nullptr, nullptr, nullptr, Q);
+}
+
+struct GkbaHist {
+  cplx *u = nullptr, *Q = nullptr, *V = nullptr, *Vs = nullptr, *Y0 = nullptr, *Y1 = nullptr;
+  int chunk = 1;
+};
+
+// G2 = sum_{k<K} w_k dt (V_k (x) V_k) Q_k (V_k (x) V_k)^dag, V_k = u_now u_k^dag, trapezoid
+// weights w_0 = w_{K-1} = 1/2 (G2 = 0 for K = 1)
+void gkba_memory(g1g2_ctx *c, Launcher &L, const GkbaHist &H, int K, const cplx *u_now, double dt, cplx *G2) {
+  const int nb = c->nb;
+  const long long N2 = (long long)nb * nb, N4 = N2 * N2;
+  if (K <= 1) {
+    cudaMemsetAsync(G2, 0, N4 * sizeof(cplx), L.stream);
+    return;
+  }
+  {
+    ZGemm g;  // V_k[i][j] = sum_p u_now[i][p] conj(u_k[j][p])
+    g.M = nb; g.N = nb; g.K = nb; g.batch = K;
+    g.A = u_now; g.sa_b = 0; g.sa_m = nb; g.sa_k = 1;
+    g.B = H.u; g.sb_b = N2; g.sb_k = 1; g.sb_n = nb; g.conjB = true;
+    g.C = H.V; g.sc_b = N2; g.sc_m = nb; g.sc_n = 1;
+    zgemm(L, g);
+  }
+  zaxpby(L, (long long)K * N2, {dt, 0.0}, H.V, {0.0, 0.0}, nullptr, H.Vs);
+  zaxpby(L, N2, {0.5 * dt, 0.0}, H.V, {0.0, 0.0}, nullptr, H.Vs);
+  zaxpby(L, N2, {0.5 * dt, 0.0}, H.V + (K - 1) * N2, {0.0, 0.0}, nullptr, H.Vs + (K - 1) * N2);
+  for (int k0 = 0; k0 < K; k0 += H.chunk) {
+    const int kc = std::min(H.chunk, K - k0);
+    mode_rotate(L, nb, kc, H.Q + k0 * N4, H.Vs + k0 * N2, false, H.Y0);
+    mode_rotate(L, nb, kc, H.Y0, H.V + k0 * N2, false, H.Y1);
+    mode_rotate(L, nb, kc, H.Y1, H.V + k0 * N2, true, H.Y0);
+    mode_rotate(L, nb, kc, H.Y0, H.V + k0 * N2, true, H.Y1);
+    batch_sum(L, N4, kc, H.Y1, k0 == 0 ? 0.0 : 1.0, G2);
+  }
 }
 
 }  // namespace
@@ -965,6 +1054,86 @@ int g1g2_propagate(g1g2_ctx *c, double dt, int nsteps, int obs_every, g1g2_obs *
   }
   if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "propagate sync"))) return rc;
   return c->tc ? tc_error(c->tc, c->stream) : G1G2_OK;
+}
+
+// Original HF-GKBA with the SOA selfenergy, the memory-integral form the G1-G2
+// equations were derived from (Sec. III.B): the correlated part at time t is
+//   G2(t) = (i hbar)^3 int_{t0}^t dtb U2(t,tb) Psi(tb) U2(tb,t)   Eq. (dtilde-solution-short)
+// with U2 = U (x) U (Eq. prop_two) and i hbar U(t,tb) = u(t) u(tb)^dag the Hartree-Fock
+// propagator of the GKBA (Eqs. GKBA_propa/b), i du/dt = hHF u.  Every evaluation sums
+// over the whole stored history (trapezoid rule): the O(N_t^2) cost of the standard
+// scheme (Table I).  n and u advance by Heun's method; the memory sum at the predictor
+// includes the predicted end point.  History entry k holds u(t_k) and Q_k = -i Psi(t_k),
+// since (i hbar)^3 (i hbar)^-4 = -i.
+int g1g2_propagate_hfgkba(g1g2_ctx *c, double dt, int nsteps, double *G1_history, size_t scratch_bytes) {
+  if (!c || nsteps < 0 || !std::isfinite(dt)) return fail(G1G2_EINVAL, "bad argument");
+  if (c->se != G1G2_SOA || c->prec != G1G2_FP64)
+    return fail(G1G2_EUNSUPPORTED, "the memory-integral HF-GKBA covers SOA in the FP64 form");
+  if (c->hasD) return fail(G1G2_EUNSUPPORTED, "the memory-integral HF-GKBA runs without a drive");
+  if (c->nb > mode_rotate_max_nb())
+    return fail(G1G2_EUNSUPPORTED, "the memory-integral HF-GKBA keeps nb^4 per time step; nb <= " +
+                                       std::to_string(mode_rotate_max_nb()));
+  const int nb = c->nb;
+  const long long N2 = (long long)nb * nb, N4 = N2 * N2;
+  const long long slots = (long long)nsteps + 2;
+  if (scratch_bytes == 0) scratch_bytes = (size_t)256 << 20;
+  GkbaHist H;
+  H.chunk = (int)std::max<long long>(
+      1, std::min<long long>(std::min<long long>(slots, 65535LL), (long long)(scratch_bytes / (2 * N4 * sizeof(cplx)))));
+  Launcher L = c->launcher();
+  int rc;
+  // the integral starts from an uncorrelated state
+  if ((rc = cuda_check(cudaMemsetAsync(c->red, 0, sizeof(double), c->stream), "memset"))) return rc;
+  count_nonzero(L, c->G, N4, c->red);
+  double nz = 0;
+  if ((rc = cuda_check(cudaMemcpyAsync(&nz, c->red, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "check")) ||
+      (rc = cuda_check(cudaStreamSynchronize(c->stream), "check sync")))
+    return rc;
+  if (nz != 0) return fail(G1G2_EINVAL, "the memory integral starts from G2 = 0; the state has a nonzero G2");
+  DevScratch S;
+  cplx *nh, *np, *dn1, *dn2, *du1, *du2;
+  if ((rc = S.get(&H.u, slots * N2)) || (rc = S.get(&H.Q, slots * N4)) || (rc = S.get(&H.V, slots * N2)) ||
+      (rc = S.get(&H.Vs, slots * N2)) || (rc = S.get(&H.Y0, H.chunk * N4)) || (rc = S.get(&H.Y1, H.chunk * N4)) ||
+      (rc = S.get(&nh, (slots - 1) * N2)) || (rc = S.get(&np, N2)) || (rc = S.get(&dn1, N2)) ||
+      (rc = S.get(&dn2, N2)) || (rc = S.get(&du1, N2)) || (rc = S.get(&du2, N2)))
+    return rc;
+  std::vector<cplx> eye(N2, cplx{0.0, 0.0});
+  for (int i = 0; i < nb; ++i) eye[(size_t)i * nb + i] = {1.0, 0.0};
+  if ((rc = cuda_check(cudaMemcpyAsync(H.u, eye.data(), N2 * sizeof(cplx), cudaMemcpyHostToDevice, c->stream), "u0")) ||
+      (rc = cuda_check(cudaMemcpyAsync(nh, c->n, N2 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream), "n0")) ||
+      (rc = cuda_check(cudaMemsetAsync(c->Cb, 0, N4 * sizeof(cplx), c->stream), "zero")))
+    return rc;
+  gkba_source(c, L, nh, H.Q);
+  gkba_memory(c, L, H, 1, H.u, dt, c->G);
+  const cplx one{1.0, 0.0}, half{0.5 * dt, 0.0}, full{dt, 0.0};
+  for (int m = 0; m < nsteps; ++m) {
+    cplx *n0 = nh + m * N2, *n1 = nh + (m + 1) * N2, *u0 = H.u + m * N2, *u1 = H.u + (m + 1) * N2;
+    cplx *Q1 = H.Q + (m + 1) * N4;
+    gkba_derivs(c, L, n0, u0, c->G, dn1, du1);
+    zaxpby(L, N2, one, n0, full, dn1, np);                 // predictor
+    zaxpby(L, N2, one, u0, full, du1, u1);
+    gkba_source(c, L, np, Q1);
+    gkba_memory(c, L, H, m + 2, u1, dt, c->Gs);
+    gkba_derivs(c, L, np, u1, c->Gs, dn2, du2);
+    zaxpby(L, N2, one, n0, half, dn1, n1);                 // corrector
+    zaxpby(L, N2, one, n1, half, dn2, n1);
+    zaxpby(L, N2, one, u0, half, du1, u1);
+    zaxpby(L, N2, one, u1, half, du2, u1);
+    gkba_source(c, L, n1, Q1);
+    gkba_memory(c, L, H, m + 2, u1, dt, c->G);
+  }
+  if ((rc = launch_status(L, "memory-integral HF-GKBA"))) return rc;
+  if ((rc = cuda_check(cudaMemcpyAsync(c->n, nh + nsteps * N2, N2 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream),
+                       "state")))
+    return rc;
+  if (G1_history &&
+      (rc = cuda_check(cudaMemcpyAsync(G1_history, nh, (size_t)(nsteps + 1) * N2 * sizeof(cplx), cudaMemcpyDeviceToHost,
+                                       c->stream),
+                       "history")))
+    return rc;
+  if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "memory-integral sync"))) return rc;
+  c->t += nsteps * dt;
+  return G1G2_OK;
 }
 
 int g1g2_get_state(g1g2_ctx *c, double *t, double *G1, double *G2) {

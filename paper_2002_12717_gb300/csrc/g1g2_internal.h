@@ -124,6 +124,15 @@ void herm_sum(Launcher &L, int nb, cplx c, const cplx *a, cplx *out);
 void real_dot_acc(Launcher &L, long long n, const cplx *x, const cplx *y, double coeff, double *partials, double *acc);
 void hf_build_t(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *x, cplx *out, bool accumulate);
 
+// Memory-integral HF-GKBA: out_b[m][i] = sum_p in_b[p][m] op(S_b[i][p]) for b < batch
+// (batch <= 65535, nb <= mode_rotate_max_nb()), m over the trailing nb^3 entries of the
+// nb^4 tensor in_b, S_b the nb x nb matrix at S + b nb^2, op = conj when conjS;
+// out[e] = beta out[e] + sum_b x[b len + e]; *cnt += number of nonzero entries of x.
+int mode_rotate_max_nb();
+void mode_rotate(Launcher &L, int nb, int batch, const cplx *in, const cplx *S, bool conjS, cplx *out);
+void batch_sum(Launcher &L, long long len, int nbatch, const cplx *x, double beta, cplx *out);
+void count_nonzero(Launcher &L, const cplx *x, long long len, double *cnt);
+
 // Text returned by g1g2_last_error_detail on this thread.
 void set_error_detail(const std::string &what);
 

@@ -65,6 +65,7 @@ def load():
         "g1g2_rhs": (ctypes.c_int, [vp, ctypes.c_double, vp, vp, vp, vp]),
         "g1g2_step": (ctypes.c_int, [vp, ctypes.c_double]),
         "g1g2_propagate": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Obs), _dp]),
+        "g1g2_propagate_hfgkba": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int, _dp, ctypes.c_size_t]),
         "g1g2_observables": (ctypes.c_int, [vp, ctypes.POINTER(Obs), _dp, _dp]),
         "g1g2_get_state": (ctypes.c_int, [vp, _dp, _dp, _dp]),
         "g1g2_set_state": (ctypes.c_int, [vp, ctypes.c_double, _dp, _dp]),
@@ -190,6 +191,14 @@ class Propagator:
         dens = np.zeros((nrec, self.nb))
         _check(self._lib.g1g2_propagate(self._ctx, float(dt), int(nsteps), int(obs_every), obs, _cptr(dens)))
         return [o.as_dict() for o in obs], dens
+
+    def propagate_hfgkba(self, dt, nsteps, scratch_bytes=0):
+        """Original memory-integral HF-GKBA (SOA, FP64 form) from the current uncorrelated
+        state; returns n(t0 + m dt) for m = 0..nsteps as an (nsteps+1, nb, nb) array."""
+        hist = np.zeros((int(nsteps) + 1, self.nb, self.nb), dtype=np.complex128)
+        _check(self._lib.g1g2_propagate_hfgkba(self._ctx, float(dt), int(nsteps), _cptr(hist.view(np.float64)),
+                                                int(scratch_bytes)))
+        return hist
 
     def observables(self, double_occ=False):
         o = Obs()

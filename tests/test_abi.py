@@ -108,6 +108,7 @@ def test_null_context_calls(lib):
     assert lib.g1g2_step(None, 0.1) == g1g2.EINVAL
     assert lib.g1g2_rhs(None, 0.0, None, None, None, None) == g1g2.EINVAL
     assert lib.g1g2_propagate(None, 0.1, 1, 1, None, None) == g1g2.EINVAL
+    assert lib.g1g2_propagate_hfgkba(None, 0.1, 1, None, 0) == g1g2.EINVAL
     assert lib.g1g2_observables(None, None, None, None) == g1g2.EINVAL
     assert lib.g1g2_get_state(None, None, None, None) == g1g2.EINVAL
     assert lib.g1g2_set_state(None, 0.0, None, None) == g1g2.EINVAL
