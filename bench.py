@@ -409,6 +409,57 @@ def hubbard_scaling(sizes, steps=3):
     return out
 
 
+def nt_scaling(nts, dt=0.02, L=8):
+    """Wall time of the memory-integral HF-GKBA (Sec. III.B, O(N_t^2)) against the G1-G2
+    equations (O(N_t)) for N_t time steps: spin-restricted Hubbard chain (J = 1, U = 1,
+    half filling, quench), SOA, FP64 form.  The G1-G2 runs take RK4 steps, on the
+    general O(nb^5) path and on the Hubbard O(nb^4) path.  Per-kernel time of
+    the longest HF-GKBA run comes from the library's CUDA-event profile."""
+    import torch
+
+    from paper_2002_12717_gb300.g1g2 import from_workload
+
+    d = inputs.hubbard_chain_restricted(L=L, U=1.0)
+    nb = d["nb"]
+    rows, prof = [], None
+    for nt in nts:
+        row = {"N_t": nt}
+        with from_workload(d) as p:
+            p.propagate_hfgkba(dt, 2)                     # warm-up (kernels loaded)
+        with from_workload(d) as p:
+            last = nt == max(nts)
+            if last:
+                p.profile(True)
+            t0 = time.perf_counter()
+            p.propagate_hfgkba(dt, nt)
+            row["hfgkba_s"] = time.perf_counter() - t0
+            if last:
+                prof = p.profile_report()
+        for hub in (False, True):
+            with from_workload(d) as p:
+                p.hubbard_path = hub
+                p.propagate(dt, 2)
+                p.set_state(0.0, d["n0"], None)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                p.propagate(dt, nt)
+                torch.cuda.synchronize()
+                row["g1g2_hubbard_s" if hub else "g1g2_general_s"] = time.perf_counter() - t0
+        rows.append(row)
+    ntm = max(nts)
+    points = ntm * (ntm - 1) + 4 * ntm                    # history points summed over all evaluations
+    rot = prof.get("hfgkba_mode_rotate", (0, 0.0))
+    flops = 4 * 8 * nb ** 5 * points                      # four mode products of nb^5 complex MACs each
+    summary = {"workload": f"hubbard-chain-restricted-nb{nb}", "dt": dt,
+               "kernels_at_max_N_t": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()},
+               "mode_rotate_gflops": round(flops / (rot[1] * 1e-3) / 1e9, 1) if rot[1] else None}
+    if len(rows) >= 2:
+        a, b = rows[-2], rows[-1]
+        for key in ("hfgkba_s", "g1g2_general_s", "g1g2_hubbard_s"):
+            summary["exponent_" + key[:-2]] = round(float(np.log(b[key] / a[key]) / np.log(b["N_t"] / a["N_t"])), 2)
+    return rows, summary
+
+
 def cpu_baseline(args):
     """The CPU oracle as it stands, one right-hand side of each workload (bounded sample)."""
     from oracle import g1g2_oracle as O
@@ -478,6 +529,8 @@ def main():
                     help="steps run in both forms from the initial state (speed-up and error vs FP64)")
     ap.add_argument("--hubbard-scaling", default="",
                     help="comma-separated nb: time the Hubbard O(nb^4) path against the general path and exit")
+    ap.add_argument("--nt-scaling", default="",
+                    help="comma-separated N_t: time the memory-integral HF-GKBA against the G1-G2 equations and exit")
     ap.add_argument("--adjoint-steps", type=int, default=100,
                     help="steps of the discrete-adjoint sample on the 4x4 Hubbard cluster (0: skip)")
     args = ap.parse_args()
@@ -494,6 +547,11 @@ def main():
         if rank == 0:
             print(json.dumps({"hubbard_scaling": hubbard_scaling([int(x) for x in args.hubbard_scaling.split(",")])}),
                   flush=True)
+        return
+    if args.nt_scaling:
+        if rank == 0:
+            rows, summary = nt_scaling([int(x) for x in args.nt_scaling.split(",")])
+            print(json.dumps({"nt_scaling": rows, "summary": summary}), flush=True)
         return
     if args.impl == "reference":
         if rank != 0:

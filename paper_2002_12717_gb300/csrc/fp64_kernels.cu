@@ -36,10 +36,35 @@ struct ZGemmDev {
   int conjA, conjB;
 };
 
+// Micro-tile product over kcount k-steps of the staged tiles: rows ty + 8 i (i < TI),
+// columns tx + 8 j (j < TJ).  TI, TJ < 4 serve tiles whose valid extent is at most 8
+// rows or columns, and kcount < GBK a ragged K tile, so that padding costs no DFMA
+// (the FP64 pipe is the bound of this kernel).
+template <int TI, int TJ, bool kFullK>
+__device__ __forceinline__ void tile_fma(const cplx (*As)[GBM + 1], const cplx (*Bs)[GBN + 1], int ty, int tx,
+                                         int kcount, cplx (&acc)[GTM][GTN]) {
+  const int kn = kFullK ? GBK : kcount;
+#pragma unroll 4
+  for (int kk = 0; kk < kn; ++kk) {
+    cplx a[TI], bb[TJ];
+#pragma unroll
+    for (int i = 0; i < TI; ++i) a[i] = As[kk][ty + i * (GBM / GTM)];
+#pragma unroll
+    for (int j = 0; j < TJ; ++j) bb[j] = Bs[kk][tx + j * (GBN / GTN)];
+#pragma unroll
+    for (int i = 0; i < TI; ++i)
+#pragma unroll
+      for (int j = 0; j < TJ; ++j) acc[i][j] = cfma(a[i], bb[j], acc[i][j]);
+  }
+}
+
 // reduce != 0: split-K form.  The reduction runs over (batch, K); it is cut
 // into batch * kparts units (unit u: batch u / kparts, K range
 // [(u % kparts) * klen, ...)), and split z sums units [z * per_split, ...)
 // into partial[z].
+// TI, TJ: micro-tile rows and columns computed per thread (GTM, GTN for operands wider
+// than 8 in M and N; 1 where that extent is at most 8, chosen by the host per GEMM).
+template <int TI, int TJ>
 __global__ void __launch_bounds__(GNT) zgemm_kernel(ZGemmDev g, int reduce, int per_split, cplx *partial, int kparts,
                                                      int klen) {
   __shared__ cplx As[GBK][GBM + 1];
@@ -89,18 +114,10 @@ __global__ void __launch_bounds__(GNT) zgemm_kernel(ZGemmDev g, int reduce, int 
           Bs[k][n] = v;
         }
         __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < GBK; ++kk) {
-          cplx a[GTM], bb[GTN];
-#pragma unroll
-          for (int i = 0; i < GTM; ++i) a[i] = As[kk][ty + i * (GBM / GTM)];
-#pragma unroll
-          for (int j = 0; j < GTN; ++j) bb[j] = Bs[kk][tx + j * (GBN / GTN)];
-#pragma unroll
-          for (int i = 0; i < GTM; ++i)
-#pragma unroll
-            for (int j = 0; j < GTN; ++j) acc[i][j] = cfma(a[i], bb[j], acc[i][j]);
-        }
+        // the full micro-tile runs the whole (zero-padded) K tile: a runtime trip count
+        // there costs registers, and wide GEMMs have few ragged K tiles
+        if (TI == GTM && TJ == GTN) tile_fma<TI, TJ, true>(As, Bs, ty, tx, GBK, acc);
+        else tile_fma<TI, TJ, false>(As, Bs, ty, tx, min(GBK, kend - k0), acc);
         __syncthreads();
       }
     }
@@ -532,11 +549,22 @@ __global__ void count_nonfinite_kernel(const cplx *x, long long len, double *cnt
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Rows (columns) beyond 8 of a tile exist only when M (N) exceeds 8; narrower GEMMs
+// run the 1-row (1-column) micro-tile so that no DFMA is spent on padding.
+void launch_zgemm(dim3 grid, cudaStream_t st, const ZGemm &g, int reduce, int per, cplx *partial, int kparts,
+                  int klen) {
+  const bool mw = g.M > GBM / GTM, nw = g.N > GBN / GTN;
+  if (mw && nw) zgemm_kernel<GTM, GTN><<<grid, GNT, 0, st>>>(to_dev(g), reduce, per, partial, kparts, klen);
+  else if (mw) zgemm_kernel<GTM, 1><<<grid, GNT, 0, st>>>(to_dev(g), reduce, per, partial, kparts, klen);
+  else if (nw) zgemm_kernel<1, GTN><<<grid, GNT, 0, st>>>(to_dev(g), reduce, per, partial, kparts, klen);
+  else zgemm_kernel<1, 1><<<grid, GNT, 0, st>>>(to_dev(g), reduce, per, partial, kparts, klen);
+}
+
 void zgemm(Launcher &L, const ZGemm &g) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, std::min(g.batch, 65535));
   L.before("fp64_zgemm");
-  zgemm_kernel<<<grid, GNT, 0, L.stream>>>(to_dev(g), 0, 1, nullptr, 1, g.K);
+  launch_zgemm(grid, L.stream, g, 0, 1, nullptr, 1, g.K);
   L.after_launch();
 }
 
@@ -552,7 +580,7 @@ void zgemm_reduce(Launcher &L, const ZGemm &g, cplx *partial, int splits) {
   splits = (int)((units + per - 1) / per);
   dim3 grid((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, splits);
   L.before("fp64_zgemm_splitk");
-  zgemm_kernel<<<grid, GNT, 0, L.stream>>>(to_dev(g), 1, per, partial, kparts, klen);
+  launch_zgemm(grid, L.stream, g, 1, per, partial, kparts, klen);
   L.after_launch();
   const long long mn = (long long)g.M * g.N;
   L.before("fp64_splitk_reduce");
@@ -839,12 +867,30 @@ __global__ void __launch_bounds__(128) mode_rotate_kernel(int nb, const cplx *__
   }
 }
 
-__global__ void batch_sum_kernel(long long len, int nbatch, const cplx *__restrict__ x, double beta, cplx *out) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
-    cplx s = (beta != 0.0) ? cscale(out[e], beta) : cplx{0.0, 0.0};
-    for (int b = 0; b < nbatch; ++b) s = cadd(s, x[(long long)b * len + e]);
-    out[e] = s;
+// out[e] = beta out[e] + sum_b x[b len + e]: 32 consecutive entries per block, the
+// batch split over the block's eight warps (b = warp + 8 r), then a fixed-order
+// reduction over the warps in shared memory (deterministic).
+__global__ void __launch_bounds__(256) batch_sum_kernel(long long len, int nbatch, const cplx *__restrict__ x,
+                                                        double beta, cplx *out) {
+  __shared__ cplx part[8][32];
+  const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+  const long long e = (long long)blockIdx.x * 32 + lane;
+  cplx s0 = {0.0, 0.0}, s1 = {0.0, 0.0};
+  if (e < len) {
+    int b = wv;
+    for (; b + 8 < nbatch; b += 16) {
+      s0 = cadd(s0, x[(long long)b * len + e]);
+      s1 = cadd(s1, x[(long long)(b + 8) * len + e]);
+    }
+    if (b < nbatch) s0 = cadd(s0, x[(long long)b * len + e]);
   }
+  part[wv][lane] = cadd(s0, s1);
+  __syncthreads();
+  if (wv != 0 || e >= len) return;
+  cplx s = (beta != 0.0) ? cscale(out[e], beta) : cplx{0.0, 0.0};
+#pragma unroll
+  for (int w = 0; w < 8; ++w) s = cadd(s, part[w][lane]);
+  out[e] = s;
 }
 
 __global__ void count_nonzero_kernel(const cplx *x, long long len, double *cnt) {
@@ -881,8 +927,7 @@ void mode_rotate(Launcher &L, int nb, int batch, const cplx *in, const cplx *S, 
 
 void batch_sum(Launcher &L, long long len, int nbatch, const cplx *x, double beta, cplx *out) {
   L.before("hfgkba_batch_sum");
-  batch_sum_kernel<<<(unsigned)std::min<long long>((len + 255) / 256, 8192), 256, 0, L.stream>>>(len, nbatch, x, beta,
-                                                                                                 out);
+  batch_sum_kernel<<<(unsigned)((len + 31) / 32), 256, 0, L.stream>>>(len, nbatch, x, beta, out);
   L.after_launch();
 }
 
