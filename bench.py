@@ -460,6 +460,55 @@ def nt_scaling(nts, dt=0.02, L=8):
     return rows, summary
 
 
+# complex multiply-adds per right-hand side of the FP64 form, by selfenergy: commutator
+# 4 nb^5, source 4 nb^5, collision nb^5; GW quasi-Hamiltonian 2 nb^5 and polarisation
+# nb^6; each T-matrix quasi-Hamiltonian 4 nb^5 and ladder product nb^6
+FP64_CMAC = {
+    "SOA": lambda n: 9 * n ** 5,
+    "GW": lambda n: 11 * n ** 5 + n ** 6,
+    "GWX": lambda n: 11 * n ** 5 + n ** 6,
+    "TPP": lambda n: 13 * n ** 5 + n ** 6,
+    "TPH": lambda n: 13 * n ** 5 + n ** 6,
+    "DSL": lambda n: 19 * n ** 5 + 3 * n ** 6,
+}
+FP64_DFMA_TFLOPS = 1.200   # measured FP64 DFMA rate of this GPU (profiles/fp64_dfma_peak.md)
+
+
+def selfenergy_sweep(sizes, steps=2):
+    """ms per RK4 step of every selfenergy in the FP64 form on the seeded general basis
+    (rank 2 nb, nb/2 occupied, gauss-sine pulse), with the algorithmic FLOP rate
+    against the measured DFMA rate."""
+    import torch
+
+    from paper_2002_12717_gb300.g1g2 import from_workload
+
+    out = []
+    for nb in sizes:
+        for se in ("SOA", "GW", "GWX", "TPP", "TPH", "DSL"):
+            d = inputs.general_basis(nb, 2 * nb, nb // 2, seed=nb, selfenergy=se, pulse=True)
+            with from_workload(d) as p:
+                p.step(0.01)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(steps):
+                    p.step(0.01)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                p.profile(True)
+                p.step(0.01)
+                prof = p.profile_report()
+                p.profile(False)
+            tot = sum(v[1] for v in prof.values())
+            top = max(prof.items(), key=lambda kv: kv[1][1])
+            tflops = 4 * 8 * FP64_CMAC[se](nb) / (ms * 1e-3) / 1e12
+            out.append({"nb": nb, "selfenergy": se, "ms_per_step": round(ms, 3),
+                        "algorithmic_tflops": round(tflops, 4), "frac_of_dfma": round(tflops / FP64_DFMA_TFLOPS, 3),
+                        "top_kernel": top[0], "top_share": round(top[1][1] / tot, 3)})
+    return out
+
+
 def cpu_baseline(args):
     """The CPU oracle as it stands, one right-hand side of each workload (bounded sample)."""
     from oracle import g1g2_oracle as O
@@ -531,6 +580,8 @@ def main():
                     help="comma-separated nb: time the Hubbard O(nb^4) path against the general path and exit")
     ap.add_argument("--nt-scaling", default="",
                     help="comma-separated N_t: time the memory-integral HF-GKBA against the G1-G2 equations and exit")
+    ap.add_argument("--selfenergy-sweep", default="",
+                    help="comma-separated nb: time every selfenergy in the FP64 form and exit")
     ap.add_argument("--adjoint-steps", type=int, default=100,
                     help="steps of the discrete-adjoint sample on the 4x4 Hubbard cluster (0: skip)")
     args = ap.parse_args()
@@ -546,6 +597,11 @@ def main():
     if args.hubbard_scaling:
         if rank == 0:
             print(json.dumps({"hubbard_scaling": hubbard_scaling([int(x) for x in args.hubbard_scaling.split(",")])}),
+                  flush=True)
+        return
+    if args.selfenergy_sweep:
+        if rank == 0:
+            print(json.dumps({"selfenergy_sweep": selfenergy_sweep([int(x) for x in args.selfenergy_sweep.split(",")])}),
                   flush=True)
         return
     if args.nt_scaling:
