@@ -5,8 +5,10 @@ TEST INFRASTRUCTURE ONLY.  Only `tests/`, `__graft_entry__.smoke()` and the
 It shares no code with the CUDA path and imports nothing from the product
 package.
 
-Everything is complex128 numpy; ħ = 1; fermions (the lower sign of every "±"
-in the paper, see the footnote to the KBE in Sec. II.A).  The equations are
+Everything is complex128 numpy; ħ = 1.  The "±" of the paper refers to
+bosons/fermions (footnote to the KBE in Sec. II.A); every function that carries
+one takes eta = +1 (bosons, upper sign) or eta = -1 (fermions, lower sign, the
+default).  The equations are
 written in the paper's own variables: the time-diagonal G^< and G^> of
 Eq. (g-glsymm), the Hartree-Fock Hamiltonian of Eq. (h_HF), the two-particle
 Hartree-Fock Hamiltonian of Eq. (twopart_hamiltonian), the source term Psi of
@@ -22,7 +24,10 @@ correlated two-particle function G2 = 𝒢 of Eq. (gscor-def), an nb^4 tensor
 indexed [i, j, k, l].
 
 Readings of the paper used here, where it leaves a choice open:
-  * fermions only; ħ = 1;
+  * fermions by default, bosons with eta = +1 (each ± of the paper followed
+    as printed: G^< of Eq. (g-glsymm), h^HF and w^± of Eq. (h_HF), I of
+    Eq. (eom_gone-I), 𝔥 of Eq. (gwhcorr), the exchange term of Eq. (ini-g2));
+    ħ = 1;
   * the integrator is classical RK4 on (n, 𝒢) jointly (the paper names none);
   * SOA uses Psi^- (w^- = w_pqrs - w_pqsr); GW uses the plain-w Psi
     (standard GW without exchange, Sec. IV.C);
@@ -57,45 +62,50 @@ HF = "HF"
 # Sec. II.B: time-diagonal G^<, G^> and the Hartree-Fock Hamiltonian
 # ---------------------------------------------------------------------------
 
-def g_less(n):
-    """Eq. (g-glsymm), lower sign: G^<_ij = -(1/i) n_ij = i n_ij."""
-    return 1j * n
+def g_less(n, eta=-1):
+    """Eq. (g-glsymm): G^<_ij = ±(1/iħ) n_ij, i.e. i n_ij for fermions, -i n_ij for bosons."""
+    return eta * n / 1j
 
 
-def g_greater(n):
-    """Eq. (g-glsymm): G^> = G^< + delta/(i ħ) = i n - i delta."""
-    return g_less(n) + np.eye(n.shape[0]) / 1j
+def g_greater(n, eta=-1):
+    """Eq. (g-glsymm): G^> = G^< + delta/(i ħ) (-i (1 - n) for fermions, -i (1 + n) for bosons)."""
+    return g_less(n, eta) + np.eye(n.shape[0]) / 1j
+
+
+def w_pm(w, eta=-1):
+    """Definition below Eq. (h_HF): w^±_ijkl = w_ijkl ± w_ijlk."""
+    return w + eta * w.transpose(0, 1, 3, 2)
 
 
 def w_antisym(w):
-    """Definition below Eq. (h_HF), lower sign: w^-_ijkl = w_ijkl - w_ijlk."""
-    return w - w.transpose(0, 1, 3, 2)
+    """w^- of Eq. (h_HF), the fermion case."""
+    return w_pm(w, -1)
 
 
-def hf_hamiltonian(h, w, n, restricted=False):
-    """Eq. (h_HF): h^HF_ij = h_ij - i Σ_kl w^-_ikjl G^<_lk  (fermions).
+def hf_hamiltonian(h, w, n, restricted=False, eta=-1):
+    """Eq. (h_HF): h^HF_ij = h_ij ± iħ Σ_kl w^±_ikjl G^<_lk.
 
     In spin-restricted mode the exchange partner of the opposite-spin
     interaction vanishes and the plain w enters (Sec. III.D, h^HF of the
     Hubbard basis).
     """
-    wt = w if restricted else w_antisym(w)
-    return h - 1j * einsum("ikjl,lk->ij", wt, g_less(n))
+    wt = w if restricted else w_pm(w, eta)
+    return h + eta * 1j * einsum("ikjl,lk->ij", wt, g_less(n, eta))
 
 
-def collision_integral(w, G2):
-    """Eq. (definition_D) / (eom_gone-I), lower sign: I_ij = -i Σ_klp w_iklp 𝒢_lpjk."""
-    return -1j * einsum("iklp,lpjk->ij", w, G2)
+def collision_integral(w, G2, eta=-1):
+    """Eq. (definition_D) / (eom_gone-I): I_ij = ±iħ Σ_klp w_iklp 𝒢_lpjk."""
+    return eta * 1j * einsum("iklp,lpjk->ij", w, G2)
 
 
-def g1_rhs(hhf, n, I):
+def g1_rhs(hhf, n, I, eta=-1):
     """Eq. (eom_gone-2): i dG^</dt = [h^HF, G^<] + I + I^dagger, returned as dn/dt.
 
-    With G^< = i n this is dn/dt = -i dG^</dt.
+    With G^< = ±(1/i) n this is dn/dt = ±i dG^</dt.
     """
-    gl = g_less(n)
+    gl = g_less(n, eta)
     dgl = -1j * (hhf @ gl - gl @ hhf + I + I.conj().T)
-    return -1j * dgl
+    return eta * 1j * dgl
 
 
 # ---------------------------------------------------------------------------
@@ -115,15 +125,15 @@ def two_particle_commutator(hhf, G2):
             - einsum("ijkp,pl->ijkl", G2, hhf))
 
 
-def psi_source(wt, n):
+def psi_source(wt, n, eta=-1):
     """Two-particle source term, Eq. (psi-pm-def) with Φ of Sec. III.B.
 
     Evaluated as Eq. (soa-skalierung): four independent single sums done as
     successive tensor contractions (s first, then r, q, p), once with
     (G^>, G^>, G^<, G^<) and once with (G^<, G^<, G^>, G^>), times (iħ)^2.
-    `wt` is w^- for SOA (Psi^-) and the plain w for GW / spin-restricted mode.
+    `wt` is w^± for SOA (Psi^±) and the plain w for GW / spin-restricted mode.
     """
-    gl, gg = g_less(n), g_greater(n)
+    gl, gg = g_less(n, eta), g_greater(n, eta)
 
     def chain(a, b, c, d):
         x = einsum("pqrs,sl->pqrl", wt, d)      # Σ_s w_pqrs d_sl
@@ -143,14 +153,14 @@ def g2_exchange(gx, gy):
     return einsum("il,jk->ijkl", gx, gy)
 
 
-def gw_hcorr(w, n):
-    """Eq. (gwhcorr), lower sign: 𝔥_ijkl = -(iħ)^2 Σ_pq w_qipk [𝒢^F,>_jplq - 𝒢^F,<_jplq].
+def gw_hcorr(w, n, eta=-1):
+    """Eq. (gwhcorr): 𝔥_ijkl = ±(iħ)^2 Σ_pq w_qipk [𝒢^F,>_jplq - 𝒢^F,<_jplq].
 
     𝒢^F,> = G^> G^< and 𝒢^F,< = G^< G^> (Eq. g2f-def, time diagonal).
     """
-    gl, gg = g_less(n), g_greater(n)
+    gl, gg = g_less(n, eta), g_greater(n, eta)
     fdiff = g2_exchange(gg, gl) - g2_exchange(gl, gg)
-    return -(1j ** 2) * einsum("qipk,jplq->ijkl", w, fdiff)
+    return eta * (1j ** 2) * einsum("qipk,jplq->ijkl", w, fdiff)
 
 
 def gw_polarisation(hcorr, G2):
@@ -162,11 +172,11 @@ def gw_polarisation(hcorr, G2):
 # Sec. IV.D: particle-particle T matrix
 # ---------------------------------------------------------------------------
 
-def tpp_hcorr(w, n):
+def tpp_hcorr(w, n, eta=-1):
     """Correlation part of the pp quasi-Hamiltonian, Eq. (HTPPcorr):
     hcorr_ijkl = (iħ)^2 Σ_pq [G^{H,>}_ijpq - G^{H,<}_ijpq] w_pqkl, with the Hartree
     product G^{H,≷}_ijpq = G^≷_ip G^≷_jq (Sec. II)."""
-    gl, gg = g_less(n), g_greater(n)
+    gl, gg = g_less(n, eta), g_greater(n, eta)
     return (1j ** 2) * (einsum("ip,jq,pqkl->ijkl", gg, gg, w) - einsum("ip,jq,pqkl->ijkl", gl, gl, w))
 
 
@@ -175,12 +185,12 @@ def tpp_ladder(hcorr, G2):
     return einsum("ijpq,pqkl->ijkl", hcorr, G2)
 
 
-def tph_hcorr(w, n):
+def tph_hcorr(w, n, eta=-1):
     """Correlation part of the ph quasi-Hamiltonian, Eq. (HTPHcorr):
     hcorr_ijkl = (iħ)^2 Σ_pq [G^{F,>}_iqlp - G^{F,<}_iqlp] w_pjkq, with the
     equal-time exchange product of Eq. (g2f-def), G^{F,≷}_iqlp = G^≷_ip G^≶_ql
     (the second factor is the opposite component)."""
-    gl, gg = g_less(n), g_greater(n)
+    gl, gg = g_less(n, eta), g_greater(n, eta)
     return (1j ** 2) * (einsum("ip,ql,pjkq->ijkl", gg, gl, w) - einsum("ip,ql,pjkq->ijkl", gl, gg, w))
 
 
@@ -196,19 +206,20 @@ def tph_ladder(hcorr, G2):
 class Problem:
     """Static data of one propagation: h(t) = h + f(t) D, w, selfenergy, basis."""
 
-    def __init__(self, h, w, selfenergy=SOA, restricted=False, D=None, drive=None):
+    def __init__(self, h, w, selfenergy=SOA, restricted=False, D=None, drive=None, bosons=False):
         self.h = np.asarray(h, dtype=np.complex128)
         self.w = np.asarray(w, dtype=np.complex128)
         self.selfenergy = selfenergy
         self.restricted = restricted
         self.D = None if D is None else np.asarray(D, dtype=np.complex128)
         self.drive = drive  # callable f(t) -> float, or None
+        self.eta = 1 if bosons else -1  # the ± of the paper
         if restricted and selfenergy in (GW, GWX, DSL):
             raise ValueError("GW couples same-spin components; no spin-restricted form")
         # source-term interaction: Psi^- for SOA in a spin-orbital basis and for
         # GW with exchange (Psi replaced by Psi^±, end of Sec. IV.C), plain w for
         # standard GW (Sec. IV.C) and for the opposite-spin restricted mode
-        self.w_source = self.w if (restricted or selfenergy == GW) else w_antisym(self.w)
+        self.w_source = self.w if (restricted or selfenergy == GW) else w_pm(self.w, self.eta)
 
     def h_of_t(self, t):
         if self.D is None or self.drive is None:
@@ -229,22 +240,23 @@ def rhs(prob: Problem, t, n, G2):
             both ladder terms, each once;
         HF: 𝒢 is not propagated (collision integral zero).
     """
-    hhf = hf_hamiltonian(prob.h_of_t(t), prob.w, n, prob.restricted)
+    eta = prob.eta
+    hhf = hf_hamiltonian(prob.h_of_t(t), prob.w, n, prob.restricted, eta)
     if prob.selfenergy == HF:
         I = np.zeros_like(n)
-        return g1_rhs(hhf, n, I), np.zeros_like(G2)
-    I = collision_integral(prob.w, G2)
-    dn = g1_rhs(hhf, n, I)
-    rhs2 = two_particle_commutator(hhf, G2) + psi_source(prob.w_source, n)
+        return g1_rhs(hhf, n, I, eta), np.zeros_like(G2)
+    I = collision_integral(prob.w, G2, eta)
+    dn = g1_rhs(hhf, n, I, eta)
+    rhs2 = two_particle_commutator(hhf, G2) + psi_source(prob.w_source, n, eta)
     if prob.selfenergy in (GW, GWX, DSL):
-        pi = gw_polarisation(gw_hcorr(prob.w, n), G2)
+        pi = gw_polarisation(gw_hcorr(prob.w, n, eta), G2)
         rhs2 = rhs2 + pi - pi.transpose(3, 2, 1, 0).conj()
     if prob.selfenergy in (TPP, TPH, DSL):
         lam = np.zeros_like(G2)
         if prob.selfenergy in (TPP, DSL):
-            lam = lam + tpp_ladder(tpp_hcorr(prob.w, n), G2)
+            lam = lam + tpp_ladder(tpp_hcorr(prob.w, n, eta), G2)
         if prob.selfenergy in (TPH, DSL):
-            lam = lam + tph_ladder(tph_hcorr(prob.w, n), G2)
+            lam = lam + tph_ladder(tph_hcorr(prob.w, n, eta), G2)
         rhs2 = rhs2 + lam - lam.transpose(2, 3, 0, 1).conj()
     return dn, -1j * rhs2
 
@@ -263,7 +275,7 @@ def rk4_step(prob: Problem, t, n, G2, dt):
 
 # ---------------------------------------------------------------------------
 # Observables: energies from Eq. (h) and the two-particle density matrix of
-# Eq. (ini-g2), n_ijkl = n_ik n_jl - n_il n_jk - 𝒢_ijkl (fermions, ħ = 1).
+# Eq. (ini-g2), n_ijkl = n_ik n_jl ± n_il n_jk - 𝒢_ijkl (ħ = 1).
 # ---------------------------------------------------------------------------
 
 def energies(prob: Problem, t, n, G2):
@@ -282,7 +294,7 @@ def energies(prob: Problem, t, n, G2):
         npart = 2.0 * np.trace(n).real
     else:
         e1 = einsum("ij,ji->", h, n).real
-        ehf = 0.5 * einsum("ijkl,ki,lj->", w_antisym(prob.w), n, n).real
+        ehf = 0.5 * einsum("ijkl,ki,lj->", w_pm(prob.w, prob.eta), n, n).real
         ecorr = -0.5 * einsum("ijkl,klij->", prob.w, G2).real if prob.selfenergy != HF else 0.0
         npart = np.trace(n).real
     return {"e_one": e1, "e_hf": ehf, "e_corr": ecorr,
@@ -301,16 +313,16 @@ def drive_power(prob: Problem, t, n):
     return s * einsum("ij,ji->", prob.D, n).real
 
 
-def double_occupancy(n, G2, nsites):
+def double_occupancy(n, G2, nsites, eta=-1):
     """E10: d_i = <n_i,up n_i,down> for spin-orbitals ordered (site, spin) = 2*site + spin.
 
-    From Eq. (ini-g2): n_ijkl = n_ik n_jl - n_il n_jk - 𝒢_ijkl with
+    From Eq. (ini-g2): n_ijkl = n_ik n_jl ± n_il n_jk - 𝒢_ijkl with
     i = k = (site, up), j = l = (site, down).
     """
     d = np.empty(nsites)
     for s in range(nsites):
         u, dn = 2 * s, 2 * s + 1
-        d[s] = (n[u, u] * n[dn, dn] - n[u, dn] * n[dn, u] - G2[u, dn, u, dn]).real
+        d[s] = (n[u, u] * n[dn, dn] + eta * n[u, dn] * n[dn, u] - G2[u, dn, u, dn]).real
     return d
 
 

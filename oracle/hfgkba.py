@@ -51,12 +51,13 @@ def propagate_hfgkba(prob: Problem, n0, dt, nsteps):
     nb = n0.shape[0]
     n = n0.astype(np.complex128)
     u = np.eye(nb, dtype=np.complex128)
-    us, psis = [u], [psi_source(prob.w_source, n)]
+    eta = prob.eta
+    us, psis = [u], [psi_source(prob.w_source, n, eta)]
     out = [n.copy()]
 
     def derivs(n_, u_, g2_):
-        hhf = hf_hamiltonian(prob.h, prob.w, n_, prob.restricted)
-        dn = g1_rhs(hhf, n_, collision_integral(prob.w, g2_))
+        hhf = hf_hamiltonian(prob.h, prob.w, n_, prob.restricted, eta)
+        dn = g1_rhs(hhf, n_, collision_integral(prob.w, g2_, eta), eta)
         du = -1j * hhf @ u_
         return dn, du
 
@@ -64,12 +65,12 @@ def propagate_hfgkba(prob: Problem, n0, dt, nsteps):
     for _ in range(nsteps):
         dn1, du1 = derivs(n, u, g2)
         n_p, u_p = n + dt * dn1, u + dt * du1
-        g2_p = _g2_memory(us + [u_p], psis + [psi_source(prob.w_source, n_p)], u_p, dt)
+        g2_p = _g2_memory(us + [u_p], psis + [psi_source(prob.w_source, n_p, eta)], u_p, dt)
         dn2, du2 = derivs(n_p, u_p, g2_p)
         n = n + dt / 2 * (dn1 + dn2)
         u = u + dt / 2 * (du1 + du2)
         us.append(u)
-        psis.append(psi_source(prob.w_source, n))
+        psis.append(psi_source(prob.w_source, n, eta))
         g2 = _g2_memory(us, psis, u, dt)
         out.append(n.copy())
     return out

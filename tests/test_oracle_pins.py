@@ -17,6 +17,7 @@ from oracle.hfgkba import propagate_hfgkba
 from paper_2002_12717_gb300 import inputs
 
 from . import fock
+from . import fock_bosons
 
 
 def sym_w(nb, rng, real=False):
@@ -442,6 +443,157 @@ def test_dsl_equals_printed_quasi_hamiltonian_form_and_is_additive():
     parts = {se: O.rhs(O.Problem(h, w, selfenergy=se), 0.0, n, g2)[1] for se in (O.SOA, O.GWX, O.TPP, O.TPH)}
     additive = parts[O.GWX] + parts[O.TPP] + parts[O.TPH] - 2 * parts[O.SOA]
     assert np.abs(additive - got).max() < 1e-12 * np.abs(got).max()
+
+
+# ---------------------------------------------------------------------------
+# Bosons (the upper sign of every ± in the paper), exact bosonic Fock space
+# ---------------------------------------------------------------------------
+
+def _random_unitary(m, rng):
+    q, r = np.linalg.qr(rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m)))
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def test_boson_g1_equation_and_energy_are_exact_for_any_state():
+    """Bosons: the G1 equation (Eq. eom_gone-2 with I of Eq. eom_gone-I, h^HF with w^+)
+    is the exact first hierarchy equation for any state, with 𝒢 from Eq. (ini-g2)
+    (upper sign), and the energy equals <H>.  Three bosons in four modes, random
+    superposition, complex w; the fermion signs fail the same check."""
+    rng = np.random.default_rng(71)
+    M = 4
+    S = fock_bosons.Space(M, 3)
+    psi = np.zeros(S.dim, dtype=np.complex128)
+    idx = S.sector(3)
+    psi[idx] = rng.standard_normal(len(idx)) + 1j * rng.standard_normal(len(idx))
+    psi /= np.linalg.norm(psi)
+    rho = np.outer(psi, psi.conj())
+    h = inputs.random_hermitian(M, rng)
+    w = sym_w(M, rng) * 0.6
+    H = S.hamiltonian(h, w)
+    n, n2 = S.rdms(rho)
+    g2 = fock_bosons.correlated_g2(n, n2)
+    assert np.abs(g2).max() > 0.1                      # a strongly correlated state
+    dn_exact, _ = S.rdm_rates(rho, H)
+    prob = O.Problem(h, w, "SOA", bosons=True)
+    dn, _ = O.rhs(prob, 0.0, n, g2)
+    assert np.abs(dn - dn_exact).max() < 1e-12 * max(1.0, np.abs(dn_exact).max())
+    e = O.energies(prob, 0.0, n, g2)
+    assert abs(e["e_total"] - np.trace(rho @ H).real) < 1e-12
+    dn_f, _ = O.rhs(O.Problem(h, w, "SOA"), 0.0, n, g2)
+    assert np.abs(dn_f - dn_exact).max() > 1e-2
+
+
+def test_boson_source_term_is_exact_initial_slope_from_gaussian_state():
+    """Bosons: from a quasi-free (Gaussian) state, where 𝒢 = 0, the exact d𝒢/dt is
+    -iΨ^+ (Eq. psi-pm-def with G^> = -i(1 + n), G^< = -i n and w^+), and dn/dt
+    follows Eq. (eom_gone-2).  Thermal state of rotated modes (non-diagonal n), three
+    modes, Fock space truncated at 16 bosons (tail below 1e-15)."""
+    rng = np.random.default_rng(72)
+    M = 3
+    S = fock_bosons.Space(M, 16)
+    rho = fock_bosons.gaussian_state(S, np.array([2.3, 2.6, 3.0]), _random_unitary(M, rng))
+    h = inputs.random_hermitian(M, rng)
+    w = sym_w(M, rng)
+    H = S.hamiltonian(h, w)
+    n, n2 = S.rdms(rho)
+    assert np.abs(fock_bosons.correlated_g2(n, n2)).max() < 1e-13
+    assert np.abs(n - np.diag(np.diag(n))).max() > 1e-2          # not diagonal in the mode basis
+    dn_exact, dn2_exact = S.rdm_rates(rho, H)
+    dg_exact = fock_bosons.correlated_g2_rate(n, n2, dn_exact, dn2_exact)
+    g0 = np.zeros((M,) * 4, dtype=np.complex128)
+    dn, dg = O.rhs(O.Problem(h, w, "SOA", bosons=True), 0.0, n, g0)
+    scale = np.abs(dg_exact).max()
+    assert scale > 1e-3
+    assert np.abs(dg - dg_exact).max() < 1e-11 * scale
+    assert np.abs(dn - dn_exact).max() < 1e-12
+    # the boson source term differs from the fermion one (w^- and 1 - n) on this state
+    _, dg_f = O.rhs(O.Problem(h, w, "SOA"), 0.0, n, g0)
+    assert np.abs(dg_f - dg_exact).max() > 1e-2 * scale
+
+
+def test_boson_gw_quasi_hamiltonian_equals_the_fermion_one():
+    """Eq. (gwhcorr) carries a ± in front and G^≷ change with the statistics; for the
+    time-diagonal products the two signs cancel (G^>G^< - G^<G^> flips sign with
+    the statistics), so 𝔥 is the same δ-reduction for bosons as for fermions."""
+    rng = np.random.default_rng(73)
+    nb = 4
+    w = sym_w(nb, rng)
+    n = inputs.random_hermitian(nb, rng) * 0.2 + 0.5 * np.eye(nb)
+    want = np.einsum("jipk,pl->ijkl", w, n) - np.einsum("qilk,jq->ijkl", w, n)
+    assert np.abs(O.gw_hcorr(w, n, eta=1) - want).max() < 1e-12
+    assert np.abs(O.gw_hcorr(w, n, eta=-1) - want).max() < 1e-12
+
+
+def test_boson_g1g2_equals_memory_integral_hfgkba():
+    """Bosons: the G1-G2 SOA equations reproduce the memory-integral HF-GKBA at second
+    order in dt (Sec. III.C), two-site Bose-Hubbard chain (spinless, w_iiii = U)."""
+    hs = inputs.chain_hopping(2)
+    hs[0, 0] += 1.0
+    w = np.zeros((2,) * 4, dtype=np.complex128)
+    w[0, 0, 0, 0] = w[1, 1, 1, 1] = 1.0
+    prob = O.Problem(hs.astype(np.complex128), w, bosons=True)
+    n0 = np.diag([0.6, 0.3]).astype(np.complex128)
+    T = 2.0
+    n_ref, _, _, _ = O.propagate(prob, n0, np.zeros((2,) * 4), 0.005, int(T / 0.005))
+    errs = []
+    for dt in (0.1, 0.05):
+        ns = propagate_hfgkba(prob, n0, dt, int(round(T / dt)))
+        errs.append(np.abs(ns[-1] - n_ref).max())
+    assert errs[1] < 2e-3 and 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_boson_t_matrix_quasi_hamiltonians_in_plain_loops():
+    """Eqs. (HTPPcorr) and (HTPHcorr) in plain loops with the boson components of
+    Eq. (g-glsymm) written out: G^< = -i n, G^> = -i (1 + n) (upper sign)."""
+    rng = np.random.default_rng(74)
+    nb = 3
+    w = sym_w(nb, rng)
+    n = inputs.random_hermitian(nb, rng) * 0.3 + 0.4 * np.eye(nb)
+    gl = -1j * n
+    gg = -1j * (np.eye(nb) + n)
+    pp = np.zeros((nb,) * 4, dtype=np.complex128)
+    ph = np.zeros((nb,) * 4, dtype=np.complex128)
+    for i in range(nb):
+        for j in range(nb):
+            for k in range(nb):
+                for l in range(nb):
+                    a = b = 0
+                    for p in range(nb):
+                        for q in range(nb):
+                            # Hartree products G^≷_ip G^≷_jq; exchange products G^≷_ip G^≶_ql
+                            a += (gg[i, p] * gg[j, q] - gl[i, p] * gl[j, q]) * w[p, q, k, l]
+                            b += (gg[i, p] * gl[q, l] - gl[i, p] * gg[q, l]) * w[p, j, k, q]
+                    pp[i, j, k, l] = -a        # (iħ)^2 = -1
+                    ph[i, j, k, l] = -b
+    assert np.abs(O.tpp_hcorr(w, n, eta=1) - pp).max() < 1e-12
+    assert np.abs(O.tph_hcorr(w, n, eta=1) - ph).max() < 1e-12
+
+
+@pytest.mark.parametrize("se", ["HF", "SOA", "GW", "GWX", "TPP", "TPH", "DSL"])
+def test_boson_conservation_laws(se):
+    """Bosons, spinless Bose-Hubbard chain (w_iiii = U): particle number to round-off,
+    energy to O(dt^4) with E_HF from w^+ (Eq. ini-g2, upper sign), the 𝒢 symmetries."""
+    L = 4
+    hs = inputs.chain_hopping(L)
+    hs[0, 0] += 1.5
+    w = np.zeros((L,) * 4, dtype=np.complex128)
+    for i in range(L):
+        w[i, i, i, i] = 0.8
+    prob = O.Problem(hs.astype(np.complex128), w, selfenergy=se, bosons=True)
+    n0 = np.diag([0.9, 0.6, 0.3, 0.1]).astype(np.complex128)
+    drifts = []
+    for dt in (0.04, 0.02):
+        steps = int(round(2.0 / dt))
+        n, g2, _, obs = O.propagate(prob, n0, np.zeros((L,) * 4), dt, steps, obs_every=steps)
+        assert abs(obs[-1]["n_particles"] - obs[0]["n_particles"]) < 1e-12
+        drifts.append(abs(obs[-1]["e_total"] - obs[0]["e_total"]))
+        assert np.abs(g2 - g2.transpose(1, 0, 3, 2)).max() < 1e-14
+        assert np.abs(g2 - g2.transpose(2, 3, 0, 1).conj()).max() < 1e-14
+    if se == "HF":
+        assert drifts[1] < 1e-8
+    else:
+        assert np.abs(g2).max() > 1e-3
+        assert drifts[0] > 0 and 10 < drifts[0] / drifts[1] < 24   # ~2^4
 
 
 @pytest.mark.parametrize("se", ["HF", "SOA", "GW", "GWX", "TPP", "TPH", "DSL"])
