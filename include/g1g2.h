@@ -92,19 +92,30 @@ typedef struct {
   int w_is_real;      /* nonzero: w is nb^4 real doubles */
   double sym_tol;     /* absolute symmetry tolerance for w, G1_0, G2_0 (scaled by max|x|); <0 skips */
   void *cuda_stream;  /* cudaStream_t used for every launch; NULL = default stream */
+  int statistics;     /* g1g2_statistics */
 } g1g2_options;
+
+/* Particle statistics: the "±" of the paper (footnote to the KBE, Sec. II.A).
+ * Bosons change the exchange sign of h^HF (w^+ of Eq. h_HF) and of the energy
+ * (Eq. ini-g2, upper sign), the source interaction w^+ of Psi^±, and
+ * G^> = -i (1 + n) (Eq. g-glsymm) in the source term and the T-matrix
+ * quasi-Hamiltonians.  The G1 equation in (n, G2), the collision integral, the
+ * commutator and the GW quasi-Hamiltonian are the same for both.  Bosons run
+ * in the spin-orbital basis and the FP64 form (G1G2_EUNSUPPORTED otherwise);
+ * the discrete adjoint and the Hubbard path are fermion-only. */
+enum { G1G2_FERMIONS = 0, G1G2_BOSONS = 1 };
 
 typedef struct {
   double t;
   double n_particles;  /* Re Tr n (x2 spin-restricted) */
   double e_one;        /* Re Tr(h(t) n) (x2 spin-restricted) */
-  double e_hf;         /* 1/2 Re sum w^-_ijkl n_ki n_lj (spin-restricted: Re sum w_ijkl n_ki n_lj) */
+  double e_hf;         /* 1/2 Re sum w^-_ijkl n_ki n_lj (w^+ for bosons; spin-restricted: Re sum w_ijkl n_ki n_lj) */
   double e_corr;       /* -1/2 Re sum w_ijkl G2_klij (spin-restricted: -Re sum w_ijkl G2_klij) */
   double e_total;      /* e_one + e_hf + e_corr */
   double pulse_work;   /* W(t) = int f'(t) Re Tr(D n) dt, RK4-weighted over the stages */
 } g1g2_obs;
 
-/* Default options: FP64, spin-orbital, complex w, sym_tol 1e-10, default stream. */
+/* Default options: FP64, spin-orbital, complex w, sym_tol 1e-10, default stream, fermions. */
 void g1g2_default_options(g1g2_options *opt);
 
 /* Create a propagation context (Sec. III.F: the initial values n^0 and G2^0).

@@ -280,12 +280,12 @@ __global__ void hf_build_kernel(int nb, const void *__restrict__ Wm_, const cplx
   }
 }
 
-__global__ void one_minus_kernel(int nb, const cplx *n, cplx *nbar) {
+__global__ void one_pm_kernel(int nb, const cplx *n, double eta, cplx *nbar) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nb * nb) return;
   const int i = idx / nb, j = idx % nb;
   cplx v = n[idx];
-  nbar[idx] = {(i == j ? 1.0 : 0.0) - v.x, -v.y};
+  nbar[idx] = {(i == j ? 1.0 : 0.0) + eta * v.x, eta * v.y};
 }
 
 // RK4 bookkeeping for one element with derivative k.
@@ -519,14 +519,14 @@ __global__ void accumulate_work_kernel(int nb, const cplx *D, const cplx *n, dou
   if (threadIdx.x == 0) *W += coeff * s[0];
 }
 
-__global__ void double_occ_kernel(int nb, const cplx *n, const cplx *G, double *out) {
+__global__ void double_occ_kernel(int nb, const cplx *n, const cplx *G, double eta, double *out) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nb / 2) return;
   const int u = 2 * s, d = 2 * s + 1;
   const long long nb_ = nb;
   const cplx nuu = n[u * nb + u], ndd = n[d * nb + d], nud = n[u * nb + d], ndu = n[d * nb + u];
   const cplx g = G[((u * nb_ + d) * nb_ + u) * nb_ + d];
-  const cplx prod = csub(cmul(nuu, ndd), cmul(nud, ndu));
+  const cplx prod = cadd(cmul(nuu, ndd), cscale(cmul(nud, ndu), eta));   // Eq. (ini-g2): the exchange term takes the ±
   out[s] = prod.x - g.x;
 }
 
@@ -615,9 +615,9 @@ void hf_build(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *h, 
   L.after_launch();
 }
 
-void one_minus(Launcher &L, int nb, const cplx *n, cplx *nbar) {
+void one_pm(Launcher &L, int nb, const cplx *n, double eta, cplx *nbar) {
   L.before("one_minus");
-  one_minus_kernel<<<(nb * nb + 255) / 256, 256, 0, L.stream>>>(nb, n, nbar);
+  one_pm_kernel<<<(nb * nb + 255) / 256, 256, 0, L.stream>>>(nb, n, eta, nbar);
   L.after_launch();
 }
 
@@ -674,9 +674,9 @@ void accumulate_work(Launcher &L, int nb, const cplx *D, const cplx *n, double c
   L.after_launch();
 }
 
-void double_occ(Launcher &L, int nb, const cplx *n, const cplx *G, double *out) {
+void double_occ(Launcher &L, int nb, const cplx *n, const cplx *G, double eta, double *out) {
   L.before("double_occ");
-  double_occ_kernel<<<(nb / 2 + 63) / 64, 64, 0, L.stream>>>(nb, n, G, out);
+  double_occ_kernel<<<(nb / 2 + 63) / 64, 64, 0, L.stream>>>(nb, n, G, eta, out);
   L.after_launch();
 }
 

@@ -31,6 +31,7 @@ void g1g2::set_error_detail(const std::string &what) { g_detail = what; }
 
 struct g1g2_ctx {
   int nb = 0, se = 0, prec = 0, basis = 0;
+  double eta = -1.0;                // statistics sign of the paper's ±: -1 fermions, +1 bosons
   bool w_real = false;
   cudaStream_t stream = nullptr;
   long long launches = 0;
@@ -182,7 +183,7 @@ void collision(g1g2_ctx *c, Launcher &L, const cplx *G_in) {
 void source_A(g1g2_ctx *c, Launcher &L, const cplx *n_in) {
   const int nb = c->nb;
   const long long N = nb, N2 = N * N, N3 = N2 * N;
-  one_minus(L, nb, n_in, c->nbar);
+  one_pm(L, nb, n_in, c->eta, c->nbar);
   {
     ZGemm g;  // T1_pqrl = sum_s wt_pqrs n_sl
     g.M = (int)N3; g.N = nb; g.K = nb;
@@ -301,8 +302,9 @@ void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *
     zgemm(L, g);
   }
   if (c->se == G1G2_TPH || c->se == G1G2_DSL) {
-    // Eq. (HTPHcorr) with G^> = -i nbar, G^< = i n: hcorr_ijkl = sum_pq (n_ip nbar_ql - nbar_ip n_ql) w_pjkq
-    const cplx one{1.0, 0.0}, mone{-1.0, 0.0};
+    // Eq. (HTPHcorr) with G^> = -i nbar, G^< = i n: hcorr_ijkl = sum_pq (n_ip nbar_ql - nbar_ip n_ql) w_pjkq;
+    // bosons (G^< = -i n, G^> = -i nbar, nbar = 1 + n) give the opposite overall sign
+    const cplx one{-c->eta, 0.0}, mone{c->eta, 0.0};
     mode_left1(c, L, n_in, c->w, c->T1, one, 0.0);       // T1_ijkq = sum_p n_ip w_pjkq
     mode_right4(c, L, c->T1, c->nbar, c->Hb, one, 0.0);  // Hb_ijkl = sum_q T1_ijkq nbar_ql
     mode_left1(c, L, c->nbar, c->w, c->T1, one, 0.0);
@@ -709,6 +711,7 @@ void g1g2_default_options(g1g2_options *opt) {
   opt->w_is_real = 0;
   opt->sym_tol = 1e-10;
   opt->cuda_stream = nullptr;
+  opt->statistics = G1G2_FERMIONS;
 }
 
 const char *g1g2_strerror(int code) {
@@ -793,6 +796,11 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   if (opt.precision != G1G2_FP64 && opt.precision != G1G2_TF32X3 && opt.precision != G1G2_BF16X4)
     return fail(G1G2_EINVAL, "bad precision");
   if (opt.basis != G1G2_SPIN_ORBITAL && opt.basis != G1G2_SPIN_RESTRICTED) return fail(G1G2_EINVAL, "bad basis");
+  if (opt.statistics != G1G2_FERMIONS && opt.statistics != G1G2_BOSONS) return fail(G1G2_EINVAL, "bad statistics");
+  const bool bosons = opt.statistics == G1G2_BOSONS;
+  if (bosons && opt.basis == G1G2_SPIN_RESTRICTED)
+    return fail(G1G2_EINVAL, "the spin-restricted mode is the fermion Hubbard form; bosons run in the spin-orbital basis");
+  if (bosons && opt.precision != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "bosons run in the FP64 form");
   if (opt.basis == G1G2_SPIN_RESTRICTED && (se == G1G2_GW || se == G1G2_DSL))
     return fail(G1G2_EINVAL, "GW couples same-spin components and has no spin-restricted form");
 
@@ -843,6 +851,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   g1g2_ctx *c = new (std::nothrow) g1g2_ctx;
   if (!c) return fail(G1G2_ENOMEM, "host allocation failed");
   c->nb = nb; c->se = se; c->prec = opt.precision; c->basis = opt.basis;
+  c->eta = bosons ? 1.0 : -1.0;
   c->stream = static_cast<cudaStream_t>(opt.cuda_stream);
   int rc = G1G2_OK;
   auto bail = [&](int code) { g1g2_destroy(c); return code; };
@@ -856,21 +865,22 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
     if (a.imag() != 0.0) real = false;
   }
   c->w_real = real;
-  // source interaction: w^- (SOA, spin-orbital), else w
-  const bool use_minus =
+  // source interaction: w^± (SOA, T matrices, DSL, GW with exchange; spin-orbital), else w
+  const bool use_pm =
       (se == G1G2_SOA || se == G1G2_TPP || se == G1G2_TPH || se == G1G2_DSL || gw_exchange) && !restricted;
+  const double eta = bosons ? 1.0 : -1.0;
   for (size_t i = 0; i < N; ++i)
     for (size_t j = 0; j < N; ++j)
       for (size_t k = 0; k < N; ++k)
         for (size_t l = 0; l < N; ++l) {
           zc a = wv(at4(i, j, k, l));
-          if (use_minus) a -= wv(at4(i, j, l, k));
+          if (use_pm) a += eta * wv(at4(i, j, l, k));
           hsrc[at4(i, j, k, l)] = {a.real(), a.imag()};
           // collision layout wP[(l,p)][i][k] = w_iklp: here (i,k,l,p) = (i,j,k,l) renamed
           const zc b = wv(at4(i, j, k, l));        // w_{i j k l} with j->k', k->l', l->p'
           hP[((k * N + l) * N + i) * N + j] = {b.real(), b.imag()};
         }
-  // Hartree-Fock matrix Wm[(ij),(lk)] = w_ikjl - w_iklj (restricted: w_ikjl)
+  // Hartree-Fock matrix Wm[(ij),(lk)] = w_ikjl ± w_iklj = w^±_ikjl (restricted: w_ikjl)
   std::vector<double> WmR;
   std::vector<cplx> WmC;
   if (real) WmR.resize(N4); else WmC.resize(N4);
@@ -879,7 +889,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
       for (size_t l = 0; l < N; ++l)
         for (size_t k = 0; k < N; ++k) {
           zc a = wv(at4(i, k, j, l));
-          if (!restricted) a -= wv(at4(i, k, l, j));
+          if (!restricted) a += eta * wv(at4(i, k, l, j));
           const size_t e = (i * N + j) * N2 + l * N + k;
           if (real) WmR[e] = a.real(); else WmC[e] = {a.real(), a.imag()};
         }
@@ -930,7 +940,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
     if ((rc = up(c->wP, hP.data(), N4 * sizeof(cplx)))) return bail(rc);
   }
   // Hubbard basis: spin-restricted SOA with an on-site interaction w_ijkl = U_i d(i=j=k=l)
-  if (se == G1G2_SOA && restricted && c->prec == G1G2_FP64 && real) {
+  if (se == G1G2_SOA && restricted && !bosons && c->prec == G1G2_FP64 && real) {
     bool onsite = true;
     std::vector<double> Ui(N);
     for (size_t i = 0; i < N && onsite; ++i)
@@ -1022,7 +1032,7 @@ int g1g2_observables(g1g2_ctx *c, g1g2_obs *out, double *density, double *dbl) {
   if (dbl) {
     if (c->basis != G1G2_SPIN_ORBITAL || c->nb % 2) return fail(G1G2_EINVAL, "double occupancy needs a spin-orbital basis");
     Launcher L = c->launcher();
-    double_occ(L, c->nb, c->n, c->G, c->red + 8);
+    double_occ(L, c->nb, c->n, c->G, c->eta, c->red + 8);
     if ((rc = launch_status(L, "double occupancy"))) return rc;
     if ((rc = cuda_check(cudaMemcpyAsync(dbl, c->red + 8, sizeof(double) * (c->nb / 2), cudaMemcpyDeviceToHost,
                                          c->stream), "copy")))
@@ -1155,6 +1165,7 @@ int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_de
   if (c->prec != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product runs on the FP64 form");
   if (c->se != G1G2_SOA && c->se != G1G2_HF)
     return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product covers HF and SOA");
+  if (c->eta > 0) return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product covers fermions");
   const long long N2 = (long long)c->nb * c->nb, N4 = N2 * N2;
   if (!c->AE) {  // scratch of the adjoint
     void *p;
@@ -1247,6 +1258,7 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
   if (!c || nsteps < 1 || !J_out) return fail(G1G2_EINVAL, "bad adjoint argument");
   if (c->prec != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint runs on the FP64 form");
   if (c->se != G1G2_SOA && c->se != G1G2_HF) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers HF and SOA");
+  if (c->eta > 0) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers fermions");
   if (objective < 0 || objective > 2) return fail(G1G2_EINVAL, "objective must be 0, 1 or 2");
   if (objective == 0 && (c->basis != G1G2_SPIN_ORBITAL || c->nb % 2))
     return fail(G1G2_EINVAL, "double occupancy needs a spin-orbital basis with index 2*site+spin");

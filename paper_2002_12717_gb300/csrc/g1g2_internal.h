@@ -81,8 +81,9 @@ void permute4(Launcher &L, int nb, const cplx *in, cplx *out, const int p[4], cp
 // hHF = h + f D + Wm * vec(n), Wm[(ij),(lk)] (real or complex), Eq. (h_HF).
 void hf_build(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *h, const cplx *D, double f,
               const cplx *n, cplx *hhf);
-// nbar = 1 - n
-void one_minus(Launcher &L, int nb, const cplx *n, cplx *nbar);
+// nbar = 1 + eta n: 1 - n for fermions (eta = -1), 1 + n for bosons (eta = +1)
+void one_pm(Launcher &L, int nb, const cplx *n, double eta, cplx *nbar);
+inline void one_minus(Launcher &L, int nb, const cplx *n, cplx *nbar) { one_pm(L, nb, n, -1.0, nbar); }
 
 // RK4 stage bookkeeping shared by the G1 and G2 updates.
 struct Rk4Stage {
@@ -111,8 +112,8 @@ void obs_one_body(Launcher &L, int nb, const cplx *h, const cplx *D, double f, c
 void obs_two_body(Launcher &L, int nb, const cplx *W, const cplx *G, double *partials, double *red);
 // W_acc += coeff * Re Tr(D n)
 void accumulate_work(Launcher &L, int nb, const cplx *D, const cplx *n, double coeff, double *W_acc);
-// out[s] = double occupancy of site s (spin-orbital index 2 s + spin).
-void double_occ(Launcher &L, int nb, const cplx *n, const cplx *G, double *out);
+// out[s] = double occupancy of site s (spin-orbital index 2 s + spin); eta the statistics sign.
+void double_occ(Launcher &L, int nb, const cplx *n, const cplx *G, double eta, double *out);
 // count non-finite entries of x (length len) into *cnt (double, accumulated)
 void count_nonfinite(Launcher &L, const cplx *x, long long len, double *cnt);
 

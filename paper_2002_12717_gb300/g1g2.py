@@ -28,7 +28,7 @@ class G1G2Error(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("basis", ctypes.c_int), ("w_is_real", ctypes.c_int),
-                ("sym_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
+                ("sym_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("statistics", ctypes.c_int)]
 
 
 class Obs(ctypes.Structure):
@@ -116,7 +116,7 @@ class Propagator:
     """One g1g2_ctx: state (G1 = n, G2), RK4 stepping, observables."""
 
     def __init__(self, h, w, n0, G2_0=None, selfenergy="SOA", precision="fp64", restricted=False,
-                 sym_tol=1e-10, stream=None):
+                 sym_tol=1e-10, stream=None, bosons=False):
         lib = load()
         self.nb = int(np.asarray(h).shape[0])
         self.restricted = restricted
@@ -127,6 +127,7 @@ class Propagator:
         opt.basis = 1 if restricted else 0
         opt.sym_tol = sym_tol
         opt.cuda_stream = stream
+        opt.statistics = 1 if bosons else 0
         w = np.asarray(w)
         if np.isrealobj(w):
             wbuf = np.ascontiguousarray(w, dtype=np.float64)

@@ -40,7 +40,7 @@ def test_strerror_and_defaults(lib):
     assert b"unknown" in lib.g1g2_strerror(42)
     opt = g1g2.Options()
     lib.g1g2_default_options(ctypes.byref(opt))
-    assert opt.precision == 0 and opt.basis == 0 and opt.sym_tol == pytest.approx(1e-10)
+    assert opt.precision == 0 and opt.basis == 0 and opt.sym_tol == pytest.approx(1e-10) and opt.statistics == 0
 
 
 def _init(lib, nb, h, w, n0, se=1, opt=None, g2=None):
@@ -82,6 +82,9 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert _init(lib, 4, *_valid(4), se=4, opt={"precision": 1}) == g1g2.EUNSUPPORTED   # T matrix: FP64 only
     assert _init(lib, 4, *_valid(4), se=5, opt={"precision": 2}) == g1g2.EUNSUPPORTED
     assert _init(lib, 4, *_valid(4), se=6, opt={"precision": 2}) == g1g2.EUNSUPPORTED
+    assert _init(lib, 3, h, w, n0, opt={"statistics": 2}) == g1g2.EINVAL
+    assert _init(lib, 3, h, w, n0, opt={"statistics": 1, "basis": 1}) == g1g2.EINVAL   # bosons: spin-orbital only
+    assert _init(lib, 4, *_valid(4), opt={"statistics": 1, "precision": 2}) == g1g2.EUNSUPPORTED
 
 
 def test_symmetry_violations_rejected_on_host(lib):

@@ -150,3 +150,76 @@ def test_dsl_rejects_the_spin_restricted_basis_and_tensor_core_forms():
     for kw in (dict(restricted=True), dict(precision="bf16x4"), dict(precision="tf32x3")):
         with pytest.raises(G1G2Error):
             Propagator(h, w, n, g2, "DSL", **kw)
+
+
+BOSON_CASES = [("HF", 5, False), ("SOA", 1, False), ("SOA", 6, True), ("SOA", 17, False), ("GW", 6, True),
+               ("GWX", 9, False), ("TPP", 6, True), ("TPH", 6, True), ("TPH", 17, False), ("DSL", 7, True)]
+
+
+@pytest.mark.parametrize("se,nb,complex_w", BOSON_CASES)
+def test_boson_rhs_parity(se, nb, complex_w):
+    """Bosons (statistics G1G2_BOSONS): w^+ in h^HF and Psi^±, nbar = 1 + n, the ph sign."""
+    from paper_2002_12717_gb300.g1g2 import Propagator
+    h, w, n, g2, D, drv = problem(nb, se, False, complex_w, seed=40 + nb)
+    prob = O.Problem(h, w, se, False, D, drv.f, bosons=True)
+    dn_ref, dg_ref = O.rhs(prob, 0.4, n, g2)
+    with Propagator(h, w, n, None, se, "fp64", bosons=True) as p:
+        p.set_drive(D, drv)
+        dn, dg = run_rhs(p, 0.4, n, g2)
+    assert rel_err(dn, dn_ref) < TOL_FP64
+    if se != "HF":
+        assert rel_err(dg, dg_ref) < TOL_FP64
+        if nb > 1:   # one mode: A is a real number and Psi = A^dag - A vanishes for both
+            _, dg_f = O.rhs(O.Problem(h, w, se, False, D, drv.f), 0.4, n, g2)
+            assert rel_err(dg_f, dg_ref) > 1e-3        # the boson form differs from the fermion one
+
+
+@pytest.mark.parametrize("se", ["SOA", "GW", "TPH"])
+def test_boson_hubbard_propagation_matches_oracle(se):
+    """Two-component Bose-Hubbard dimer with intra- and inter-component on-site
+    interaction, 100 RK4 steps: state, energies and double occupancy."""
+    from paper_2002_12717_gb300.g1g2 import Propagator
+    L = 2
+    hs = inputs.chain_hopping(L)
+    hs[0, 0] += 1.0
+    h = inputs.spin_orbital_h(hs)
+    w = inputs.spin_orbital_hubbard_w(L, 0.7).astype(np.complex128)
+    for i in range(2 * L):
+        w[i, i, i, i] += 0.5
+    n0 = np.diag([0.8, 0.6, 0.3, 0.2]).astype(np.complex128)
+    prob = O.Problem(h, w, se, bosons=True)
+    n_ref, g_ref, _, obs_ref = O.propagate(prob, n0, np.zeros((4,) * 4), 0.02, 100, obs_every=100)
+    with Propagator(h, w, n0, None, se, "fp64", bosons=True) as p:
+        obs, _ = p.propagate(0.02, 100, 100)
+        _, n, g = p.get_state()
+        o = p.observables(double_occ=True)
+    assert np.abs(n - n_ref).max() < 1e-12 and np.abs(g - g_ref).max() < 1e-12
+    for k in ("e_one", "e_hf", "e_corr", "e_total", "n_particles"):
+        assert abs(obs[-1][k] - obs_ref[-1][k]) < 1e-12, k
+    assert np.abs(o["double_occ"] - O.double_occupancy(n_ref, g_ref, L, eta=1)).max() < 1e-12
+    assert np.abs(g_ref).max() > 1e-3
+
+
+def test_boson_memory_integral_hfgkba_matches_oracle():
+    from oracle.hfgkba import propagate_hfgkba
+    from paper_2002_12717_gb300.g1g2 import Propagator
+    hs = inputs.chain_hopping(3)
+    hs[0, 0] += 1.0
+    w = np.zeros((3,) * 4, dtype=np.complex128)
+    for i in range(3):
+        w[i, i, i, i] = 1.0
+    n0 = np.diag([0.7, 0.4, 0.2]).astype(np.complex128)
+    ref = propagate_hfgkba(O.Problem(hs.astype(np.complex128), w, bosons=True), n0, 0.05, 20)
+    with Propagator(hs.astype(np.complex128), w, n0, None, "SOA", "fp64", bosons=True) as p:
+        got = p.propagate_hfgkba(0.05, 20)
+    assert np.abs(got - np.array(ref)).max() < 1e-12
+
+
+def test_boson_rejections():
+    from paper_2002_12717_gb300.g1g2 import G1G2Error, Propagator
+    h, w, n, g2, _, _ = problem(4, "SOA", seed=8, drive=False)
+    for kw in (dict(restricted=True), dict(precision="bf16x4"), dict(precision="tf32x3")):
+        with pytest.raises(G1G2Error):
+            Propagator(h, w, n, g2, "SOA", bosons=True, **kw)
+    with Propagator(h, w, n, None, "SOA", bosons=True) as p, pytest.raises(G1G2Error):
+        p.adjoint(0.01, 2, objective=0, ckpt_every=1, n_drive_params=0)
