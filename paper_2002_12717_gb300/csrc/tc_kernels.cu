@@ -328,6 +328,96 @@ __global__ void realify_pi_sliced_kernel(int nb, int kpad, const float *__restri
   }
 }
 
+// B operand of the particle-particle ladder product Lambda^dag = G2 H^dag (Eq. lambdapp;
+// G2 is Hermitian as an nb^2 x nb^2 matrix): the polarisation GEMM's layout, rows (c,d,v)
+// interleaved as 2 (c nb + d) + v, K = (u, p, q) as (u nb + p) kpad + q, value R(X)[u][v]
+// with X = H^dag_pqcd = conj(hcorr_cdpq) = P1_pqcd - P2_pqcd, both stored as [q][p][c][d]
+// (the two right-multiplication passes w x3 S x4 S with S = nbar and S = n).  Four BF16
+// slices with the exponent of max|P1| + max|P2|.  One CTA per (p, c) and a 32 x 32 tile
+// of (q, d): read along d, transposed in shared memory, written along q; q in
+// [nb, kpad) is written as zero padding.
+__global__ void realify_lam_sliced_kernel(int nb, int kpad, const float *__restrict__ P1s,
+                                          const float *__restrict__ P2s, long long P, const int *amax, int L,
+                                          __nv_bfloat16 *out, long long ldb, long long slice_stride) {
+  __shared__ float2 t1[32][33];
+  const long long N = nb;
+  const long long pc = blockIdx.y;
+  const long long p = pc / N, c = pc % N;
+  const int ntd = (nb + 31) / 32;
+  const int q0 = (blockIdx.x / ntd) * 32, d0 = (blockIdx.x % ntd) * 32;
+  const int tx = threadIdx.x, ty0 = threadIdx.y;
+  int E = 0;
+  {
+    const double bound = (double)__int_as_float(amax[0]) + (double)__int_as_float(amax[1]);
+    if (bound > 0.0) frexp(bound, &E);
+  }
+  float cut[4];
+#pragma unroll
+  for (int z = 0; z < 4; ++z) cut[z] = ldexpf(1.5f, 23 + E - L - 8 * z);
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int q = q0 + ty, d = d0 + tx;
+    float2 v = make_float2(0.f, 0.f);
+    if (q < nb && d < nb) {
+      const long long g = ((q * N + p) * N + c) * N + d;   // H^dag_{p q c d} at [q][p][c][d]
+      v = make_float2(P1s[g] - P2s[g], P1s[P + g] - P2s[P + g]);
+    }
+    t1[ty][tx] = v;
+  }
+  __syncthreads();
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int d = d0 + ty, q = q0 + tx;
+    if (d >= nb) continue;
+    const float2 h = t1[tx][ty];
+    for (int u = 0; u < 2; ++u)
+      for (int v = 0; v < 2; ++v) {
+        const float x = (u == 0) ? (v ? h.y : h.x) : (v ? h.x : -h.y);
+        const long long row = 2 * (c * N + d) + v;
+        const long long col = ((long long)u * N + p) * kpad + q;
+        float sl[4];
+        slice4(x, sl, cut);
+#pragma unroll
+        for (int z = 0; z < 4; ++z) out[z * slice_stride + row * ldb + col] = __float2bfloat16_rn(sl[z]);
+      }
+  }
+}
+
+// Gp[u][i][p][j][q] = G[u][i][j][p][q] (planar FP32): G2 seen by the polarisation GEMM's
+// row gather as rows (i, j) and K (p, q), the layout of the ladder product.
+__global__ void swap12_planar_kernel(int nb, const float *__restrict__ G, float *__restrict__ Gp, long long total) {
+  const long long N = nb;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long q = e % N, pp = (e / N) % N, j = (e / (N * N)) % N, ui = e / (N * N * N);
+    Gp[((ui * N + pp) * N + j) * N + q] = G[e];
+  }
+}
+
+// Q[a][b][c][d] -= Lam[a][d][c][b] (interleaved complex FP32): the ladder product from the
+// polarisation epilogue's layout into the source-term buffer's.  One CTA per (a, c) and a
+// 32 x 32 tile of (b, d), transposed in shared memory.
+__global__ void sub_swap13_kernel(int nb, const float2 *__restrict__ Lam, float2 *Q) {
+  __shared__ float2 t1[32][33];
+  const long long N = nb;
+  const long long ac = blockIdx.y;
+  const long long a = ac / N, c = ac % N;
+  const int nt = (nb + 31) / 32;
+  const int b0 = (blockIdx.x / nt) * 32, d0 = (blockIdx.x % nt) * 32;
+  const int tx = threadIdx.x, ty0 = threadIdx.y;
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int d = d0 + ty, b = b0 + tx;
+    if (d < nb && b < nb) t1[ty][tx] = Lam[((a * N + d) * N + c) * N + b];
+  }
+  __syncthreads();
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int b = b0 + ty, d = d0 + tx;
+    if (b < nb && d < nb) {
+      float2 *o = Q + ((a * N + b) * N + c) * N + d;
+      const float2 l = t1[tx][ty];
+      *o = make_float2(o->x - l.x, o->y - l.y);
+    }
+  }
+}
+
 struct AsmParams {
   int nb, nblk;
   const int4 *blocks;
@@ -600,6 +690,10 @@ struct TcPath {
   // GW: Y1 = w x_4 n, Y2 = w x_4 n^T, polarisation Pi, its B operand
   float *Y1 = nullptr, *Y2 = nullptr, *Pi = nullptr, *bpi_hi = nullptr, *bpi_lo = nullptr;
   float *bnt_hi = nullptr, *bnt_lo = nullptr;   // n^T, real A
+  // particle-particle T matrix: Y1/Y2 hold the two terms of H^dag, Pi the ladder product,
+  // bpi_s its B operand; Gp32 = G2 with its middle indices exchanged
+  float *Gp32 = nullptr;
+  __nv_bfloat16 *bnbr_s = nullptr, *bnbc_s = nullptr;  // nbar in the real-A and complex-A forms
   int pi_nout = 0, pi_ntiles = 0, pi_mtiles = 0;
   long long pi_ldb = 0;
   int4 *blocks = nullptr;
@@ -618,6 +712,7 @@ struct TcPath {
   CUtensorMap mZin_y32, mZin_ys32, mCol_y32, mCol_ys32, mW32, mWh32, mBuf1Gather, mBuf2Lin, mBuf1Lin;
   CUtensorMap mBh_hi, mBh_lo, mBnr_hi, mBnr_lo, mBnc_hi, mBnc_lo, mBnb_hi, mBnb_lo, mW_hi, mW_lo;
   CUtensorMap mPi_y32, mPi_ys32, mBpi_hi, mBpi_lo, mBnt_hi, mBnt_lo;
+  CUtensorMap mLam, mBnbr_s, mBnbc_s;
 };
 
 namespace {
@@ -625,7 +720,7 @@ namespace {
 // amax slots: FP32 bit patterns of the largest |A| of each A tensor of the sliced form
 enum : int {
   kAmaxW = 0, kAmaxY = 1, kAmaxYs = 2, kAmaxP1 = 3, kAmaxP2 = 4, kAmaxP3 = 5, kAmaxH1 = 6, kAmaxH2 = 7,
-  kAmaxWh = 8, kAmaxSlots = 16
+  kAmaxWh = 8, kAmaxT1 = 9, kAmaxT2 = 10, kAmaxSlots = 16
 };
 
 template <class T>
@@ -708,6 +803,11 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
     set_error_detail("the tensor-core form needs nb divisible by 4 (TMA row pitch)");
     return G1G2_EUNSUPPORTED;
   }
+  if (se == G1G2_TPP && !sliced) {
+    set_error_detail("the tensor-core ladder product runs in the BF16-slice form");
+    return G1G2_EUNSUPPORTED;
+  }
+  const bool big = se == G1G2_GW || se == G1G2_TPP;  // an nb^2 x nb^2 x nb^2 product (polarisation or ladder)
   const long long N = nb, N4 = N * N * N * N;
   for (long long e = 0; e < N4; ++e)
     if (hw[e].y != 0.0) {
@@ -750,7 +850,7 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
       return bail(rc);
     if (cudaMemset(t->amax, 0, kAmaxSlots * sizeof(int)) != cudaSuccess) return bail(G1G2_ECUDA);
   }
-  if (se == G1G2_GW) {
+  if (big) {
     const long long ncol = 2 * N * N;  // output columns (j, l, v)
     // the sliced form keeps three accumulators of nout columns in TMEM (512 columns)
     t->pi_nout = (int)std::min<long long>(sliced ? kPiNoutSliced : 256, ((ncol + 15) / 16) * 16);
@@ -772,6 +872,11 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
       if ((rc = talloc(t, &t->bpi_s, (size_t)kSlices * brows * t->pi_ldb))) return bail(rc);
       if (cudaMemset(t->bpi_s, 0, (size_t)kSlices * brows * t->pi_ldb * sizeof(__nv_bfloat16)) != cudaSuccess)
         return bail(G1G2_ECUDA);
+    }
+    if (se == G1G2_TPP) {
+      const size_t bs_c = (size_t)kSlices * t->nout2 * kt_c, bs_r = (size_t)kSlices * t->nout2 * kt_r;
+      if ((rc = talloc(t, &t->Gp32, 2 * N4)) || (rc = talloc(t, &t->bnbr_s, bs_r)) || (rc = talloc(t, &t->bnbc_s, bs_c)))
+        return bail(rc);
     }
   }
   // collision split-K geometry: K = nb^3 floats, both planes
@@ -815,7 +920,7 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
     if (cudaMemcpy(t->W32, w32.data(), N4 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(G1G2_ECUDA);
     t->Wh32 = t->W32;
-    if (se == G1G2_GW && !src_is_w) {
+    if (big && !src_is_w) {
       std::vector<float> wh(N4);
       float hmax = 0.f;
       for (long long e = 0; e < N4; ++e) {
@@ -872,7 +977,7 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
       (rc = map_b(&t->mBnb_lo, t->bnb_lo, kt_c, t->nout2, t->nout2)) ||
       (rc = map_b(&t->mW_hi, t->w_hi, (int)N3, nb, t->nout1)) ||
       (rc = map_b(&t->mW_lo, t->w_lo, (int)N3, nb, t->nout1)) ||
-      (se == G1G2_GW &&
+      (big &&
        ((rc = map_gather(&t->mPi_y32, t->y32, nb, 32, 1, 4)) || (rc = map_gather(&t->mPi_ys32, t->ys32, nb, 32, 1, 4)) ||
         (rc = map_b(&t->mBpi_hi, t->bpi_hi, (int)t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
         (rc = map_b(&t->mBpi_lo, t->bpi_lo, (int)t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
@@ -884,17 +989,21 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
                   (rc = map_bs(&t->mBnb_s, t->bnb_s, kt_c, t->nout2, t->nout2)) ||
                   (rc = map_bs(&t->mBnt_s, t->bnt_s, kt_r, t->nout2, t->nout2)) ||
                   (rc = map_bs(&t->mW_s, t->w_s, N3, nb, t->nout1)) ||
-                  (se == G1G2_GW &&
+                  (big &&
                    ((rc = map_bs(&t->mBpi_s, t->bpi_s, t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
                     (rc = map_bs(&t->mBpi_s_half, t->bpi_s, t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout / 2,
-                                 1))))))) {
+                                 1)))) ||
+                  (se == G1G2_TPP &&
+                   ((rc = map_gather(&t->mLam, t->Gp32, nb, 32, 1, 4)) ||
+                    (rc = map_bs(&t->mBnbr_s, t->bnbr_s, kt_r, t->nout2, t->nout2)) ||
+                    (rc = map_bs(&t->mBnbc_s, t->bnbc_s, kt_c, t->nout2, t->nout2))))))) {
     set_error_detail("cuTensorMapEncodeTiled failed");
     return bail(rc);
   }
   int st = 0;
   const size_t acc64 = (size_t)nb * (nb + 1) * sizeof(float2);
   size_t smax = std::max(gemm_smem(sliced, t->nout2, &st), gemm_smem(sliced, t->nout1, &st, acc64));
-  if (se == G1G2_GW) smax = std::max(smax, gemm_smem(sliced, t->pi_nout, &st));
+  if (big) smax = std::max(smax, gemm_smem(sliced, t->pi_nout, &st));
   if (smax > 227 * 1024) {
     set_error_detail("basis too large for the FP64 split-K accumulator of the tensor-core collision integral");
     return bail(G1G2_EUNSUPPORTED);
@@ -1007,15 +1116,19 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   one_minus(L, nb, n_in, t->nbar);
   if (sl) {
     const int kc = 2 * t->kpad;
-    struct { const cplx *S; int complex_a, shift, ld, transpose, il; __nv_bfloat16 *out; } ops[5] = {
+    struct { const cplx *S; int complex_a, shift, ld, transpose, il; __nv_bfloat16 *out; } ops[7] = {
         {hhf, 1, 1, kc, 0, 1, t->bh_s},
         {n_in, 0, 0, t->kpad, 0, 0, t->bnr_s},
         {n_in, 1, 0, kc, 0, 0, t->bnc_s},
         {t->nbar, 1, 0, kc, 0, 1, t->bnb_s},
-        {n_in, 0, 0, t->kpad, 1, 0, t->bnt_s}};
-    const int nops = (t->se == G1G2_GW) ? 5 : 4;
-    for (int q = 0; q < nops; ++q) {
-      const auto &o = ops[q];
+        {n_in, 0, 0, t->kpad, 1, 0, t->bnt_s},       // GW: n^T
+        {t->nbar, 0, 0, t->kpad, 0, 0, t->bnbr_s},   // ladder: nbar, real A
+        {t->nbar, 1, 0, kc, 0, 0, t->bnbc_s}};       // ladder: nbar, complex A
+    int sel[7] = {0, 1, 2, 3, 0, 0, 0}, nops = 4;
+    if (t->se == G1G2_GW) sel[nops++] = 4;
+    if (t->se == G1G2_TPP) { sel[nops++] = 5; sel[nops++] = 6; }
+    for (int qi = 0; qi < nops; ++qi) {
+      const auto &o = ops[sel[qi]];
       L.before("tc_slice_b");
       slice_b_kernel<<<64, 256, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.ld, o.transpose, o.il,
                                                o.S, o.out, (long long)t->nout2 * o.ld);
@@ -1137,6 +1250,58 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     g.cluster2 = (sl && t->pi_pair) ? 1 : 0;
     launch_gemm(t, L, "tc_gemm_pi", from_y ? t->mPi_y32 : t->mPi_ys32,
                 sl ? (g.cluster2 ? t->mBpi_s_half : t->mBpi_s) : t->mBpi_hi, t->mBpi_lo, g, sl);
+  }
+  if (t->se == G1G2_TPP) {
+    // Eq. (HTPPcorr): H^dag_pqkl = sum_rs w_pqrs (nbar_rk nbar_sl - n_rk n_sl), each term as two
+    // right multiplications of w (x_4 S into the exchange-permuted layout, then x_4 S again),
+    // stored as [q][p][k][l] in Y1 (nbar) and Y2 (n)
+    cudaMemsetAsync(amax + kAmaxH1, 0, 2 * sizeof(int), L.stream);
+    cudaMemsetAsync(amax + kAmaxT1, 0, 2 * sizeof(int), L.stream);
+    const int wh_slot = (t->Wh32 == t->W32) ? kAmaxW : kAmaxWh;
+    launch_gemm(t, L, "tc_gemm_ladder_h", t->mWh32, t->mBnbr_s, t->mBnbr_s,
+                lp(N3, 1, EP_EXCH_T, t->buf1, wh_slot, kAmaxT1), sl);
+    launch_gemm(t, L, "tc_gemm_ladder_h", t->mBuf1Lin, t->mBnbc_s, t->mBnbc_s,
+                lp(N3, 2, EP_SWAP34, t->Y1, kAmaxT1, kAmaxH1), sl);
+    launch_gemm(t, L, "tc_gemm_ladder_h", t->mWh32, t->mBnr_s, t->mBnr_s,
+                lp(N3, 1, EP_EXCH_T, t->buf1, wh_slot, kAmaxT2), sl);
+    launch_gemm(t, L, "tc_gemm_ladder_h", t->mBuf1Lin, t->mBnc_s, t->mBnc_s,
+                lp(N3, 2, EP_SWAP34, t->Y2, kAmaxT2, kAmaxH2), sl);
+    const long long brows = (long long)t->pi_ntiles * t->pi_nout;
+    L.before("tc_realify_ladder");
+    realify_lam_sliced_kernel<<<dim3((unsigned)((t->kpad / 32) * ((nb + 31) / 32)), (unsigned)(N * N)), dim3(32, 8), 0,
+                                L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, amax + kAmaxH1, t->pi_lead, t->bpi_s,
+                                            t->pi_ldb, brows * t->pi_ldb);
+    L.after_launch();
+    L.before("tc_swap12");
+    swap12_planar_kernel<<<2048, 256, 0, L.stream>>>(nb, from_y ? t->y32 : t->ys32, t->Gp32, 2 * t->N4);
+    L.after_launch();
+    // Eq. (lambdapp): Lambda^dag_(ij),(kl) = sum_(pq) G_ijpq H^dag_pqkl, the polarisation
+    // GEMM with G2 read through the exchanged copy (rows (i, j), K (p, q))
+    GemmParams g{};
+    g.nb = nb;
+    g.a_rows = AR_PI;
+    g.epi = EP_PI;
+    g.n_tiles = t->pi_ntiles;
+    g.pi_mk = (nb + 31) / 32;
+    g.pi_kq = t->kpad / kBlockK;
+    g.pi_mtiles = t->pi_mtiles;
+    g.tiles = t->pi_mtiles * t->pi_ntiles;
+    g.nout = t->pi_nout;
+    g.n_valid = t->pi_nout;
+    g.rows = 2 * N * N;
+    g.out = t->Pi;
+    g.out_plane = t->N4;
+    g.a_amax = g2_amax;
+    g.slice_lead = t->pi_lead;
+    g.acc3 = 1;
+    g.cluster2 = t->pi_pair ? 1 : 0;
+    launch_gemm(t, L, "tc_gemm_ladder", t->mLam, g.cluster2 ? t->mBpi_s_half : t->mBpi_s, t->mBpi_s, g, sl);
+    // the source term becomes (A - Lambda)^dag: Psi + Lambda - Lambda^dag in the assembly
+    const int nt = (nb + 31) / 32;
+    L.before("tc_ladder_into_source");
+    sub_swap13_kernel<<<dim3((unsigned)(nt * nt), (unsigned)(N * N)), dim3(32, 8), 0, L.stream>>>(
+        nb, reinterpret_cast<const float2 *>(t->Pi), reinterpret_cast<float2 *>(t->buf2));
+    L.after_launch();
   }
   // a7: orbit assembly + RK4
   AsmParams a{};
