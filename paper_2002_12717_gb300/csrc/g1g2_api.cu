@@ -788,10 +788,8 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   if (nb < 1 || nb > 128) return fail(G1G2_EINVAL, "nb must be in [1, 128]");
   if (!h || !w || !G1_0) return fail(G1G2_EINVAL, "h, w and G1_0 must be non-NULL");
   if (se < G1G2_HF || se > G1G2_DSL) return fail(G1G2_EINVAL, "bad selfenergy");
-  if ((se == G1G2_TPH || se == G1G2_DSL) && opt.precision != G1G2_FP64)
-    return fail(G1G2_EUNSUPPORTED, "the particle-hole ladder term runs on the FP64 form");
-  if (se == G1G2_TPP && opt.precision == G1G2_TF32X3)
-    return fail(G1G2_EUNSUPPORTED, "the particle-particle ladder term runs on the FP64 and BF16-slice forms");
+  if ((se == G1G2_TPP || se == G1G2_TPH || se == G1G2_DSL) && opt.precision == G1G2_TF32X3)
+    return fail(G1G2_EUNSUPPORTED, "the ladder terms run on the FP64 and BF16-slice forms");
   // GW with exchange is GW with the source term Psi^± (w^- in Psi)
   const bool gw_exchange = se == G1G2_GW_EXCHANGE;
   if (gw_exchange) se = G1G2_GW;

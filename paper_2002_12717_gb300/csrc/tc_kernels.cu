@@ -392,6 +392,56 @@ __global__ void swap12_planar_kernel(int nb, const float *__restrict__ G, float 
   }
 }
 
+// Gq[u][i][p][l][q] = G[u][i][p][q][l] (planar FP32): G2 with its last two indices exchanged,
+// seen by the polarisation GEMM's row gather as rows (i, l) and K (p, q), the layout of the
+// particle-hole ladder product.  One CTA per (u, i, p) and 32 x 32 tile of (q, l), all in
+// blockIdx.x (2 nb^2 nt^2 blocks).
+__global__ void swap34_planar_kernel(int nb, const float *__restrict__ G, float *__restrict__ Gq) {
+  __shared__ float t1[32][33];
+  const long long N = nb;
+  const int nt = (nb + 31) / 32;
+  const long long uip = (long long)blockIdx.x / (nt * nt);   // (u nb + i) nb + p
+  const int tile = (int)((long long)blockIdx.x % (nt * nt));
+  const int q0 = (tile / nt) * 32, l0 = (tile % nt) * 32;
+  const int tx = threadIdx.x, ty0 = threadIdx.y;
+  const long long base = uip * N * N;
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int q = q0 + ty, l = l0 + tx;
+    if (q < nb && l < nb) t1[ty][tx] = G[base + q * N + l];
+  }
+  __syncthreads();
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int l = l0 + ty, q = q0 + tx;
+    if (l < nb && q < nb) Gq[base + l * N + q] = t1[tx][ty];
+  }
+}
+
+// Q[a][b][c][d] -= Lam[a][d][b][c] (interleaved complex FP32): the particle-hole ladder
+// product from the polarisation epilogue's layout into the source-term buffer's.  One
+// CTA per (a, b) and a 32 x 32 tile of (c, d), transposed in shared memory.
+__global__ void sub_rot_kernel(int nb, const float2 *__restrict__ Lam, float2 *Q) {
+  __shared__ float2 t1[32][33];
+  const long long N = nb;
+  const long long ab = blockIdx.y;
+  const long long a = ab / N, b = ab % N;
+  const int nt = (nb + 31) / 32;
+  const int c0 = (blockIdx.x / nt) * 32, d0 = (blockIdx.x % nt) * 32;
+  const int tx = threadIdx.x, ty0 = threadIdx.y;
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int d = d0 + ty, c = c0 + tx;
+    if (d < nb && c < nb) t1[ty][tx] = Lam[((a * N + d) * N + b) * N + c];
+  }
+  __syncthreads();
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int c = c0 + ty, d = d0 + tx;
+    if (c < nb && d < nb) {
+      float2 *o = Q + ((a * N + b) * N + c) * N + d;
+      const float2 l = t1[tx][ty];
+      *o = make_float2(o->x - l.x, o->y - l.y);
+    }
+  }
+}
+
 // Q[a][b][c][d] -= Lam[a][d][c][b] (interleaved complex FP32): the ladder product from the
 // polarisation epilogue's layout into the source-term buffer's.  One CTA per (a, c) and a
 // 32 x 32 tile of (b, d), transposed in shared memory.
@@ -694,6 +744,11 @@ struct TcPath {
   // bpi_s its B operand; Gp32 = G2 with its middle indices exchanged
   float *Gp32 = nullptr;
   __nv_bfloat16 *bnbr_s = nullptr, *bnbc_s = nullptr;  // nbar in the real-A and complex-A forms
+  // particle-hole T matrix: Wp32[p][q][r][s] = w_rpqs, nbar^T in the real-A form; Lam: the
+  // ladder products' output when the polarisation output Pi must survive (DSL)
+  float *Wp32 = nullptr, *Lam = nullptr;
+  __nv_bfloat16 *bnbt_s = nullptr;
+  bool has_pi = false, has_pp = false, has_ph = false;
   int pi_nout = 0, pi_ntiles = 0, pi_mtiles = 0;
   long long pi_ldb = 0;
   int4 *blocks = nullptr;
@@ -712,7 +767,7 @@ struct TcPath {
   CUtensorMap mZin_y32, mZin_ys32, mCol_y32, mCol_ys32, mW32, mWh32, mBuf1Gather, mBuf2Lin, mBuf1Lin;
   CUtensorMap mBh_hi, mBh_lo, mBnr_hi, mBnr_lo, mBnc_hi, mBnc_lo, mBnb_hi, mBnb_lo, mW_hi, mW_lo;
   CUtensorMap mPi_y32, mPi_ys32, mBpi_hi, mBpi_lo, mBnt_hi, mBnt_lo;
-  CUtensorMap mLam, mBnbr_s, mBnbc_s;
+  CUtensorMap mLam, mBnbr_s, mBnbc_s, mWp32, mBnbt_s;
 };
 
 namespace {
@@ -803,11 +858,13 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
     set_error_detail("the tensor-core form needs nb divisible by 4 (TMA row pitch)");
     return G1G2_EUNSUPPORTED;
   }
-  if (se == G1G2_TPP && !sliced) {
+  const bool has_pi = se == G1G2_GW || se == G1G2_DSL, has_pp = se == G1G2_TPP || se == G1G2_DSL,
+             has_ph = se == G1G2_TPH || se == G1G2_DSL;
+  if ((has_pp || has_ph) && !sliced) {
     set_error_detail("the tensor-core ladder product runs in the BF16-slice form");
     return G1G2_EUNSUPPORTED;
   }
-  const bool big = se == G1G2_GW || se == G1G2_TPP;  // an nb^2 x nb^2 x nb^2 product (polarisation or ladder)
+  const bool big = has_pi || has_pp || has_ph;  // an nb^2 x nb^2 x nb^2 product (polarisation or ladder)
   const long long N = nb, N4 = N * N * N * N;
   for (long long e = 0; e < N4; ++e)
     if (hw[e].y != 0.0) {
@@ -819,6 +876,9 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
   t->se = se;
   t->restricted = restricted;
   t->sliced = sliced;
+  t->has_pi = has_pi;
+  t->has_pp = has_pp;
+  t->has_ph = has_ph;
   t->N4 = N4;
   t->kpad = round_up(nb, kBlockK);
   t->nout2 = round_up(2 * nb, 16);
@@ -873,11 +933,15 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
       if (cudaMemset(t->bpi_s, 0, (size_t)kSlices * brows * t->pi_ldb * sizeof(__nv_bfloat16)) != cudaSuccess)
         return bail(G1G2_ECUDA);
     }
-    if (se == G1G2_TPP) {
+    if (has_pp || has_ph) {
       const size_t bs_c = (size_t)kSlices * t->nout2 * kt_c, bs_r = (size_t)kSlices * t->nout2 * kt_r;
-      if ((rc = talloc(t, &t->Gp32, 2 * N4)) || (rc = talloc(t, &t->bnbr_s, bs_r)) || (rc = talloc(t, &t->bnbc_s, bs_c)))
+      if ((rc = talloc(t, &t->Gp32, 2 * N4)) || (rc = talloc(t, &t->bnbr_s, bs_r)) ||
+          (rc = talloc(t, &t->bnbc_s, bs_c)) || (rc = talloc(t, &t->bnbt_s, bs_r)))
         return bail(rc);
+      t->Lam = t->Pi;
+      if (has_pi && (rc = talloc(t, &t->Lam, 2 * N4))) return bail(rc);
     }
+    if (has_ph && (rc = talloc(t, &t->Wp32, N4))) return bail(rc);
   }
   // collision split-K geometry: K = nb^3 floats, both planes
   t->kb_all_coll = (int)((N * N * N + kBlockK - 1) / kBlockK);
@@ -931,6 +995,23 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
       if (cudaMemcpy(t->Wh32, wh.data(), N4 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(G1G2_ECUDA);
       if (sliced) {
+        int bits = 0;
+        std::memcpy(&bits, &hmax, sizeof(bits));
+        cudaMemcpy(t->amax + kAmaxWh, &bits, sizeof(int), cudaMemcpyHostToDevice);
+      }
+    }
+    if (has_ph) {  // Wp32[p][q][r][s] = w_rpqs: the particle-hole quasi-Hamiltonian as right multiplications
+      std::vector<float> wp(N4);
+      for (long long r = 0; r < N; ++r)
+        for (long long p = 0; p < N; ++p)
+          for (long long q = 0; q < N; ++q)
+            for (long long u = 0; u < N; ++u)
+              wp[((p * N + q) * N + r) * N + u] = (float)hw[((r * N + p) * N + q) * N + u].x;
+      if (cudaMemcpy(t->Wp32, wp.data(), N4 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(G1G2_ECUDA);
+      if (sliced && t->Wh32 == t->W32) {  // the slot of plain w must hold max|w|
+        float hmax = 0.f;
+        for (long long e = 0; e < N4; ++e) hmax = std::max(hmax, std::fabs(wp[e]));
         int bits = 0;
         std::memcpy(&bits, &hmax, sizeof(bits));
         cudaMemcpy(t->amax + kAmaxWh, &bits, sizeof(int), cudaMemcpyHostToDevice);
@@ -993,10 +1074,12 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
                    ((rc = map_bs(&t->mBpi_s, t->bpi_s, t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
                     (rc = map_bs(&t->mBpi_s_half, t->bpi_s, t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout / 2,
                                  1)))) ||
-                  (se == G1G2_TPP &&
+                  ((has_pp || has_ph) &&
                    ((rc = map_gather(&t->mLam, t->Gp32, nb, 32, 1, 4)) ||
                     (rc = map_bs(&t->mBnbr_s, t->bnbr_s, kt_r, t->nout2, t->nout2)) ||
-                    (rc = map_bs(&t->mBnbc_s, t->bnbc_s, kt_c, t->nout2, t->nout2))))))) {
+                    (rc = map_bs(&t->mBnbc_s, t->bnbc_s, kt_c, t->nout2, t->nout2)) ||
+                    (rc = map_bs(&t->mBnbt_s, t->bnbt_s, kt_r, t->nout2, t->nout2)))) ||
+                  (has_ph && (rc = map_linear(&t->mWp32, t->Wp32, nb, N3, 1)))))) {
     set_error_detail("cuTensorMapEncodeTiled failed");
     return bail(rc);
   }
@@ -1116,17 +1199,20 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   one_minus(L, nb, n_in, t->nbar);
   if (sl) {
     const int kc = 2 * t->kpad;
-    struct { const cplx *S; int complex_a, shift, ld, transpose, il; __nv_bfloat16 *out; } ops[7] = {
+    struct { const cplx *S; int complex_a, shift, ld, transpose, il; __nv_bfloat16 *out; } ops[8] = {
         {hhf, 1, 1, kc, 0, 1, t->bh_s},
         {n_in, 0, 0, t->kpad, 0, 0, t->bnr_s},
         {n_in, 1, 0, kc, 0, 0, t->bnc_s},
         {t->nbar, 1, 0, kc, 0, 1, t->bnb_s},
         {n_in, 0, 0, t->kpad, 1, 0, t->bnt_s},       // GW: n^T
         {t->nbar, 0, 0, t->kpad, 0, 0, t->bnbr_s},   // ladder: nbar, real A
-        {t->nbar, 1, 0, kc, 0, 0, t->bnbc_s}};       // ladder: nbar, complex A
-    int sel[7] = {0, 1, 2, 3, 0, 0, 0}, nops = 4;
-    if (t->se == G1G2_GW) sel[nops++] = 4;
-    if (t->se == G1G2_TPP) { sel[nops++] = 5; sel[nops++] = 6; }
+        {t->nbar, 1, 0, kc, 0, 0, t->bnbc_s},        // ladder: nbar, complex A
+        {t->nbar, 0, 0, t->kpad, 1, 0, t->bnbt_s}};  // particle-hole ladder: nbar^T, real A
+    int sel[8] = {0, 1, 2, 3, 0, 0, 0, 0}, nops = 4;
+    if (t->has_pi || t->has_ph) sel[nops++] = 4;
+    if (t->has_pp) sel[nops++] = 5;
+    if (t->has_pp || t->has_ph) sel[nops++] = 6;
+    if (t->has_ph) sel[nops++] = 7;
     for (int qi = 0; qi < nops; ++qi) {
       const auto &o = ops[sel[qi]];
       L.before("tc_slice_b");
@@ -1143,7 +1229,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
         {n_in, 1, 0, 1.0, kc, 0, 0, 0, t->bnc_hi, t->bnc_lo},
         {t->nbar, 1, 0, 1.0, kc, 0, 0, 1, t->bnb_hi, t->bnb_lo},
         {n_in, 0, 0, 1.0, t->kpad, 0, 1, 0, t->bnt_hi, t->bnt_lo}};
-    const int nops = sl ? 0 : (t->se == G1G2_GW) ? 5 : 4;  // the sliced form slices these above
+    const int nops = sl ? 0 : t->has_pi ? 5 : 4;  // the sliced form slices these above
     for (int q = 0; q < nops; ++q) {
       const auto &o = ops[q];
       L.before("tc_realify");
@@ -1209,7 +1295,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
               il(lp(N3, 2, EP_SWAP34, t->Z, -1, -1), true), sl);
   launch_gemm(t, L, "tc_gemm_psi4", t->mBuf1Lin, sl ? t->mBnb_s : t->mBnb_hi, t->mBnb_lo,
               il(lp(N3, 2, EP_SWAP34, t->buf2, kAmaxP3, -1), true), sl);
-  if (t->se == G1G2_GW) {
+  if (t->has_pi) {
     // a5: Y1 = w x_4 n, Y2 = w x_4 n^T (hcorr_ijkl = Y1_ijkl - Y2_klij), swapped layout
     if (sl) cudaMemsetAsync(amax + kAmaxH1, 0, 2 * sizeof(int), L.stream);
     const int wh_slot = (t->Wh32 == t->W32) ? kAmaxW : kAmaxWh;
@@ -1251,32 +1337,27 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     launch_gemm(t, L, "tc_gemm_pi", from_y ? t->mPi_y32 : t->mPi_ys32,
                 sl ? (g.cluster2 ? t->mBpi_s_half : t->mBpi_s) : t->mBpi_hi, t->mBpi_lo, g, sl);
   }
-  if (t->se == G1G2_TPP) {
-    // Eq. (HTPPcorr): H^dag_pqkl = sum_rs w_pqrs (nbar_rk nbar_sl - n_rk n_sl), each term as two
-    // right multiplications of w (x_4 S into the exchange-permuted layout, then x_4 S again),
-    // stored as [q][p][k][l] in Y1 (nbar) and Y2 (n)
+  // Ladder terms (Sec. IV.D/E): H^dag as P1 - P2, each term two right multiplications of a
+  // real interaction tensor Wt (x_4 S into the exchange-permuted layout, then x_4 S' again,
+  // stored as [q][p][k][l] = sum_rs Wt_pqrs S'_rk S_sl in Y1, Y2), the sliced B operand, then
+  // the polarisation GEMM with G2 read through a permuted copy, and the product subtracted
+  // from the source-term buffer: Psi + Lambda - Lambda^dag = -(A - Lambda) + (A - Lambda)^dag.
+  auto ladder = [&](const char *tag, const CUtensorMap &mWt, int wt_slot, const CUtensorMap &B1a,
+                    const CUtensorMap &B1b, const CUtensorMap &B2a, const CUtensorMap &B2b) {
     cudaMemsetAsync(amax + kAmaxH1, 0, 2 * sizeof(int), L.stream);
     cudaMemsetAsync(amax + kAmaxT1, 0, 2 * sizeof(int), L.stream);
-    const int wh_slot = (t->Wh32 == t->W32) ? kAmaxW : kAmaxWh;
-    launch_gemm(t, L, "tc_gemm_ladder_h", t->mWh32, t->mBnbr_s, t->mBnbr_s,
-                lp(N3, 1, EP_EXCH_T, t->buf1, wh_slot, kAmaxT1), sl);
-    launch_gemm(t, L, "tc_gemm_ladder_h", t->mBuf1Lin, t->mBnbc_s, t->mBnbc_s,
-                lp(N3, 2, EP_SWAP34, t->Y1, kAmaxT1, kAmaxH1), sl);
-    launch_gemm(t, L, "tc_gemm_ladder_h", t->mWh32, t->mBnr_s, t->mBnr_s,
-                lp(N3, 1, EP_EXCH_T, t->buf1, wh_slot, kAmaxT2), sl);
-    launch_gemm(t, L, "tc_gemm_ladder_h", t->mBuf1Lin, t->mBnc_s, t->mBnc_s,
-                lp(N3, 2, EP_SWAP34, t->Y2, kAmaxT2, kAmaxH2), sl);
+    launch_gemm(t, L, tag, mWt, B1a, B1a, lp(N3, 1, EP_EXCH_T, t->buf1, wt_slot, kAmaxT1), sl);
+    launch_gemm(t, L, tag, t->mBuf1Lin, B1b, B1b, lp(N3, 2, EP_SWAP34, t->Y1, kAmaxT1, kAmaxH1), sl);
+    launch_gemm(t, L, tag, mWt, B2a, B2a, lp(N3, 1, EP_EXCH_T, t->buf1, wt_slot, kAmaxT2), sl);
+    launch_gemm(t, L, tag, t->mBuf1Lin, B2b, B2b, lp(N3, 2, EP_SWAP34, t->Y2, kAmaxT2, kAmaxH2), sl);
     const long long brows = (long long)t->pi_ntiles * t->pi_nout;
     L.before("tc_realify_ladder");
     realify_lam_sliced_kernel<<<dim3((unsigned)((t->kpad / 32) * ((nb + 31) / 32)), (unsigned)(N * N)), dim3(32, 8), 0,
                                 L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, amax + kAmaxH1, t->pi_lead, t->bpi_s,
                                             t->pi_ldb, brows * t->pi_ldb);
     L.after_launch();
-    L.before("tc_swap12");
-    swap12_planar_kernel<<<2048, 256, 0, L.stream>>>(nb, from_y ? t->y32 : t->ys32, t->Gp32, 2 * t->N4);
-    L.after_launch();
-    // Eq. (lambdapp): Lambda^dag_(ij),(kl) = sum_(pq) G_ijpq H^dag_pqkl, the polarisation
-    // GEMM with G2 read through the exchanged copy (rows (i, j), K (p, q))
+  };
+  auto ladder_gemm = [&](const char *tag) {
     GemmParams g{};
     g.nb = nb;
     g.a_rows = AR_PI;
@@ -1289,18 +1370,42 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     g.nout = t->pi_nout;
     g.n_valid = t->pi_nout;
     g.rows = 2 * N * N;
-    g.out = t->Pi;
+    g.out = t->Lam;
     g.out_plane = t->N4;
     g.a_amax = g2_amax;
     g.slice_lead = t->pi_lead;
     g.acc3 = 1;
     g.cluster2 = t->pi_pair ? 1 : 0;
-    launch_gemm(t, L, "tc_gemm_ladder", t->mLam, g.cluster2 ? t->mBpi_s_half : t->mBpi_s, t->mBpi_s, g, sl);
-    // the source term becomes (A - Lambda)^dag: Psi + Lambda - Lambda^dag in the assembly
-    const int nt = (nb + 31) / 32;
+    launch_gemm(t, L, tag, t->mLam, g.cluster2 ? t->mBpi_s_half : t->mBpi_s, t->mBpi_s, g, sl);
+  };
+  const float *g32 = from_y ? t->y32 : t->ys32;
+  const int nt32 = (nb + 31) / 32;
+  if (t->has_pp) {
+    // Eq. (HTPPcorr): H^dag_pqkl = sum_rs w_pqrs (nbar_rk nbar_sl - n_rk n_sl)
+    const int wh_slot = (t->Wh32 == t->W32) ? kAmaxW : kAmaxWh;
+    ladder("tc_gemm_ladder_h", t->mWh32, wh_slot, t->mBnbr_s, t->mBnbc_s, t->mBnr_s, t->mBnc_s);
+    L.before("tc_swap12");
+    swap12_planar_kernel<<<2048, 256, 0, L.stream>>>(nb, g32, t->Gp32, 2 * t->N4);
+    L.after_launch();
+    // Eq. (lambdapp): Lambda^dag_(ij),(kl) = sum_(pq) G_ijpq H^dag_pqkl (rows (i, j), K (p, q))
+    ladder_gemm("tc_gemm_ladder");
     L.before("tc_ladder_into_source");
-    sub_swap13_kernel<<<dim3((unsigned)(nt * nt), (unsigned)(N * N)), dim3(32, 8), 0, L.stream>>>(
-        nb, reinterpret_cast<const float2 *>(t->Pi), reinterpret_cast<float2 *>(t->buf2));
+    sub_swap13_kernel<<<dim3((unsigned)(nt32 * nt32), (unsigned)(N * N)), dim3(32, 8), 0, L.stream>>>(
+        nb, reinterpret_cast<const float2 *>(t->Lam), reinterpret_cast<float2 *>(t->buf2));
+    L.after_launch();
+  }
+  if (t->has_ph) {
+    // Eq. (HTPHcorr): X_(pq),(kj) = conj(hcorr_kpqj) = sum_rs w_rpqs (n_rk nbar_js - nbar_rk n_js),
+    // with Wp32[p][q][r][s] = w_rpqs: S' = n, S = nbar^T, then S' = nbar, S = n^T
+    ladder("tc_gemm_ladder_h", t->mWp32, kAmaxWh, t->mBnbt_s, t->mBnc_s, t->mBnt_s, t->mBnbc_s);
+    L.before("tc_swap34");
+    swap34_planar_kernel<<<(unsigned)(2 * N * N * nt32 * nt32), dim3(32, 8), 0, L.stream>>>(nb, g32, t->Gp32);
+    L.after_launch();
+    // Eq. (lambdaph): Lambda^dag_ijkl = sum_pq G_ipql X_(pq),(kj) (rows (i, l), K (p, q))
+    ladder_gemm("tc_gemm_ladder");
+    L.before("tc_ladder_into_source");
+    sub_rot_kernel<<<dim3((unsigned)(nt32 * nt32), (unsigned)(N * N)), dim3(32, 8), 0, L.stream>>>(
+        nb, reinterpret_cast<const float2 *>(t->Lam), reinterpret_cast<float2 *>(t->buf2));
     L.after_launch();
   }
   // a7: orbit assembly + RK4
@@ -1310,7 +1415,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   a.blocks = t->blocks;
   a.Z = t->Z;
   a.Q = t->buf2;
-  a.Pi = (t->se == G1G2_GW) ? t->Pi : nullptr;
+  a.Pi = t->has_pi ? t->Pi : nullptr;
   a.P = t->N4;
   a.y = Gy;
   a.acc = t->acc;

@@ -144,10 +144,10 @@ def test_t_matrix_propagation_matches_oracle(se):
     assert abs(obs[-1]["e_total"] - obs_ref[-1]["e_total"]) < 1e-12
 
 
-def test_dsl_rejects_the_spin_restricted_basis_and_tensor_core_forms():
+def test_dsl_rejects_the_spin_restricted_basis_and_the_tf32_form():
     from paper_2002_12717_gb300.g1g2 import G1G2Error, Propagator
-    h, w, n, g2, _, _ = problem(6, "DSL", seed=2, drive=False)
-    for kw in (dict(restricted=True), dict(precision="bf16x4"), dict(precision="tf32x3")):
+    h, w, n, g2, _, _ = problem(8, "DSL", seed=2, drive=False)
+    for kw in (dict(restricted=True), dict(precision="tf32x3")):
         with pytest.raises(G1G2Error):
             Propagator(h, w, n, g2, "DSL", **kw)
 

@@ -72,27 +72,33 @@ def test_tc_rhs_parity(se, nb, restricted, prec):
     assert e1 < tol_rhs(se, nb, prec) and e2 < tol_rhs(se, nb, prec)
 
 
-@pytest.mark.parametrize("nb,restricted", [(4, False), (8, False), (12, False), (20, False), (32, False),
-                                          (36, False), (8, True)])
-def test_tc_ladder_rhs_parity(nb, restricted):
-    """Particle-particle T matrix in the BF16-slice form: the ladder product sums
-    K' = 2 nb^2 products of two FP32-stored tensors, the bar of the polarisation."""
+LADDER_CASES = [("TPP", 4, False), ("TPP", 8, False), ("TPP", 12, False), ("TPP", 20, False), ("TPP", 32, False),
+                ("TPP", 36, False), ("TPP", 8, True), ("TPH", 4, False), ("TPH", 8, False), ("TPH", 12, False),
+                ("TPH", 20, False), ("TPH", 36, False), ("TPH", 8, True), ("DSL", 4, False), ("DSL", 12, False),
+                ("DSL", 32, False)]
+
+
+@pytest.mark.parametrize("se,nb,restricted", LADDER_CASES)
+def test_tc_ladder_rhs_parity(se, nb, restricted):
+    """T matrices and DSL in the BF16-slice form: each ladder product sums K' = 2 nb^2
+    products of two FP32-stored tensors, the bar of the polarisation."""
     from paper_2002_12717_gb300.g1g2 import Propagator
-    h, w, n, g2, D, drv = problem(nb, "TPP", restricted, False, seed=300 + nb)
-    prob = O.Problem(h, w, "TPP", restricted, D, drv.f)
+    h, w, n, g2, D, drv = problem(nb, se, restricted, False, seed=300 + nb)
+    prob = O.Problem(h, w, se, restricted, D, drv.f)
     dn_ref, dg_ref = O.rhs(prob, 0.4, n, g2)
-    with Propagator(h, w, n, None, "TPP", "bf16x4", restricted) as p:
+    with Propagator(h, w, n, None, se, "bf16x4", restricted) as p:
         p.set_drive(D, drv)
         dn, dg = run_rhs(p, 0.4, n, g2)
     e1, e2 = rel_err(dn, dn_ref), rel_err(dg, dg_ref)
-    print(f"bf16x4 TPP nb={nb} restricted={restricted}: dn {e1:.2e} dG2 {e2:.2e}")
+    print(f"bf16x4 {se} nb={nb} restricted={restricted}: dn {e1:.2e} dG2 {e2:.2e}")
     assert e1 < tol_rhs("GW", nb, "bf16x4") and e2 < tol_rhs("GW", nb, "bf16x4")
 
 
-def test_tc_ladder_propagation_tracks_fp64_form():
-    """nb=16 seeded general basis, 100 RK4 steps of the particle-particle T matrix."""
+@pytest.mark.parametrize("se", ["TPP", "TPH", "DSL"])
+def test_tc_ladder_propagation_tracks_fp64_form(se):
+    """nb=16 seeded general basis, 100 RK4 steps of the T matrices and DSL."""
     from paper_2002_12717_gb300.g1g2 import from_workload
-    d = inputs.general_basis(16, 32, 8, seed=12, selfenergy="TPP", pulse=True)
+    d = inputs.general_basis(16, 32, 8, seed=12, selfenergy=se, pulse=True)
     d["drive"] = inputs.GaussSine(A=0.5, omega=1.5, t0=0.5, sigma=0.3)
     res = {}
     for pr in ("fp64", "bf16x4"):
@@ -103,7 +109,7 @@ def test_tc_ladder_propagation_tracks_fp64_form():
     dn = np.abs(res["bf16x4"][1] - res["fp64"][1]).max()
     dg = np.abs(res["bf16x4"][2] - res["fp64"][2]).max()
     de = max(abs(a["e_total"] - b["e_total"]) for a, b in zip(res["bf16x4"][0], res["fp64"][0]))
-    print(f"bf16x4 TPP: max|dG1| {dn:.2e}  max|dG2| {dg:.2e}  max|dE| {de:.2e}")
+    print(f"bf16x4 {se}: max|dG1| {dn:.2e}  max|dG2| {dg:.2e}  max|dE| {de:.2e}")
     assert np.abs(res["fp64"][2]).max() > 1e-3
     assert dn < 1e-6 and dg < 1e-6 and de < 1e-6
 
@@ -111,7 +117,7 @@ def test_tc_ladder_propagation_tracks_fp64_form():
 def test_tc_ladder_rejects_tf32():
     from paper_2002_12717_gb300.g1g2 import EUNSUPPORTED, G1G2Error, Propagator
     h, w, n, _, _, _ = problem(8, "TPP", seed=2, drive=False)
-    for se, prec in (("TPP", "tf32x3"), ("TPH", "bf16x4"), ("DSL", "bf16x4")):
+    for se, prec in (("TPP", "tf32x3"), ("TPH", "tf32x3"), ("DSL", "tf32x3")):
         with pytest.raises(G1G2Error) as e:
             Propagator(h, w, n, None, se, prec)
         assert e.value.code == EUNSUPPORTED
