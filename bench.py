@@ -92,7 +92,7 @@ def kernel_work(tag, nb, se, precision="tf32x3"):
     """
     n = float(nb)
     split = SPLIT_PRODUCTS.get(precision, 3) * 2
-    if tag == "tc_gemm_pi":
+    if tag in ("tc_gemm_pi", "tc_gemm_ladder"):
         return "tensor", split * n * n * (2 * n * n) * (2 * n * n)
     if tag in ("tc_gemm_commutator", "tc_gemm_psi2", "tc_gemm_psi3", "tc_gemm_psi4"):
         return "tensor", split * n ** 3 * (2 * n) * (2 * n)
@@ -471,41 +471,53 @@ FP64_CMAC = {
     "TPH": lambda n: 13 * n ** 5 + n ** 6,
     "DSL": lambda n: 19 * n ** 5 + 3 * n ** 6,
 }
-FP64_DFMA_TFLOPS = 1.200   # measured FP64 DFMA rate of this GPU (profiles/fp64_dfma_peak.md)
 
 
-def selfenergy_sweep(sizes, steps=2):
-    """ms per RK4 step of every selfenergy in the FP64 form on the seeded general basis
-    (rank 2 nb, nb/2 occupied, gauss-sine pulse), with the algorithmic FLOP rate
-    against the measured DFMA rate."""
+def selfenergy_sweep(sizes, precisions=("fp64",), steps=2):
+    """ms per RK4 step of every selfenergy on the seeded general basis (rank 2 nb, nb/2
+    occupied, gauss-sine pulse).  FP64 form: the algorithmic FLOP rate against the
+    measured DFMA rate; BF16-slice form: the rate of its nb^2 x nb^2 x nb^2 products
+    (polarisation, ladder) in issued slice products against the measured sustained BF16
+    rate."""
     import torch
 
     from paper_2002_12717_gb300.g1g2 import from_workload
 
+    peaks, _ = load_peaks()
     out = []
-    for nb in sizes:
-        for se in ("SOA", "GW", "GWX", "TPP", "TPH", "DSL"):
-            d = inputs.general_basis(nb, 2 * nb, nb // 2, seed=nb, selfenergy=se, pulse=True)
-            with from_workload(d) as p:
+    for prec, nb, se in ((pr, nb, se) for pr in precisions for nb in sizes
+                         for se in ("SOA", "GW", "GWX", "TPP", "TPH", "DSL")):
+        d = inputs.general_basis(nb, 2 * nb, nb // 2, seed=nb, selfenergy=se, pulse=True)
+        with from_workload(d, precision=prec) as p:
+            p.step(0.01)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
                 p.step(0.01)
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(steps):
-                    p.step(0.01)
-                e1.record()
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / steps
-                p.profile(True)
-                p.step(0.01)
-                prof = p.profile_report()
-                p.profile(False)
-            tot = sum(v[1] for v in prof.values())
-            top = max(prof.items(), key=lambda kv: kv[1][1])
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            p.profile(True)
+            p.step(0.01)
+            prof = p.profile_report()
+            p.profile(False)
+        tot = sum(v[1] for v in prof.values())
+        top = max(prof.items(), key=lambda kv: kv[1][1])
+        row = {"precision": prec, "nb": nb, "selfenergy": se, "ms_per_step": round(ms, 3),
+               "top_kernel": top[0], "top_share": round(top[1][1] / tot, 3)}
+        if prec == "fp64":
             tflops = 4 * 8 * FP64_CMAC[se](nb) / (ms * 1e-3) / 1e12
-            out.append({"nb": nb, "selfenergy": se, "ms_per_step": round(ms, 3),
-                        "algorithmic_tflops": round(tflops, 4), "frac_of_dfma": round(tflops / FP64_DFMA_TFLOPS, 3),
-                        "top_kernel": top[0], "top_share": round(top[1][1] / tot, 3)})
+            row.update(algorithmic_tflops=round(tflops, 4), frac_of_dfma=round(tflops / FP64_PEAK_TFLOPS, 3))
+        else:
+            for tag in ("tc_gemm_pi", "tc_gemm_ladder"):
+                if tag in prof:
+                    launches, tms = prof[tag]
+                    work = kernel_work(tag, nb, se, prec)[1]
+                    tf = work * launches / (tms * 1e-3) / 1e12
+                    row[tag] = {"ms_per_launch": round(tms / launches, 3), "issued_tflops": round(tf, 1),
+                                "frac_of_bf16_sustained": round(tf / peaks["bf16_tflops_sustained"], 3)}
+        out.append(row)
     return out
 
 
@@ -581,7 +593,8 @@ def main():
     ap.add_argument("--nt-scaling", default="",
                     help="comma-separated N_t: time the memory-integral HF-GKBA against the G1-G2 equations and exit")
     ap.add_argument("--selfenergy-sweep", default="",
-                    help="comma-separated nb: time every selfenergy in the FP64 form and exit")
+                    help="comma-separated nb: time every selfenergy and exit (forms: --sweep-precisions)")
+    ap.add_argument("--sweep-precisions", default="fp64", help="comma-separated forms of --selfenergy-sweep")
     ap.add_argument("--adjoint-steps", type=int, default=100,
                     help="steps of the discrete-adjoint sample on the 4x4 Hubbard cluster (0: skip)")
     args = ap.parse_args()
@@ -601,8 +614,9 @@ def main():
         return
     if args.selfenergy_sweep:
         if rank == 0:
-            print(json.dumps({"selfenergy_sweep": selfenergy_sweep([int(x) for x in args.selfenergy_sweep.split(",")])}),
-                  flush=True)
+            sweep = selfenergy_sweep([int(x) for x in args.selfenergy_sweep.split(",")],
+                                     args.sweep_precisions.split(","))
+            print(json.dumps({"selfenergy_sweep": sweep}), flush=True)
         return
     if args.nt_scaling:
         if rank == 0:
