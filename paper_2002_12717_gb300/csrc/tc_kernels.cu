@@ -48,7 +48,8 @@ using namespace tc;
 
 namespace {
 
-constexpr int BSZ = 8;                      // assembly block edge
+constexpr int BSZ_LOG = 2;
+constexpr int BSZ = 1 << BSZ_LOG;            // assembly block edge; divides nb (nb % 4 == 0 here)
 constexpr int kPiNoutSliced = 128;          // polarisation N tile of the sliced form (3 accumulators in TMEM)
 constexpr int BEL = BSZ * BSZ * BSZ * BSZ;  // elements per block
 
@@ -486,109 +487,87 @@ struct AsmParams {
 __device__ __forceinline__ int bidx(int a, int b, int c, int d) { return ((a * BSZ + b) * BSZ + c) * BSZ + d; }
 // Shared-memory slot of block element (a,b,c,d): the last coordinate is XOR-swizzled
 // with the other three so that the four orbit permutations hit (nearly) distinct banks.
-__device__ __forceinline__ int sidx(int a, int b, int c, int d) { return bidx(a, b, c, d ^ ((a ^ b ^ c) & 7)); }
+__device__ __forceinline__ int sidx(int a, int b, int c, int d) {
+  return bidx(a, b, c, d ^ ((a ^ b ^ c) & (BSZ - 1)));
+}
 
-constexpr int ATHREADS = 1024;              // assembly threads per CTA
+// 4^4 blocks: 8 KB of shared memory and 256 threads per orbit CTA, so that eight CTAs
+// share an SM and the load, combine and update phases of different orbits overlap
+constexpr int ATHREADS = 256;               // assembly threads per CTA
 constexpr int APER = BEL / ATHREADS;        // element orbits per thread
 
 __device__ __forceinline__ void elem(int e, int &a, int &b, int &c, int &d) {
-  a = e >> 9; b = (e >> 6) & 7; c = (e >> 3) & 7; d = e & 7;
-}
-
-// Load the four member blocks of src (interleaved complex FP32) into sm.  With
-// swap34 the tensor is stored with its last two indices exchanged (the GEMM
-// epilogue layout), so block (B0,B1,B2,B3) is read as the stored block
-// (B0,B1,B3,B2); its element for the natural index (a,b,c,d) then sits at
-// bidx(a,b,d,c).  A block row is 8 consecutive complex values (64 bytes).
-__device__ __forceinline__ void load_blocks(const AsmParams &p, const float *src, const int (&X)[4][4], float2 *sm,
-                                            bool swap34) {
-  const long long N = p.nb;
-  float2 v[4][APER];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const int B2 = swap34 ? X[m][3] : X[m][2], B3 = swap34 ? X[m][2] : X[m][3];
-#pragma unroll
-    for (int t = 0; t < APER; ++t) {
-      int a, b, c, d;
-      elem(threadIdx.x + ATHREADS * t, a, b, c, d);
-      const long long g0 = X[m][0] * BSZ + a, g1 = X[m][1] * BSZ + b, g2 = B2 * BSZ + c, g3 = B3 * BSZ + d;
-      v[m][t] = make_float2(0.f, 0.f);
-      if (g0 < N && g1 < N && g2 < N && g3 < N) {
-        const long long g = ((g0 * N + g1) * N + g2) * N + g3;
-        v[m][t] = reinterpret_cast<const float2 *>(src)[g];
-      }
-    }
-  }
-#pragma unroll
-  for (int m = 0; m < 4; ++m)
-#pragma unroll
-    for (int t = 0; t < APER; ++t) {
-      int a, b, c, d;
-      elem(threadIdx.x + ATHREADS * t, a, b, c, d);
-      sm[m * BEL + sidx(a, b, c, d)] = v[m][t];
-    }
+  a = e >> (3 * BSZ_LOG); b = (e >> (2 * BSZ_LOG)) & (BSZ - 1); c = (e >> BSZ_LOG) & (BSZ - 1); d = e & (BSZ - 1);
 }
 
 __device__ __forceinline__ float2 sval(const float2 *sm, int m, int a, int b, int c, int d, bool swap34) {
   return sm[m * BEL + (swap34 ? sidx(a, b, d, c) : sidx(a, b, c, d))];
 }
 
-// One CTA per orbit {X, exch X, trans X, exch trans X} of 8^4 blocks, each
-// thread APER element orbits.  Z and Q arrive in the swapped layout.
-__global__ void __launch_bounds__(ATHREADS) orbit_assemble_kernel(const AsmParams p) {
+// One CTA per orbit {X, exch X, trans X, exch trans X} of BSZ^4 blocks, each thread
+// APER element orbits.  Z, Q and Pi arrive in the swapped layout and enter only as
+// V = Z - Q/2 - Pi/2 per element: with P = U - (Q + exch Q)/2 and U = Z + exch Z,
+// dG2 = -i (P^dag - P) plus the polarisation term (Pi_ijkl - conj(Pi_lkji), symmetrised
+// over the exchange) is, on the two exchange pairs (0,1) and (2,3) of the orbit,
+//   k0 = -i (conj(V2 + V3) - (V0 + V1)),   k2 = -i (conj(V0 + V1) - (V2 + V3)).
+// So one load phase reads Z, Q and Pi together with the RK4 state of the update, one
+// shared-memory exchange forms the orbit sums, and the update stores.  The tensor-core
+// form requires nb % 4 == 0 (tc_create), so BSZ = 4 blocks tile the tensor exactly and
+// no element of a block lies outside it.
+__global__ void __launch_bounds__(ATHREADS, 4) orbit_assemble_kernel(const AsmParams p) {
   extern __shared__ float2 sm[];  // 4 * BEL
   const int4 base = p.blocks[blockIdx.x];
   const int X[4][4] = {{base.x, base.y, base.z, base.w},
                        {base.y, base.x, base.w, base.z},
                        {base.z, base.w, base.x, base.y},
                        {base.w, base.z, base.y, base.x}};
-  float2 kx[APER], ky[APER];
-
-  load_blocks(p, p.Z, X, sm, true);
-  __syncthreads();
+  const long long N = p.nb;
+  bool dup[4];
 #pragma unroll
-  for (int t = 0; t < APER; ++t) {
-    int a, b, c, d;
-    elem(threadIdx.x + ATHREADS * t, a, b, c, d);
-    const float2 z0 = sval(sm, 0, a, b, c, d, true), z1 = sval(sm, 1, b, a, d, c, true);
-    const float2 z2 = sval(sm, 2, c, d, a, b, true), z3 = sval(sm, 3, d, c, b, a, true);
-    kx[t] = make_float2(z0.x + z1.x, z0.y + z1.y);
-    ky[t] = make_float2(z2.x + z3.x, z2.y + z3.y);
+  for (int m = 0; m < 4; ++m) {
+    dup[m] = false;
+    for (int q = 0; q < m; ++q)
+      dup[m] |= (X[q][0] == X[m][0] && X[q][1] == X[m][1] && X[q][2] == X[m][2] && X[q][3] == X[m][3]);
   }
-  __syncthreads();
-  load_blocks(p, p.Q, X, sm, true);
-  __syncthreads();
+  const bool rk = p.stage >= 0, acc_in = p.stage > 0;
+  cplx y0[4][APER];
+  float2 ac[4][APER];
 #pragma unroll
-  for (int t = 0; t < APER; ++t) {
-    int a, b, c, d;
-    elem(threadIdx.x + ATHREADS * t, a, b, c, d);
-    // P = U - (Q + exch Q)/2 on the two exchange pairs of the orbit
-    const float2 q0 = sval(sm, 0, a, b, c, d, true), q1 = sval(sm, 1, b, a, d, c, true);
-    const float2 q2 = sval(sm, 2, c, d, a, b, true), q3 = sval(sm, 3, d, c, b, a, true);
-    const float2 P0 = make_float2(kx[t].x - 0.5f * (q0.x + q1.x), kx[t].y - 0.5f * (q0.y + q1.y));
-    const float2 P2 = make_float2(ky[t].x - 0.5f * (q2.x + q3.x), ky[t].y - 0.5f * (q2.y + q3.y));
-    // k0 = -i (conj(P2) - P0),  k2 = -i (conj(P0) - P2)
-    const float2 D = make_float2(P2.x - P0.x, -P2.y - P0.y);
-    const float2 E = make_float2(P0.x - P2.x, -P0.y - P2.y);
-    kx[t] = make_float2(D.y, -D.x);
-    ky[t] = make_float2(E.y, -E.x);
-  }
-  if (p.Pi) {
-    __syncthreads();
-    load_blocks(p, p.Pi, X, sm, true);
-    __syncthreads();
+  for (int m = 0; m < 4; ++m)
 #pragma unroll
     for (int t = 0; t < APER; ++t) {
       int a, b, c, d;
       elem(threadIdx.x + ATHREADS * t, a, b, c, d);
-      const float2 p0 = sval(sm, 0, a, b, c, d, true), p1 = sval(sm, 1, b, a, d, c, true);
-      const float2 p2 = sval(sm, 2, c, d, a, b, true), p3 = sval(sm, 3, d, c, b, a, true);
-      // R = Pi_ijkl - conj(Pi_lkji) on the four members, symmetrised over exchange
-      const float2 s01 = make_float2(0.5f * ((p0.x - p3.x) + (p1.x - p2.x)), 0.5f * ((p0.y + p3.y) + (p1.y + p2.y)));
-      const float2 s23 = make_float2(0.5f * ((p2.x - p1.x) + (p3.x - p0.x)), 0.5f * ((p2.y + p1.y) + (p3.y + p0.y)));
-      kx[t] = make_float2(kx[t].x + s01.y, kx[t].y - s01.x);
-      ky[t] = make_float2(ky[t].x + s23.y, ky[t].y - s23.x);
+      // stored (swapped) element of block (X0, X1, X3, X2): natural in-block index (a, b, d, c)
+      const long long gs = (((X[m][0] * BSZ + a) * N + X[m][1] * BSZ + b) * N + X[m][3] * BSZ + c) * N +
+                           X[m][2] * BSZ + d;
+      const float2 z = reinterpret_cast<const float2 *>(p.Z)[gs];
+      const float2 q = reinterpret_cast<const float2 *>(p.Q)[gs];
+      float2 v = make_float2(z.x - 0.5f * q.x, z.y - 0.5f * q.y);
+      if (p.Pi) {
+        const float2 pi = reinterpret_cast<const float2 *>(p.Pi)[gs];
+        v = make_float2(v.x - 0.5f * pi.x, v.y - 0.5f * pi.y);
+      }
+      sm[m * BEL + sidx(a, b, c, d)] = v;
+      // RK4 state of the natural element (a, b, c, d) of member m
+      const long long gn = (((X[m][0] * BSZ + a) * N + X[m][1] * BSZ + b) * N + X[m][2] * BSZ + c) * N +
+                           X[m][3] * BSZ + d;
+      y0[m][t] = rk && !dup[m] ? p.y[gn] : make_double2(0.0, 0.0);
+      ac[m][t] = acc_in && !dup[m] ? reinterpret_cast<const float2 *>(p.acc)[gn] : make_float2(0.f, 0.f);
     }
+  __syncthreads();
+  float2 kx[APER], ky[APER];
+#pragma unroll
+  for (int t = 0; t < APER; ++t) {
+    int a, b, c, d;
+    elem(threadIdx.x + ATHREADS * t, a, b, c, d);
+    const float2 v0 = sval(sm, 0, a, b, c, d, true), v1 = sval(sm, 1, b, a, d, c, true);
+    const float2 v2 = sval(sm, 2, c, d, a, b, true), v3 = sval(sm, 3, d, c, b, a, true);
+    const float2 s01 = make_float2(v0.x + v1.x, v0.y + v1.y), s23 = make_float2(v2.x + v3.x, v2.y + v3.y);
+    const float2 D = make_float2(s23.x - s01.x, -s23.y - s01.y);   // conj(s23) - s01
+    const float2 E = make_float2(s01.x - s23.x, -s01.y - s23.y);   // conj(s01) - s23
+    kx[t] = make_float2(D.y, -D.x);
+    ky[t] = make_float2(E.y, -E.x);
   }
   __syncthreads();
 #pragma unroll
@@ -601,58 +580,39 @@ __global__ void __launch_bounds__(ATHREADS) orbit_assemble_kernel(const AsmParam
     sm[3 * BEL + sidx(d, c, b, a)] = ky[t];
   }
   __syncthreads();
-  // RK4 update of each distinct member block, in natural (coalesced) order;
-  // all loads of a member are issued before its stores
-  const long long N = p.nb;
-  cplx *__restrict__ yv = p.y;
+  // RK4 update of each distinct member block, in natural (coalesced) order
   float *__restrict__ accv = p.acc;
   float *__restrict__ ysv = p.ys;
   float *__restrict__ y32v = p.y32;
   const long long P = p.P;
   const double dt = p.dt;
   float mx = 0.f;
+#pragma unroll
   for (int m = 0; m < 4; ++m) {
-    bool dup = false;
-    for (int q = 0; q < m; ++q)
-      dup |= (X[q][0] == X[m][0] && X[q][1] == X[m][1] && X[q][2] == X[m][2] && X[q][3] == X[m][3]);
-    if (dup) continue;
-    long long g[APER];
-    bool in[APER];
-    float2 k[APER];
-    cplx y0[APER];
-    float2 ac[APER];
+    if (dup[m]) continue;
 #pragma unroll
     for (int t = 0; t < APER; ++t) {
       int a, b, c, d;
       elem(threadIdx.x + ATHREADS * t, a, b, c, d);
-      const long long g0 = X[m][0] * BSZ + a, g1 = X[m][1] * BSZ + b, g2 = X[m][2] * BSZ + c, g3 = X[m][3] * BSZ + d;
-      in[t] = g0 < N && g1 < N && g2 < N && g3 < N;
-      g[t] = ((g0 * N + g1) * N + g2) * N + g3;
-      k[t] = sm[m * BEL + sidx(a, b, c, d)];
-      if (in[t] && p.stage >= 0) {
-        y0[t] = yv[g[t]];
-        ac[t] = (p.stage > 0) ? reinterpret_cast<const float2 *>(accv)[g[t]] : make_float2(0.f, 0.f);
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < APER; ++t) {
-      if (!in[t]) continue;
+      const long long g = (((X[m][0] * BSZ + a) * N + X[m][1] * BSZ + b) * N + X[m][2] * BSZ + c) * N +
+                          X[m][3] * BSZ + d;
+      const float2 k = sm[m * BEL + sidx(a, b, c, d)];
       if (p.stage < 0) {
-        p.kout[g[t]] = make_double2((double)k[t].x, (double)k[t].y);
+        p.kout[g] = make_double2((double)k.x, (double)k.y);
       } else if (p.stage < 3) {
         const double h = (p.stage == 2) ? dt : 0.5 * dt;
         const float w = (p.stage == 0) ? 1.f : 2.f;
-        reinterpret_cast<float2 *>(accv)[g[t]] = make_float2(ac[t].x + w * k[t].x, ac[t].y + w * k[t].y);
-        const float sx = (float)(y0[t].x + h * k[t].x), sy = (float)(y0[t].y + h * k[t].y);
-        ysv[g[t]] = sx;
-        ysv[P + g[t]] = sy;
+        reinterpret_cast<float2 *>(accv)[g] = make_float2(ac[m][t].x + w * k.x, ac[m][t].y + w * k.y);
+        const float sx = (float)(y0[m][t].x + h * k.x), sy = (float)(y0[m][t].y + h * k.y);
+        ysv[g] = sx;
+        ysv[P + g] = sy;
         mx = fmaxf(mx, fmaxf(fabsf(sx), fabsf(sy)));
       } else {
-        const double nx = y0[t].x + dt / 6.0 * ((double)ac[t].x + (double)k[t].x);
-        const double ny = y0[t].y + dt / 6.0 * ((double)ac[t].y + (double)k[t].y);
-        yv[g[t]] = make_double2(nx, ny);
-        y32v[g[t]] = (float)nx;
-        y32v[P + g[t]] = (float)ny;
+        const double nx = y0[m][t].x + dt / 6.0 * ((double)ac[m][t].x + (double)k.x);
+        const double ny = y0[m][t].y + dt / 6.0 * ((double)ac[m][t].y + (double)k.y);
+        p.y[g] = make_double2(nx, ny);
+        y32v[g] = (float)nx;
+        y32v[P + g] = (float)ny;
         mx = fmaxf(mx, fmaxf(fabsf((float)nx), fabsf((float)ny)));
       }
     }
