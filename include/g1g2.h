@@ -101,8 +101,8 @@ typedef struct {
  * G^> = -i (1 + n) (Eq. g-glsymm) in the source term and the T-matrix
  * quasi-Hamiltonians.  The G1 equation in (n, G2), the collision integral, the
  * commutator and the GW quasi-Hamiltonian are the same for both.  Bosons run
- * in the spin-orbital basis and the FP64 form (G1G2_EUNSUPPORTED otherwise);
- * the discrete adjoint and the Hubbard path are fermion-only. */
+ * in the spin-orbital basis (G1G2_EINVAL otherwise), in every precision; the
+ * discrete adjoint and the Hubbard path are fermion-only. */
 enum { G1G2_FERMIONS = 0, G1G2_BOSONS = 1 };
 
 typedef struct {

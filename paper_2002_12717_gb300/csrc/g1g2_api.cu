@@ -800,7 +800,6 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   const bool bosons = opt.statistics == G1G2_BOSONS;
   if (bosons && opt.basis == G1G2_SPIN_RESTRICTED)
     return fail(G1G2_EINVAL, "the spin-restricted mode is the fermion Hubbard form; bosons run in the spin-orbital basis");
-  if (bosons && opt.precision != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "bosons run in the FP64 form");
   if (opt.basis == G1G2_SPIN_RESTRICTED && (se == G1G2_GW || se == G1G2_DSL))
     return fail(G1G2_EINVAL, "GW couples same-spin components and has no spin-restricted form");
 
@@ -964,7 +963,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   if (correlated && c->prec != G1G2_FP64) {
     if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "init sync"))) return bail(rc);
     g_detail.clear();
-    rc = tc_create(&c->tc, nb, se, restricted, c->prec == G1G2_BF16X4, hw.data(), hsrc.data(), c->stream);
+    rc = tc_create(&c->tc, nb, se, restricted, c->prec == G1G2_BF16X4, bosons, hw.data(), hsrc.data(), c->stream);
     if (rc) return bail(rc);
     Launcher L = c->launcher();
     tc_load_state(c->tc, L, c->G);

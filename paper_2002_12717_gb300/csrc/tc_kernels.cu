@@ -709,6 +709,7 @@ struct TcPath {
   float *Wp32 = nullptr, *Lam = nullptr;
   __nv_bfloat16 *bnbt_s = nullptr;
   bool has_pi = false, has_pp = false, has_ph = false;
+  double eta = -1.0;    // statistics sign: nbar = 1 + eta n (-1 fermions, +1 bosons)
   int pi_nout = 0, pi_ntiles = 0, pi_mtiles = 0;
   long long pi_ldb = 0;
   int4 *blocks = nullptr;
@@ -811,7 +812,7 @@ GemmParams linear_params(const TcPath *t, long long rows, int planes, int epi, f
 
 }  // namespace
 
-int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const cplx *hw, const cplx *hsrc,
+int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool bosons, const cplx *hw, const cplx *hsrc,
               cudaStream_t stream) {
   *out = nullptr;
   if (nb % 4 != 0) {
@@ -837,6 +838,7 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const 
   t->restricted = restricted;
   t->sliced = sliced;
   t->has_pi = has_pi;
+  t->eta = bosons ? 1.0 : -1.0;
   t->has_pp = has_pp;
   t->has_ph = has_ph;
   t->N4 = N4;
@@ -1156,7 +1158,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   const int *g2_amax = sl ? amax + (from_y ? kAmaxY : kAmaxYs) : nullptr;
   if (sl) cudaMemsetAsync(amax + kAmaxP1, 0, 3 * sizeof(int), L.stream);  // this call's source-term passes
   // small operands
-  one_minus(L, nb, n_in, t->nbar);
+  one_pm(L, nb, n_in, t->eta, t->nbar);
   if (sl) {
     const int kc = 2 * t->kpad;
     struct { const cplx *S; int complex_a, shift, ld, transpose, il; __nv_bfloat16 *out; } ops[8] = {
@@ -1356,8 +1358,12 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   }
   if (t->has_ph) {
     // Eq. (HTPHcorr): X_(pq),(kj) = conj(hcorr_kpqj) = sum_rs w_rpqs (n_rk nbar_js - nbar_rk n_js),
-    // with Wp32[p][q][r][s] = w_rpqs: S' = n, S = nbar^T, then S' = nbar, S = n^T
-    ladder("tc_gemm_ladder_h", t->mWp32, kAmaxWh, t->mBnbt_s, t->mBnc_s, t->mBnt_s, t->mBnbc_s);
+    // with Wp32[p][q][r][s] = w_rpqs: S' = n, S = nbar^T, then S' = nbar, S = n^T; bosons
+    // (G^< = -i n, G^> = -i (1 + n)) have the opposite sign: the two terms trade places
+    if (t->eta < 0)
+      ladder("tc_gemm_ladder_h", t->mWp32, kAmaxWh, t->mBnbt_s, t->mBnc_s, t->mBnt_s, t->mBnbc_s);
+    else
+      ladder("tc_gemm_ladder_h", t->mWp32, kAmaxWh, t->mBnt_s, t->mBnbc_s, t->mBnbt_s, t->mBnc_s);
     L.before("tc_swap34");
     swap34_planar_kernel<<<(unsigned)(2 * N * N * nt32 * nt32), dim3(32, 8), 0, L.stream>>>(nb, g32, t->Gp32);
     L.after_launch();

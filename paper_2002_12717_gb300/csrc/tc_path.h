@@ -10,7 +10,8 @@ struct TcPath;
 // Build the tensor-core path for one context. hw: w (complex, [(ij),(kl)]),
 // hsrc: source-term interaction (w^- for SOA in a spin-orbital basis, else w).
 // sliced: BF16-slice operands with an exact leading product instead of TF32 hi/lo.
-int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, const cplx *hw, const cplx *hsrc,
+// bosons: nbar = 1 + n (instead of 1 - n) and the sign of the particle-hole quasi-Hamiltonian.
+int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool bosons, const cplx *hw, const cplx *hsrc,
               cudaStream_t stream);
 void tc_destroy(TcPath *p);
 

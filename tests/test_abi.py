@@ -84,7 +84,6 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert _init(lib, 4, *_valid(4), se=6, opt={"precision": 1}) == g1g2.EUNSUPPORTED
     assert _init(lib, 3, h, w, n0, opt={"statistics": 2}) == g1g2.EINVAL
     assert _init(lib, 3, h, w, n0, opt={"statistics": 1, "basis": 1}) == g1g2.EINVAL   # bosons: spin-orbital only
-    assert _init(lib, 4, *_valid(4), opt={"statistics": 1, "precision": 2}) == g1g2.EUNSUPPORTED
 
 
 def test_symmetry_violations_rejected_on_host(lib):

@@ -218,8 +218,7 @@ def test_boson_memory_integral_hfgkba_matches_oracle():
 def test_boson_rejections():
     from paper_2002_12717_gb300.g1g2 import G1G2Error, Propagator
     h, w, n, g2, _, _ = problem(4, "SOA", seed=8, drive=False)
-    for kw in (dict(restricted=True), dict(precision="bf16x4"), dict(precision="tf32x3")):
-        with pytest.raises(G1G2Error):
-            Propagator(h, w, n, g2, "SOA", bosons=True, **kw)
+    with pytest.raises(G1G2Error):
+        Propagator(h, w, n, g2, "SOA", bosons=True, restricted=True)
     with Propagator(h, w, n, None, "SOA", bosons=True) as p, pytest.raises(G1G2Error):
         p.adjoint(0.01, 2, objective=0, ckpt_every=1, n_drive_params=0)

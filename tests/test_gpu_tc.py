@@ -94,6 +94,26 @@ def test_tc_ladder_rhs_parity(se, nb, restricted):
     assert e1 < tol_rhs("GW", nb, "bf16x4") and e2 < tol_rhs("GW", nb, "bf16x4")
 
 
+BOSON_TC_CASES = [("SOA", 8, "tf32x3"), ("SOA", 12, "bf16x4"), ("GW", 12, "tf32x3"), ("GW", 12, "bf16x4"),
+                  ("GWX", 8, "bf16x4"), ("TPP", 12, "bf16x4"), ("TPH", 12, "bf16x4"), ("DSL", 8, "bf16x4")]
+
+
+@pytest.mark.parametrize("se,nb,prec", BOSON_TC_CASES)
+def test_tc_boson_rhs_parity(se, nb, prec):
+    """Bosons in the tensor-core forms (nbar = 1 + n, w^+ source, the ph sign)."""
+    from paper_2002_12717_gb300.g1g2 import Propagator
+    h, w, n, g2, D, drv = problem(nb, se, False, False, seed=500 + nb)
+    prob = O.Problem(h, w, se, False, D, drv.f, bosons=True)
+    dn_ref, dg_ref = O.rhs(prob, 0.4, n, g2)
+    with Propagator(h, w, n, None, se, prec, bosons=True) as p:
+        p.set_drive(D, drv)
+        dn, dg = run_rhs(p, 0.4, n, g2)
+    e1, e2 = rel_err(dn, dn_ref), rel_err(dg, dg_ref)
+    print(f"{prec} {se} bosons nb={nb}: dn {e1:.2e} dG2 {e2:.2e}")
+    tol = tol_rhs("GW" if se != "SOA" else "SOA", nb, prec)
+    assert e1 < tol and e2 < tol
+
+
 @pytest.mark.parametrize("se", ["TPP", "TPH", "DSL"])
 def test_tc_ladder_propagation_tracks_fp64_form(se):
     """nb=16 seeded general basis, 100 RK4 steps of the T matrices and DSL."""
