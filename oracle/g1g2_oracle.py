@@ -261,54 +261,6 @@ def rhs(prob: Problem, t, n, G2):
     return dn, -1j * rhs2
 
 
-def rhs_samples(prob: Problem, t, n, G2, idx):
-    """dn/dt in full and d𝒢/dt at the listed elements idx = [(i, j, k, l), ...] only,
-    each element from the definitions used by `rhs` (same equations, same order of the
-    sums), for basis sizes where the full nb^5 / nb^6 evaluation is too slow: the
-    source-term chains and the polarisation sum are nb^4 work per element.
-    SOA, GW, GWX and HF (the selfenergies of the full-size workloads)."""
-    if prob.selfenergy not in (SOA, GW, GWX, HF):
-        raise ValueError("element-wise evaluation covers SOA, GW, GWX and HF")
-    eta = prob.eta
-    nb = n.shape[0]
-    hhf = hf_hamiltonian(prob.h_of_t(t), prob.w, n, prob.restricted, eta)
-    if prob.selfenergy == HF:
-        return g1_rhs(hhf, n, np.zeros_like(n), eta), np.zeros(len(idx), dtype=np.complex128)
-    dn = g1_rhs(hhf, n, collision_integral(prob.w, G2, eta), eta)
-    gl, gg = g_less(n, eta), g_greater(n, eta)
-    wt = prob.w_source.reshape(nb * nb, nb * nb)
-
-    def chain_elem(a, b, c, d, i, j, k, l):
-        # Σ_pqrs a_ip b_jq wt_pqrs c_rk d_sl (the chain of psi_source) for one element
-        left = np.outer(a[i, :], b[j, :]).reshape(-1)
-        right = np.outer(c[:, k], d[:, l]).reshape(-1)
-        return left @ wt @ right
-
-    def psi_elem(i, j, k, l):
-        return (1j ** 2) * (chain_elem(gg, gg, gl, gl, i, j, k, l) - chain_elem(gl, gl, gg, gg, i, j, k, l))
-
-    def hcorr_slice(j, l):
-        # Eq. (gwhcorr) at fixed (j, l): 𝔥_ajbl = ±(iħ)^2 Σ_pq w_qapb F_pq for all (a, b),
-        # F_pq = 𝒢^F,>_jplq - 𝒢^F,<_jplq = G^>_jq G^<_pl - G^<_jq G^>_pl (Eq. g2f-def)
-        F = np.einsum("q,p->pq", gg[j, :], gl[:, l]) - np.einsum("q,p->pq", gl[j, :], gg[:, l])
-        return eta * (1j ** 2) * np.einsum("qapb,pq->ab", prob.w, F)
-
-    def pi_elem(i, j, k, l):
-        # Eq. (gwpi): Π_ijkl = Σ_pq 𝔥_qjpl 𝒢_ipkq
-        h = hcorr_slice(j, l)                     # h[q, p] = 𝔥_qjpl
-        return np.sum(h * G2[i, :, k, :].T)       # G2[i, p, k, q] transposed to [q, p]
-
-    out = np.empty(len(idx), dtype=np.complex128)
-    for e, (i, j, k, l) in enumerate(idx):
-        comm = (hhf[i, :] @ G2[:, j, k, l] + hhf[j, :] @ G2[i, :, k, l]
-                - G2[i, j, :, l] @ hhf[:, k] - G2[i, j, k, :] @ hhf[:, l])
-        r = comm + psi_elem(i, j, k, l)
-        if prob.selfenergy in (GW, GWX):
-            r = r + pi_elem(i, j, k, l) - np.conj(pi_elem(l, k, j, i))
-        out[e] = -1j * r
-    return dn, out
-
-
 def rk4_step(prob: Problem, t, n, G2, dt):
     """Classical fourth-order Runge-Kutta step on (n, 𝒢) jointly."""
     k1 = rhs(prob, t, n, G2)

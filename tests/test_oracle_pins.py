@@ -419,24 +419,6 @@ def test_tph_separated_form_equals_full_quasi_hamiltonian_form():
     assert np.abs(-1j * full - got).max() < 1e-12 * np.abs(got).max()
 
 
-@pytest.mark.parametrize("se,bosons", [("SOA", False), ("GW", False), ("GWX", False), ("HF", False),
-                                       ("SOA", True), ("GW", True)])
-def test_element_wise_rhs_equals_full_rhs(se, bosons):
-    """The element-wise evaluation used at the full-size workloads gives the full
-    right-hand side's elements (every element of a 5-orbital problem)."""
-    rng = np.random.default_rng(80)
-    nb = 5
-    h = inputs.random_hermitian(nb, rng)
-    w = sym_w(nb, rng)
-    n, g2 = inputs.random_state(nb, rng, soa=False)
-    prob = O.Problem(h, w, se, bosons=bosons)
-    dn_ref, dg_ref = O.rhs(prob, 0.0, n, g2)
-    idx = [tuple(x) for x in np.ndindex(nb, nb, nb, nb)]
-    dn, dg = O.rhs_samples(prob, 0.0, n, g2, idx)
-    assert np.abs(dn - dn_ref).max() < 1e-13
-    assert np.abs(dg - dg_ref.reshape(-1)).max() < 1e-13 * max(1.0, np.abs(dg_ref).max())
-
-
 def test_dsl_equals_printed_quasi_hamiltonian_form_and_is_additive():
     """Eq. (g2-dsl-equation): Psi^± plus, for each of the GW, pp and ph quasi-Hamiltonians,
     hcorr times conjugated 𝒢 minus its conjugate, in the index patterns printed there
