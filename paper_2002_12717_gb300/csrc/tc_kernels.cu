@@ -276,9 +276,45 @@ __global__ void realify_pi_kernel(int nb, int kpad, const float *__restrict__ Y1
   }
 }
 
+// max over (q, j, p, l) of the larger component of hcorr_qjpl = Y1_qjpl - Y2_plqj, folded
+// into *amax (FP32 bits): the exponent of the sliced B operand of the polarisation GEMM.
+// The bound max|Y1| + max|Y2| can sit several bits above max|hcorr|, and every bit lost
+// there moves the mass of the products into the lower slice orders, whose FP32 sum the
+// tensor cores accumulate with truncation.  Same tiling as realify_pi_sliced_kernel.
+__global__ void hcorr_amax_kernel(int nb, int kpad, const float *__restrict__ Y1s, const float *__restrict__ Y2s,
+                                  long long P, int *amax) {
+  __shared__ float2 t1[32][33];
+  const long long N = nb;
+  const long long jl = blockIdx.y;
+  const long long j = jl / N, l = jl % N;
+  const int ntq = kpad / 32;
+  const int p0 = (blockIdx.x / ntq) * 32, q0 = (blockIdx.x % ntq) * 32;
+  const int tx = threadIdx.x, ty0 = threadIdx.y;
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int q = q0 + ty, pp = p0 + tx;
+    float2 v = make_float2(0.f, 0.f);
+    if (q < nb && pp < nb) {
+      const long long g = ((q * N + j) * N + l) * N + pp;   // Y1_{q j p l} at [q][j][l][p]
+      v = make_float2(Y1s[g], Y1s[P + g]);
+    }
+    t1[ty][tx] = v;
+  }
+  __syncthreads();
+  float mx = 0.f;
+  for (int ty = ty0; ty < 32; ty += blockDim.y) {
+    const int pp = p0 + ty, q = q0 + tx;
+    if (pp < nb && q < nb) {
+      const long long g = ((pp * N + l) * N + j) * N + q;   // Y2_{p l q j} at [p][l][j][q]
+      const float2 a = t1[tx][ty];
+      mx = fmaxf(mx, fmaxf(fabsf(a.x - Y2s[g]), fabsf(a.y - Y2s[P + g])));
+    }
+  }
+  block_amax(mx, amax);
+}
+
 // Sliced form of realify_pi_kernel: the same B values, as four BF16 slices
-// [q][row][ldb] with leading width L and the exponent of max|Y1| + max|Y2|
-// (a bound on max|hcorr|; amax holds the FP32 bit patterns of both maxima).
+// [q][row][ldb] with leading width L and the exponent of amax[0] + amax[1] (FP32 bit
+// patterns: the exact max|hcorr| and a zero slot).
 __global__ void realify_pi_sliced_kernel(int nb, int kpad, const float *__restrict__ Y1s,
                                          const float *__restrict__ Y2s, long long P, const int *amax, int L,
                                          __nv_bfloat16 *out, long long ldb, long long slice_stride) {
@@ -736,7 +772,7 @@ namespace {
 // amax slots: FP32 bit patterns of the largest |A| of each A tensor of the sliced form
 enum : int {
   kAmaxW = 0, kAmaxY = 1, kAmaxYs = 2, kAmaxP1 = 3, kAmaxP2 = 4, kAmaxP3 = 5, kAmaxH1 = 6, kAmaxH2 = 7,
-  kAmaxWh = 8, kAmaxT1 = 9, kAmaxT2 = 10, kAmaxSlots = 16
+  kAmaxWh = 8, kAmaxT1 = 9, kAmaxT2 = 10, kAmaxHc = 11, kAmaxZero = 12, kAmaxSlots = 16
 };
 
 template <class T>
@@ -1268,9 +1304,12 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     const dim3 pgrid((unsigned)(((nb + 31) / 32) * (t->kpad / 32)), (unsigned)(N * N));
     L.before("tc_realify_pi");
     if (sl) {
+      // exponent from the exact max|hcorr| (slot kAmaxHc; kAmaxZero stays 0)
+      cudaMemsetAsync(amax + kAmaxHc, 0, sizeof(int), L.stream);
+      hcorr_amax_kernel<<<pgrid, dim3(32, 8), 0, L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, amax + kAmaxHc);
       const long long brows = (long long)t->pi_ntiles * t->pi_nout;
       realify_pi_sliced_kernel<<<pgrid, dim3(32, 8), 0, L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4,
-                                                                    amax + kAmaxH1, t->pi_lead, t->bpi_s,
+                                                                    amax + kAmaxHc, t->pi_lead, t->bpi_s,
                                                                     t->pi_ldb, brows * t->pi_ldb);
     } else {
       realify_pi_kernel<<<pgrid, dim3(32, 8), 0, L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, t->bpi_hi,
