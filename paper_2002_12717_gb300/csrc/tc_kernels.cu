@@ -370,7 +370,8 @@ __global__ void realify_pi_sliced_kernel(int nb, int kpad, const float *__restri
 // interleaved as 2 (c nb + d) + v, K = (u, p, q) as (u nb + p) kpad + q, value R(X)[u][v]
 // with X = H^dag_pqcd = conj(hcorr_cdpq) = P1_pqcd - P2_pqcd, both stored as [q][p][c][d]
 // (the two right-multiplication passes w x3 S x4 S with S = nbar and S = n).  Four BF16
-// slices with the exponent of max|P1| + max|P2|.  One CTA per (p, c) and a 32 x 32 tile
+// slices with the exponent of amax[0] + amax[1] (the exact max|P1 - P2| and a zero
+// slot).  One CTA per (p, c) and a 32 x 32 tile
 // of (q, d): read along d, transposed in shared memory, written along q; q in
 // [nb, kpad) is written as zero padding.
 __global__ void realify_lam_sliced_kernel(int nb, int kpad, const float *__restrict__ P1s,
@@ -416,6 +417,27 @@ __global__ void realify_lam_sliced_kernel(int nb, int kpad, const float *__restr
         for (int z = 0; z < 4; ++z) out[z * slice_stride + row * ldb + col] = __float2bfloat16_rn(sl[z]);
       }
   }
+}
+
+// max over all elements of the larger component of P1 - P2 ([q][p][c][d] layout), folded
+// into *amax: the exponent of the ladder product's sliced B operand (the exact maximum,
+// for the reason given at hcorr_amax_kernel).  Same tiling as realify_lam_sliced_kernel.
+__global__ void ladder_amax_kernel(int nb, int kpad, const float *__restrict__ P1s, const float *__restrict__ P2s,
+                                   long long P, int *amax) {
+  const long long N = nb;
+  const long long pc = blockIdx.y;
+  const long long p = pc / N, c = pc % N;
+  const int ntd = (nb + 31) / 32;
+  const int q0 = (blockIdx.x / ntd) * 32, d0 = (blockIdx.x % ntd) * 32;
+  float mx = 0.f;
+  for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
+    const int q = q0 + ty, d = d0 + threadIdx.x;
+    if (q < nb && d < nb) {
+      const long long g = ((q * N + p) * N + c) * N + d;
+      mx = fmaxf(mx, fmaxf(fabsf(P1s[g] - P2s[g]), fabsf(P1s[P + g] - P2s[P + g])));
+    }
+  }
+  block_amax(mx, amax);
 }
 
 // Gp[u][i][p][j][q] = G[u][i][j][p][q] (planar FP32): G2 seen by the polarisation GEMM's
@@ -1352,10 +1374,13 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     launch_gemm(t, L, tag, mWt, B2a, B2a, lp(N3, 1, EP_EXCH_T, t->buf1, wt_slot, kAmaxT2), sl);
     launch_gemm(t, L, tag, t->mBuf1Lin, B2b, B2b, lp(N3, 2, EP_SWAP34, t->Y2, kAmaxT2, kAmaxH2), sl);
     const long long brows = (long long)t->pi_ntiles * t->pi_nout;
+    const dim3 lgrid((unsigned)((t->kpad / 32) * ((nb + 31) / 32)), (unsigned)(N * N));
+    cudaMemsetAsync(amax + kAmaxHc, 0, sizeof(int), L.stream);
     L.before("tc_realify_ladder");
-    realify_lam_sliced_kernel<<<dim3((unsigned)((t->kpad / 32) * ((nb + 31) / 32)), (unsigned)(N * N)), dim3(32, 8), 0,
-                                L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, amax + kAmaxH1, t->pi_lead, t->bpi_s,
-                                            t->pi_ldb, brows * t->pi_ldb);
+    ladder_amax_kernel<<<lgrid, dim3(32, 8), 0, L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, amax + kAmaxHc);
+    realify_lam_sliced_kernel<<<lgrid, dim3(32, 8), 0, L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, amax + kAmaxHc,
+                                                                   t->pi_lead, t->bpi_s, t->pi_ldb,
+                                                                   brows * t->pi_ldb);
     L.after_launch();
   };
   auto ladder_gemm = [&](const char *tag) {

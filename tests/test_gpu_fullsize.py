@@ -19,11 +19,13 @@ def tol_bf16x4(se, nb):
     return 1e-6 if se == "SOA" else max(1e-6, 2 * 2.0 ** -24 * np.sqrt(2 * nb * nb))
 
 
-@pytest.mark.parametrize("name", ["general-soa-nb96", "general-gw-nb64"])
-def test_full_size_rhs_matches_oracle(name):
+@pytest.mark.parametrize("name,se", [("general-soa-nb96", "SOA"), ("general-gw-nb64", "GW"),
+                                     ("general-gw-nb64", "TPP"), ("general-gw-nb64", "TPH")])
+def test_full_size_rhs_matches_oracle(name, se):
+    """The two bench workloads, and the T matrices on the GW workload's basis (nb = 64)."""
     from paper_2002_12717_gb300.g1g2 import from_workload
-    d = inputs.workload(name)
-    nb, se = d["nb"], d["selfenergy"]
+    d = dict(inputs.workload(name), selfenergy=se)
+    nb = d["nb"]
     rng = np.random.default_rng(17)
     _, g2 = inputs.random_state(nb, rng, g2_scale=1e-3, soa=(se == "SOA"))
     g2 = np.ascontiguousarray(g2)
@@ -41,7 +43,7 @@ def test_full_size_rhs_matches_oracle(name):
     tol = tol_bf16x4(se, nb)
     e_dn = np.abs(dn - dn_ref).max() / np.abs(dn_ref).max()
     e_dg = np.abs(dg - dg_ref).max() / np.abs(dg_ref).max()
-    print(f"{name} bf16x4: dn {e_dn:.2e}  dG2 {e_dg:.2e} (bar {tol:.1e})")
+    print(f"{name} {se} bf16x4: dn {e_dn:.2e}  dG2 {e_dg:.2e} (bar {tol:.1e})")
     assert e_dn < tol and e_dg < tol
     # any size: Tr dn = dN/dt = 0 (a sum of nb elements), and d𝒢 keeps the symmetries
     assert abs(np.trace(dn)) < nb * tol * np.abs(dn).max()
