@@ -56,7 +56,11 @@ typedef struct g1g2_ctx g1g2_ctx;  /* opaque */
 typedef enum {
   G1G2_HF = 0,   /* I = 0, G2 frozen: time-dependent Hartree-Fock (Eq. eom_gone-2 without I) */
   G1G2_SOA = 1,  /* second-order Born, Sec. III.C, Eq. (result_eom_soa) */
-  G1G2_GW = 2,   /* GW, Sec. IV.C, Eq. (g2-eq-gw-pi) */
+  G1G2_GW = 2,   /* GW, Sec. IV.C, Eq. (g2-eq-gw-pi); in the spin-restricted basis only for an
+                    on-site w (the Hubbard form, Eqs. g2-gw-hubbard1/2, FP64): G2 is the
+                    opposite-spin block, the context keeps the same-spin block its
+                    polarisation couples to (zero at init and after g1g2_set_state), and
+                    g1g2_rhs is refused (G1G2_EUNSUPPORTED) */
   G1G2_GW_EXCHANGE = 3, /* GW with exchange: Psi replaced by Psi^± in Eq. (g2-eq-gw-pi)
                            (end of Sec. IV.C); spin-orbital basis only */
   G1G2_TPP = 4,         /* particle-particle T matrix, Sec. IV.D, Eq. (g2-eq-tpp-lambda): the SOA

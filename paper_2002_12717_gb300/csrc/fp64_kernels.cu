@@ -372,9 +372,16 @@ __global__ void g2_assemble_kernel(int nb, const cplx *__restrict__ Cb, const cp
 //                + U_l n_il n_jl n_lk + U_k n_ik n_jk n_kl - d_kl U_k n_ik n_jk;
 //   * the collision integral is I_ij = -i U_i G_iiji.
 // ---------------------------------------------------------------------------
+// With Go (GW, the other spin block of G2: same-spin for the opposite-spin equation and
+// vice versa) the polarisation term is added, Pi_ijkl - conj(Pi_lkji) with
+// Pi_ijkl = n_jl (U_j Go_ijkj - U_l Go_ilkl): the Hubbard-basis reduction of Eqs.
+// (pihubbardtrans, pihubbardcis) with G^> = G^< - i and G^< = i n (U_p inside the sum
+// over the site p).  psi = 0 leaves out the source term (the same-spin equation, whose
+// source vanishes for an on-site interaction).
 __global__ void hubbard_c_kernel(int nb, const int *__restrict__ rp, const int *__restrict__ ci,
                                  const cplx *__restrict__ hhf, const double *__restrict__ U,
-                                 const cplx *__restrict__ n, const cplx *__restrict__ G, cplx *C) {
+                                 const cplx *__restrict__ n, const cplx *__restrict__ G,
+                                 const cplx *__restrict__ Go, int psi, cplx *C) {
   // grid: y = i nb + j, x over (k, l); index arithmetic in 32 bits where it fits
   const long long N = nb, N2 = N * N, N3 = N2 * N;
   const int ij = blockIdx.y, i = ij / nb, j = ij - i * nb;
@@ -400,16 +407,25 @@ __global__ void hubbard_c_kernel(int nb, const int *__restrict__ rp, const int *
       const int p = ci[q];
       acc = csub(acc, cmul(G[e - l + p], hhf[p * N + l]));
     }
-    // Psi = -S
-    const cplx nij = n[i * N + j], nji = n[j * N + i], nik = n[i * N + k], nil = n[i * N + l];
-    const cplx njk = n[j * N + k], njl = n[j * N + l], nlk = n[l * N + k], nkl = n[k * N + l];
-    cplx S = cscale(cmul(cmul(nij, njk), njl), -U[j]);
-    S = cadd(S, cscale(cmul(cmul(nji, nik), nil), -U[i]));
-    S = cadd(S, cscale(cmul(cmul(nil, njl), nlk), U[l]));
-    S = cadd(S, cscale(cmul(cmul(nik, njk), nkl), U[k]));
-    if (i == j) S = cadd(S, cscale(cmul(nik, nil), U[i]));
-    if (k == l) S = csub(S, cscale(cmul(nik, njk), U[k]));
-    C[e] = csub(acc, S);
+    if (psi) {
+      // Psi = -S
+      const cplx nij = n[i * N + j], nji = n[j * N + i], nik = n[i * N + k], nil = n[i * N + l];
+      const cplx njk = n[j * N + k], njl = n[j * N + l], nlk = n[l * N + k], nkl = n[k * N + l];
+      cplx S = cscale(cmul(cmul(nij, njk), njl), -U[j]);
+      S = cadd(S, cscale(cmul(cmul(nji, nik), nil), -U[i]));
+      S = cadd(S, cscale(cmul(cmul(nil, njl), nlk), U[l]));
+      S = cadd(S, cscale(cmul(cmul(nik, njk), nkl), U[k]));
+      if (i == j) S = cadd(S, cscale(cmul(nik, nil), U[i]));
+      if (k == l) S = csub(S, cscale(cmul(nik, njk), U[k]));
+      acc = csub(acc, S);
+    }
+    if (Go) {
+      auto g4 = [&](int a, int b, int c, int d) { return Go[((a * N + b) * N + c) * N + d]; };
+      const cplx pi = cmul(n[j * N + l], csub(cscale(g4(i, j, k, j), U[j]), cscale(g4(i, l, k, l), U[l])));
+      const cplx pt = cmul(n[k * N + i], csub(cscale(g4(l, k, j, k), U[k]), cscale(g4(l, i, j, i), U[i])));
+      acc = csub(cadd(acc, pi), cconj(pt));   // + Pi_ijkl - conj(Pi_lkji)
+    }
+    C[e] = acc;
   }
 }
 
@@ -638,9 +654,10 @@ void g2_assemble(Launcher &L, int nb, const cplx *Cb, const cplx *Ab, Rk4Stage s
 }
 
 void hubbard_c(Launcher &L, int nb, const int *rp, const int *ci, const cplx *hhf, const double *U, const cplx *n,
-               const cplx *G, cplx *C) {
+               const cplx *G, const cplx *Go, bool psi, cplx *C) {
   L.before("hubbard_c");
-  hubbard_c_kernel<<<dim3((nb * nb + 127) / 128, nb * nb), 128, 0, L.stream>>>(nb, rp, ci, hhf, U, n, G, C);
+  hubbard_c_kernel<<<dim3((nb * nb + 127) / 128, nb * nb), 128, 0, L.stream>>>(nb, rp, ci, hhf, U, n, G, Go, psi ? 1 : 0,
+                                                                                C);
   L.after_launch();
 }
 

@@ -70,6 +70,11 @@ struct g1g2_ctx {
   std::vector<void *> adj_allocs;
   // Hubbard basis (spin-restricted SOA, on-site w): O(nb^4) right-hand side
   bool hub_ok = false, hub_on = false;
+  // GW in the spin-restricted Hubbard basis (Eqs. g2-gw-hubbard1/2): G holds the opposite-spin
+  // block, Gss the same-spin block that its polarisation term couples to (RK4 state Gss,
+  // stage input Gss_s, accumulator Gss_acc, right-hand side Cb2)
+  bool hub_gw = false;
+  cplx *Gss = nullptr, *Gss_s = nullptr, *Gss_acc = nullptr, *Cb2 = nullptr;
   double *hub_U = nullptr;                      // U_i = w_iiii
   int *hub_rp = nullptr, *hub_ci = nullptr;     // CSR pattern of h^HF (h, D, diagonal), symmetric
   std::vector<unsigned char> hub_hpat;          // nonzero pattern of h (host)
@@ -237,7 +242,17 @@ void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *
     // Hubbard basis: I, then C = [h2, G] + Psi in O(nb^4); the assembly forms dG = -i C
     hubbard_collision(L, nb, c->hub_U, G_in, c->I);
     g1_update(L, nb, c->hhf, n_in, c->I, st, o.ny, o.nys, o.nacc, o.nk);
-    hubbard_c(L, nb, c->hub_rp, c->hub_ci, c->hhf, c->hub_U, n_in, G_in, c->Cb);
+    if (c->hub_gw) {
+      // GW: each spin block with the polarisation of the other (every read of a stage input
+      // is queued before the assemblies overwrite it)
+      const cplx *Gss_in = (st.stage <= 0) ? c->Gss : c->Gss_s;
+      hubbard_c(L, nb, c->hub_rp, c->hub_ci, c->hhf, c->hub_U, n_in, G_in, Gss_in, true, c->Cb);
+      hubbard_c(L, nb, c->hub_rp, c->hub_ci, c->hhf, c->hub_U, n_in, Gss_in, G_in, false, c->Cb2);
+      g2_assemble(L, nb, c->Cb, nullptr, st, o.Gy, o.Gys, o.Gacc, o.Gk);
+      g2_assemble(L, nb, c->Cb2, nullptr, st, c->Gss, c->Gss_s, c->Gss_acc, nullptr);
+      return;
+    }
+    hubbard_c(L, nb, c->hub_rp, c->hub_ci, c->hhf, c->hub_U, n_in, G_in, nullptr, true, c->Cb);
     g2_assemble(L, nb, c->Cb, nullptr, st, o.Gy, o.Gys, o.Gacc, o.Gk);
     return;
   }
@@ -800,8 +815,27 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   const bool bosons = opt.statistics == G1G2_BOSONS;
   if (bosons && opt.basis == G1G2_SPIN_RESTRICTED)
     return fail(G1G2_EINVAL, "the spin-restricted mode is the fermion Hubbard form; bosons run in the spin-orbital basis");
-  if (opt.basis == G1G2_SPIN_RESTRICTED && (se == G1G2_GW || se == G1G2_DSL))
-    return fail(G1G2_EINVAL, "GW couples same-spin components and has no spin-restricted form");
+  // GW in the spin-restricted basis: only the Hubbard form, which carries the same-spin block
+  // besides the opposite-spin one (Eqs. g2-gw-hubbard1/2); GW with exchange and DSL have none
+  const bool restricted_gw = opt.basis == G1G2_SPIN_RESTRICTED && se == G1G2_GW && !gw_exchange;
+  if (opt.basis == G1G2_SPIN_RESTRICTED && (se == G1G2_DSL || gw_exchange))
+    return fail(G1G2_EINVAL, "GW couples same-spin components and has no general spin-restricted form");
+  if (restricted_gw) {
+    if (opt.precision != G1G2_FP64)
+      return fail(G1G2_EUNSUPPORTED, "spin-restricted GW runs the Hubbard form in FP64");
+    const size_t M = nb;
+    bool onsite = true;
+    for (size_t i = 0; i < M && onsite; ++i)
+      for (size_t j = 0; j < M && onsite; ++j)
+        for (size_t k = 0; k < M && onsite; ++k)
+          for (size_t l = 0; l < M; ++l) {
+            const size_t e = ((i * M + j) * M + k) * M + l;
+            const double re = opt.w_is_real ? w[e] : w[2 * e], im = opt.w_is_real ? 0.0 : w[2 * e + 1];
+            if (im != 0.0 || (!(i == j && j == k && k == l) && re != 0.0)) { onsite = false; break; }
+          }
+    if (!onsite)
+      return fail(G1G2_EINVAL, "GW has a spin-restricted form only in the Hubbard basis (real on-site w)");
+  }
 
   const size_t N = nb, N2 = N * N, N4 = N2 * N2;
   const bool restricted = opt.basis == G1G2_SPIN_RESTRICTED;
@@ -851,6 +885,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   if (!c) return fail(G1G2_ENOMEM, "host allocation failed");
   c->nb = nb; c->se = se; c->prec = opt.precision; c->basis = opt.basis;
   c->eta = bosons ? 1.0 : -1.0;
+  c->hub_gw = restricted_gw;
   c->stream = static_cast<cudaStream_t>(opt.cuda_stream);
   int rc = G1G2_OK;
   auto bail = [&](int code) { g1g2_destroy(c); return code; };
@@ -912,12 +947,17 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
       return bail(rc);
     c->splits = 4 * 152;
     if ((rc = dalloc(c, &c->partial, (size_t)c->splits * N2))) return bail(rc);
-    if (se == G1G2_GW || se == G1G2_TPH || se == G1G2_DSL) {
+    if ((se == G1G2_GW && !restricted_gw) || se == G1G2_TPH || se == G1G2_DSL) {
       if ((rc = dalloc(c, &c->Hb, N4)) || (rc = dalloc(c, &c->Gp, N4)) || (rc = dalloc(c, &c->Hp, N4)) ||
           (rc = dalloc(c, &c->Pp, N4)))
         return bail(rc);
     }
     if (se == G1G2_TPP && (rc = dalloc(c, &c->Hb, N4))) return bail(rc);
+    if (restricted_gw && ((rc = dalloc(c, &c->Gss, N4)) || (rc = dalloc(c, &c->Gss_s, N4)) ||
+                          (rc = dalloc(c, &c->Gss_acc, N4)) || (rc = dalloc(c, &c->Cb2, N4))))
+      return bail(rc);
+    if (restricted_gw && (rc = cuda_check(cudaMemsetAsync(c->Gss, 0, N4 * sizeof(cplx), c->stream), "memset")))
+      return bail(rc);
   }
   // uploads
   auto up = [&](void *dst, const void *src, size_t bytes) {
@@ -939,7 +979,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
     if ((rc = up(c->wP, hP.data(), N4 * sizeof(cplx)))) return bail(rc);
   }
   // Hubbard basis: spin-restricted SOA with an on-site interaction w_ijkl = U_i d(i=j=k=l)
-  if (se == G1G2_SOA && restricted && !bosons && c->prec == G1G2_FP64 && real) {
+  if ((se == G1G2_SOA || restricted_gw) && restricted && !bosons && c->prec == G1G2_FP64 && real) {
     bool onsite = true;
     std::vector<double> Ui(N);
     for (size_t i = 0; i < N && onsite; ++i)
@@ -960,6 +1000,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
       c->hub_ok = c->hub_on = true;
     }
   }
+  if (restricted_gw && !c->hub_ok) return bail(fail(G1G2_EINVAL, "spin-restricted GW needs the Hubbard form"));
   if (correlated && c->prec != G1G2_FP64) {
     if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "init sync"))) return bail(rc);
     g_detail.clear();
@@ -1005,6 +1046,8 @@ int g1g2_set_drive(g1g2_ctx *c, const double *D, int kind, const double *params,
 int g1g2_rhs(g1g2_ctx *c, double t, const double *n_dev, const double *G2_dev, double *dn_dev, double *dG2_dev) {
   if (!c || !n_dev || !dn_dev) return fail(G1G2_EINVAL, "NULL argument");
   if (c->se != G1G2_HF && (!G2_dev || !dG2_dev)) return fail(G1G2_EINVAL, "G2 and dG2 must be non-NULL");
+  if (c->hub_gw)
+    return fail(G1G2_EUNSUPPORTED, "spin-restricted GW keeps its same-spin block in the context: use g1g2_step");
   Launcher L = c->launcher();
   Rk4Stage st{-1, 0.0};
   StageOut o{nullptr, nullptr, nullptr, reinterpret_cast<cplx *>(dn_dev),
@@ -1224,6 +1267,7 @@ static AdjPlan adjoint_plan(int nsteps, size_t SB, int ckpt_every, int where_req
 
 int g1g2_set_hubbard_path(g1g2_ctx *c, int enable) {
   if (!c) return fail(G1G2_EINVAL, "ctx is NULL");
+  if (!enable && c->hub_gw) return fail(G1G2_EUNSUPPORTED, "spin-restricted GW runs only in the Hubbard form");
   if (enable && !c->hub_ok)
     return fail(G1G2_EUNSUPPORTED, "the O(nb^4) path needs spin-restricted SOA, the FP64 form and an on-site w");
   c->hub_on = enable != 0;
@@ -1568,6 +1612,7 @@ int g1g2_set_state(g1g2_ctx *c, double t, const double *G1, const double *G2) {
   if (G2) rc = cuda_check(cudaMemcpyAsync(c->G, G2, N4 * sizeof(cplx), cudaMemcpyHostToDevice, c->stream), "set");
   else rc = cuda_check(cudaMemsetAsync(c->G, 0, N4 * sizeof(cplx), c->stream), "set");
   if (rc) return rc;
+  if (c->hub_gw && (rc = cuda_check(cudaMemsetAsync(c->Gss, 0, N4 * sizeof(cplx), c->stream), "set"))) return rc;
   c->t = t;
   if (c->tc) {
     Launcher L = c->launcher();

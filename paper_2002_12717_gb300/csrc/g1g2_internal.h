@@ -103,8 +103,11 @@ void g2_assemble(Launcher &L, int nb, const cplx *Cb, const cplx *Ab, Rk4Stage s
 // red[0..] = {Re Tr(h n), Re Tr((hHF-h(t)) n), Re Tr n, Re Tr(D n)} for state n;
 // Hubbard basis, spin-restricted SOA (on-site w_ijkl = U_i d(i=j=k=l)): C = [h2, G] + Psi
 // with the commutator over the CSR pattern (rp, ci) of h^HF, and I_ij = -i U_i G_iiji.
+// GW (Go non-null: the other spin block, same-spin for the opposite-spin equation and
+// vice versa) adds Pi - (Pi_lkji)^* of the reduced Hubbard polarisation; psi = false
+// leaves out the source term (the same-spin equation).
 void hubbard_c(Launcher &L, int nb, const int *rp, const int *ci, const cplx *hhf, const double *U, const cplx *n,
-               const cplx *G, cplx *C);
+               const cplx *G, const cplx *Go, bool psi, cplx *C);
 void hubbard_collision(Launcher &L, int nb, const double *U, const cplx *G, cplx *I);
 void obs_one_body(Launcher &L, int nb, const cplx *h, const cplx *D, double f, const cplx *hhf,
                   const cplx *n, double *red);
