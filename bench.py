@@ -382,18 +382,19 @@ def adjoint_sample(args):
             "grad_controls_norm": float(np.linalg.norm(gd))}
 
 
-def hubbard_scaling(sizes, steps=3):
+def hubbard_scaling(sizes, steps=3, selfenergy="SOA"):
     """ms per RK4 step of the spin-restricted Hubbard chain (J = 1, U = 2, half filling,
-    quench) on the O(nb^4) Hubbard path and on the general O(nb^5) FP64 path."""
+    quench) on the O(nb^4) Hubbard path and, for SOA, on the general O(nb^5) FP64 path
+    (spin-restricted GW exists only in the Hubbard form)."""
     import torch
 
     from paper_2002_12717_gb300.g1g2 import from_workload
 
     out = []
     for nb in sizes:
-        d = inputs.hubbard_chain_restricted(L=nb, U=2.0)
-        row = {"nb": nb}
-        for hub in (True, False):
+        d = dict(inputs.hubbard_chain_restricted(L=nb, U=2.0), selfenergy=selfenergy)
+        row = {"nb": nb, "selfenergy": selfenergy}
+        for hub in ((True, False) if selfenergy == "SOA" else (True,)):
             with from_workload(d, precision="fp64") as p:
                 p.hubbard_path = hub
                 p.propagate(0.02, 2)
@@ -590,6 +591,8 @@ def main():
                     help="steps run in both forms from the initial state (speed-up and error vs FP64)")
     ap.add_argument("--hubbard-scaling", default="",
                     help="comma-separated nb: time the Hubbard O(nb^4) path against the general path and exit")
+    ap.add_argument("--hubbard-selfenergy", default="SOA", choices=["SOA", "GW"],
+                    help="selfenergy of --hubbard-scaling")
     ap.add_argument("--nt-scaling", default="",
                     help="comma-separated N_t: time the memory-integral HF-GKBA against the G1-G2 equations and exit")
     ap.add_argument("--selfenergy-sweep", default="",
@@ -609,7 +612,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.hubbard_scaling:
         if rank == 0:
-            print(json.dumps({"hubbard_scaling": hubbard_scaling([int(x) for x in args.hubbard_scaling.split(",")])}),
+            sizes = [int(x) for x in args.hubbard_scaling.split(",")]
+            print(json.dumps({"hubbard_scaling": hubbard_scaling(sizes, selfenergy=args.hubbard_selfenergy)}),
                   flush=True)
         return
     if args.selfenergy_sweep:
