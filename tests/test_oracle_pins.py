@@ -666,6 +666,52 @@ def test_g1g2_equals_memory_integral_hfgkba():
     assert 3.0 < errs[0] / errs[1] < 5.0
 
 
+def test_g1g2_solution_satisfies_the_interval_recursion():
+    """Eq. (linintG): 𝒢(T + Δ) is 𝒢(T) carried by the two-particle HF propagator,
+    (u⊗u) 𝒢(T) (u⊗u)^† with u = u(T+Δ, T), plus the memory integral of Eq.
+    (dtilde-solution-short) over [T, T + Δ] alone.  The G1-G2 RK4 solution (fine step)
+    satisfies it up to the quadrature of the reconstruction: midpoint propagators and
+    the trapezoid rule on a grid of step h, second order in h."""
+    L = 2
+    hs = inputs.chain_hopping(L)
+    hs[0, 0] += 1.0
+    prob = O.Problem(inputs.spin_orbital_h(hs), inputs.spin_orbital_hubbard_w(L, 1.0))
+    nb = 2 * L
+    n = np.kron(inputs.lowest_projector(inputs.chain_hopping(L), 1), np.eye(2)).astype(np.complex128)
+    g2 = np.zeros((nb,) * 4, dtype=np.complex128)
+    fine, T, Delta = 0.0025, 1.0, 0.4
+    for _ in range(int(round(T / fine))):
+        n, g2, _ = O.rk4_step(prob, 0.0, n, g2, fine)
+    traj = [(n, g2)]                                   # the fine trajectory over [T, T + Δ]
+    for _ in range(int(round(Delta / fine))):
+        n, g2, _ = O.rk4_step(prob, 0.0, *traj[-1], fine)
+        traj.append((n, g2))
+    g_end = traj[-1][1]
+
+    def u2(u, x):
+        return np.einsum("ip,jq,pqrs,kr,ls->ijkl", u, u, x, u.conj(), u.conj())
+
+    errs = []
+    for h in (0.05, 0.025):
+        stride = int(round(h / fine))
+        grid = traj[::stride]
+        us = [np.eye(nb, dtype=np.complex128)]          # u(t_m, T) by midpoint exponentials
+        for m in range(len(grid) - 1):
+            nm = 0.5 * (grid[m][0] + grid[m + 1][0])
+            us.append(expm(-1j * h * O.hf_hamiltonian(prob.h, prob.w, nm)) @ us[-1])
+        u_end = us[-1]
+        hom = u2(u_end, grid[0][1])
+        mem = np.zeros_like(hom)
+        for m, (nm, _) in enumerate(grid):
+            wgt = 0.5 if m in (0, len(grid) - 1) else 1.0
+            # (iħ)^3 𝒰2 Ψ 𝒰2 with iħ𝒰 = u(T+Δ, t_m) = u_end u_m^†: -i (u⊗u) Ψ (u⊗u)^†
+            mem = mem + wgt * h * (-1j) * u2(u_end @ us[m].conj().T, O.psi_source(prob.w_source, nm))
+        errs.append(np.abs(hom + mem - g_end).max())
+    print(f"interval recursion: |G(T+D)| {np.abs(g_end).max():.3e}, residual at h, h/2: {errs[0]:.3e} {errs[1]:.3e}")
+    assert np.abs(g_end).max() > 1e-3
+    assert errs[1] < 2e-4 and 3.0 < errs[0] / errs[1] < 5.0
+
+
 def test_torch_restatement_matches_oracle():
     """The autograd restatement (oracle/torch_oracle.py) reproduces the numpy oracle's RK4 run."""
     import torch
