@@ -600,6 +600,72 @@ void vjp_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n, const cplx *G, 
   mode_left2(c, L, c->nbar, c->AB1, c->T2, one, 0.0);
   mode_left1(c, L, c->nbar, c->T2, c->AB2, one, 0.0);      // B4 = nbar x_1 nbar x_2 T1'
   contract3(c, L, 4, c->AE, c->AB2, one, 1.0, nbar);
+  if (c->se != G1G2_GW) return;
+  // GW: dG2 += -i (Pi - conj(Pi_lkji)), Pi_ijkl = sum_pq hcorr_qjpl G_ipkq, hcorr = w x_4 n - n x_2 w
+  // (Eqs. gwpi, gwhcorr).  Cotangent of Pi: Pibar = i (Y + conj(Y_lkji)); then the transposed
+  // products of the forward GEMM (Pp = Gp Hp) and of the two mode products of hcorr.
+  {
+    ZGemm g;  // Hb = hcorr (recomputed as in the forward pass)
+    g.M = (int)(N2 * N); g.N = nb; g.K = nb;
+    g.A = c->w; g.sa_m = N; g.sa_k = 1;
+    g.B = n; g.sb_k = N; g.sb_n = 1;
+    g.C = c->Hb; g.sc_m = N; g.sc_n = 1;
+    zgemm(L, g);
+  }
+  {
+    ZGemm g;
+    g.M = nb; g.N = (int)N2; g.K = nb; g.batch = nb;
+    g.A = n; g.sa_m = N; g.sa_k = 1;
+    g.B = c->w; g.sb_b = N2 * N; g.sb_k = N2; g.sb_n = 1;
+    g.C = c->Hb; g.sc_b = N2 * N; g.sc_m = N2; g.sc_n = 1;
+    g.alpha = mone; g.beta = 1.0;
+    zgemm(L, g);
+  }
+  const int pG[4] = {0, 2, 1, 3};  // Gp[i][k][p][q] = G[i][p][k][q]
+  permute4(L, nb, G, c->Gp, pG, one, 0.0, false);
+  const int pH[4] = {1, 2, 0, 3};  // Hp[p][q][j][l] = hcorr[q][j][p][l]
+  permute4(L, nb, c->Hb, c->Hp, pH, one, 0.0, false);
+  const int pT[4] = {3, 2, 1, 0};  // AB1 = Pibar = i Y + i conj(Y_lkji)
+  permute4(L, nb, Y, c->AB1, pT, I1, 0.0, true);
+  zaxpby(L, N4, I1, Y, one, c->AB1, c->AB1);
+  permute4(L, nb, c->AB1, c->Pp, pG, one, 0.0, false);  // Pp[i][k][j][l] = Pibar_ijkl
+  {
+    ZGemm g;  // AB2[(ik)][(pq)] = sum_(jl) Pp[(ik)][(jl)] conj(Hp[(pq)][(jl)])
+    g.M = (int)N2; g.N = (int)N2; g.K = (int)N2;
+    g.A = c->Pp; g.sa_m = N2; g.sa_k = 1;
+    g.B = c->Hp; g.sb_k = 1; g.sb_n = N2; g.conjB = true;
+    g.C = c->AB2; g.sc_m = N2; g.sc_n = 1;
+    zgemm(L, g);
+  }
+  permute4(L, nb, c->AB2, Gbar, pG, one, 1.0, false);   // Gbar[i][p][k][q] += AB2[i][k][p][q]
+  {
+    ZGemm g;  // AE[(pq)][(jl)] = sum_(ik) conj(Gp[(ik)][(pq)]) Pp[(ik)][(jl)]  (cotangent of Hp)
+    g.M = (int)N2; g.N = (int)N2; g.K = (int)N2;
+    g.A = c->Gp; g.sa_m = 1; g.sa_k = N2; g.conjA = true;
+    g.B = c->Pp; g.sb_k = N2; g.sb_n = 1;
+    g.C = c->AE; g.sc_m = N2; g.sc_n = 1;
+    zgemm(L, g);
+  }
+  const int pHt[4] = {2, 0, 1, 3};  // Hb = hcorr-bar[q][j][p][l] = AE[p][q][j][l]
+  permute4(L, nb, c->AE, c->Hb, pHt, one, 0.0, false);
+  {
+    ZGemm g;  // nbar_pl += sum_(ijk) conj(w_ijkp) hbar_ijkl
+    g.M = nb; g.N = nb; g.K = (int)(N2 * N);
+    g.A = c->w; g.sa_m = 1; g.sa_k = N; g.conjA = true;
+    g.B = c->Hb; g.sb_k = N; g.sb_n = 1;
+    g.C = nbar; g.sc_m = N; g.sc_n = 1;
+    g.beta = 1.0;
+    zgemm_reduce(L, g, c->partial, c->splits);
+  }
+  {
+    ZGemm g;  // nbar_jq -= sum_i sum_(kl) hbar_ijkl conj(w_iqkl)
+    g.M = nb; g.N = nb; g.K = (int)N2; g.batch = nb;
+    g.A = c->Hb; g.sa_b = N2 * N; g.sa_m = N2; g.sa_k = 1;
+    g.B = c->w; g.sb_b = N2 * N; g.sb_k = 1; g.sb_n = N2; g.conjB = true;
+    g.C = nbar; g.sc_m = N; g.sc_n = 1;
+    g.alpha = mone; g.beta = 1.0;
+    zgemm_reduce(L, g, c->partial, c->splits);
+  }
 }
 
 // CSR pattern of h^HF for the Hubbard path: the nonzeros of h (and of D when a
@@ -1205,8 +1271,8 @@ int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_de
   if (!c || !n_dev || !G2_dev || !dn_bar || !dG2_bar || !n_bar || !G2_bar || !h_bar)
     return fail(G1G2_EINVAL, "NULL argument");
   if (c->prec != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product runs on the FP64 form");
-  if (c->se != G1G2_SOA && c->se != G1G2_HF)
-    return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product covers HF and SOA");
+  if ((c->se != G1G2_SOA && c->se != G1G2_HF && c->se != G1G2_GW) || c->hub_gw)
+    return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product covers HF, SOA and GW in a general basis");
   if (c->eta > 0) return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product covers fermions");
   const long long N2 = (long long)c->nb * c->nb, N4 = N2 * N2;
   if (!c->AE) {  // scratch of the adjoint
@@ -1300,7 +1366,8 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
                  double *grad_drive, double *grad_wscale, double *grad_h) {
   if (!c || nsteps < 1 || !J_out) return fail(G1G2_EINVAL, "bad adjoint argument");
   if (c->prec != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint runs on the FP64 form");
-  if (c->se != G1G2_SOA && c->se != G1G2_HF) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers HF and SOA");
+  if ((c->se != G1G2_SOA && c->se != G1G2_HF && c->se != G1G2_GW) || c->hub_gw)
+    return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers HF, SOA and GW in a general basis");
   if (c->eta > 0) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers fermions");
   if (objective < 0 || objective > 2) return fail(G1G2_EINVAL, "objective must be 0, 1 or 2");
   if (objective == 0 && (c->basis != G1G2_SPIN_ORBITAL || c->nb % 2))

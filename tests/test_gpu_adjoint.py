@@ -22,17 +22,18 @@ def rdot(x, y):
     return float((x.conj() * y).real.sum())
 
 
-@pytest.mark.parametrize("nb,restricted", [(6, False), (8, False), (5, True)])
-def test_vjp_dot_product(nb, restricted):
+@pytest.mark.parametrize("nb,restricted,se", [(6, False, "SOA"), (8, False, "SOA"), (5, True, "SOA"),
+                                              (6, False, "GW"), (7, False, "GWX")])
+def test_vjp_dot_product(nb, restricted, se):
     """<J d, ybar> by central differences of g1g2_rhs equals <d, VJP(ybar)>."""
     from paper_2002_12717_gb300.g1g2 import Propagator
-    h, w, n, g2, D, drv = problem(nb, "SOA", restricted, False, seed=70 + nb)
+    h, w, n, g2, D, drv = problem(nb, se, restricted, False, seed=70 + nb)
     rng = np.random.default_rng(5)
     cn = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
     dn_dir, dg_dir = cn(nb, nb), 0.1 * cn(*(nb,) * 4)
     a, Y = cn(nb, nb), cn(*(nb,) * 4)
     t = 0.3
-    with Propagator(h, w, n, None, "SOA", "fp64", restricted) as p:
+    with Propagator(h, w, n, None, se, "fp64", restricted) as p:
         p.set_drive(D, drv)
         eps = 1e-5
 
@@ -73,10 +74,10 @@ def _hubbard_case(ncontrols=6, nsteps=50, dt=0.02):
     return d
 
 
-def _run_J(d, objective, nsteps, dt, h=None, wscale=1.0, controls=None):
+def _run_J(d, objective, nsteps, dt, h=None, wscale=1.0, controls=None, se="SOA"):
     from paper_2002_12717_gb300.g1g2 import Propagator
     drv = d["drive"] if controls is None else inputs.PiecewiseLinear(controls, d["drive"].ta, d["drive"].tb)
-    with Propagator(d["h"] if h is None else h, d["w"] * wscale, d["n0"], None, "SOA", "fp64") as p:
+    with Propagator(d["h"] if h is None else h, d["w"] * wscale, d["n0"], None, se, "fp64") as p:
         p.set_drive(d["D"], drv)
         J, _, _, _ = p.adjoint(dt, nsteps, objective=objective, ckpt_every=nsteps)
     return J
@@ -113,6 +114,38 @@ def test_adjoint_matches_central_differences(objective):
         fd = (_run_J(d, objective, nsteps, dt, h=d["h"] + eps * dh)
               - _run_J(d, objective, nsteps, dt, h=d["h"] - eps * dh)) / (2 * eps)
         assert abs(fd - want) <= TOL_GRAD * max(abs(fd), 1e-3), (kind, fd, want)
+
+
+def test_gw_adjoint_matches_central_differences():
+    """GW (Eqs. g2-eq-gw-pi, gwpi, gwhcorr): the adjoint's gradients with respect to the
+    drive controls, the scale of w and a hopping against central differences."""
+    from paper_2002_12717_gb300.g1g2 import Propagator
+    dt, nsteps, M = 0.02, 40, 4
+    d = _hubbard_case(M, nsteps, dt)
+    with Propagator(d["h"], d["w"], d["n0"], None, "GW", "fp64") as p:
+        p.set_drive(d["D"], d["drive"])
+        J, gdrive, gws, gh = p.adjoint(dt, nsteps, objective=0, ckpt_every=9, n_drive_params=M)
+    eps = 1e-5
+    vals = d["drive"].values
+    run = lambda **kw: _run_J(d, 0, nsteps, dt, se="GW", **kw)
+    for m in range(M):
+        vp, vm = vals.copy(), vals.copy()
+        vp[m] += eps
+        vm[m] -= eps
+        fd = (run(controls=vp) - run(controls=vm)) / (2 * eps)
+        assert abs(fd - gdrive[m]) <= TOL_GRAD * max(abs(fd), 1e-3), (m, fd, gdrive[m])
+    fd = (run(wscale=1 + eps) - run(wscale=1 - eps)) / (2 * eps)
+    assert abs(fd - gws) <= TOL_GRAD * max(abs(fd), 1e-3), (fd, gws)
+    i, j = 0, 2
+    dh = np.zeros_like(d["h"])
+    dh[i, j] = dh[j, i] = 1.0
+    fd = (run(h=d["h"] + eps * dh) - run(h=d["h"] - eps * dh)) / (2 * eps)
+    assert abs(fd - (gh[i, j].real + gh[j, i].real)) <= TOL_GRAD * max(abs(fd), 1e-3)
+    # the GW gradients differ from the SOA ones on this cluster
+    with Propagator(d["h"], d["w"], d["n0"], None, "SOA", "fp64") as p:
+        p.set_drive(d["D"], d["drive"])
+        _, gdrive_soa, _, _ = p.adjoint(dt, nsteps, objective=0, ckpt_every=9, n_drive_params=M)
+    assert np.abs(gdrive - gdrive_soa).max() > 1e-3 * np.abs(gdrive).max()
 
 
 def test_adjoint_independent_of_checkpoint_interval():
