@@ -600,7 +600,69 @@ void vjp_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n, const cplx *G, 
   mode_left2(c, L, c->nbar, c->AB1, c->T2, one, 0.0);
   mode_left1(c, L, c->nbar, c->T2, c->AB2, one, 0.0);      // B4 = nbar x_1 nbar x_2 T1'
   contract3(c, L, 4, c->AE, c->AB2, one, 1.0, nbar);
-  if (c->se != G1G2_GW) return;
+  // Ladder terms (Eqs. lambdapp, lambdaph): the source buffer holds A - Lambda, so the cotangent
+  // of Lambda is -AE.  With nbar = 1 - n, dH^pp_ijkl = -sum_p dn_ip w_pjkl - sum_q dn_jq w_iqkl
+  // and dH^ph_ijkl = sum_p dn_ip w_pjkl - sum_q dn_ql w_ijkq (Eqs. HTPPcorr, HTPHcorr).
+  if (c->se == G1G2_TPP || c->se == G1G2_DSL) {
+    mode_left2(c, L, c->nbar, c->w, c->T1, one, 0.0);    // Hb = (nbar (x) nbar - n (x) n) w
+    mode_left1(c, L, c->nbar, c->T1, c->Hb, one, 0.0);
+    mode_left2(c, L, n, c->w, c->T1, one, 0.0);
+    mode_left1(c, L, n, c->T1, c->Hb, mone, 1.0);
+    {
+      ZGemm g;  // Gbar_(pq),(kl) -= sum_(ij) conj(H_(ij),(pq)) AE_(ij),(kl)
+      g.M = (int)N2; g.N = (int)N2; g.K = (int)N2;
+      g.A = c->Hb; g.sa_m = 1; g.sa_k = N2; g.conjA = true;
+      g.B = c->AE; g.sb_k = N2; g.sb_n = 1;
+      g.C = Gbar; g.sc_m = N2; g.sc_n = 1;
+      g.alpha = mone; g.beta = 1.0;
+      zgemm(L, g);
+    }
+    {
+      ZGemm g;  // AB1 = Hbar_(ij),(pq) = -sum_(kl) AE_(ij),(kl) conj(G_(pq),(kl))
+      g.M = (int)N2; g.N = (int)N2; g.K = (int)N2;
+      g.A = c->AE; g.sa_m = N2; g.sa_k = 1;
+      g.B = G; g.sb_k = 1; g.sb_n = N2; g.conjB = true;
+      g.C = c->AB1; g.sc_m = N2; g.sc_n = 1;
+      g.alpha = mone;
+      zgemm(L, g);
+    }
+    contract3(c, L, 1, c->AB1, c->w, mone, 1.0, nbar);
+    contract3(c, L, 2, c->AB1, c->w, mone, 1.0, nbar);
+  }
+  if (c->se == G1G2_TPH || c->se == G1G2_DSL) {
+    mode_left1(c, L, n, c->w, c->T1, one, 0.0);           // Hb = n w nbar - nbar w n (modes 1 and 4)
+    mode_right4(c, L, c->T1, c->nbar, c->Hb, one, 0.0);
+    mode_left1(c, L, c->nbar, c->w, c->T1, one, 0.0);
+    mode_right4(c, L, c->T1, n, c->Hb, mone, 1.0);
+    const int pH[4] = {0, 2, 3, 1};  // Hp[i][l][p][q] = H[i][p][q][l]
+    permute4(L, nb, c->Hb, c->Hp, pH, one, 0.0, false);
+    const int pGt[4] = {1, 2, 3, 0};  // Gp[p][q][j][k] = G[q][j][k][p]
+    permute4(L, nb, G, c->Gp, pGt, one, 0.0, false);
+    permute4(L, nb, c->AE, c->Pp, pH, mone, 0.0, false);  // Pp[i][l][j][k] = -AE_ijkl (cotangent of Lambda)
+    {
+      ZGemm g;  // AB2[(pq)][(jk)] = sum_(il) conj(Hp[(il)][(pq)]) Pp[(il)][(jk)]
+      g.M = (int)N2; g.N = (int)N2; g.K = (int)N2;
+      g.A = c->Hp; g.sa_m = 1; g.sa_k = N2; g.conjA = true;
+      g.B = c->Pp; g.sb_k = N2; g.sb_n = 1;
+      g.C = c->AB2; g.sc_m = N2; g.sc_n = 1;
+      zgemm(L, g);
+    }
+    const int pGb[4] = {3, 0, 1, 2};  // Gbar[q][j][k][p] += AB2[p][q][j][k]
+    permute4(L, nb, c->AB2, Gbar, pGb, one, 1.0, false);
+    {
+      ZGemm g;  // AB1[(il)][(pq)] = sum_(jk) Pp[(il)][(jk)] conj(Gp[(pq)][(jk)])
+      g.M = (int)N2; g.N = (int)N2; g.K = (int)N2;
+      g.A = c->Pp; g.sa_m = N2; g.sa_k = 1;
+      g.B = c->Gp; g.sb_k = 1; g.sb_n = N2; g.conjB = true;
+      g.C = c->AB1; g.sc_m = N2; g.sc_n = 1;
+      zgemm(L, g);
+    }
+    const int pHb[4] = {0, 3, 1, 2};  // T2 = Hbar[i][p][q][l] = AB1[i][l][p][q]
+    permute4(L, nb, c->AB1, c->T2, pHb, one, 0.0, false);
+    contract3(c, L, 1, c->T2, c->w, one, 1.0, nbar);
+    contract3(c, L, 4, c->T2, c->w, mone, 1.0, nbar);
+  }
+  if (c->se != G1G2_GW && c->se != G1G2_DSL) return;
   // GW: dG2 += -i (Pi - conj(Pi_lkji)), Pi_ijkl = sum_pq hcorr_qjpl G_ipkq, hcorr = w x_4 n - n x_2 w
   // (Eqs. gwpi, gwhcorr).  Cotangent of Pi: Pibar = i (Y + conj(Y_lkji)); then the transposed
   // products of the forward GEMM (Pp = Gp Hp) and of the two mode products of hcorr.
@@ -1271,8 +1333,7 @@ int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_de
   if (!c || !n_dev || !G2_dev || !dn_bar || !dG2_bar || !n_bar || !G2_bar || !h_bar)
     return fail(G1G2_EINVAL, "NULL argument");
   if (c->prec != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product runs on the FP64 form");
-  if ((c->se != G1G2_SOA && c->se != G1G2_HF && c->se != G1G2_GW) || c->hub_gw)
-    return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product covers HF, SOA and GW in a general basis");
+  if (c->hub_gw) return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product covers the general basis");
   if (c->eta > 0) return fail(G1G2_EUNSUPPORTED, "the vector-Jacobian product covers fermions");
   const long long N2 = (long long)c->nb * c->nb, N4 = N2 * N2;
   if (!c->AE) {  // scratch of the adjoint
@@ -1366,8 +1427,7 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
                  double *grad_drive, double *grad_wscale, double *grad_h) {
   if (!c || nsteps < 1 || !J_out) return fail(G1G2_EINVAL, "bad adjoint argument");
   if (c->prec != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint runs on the FP64 form");
-  if ((c->se != G1G2_SOA && c->se != G1G2_HF && c->se != G1G2_GW) || c->hub_gw)
-    return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers HF, SOA and GW in a general basis");
+  if (c->hub_gw) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers the general basis");
   if (c->eta > 0) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers fermions");
   if (objective < 0 || objective > 2) return fail(G1G2_EINVAL, "objective must be 0, 1 or 2");
   if (objective == 0 && (c->basis != G1G2_SPIN_ORBITAL || c->nb % 2))

@@ -23,7 +23,8 @@ def rdot(x, y):
 
 
 @pytest.mark.parametrize("nb,restricted,se", [(6, False, "SOA"), (8, False, "SOA"), (5, True, "SOA"),
-                                              (6, False, "GW"), (7, False, "GWX")])
+                                              (6, False, "GW"), (7, False, "GWX"), (6, False, "TPP"),
+                                              (6, False, "TPH"), (5, True, "TPP"), (5, False, "DSL")])
 def test_vjp_dot_product(nb, restricted, se):
     """<J d, ybar> by central differences of g1g2_rhs equals <d, VJP(ybar)>."""
     from paper_2002_12717_gb300.g1g2 import Propagator
@@ -116,18 +117,20 @@ def test_adjoint_matches_central_differences(objective):
         assert abs(fd - want) <= TOL_GRAD * max(abs(fd), 1e-3), (kind, fd, want)
 
 
-def test_gw_adjoint_matches_central_differences():
-    """GW (Eqs. g2-eq-gw-pi, gwpi, gwhcorr): the adjoint's gradients with respect to the
-    drive controls, the scale of w and a hopping against central differences."""
+@pytest.mark.parametrize("se", ["GW", "TPP", "TPH", "DSL"])
+def test_correlated_adjoint_matches_central_differences(se):
+    """GW (Eqs. g2-eq-gw-pi, gwpi, gwhcorr), the T matrices (Eqs. g2-eq-tpp-lambda,
+    g2-eq-tph-lambda) and DSL: the adjoint's gradients with respect to the drive
+    controls, the scale of w and a hopping against central differences."""
     from paper_2002_12717_gb300.g1g2 import Propagator
     dt, nsteps, M = 0.02, 40, 4
     d = _hubbard_case(M, nsteps, dt)
-    with Propagator(d["h"], d["w"], d["n0"], None, "GW", "fp64") as p:
+    with Propagator(d["h"], d["w"], d["n0"], None, se, "fp64") as p:
         p.set_drive(d["D"], d["drive"])
         J, gdrive, gws, gh = p.adjoint(dt, nsteps, objective=0, ckpt_every=9, n_drive_params=M)
     eps = 1e-5
     vals = d["drive"].values
-    run = lambda **kw: _run_J(d, 0, nsteps, dt, se="GW", **kw)
+    run = lambda **kw: _run_J(d, 0, nsteps, dt, se=se, **kw)
     for m in range(M):
         vp, vm = vals.copy(), vals.copy()
         vp[m] += eps
@@ -141,7 +144,7 @@ def test_gw_adjoint_matches_central_differences():
     dh[i, j] = dh[j, i] = 1.0
     fd = (run(h=d["h"] + eps * dh) - run(h=d["h"] - eps * dh)) / (2 * eps)
     assert abs(fd - (gh[i, j].real + gh[j, i].real)) <= TOL_GRAD * max(abs(fd), 1e-3)
-    # the GW gradients differ from the SOA ones on this cluster
+    # the gradients differ from the SOA ones on this cluster
     with Propagator(d["h"], d["w"], d["n0"], None, "SOA", "fp64") as p:
         p.set_drive(d["D"], d["drive"])
         _, gdrive_soa, _, _ = p.adjoint(dt, nsteps, objective=0, ckpt_every=9, n_drive_params=M)
