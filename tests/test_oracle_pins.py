@@ -712,6 +712,56 @@ def test_g1g2_solution_satisfies_the_interval_recursion():
     assert errs[1] < 2e-4 and 3.0 < errs[0] / errs[1] < 5.0
 
 
+def test_hubbard_gw_reduced_polarisation_with_site_dependent_u():
+    """Sec. VIII.B: with G^> = G^< - i the Hubbard polarisation terms (Eqs. pihubbardtrans,
+    pihubbardcis) reduce to Pi^{ud ud}_ijkl = -i G^<_jl (U_j G^{uuuu}_ijkj - U_l G^{uuuu}_ilkl)
+    and the same with the spin blocks exchanged; U_p sits inside the site sum.  Checked
+    against the general spin-orbital polarisation (Eq. gwpi) of a 3-site cluster with
+    site-dependent U; the blocks mixing the spins crosswise vanish."""
+    rng = np.random.default_rng(5)
+    L = 3
+    nb = 2 * L
+    U = np.array([1.0, 0.7, 1.3])
+    w = np.zeros((nb,) * 4)
+    for i in range(L):
+        for a in range(2):
+            w[2 * i + a, 2 * i + 1 - a, 2 * i + a, 2 * i + 1 - a] = U[i]
+    ns = inputs.random_hermitian(L, rng) * 0.2 + 0.4 * np.eye(L)
+    n = np.kron(ns, np.eye(2)).astype(complex)
+    _, g2 = inputs.random_state(nb, rng, soa=False)
+    pi = O.gw_polarisation(O.gw_hcorr(w.astype(complex), n), g2)
+
+    def blk(t, spins):
+        return t[np.ix_(*[np.arange(L) * 2 + x for x in spins])]
+
+    gl = 1j * ns
+    reduced = lambda Go: (-1j * (np.einsum("jl,j,ijkj->ijkl", gl, U, Go) - np.einsum("jl,l,ilkl->ijkl", gl, U, Go)))
+    assert np.abs(blk(pi, (0, 1, 0, 1)) - reduced(blk(g2, (0, 0, 0, 0)))).max() < 1e-14
+    assert np.abs(blk(pi, (0, 0, 0, 0)) - reduced(blk(g2, (0, 1, 0, 1)))).max() < 1e-14
+    assert np.abs(blk(pi, (0, 1, 1, 0))).max() == 0.0
+
+
+def test_correlation_terms_are_exchange_symmetric():
+    """The tensor-core assembly symmetrises every G2 term over the exchange (ij) <-> (ji),
+    (kl) <-> (lk), which is exact because each correlation term keeps 𝒢_ijkl = 𝒢_jilk
+    (Eq. Gsymm_a): Pi - conj(Pi_lkji) and both Lambda - conj(Lambda_klij).  And the
+    ladder product the tensor cores compute is Lambda^dag = 𝒢 H^dag (𝒢 Hermitian as an
+    nb^2 x nb^2 matrix, Eq. Gsymm_b)."""
+    rng = np.random.default_rng(6)
+    nb = 4
+    w = sym_w(nb, rng)
+    n, g2 = inputs.random_state(nb, rng, soa=False)
+    ex = lambda t: np.abs(t - t.transpose(1, 0, 3, 2)).max() / np.abs(t).max()
+    pi = O.gw_polarisation(O.gw_hcorr(w, n), g2)
+    assert ex(pi - pi.transpose(3, 2, 1, 0).conj()) < 1e-13
+    for hc, lad in ((O.tpp_hcorr, O.tpp_ladder), (O.tph_hcorr, O.tph_ladder)):
+        lam = lad(hc(w, n), g2)
+        assert ex(lam - lam.transpose(2, 3, 0, 1).conj()) < 1e-13
+    H = O.tpp_hcorr(w, n).reshape(nb * nb, nb * nb)
+    lam_dag = O.tpp_ladder(O.tpp_hcorr(w, n), g2).transpose(2, 3, 0, 1).conj().reshape(nb * nb, nb * nb)
+    assert np.abs(lam_dag - g2.reshape(nb * nb, nb * nb) @ H.conj().T).max() < 1e-13
+
+
 def test_torch_restatement_matches_oracle():
     """The autograd restatement (oracle/torch_oracle.py) reproduces the numpy oracle's RK4 run."""
     import torch
