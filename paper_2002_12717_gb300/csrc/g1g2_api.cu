@@ -755,7 +755,7 @@ int hub_upload_pattern(g1g2_ctx *c, const std::vector<cplx> *D) {
   return G1G2_OK;
 }
 
-int adj_alloc(g1g2_ctx *c, std::vector<void *> &own, void **p, size_t bytes) {
+int adj_alloc(g1g2_ctx *, std::vector<void *> &own, void **p, size_t bytes) {
   void *q = nullptr;
   if (cudaMalloc(&q, bytes) != cudaSuccess) {
     cudaGetLastError();
