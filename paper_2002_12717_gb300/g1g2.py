@@ -74,6 +74,7 @@ def load():
         "g1g2_adjoint": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
                                         _dp]),
         "g1g2_wait_selftest": (ctypes.c_int, [ctypes.c_int]),
+        "g1g2_g1_rhs_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int] + [vp] * 6),
         "g1g2_set_hubbard_path": (ctypes.c_int, [vp, ctypes.c_int]),
         "g1g2_hubbard_path": (ctypes.c_int, [vp]),
         "g1g2_set_adjoint_checkpoints": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -91,6 +92,18 @@ def load():
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def g1_rhs_noalloc(h, w, n, g2, dn, restricted=False, stream=None):
+    """G1 right-hand side dn = -i[hHF, n] - (I + I^dag) through g1g2_g1_rhs_noalloc, which
+    allocates no device memory; all arguments are contiguous complex128 CUDA tensors
+    (w in the nb^4 complex ABI layout), dn is written."""
+    for x in (h, w, n, g2, dn):
+        if not (x.is_cuda and x.is_contiguous()):
+            raise ValueError("device tensors must be contiguous CUDA tensors")
+    _check(load().g1g2_g1_rhs_noalloc(int(h.shape[0]), 1 if restricted else 0, h.data_ptr(), w.data_ptr(),
+                                       n.data_ptr(), g2.data_ptr(), dn.data_ptr(),
+                                       None if stream is None else int(stream)))
 
 
 def wait_selftest(limit_us=20000):
