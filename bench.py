@@ -37,8 +37,9 @@ from paper_2002_12717_gb300 import inputs  # noqa: E402
 METRIC = "G1-G2 RK4 steps/s (one step = SOA nb=96 + GW nb=64)"
 WORKLOADS = ("general-soa-nb96", "general-gw-nb64")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 (DFMA) throughput of one GB300, measured with a dependent-free DFMA loop over
-# all SMs (profiles/fp64_dfma_peak.md); used as the ALU roofline of the FP64 form.
+# FP64 (DFMA) throughput of one GB300 (profiles/fp64_dfma_peak.md: the FP64 GEMM sustains
+# 1.212 TFLOP/s; `--fp64-peak` runs the committed probe, a lower bound); used as the ALU
+# roofline of the FP64 form.
 FP64_PEAK_TFLOPS = 1.200
 FP64_PEAK_NOTE = "profiles/fp64_dfma_peak.md"
 # nominal dense tensor ratio TF32 / BF16 (1.1 / 2.25 PFLOP/s)
@@ -595,6 +596,8 @@ def main():
                     help="selfenergy of --hubbard-scaling")
     ap.add_argument("--nt-scaling", default="",
                     help="comma-separated N_t: time the memory-integral HF-GKBA against the G1-G2 equations and exit")
+    ap.add_argument("--fp64-peak", action="store_true",
+                    help="measure the FP64 FMA rate of the GPU (the FP64 roofline) and exit")
     ap.add_argument("--selfenergy-sweep", default="",
                     help="comma-separated nb: time every selfenergy and exit (forms: --sweep-precisions)")
     ap.add_argument("--sweep-precisions", default="fp64", help="comma-separated forms of --selfenergy-sweep")
@@ -615,6 +618,14 @@ def main():
             sizes = [int(x) for x in args.hubbard_scaling.split(",")]
             print(json.dumps({"hubbard_scaling": hubbard_scaling(sizes, selfenergy=args.hubbard_selfenergy)}),
                   flush=True)
+        return
+    if args.fp64_peak:
+        if rank == 0:
+            from paper_2002_12717_gb300.g1g2 import fp64_rate
+            sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+            sampler.start()
+            rate = fp64_rate()
+            print(json.dumps({"fp64_fma_tflops": round(rate, 4), "clocks": sampler.stop()}), flush=True)
         return
     if args.selfenergy_sweep:
         if rank == 0:

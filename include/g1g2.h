@@ -248,6 +248,13 @@ int g1g2_adjoint_plan(const g1g2_ctx *c, int *ckpt_every, int *where);
  *   g1g2_set_hubbard_path(c, 1) back (G1G2_EUNSUPPORTED if the structure does
  *   not qualify); g1g2_hubbard_path returns 1 when it is in use, 0 when not,
  *   G1G2_EINVAL for a NULL context. */
+/* The FP64 FMA throughput of the current device in TFLOP/s: eight independent
+ * DFMA chains per thread over 8 blocks of 256 threads per SM, best of three
+ * launches timed with CUDA events after two untimed ones (about 4 s in all).  The ALU roofline of
+ * the FP64 form and of the memory-integral HF-GKBA.  Not part of the paper's
+ * method.  G1G2_ECUDA on a CUDA failure. */
+int g1g2_fp64_rate(double *tflops);
+
 int g1g2_set_hubbard_path(g1g2_ctx *c, int enable);
 int g1g2_hubbard_path(const g1g2_ctx *c);
 

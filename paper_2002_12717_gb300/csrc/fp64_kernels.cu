@@ -956,3 +956,58 @@ void count_nonzero(Launcher &L, const cplx *x, long long len, double *cnt) {
 }
 
 }  // namespace g1g2
+
+// ---------------------------------------------------------------------------
+// FP64 FMA throughput probe: the ALU roofline of the FP64 form
+// ---------------------------------------------------------------------------
+namespace g1g2 {
+namespace {
+
+// eight independent DFMA chains per thread, no memory traffic but one store per thread
+__global__ void __launch_bounds__(256) dfma_probe_kernel(int iters, double *out) {
+  const double m = 0.9999999, a = 1e-9;
+  double x0 = threadIdx.x * 1e-6, x1 = x0 + 0.1, x2 = x0 + 0.2, x3 = x0 + 0.3;
+  double x4 = x0 + 0.4, x5 = x0 + 0.5, x6 = x0 + 0.6, x7 = x0 + 0.7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, m, a); x1 = fma(x1, m, a); x2 = fma(x2, m, a); x3 = fma(x3, m, a);
+    x4 = fma(x4, m, a); x5 = fma(x5, m, a); x6 = fma(x6, m, a); x7 = fma(x7, m, a);
+  }
+  out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+}  // namespace
+
+double dfma_rate(cudaStream_t stream, int *err) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 8, threads = 256, iters = 16384;   // about 0.8 s per launch
+  double *out = nullptr;
+  *err = 0;
+  if (cudaMalloc(&out, (size_t)blocks * threads * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    *err = 1;
+    return 0.0;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 0.0;
+  for (int rep = 0; rep < 5; ++rep) {   // the first two launches bring the clocks up
+    cudaEventRecord(e0, stream);
+    dfma_probe_kernel<<<blocks, threads, 0, stream>>>(iters, out);
+    cudaEventRecord(e1, stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { *err = 1; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double flop = 2.0 * 8.0 * iters * (double)blocks * threads;
+    if (rep > 1 && ms > 0.f) best = std::max(best, flop / (ms * 1e-3) / 1e12);
+  }
+  if (cudaGetLastError() != cudaSuccess) *err = 1;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  return best;
+}
+
+}  // namespace g1g2

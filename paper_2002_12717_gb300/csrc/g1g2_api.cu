@@ -1403,6 +1403,13 @@ int g1g2_set_hubbard_path(g1g2_ctx *c, int enable) {
 
 int g1g2_hubbard_path(const g1g2_ctx *c) { return c ? (c->hub_on ? 1 : 0) : G1G2_EINVAL; }
 
+int g1g2_fp64_rate(double *tflops) {
+  if (!tflops) return fail(G1G2_EINVAL, "tflops is NULL");
+  int err = 0;
+  *tflops = dfma_rate(nullptr, &err);
+  return err ? fail(G1G2_ECUDA, "FP64 rate probe failed") : G1G2_OK;
+}
+
 int g1g2_wait_selftest(int limit_us) {
   if (limit_us < 1 || limit_us > 10000000) return fail(G1G2_EINVAL, "limit must be 1 us .. 10 s");
   return tc_wait_selftest(1000ull * (unsigned long long)limit_us, nullptr);

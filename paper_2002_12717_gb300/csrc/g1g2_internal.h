@@ -137,6 +137,10 @@ void mode_rotate(Launcher &L, int nb, int batch, const cplx *in, const cplx *S, 
 void batch_sum(Launcher &L, long long len, int nbatch, const cplx *x, double beta, cplx *out);
 void count_nonzero(Launcher &L, const cplx *x, long long len, double *cnt);
 
+// Measured FP64 FMA rate of the current device in TFLOP/s (eight independent DFMA chains
+// per thread, best of three timed launches after two untimed ones); *err != 0 on a CUDA failure.
+double dfma_rate(cudaStream_t stream, int *err);
+
 // Text returned by g1g2_last_error_detail on this thread.
 void set_error_detail(const std::string &what);
 

@@ -74,6 +74,7 @@ def load():
         "g1g2_adjoint": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
                                         _dp]),
         "g1g2_wait_selftest": (ctypes.c_int, [ctypes.c_int]),
+        "g1g2_fp64_rate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
         "g1g2_g1_rhs_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int] + [vp] * 6),
         "g1g2_set_hubbard_path": (ctypes.c_int, [vp, ctypes.c_int]),
         "g1g2_hubbard_path": (ctypes.c_int, [vp]),
@@ -104,6 +105,13 @@ def g1_rhs_noalloc(h, w, n, g2, dn, restricted=False, stream=None):
     _check(load().g1g2_g1_rhs_noalloc(int(h.shape[0]), 1 if restricted else 0, h.data_ptr(), w.data_ptr(),
                                        n.data_ptr(), g2.data_ptr(), dn.data_ptr(),
                                        None if stream is None else int(stream)))
+
+
+def fp64_rate():
+    """Measured FP64 FMA throughput of the current GPU in TFLOP/s (g1g2_fp64_rate)."""
+    v = ctypes.c_double()
+    _check(load().g1g2_fp64_rate(ctypes.byref(v)))
+    return v.value
 
 
 def wait_selftest(limit_us=20000):
