@@ -65,13 +65,14 @@ typedef enum {
                            (end of Sec. IV.C); spin-orbital basis only */
   G1G2_TPP = 4,         /* particle-particle T matrix, Sec. IV.D, Eq. (g2-eq-tpp-lambda): the SOA
                            equation plus the ladder term Lambda - (Lambda_klij)^*, Lambda = hcorr G2
-                           (Eqs. HTPPcorr, lambdapp); FP64 form only */
+                           (Eqs. HTPPcorr, lambdapp); FP64 and BF16-slice forms */
   G1G2_TPH = 5,         /* particle-hole T matrix, Sec. IV.E, Eq. (g2-eq-tph-lambda): the same with
                            Lambda_ijkl = sum_pq hcorr_ipql G2_qjkp (Eqs. HTPHcorr, lambdaph); FP64
-                           form only */
+                           and BF16-slice forms */
   G1G2_DSL = 6          /* dynamically screened ladder, Sec. V, Eq. (g2-dsl-equation-pi-lambda):
                            Psi^± plus the GW term Pi - (Pi_lkji)^* plus the ladder term with
-                           Lambda = Lambda^pp + Lambda^ph; spin-orbital basis, FP64 form only */
+                           Lambda = Lambda^pp + Lambda^ph; spin-orbital basis, FP64 and
+                           BF16-slice forms */
 } g1g2_selfenergy;
 
 /* Arithmetic of the contractions. The RK4 state update, the Hartree-Fock
@@ -189,7 +190,8 @@ int g1g2_propagate_hfgkba(g1g2_ctx *c, double dt, int nsteps, double *G1_history
  * (E10: d_i = n_{i+,i+} n_{i-,i-} - |n_{i+,i-}|^2 - G2_{i+ i- i+ i-}). */
 int g1g2_observables(g1g2_ctx *c, g1g2_obs *out, double *density, double *double_occ);
 
-/* Vector-Jacobian product of the right-hand side (FP64 form, SOA): given the
+/* Vector-Jacobian product of the right-hand side (FP64 form; fermions in a general
+ * basis, every selfenergy; not the spin-restricted Hubbard GW): given the
  * cotangents (dn_bar, dG2_bar) of (dn/dt, dG2/dt) at the state (n, G2) at time
  * t, write the cotangents of n, of G2 and of h^HF (= of the explicit h(t)),
  * with respect to Re sum conj(x) y.  All pointers are caller-owned device
@@ -198,7 +200,8 @@ int g1g2_observables(g1g2_ctx *c, g1g2_obs *out, double *density, double *double
 int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_dev, const double *dn_bar,
                  const double *dG2_bar, double *n_bar, double *G2_bar, double *h_bar);
 
-/* Discrete adjoint of nsteps RK4 steps of the FP64 form (HF or SOA), starting
+/* Discrete adjoint of nsteps RK4 steps of the FP64 form (fermions, every selfenergy
+ * in a general basis), starting
  * from the current state: the gradient of a final-time objective J with
  * respect to the drive parameters, a global scale of w and the entries of h.
  * Not in the paper; the reverse sweep is the exact transpose of the discrete
@@ -219,7 +222,8 @@ int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_de
  *               perturbation dh, dJ = Re sum conj(G_ij) dh_ij (G is Hermitian), or NULL
  * Cotangents use Re sum conj(x) y over every complex entry of (G1, G2).  On
  * return the context holds the final state (as after g1g2_propagate).
- * G1G2_EUNSUPPORTED for the tensor-core precision or GW. */
+ * G1G2_EUNSUPPORTED for the tensor-core precision, bosons and the spin-restricted
+ * Hubbard GW. */
 int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objective, double *J_out,
                  double *grad_drive, double *grad_wscale, double *grad_h);
 
