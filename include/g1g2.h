@@ -187,7 +187,8 @@ int g1g2_propagate_hfgkba(g1g2_ctx *c, double dt, int nsteps, double *G1_history
 
 /* Observables of the current state (synchronous). density: nb doubles or NULL.
  * double_occ: nb/2 doubles or NULL, spin-orbital basis with index 2*site+spin only
- * (E10: d_i = n_{i+,i+} n_{i-,i-} - |n_{i+,i-}|^2 - G2_{i+ i- i+ i-}). */
+ * (E10: d_i = n_{i+,i+} n_{i-,i-} - |n_{i+,i-}|^2 - G2_{i+ i- i+ i-}; + |n_{i+,i-}|^2
+ * for bosons, Eq. ini-g2). */
 int g1g2_observables(g1g2_ctx *c, g1g2_obs *out, double *density, double *double_occ);
 
 /* Vector-Jacobian product of the right-hand side (FP64 form; fermions in a general

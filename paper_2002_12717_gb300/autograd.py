@@ -39,7 +39,8 @@ def _drive(problem, params):
 
 
 class FinalTimeObjective(torch.autograd.Function):
-    """J(theta, s, h) of a final-time observable after nsteps RK4 steps (SOA or HF, FP64 form)."""
+    """J(theta, s, h) of a final-time observable after nsteps RK4 steps (FP64 form, any fermion selfenergy
+    in a general basis)."""
 
     @staticmethod
     def forward(ctx, drive_params, wscale, h, problem, dt, nsteps, objective, ckpt_every):
