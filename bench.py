@@ -83,30 +83,36 @@ SPLIT_PRODUCTS = {"tf32x3": 3, "bf16x4": 10}
 
 
 def kernel_work(tag, nb, se, precision="tf32x3"):
-    """(bound, work per launch) of the dominant-kernel candidates.
+    """(bound, algorithmic work per launch, issued work per launch) of the dominant-kernel
+    candidates.
 
-    Tensor kernels count the real flops of the split-precision products the
-    kernel must issue (three TF32 products, or ten BF16 slice products, per
-    real multiply-add, 2 flops each) on the unpadded problem; the assembly
-    counts its algorithmic HBM bytes (FP32 intermediates, FP64 state, FP32
-    RK4 accumulator and stage input), averaged over the four RK4 stages.
+    Algorithmic work is the contraction the launch evaluates at 8 real flops per
+    complex multiply-add (4 per real-by-complex one): the polarisation and the
+    ladder products nb^6 complex MACs, a complex nb^5 pass nb^5, a pass with the
+    real w as A (source pass 1, quasi-Hamiltonian, collision) nb^5 real-by-complex
+    MACs.  Issued work counts the split-precision products the kernel runs on the
+    realified problem (three TF32 products, or ten BF16 slice products, per real
+    multiply-add, 2 flops each): issued / algorithmic is the cost of the emulated
+    FP32-class accuracy.  The assembly counts its algorithmic HBM bytes (FP32
+    intermediates, FP64 state, FP32 RK4 accumulator and stage input), averaged over
+    the four RK4 stages.
     """
     n = float(nb)
     split = SPLIT_PRODUCTS.get(precision, 3) * 2
     if tag in ("tc_gemm_pi", "tc_gemm_ladder"):
-        return "tensor", split * n * n * (2 * n * n) * (2 * n * n)
+        return "tensor", 8 * n ** 6, split * n * n * (2 * n * n) * (2 * n * n)
     if tag in ("tc_gemm_commutator", "tc_gemm_psi2", "tc_gemm_psi3", "tc_gemm_psi4"):
-        return "tensor", split * n ** 3 * (2 * n) * (2 * n)
+        return "tensor", 8 * n ** 5, split * n ** 3 * (2 * n) * (2 * n)
     if tag in ("tc_gemm_psi1", "tc_gemm_hcorr"):
-        return "tensor", split * n ** 3 * (2 * n) * n
+        return "tensor", 4 * n ** 5, split * n ** 3 * (2 * n) * n
     if tag == "tc_gemm_collision":
-        return "tensor", split * (2 * n) * n * n ** 3
+        return "tensor", 4 * n ** 5, split * (2 * n) * n * n ** 3
     if tag == "tc_orbit_assemble_rk4":
         per_elem = 8 + 8 + 16 + 0.75 * 8 + 18 + (8 if se == "GW" else 0)
-        return "hbm", per_elem * n ** 4
+        return "hbm", per_elem * n ** 4, per_elem * n ** 4
     if tag in ("fp64_zgemm", "fp64_zgemm_splitk"):
-        return "alu", None
-    return None, None
+        return "alu", None, None
+    return None, None, None
 
 
 class ClockSampler:
@@ -207,10 +213,10 @@ def run_ours(args, rank, world, dist):
         prop.propagate(dt, args.warmup)          # warm-up steps (untimed)
         torch.cuda.synchronize()
         barrier()
-        prop.profile(True)
         c0 = prop.launch_count
         if not per:
             clocks.start()
+        # the library launches on the default stream, where these events are recorded
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         start.record()
@@ -221,6 +227,11 @@ def run_ours(args, rank, world, dist):
         ms = start.elapsed_time(end) / args.steps
         launches = prop.launch_count - c0
         launches_total += launches
+        # per-kernel device time from a separate pass of the same number of steps, with a
+        # CUDA-event pair around every launch (kept out of the timed region above)
+        prop.profile(True)
+        for _ in range(args.steps):
+            prop.step(dt)
         rep = prop.profile_report()
         prop.profile(False)
         for k, (n_l, t_ms) in rep.items():
@@ -288,18 +299,20 @@ def run_ours(args, rank, world, dist):
         cands = [(0.0, "none", next(iter(per)), 1)]
     t_ms, dom_tag, dom_wl, dom_n = cands[0]
     d_nb, d_se = per[dom_wl]["nb"], per[dom_wl]["selfenergy"]
-    bound, work = kernel_work(dom_tag, d_nb, d_se, args.precision)
+    bound, work, issued = kernel_work(dom_tag, d_nb, d_se, args.precision)
     avg_s = t_ms * 1e-3 / dom_n
-    if bound == "tensor" and args.precision == "bf16x4":
-        peak = peaks["bf16_tflops_sustained"]
+    if bound == "tensor":
+        if args.precision == "bf16x4":
+            peak = peaks["bf16_tflops_sustained"]
+            src = f"{peak_kind} bf16 sustained (cuBLAS loop), of {peak_kind}"
+        else:
+            peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+            src = f"{peak_kind} bf16 sustained x TF32/BF16 nominal ratio (1.1/2.25), of {peak_kind}"
         achieved = work / avg_s / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"{peak_kind} bf16 sustained (cuBLAS loop), of {peak_kind}"}
-    elif bound == "tensor":
-        peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
-        achieved = work / avg_s / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"{peak_kind} bf16 sustained x TF32/BF16 nominal ratio (1.1/2.25), of {peak_kind}"}
+                "work": "algorithmic: 8 flop per complex MAC of the contraction the launch evaluates",
+                "issued_achieved": issued / avg_s / 1e12, "issued_frac": issued / avg_s / 1e12 / peak,
+                "issued_over_algorithmic": issued / work, "peak_source": src}
     elif bound == "hbm":
         peak = peaks["hbm_gbs"]
         achieved = work / avg_s / 1e9
@@ -479,8 +492,8 @@ def selfenergy_sweep(sizes, precisions=("fp64",), steps=2):
     """ms per RK4 step of every selfenergy on the seeded general basis (rank 2 nb, nb/2
     occupied, gauss-sine pulse).  FP64 form: the algorithmic FLOP rate against the
     measured DFMA rate; BF16-slice form: the rate of its nb^2 x nb^2 x nb^2 products
-    (polarisation, ladder) in issued slice products against the measured sustained BF16
-    rate."""
+    (polarisation, ladder), algorithmic and in issued slice products, against the measured
+    sustained BF16 rate."""
     import torch
 
     from paper_2002_12717_gb300.g1g2 import from_workload
@@ -515,34 +528,75 @@ def selfenergy_sweep(sizes, precisions=("fp64",), steps=2):
             for tag in ("tc_gemm_pi", "tc_gemm_ladder"):
                 if tag in prof:
                     launches, tms = prof[tag]
-                    work = kernel_work(tag, nb, se, prec)[1]
+                    _, work, issued = kernel_work(tag, nb, se, prec)
                     tf = work * launches / (tms * 1e-3) / 1e12
-                    row[tag] = {"ms_per_launch": round(tms / launches, 3), "issued_tflops": round(tf, 1),
-                                "frac_of_bf16_sustained": round(tf / peaks["bf16_tflops_sustained"], 3)}
+                    tfi = issued * launches / (tms * 1e-3) / 1e12
+                    row[tag] = {"ms_per_launch": round(tms / launches, 3), "algorithmic_tflops": round(tf, 1),
+                                "frac_of_bf16_sustained": round(tf / peaks["bf16_tflops_sustained"], 3),
+                                "issued_tflops": round(tfi, 1),
+                                "issued_frac_of_bf16_sustained": round(tfi / peaks["bf16_tflops_sustained"], 3)}
         out.append(row)
     return out
 
 
-def cpu_baseline(args):
-    """The CPU oracle as it stands, one right-hand side of each workload (bounded sample)."""
+def oracle_rhs_seconds(names):
+    """Wall seconds of one oracle right-hand side of each named workload (the oracle as it
+    stands, on whatever BLAS threads the process has)."""
     from oracle import g1g2_oracle as O
 
     times = {}
-    for name in args.workloads:
+    for name in names:
         d = inputs.workload(name)
         prob = O.Problem(d["h"], d["w"], d["selfenergy"], d["restricted"], d["D"], d["drive"].f)
         g0 = np.zeros((d["nb"],) * 4, dtype=np.complex128)
         t0 = time.perf_counter()
         O.rhs(prob, 0.0, d["n0"], g0)
         times[name] = time.perf_counter() - t0
+    return times
+
+
+SINGLE_THREAD_ENV = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                      "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")}
+
+
+def oracle_rhs_seconds_single_thread(names, timeout=300):
+    """oracle_rhs_seconds in a child process whose BLAS runs one thread (the thread
+    count of numpy's BLAS is fixed when it loads, hence the separate process)."""
+    env = dict(os.environ, **SINGLE_THREAD_ENV)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-rhs-times", ",".join(names)],
+                       env=env, capture_output=True, text=True, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(args):
+    """The CPU oracle as it stands (a bounded sample): one right-hand side of each workload
+    on all host cores, and one right-hand side of the GW workload on one thread."""
+    times = oracle_rhs_seconds(args.workloads)
     step_s = 4 * sum(times.values())   # an RK4 step is four right-hand sides
-    return {"value": 1.0 / step_s, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one right-hand side per workload (" + ", ".join(f"{k}: {v:.1f} s" for k, v in times.items())
-                      + "); RK4 step = 4 x the sum"}
+    out = {"value": 1.0 / step_s, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "one right-hand side per workload on all cores (" +
+                     ", ".join(f"{k}: {v:.1f} s" for k, v in times.items()) + "); RK4 step = 4 x the sum"}
+    one = [w for w in args.workloads if "gw" in w][:1] or args.workloads[:1]
+    try:
+        st = oracle_rhs_seconds_single_thread(one)
+        out["single_thread"] = {"cores": 1, "rhs_s": st, "all_cores_rhs_s": {k: times[k] for k in st},
+                                "all_core_speedup": {k: st[k] / times[k] for k in st},
+                                "sample": "one right-hand side of " + ", ".join(st) + " with BLAS on one thread"}
+    except (RuntimeError, subprocess.TimeoutExpired, ValueError) as e:
+        out["single_thread"] = {"unavailable": str(e)[-200:]}
+    return out
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle, alternating one RHS of each workload per step."""
+    """--impl reference: the CPU oracle, as it stands, on the host cores.
+
+    Each timed step is a bounded sample: one oracle right-hand side, alternating
+    between the workloads, so ms_per_step is the measured wall time of one such
+    sample.  value converts to the metric's unit: one bench step (one RK4 step of
+    each workload) is four right-hand sides of each workload.
+    """
     from oracle import g1g2_oracle as O
 
     probs = []
@@ -552,31 +606,94 @@ def run_reference(args):
                       d["n0"], np.zeros((d["nb"],) * 4, dtype=np.complex128)))
     times = {name: [] for name, *_ in probs}
     warm = min(args.warmup, 1)   # the oracle has no caches to warm; one untimed call
+    samples = []
     for i in range(warm + args.steps):
         name, prob, n0, g0 = probs[i % len(probs)]
         t0 = time.perf_counter()
         O.rhs(prob, 0.0, n0, g0)
         if i >= warm:
-            times[name].append(time.perf_counter() - t0)
+            dt = time.perf_counter() - t0
+            times[name].append(dt)
+            samples.append(dt)
     for name, *_ in probs:
         if not times[name]:   # K too small to visit every workload: time one call
             _, prob, n0, g0 = next(p for p in probs if p[0] == name)
             t0 = time.perf_counter()
             O.rhs(prob, 0.0, n0, g0)
             times[name].append(time.perf_counter() - t0)
-    step_s = 4 * sum(statistics.mean(v) for v in times.values())
-    value = 1.0 / step_s
-    sample = "per bench step one oracle right-hand side, alternating " + " / ".join(times) + \
-             "; RK4 step = 4 x (mean RHS time of each workload)"
+    bench_step_s = 4 * sum(statistics.mean(v) for v in times.values())
+    value = 1.0 / bench_step_s
+    sample = ("per timed step one oracle right-hand side, alternating " + " / ".join(times) +
+              "; one bench step = 4 right-hand sides of each workload = " +
+              " + ".join(f"4 x {statistics.mean(v):.2f} s" for v in times.values()))
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
+        "steps": args.steps, "warmup": warm, "ms_per_step": 1e3 * statistics.mean(samples) if samples else None,
+        "step": "one oracle right-hand side (a bounded sample); value converts it to RK4 bench steps",
+        "ms_per_bench_step": 1e3 * bench_step_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "+".join(args.workloads), "precision": "fp64-oracle"},
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+
+
+def accuracy_run(names, every, out_path):
+    """North-star accuracy over whole runs: each named workload propagated for its full
+    length in the BF16-slice tensor-core form and in the FP64 GPU form from the same
+    initial state, recorded every `every` steps: max|dG1| and max|dG2| between the two,
+    each form's energy drift |E(t) - E(0) - W(t)| / |E(0)| (W the drive work), and the
+    relative energy difference between the forms.  One JSON line per record, appended to
+    out_path as it is taken."""
+    import torch
+
+    from paper_2002_12717_gb300.g1g2 import from_workload
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    summary = []
+    for name in names:
+        d = inputs.workload(name)
+        dt, nsteps = d["dt"], d["nsteps"]
+        forms = {"bf16x4": from_workload(d, precision="bf16x4"), "fp64": from_workload(d, precision="fp64")}
+        o0 = {k: p.observables() for k, p in forms.items()}
+        secs = {k: 0.0 for k in forms}
+        worst = {"max_abs_dG1": 0.0, "max_abs_dG2": 0.0, "rel_dE": 0.0}
+        step = 0
+        while step < nsteps:
+            m = min(every, nsteps - step)
+            for k, p in forms.items():
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                p.propagate(dt, m)
+                torch.cuda.synchronize()
+                secs[k] += time.perf_counter() - t0
+            step += m
+            st = {k: p.get_state() for k, p in forms.items()}
+            ob = {k: p.observables() for k, p in forms.items()}
+            (_, n_m, g_m), (_, n_r, g_r) = st["bf16x4"], st["fp64"]
+            e0 = abs(o0["fp64"]["e_total"])
+            row = {"workload": name, "step": step, "t": ob["fp64"]["t"],
+                   "max_abs_dG1": float(np.abs(n_m - n_r).max()),
+                   "max_abs_dG2": float(np.abs(g_m - g_r).max()), "max_abs_G2": float(np.abs(g_r).max()),
+                   "rel_dE": abs(ob["bf16x4"]["e_total"] - ob["fp64"]["e_total"]) / e0,
+                   "drift": {k: abs(ob[k]["e_total"] - o0[k]["e_total"] - ob[k]["pulse_work"]) / abs(o0[k]["e_total"])
+                             for k in forms},
+                   "pulse_work": ob["fp64"]["pulse_work"], "seconds": dict(secs)}
+            del st, g_m, g_r
+            for key in worst:
+                worst[key] = max(worst[key], row[key])
+            with open(out_path, "a") as f:
+                f.write(json.dumps(row) + "\n")
+            print(json.dumps(row), flush=True)
+        for p in forms.values():
+            p.close()
+        summary.append({"workload": name, "steps": nsteps, "dt": dt, "record_every": every, **worst,
+                        "final_drift": row["drift"], "ms_per_step": {k: 1e3 * v / nsteps for k, v in secs.items()},
+                        "speedup": secs["fp64"] / secs["bf16x4"],
+                        "meets_target": worst["max_abs_dG1"] <= 1e-6 and worst["rel_dE"] <= 1e-7})
+        torch.cuda.empty_cache()
+    return summary
 
 
 def main():
@@ -601,6 +718,12 @@ def main():
     ap.add_argument("--selfenergy-sweep", default="",
                     help="comma-separated nb: time every selfenergy and exit (forms: --sweep-precisions)")
     ap.add_argument("--sweep-precisions", default="fp64", help="comma-separated forms of --selfenergy-sweep")
+    ap.add_argument("--accuracy-run", default="",
+                    help="comma-separated workloads: propagate each for its full length in the BF16-slice and "
+                         "FP64 forms side by side, record the differences and energy drifts, and exit")
+    ap.add_argument("--accuracy-every", type=int, default=50, help="record interval of --accuracy-run")
+    ap.add_argument("--accuracy-out", default="gpurun_out/accuracy.jsonl", help="JSON-lines file of --accuracy-run")
+    ap.add_argument("--oracle-rhs-times", default="", help=argparse.SUPPRESS)
     ap.add_argument("--adjoint-steps", type=int, default=100,
                     help="steps of the discrete-adjoint sample on the 4x4 Hubbard cluster (0: skip)")
     args = ap.parse_args()
@@ -613,6 +736,15 @@ def main():
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.oracle_rhs_times:
+        print(json.dumps(oracle_rhs_seconds(args.oracle_rhs_times.split(","))), flush=True)
+        return
+    if args.accuracy_run:
+        if rank == 0:
+            os.makedirs(os.path.dirname(os.path.abspath(args.accuracy_out)), exist_ok=True)
+            summary = accuracy_run(args.accuracy_run.split(","), args.accuracy_every, args.accuracy_out)
+            print(json.dumps({"accuracy_run": summary}), flush=True)
+        return
     if args.hubbard_scaling:
         if rank == 0:
             sizes = [int(x) for x in args.hubbard_scaling.split(",")]

@@ -314,9 +314,11 @@ int g1g2_profile_report(g1g2_ctx *c, g1g2_kernel_stat *out, int max_entries, int
  * exits and shared by every call on that GPU: calls whose kernels overlap on
  * the GPU (different streams, or threads without ordering) race on it.  The
  * first call on a device looks the array's address up (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
- * Nothing in the scratch needs clearing between calls: each call writes every
- * scratch element it reads. */
+ * with that device current; make that first call before any stream capture
+ * (a lookup that fails is not cached: the next call tries again).  Nothing in
+ * the scratch needs clearing between calls: each call writes every scratch
+ * element it reads.  A non-sticky CUDA error left pending by earlier work is
+ * cleared on entry, so it is not reported as this call's failure. */
 int g1g2_g1_rhs_noalloc(int nb, int restricted, const double *h_dev, const double *w_dev, const double *n_dev,
                         const double *G2_dev, double *dn_dev, void *cuda_stream);
 

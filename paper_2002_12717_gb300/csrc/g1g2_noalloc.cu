@@ -22,9 +22,11 @@ constexpr size_t kScratchElems = (size_t)(kMaxSplits + 2) * kMaxNb * kMaxNb;  //
 static __device__ __align__(256) double2 g_noalloc_scratch[kScratchElems];
 
 constexpr int kMaxDevices = 64;
+// Address of the array on each device; only a successful lookup is kept, so a
+// first call that failed for a passing reason (say, inside a stream capture)
+// does not block later calls on that device.
 double2 *g_scratch_ptr[kMaxDevices] = {};
-std::once_flag g_scratch_once[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices] = {};
+std::mutex g_scratch_mu;
 
 // h^HF_ij = h_ij + sum_kl (w_ikjl - w_iklj) n_lk  (restricted: no exchange term), w in the ABI layout.
 __global__ void hf_from_abi_w_kernel(int nb, int restricted, const double2 *__restrict__ h,
@@ -56,18 +58,23 @@ __global__ void hf_from_abi_w_kernel(int nb, int restricted, const double2 *__re
   if (lane == 0) hhf[warp] = {h[warp].x + acc.x, h[warp].y + acc.y};
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array on the current device: looked up with that
+// device current until one lookup succeeds, then reused.
 cudaError_t scratch_on_current_device(double2 **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::call_once(g_scratch_once[dev], [dev]() {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
     void *p = nullptr;
-    g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (g_scratch_err[dev] == cudaSuccess) g_scratch_ptr[dev] = static_cast<double2 *>(p);
-  });
-  if (g_scratch_err[dev] != cudaSuccess) return g_scratch_err[dev];
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // the failed lookup leaves no pending error behind
+      return e;
+    }
+    g_scratch_ptr[dev] = static_cast<double2 *>(p);
+  }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;
 }
@@ -86,6 +93,9 @@ extern "C" int g1g2_g1_rhs_noalloc(int nb, int restricted, const double *h_dev, 
     g1g2::set_error_detail("NULL device pointer");
     return G1G2_EINVAL;
   }
+  // A non-sticky error left pending by unrelated earlier work would otherwise be
+  // picked up by the launch checks below and reported as this call's failure.
+  cudaGetLastError();
   double2 *scratch = nullptr;
   cudaError_t e = scratch_on_current_device(&scratch);
   if (e != cudaSuccess) {

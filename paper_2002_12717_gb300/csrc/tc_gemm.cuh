@@ -1,30 +1,32 @@
-// Persistent tcgen05 GEMM with split-precision TF32 operands for the G1-G2
-// contractions.
+// Persistent tcgen05 GEMM for the nb^5 contractions of the G1-G2 right-hand
+// side, in two split-precision operand forms.
 //
 //   D[m][n] = sum_k A[m][k] B[n][k]        (both operands K-major)
 //
 // A is a big FP32 tensor streamed by TMA (128-row tiles, 32-float K blocks,
-// 128-byte swizzle); two converter warps split each landed A tile into a
-// round-to-nearest TF32 "hi" part (in place) and a TF32 "lo" remainder.  B is
-// small and arrives pre-split (hi and lo arrays).  Each K step issues three
-// MMAs, A_hi B_hi + A_lo B_hi + A_hi B_lo, into an FP32 accumulator in TMEM,
-// which carries about 21 significant bits of every product.  The accumulator
-// is double-buffered (2 x 256 TMEM columns) so the epilogue of one tile
-// overlaps the main loop of the next.
+// 128-byte swizzle); six converter warps turn each landed A tile into the MMA
+// operands; B is small and arrives pre-split in global memory.
 //
-// Sliced form (kSliced): the converters cut each A element, scaled by one
-// power of two per tensor (from its largest magnitude), into four
-// integer-valued BF16 slices (8 bits each, Ozaki-style), and B arrives as four
-// such slices.  The leading product A_0 B_0 is a sum of integers below 2^24
-// times one common scale, so its FP32 accumulation in TMEM is exact whatever
-// rounding the tensor core applies; the nine lower-order products (2^-8 and
-// smaller) go to a second accumulator.  This removes the systematic
-// round-toward-zero drift of long FP32 tensor-core accumulations, at 20 BF16
-// MMAs per 32-element K block instead of 12 TF32 ones.
+// Sliced form (kSliced, the default "bf16x4"): the converters cut each A
+// element, scaled by one power of two per tensor (from its largest magnitude),
+// into four integer-valued BF16 slices (8 bits each, Ozaki-style), and B
+// arrives as four such slices.  The leading product A_0 B_0 is a sum of
+// integers below 2^24 times one common scale, so its FP32 accumulation in TMEM
+// is exact whatever rounding the tensor core applies; the nine lower-order
+// products (2^-8 and smaller) go to a second accumulator.  This removes the
+// systematic round-toward-zero drift of long FP32 tensor-core accumulations,
+// at 20 BF16 MMAs per 32-element K block.
 //
-// Warp roles (384 threads): warp 0 TMA producer, warp 1 TMEM owner and MMA
-// issuer, warps 2-7 converters, warps 8-11 epilogue (TMEM lanes 0..127: a
-// warp reaches the lane quarter warp % 4).
+// TF32 form ("tf32x3"): the converters split A into a round-to-nearest TF32
+// "hi" part (in place) and a TF32 "lo" remainder, B arrives as hi and lo
+// arrays, and each K step issues three MMAs, A_hi B_hi + A_lo B_hi + A_hi B_lo,
+// into one FP32 accumulator (about 21 significant bits of every product).
+//
+// Accumulators are double-buffered in TMEM where they fit, so the epilogue of
+// one tile overlaps the main loop of the next.  Warp roles (384 threads):
+// warp 0 TMA producer, warp 1 TMEM owner and MMA issuer, warps 2-7
+// converters, warps 8-11 epilogue (TMEM lanes 0..127: a warp reaches the lane
+// quarter warp % 4).
 #pragma once
 
 #include "tc_ptx.cuh"
@@ -94,10 +96,6 @@ struct GemmParams {
   int *err;
   const int *a_amax;  // sliced form: FP32 bit pattern of max |A| (the A slice scale)
   int slice_lead;     // sliced form: leading-slice width L (slice_lead_for(K)); 0 means 7
-  int cluster2;       // sliced form, launched as CTA pairs whose tiles share the B column tile
-                      // (tile 2p and 2p+1): each CTA multicasts half of every B slice to both
-                      // (tmBhi then has a box of nout/2 rows x one slice), and a stage is free
-                      // once both CTAs' MMAs are done with it
   int col_il;         // B rows (output columns) ordered 2 l + v instead of v nb + l
   int out_il;         // EP_SWAP34 with col_il: interleaved complex FP32 output out[i][j][l][k]
   int acc3;           // sliced form: order-1 products in their own exact accumulator (nout <= 128,
@@ -146,13 +144,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   float2 *acc2 = reinterpret_cast<float2 *>(smem + (size_t)stages * stage_bytes + 256);  // (sum, error) pairs
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool pair = kSliced && p.cluster2;
-  const uint32_t crank = pair ? cluster_ctarank() : 0u;
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&conv[s], kConvThreads);
-      mbar_init(&empty[s], pair ? 2 : 1);
+      mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -163,7 +159,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   }
   if (warp == 1) tmem_alloc(tmem_slot, 2 * kAccCols);
   __syncthreads();
-  if (pair) cluster_sync();  // the partner's barriers exist before anything is multicast to them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const int N = p.nb;
@@ -206,27 +201,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             bk = kglob;
           }
           const int brow = (p.a_rows == AR_PI) ? (tile / p.pi_mtiles) * p.nout : 0;
-          if (pair) {
-            // this CTA's half of the rows of each slice, to both CTAs of the pair
-            const int half = p.nout / 2;
-#pragma unroll
-            for (int q = 0; q < kSlices; ++q)
-              tma_load_3d_mc(st + kSlicedBOff + q * b_bytes + crank * (b_bytes / 2), &tmBhi, &full[s], bk,
-                             brow + (int)crank * half, q, (uint16_t)0x3);
-          } else if (kSliced) {
+          if (kSliced) {
             tma_load_3d(st + kSlicedBOff, &tmBhi, &full[s], bk, brow, 0);  // all four slices
           } else {
             tma_load_3d(st + 2 * kABytes, &tmBhi, &full[s], bk, brow, 0);
             tma_load_3d(st + 2 * kABytes + b_bytes, &tmBlo, &full[s], bk, brow, 0);
           }
-          if (++s == stages) { s = 0; ph ^= 1u; }
-        }
-      }
-      if (pair) {
-        // the partner's last MMA commits arrive on this CTA's empty barriers: wait for the
-        // final use of every stage before the pair may leave
-        for (int i = 0; i < stages; ++i) {
-          mbar_wait(&empty[s], ph ^ 1u, p.err);
           if (++s == stages) { s = 0; ph ^= 1u; }
         }
       }
@@ -290,10 +270,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
               mma_tf32(d_tmem, ah, bl, idesc, 1u);
             }
           }
-          if (pair)
-            mma_commit_mc(&empty[s], (uint16_t)0x3);  // both producers write into this stage
-          else
-            mma_commit(&empty[s]);
+          mma_commit(&empty[s]);
           if (++s == stages) { s = 0; ph ^= 1u; }
           if (chunk_end) {
             mma_commit(&tfull[acc]);
@@ -566,9 +543,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     tc_fence_after();
     tmem_dealloc(tmem_base, 2 * kAccCols);
   }
-  // neither CTA of a pair leaves while the other may still multicast into it
-  // or arrive on its barriers
-  if (pair) cluster_sync();
 }
 
 }  // namespace tc

@@ -780,8 +780,7 @@ struct TcPath {
                 *w_s = nullptr, *bpi_s = nullptr;
   int *amax = nullptr;  // slots: see kAmax*
   int pi_lead = 7;      // leading-slice width of the polarisation GEMM (K = 2 nb kpad)
-  CUtensorMap mBh_s, mBnr_s, mBnc_s, mBnb_s, mBnt_s, mW_s, mBpi_s, mBpi_s_half;
-  bool pi_pair = false;  // polarisation GEMM launched as CTA pairs sharing B (TMA multicast)
+  CUtensorMap mBh_s, mBnr_s, mBnc_s, mBnb_s, mBnt_s, mW_s, mBpi_s;
   // tensor maps
   CUtensorMap mZin_y32, mZin_ys32, mCol_y32, mCol_ys32, mW32, mWh32, mBuf1Gather, mBuf2Lin, mBuf1Lin;
   CUtensorMap mBh_hi, mBh_lo, mBnr_hi, mBnr_lo, mBnc_hi, mBnc_lo, mBnb_hi, mBnb_lo, mW_hi, mW_lo;
@@ -826,25 +825,9 @@ void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, 
   int stages = 0;
   const size_t acc64 = gp.kb_chunks ? (size_t)gp.nb * (gp.n_valid + 1) * sizeof(float2) : 0;
   const size_t smem = gemm_smem(sliced, gp.nout, &stages, acc64);
-  int grid = std::max(1, std::min(gp.tiles, t->sms));
+  const int grid = std::max(1, std::min(gp.tiles, t->sms));
   L.before(tag);
-  if (sliced && gp.cluster2) {
-    // CTA pairs (cluster of 2): even grid, even tile count (the caller checks the latter)
-    grid = std::max(2, grid & ~1);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(kGemmThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = L.stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, tc_gemm_kernel<true>, A, A2 ? *A2 : A, Bh, Bl, gp, stages);
-  } else if (sliced) {
+  if (sliced) {
     tc_gemm_kernel<true><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
   } else {
     tc_gemm_kernel<false><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
@@ -947,8 +930,6 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
       return bail(G1G2_ECUDA);
     if (sliced) {
       t->pi_lead = slice_lead_order1(2LL * N * t->kpad);
-      // pairs need an even number of row tiles per column tile (both tiles of a pair share it)
-      t->pi_pair = (t->pi_mtiles % 2 == 0) && (t->pi_nout % 32 == 0);
       if ((rc = talloc(t, &t->bpi_s, (size_t)kSlices * brows * t->pi_ldb))) return bail(rc);
       if (cudaMemset(t->bpi_s, 0, (size_t)kSlices * brows * t->pi_ldb * sizeof(__nv_bfloat16)) != cudaSuccess)
         return bail(G1G2_ECUDA);
@@ -1091,9 +1072,7 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
                   (rc = map_bs(&t->mBnt_s, t->bnt_s, kt_r, t->nout2, t->nout2)) ||
                   (rc = map_bs(&t->mW_s, t->w_s, N3, nb, t->nout1)) ||
                   (big &&
-                   ((rc = map_bs(&t->mBpi_s, t->bpi_s, t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
-                    (rc = map_bs(&t->mBpi_s_half, t->bpi_s, t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout / 2,
-                                 1)))) ||
+                   (rc = map_bs(&t->mBpi_s, t->bpi_s, t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout))) ||
                   ((has_pp || has_ph) &&
                    ((rc = map_gather(&t->mLam, t->Gp32, nb, 32, 1, 4)) ||
                     (rc = map_bs(&t->mBnbr_s, t->bnbr_s, kt_r, t->nout2, t->nout2)) ||
@@ -1356,9 +1335,8 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     g.a_amax = g2_amax;
     g.slice_lead = t->pi_lead;
     g.acc3 = 1;
-    g.cluster2 = (sl && t->pi_pair) ? 1 : 0;
-    launch_gemm(t, L, "tc_gemm_pi", from_y ? t->mPi_y32 : t->mPi_ys32,
-                sl ? (g.cluster2 ? t->mBpi_s_half : t->mBpi_s) : t->mBpi_hi, t->mBpi_lo, g, sl);
+    launch_gemm(t, L, "tc_gemm_pi", from_y ? t->mPi_y32 : t->mPi_ys32, sl ? t->mBpi_s : t->mBpi_hi, t->mBpi_lo, g,
+                sl);
   }
   // Ladder terms (Sec. IV.D/E): H^dag as P1 - P2, each term two right multiplications of a
   // real interaction tensor Wt (x_4 S into the exchange-permuted layout, then x_4 S' again,
@@ -1401,8 +1379,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     g.a_amax = g2_amax;
     g.slice_lead = t->pi_lead;
     g.acc3 = 1;
-    g.cluster2 = t->pi_pair ? 1 : 0;
-    launch_gemm(t, L, tag, t->mLam, g.cluster2 ? t->mBpi_s_half : t->mBpi_s, t->mBpi_s, g, sl);
+    launch_gemm(t, L, tag, t->mLam, t->mBpi_s, t->mBpi_s, g, sl);
   };
   const float *g32 = from_y ? t->y32 : t->ys32;
   const int nt32 = (nb + 31) / 32;

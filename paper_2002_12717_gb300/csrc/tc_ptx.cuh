@@ -1,7 +1,8 @@
 // Inline-PTX helpers for the sm_103a tensor-core path: mbarriers with bounded
-// waits, TMA tiled loads, TMEM allocation, tcgen05.mma (kind::tf32) and
-// tcgen05.ld.  Every wait gives up after a wall-clock limit and reports it
-// through an error word instead of spinning forever.
+// waits, TMA tiled loads, TMEM allocation, tcgen05.mma (kind::f16 with BF16
+// operands, kind::tf32), tcgen05.ld, and the BF16 slicing of FP32 values.
+// Every wait gives up after a wall-clock limit and reports it through an error
+// word instead of spinning forever.
 #pragma once
 
 #include <cstdint>
@@ -80,25 +81,6 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, u
       "[%7];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
       : "memory");
-}
-// The same load delivered to every CTA of the cluster in cta_mask, at the same
-// shared-memory offsets, signalling each destination CTA's barrier at bar's offset.
-__device__ __forceinline__ void tma_load_3d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z,
-                                               uint16_t cta_mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "h"(cta_mask)
-      : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// every thread of every CTA of the cluster
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -180,14 +162,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-// arrive on the barrier at bar's offset in every CTA of cta_mask once the issued MMAs complete
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t cta_mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(cta_mask)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {

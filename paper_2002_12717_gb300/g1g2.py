@@ -95,16 +95,46 @@ def load():
     return lib
 
 
+def check_noalloc_args(h, w, n, g2, dn, current_device):
+    """Validate the tensors of g1_rhs_noalloc before anything is launched: contiguous
+    complex128 CUDA tensors on the current device, h, n, dn of shape (nb, nb) and w, g2
+    with nb^4 elements.  Returns nb; raises ValueError otherwise (a short
+    or mistyped buffer would make the kernels read past its end)."""
+    import torch
+    if getattr(h, "dim", lambda: 0)() != 2 or h.shape[0] != h.shape[1]:
+        raise ValueError("h must be an (nb, nb) tensor")
+    nb = int(h.shape[0])
+    for name, x, numel in (("h", h, nb * nb), ("w", w, nb ** 4), ("n", n, nb * nb), ("g2", g2, nb ** 4),
+                           ("dn", dn, nb * nb)):
+        if not getattr(x, "is_cuda", False):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if x.dtype != torch.complex128:
+            raise ValueError(f"{name} must be complex128, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if x.numel() != numel or (numel == nb * nb and tuple(x.shape) != (nb, nb)):
+            raise ValueError(f"{name} has shape {tuple(x.shape)}; nb = {nb} needs {numel} elements"
+                             + (" as (nb, nb)" if numel == nb * nb else ""))
+        if x.device.index != current_device:
+            raise ValueError(f"{name} is on cuda:{x.device.index}, the current device is cuda:{current_device}")
+    return nb
+
+
 def g1_rhs_noalloc(h, w, n, g2, dn, restricted=False, stream=None):
     """G1 right-hand side dn = -i[hHF, n] - (I + I^dag) through g1g2_g1_rhs_noalloc, which
-    allocates no device memory; all arguments are contiguous complex128 CUDA tensors
-    (w in the nb^4 complex ABI layout), dn is written."""
-    for x in (h, w, n, g2, dn):
-        if not (x.is_cuda and x.is_contiguous()):
-            raise ValueError("device tensors must be contiguous CUDA tensors")
-    _check(load().g1g2_g1_rhs_noalloc(int(h.shape[0]), 1 if restricted else 0, h.data_ptr(), w.data_ptr(),
-                                       n.data_ptr(), g2.data_ptr(), dn.data_ptr(),
-                                       None if stream is None else int(stream)))
+    allocates no device memory; all arguments are contiguous complex128 CUDA tensors on
+    the current device (w and g2 with nb^4 elements, the ABI layout), dn is written.
+    stream: a torch.cuda.Stream, a raw cudaStream_t handle (int), or None (default stream)."""
+    import torch
+    nb = check_noalloc_args(h, w, n, g2, dn, torch.cuda.current_device())
+    if stream is None:
+        handle = None
+    elif isinstance(stream, torch.cuda.Stream):
+        handle = stream.cuda_stream
+    else:
+        handle = int(stream)
+    _check(load().g1g2_g1_rhs_noalloc(nb, 1 if restricted else 0, h.data_ptr(), w.data_ptr(), n.data_ptr(),
+                                       g2.data_ptr(), dn.data_ptr(), handle))
 
 
 def fp64_rate():
