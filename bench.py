@@ -45,13 +45,9 @@ FP64_PEAK_NOTE = "profiles/fp64_dfma_peak.md"
 # nominal dense tensor ratio TF32 / BF16 (1.1 / 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
 # DRAM bytes (read + write) per launch of the dominant kernel, keyed by (kernel tag,
-# workload), missing entries report null; from one ncu capture of
-# the current kernel: ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum
-# --clock-control none -k regex:tc_gemm_kernel -s 116 -c 1 on
-# `bench.py --workloads general-gw-nb64 --steps 1 --warmup 3` (the 117th GEMM launch
-# is the polarisation pass of the 13th right-hand side); bf16x4 form
-# (profiles/tc_gemm_pi_bf16x4_gw64.md).
-TRAFFIC = {("tc_gemm_pi", "general-gw-nb64"): 2497462784 + 132801536}
+# workload), from one ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum, profiles/); missing entries report null.
+TRAFFIC = {}
 
 
 def load_peaks():
@@ -78,8 +74,10 @@ def algorithmic_flops(nb, se, stage_launches=None):
     return 8.0 * per_rhs * 4
 
 
-# tensor products issued per real multiply-add: TF32 hi/lo (3) or BF16 slices (10)
+# tensor products issued per real multiply-add: TF32 hi/lo (3) or BF16 slices (10 in the
+# nb^5 passes, 6 in the nb^2 x nb^2 x nb^2 products of tc_pi_gemm_kernel)
 SPLIT_PRODUCTS = {"tf32x3": 3, "bf16x4": 10}
+SPLIT_PRODUCTS_PI = {"tf32x3": 3, "bf16x4": 6}
 
 
 def kernel_work(tag, nb, se, precision="tf32x3"):
@@ -91,8 +89,9 @@ def kernel_work(tag, nb, se, precision="tf32x3"):
     ladder products nb^6 complex MACs, a complex nb^5 pass nb^5, a pass with the
     real w as A (source pass 1, quasi-Hamiltonian, collision) nb^5 real-by-complex
     MACs.  Issued work counts the split-precision products the kernel runs on the
-    realified problem (three TF32 products, or ten BF16 slice products, per real
-    multiply-add, 2 flops each): issued / algorithmic is the cost of the emulated
+    realified problem (three TF32 products, or ten BF16 slice products in the nb^5
+    passes and six in the nb^2 x nb^2 x nb^2 products, per real multiply-add, 2 flops
+    each): issued / algorithmic is the cost of the emulated
     FP32-class accuracy.  The assembly counts its algorithmic HBM bytes (FP32
     intermediates, FP64 state, FP32 RK4 accumulator and stage input), averaged over
     the four RK4 stages.
@@ -100,7 +99,7 @@ def kernel_work(tag, nb, se, precision="tf32x3"):
     n = float(nb)
     split = SPLIT_PRODUCTS.get(precision, 3) * 2
     if tag in ("tc_gemm_pi", "tc_gemm_ladder"):
-        return "tensor", 8 * n ** 6, split * n * n * (2 * n * n) * (2 * n * n)
+        return "tensor", 8 * n ** 6, SPLIT_PRODUCTS_PI.get(precision, 3) * 2 * n * n * (2 * n * n) * (2 * n * n)
     if tag in ("tc_gemm_commutator", "tc_gemm_psi2", "tc_gemm_psi3", "tc_gemm_psi4"):
         return "tensor", 8 * n ** 5, split * n ** 3 * (2 * n) * (2 * n)
     if tag in ("tc_gemm_psi1", "tc_gemm_hcorr"):

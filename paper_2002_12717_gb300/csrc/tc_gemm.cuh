@@ -55,7 +55,7 @@ enum ARows : int {
   AR_LINEAR = 0,   // A viewed as [plane][row][k]; tile = 128 consecutive rows
   AR_GATHER4 = 1,  // A = T[plane][a][b][c][k]; tile = rows (a: 4, b: 32) at fixed c
   AR_SPLITK = 2,   // A = G[plane][j][c]; tile = (plane, K split), rows j
-  AR_PI = 3,       // A = G[plane][i][p][k][q]; tile rows (i: 4, k: 32), K blocks over (plane, p, q)
+  AR_PI = 3,       // TF32 form: A = G[plane][i][p][k][q]; tile rows (i: 4, k: 32), K blocks over (plane, p, q)
 };
 
 // Output index maps.  In every map the fastest-varying output index is the
@@ -98,9 +98,6 @@ struct GemmParams {
   int slice_lead;     // sliced form: leading-slice width L (slice_lead_for(K)); 0 means 7
   int col_il;         // B rows (output columns) ordered 2 l + v instead of v nb + l
   int out_il;         // EP_SWAP34 with col_il: interleaved complex FP32 output out[i][j][l][k]
-  int acc3;           // sliced form: order-1 products in their own exact accumulator (nout <= 128,
-                      // L = slice_lead_order1(K)); for long K, where the lower-order accumulator
-                      // would collect a visible truncation bias
   int *out_amax;      // sliced form, optional: atomic max of |stored outputs| (FP32 bits)
 };
 
@@ -128,11 +125,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   const uint32_t stage_bytes = stage_bytes_for(kSliced, p.nout);
   // accumulator buffers: TF32 form two (double-buffered); sliced form a pair
   // (exact leading product, lower-order products) per buffer, two buffers when they fit
-  // acc3: three accumulators D0 (order 0), D1 (order 1), D2 (orders 2-3) at columns 0, 128, 256
-  const bool acc3 = kSliced && p.acc3;
-  const int nbuf = (!kSliced || (!acc3 && p.nout <= 128)) ? 2 : 1;
-  const uint32_t dlo_off = (nbuf == 2) ? 128u : 256u;
-  const uint32_t d1_off = acc3 ? 128u : dlo_off, d2_off = acc3 ? 256u : dlo_off;
+  const int nbuf = (!kSliced || p.nout <= 128) ? 2 : 1;
+  const uint32_t d1_off = (nbuf == 2) ? 128u : 256u;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stage_bytes);
   uint64_t *full = bars;
   uint64_t *conv = bars + stages;
@@ -251,13 +245,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
               mma_bf16(d_tmem, ad[0], bd[0], idesc, acc_in);               // exact: integers < 2^24
               mma_bf16(d_tmem + d1_off, ad[0], bd[1], idesc, acc_in);      // order 1 ...
               mma_bf16(d_tmem + d1_off, ad[1], bd[0], idesc, 1u);
-              mma_bf16(d_tmem + d2_off, ad[0], bd[2], idesc, acc3 ? acc_in : 1u);  // order 2
-              mma_bf16(d_tmem + d2_off, ad[1], bd[1], idesc, 1u);
-              mma_bf16(d_tmem + d2_off, ad[2], bd[0], idesc, 1u);
-              mma_bf16(d_tmem + d2_off, ad[0], bd[3], idesc, 1u);          // order 3
-              mma_bf16(d_tmem + d2_off, ad[1], bd[2], idesc, 1u);
-              mma_bf16(d_tmem + d2_off, ad[2], bd[1], idesc, 1u);
-              mma_bf16(d_tmem + d2_off, ad[3], bd[0], idesc, 1u);
+              mma_bf16(d_tmem + d1_off, ad[0], bd[2], idesc, 1u);          // order 2
+              mma_bf16(d_tmem + d1_off, ad[1], bd[1], idesc, 1u);
+              mma_bf16(d_tmem + d1_off, ad[2], bd[0], idesc, 1u);
+              mma_bf16(d_tmem + d1_off, ad[0], bd[3], idesc, 1u);          // order 3
+              mma_bf16(d_tmem + d1_off, ad[1], bd[2], idesc, 1u);
+              mma_bf16(d_tmem + d1_off, ad[2], bd[1], idesc, 1u);
+              mma_bf16(d_tmem + d1_off, ad[3], bd[0], idesc, 1u);
             }
           } else {
             const uint32_t sal = sa + kABytes, sbh = sa + 2 * kABytes, sbl = sbh + b_bytes;
@@ -375,12 +369,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             if (kSliced) {
               float vl[32];
               tmem_ld32(tbase + d1_off + (uint32_t)c0, vl);
-              if (acc3) {
-                float v2[32];
-                tmem_ld32(tbase + d2_off + (uint32_t)c0, v2);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) vl[j] += v2[j];
-              }
 #pragma unroll
               for (int j = 0; j < 32; ++j) v[j] += vl[j];
             }
@@ -467,12 +455,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         if (kSliced) {
           float vl[32];
           tmem_ld32(tbase + d1_off + (uint32_t)c0, vl);
-          if (acc3) {
-            float v2[32];
-            tmem_ld32(tbase + d2_off + (uint32_t)c0, v2);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) vl[j] += v2[j];
-          }
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += vl[j];
         }

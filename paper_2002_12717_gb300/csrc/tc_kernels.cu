@@ -18,20 +18,25 @@
 //       A^dag = T2~ x_4 nbar                                          (4 passes)
 //   collision integral (Eq. eom_gone-I): I_ij = -i sum_c w_ic conj(G2_jc) with
 //     c = (k,l,p), both operands row-contiguous; split-K over c.
+//   polarisation and ladder products (Eqs. gwpi, lambdapp, lambdaph): one
+//     nb^2 x nb^2 x nb^2 GEMM each, A = G2 read through a permutation of its
+//     indices, B the realified quasi-Hamiltonian (tc_pi_gemm.cuh).
 //   assembly: P = U - (Q + exch Q)/2 with Q = A^dag and dG2 = -i (P^dag - P), read as
-//     the orbit {X, exch X, trans X, exch trans X} of 8^4 blocks so every
+//     the orbit {X, exch X, trans X, exch trans X} of 4^4 blocks so every
 //     input block is read once; the RK4 stage update is fused.
 //
-// Two operand forms: TF32 hi/lo (three TF32 products) and four BF16 slices
-// with an exact leading product (tc_gemm.cuh).  The sliced form needs the
-// largest magnitude of every A tensor before it is read; each producer (the
+// Two operand forms: TF32 hi/lo (three TF32 products) and BF16 slices with an
+// exact leading product.  In the nb^5 passes (tc_gemm.cuh) the converters cut
+// four slices with one exponent per tensor; the sliced form needs the largest
+// magnitude of every A tensor before it is read, and each producer (the
 // assembly, the FP32 copy of the state, the source-term passes) folds it into
-// a slot of amax with an atomic maximum.  The polarisation GEMM accumulates
-// K = 2 nb^2 products in TMEM; there the order-1 products get an exact
-// accumulator of their own and the leading slice is narrowed
-// (slice_lead_order1) so that both exact sums stay below 2^24.
+// a slot of amax with an atomic maximum.  The nb^2 x nb^2 x nb^2 products take
+// both operands as three slices cut beforehand by memory-bound passes, with
+// one exponent per row of A and per column of B (a_rowmax/a_slice3,
+// *_colmax/realify_*_slice3 below).
 #include "tc_path.h"
 #include "tc_gemm.cuh"
+#include "tc_pi_gemm.cuh"
 
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -50,7 +55,6 @@ namespace {
 
 constexpr int BSZ_LOG = 2;
 constexpr int BSZ = 1 << BSZ_LOG;            // assembly block edge; divides nb (nb % 4 == 0 here)
-constexpr int kPiNoutSliced = 128;          // polarisation N tile of the sliced form (3 accumulators in TMEM)
 constexpr int BEL = BSZ * BSZ * BSZ * BSZ;  // elements per block
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -276,19 +280,18 @@ __global__ void realify_pi_kernel(int nb, int kpad, const float *__restrict__ Y1
   }
 }
 
-// max over (q, j, p, l) of the larger component of hcorr_qjpl = Y1_qjpl - Y2_plqj, folded
-// into *amax (FP32 bits): the exponent of the sliced B operand of the polarisation GEMM.
-// The bound max|Y1| + max|Y2| can sit several bits above max|hcorr|, and every bit lost
-// there moves the mass of the products into the lower slice orders, whose FP32 sum the
-// tensor cores accumulate with truncation.  Same tiling as realify_pi_sliced_kernel.
-__global__ void hcorr_amax_kernel(int nb, int kpad, const float *__restrict__ Y1s, const float *__restrict__ Y2s,
-                                  long long P, int *amax) {
+// Per-column maxima of the polarisation GEMM's B operand: colmax[j nb + l] = max over
+// (q, p) of the larger component of hcorr_qjpl = Y1_qjpl - Y2_plqj (FP32 bits, atomic max),
+// so that every column (j, l, v) of B gets its own slice exponent.  One CTA per (j, l)
+// and 32 x 32 tile of (p, q), read along p for Y1 and along q for Y2.
+__global__ void hcorr_colmax_kernel(int nb, const float *__restrict__ Y1s, const float *__restrict__ Y2s,
+                                    long long P, int *colmax) {
   __shared__ float2 t1[32][33];
   const long long N = nb;
   const long long jl = blockIdx.y;
   const long long j = jl / N, l = jl % N;
-  const int ntq = kpad / 32;
-  const int p0 = (blockIdx.x / ntq) * 32, q0 = (blockIdx.x % ntq) * 32;
+  const int nt = (nb + 31) / 32;
+  const int p0 = (blockIdx.x / nt) * 32, q0 = (blockIdx.x % nt) * 32;
   const int tx = threadIdx.x, ty0 = threadIdx.y;
   for (int ty = ty0; ty < 32; ty += blockDim.y) {
     const int q = q0 + ty, pp = p0 + tx;
@@ -309,30 +312,25 @@ __global__ void hcorr_amax_kernel(int nb, int kpad, const float *__restrict__ Y1
       mx = fmaxf(mx, fmaxf(fabsf(a.x - Y2s[g]), fabsf(a.y - Y2s[P + g])));
     }
   }
-  block_amax(mx, amax);
+  block_amax(mx, colmax + jl);
 }
 
-// Sliced form of realify_pi_kernel: the same B values, as four BF16 slices
-// [q][row][ldb] with leading width L and the exponent of amax[0] + amax[1] (FP32 bit
-// patterns: the exact max|hcorr| and a zero slot).
-__global__ void realify_pi_sliced_kernel(int nb, int kpad, const float *__restrict__ Y1s,
-                                         const float *__restrict__ Y2s, long long P, const int *amax, int L,
-                                         __nv_bfloat16 *out, long long ldb, long long slice_stride) {
+// B operand of the polarisation GEMM (tc_pi_gemm_kernel): rows (j, l, v) interleaved as
+// 2 (j nb + l) + v, K = (u, p, q) as (u nb + p) nb + q, value R(hcorr_qjpl)[u][v] (the
+// real 2 x 2 block [[Re, Im], [-Im, Re]] of the complex product), as three BF16 slices
+// [slice][row][K] with the exponent of the column's maximum colmax[j nb + l].  Same
+// tiling as hcorr_colmax_kernel.
+__global__ void realify_pi_slice3_kernel(int nb, const float *__restrict__ Y1s, const float *__restrict__ Y2s,
+                                         long long P, const int *__restrict__ colmax, __nv_bfloat16 *out,
+                                         long long slice_stride) {
   __shared__ float2 t1[32][33];
-  const long long N = nb;
+  const long long N = nb, K = 2 * N * N;
   const long long jl = blockIdx.y;
   const long long j = jl / N, l = jl % N;
-  const int ntq = kpad / 32;
-  const int p0 = (blockIdx.x / ntq) * 32, q0 = (blockIdx.x % ntq) * 32;
+  const int nt = (nb + 31) / 32;
+  const int p0 = (blockIdx.x / nt) * 32, q0 = (blockIdx.x % nt) * 32;
   const int tx = threadIdx.x, ty0 = threadIdx.y;
-  int E = 0;
-  {
-    const double bound = (double)__int_as_float(amax[0]) + (double)__int_as_float(amax[1]);
-    if (bound > 0.0) frexp(bound, &E);
-  }
-  float cut[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) cut[q] = ldexpf(1.5f, 23 + E - L - 8 * q);
+  const int E = slice_exponent(colmax[jl]);
   for (int ty = ty0; ty < 32; ty += blockDim.y) {
     const int q = q0 + ty, pp = p0 + tx;
     float2 v = make_float2(0.f, 0.f);
@@ -345,53 +343,42 @@ __global__ void realify_pi_sliced_kernel(int nb, int kpad, const float *__restri
   __syncthreads();
   for (int ty = ty0; ty < 32; ty += blockDim.y) {
     const int pp = p0 + ty, q = q0 + tx;
-    if (pp >= nb) continue;
-    float2 h = make_float2(0.f, 0.f);
-    if (q < nb) {
-      const long long g = ((pp * N + l) * N + j) * N + q;   // Y2_{p l q j} at [p][l][j][q]
-      const float2 a = t1[tx][ty];
-      h = make_float2(a.x - Y2s[g], a.y - Y2s[P + g]);
-    }
+    if (pp >= nb || q >= nb) continue;
+    const long long g = ((pp * N + l) * N + j) * N + q;     // Y2_{p l q j} at [p][l][j][q]
+    const float2 a = t1[tx][ty];
+    const float2 h = make_float2(a.x - Y2s[g], a.y - Y2s[P + g]);
     for (int u = 0; u < 2; ++u)
       for (int v = 0; v < 2; ++v) {
         const float x = (u == 0) ? (v ? h.y : h.x) : (v ? h.x : -h.y);
         const long long row = 2 * jl + v;
-        const long long col = ((long long)u * N + pp) * kpad + q;
-        float sl[4];
-        slice4(x, sl, cut);
+        const long long col = ((long long)u * N + pp) * N + q;
+        float sl[3];
+        slice3_lead8(x, E, sl);
 #pragma unroll
-        for (int z = 0; z < 4; ++z) out[z * slice_stride + row * ldb + col] = __float2bfloat16_rn(sl[z]);
+        for (int z = 0; z < 3; ++z) out[z * slice_stride + row * K + col] = __float2bfloat16_rn(sl[z]);
       }
   }
 }
 
-// B operand of the particle-particle ladder product Lambda^dag = G2 H^dag (Eq. lambdapp;
-// G2 is Hermitian as an nb^2 x nb^2 matrix): the polarisation GEMM's layout, rows (c,d,v)
-// interleaved as 2 (c nb + d) + v, K = (u, p, q) as (u nb + p) kpad + q, value R(X)[u][v]
-// with X = H^dag_pqcd = conj(hcorr_cdpq) = P1_pqcd - P2_pqcd, both stored as [q][p][c][d]
-// (the two right-multiplication passes w x3 S x4 S with S = nbar and S = n).  Four BF16
-// slices with the exponent of amax[0] + amax[1] (the exact max|P1 - P2| and a zero
-// slot).  One CTA per (p, c) and a 32 x 32 tile
-// of (q, d): read along d, transposed in shared memory, written along q; q in
-// [nb, kpad) is written as zero padding.
-__global__ void realify_lam_sliced_kernel(int nb, int kpad, const float *__restrict__ P1s,
-                                          const float *__restrict__ P2s, long long P, const int *amax, int L,
-                                          __nv_bfloat16 *out, long long ldb, long long slice_stride) {
+// B operand of the ladder products Lambda^dag = G2 H^dag (Eqs. lambdapp, lambdaph; G2 is
+// Hermitian as an nb^2 x nb^2 matrix) for tc_pi_gemm_kernel: rows (c, d, v) interleaved as
+// 2 (c nb + d) + v, K = (u, p, q) as (u nb + p) nb + q, value R(X)[u][v] with
+// X = H^dag_pqcd = conj(hcorr_cdpq) = P1_pqcd - P2_pqcd, both stored as [q][p][c][d] (the
+// two right-multiplication passes w x3 S x4 S with S = nbar and S = n), as three BF16
+// slices with the exponent of the column's maximum colmax[c nb + d].  One CTA per (p, c)
+// and a 32 x 32 tile of (q, d): read along d, transposed in shared memory, written along q.
+__global__ void realify_lam_slice3_kernel(int nb, const float *__restrict__ P1s, const float *__restrict__ P2s,
+                                          long long P, const int *__restrict__ colmax, __nv_bfloat16 *out,
+                                          long long slice_stride) {
   __shared__ float2 t1[32][33];
-  const long long N = nb;
+  __shared__ int se[32];
+  const long long N = nb, K = 2 * N * N;
   const long long pc = blockIdx.y;
   const long long p = pc / N, c = pc % N;
   const int ntd = (nb + 31) / 32;
   const int q0 = (blockIdx.x / ntd) * 32, d0 = (blockIdx.x % ntd) * 32;
   const int tx = threadIdx.x, ty0 = threadIdx.y;
-  int E = 0;
-  {
-    const double bound = (double)__int_as_float(amax[0]) + (double)__int_as_float(amax[1]);
-    if (bound > 0.0) frexp(bound, &E);
-  }
-  float cut[4];
-#pragma unroll
-  for (int z = 0; z < 4; ++z) cut[z] = ldexpf(1.5f, 23 + E - L - 8 * z);
+  if (ty0 == 0) se[tx] = (d0 + tx < nb) ? slice_exponent(colmax[c * N + d0 + tx]) : 0;
   for (int ty = ty0; ty < 32; ty += blockDim.y) {
     const int q = q0 + ty, d = d0 + tx;
     float2 v = make_float2(0.f, 0.f);
@@ -404,74 +391,144 @@ __global__ void realify_lam_sliced_kernel(int nb, int kpad, const float *__restr
   __syncthreads();
   for (int ty = ty0; ty < 32; ty += blockDim.y) {
     const int d = d0 + ty, q = q0 + tx;
-    if (d >= nb) continue;
+    if (d >= nb || q >= nb) continue;
     const float2 h = t1[tx][ty];
+    const int E = se[ty];
     for (int u = 0; u < 2; ++u)
       for (int v = 0; v < 2; ++v) {
         const float x = (u == 0) ? (v ? h.y : h.x) : (v ? h.x : -h.y);
         const long long row = 2 * (c * N + d) + v;
-        const long long col = ((long long)u * N + p) * kpad + q;
-        float sl[4];
-        slice4(x, sl, cut);
+        const long long col = ((long long)u * N + p) * N + q;
+        float sl[3];
+        slice3_lead8(x, E, sl);
 #pragma unroll
-        for (int z = 0; z < 4; ++z) out[z * slice_stride + row * ldb + col] = __float2bfloat16_rn(sl[z]);
+        for (int z = 0; z < 3; ++z) out[z * slice_stride + row * K + col] = __float2bfloat16_rn(sl[z]);
       }
   }
 }
 
-// max over all elements of the larger component of P1 - P2 ([q][p][c][d] layout), folded
-// into *amax: the exponent of the ladder product's sliced B operand (the exact maximum,
-// for the reason given at hcorr_amax_kernel).  Same tiling as realify_lam_sliced_kernel.
-__global__ void ladder_amax_kernel(int nb, int kpad, const float *__restrict__ P1s, const float *__restrict__ P2s,
-                                   long long P, int *amax) {
+// Per-column maxima of the ladder products' B operand: colmax[c nb + d] = max over (p, q)
+// of the larger component of P1_pqcd - P2_pqcd ([q][p][c][d] layout), atomic max of FP32
+// bits.  One CTA per (p, c) and 32 x 32 tile of (q, d).
+__global__ void ladder_colmax_kernel(int nb, const float *__restrict__ P1s, const float *__restrict__ P2s,
+                                     long long P, int *colmax) {
+  __shared__ float red[8][33];
   const long long N = nb;
   const long long pc = blockIdx.y;
   const long long p = pc / N, c = pc % N;
   const int ntd = (nb + 31) / 32;
   const int q0 = (blockIdx.x / ntd) * 32, d0 = (blockIdx.x % ntd) * 32;
   float mx = 0.f;
+  const int d = d0 + threadIdx.x;
   for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
-    const int q = q0 + ty, d = d0 + threadIdx.x;
+    const int q = q0 + ty;
     if (q < nb && d < nb) {
       const long long g = ((q * N + p) * N + c) * N + d;
       mx = fmaxf(mx, fmaxf(fabsf(P1s[g] - P2s[g]), fabsf(P1s[P + g] - P2s[P + g])));
     }
   }
-  block_amax(mx, amax);
-}
-
-// Gp[u][i][p][j][q] = G[u][i][j][p][q] (planar FP32): G2 seen by the polarisation GEMM's
-// row gather as rows (i, j) and K (p, q), the layout of the ladder product.
-__global__ void swap12_planar_kernel(int nb, const float *__restrict__ G, float *__restrict__ Gp, long long total) {
-  const long long N = nb;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long q = e % N, pp = (e / N) % N, j = (e / (N * N)) % N, ui = e / (N * N * N);
-    Gp[((ui * N + pp) * N + j) * N + q] = G[e];
-  }
-}
-
-// Gq[u][i][p][l][q] = G[u][i][p][q][l] (planar FP32): G2 with its last two indices exchanged,
-// seen by the polarisation GEMM's row gather as rows (i, l) and K (p, q), the layout of the
-// particle-hole ladder product.  One CTA per (u, i, p) and 32 x 32 tile of (q, l), all in
-// blockIdx.x (2 nb^2 nt^2 blocks).
-__global__ void swap34_planar_kernel(int nb, const float *__restrict__ G, float *__restrict__ Gq) {
-  __shared__ float t1[32][33];
-  const long long N = nb;
-  const int nt = (nb + 31) / 32;
-  const long long uip = (long long)blockIdx.x / (nt * nt);   // (u nb + i) nb + p
-  const int tile = (int)((long long)blockIdx.x % (nt * nt));
-  const int q0 = (tile / nt) * 32, l0 = (tile % nt) * 32;
-  const int tx = threadIdx.x, ty0 = threadIdx.y;
-  const long long base = uip * N * N;
-  for (int ty = ty0; ty < 32; ty += blockDim.y) {
-    const int q = q0 + ty, l = l0 + tx;
-    if (q < nb && l < nb) t1[ty][tx] = G[base + q * N + l];
-  }
+  red[threadIdx.y][threadIdx.x] = mx;
   __syncthreads();
-  for (int ty = ty0; ty < 32; ty += blockDim.y) {
-    const int l = l0 + ty, q = q0 + tx;
-    if (l < nb && q < nb) Gq[base + l * N + q] = t1[tx][ty];
+  if (threadIdx.y == 0 && d < nb) {
+    for (int y = 1; y < (int)blockDim.y; ++y) mx = fmaxf(mx, red[y][threadIdx.x]);
+    atomicMax(colmax + c * N + d, __float_as_int(mx));
+  }
+}
+
+// The A operand of the nb^2 x nb^2 x nb^2 products read from the planar FP32 state G
+// (plane stride P): row m = (a, b) = a nb + b, K = (u, p, q) as (u nb + p) nb + q, value
+// G[u P + a sA + b sB + p sP + q sQ].  The polarisation reads G_ipkq (rows (i, k)), the
+// particle-particle ladder G_ijpq (rows (i, j)), the particle-hole ladder G_ipql (rows (i, l)).
+struct AOperand {
+  long long sA, sB, sP, sQ;
+};
+
+// rowmax[a nb + b] = max over (u, p, q) of |G element| (FP32 bits, atomic max).  One CTA
+// (32 x 8 threads) per (a, 32-row block of b) and (u, 8 values of p); the fast thread index
+// runs along whichever of b and q is contiguous in memory.
+__global__ void a_rowmax_kernel(int nb, const float *__restrict__ G, long long P, AOperand m, int *rowmax) {
+  __shared__ float red[8][33];
+  const long long N = nb;
+  const int nbt = (nb + 31) / 32;
+  const long long a = blockIdx.x / nbt;
+  const int b0 = (blockIdx.x % nbt) * 32;
+  const int npb = (nb + 7) / 8;
+  const int u = blockIdx.y / npb, p0 = (blockIdx.y % npb) * 8;
+  const bool b_fast = m.sB == 1;
+  const float *base = G + u * P + a * m.sA;
+  float mx = 0.f;  // b_fast: row b0 + x; else per-thread over its rows, reduced below
+  float rmx[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int pp = p0; pp < min(p0 + 8, nb); ++pp)
+    for (int q0 = 0; q0 < nb; q0 += 32) {
+      if (b_fast) {
+        const int b = b0 + threadIdx.x;
+        for (int ty = threadIdx.y; ty < 32; ty += 8) {
+          const int q = q0 + ty;
+          if (b < nb && q < nb) mx = fmaxf(mx, fabsf(base[b * m.sB + pp * m.sP + q * m.sQ]));
+        }
+      } else {
+        const int q = q0 + threadIdx.x;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int b = b0 + threadIdx.y + 8 * i;
+          if (b < nb && q < nb) rmx[i] = fmaxf(rmx[i], fabsf(base[b * m.sB + pp * m.sP + q * m.sQ]));
+        }
+      }
+    }
+  if (b_fast) {
+    red[threadIdx.y][threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.y == 0 && b0 + (int)threadIdx.x < nb) {
+      for (int y = 1; y < 8; ++y) mx = fmaxf(mx, red[y][threadIdx.x]);
+      atomicMax(rowmax + a * N + b0 + threadIdx.x, __float_as_int(mx));
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float v = rmx[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      const int b = b0 + threadIdx.y + 8 * i;
+      if (threadIdx.x == 0 && b < nb) atomicMax(rowmax + a * N + b, __float_as_int(v));
+    }
+  }
+}
+
+// Three BF16 slices [slice][row][K] of the A operand (see AOperand) with the exponent of
+// each row's maximum rowmax[row] and a 9-bit leading slice (slice3_lead8).  One CTA
+// (32 x 8 threads) per (a, 32-row block of b) and (u, p): a 32 x 32 tile of (b, q) is read
+// along the contiguous index, kept in shared memory and written along q.
+__global__ void a_slice3_kernel(int nb, const float *__restrict__ G, long long P, AOperand m,
+                                const int *__restrict__ rowmax, __nv_bfloat16 *out, long long slice_stride) {
+  __shared__ float t[32][33];
+  __shared__ int se[32];
+  const long long N = nb, K = 2 * N * N;
+  const int nbt = (nb + 31) / 32;
+  const long long a = blockIdx.x / nbt;
+  const int b0 = (blockIdx.x % nbt) * 32;
+  const int u = blockIdx.y / nb, pp = blockIdx.y % nb;
+  const bool b_fast = m.sB == 1;
+  const float *base = G + u * P + a * m.sA + pp * m.sP;
+  if (threadIdx.y == 0) se[threadIdx.x] = (b0 + (int)threadIdx.x < nb) ? slice_exponent(rowmax[a * N + b0 + threadIdx.x]) : 0;
+  for (int q0 = 0; q0 < nb; q0 += 32) {
+    __syncthreads();
+    for (int ty = threadIdx.y; ty < 32; ty += 8) {
+      // t[b][q]
+      const int b = b0 + (b_fast ? (int)threadIdx.x : ty), q = q0 + (b_fast ? ty : (int)threadIdx.x);
+      const float x = (b < nb && q < nb) ? base[b * m.sB + q * m.sQ] : 0.f;
+      if (b_fast) t[threadIdx.x][ty] = x;
+      else t[ty][threadIdx.x] = x;
+    }
+    __syncthreads();
+    for (int ty = threadIdx.y; ty < 32; ty += 8) {
+      const int b = b0 + ty, q = q0 + threadIdx.x;
+      if (b >= nb || q >= nb) continue;
+      float sl[3];
+      slice3_lead8(t[ty][threadIdx.x], se[ty], sl);
+      const long long o = (a * N + b) * K + ((long long)u * N + pp) * N + q;
+#pragma unroll
+      for (int z = 0; z < 3; ++z) out[z * slice_stride + o] = __float2bfloat16_rn(sl[z]);
+    }
   }
 }
 
@@ -728,9 +785,10 @@ int map_b(CUtensorMap *m, const float *base, int kt, int rows, int box_rows) {
   cuuint32_t box[3] = {(cuuint32_t)kBlockK, (cuuint32_t)box_rows, 1};
   return encode_map(m, base, 3, dims, str, box);
 }
-// B as four BF16 slices [q][rows][kt]; one box carries all four (box_slices = 4) or one
-int map_bs(CUtensorMap *m, const __nv_bfloat16 *base, long long kt, int rows, int box_rows, int box_slices = kSlices) {
-  cuuint64_t dims[3] = {(cuuint64_t)kt, (cuuint64_t)rows, (cuuint64_t)kSlices};
+// B as BF16 slices [q][rows][kt] (four, or nslices); one box carries all of them
+int map_bs(CUtensorMap *m, const __nv_bfloat16 *base, long long kt, int rows, int box_rows, int box_slices = kSlices,
+           int nslices = kSlices) {
+  cuuint64_t dims[3] = {(cuuint64_t)kt, (cuuint64_t)rows, (cuuint64_t)nslices};
   cuuint64_t str[2] = {(cuuint64_t)kt * 2, (cuuint64_t)kt * 2 * rows};
   cuuint32_t box[3] = {(cuuint32_t)kBlockK, (cuuint32_t)box_rows, (cuuint32_t)box_slices};
   return encode_map(m, base, 3, dims, str, box, true);
@@ -758,9 +816,7 @@ struct TcPath {
   // GW: Y1 = w x_4 n, Y2 = w x_4 n^T, polarisation Pi, its B operand
   float *Y1 = nullptr, *Y2 = nullptr, *Pi = nullptr, *bpi_hi = nullptr, *bpi_lo = nullptr;
   float *bnt_hi = nullptr, *bnt_lo = nullptr;   // n^T, real A
-  // particle-particle T matrix: Y1/Y2 hold the two terms of H^dag, Pi the ladder product,
-  // bpi_s its B operand; Gp32 = G2 with its middle indices exchanged
-  float *Gp32 = nullptr;
+  // particle-particle T matrix: Y1/Y2 hold the two terms of H^dag, Pi the ladder product
   __nv_bfloat16 *bnbr_s = nullptr, *bnbc_s = nullptr;  // nbar in the real-A and complex-A forms
   // particle-hole T matrix: Wp32[p][q][r][s] = w_rpqs, nbar^T in the real-A form; Lam: the
   // ladder products' output when the polarisation output Pi must survive (DSL)
@@ -777,15 +833,19 @@ struct TcPath {
   // sliced form: BF16 slices [4][rows][kt] of the B operands and of w; A maxima
   bool sliced = false;
   __nv_bfloat16 *bh_s = nullptr, *bnr_s = nullptr, *bnc_s = nullptr, *bnb_s = nullptr, *bnt_s = nullptr,
-                *w_s = nullptr, *bpi_s = nullptr;
+                *w_s = nullptr;
   int *amax = nullptr;  // slots: see kAmax*
-  int pi_lead = 7;      // leading-slice width of the polarisation GEMM (K = 2 nb kpad)
-  CUtensorMap mBh_s, mBnr_s, mBnc_s, mBnb_s, mBnt_s, mW_s, mBpi_s;
+  // sliced nb^2 x nb^2 x nb^2 products (tc_pi_gemm_kernel): three BF16 slices of the A
+  // operand [3][nb^2][2 nb^2] and of the B operand [3][2 nb^2][2 nb^2], per-row maxima of A
+  // and per-column maxima of B (FP32 bits)
+  __nv_bfloat16 *pa_s = nullptr, *pb_s = nullptr;
+  int *rowmax = nullptr, *colmax = nullptr;
+  CUtensorMap mBh_s, mBnr_s, mBnc_s, mBnb_s, mBnt_s, mW_s, mPa_s, mPb_s;
   // tensor maps
   CUtensorMap mZin_y32, mZin_ys32, mCol_y32, mCol_ys32, mW32, mWh32, mBuf1Gather, mBuf2Lin, mBuf1Lin;
   CUtensorMap mBh_hi, mBh_lo, mBnr_hi, mBnr_lo, mBnc_hi, mBnc_lo, mBnb_hi, mBnb_lo, mW_hi, mW_lo;
   CUtensorMap mPi_y32, mPi_ys32, mBpi_hi, mBpi_lo, mBnt_hi, mBnt_lo;
-  CUtensorMap mLam, mBnbr_s, mBnbc_s, mWp32, mBnbt_s;
+  CUtensorMap mBnbr_s, mBnbc_s, mWp32, mBnbt_s;
 };
 
 namespace {
@@ -793,7 +853,7 @@ namespace {
 // amax slots: FP32 bit patterns of the largest |A| of each A tensor of the sliced form
 enum : int {
   kAmaxW = 0, kAmaxY = 1, kAmaxYs = 2, kAmaxP1 = 3, kAmaxP2 = 4, kAmaxP3 = 5, kAmaxH1 = 6, kAmaxH2 = 7,
-  kAmaxWh = 8, kAmaxT1 = 9, kAmaxT2 = 10, kAmaxHc = 11, kAmaxZero = 12, kAmaxSlots = 16
+  kAmaxWh = 8, kAmaxT1 = 9, kAmaxT2 = 10, kAmaxSlots = 16
 };
 
 template <class T>
@@ -915,29 +975,32 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
   }
   if (big) {
     const long long ncol = 2 * N * N;  // output columns (j, l, v)
-    // the sliced form keeps three accumulators of nout columns in TMEM (512 columns)
-    t->pi_nout = (int)std::min<long long>(sliced ? kPiNoutSliced : 256, ((ncol + 15) / 16) * 16);
+    // TF32 form: the tc_gemm_kernel geometry of the polarisation (column tiles of up to 256)
+    t->pi_nout = (int)std::min<long long>(256, ((ncol + 15) / 16) * 16);
     t->pi_ntiles = (int)((ncol + t->pi_nout - 1) / t->pi_nout);
     t->pi_mtiles = ((nb + 3) / 4) * ((nb + 31) / 32);
     t->pi_ldb = 2 * N * t->kpad;
     const size_t brows = (size_t)t->pi_ntiles * t->pi_nout;
     if ((rc = talloc(t, &t->Y1, 2 * N4)) || (rc = talloc(t, &t->Y2, 2 * N4)) || (rc = talloc(t, &t->Pi, 2 * N4)) ||
-        (rc = talloc(t, &t->bpi_hi, brows * t->pi_ldb)) || (rc = talloc(t, &t->bpi_lo, brows * t->pi_ldb)) ||
         (rc = talloc(t, &t->bnt_hi, (size_t)t->nout2 * kt_r)) || (rc = talloc(t, &t->bnt_lo, (size_t)t->nout2 * kt_r)))
       return bail(rc);
-    if (cudaMemset(t->bpi_hi, 0, brows * t->pi_ldb * sizeof(float)) != cudaSuccess ||
-        cudaMemset(t->bpi_lo, 0, brows * t->pi_ldb * sizeof(float)) != cudaSuccess)
-      return bail(G1G2_ECUDA);
-    if (sliced) {
-      t->pi_lead = slice_lead_order1(2LL * N * t->kpad);
-      if ((rc = talloc(t, &t->bpi_s, (size_t)kSlices * brows * t->pi_ldb))) return bail(rc);
-      if (cudaMemset(t->bpi_s, 0, (size_t)kSlices * brows * t->pi_ldb * sizeof(__nv_bfloat16)) != cudaSuccess)
+    if (!sliced) {
+      if ((rc = talloc(t, &t->bpi_hi, brows * t->pi_ldb)) || (rc = talloc(t, &t->bpi_lo, brows * t->pi_ldb)))
+        return bail(rc);
+      if (cudaMemset(t->bpi_hi, 0, brows * t->pi_ldb * sizeof(float)) != cudaSuccess ||
+          cudaMemset(t->bpi_lo, 0, brows * t->pi_ldb * sizeof(float)) != cudaSuccess)
         return bail(G1G2_ECUDA);
+    } else {
+      const size_t K = 2 * (size_t)N * N;
+      if ((rc = talloc(t, &t->pa_s, (size_t)kPiSlices * N * N * K)) ||
+          (rc = talloc(t, &t->pb_s, (size_t)kPiSlices * K * K)) || (rc = talloc(t, &t->rowmax, (size_t)N * N)) ||
+          (rc = talloc(t, &t->colmax, (size_t)N * N)))
+        return bail(rc);
     }
     if (has_pp || has_ph) {
       const size_t bs_c = (size_t)kSlices * t->nout2 * kt_c, bs_r = (size_t)kSlices * t->nout2 * kt_r;
-      if ((rc = talloc(t, &t->Gp32, 2 * N4)) || (rc = talloc(t, &t->bnbr_s, bs_r)) ||
-          (rc = talloc(t, &t->bnbc_s, bs_c)) || (rc = talloc(t, &t->bnbt_s, bs_r)))
+      if ((rc = talloc(t, &t->bnbr_s, bs_r)) || (rc = talloc(t, &t->bnbc_s, bs_c)) ||
+          (rc = talloc(t, &t->bnbt_s, bs_r)))
         return bail(rc);
       t->Lam = t->Pi;
       if (has_pi && (rc = talloc(t, &t->Lam, 2 * N4))) return bail(rc);
@@ -1060,11 +1123,12 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
       (rc = map_b(&t->mW_hi, t->w_hi, (int)N3, nb, t->nout1)) ||
       (rc = map_b(&t->mW_lo, t->w_lo, (int)N3, nb, t->nout1)) ||
       (big &&
+       ((rc = map_b(&t->mBnt_hi, t->bnt_hi, kt_r, t->nout2, t->nout2)) ||
+        (rc = map_b(&t->mBnt_lo, t->bnt_lo, kt_r, t->nout2, t->nout2)))) ||
+      (big && !sliced &&
        ((rc = map_gather(&t->mPi_y32, t->y32, nb, 32, 1, 4)) || (rc = map_gather(&t->mPi_ys32, t->ys32, nb, 32, 1, 4)) ||
         (rc = map_b(&t->mBpi_hi, t->bpi_hi, (int)t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
-        (rc = map_b(&t->mBpi_lo, t->bpi_lo, (int)t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
-        (rc = map_b(&t->mBnt_hi, t->bnt_hi, kt_r, t->nout2, t->nout2)) ||
-        (rc = map_b(&t->mBnt_lo, t->bnt_lo, kt_r, t->nout2, t->nout2)))) ||
+        (rc = map_b(&t->mBpi_lo, t->bpi_lo, (int)t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)))) ||
       (sliced && ((rc = map_bs(&t->mBh_s, t->bh_s, kt_c, t->nout2, t->nout2)) ||
                   (rc = map_bs(&t->mBnr_s, t->bnr_s, kt_r, t->nout2, t->nout2)) ||
                   (rc = map_bs(&t->mBnc_s, t->bnc_s, kt_c, t->nout2, t->nout2)) ||
@@ -1072,10 +1136,11 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
                   (rc = map_bs(&t->mBnt_s, t->bnt_s, kt_r, t->nout2, t->nout2)) ||
                   (rc = map_bs(&t->mW_s, t->w_s, N3, nb, t->nout1)) ||
                   (big &&
-                   (rc = map_bs(&t->mBpi_s, t->bpi_s, t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout))) ||
+                   ((rc = map_bs(&t->mPa_s, t->pa_s, 2 * N * N, (int)(N * N), kPiTileM, kPiSlices, kPiSlices)) ||
+                    (rc = map_bs(&t->mPb_s, t->pb_s, 2 * N * N, (int)(2 * N * N), kPiTileN, kPiSlices,
+                                 kPiSlices)))) ||
                   ((has_pp || has_ph) &&
-                   ((rc = map_gather(&t->mLam, t->Gp32, nb, 32, 1, 4)) ||
-                    (rc = map_bs(&t->mBnbr_s, t->bnbr_s, kt_r, t->nout2, t->nout2)) ||
+                   ((rc = map_bs(&t->mBnbr_s, t->bnbr_s, kt_r, t->nout2, t->nout2)) ||
                     (rc = map_bs(&t->mBnbc_s, t->bnbc_s, kt_c, t->nout2, t->nout2)) ||
                     (rc = map_bs(&t->mBnbt_s, t->bnbt_s, kt_r, t->nout2, t->nout2)))) ||
                   (has_ph && (rc = map_linear(&t->mWp32, t->Wp32, nb, N3, 1)))))) {
@@ -1101,7 +1166,8 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
     return dyn >= (int)need && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess;
   };
   if (!raise_limit((const void *)tc_gemm_kernel<false>, smax) || !raise_limit((const void *)tc_gemm_kernel<true>, smax) ||
-      !raise_limit((const void *)orbit_assemble_kernel, 4 * BEL * sizeof(float2))) {
+      !raise_limit((const void *)orbit_assemble_kernel, 4 * BEL * sizeof(float2)) ||
+      (big && sliced && !raise_limit((const void *)tc_pi_gemm_kernel, kPiSmemBytes))) {
     cudaGetLastError();
     set_error_detail("cannot raise the shared-memory limit of the tensor-core kernels");
     return bail(G1G2_ECUDA);
@@ -1173,6 +1239,40 @@ void tc_load_state(TcPath *p, Launcher &L, const cplx *G) {
   to_planar_f32_kernel<<<2048, 256, 0, L.stream>>>(p->N4, G, p->y32, slot);
   L.after_launch();
 }
+
+namespace {
+// out = A B^T for one nb^2 x nb^2 x nb^2 product of the sliced form: the A operand read from
+// the planar FP32 state G32 through m, its per-row maxima and three BF16 slices, then
+// tc_pi_gemm_kernel against the B slices already in pb_s (out in the layout
+// out[a][c][d][b], complex).
+void sliced_product(TcPath *t, Launcher &L, const float *G32, AOperand m, float *out, const char *tag) {
+  const int nb = t->nb;
+  const long long N = nb, K = 2 * N * N;
+  const int nbt = (nb + 31) / 32;
+  cudaMemsetAsync(t->rowmax, 0, N * N * sizeof(int), L.stream);
+  L.before("tc_product_a_rowmax");
+  a_rowmax_kernel<<<dim3((unsigned)(nb * nbt), (unsigned)(2 * ((nb + 7) / 8))), dim3(32, 8), 0, L.stream>>>(
+      nb, G32, t->N4, m, t->rowmax);
+  L.after_launch();
+  L.before("tc_product_a_slices");
+  a_slice3_kernel<<<dim3((unsigned)(nb * nbt), (unsigned)(2 * nb)), dim3(32, 8), 0, L.stream>>>(
+      nb, G32, t->N4, m, t->rowmax, t->pa_s, N * N * K);
+  L.after_launch();
+  PiGemmParams g{};
+  g.nb = nb;
+  g.M = nb * nb;
+  g.ncols = 2 * nb * nb;
+  g.kblocks = (int)(K / kPiBlockK);
+  g.mtiles = (g.M + kPiTileM - 1) / kPiTileM;
+  g.tiles = g.mtiles * ((g.ncols + kPiTileN - 1) / kPiTileN);
+  g.out = reinterpret_cast<float2 *>(out);
+  g.err = t->err;
+  const int grid = std::max(1, std::min(g.tiles, t->sms));
+  L.before(tag);
+  tc_pi_gemm_kernel<<<grid, kPiThreads, kPiSmemBytes, L.stream>>>(t->mPa_s, t->mPb_s, g);
+  L.after_launch();
+}
+}  // namespace
 
 void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cplx *hhf, Rk4Stage st, cplx *ny,
             cplx *nys, cplx *nacc, cplx *nk, cplx *Gy, cplx *Gys, cplx *Gacc, cplx *Gk) {
@@ -1302,41 +1402,43 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
                 lp(N3, 1, EP_SWAP34, t->Y1, wh_slot, kAmaxH1), sl);
     launch_gemm(t, L, "tc_gemm_hcorr", t->mWh32, sl ? t->mBnt_s : t->mBnt_hi, t->mBnt_lo,
                 lp(N3, 1, EP_SWAP34, t->Y2, wh_slot, kAmaxH2), sl);
-    const dim3 pgrid((unsigned)(((nb + 31) / 32) * (t->kpad / 32)), (unsigned)(N * N));
-    L.before("tc_realify_pi");
     if (sl) {
-      // exponent from the exact max|hcorr| (slot kAmaxHc; kAmaxZero stays 0)
-      cudaMemsetAsync(amax + kAmaxHc, 0, sizeof(int), L.stream);
-      hcorr_amax_kernel<<<pgrid, dim3(32, 8), 0, L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, amax + kAmaxHc);
-      const long long brows = (long long)t->pi_ntiles * t->pi_nout;
-      realify_pi_sliced_kernel<<<pgrid, dim3(32, 8), 0, L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4,
-                                                                    amax + kAmaxHc, t->pi_lead, t->bpi_s,
-                                                                    t->pi_ldb, brows * t->pi_ldb);
+      // B = R(hcorr) as three BF16 slices with per-column exponents, then the product
+      const int nt = (nb + 31) / 32;
+      const dim3 bgrid((unsigned)(nt * nt), (unsigned)(N * N));
+      cudaMemsetAsync(t->colmax, 0, N * N * sizeof(int), L.stream);
+      L.before("tc_pi_b_colmax");
+      hcorr_colmax_kernel<<<bgrid, dim3(32, 8), 0, L.stream>>>(nb, t->Y1, t->Y2, t->N4, t->colmax);
+      L.after_launch();
+      L.before("tc_pi_b_slices");
+      realify_pi_slice3_kernel<<<bgrid, dim3(32, 8), 0, L.stream>>>(nb, t->Y1, t->Y2, t->N4, t->colmax, t->pb_s,
+                                                                     4 * N * N * N * N);
+      L.after_launch();
+      // a6: Pi_(ik),(jl) = sum_(pq) G_ipkq hcorr_qjpl, rows (i, k) of G_ipkq
+      sliced_product(t, L, from_y ? t->y32 : t->ys32, AOperand{N * N * N, N, N * N, 1}, t->Pi, "tc_gemm_pi");
     } else {
+      const dim3 pgrid((unsigned)(((nb + 31) / 32) * (t->kpad / 32)), (unsigned)(N * N));
+      L.before("tc_realify_pi");
       realify_pi_kernel<<<pgrid, dim3(32, 8), 0, L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, t->bpi_hi,
                                                              t->bpi_lo, t->pi_ldb);
+      L.after_launch();
+      // a6: Pi_(ik),(jl) = sum_(pq) G_ipkq hcorr_qjpl, one GEMM with M = N' = K = nb^2
+      GemmParams g{};
+      g.nb = nb;
+      g.a_rows = AR_PI;
+      g.epi = EP_PI;
+      g.n_tiles = t->pi_ntiles;
+      g.pi_mk = (nb + 31) / 32;
+      g.pi_kq = t->kpad / kBlockK;
+      g.pi_mtiles = t->pi_mtiles;
+      g.tiles = t->pi_mtiles * t->pi_ntiles;
+      g.nout = t->pi_nout;
+      g.n_valid = t->pi_nout;
+      g.rows = 2 * N * N;
+      g.out = t->Pi;
+      g.out_plane = t->N4;
+      launch_gemm(t, L, "tc_gemm_pi", from_y ? t->mPi_y32 : t->mPi_ys32, t->mBpi_hi, t->mBpi_lo, g, false);
     }
-    L.after_launch();
-    // a6: Pi_(ik),(jl) = sum_(pq) G_ipkq hcorr_qjpl, one GEMM with M = N' = K = nb^2
-    GemmParams g{};
-    g.nb = nb;
-    g.a_rows = AR_PI;
-    g.epi = EP_PI;
-    g.n_tiles = t->pi_ntiles;
-    g.pi_mk = (nb + 31) / 32;
-    g.pi_kq = t->kpad / kBlockK;
-    g.pi_mtiles = t->pi_mtiles;
-    g.tiles = t->pi_mtiles * t->pi_ntiles;
-    g.nout = t->pi_nout;
-    g.n_valid = t->pi_nout;
-    g.rows = 2 * N * N;
-    g.out = t->Pi;
-    g.out_plane = t->N4;
-    g.a_amax = g2_amax;
-    g.slice_lead = t->pi_lead;
-    g.acc3 = 1;
-    launch_gemm(t, L, "tc_gemm_pi", from_y ? t->mPi_y32 : t->mPi_ys32, sl ? t->mBpi_s : t->mBpi_hi, t->mBpi_lo, g,
-                sl);
   }
   // Ladder terms (Sec. IV.D/E): H^dag as P1 - P2, each term two right multiplications of a
   // real interaction tensor Wt (x_4 S into the exchange-permuted layout, then x_4 S' again,
@@ -1351,35 +1453,15 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     launch_gemm(t, L, tag, t->mBuf1Lin, B1b, B1b, lp(N3, 2, EP_SWAP34, t->Y1, kAmaxT1, kAmaxH1), sl);
     launch_gemm(t, L, tag, mWt, B2a, B2a, lp(N3, 1, EP_EXCH_T, t->buf1, wt_slot, kAmaxT2), sl);
     launch_gemm(t, L, tag, t->mBuf1Lin, B2b, B2b, lp(N3, 2, EP_SWAP34, t->Y2, kAmaxT2, kAmaxH2), sl);
-    const long long brows = (long long)t->pi_ntiles * t->pi_nout;
     const dim3 lgrid((unsigned)((t->kpad / 32) * ((nb + 31) / 32)), (unsigned)(N * N));
-    cudaMemsetAsync(amax + kAmaxHc, 0, sizeof(int), L.stream);
-    L.before("tc_realify_ladder");
-    ladder_amax_kernel<<<lgrid, dim3(32, 8), 0, L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, amax + kAmaxHc);
-    realify_lam_sliced_kernel<<<lgrid, dim3(32, 8), 0, L.stream>>>(nb, t->kpad, t->Y1, t->Y2, t->N4, amax + kAmaxHc,
-                                                                   t->pi_lead, t->bpi_s, t->pi_ldb,
-                                                                   brows * t->pi_ldb);
+    cudaMemsetAsync(t->colmax, 0, N * N * sizeof(int), L.stream);
+    L.before("tc_ladder_b_colmax");
+    ladder_colmax_kernel<<<lgrid, dim3(32, 8), 0, L.stream>>>(nb, t->Y1, t->Y2, t->N4, t->colmax);
     L.after_launch();
-  };
-  auto ladder_gemm = [&](const char *tag) {
-    GemmParams g{};
-    g.nb = nb;
-    g.a_rows = AR_PI;
-    g.epi = EP_PI;
-    g.n_tiles = t->pi_ntiles;
-    g.pi_mk = (nb + 31) / 32;
-    g.pi_kq = t->kpad / kBlockK;
-    g.pi_mtiles = t->pi_mtiles;
-    g.tiles = t->pi_mtiles * t->pi_ntiles;
-    g.nout = t->pi_nout;
-    g.n_valid = t->pi_nout;
-    g.rows = 2 * N * N;
-    g.out = t->Lam;
-    g.out_plane = t->N4;
-    g.a_amax = g2_amax;
-    g.slice_lead = t->pi_lead;
-    g.acc3 = 1;
-    launch_gemm(t, L, tag, t->mLam, t->mBpi_s, t->mBpi_s, g, sl);
+    L.before("tc_ladder_b_slices");
+    realify_lam_slice3_kernel<<<lgrid, dim3(32, 8), 0, L.stream>>>(nb, t->Y1, t->Y2, t->N4, t->colmax, t->pb_s,
+                                                                    4 * N * N * N * N);
+    L.after_launch();
   };
   const float *g32 = from_y ? t->y32 : t->ys32;
   const int nt32 = (nb + 31) / 32;
@@ -1387,11 +1469,8 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     // Eq. (HTPPcorr): H^dag_pqkl = sum_rs w_pqrs (nbar_rk nbar_sl - n_rk n_sl)
     const int wh_slot = (t->Wh32 == t->W32) ? kAmaxW : kAmaxWh;
     ladder("tc_gemm_ladder_h", t->mWh32, wh_slot, t->mBnbr_s, t->mBnbc_s, t->mBnr_s, t->mBnc_s);
-    L.before("tc_swap12");
-    swap12_planar_kernel<<<2048, 256, 0, L.stream>>>(nb, g32, t->Gp32, 2 * t->N4);
-    L.after_launch();
     // Eq. (lambdapp): Lambda^dag_(ij),(kl) = sum_(pq) G_ijpq H^dag_pqkl (rows (i, j), K (p, q))
-    ladder_gemm("tc_gemm_ladder");
+    sliced_product(t, L, g32, AOperand{N * N * N, N * N, N, 1}, t->Lam, "tc_gemm_ladder");
     L.before("tc_ladder_into_source");
     sub_swap13_kernel<<<dim3((unsigned)(nt32 * nt32), (unsigned)(N * N)), dim3(32, 8), 0, L.stream>>>(
         nb, reinterpret_cast<const float2 *>(t->Lam), reinterpret_cast<float2 *>(t->buf2));
@@ -1405,11 +1484,8 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
       ladder("tc_gemm_ladder_h", t->mWp32, kAmaxWh, t->mBnbt_s, t->mBnc_s, t->mBnt_s, t->mBnbc_s);
     else
       ladder("tc_gemm_ladder_h", t->mWp32, kAmaxWh, t->mBnt_s, t->mBnbc_s, t->mBnbt_s, t->mBnc_s);
-    L.before("tc_swap34");
-    swap34_planar_kernel<<<(unsigned)(2 * N * N * nt32 * nt32), dim3(32, 8), 0, L.stream>>>(nb, g32, t->Gp32);
-    L.after_launch();
     // Eq. (lambdaph): Lambda^dag_ijkl = sum_pq G_ipql X_(pq),(kj) (rows (i, l), K (p, q))
-    ladder_gemm("tc_gemm_ladder");
+    sliced_product(t, L, g32, AOperand{N * N * N, 1, N * N, N}, t->Lam, "tc_gemm_ladder");
     L.before("tc_ladder_into_source");
     sub_rot_kernel<<<dim3((unsigned)(nt32 * nt32), (unsigned)(N * N)), dim3(32, 8), 0, L.stream>>>(
         nb, reinterpret_cast<const float2 *>(t->Lam), reinterpret_cast<float2 *>(t->buf2));

@@ -200,13 +200,6 @@ __host__ __device__ constexpr int slice_lead_for(long long K) {
   while (L > 1 && K * (1LL << (2 * L)) >= (1LL << 24)) --L;
   return L;
 }
-// ... and when the two order-1 products (|q_0 q_1| <= 2^(L+7)) must sum exactly too
-__host__ __device__ constexpr int slice_lead_order1(long long K) {
-  int L = slice_lead_for(K);
-  while (L > 1 && 2 * K * (1LL << (L + 7)) >= (1LL << 24)) --L;
-  return L;
-}
-
 // Four slices of x (|x| < 2^E): x = v_0 + v_1 + v_2 + v_3 + O(2^(E-L-25)), where
 // v_s is an integer multiple of 2^(E-L-8s) with |v_0| <= 2^E and
 // |v_s| <= 2^(E-L-8s+7) for s > 0, i.e. at most 8 significant bits: exact in
@@ -219,6 +212,20 @@ __device__ __forceinline__ void slice4(float x, float (&v)[4], const float (&c)[
   for (int s = 0; s < 4; ++s) {
     v[s] = __fsub_rn(__fadd_rn(r, c[s]), c[s]);
     r = __fsub_rn(r, v[s]);
+  }
+}
+
+// Three slices of x (|x| < 2^E) with a 9-bit leading slice (L = 8): the cuts of slice4
+// with c_q = 1.5 2^(15 + E - 8q); v_q is x's remainder rounded to nearest-even on the
+// grid 2^(E - 8 - 8q), |v_0| <= 2^E, |v_1|, |v_2| <= 2^(E - 9 - 8(q - 1)), each exact in
+// BF16.  The part of x below 2^(E - 25) is dropped.
+__device__ __forceinline__ void slice3_lead8(float x, int E, float (&v)[3]) {
+  float r = x;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float c = ldexpf(1.5f, 15 + E - 8 * q);
+    v[q] = __fsub_rn(__fadd_rn(r, c), c);
+    r = __fsub_rn(r, v[q]);
   }
 }
 

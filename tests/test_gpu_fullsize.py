@@ -14,9 +14,9 @@ pytestmark = pytest.mark.gpu
 
 
 def tol_bf16x4(se, nb):
-    """The BF16-slice bars of one right-hand side (test_gpu_tc.py): 1e-6 for the nb^5
-    passes, the polarisation's 2^-23 sqrt(2 nb^2) random-walk bound for GW."""
-    return 1e-6 if se == "SOA" else max(1e-6, 2 * 2.0 ** -24 * np.sqrt(2 * nb * nb))
+    """The BF16-slice bar of one right-hand side (test_gpu_tc.py): 1e-6 for every
+    selfenergy, the nb^2 x nb^2 x nb^2 products included."""
+    return 1e-6
 
 
 @pytest.mark.parametrize("name,se", [("general-soa-nb96", "SOA"), ("general-gw-nb64", "GW"),

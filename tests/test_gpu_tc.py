@@ -8,13 +8,14 @@ steps, each rounding at 2^-24; its random-walk error is 2^-24 sqrt(3 K'/8).
 The bar for one right-hand side (max |Δ| / max |ref|) is eight times that,
 and never below 2e-6.
 
-The BF16-slice form (bf16x4) accumulates its leading products exactly and
-carries 27-32 bits of every operand relative to the tensor's largest entry;
-what remains is the FP32 storage of the state and of the intermediates
-(2^-24 each, round to nearest).  For SOA its bar is 1e-6.  The GW
-polarisation sums K' = 2 nb^2 products of two FP32-stored tensors (G2 and
-hcorr) with mostly random signs, so their storage rounding reaches the result
-as about 2^-24 sqrt(K'); the GW bar is twice that, and never below 1e-6.
+The BF16-slice form (bf16x4) accumulates its leading products exactly.  Its
+nb^5 passes carry 27-32 bits of every operand relative to the tensor's largest
+entry; its nb^2 x nb^2 x nb^2 products (polarisation, ladders) carry 25 bits
+relative to the largest entry of each row of A and each column of B and drop
+only the order-3 and order-4 slice products, which sit near the FP32 rounding
+of the inputs.  What remains is the FP32 storage of the state and of the
+intermediates (2^-24 each, round to nearest).  The bar is 1e-6 for every
+selfenergy and size (measured: at most 2.4e-7, at the full nb = 64).
 """
 import math
 import numpy as np
@@ -32,7 +33,7 @@ pytestmark = pytest.mark.gpu
 
 def tol_rhs(se, nb, prec="tf32x3"):
     if prec == "bf16x4":
-        return max(1e-6, 2 * 2.0 ** -24 * math.sqrt(2 * nb * nb)) if se in ("GW", "GWX") else 1e-6
+        return 1e-6
     kp = 2 * nb * nb if se in ("GW", "GWX") else 2 * nb
     return max(2e-6, 8 * 2.0 ** -24 * math.sqrt(3 * kp / 8))
 
