@@ -1,0 +1,81 @@
+"""The partition of the right-hand side over ranks (G2 and w split along their first
+index, paper_2002_12717_gb300/shard.py) on CPU ranks with the gloo backend: every
+rank's slab of dG2/dt, the replicated dn/dt and the correlation energy against the
+oracle's full right-hand side, element by element, for 2 ranks (nb = 6, and nb = 5
+with a ragged last block) and 3 ranks (nb = 5: blocks 2, 2, 1)."""
+import os
+import socket
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import g1g2_oracle as O
+
+from .helpers import problem
+
+torch = pytest.importorskip("torch")
+
+CASES = [("SOA", 6), ("SOA", 5), ("GW", 6), ("GW", 5), ("GWX", 5), ("HF", 5)]
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _state(nb, se, seed):
+    h, w, n, g2, _, _ = problem(nb, se if se != "HF" else "SOA", complex_w=True, seed=seed, drive=False)
+    return h, w, n, g2
+
+
+def _worker(rank, world, port, outdir, cases):
+    import torch.distributed as dist
+
+    from paper_2002_12717_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        for ci, (se, nb) in enumerate(cases):
+            h, w, n, g2 = _state(nb, se, 60 + ci)
+            part = shard.Partition(nb, world, rank)
+            t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128))
+            dn, dg = shard.rhs_sharded(part, t(h), part.slab(t(w)), t(n), part.slab(t(g2)), se)
+            ec = shard.correlation_energy_sharded(part, part.slab(t(w)), part.slab(t(g2)))
+            np.savez(os.path.join(outdir, f"r{rank}_c{ci}.npz"), dn=dn.numpy(), dg=dg.numpy(), ec=ec,
+                     lo=part.lo, hi=part.hi)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_rhs_matches_oracle(world):
+    import torch.multiprocessing as mp
+    cases = CASES if world == 2 else [c for c in CASES if c[1] == 5]
+    with tempfile.TemporaryDirectory() as outdir:
+        mp.spawn(_worker, args=(world, _free_port(), outdir, cases), nprocs=world, join=True)
+        for ci, (se, nb) in enumerate(cases):
+            h, w, n, g2 = _state(nb, se, 60 + ci)
+            prob = O.Problem(h, w, se, False)
+            dn_ref, dg_ref = O.rhs(prob, 0.0, n, g2)
+            e_ref = -0.5 * np.real(np.einsum("ijkl,klij->", w, g2))
+            covered = np.zeros(nb, dtype=bool)
+            for r in range(world):
+                z = np.load(os.path.join(outdir, f"r{r}_c{ci}.npz"))
+                lo, hi = int(z["lo"]), int(z["hi"])
+                covered[lo:hi] = True
+                scale = max(np.abs(dg_ref).max(), 1e-300)
+                assert np.abs(z["dg"] - dg_ref[lo:hi]).max() <= 1e-12 * scale, (se, nb, r)
+                assert np.abs(z["dn"] - dn_ref).max() <= 1e-12 * np.abs(dn_ref).max(), (se, nb, r)
+                assert abs(float(z["ec"]) - e_ref) <= 1e-12 * max(abs(e_ref), 1e-12)
+            assert covered.all()
+
+
+def test_partition_blocks():
+    from paper_2002_12717_gb300.shard import Partition
+    for nb, world in ((5, 2), (5, 3), (6, 4), (7, 7), (3, 4)):
+        ranges = [Partition(nb, world, r).range(r) for r in range(world)]
+        assert ranges[0][0] == 0 and ranges[-1][1] == nb
+        assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
