@@ -204,7 +204,8 @@ int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_de
 /* Discrete adjoint of nsteps RK4 steps of the FP64 form (fermions, every selfenergy
  * in a general basis), starting
  * from the current state: the gradient of a final-time objective J with
- * respect to the drive parameters, a global scale of w and the entries of h.
+ * respect to the drive parameters, a global scale of w, the entries of h and
+ * the entries of w.
  * Not in the paper; the reverse sweep is the exact transpose of the discrete
  * RK4 map, with the state (n, G2) checkpointed every ckpt_every steps and
  * each segment recomputed once.  ckpt_every <= 0 chooses the interval from
@@ -221,12 +222,20 @@ int g1g2_rhs_vjp(g1g2_ctx *c, double t, const double *n_dev, const double *G2_de
  *   grad_wscale dJ/ds for w -> s w at s = 1 (e.g. U dJ/dU for a Hubbard w), or NULL
  *   grad_h      nb*nb interleaved gradient G on Hermitian h: for every Hermitian
  *               perturbation dh, dJ = Re sum conj(G_ij) dh_ij (G is Hermitian), or NULL
+ *   grad_w      nb^4 interleaved gradient W on the interactions g1g2_init accepts
+ *               (w_ijkl = w_jilk = conj(w_klij)): for every such perturbation dw,
+ *               dJ = Re sum conj(W_ijkl) dw_ijkl, and W has the same symmetries (for a
+ *               real w and real dw only Re W acts).  Every place w enters the right-hand
+ *               side contributes: Eq. (h_HF), Eq. (eom_gone-I), the source term of
+ *               Eq. (psi-pm-def), Eq. (gwhcorr) and the ladder quasi-Hamiltonians of
+ *               Eqs. (HTPPcorr), (HTPHcorr), plus the interaction energies of objective 2.
+ *               Host array, or NULL (then none of that work is done)
  * Cotangents use Re sum conj(x) y over every complex entry of (G1, G2).  On
  * return the context holds the final state (as after g1g2_propagate).
  * G1G2_EUNSUPPORTED for the tensor-core precision, bosons and the spin-restricted
  * Hubbard GW. */
 int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objective, double *J_out,
-                 double *grad_drive, double *grad_wscale, double *grad_h);
+                 double *grad_drive, double *grad_wscale, double *grad_h, double *grad_w);
 
 /* Where g1g2_adjoint keeps its checkpoints: G1G2_CKPT_AUTO (device memory when
  * the checkpoints and one segment fit in 80% of the free device memory, else

@@ -256,18 +256,40 @@ __global__ void hf_build_kernel(int nb, const void *__restrict__ Wm_, const cplx
   const int lane = threadIdx.x & 31;
   const int nb2 = nb * nb;
   if (warp >= nb2) return;
-  cplx acc = {0.0, 0.0};
+  // the row of Wm streams from HBM: four independent loads per lane in flight
+  cplx acc = {0.0, 0.0}, acc2 = {0.0, 0.0};
+  int c = lane;
   if (REAL) {
     const double *Wm = static_cast<const double *>(Wm_) + (long long)warp * nb2;
-    for (int c = lane; c < nb2; c += 32) {
+    for (; c + 96 < nb2; c += 128) {
+      const double w0 = Wm[c], w1 = Wm[c + 32], w2 = Wm[c + 64], w3 = Wm[c + 96];
+      const cplx n0 = n[c], n1 = n[c + 32], n2 = n[c + 64], n3 = n[c + 96];
+      acc.x = fma(w0, n0.x, acc.x);
+      acc.y = fma(w0, n0.y, acc.y);
+      acc2.x = fma(w1, n1.x, acc2.x);
+      acc2.y = fma(w1, n1.y, acc2.y);
+      acc.x = fma(w2, n2.x, acc.x);
+      acc.y = fma(w2, n2.y, acc.y);
+      acc2.x = fma(w3, n3.x, acc2.x);
+      acc2.y = fma(w3, n3.y, acc2.y);
+    }
+    for (; c < nb2; c += 32) {
       const double wv = Wm[c];
       acc.x = fma(wv, n[c].x, acc.x);
       acc.y = fma(wv, n[c].y, acc.y);
     }
   } else {
     const cplx *Wm = static_cast<const cplx *>(Wm_) + (long long)warp * nb2;
-    for (int c = lane; c < nb2; c += 32) acc = cfma(Wm[c], n[c], acc);
+    for (; c + 96 < nb2; c += 128) {
+      const cplx w0 = Wm[c], w1 = Wm[c + 32], w2 = Wm[c + 64], w3 = Wm[c + 96];
+      acc = cfma(w0, n[c], acc);
+      acc2 = cfma(w1, n[c + 32], acc2);
+      acc = cfma(w2, n[c + 64], acc);
+      acc2 = cfma(w3, n[c + 96], acc2);
+    }
+    for (; c < nb2; c += 32) acc = cfma(Wm[c], n[c], acc);
   }
+  acc = cadd(acc, acc2);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
@@ -804,6 +826,50 @@ __global__ void hf_build_t_kernel(int nb, const void *__restrict__ Wm_, const cp
 void zaxpby(Launcher &L, long long n, cplx alpha, const cplx *x, cplx beta, const cplx *y, cplx *out) {
   L.before("adj_axpby");
   zaxpby_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8192), 256, 0, L.stream>>>(n, alpha, x, beta, y, out);
+  L.after_launch();
+}
+
+// Cotangent of w from the Hartree-Fock build (Eq. h_HF): with Wm[(ij),(lk)] = w_ikjl + eta
+// w_iklj, the cotangent x of h^HF gives Wmbar[(ij),(lk)] = x_ij conj(n_lk), so
+// wbar_abcd += c (x_ac conj(n_db) + eta x_ad conj(n_cb)).  One thread per element of w.
+__global__ void hf_wbar_kernel(int nb, const cplx *__restrict__ x, const cplx *__restrict__ n, double c, double eta,
+                               cplx *wbar) {
+  const long long N = nb, N4 = N * N * N * N;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N4; e += (long long)gridDim.x * blockDim.x) {
+    const long long d = e % N, cc = (e / N) % N, b = (e / (N * N)) % N, a = e / (N * N * N);
+    const cplx x1 = x[a * N + cc], n1 = n[d * N + b];
+    double re = x1.x * n1.x + x1.y * n1.y, im = x1.y * n1.x - x1.x * n1.y;   // x1 conj(n1)
+    if (eta != 0.0) {
+      const cplx x2 = x[a * N + d], n2 = n[cc * N + b];
+      re += eta * (x2.x * n2.x + x2.y * n2.y);
+      im += eta * (x2.y * n2.x - x2.x * n2.y);
+    }
+    wbar[e].x += c * re;
+    wbar[e].y += c * im;
+  }
+}
+
+// out = (X + X_jilk + conj(X_klij) + conj(X_lkji)) / 4: the orthogonal projection (for
+// Re sum conj(x) y) onto the tensors with the symmetries w_ijkl = w_jilk = conj(w_klij).
+__global__ void w_symmetrize_kernel(int nb, const cplx *__restrict__ X, cplx *out) {
+  const long long N = nb, N4 = N * N * N * N;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N4; e += (long long)gridDim.x * blockDim.x) {
+    const long long l = e % N, k = (e / N) % N, j = (e / (N * N)) % N, i = e / (N * N * N);
+    const cplx a = X[e], b = X[((j * N + i) * N + l) * N + k];
+    const cplx h = X[((k * N + l) * N + i) * N + j], g = X[((l * N + k) * N + j) * N + i];
+    out[e] = make_double2(0.25 * (a.x + b.x + h.x + g.x), 0.25 * (a.y + b.y - h.y - g.y));
+  }
+}
+
+void hf_wbar(Launcher &L, int nb, const cplx *x, const cplx *n, double c, double eta, cplx *wbar) {
+  L.before("adj_hf_wbar");
+  hf_wbar_kernel<<<1024, 256, 0, L.stream>>>(nb, x, n, c, eta, wbar);
+  L.after_launch();
+}
+
+void w_symmetrize(Launcher &L, int nb, const cplx *X, cplx *out) {
+  L.before("adj_w_symmetrize");
+  w_symmetrize_kernel<<<1024, 256, 0, L.stream>>>(nb, X, out);
   L.after_launch();
 }
 

@@ -45,6 +45,7 @@ struct g1g2_ctx {
   void *Wm = nullptr;               // Hartree-Fock matrix [(ij),(lk)], real or complex
   cplx *w = nullptr;                // w (complex), [(ij),(kl)]
   cplx *wsrc = nullptr;             // source-term interaction (w^- or w)
+  bool src_pm = false;              // wsrc = w + eta w_ijlk (else wsrc = w)
   cplx *wP = nullptr;               // collision layout [(lp)][i][k] = w_iklp
   cplx *n = nullptr, *ns = nullptr, *ns2 = nullptr, *nacc = nullptr;
   cplx *G = nullptr, *Gs = nullptr, *Gacc = nullptr;
@@ -67,6 +68,7 @@ struct g1g2_ctx {
   long long adj_acc_len = 0;
   cplx *adj_hsum = nullptr;                     // accumulated cotangent of h
   cplx *adj_hbar = nullptr;                     // cotangent of hHF of one stage
+  cplx *adj_wbar = nullptr;                     // accumulated cotangent of w (grad_w requested)
   std::vector<void *> adj_allocs;
   // Hubbard basis (spin-restricted SOA, on-site w): O(nb^4) right-hand side
   bool hub_ok = false, hub_on = false;
@@ -539,9 +541,12 @@ void matmul(g1g2_ctx *c, Launcher &L, const cplx *A, const cplx *B, cplx *out, c
 
 // Vector-Jacobian product of the FP64 right-hand side at (t, n, G): given the
 // cotangents (a, Y) of (dn, dG2), write the cotangents nbar of n, Gbar of G2
-// and hbar of h^HF (which is also the cotangent of the explicit h(t)).
+// and hbar of h^HF (which is also the cotangent of the explicit h(t)); with wbar
+// non-null, add the cotangent of the interaction w (every place w enters: the
+// Hartree-Fock build, the collision integral, the source term, the GW
+// quasi-Hamiltonian and the ladder quasi-Hamiltonians) to wbar.
 void vjp_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n, const cplx *G, const cplx *a, const cplx *Y,
-              cplx *nbar, cplx *Gbar, cplx *hbar) {
+              cplx *nbar, cplx *Gbar, cplx *hbar, cplx *wbar = nullptr) {
   const int nb = c->nb;
   const long long N = nb, N2 = N * N, N4 = N2 * N2;
   const cplx I1{0.0, 1.0}, mI{0.0, -1.0}, one{1.0, 0.0}, mone{-1.0, 0.0};
@@ -562,6 +567,9 @@ void vjp_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n, const cplx *G, 
   matmul(c, L, c->hhf, a, nbar, I1, 0.0);
   matmul(c, L, a, c->hhf, nbar, mI, 1.0);
   hf_build_t(L, nb, c->Wm, c->w_real, hbar, nbar, true);
+  const bool restricted = c->basis == G1G2_SPIN_RESTRICTED;
+  // wbar from Eq. (h_HF): Wm[(ij),(lk)] = w_ikjl + eta w_iklj (restricted: w_ikjl)
+  if (wbar) hf_wbar(L, nb, hbar, n, 1.0, restricted ? 0.0 : c->eta, wbar);
   if (!corr) {
     cudaMemsetAsync(Gbar, 0, N4 * sizeof(cplx), c->stream);
     return;
@@ -583,6 +591,15 @@ void vjp_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n, const cplx *G, 
     g.alpha = I1; g.beta = 1.0;
     zgemm(L, g);
   }
+  if (wbar) {
+    ZGemm g;  // wbar_iklp += i sum_j Ibar_ij conj(G_lpjk)  (batched over (lp), Ibar shared)
+    g.M = nb; g.N = nb; g.K = nb; g.batch = (int)N2;
+    g.A = c->I; g.sa_b = 0; g.sa_m = N; g.sa_k = 1;
+    g.B = G; g.sb_b = N2; g.sb_k = N; g.sb_n = 1; g.conjB = true;
+    g.C = wbar; g.sc_b = 1; g.sc_m = N2 * N; g.sc_n = N2;
+    g.alpha = I1; g.beta = 1.0;
+    zgemm(L, g);
+  }
   // source term: -i Psi = i A - i A^dag, cotangent of A: E = -i (Y + Y^dag);
   // A = nbar1 nbar2 w~ n3 n4, one n-factor at a time
   tconj_add(L, nb, mI, Y, c->AE);
@@ -600,6 +617,17 @@ void vjp_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n, const cplx *G, 
   mode_left2(c, L, c->nbar, c->AB1, c->T2, one, 0.0);
   mode_left1(c, L, c->nbar, c->T2, c->AB2, one, 0.0);      // B4 = nbar x_1 nbar x_2 T1'
   contract3(c, L, 4, c->AE, c->AB2, one, 1.0, nbar);
+  if (wbar) {
+    // A = (nbar (x) nbar) w~ (n (x) n): w~bar_pqrs = sum_ijkl nbar_pi nbar_qj E_ijkl n_kr n_ls
+    // (n, nbar Hermitian); w~ = w + eta w_pqsr (source w^±) or w
+    mode_left1(c, L, c->nbar, c->AE, c->AB1, one, 0.0);
+    mode_left2(c, L, c->nbar, c->AB1, c->AB2, one, 0.0);
+    mode_right3(c, L, c->AB2, n, c->AB1, one, 0.0);
+    mode_right4(c, L, c->AB1, n, c->AB2, one, 0.0);
+    zaxpby(L, N4, one, wbar, one, c->AB2, wbar);
+    const int p34[4] = {0, 1, 3, 2};
+    if (c->src_pm) permute4(L, nb, c->AB2, wbar, p34, cplx{c->eta, 0.0}, 1.0, false);
+  }
   // Ladder terms (Eqs. lambdapp, lambdaph): the source buffer holds A - Lambda, so the cotangent
   // of Lambda is -AE.  With nbar = 1 - n, dH^pp_ijkl = -sum_p dn_ip w_pjkl - sum_q dn_jq w_iqkl
   // and dH^ph_ijkl = sum_p dn_ip w_pjkl - sum_q dn_ql w_ijkq (Eqs. HTPPcorr, HTPHcorr).
@@ -628,6 +656,13 @@ void vjp_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n, const cplx *G, 
     }
     contract3(c, L, 1, c->AB1, c->w, mone, 1.0, nbar);
     contract3(c, L, 2, c->AB1, c->w, mone, 1.0, nbar);
+    if (wbar) {
+      // H = (nbar (x) nbar - n (x) n) w: wbar_pqkl += sum_ij (nbar_pi nbar_qj - n_pi n_qj) Hbar_ijkl
+      mode_left1(c, L, c->nbar, c->AB1, c->T1, one, 0.0);
+      mode_left2(c, L, c->nbar, c->T1, wbar, one, 1.0);
+      mode_left1(c, L, n, c->AB1, c->T1, one, 0.0);
+      mode_left2(c, L, n, c->T1, wbar, mone, 1.0);
+    }
   }
   if (c->se == G1G2_TPH || c->se == G1G2_DSL) {
     mode_left1(c, L, n, c->w, c->T1, one, 0.0);           // Hb = n w nbar - nbar w n (modes 1 and 4)
@@ -661,6 +696,13 @@ void vjp_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n, const cplx *G, 
     permute4(L, nb, c->AB1, c->T2, pHb, one, 0.0, false);
     contract3(c, L, 1, c->T2, c->w, one, 1.0, nbar);
     contract3(c, L, 4, c->T2, c->w, mone, 1.0, nbar);
+    if (wbar) {
+      // H = n w nbar - nbar w n (modes 1 and 4): wbar_pjks += sum_il (n_pi Hbar_ijkl nbar_ls - nbar_pi Hbar_ijkl n_ls)
+      mode_left1(c, L, n, c->T2, c->T1, one, 0.0);
+      mode_right4(c, L, c->T1, c->nbar, wbar, one, 1.0);
+      mode_left1(c, L, c->nbar, c->T2, c->T1, one, 0.0);
+      mode_right4(c, L, c->T1, n, wbar, mone, 1.0);
+    }
   }
   if (c->se != G1G2_GW && c->se != G1G2_DSL) return;
   // GW: dG2 += -i (Pi - conj(Pi_lkji)), Pi_ijkl = sum_pq hcorr_qjpl G_ipkq, hcorr = w x_4 n - n x_2 w
@@ -727,6 +769,11 @@ void vjp_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n, const cplx *G, 
     g.C = nbar; g.sc_m = N; g.sc_n = 1;
     g.alpha = mone; g.beta = 1.0;
     zgemm_reduce(L, g, c->partial, c->splits);
+  }
+  if (wbar) {
+    // hcorr = w x_4 n - n x_2 w: wbar_ijks += sum_l hbar_ijkl n_ls, wbar_iqkl -= sum_j n_qj hbar_ijkl
+    mode_right4(c, L, c->Hb, n, wbar, one, 1.0);
+    mode_left2(c, L, n, c->Hb, wbar, mone, 1.0);
   }
 }
 
@@ -1031,6 +1078,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   const bool use_pm =
       (se == G1G2_SOA || se == G1G2_TPP || se == G1G2_TPH || se == G1G2_DSL || gw_exchange) && !restricted;
   const double eta = bosons ? 1.0 : -1.0;
+  c->src_pm = use_pm;
   for (size_t i = 0; i < N; ++i)
     for (size_t j = 0; j < N; ++j)
       for (size_t k = 0; k < N; ++k)
@@ -1431,7 +1479,7 @@ int g1g2_adjoint_plan(const g1g2_ctx *c, int *ckpt_every, int *where) {
 }
 
 int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objective, double *J_out,
-                 double *grad_drive, double *grad_wscale, double *grad_h) {
+                 double *grad_drive, double *grad_wscale, double *grad_h, double *grad_w) {
   if (!c || nsteps < 1 || !J_out) return fail(G1G2_EINVAL, "bad adjoint argument");
   if (c->prec != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint runs on the FP64 form");
   if (c->hub_gw) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers the general basis");
@@ -1512,6 +1560,12 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
       (rc = adj_alloc(c, own, &kbar, SB)) || (rc = adj_alloc(c, own, &Ybar, SB)) || (rc = adj_alloc(c, own, &kk, SB)) ||
       (rc = adj_alloc(c, own, &acc, sizeof(double) * (1 + 4 * (size_t)nsteps))))
     return done(rc);
+  if (grad_w && !c->adj_wbar) {
+    void *p;
+    if ((rc = adj_alloc(c, c->adj_allocs, &p, N4 * sizeof(cplx)))) return done(rc);
+    c->adj_wbar = (cplx *)p;
+  }
+  if (grad_w) cudaMemsetAsync(c->adj_wbar, 0, N4 * sizeof(cplx), c->stream);
   double *dacc = (double *)acc;
   cudaMemsetAsync(dacc, 0, sizeof(double) * (1 + 4 * (size_t)nsteps), c->stream);
   cudaMemsetAsync(c->adj_hsum, 0, N2 * sizeof(cplx), c->stream);
@@ -1634,7 +1688,7 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
         }
         const double ts = tm + cs[s] * dt;
         vjp_fp64(c, L, ts, state_n(Ys[s]), state_G(Ys[s]), state_n(kbar), state_G(kbar), state_n(Ybar),
-                 state_G(Ybar), c->adj_hbar);
+                 state_G(Ybar), c->adj_hbar, grad_w ? c->adj_wbar : nullptr);
         // parameter cotangents of this stage: <D, hbar> (drive), hbar (h), <f_w, kbar> (scale of w)
         if (c->hasD) real_dot_acc(L, N2, c->D, c->adj_hbar, 1.0, c->adj_red, dacc + 1 + 4 * (size_t)m + s);
         if (grad_h) zaxpby(L, N2, one, c->adj_hsum, one, c->adj_hbar, c->adj_hsum);
@@ -1656,6 +1710,26 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
   cudaMemcpyAsync(c->n, state_n(at(ckpt, nseg)), N2 * sizeof(cplx), cudaMemcpyDefault, c->stream);
   cudaMemcpyAsync(c->G, state_G(at(ckpt, nseg)), N4 * sizeof(cplx), cudaMemcpyDefault, c->stream);
   c->t = tM;
+  if (grad_w) {
+    if (objective == 2) {
+      // E(T) - E(0) depends on w directly: E_HF = (s_HF) Re sum Wm[(ij),(lk)] n_lk n_ji gives the
+      // Hartree-Fock-build cotangent x = s_HF n (n Hermitian), E_corr = -(s_c) Re sum w_ijkl G_klij
+      // gives wbar += -(s_c) conj(G_klij) = -(s_c) G_ijkl (G Hermitian); minus the same at t0
+      const double s_hf = restricted ? 1.0 : 0.5, s_c = restricted ? 1.0 : 0.5;
+      const double eta_hf = restricted ? 0.0 : c->eta;
+      cudaMemcpyAsync(c->adj_hbar, c->n, N2 * sizeof(cplx), cudaMemcpyDeviceToDevice, c->stream);
+      hf_wbar(L, nb, c->adj_hbar, c->n, s_hf, eta_hf, c->adj_wbar);
+      zaxpby(L, N4, one, c->adj_wbar, cplx{-s_c, 0.0}, c->G, c->adj_wbar);
+      cudaMemcpyAsync(c->adj_hbar, state_n(at(ckpt, 0)), N2 * sizeof(cplx), cudaMemcpyDefault, c->stream);
+      hf_wbar(L, nb, c->adj_hbar, c->adj_hbar, -s_hf, eta_hf, c->adj_wbar);
+      cudaMemcpyAsync(state_G(kk), state_G(at(ckpt, 0)), N4 * sizeof(cplx), cudaMemcpyDefault, c->stream);
+      zaxpby(L, N4, one, c->adj_wbar, cplx{s_c, 0.0}, state_G(kk), c->adj_wbar);
+    }
+    // the gradient on the space of admissible w (w_ijkl = w_jilk = conj(w_klij), which g1g2_init
+    // enforces): the orthogonal projection of the accumulated cotangent
+    w_symmetrize(L, nb, c->adj_wbar, state_G(kk));
+    cudaMemcpyAsync(grad_w, state_G(kk), N4 * sizeof(cplx), cudaMemcpyDeviceToHost, c->stream);
+  }
   std::vector<double> hacc(1 + 4 * (size_t)nsteps);
   cudaMemcpyAsync(hacc.data(), dacc, hacc.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   std::vector<cplx> hg(N2);

@@ -127,6 +127,11 @@ void tconj_add(Launcher &L, int nb, cplx c, const cplx *Y, cplx *out);
 void herm_sum(Launcher &L, int nb, cplx c, const cplx *a, cplx *out);
 void real_dot_acc(Launcher &L, long long n, const cplx *x, const cplx *y, double coeff, double *partials, double *acc);
 void hf_build_t(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *x, cplx *out, bool accumulate);
+// Cotangent of w through the Hartree-Fock matrix Wm[(ij),(lk)] = w_ikjl + eta w_iklj given the
+// cotangent x of h^HF at the state n: wbar_abcd += c (x_ac conj(n_db) + eta x_ad conj(n_cb)).
+void hf_wbar(Launcher &L, int nb, const cplx *x, const cplx *n, double c, double eta, cplx *wbar);
+// out = projection of X onto the symmetries of w: (X + X_jilk + conj(X_klij) + conj(X_lkji)) / 4.
+void w_symmetrize(Launcher &L, int nb, const cplx *X, cplx *out);
 
 // Memory-integral HF-GKBA: out_b[m][i] = sum_p in_b[p][m] op(S_b[i][p]) for b < batch
 // (batch <= 65535, nb <= mode_rotate_max_nb()), m over the trailing nb^3 entries of the

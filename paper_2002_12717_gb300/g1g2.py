@@ -72,7 +72,7 @@ def load():
         "g1g2_launch_count": (ctypes.c_longlong, [vp]),
         "g1g2_rhs_vjp": (ctypes.c_int, [vp, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp]),
         "g1g2_adjoint": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
-                                        _dp]),
+                                        _dp, _dp]),
         "g1g2_wait_selftest": (ctypes.c_int, [ctypes.c_int]),
         "g1g2_fp64_rate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
         "g1g2_g1_rhs_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int] + [vp] * 6),
@@ -282,19 +282,22 @@ class Propagator:
         _check(self._lib.g1g2_rhs_vjp(self._ctx, float(t), ptr(n_dev), ptr(G2_dev), ptr(dn_bar), ptr(dG2_bar),
                                       ptr(n_bar), ptr(G2_bar), ptr(h_bar)))
 
-    def adjoint(self, dt, nsteps, objective=0, ckpt_every=0, n_drive_params=0):
-        """Discrete adjoint from the current state: (J, grad_drive, grad_wscale, grad_h).
+    def adjoint(self, dt, nsteps, objective=0, ckpt_every=0, n_drive_params=0, grad_w=False):
+        """Discrete adjoint from the current state: (J, grad_drive, grad_wscale, grad_h), and
+        grad_w (nb^4 complex, on the symmetric interactions) as a fifth entry when asked.
 
         objective 0: mean double occupancy, 1: density imbalance, 2: energy absorbed.
         """
         J = ctypes.c_double()
         gd = np.zeros(max(n_drive_params, 1))
-        gw = ctypes.c_double()
+        gws = ctypes.c_double()
         gh = np.zeros((self.nb, self.nb), dtype=np.complex128)
+        gw = np.zeros((self.nb,) * 4, dtype=np.complex128) if grad_w else None
         _check(self._lib.g1g2_adjoint(self._ctx, float(dt), int(nsteps), int(ckpt_every), int(objective),
-                                      ctypes.byref(J), _cptr(gd) if n_drive_params else None, ctypes.byref(gw),
-                                      _cptr(gh)))
-        return J.value, gd[:n_drive_params], gw.value, gh
+                                      ctypes.byref(J), _cptr(gd) if n_drive_params else None, ctypes.byref(gws),
+                                      _cptr(gh), None if gw is None else _cptr(gw)))
+        out = (J.value, gd[:n_drive_params], gws.value, gh)
+        return out + (gw,) if grad_w else out
 
     @property
     def hubbard_path(self):

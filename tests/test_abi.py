@@ -123,7 +123,7 @@ def test_adjoint_and_selftest_arguments_rejected_on_host(lib):
     k, w = ctypes.c_int(), ctypes.c_int()
     assert lib.g1g2_set_adjoint_checkpoints(None, 0) == g1g2.EINVAL
     assert lib.g1g2_adjoint_plan(None, ctypes.byref(k), ctypes.byref(w)) == g1g2.EINVAL
-    assert lib.g1g2_adjoint(None, 0.01, 10, 0, 0, None, None, None, None) == g1g2.EINVAL
+    assert lib.g1g2_adjoint(None, 0.01, 10, 0, 0, None, None, None, None, None) == g1g2.EINVAL
     assert lib.g1g2_wait_selftest(0) == g1g2.EINVAL
     assert lib.g1g2_wait_selftest(20000000) == g1g2.EINVAL
 
