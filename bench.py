@@ -48,6 +48,9 @@ TF32_OVER_BF16 = 1.1 / 2.25
 # workload), from one ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum, profiles/); missing entries report null.
 TRAFFIC = {}
+# sm__pipe_tensor_cycles_active (percent of peak, sustained over active cycles) of the
+# dominant kernel from the same capture; missing entries report null.
+TENSOR_PIPE = {}
 
 
 def load_peaks():
@@ -325,6 +328,7 @@ def run_ours(args, rank, world, dist):
                 "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_NOTE + " (measured DFMA)"}
         dom_tag = "fp64_zgemm (+ split-K): every complex contraction"
     roof.update({"traffic": TRAFFIC.get((dom_tag, dom_wl)) if args.precision == "bf16x4" else None,
+                 "tensor_pipe_active_pct": TENSOR_PIPE.get((dom_tag, dom_wl)) if args.precision == "bf16x4" else None,
                  "kernel": dom_tag, "workload": dom_wl,
                  "avg_launch_ms": avg_s * 1e3, "launches": dom_n, "share": t_ms / total_ms})
 
@@ -393,6 +397,66 @@ def adjoint_sample(args):
             "adjoint_over_forward": t_adj / t_fwd, "J": J, "J_forward": J_f,
             "dJ_dU": gws / U, "fd_dJ_dU": fd / U, "rel_diff_dJ_dU": abs(gws - fd) / abs(fd),
             "grad_controls_norm": float(np.linalg.norm(gd))}
+
+
+def adjoint_run(eps=1e-5):
+    """The discrete adjoint over the whole 4x4 Hubbard workload (32 spin-orbitals, U = 2,
+    64 piecewise-linear controls on [0, 10], 1000 steps of dt = 0.01, checkpoints every
+    32 steps), FP64 form: the gradient of the final mean double occupancy with respect to
+    the controls, the w scale (U dJ/dU), h and the entries of w, timed against the
+    forward propagation, and checked by central differences (eps) on three controls, on
+    U and on two perturbations of w with its symmetries (the on-site U of one site, and
+    a random dense one)."""
+    from paper_2002_12717_gb300.g1g2 import Propagator
+
+    d = inputs.workload("hubbard-2d-4x4")
+    steps, dt, k = d["nsteps"], d["dt"], 32
+    M = len(d["drive"].values)
+    nb = d["nb"]
+
+    def J_of(w=None, controls=None):
+        drv = d["drive"] if controls is None else inputs.PiecewiseLinear(controls, d["drive"].ta, d["drive"].tb)
+        with Propagator(d["h"], d["w"] if w is None else w, d["n0"], None, "SOA", "fp64") as p:
+            p.set_drive(d["D"], drv)
+            t0 = time.perf_counter()
+            p.propagate(dt, steps)
+            J = float(p.observables(double_occ=True)["double_occ"].mean())
+            return J, time.perf_counter() - t0
+
+    J_of()  # warm-up
+    J_f, t_fwd = J_of()
+    with Propagator(d["h"], d["w"], d["n0"], None, "SOA", "fp64") as p:
+        p.set_drive(d["D"], d["drive"])
+        t0 = time.perf_counter()
+        J, gd, gws, gh, gw = p.adjoint(dt, steps, objective=0, ckpt_every=k, n_drive_params=M, grad_w=True)
+        t_adj = time.perf_counter() - t0
+    rel = lambda a, b: abs(a - b) / max(abs(b), 1e-300)
+    checks = {}
+    vals = d["drive"].values
+    for m in (5, 31, 50):
+        vp, vm = vals.copy(), vals.copy()
+        vp[m] += eps
+        vm[m] -= eps
+        fd = (J_of(controls=vp)[0] - J_of(controls=vm)[0]) / (2 * eps)
+        checks[f"control_{m}"] = {"adjoint": float(gd[m]), "fd": fd, "rel_diff": rel(float(gd[m]), fd)}
+    fd = (J_of(w=d["w"] * (1 + eps))[0] - J_of(w=d["w"] * (1 - eps))[0]) / (2 * eps)
+    checks["wscale"] = {"adjoint": gws, "fd": fd, "rel_diff": rel(gws, fd)}
+    E1 = np.zeros((nb,) * 4)
+    for a in ((0, 1, 0, 1), (1, 0, 1, 0)):        # the on-site U of site 0 (spin-orbitals 0, 1)
+        E1[a] = 1.0
+    rng = np.random.default_rng(9)
+    E2 = rng.standard_normal((nb,) * 4)
+    E2 = E2 + E2.transpose(1, 0, 3, 2)
+    E2 = 0.01 * (E2 + E2.transpose(2, 3, 0, 1)) / 4
+    for name, E in (("w_onsite_site0", E1), ("w_random_symmetric", E2)):
+        fd = (J_of(w=d["w"] + eps * E)[0] - J_of(w=d["w"] - eps * E)[0]) / (2 * eps)
+        want = float((np.conj(gw) * E).real.sum())
+        checks[name] = {"adjoint": want, "fd": fd, "rel_diff": rel(want, fd)}
+    return {"workload": f"hubbard-2d-4x4 ({nb} spin-orbitals, U = 2, {M} controls, {steps} steps of dt = {dt})",
+            "objective": "mean double occupancy at t = 10", "ckpt_every": k, "precision": "fp64",
+            "J": J, "J_forward": J_f, "adjoint_s": t_adj, "forward_s": t_fwd, "adjoint_over_forward": t_adj / t_fwd,
+            "grad_controls_norm": float(np.linalg.norm(gd)), "grad_w_norm": float(np.linalg.norm(gw)),
+            "checks": checks, "max_rel_diff": max(c["rel_diff"] for c in checks.values())}
 
 
 def hubbard_scaling(sizes, steps=3, selfenergy="SOA"):
@@ -723,6 +787,9 @@ def main():
     ap.add_argument("--accuracy-every", type=int, default=50, help="record interval of --accuracy-run")
     ap.add_argument("--accuracy-out", default="gpurun_out/accuracy.jsonl", help="JSON-lines file of --accuracy-run")
     ap.add_argument("--oracle-rhs-times", default="", help=argparse.SUPPRESS)
+    ap.add_argument("--adjoint-run", action="store_true",
+                    help="the discrete adjoint over the whole 4x4 Hubbard workload with finite-difference checks, "
+                         "and exit")
     ap.add_argument("--adjoint-steps", type=int, default=100,
                     help="steps of the discrete-adjoint sample on the 4x4 Hubbard cluster (0: skip)")
     args = ap.parse_args()
@@ -737,6 +804,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.oracle_rhs_times:
         print(json.dumps(oracle_rhs_seconds(args.oracle_rhs_times.split(","))), flush=True)
+        return
+    if args.adjoint_run:
+        if rank == 0:
+            print(json.dumps({"adjoint_run": adjoint_run()}), flush=True)
         return
     if args.accuracy_run:
         if rank == 0:

@@ -43,11 +43,13 @@ constexpr int kConvThreads = 192;                  // warps 2-7
 constexpr int kEpiWarp0 = 8;                       // first epilogue warp
 constexpr int kSlices = 4;                         // BF16 slices per operand (sliced form)
 constexpr uint32_t kASliceBytes = kTileM * kBlockK * 2;  // 8 KB: one slice of an A tile, 64-byte rows
-constexpr uint32_t kSlicedBOff = kABytes + kSlices * kASliceBytes;  // 48 KB: B slices within a stage
+constexpr uint32_t kSlicedBOff = kSlices * kASliceBytes;  // 32 KB: B slices within a sliced MMA stage
 
-// shared memory of one pipeline stage
+// shared memory of one MMA stage: TF32 form the FP32 A tile, its lo part and B (hi, lo);
+// sliced form the four A slices and the four B slices (the FP32 A tiles land in a ring of
+// their own, kABytes per slot)
 __host__ __device__ constexpr uint32_t stage_bytes_for(bool sliced, int nout) {
-  return sliced ? kSlicedBOff + (uint32_t)kSlices * (uint32_t)nout * kBlockK * 2
+  return sliced ? (uint32_t)kSlices * kASliceBytes + (uint32_t)kSlices * (uint32_t)nout * kBlockK * 2
                 : 2 * kABytes + 2 * (uint32_t)nout * kBlockK * 4;
 }
 
@@ -98,8 +100,15 @@ struct GemmParams {
   int slice_lead;     // sliced form: leading-slice width L (slice_lead_for(K)); 0 means 7
   int col_il;         // B rows (output columns) ordered 2 l + v instead of v nb + l
   int out_il;         // EP_SWAP34 with col_il: interleaved complex FP32 output out[i][j][l][k]
+  int out_blk;        // out_il and EP_PI: that output in 4^4 blocks (blk4 of (i, j, l, k))
   int *out_amax;      // sliced form, optional: atomic max of |stored outputs| (FP32 bits)
 };
+
+// K coordinate (elements) and first row of the B tile of K block kb of a tile
+__device__ __forceinline__ void b_coords(const GemmParams &p, int tile, int kb, int &bk, int &brow) {
+  bk = (p.a_rows == AR_SPLITK) ? ((tile % p.splits) * p.kb_per_split + kb) * kBlockK : kb * kBlockK;
+  brow = (p.a_rows == AR_PI) ? (tile / p.pi_mtiles) * p.nout : 0;
+}
 
 __device__ __forceinline__ int tile_kblocks(const GemmParams &p, int tile) {
   if (p.a_rows == AR_SPLITK) {
@@ -114,28 +123,41 @@ __device__ __forceinline__ int tile_kblocks(const GemmParams &p, int tile) {
 
 // tmBhi/tmBlo: TF32 hi and lo parts of B; in the sliced form tmBhi holds the
 // four BF16 slices of B as [slice][row][k] (tmBlo unused).
+//
+// Pipeline.  TF32 form: `stages` stages, each filled by one TMA transaction (A and
+// B), converted in place, consumed by the MMAs.  Sliced form: the FP32 A tiles land
+// in a ring of `fstages` slots of their own, so that the TMA runs ahead of the
+// conversion by the depth of that ring; the converters take an MMA stage (one of
+// `stages`), have one of their threads load that K block's B slices into it, cut the
+// FP32 tile of the matching slot into the stage's A slices and release the slot.
 template <bool kSliced>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
-                   const GemmParams p, const int stages) {
+                   const GemmParams p, const int stages, const int fstages) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t b_bytes = kSliced ? (uint32_t)p.nout * kBlockK * 2 : (uint32_t)p.nout * kBlockK * 4;
   const uint32_t stage_bytes = stage_bytes_for(kSliced, p.nout);
+  const int nf = kSliced ? fstages : 0;
+  uint8_t *fring = smem;                                   // sliced form: FP32 A slots
+  uint8_t *stg = smem + (size_t)nf * kABytes;              // MMA stages
   // accumulator buffers: TF32 form two (double-buffered); sliced form a pair
   // (exact leading product, lower-order products) per buffer, two buffers when they fit
   const int nbuf = (!kSliced || p.nout <= 128) ? 2 : 1;
   const uint32_t d1_off = (nbuf == 2) ? 128u : 256u;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)stages * stage_bytes);
-  uint64_t *full = bars;
+  uint8_t *bar_area = stg + (size_t)stages * stage_bytes;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(bar_area);
+  uint64_t *full = bars;                // TF32: A and B landed; sliced: B landed
   uint64_t *conv = bars + stages;
   uint64_t *empty = bars + 2 * stages;
-  uint64_t *tfull = bars + 3 * stages;
+  uint64_t *ffull = bars + 3 * stages;  // sliced: FP32 A tile landed in slot
+  uint64_t *fempty = ffull + nf;        // sliced: slot read by the converters
+  uint64_t *tfull = fempty + nf;
   uint64_t *tempty = tfull + 2;
   uint64_t *fin = tempty + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
-  float2 *acc2 = reinterpret_cast<float2 *>(smem + (size_t)stages * stage_bytes + 256);  // (sum, error) pairs
+  float2 *acc2 = reinterpret_cast<float2 *>(bar_area + 256);  // (sum, error) pairs
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -143,6 +165,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&conv[s], kConvThreads);
       mbar_init(&empty[s], 1);
+    }
+    for (int f = 0; f < nf; ++f) {
+      mbar_init(&ffull[f], 1);
+      mbar_init(&fempty[f], kConvThreads);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -166,42 +192,46 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
         const int nkb = tile_kblocks(p, tile);
         for (int kb = 0; kb < nkb; ++kb) {
-          if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
-          uint8_t *st = smem + (size_t)s * stage_bytes;
-          mbar_arrive_expect_tx(&full[s], kABytes + (kSliced ? kSlices : 2) * b_bytes);
-          int bk;  // K coordinate (floats) of this block in B
+          // the A tile goes to the FP32 slot (sliced) or to the MMA stage (TF32)
+          uint8_t *dst;
+          uint64_t *bar;
+          if (kSliced) {
+            if (!mbar_wait(&fempty[s], ph ^ 1u, p.err)) { ok = false; break; }
+            dst = fring + (size_t)s * kABytes;
+            bar = &ffull[s];
+            mbar_arrive_expect_tx(bar, kABytes);
+          } else {
+            if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
+            dst = stg + (size_t)s * stage_bytes;
+            bar = &full[s];
+            mbar_arrive_expect_tx(bar, kABytes + 2 * b_bytes);
+          }
           if (p.a_rows == AR_LINEAR) {
             const bool second = p.kb_first && kb >= p.kb_first;
             const int kl = second ? kb - p.kb_first : kb;
             const int u = kl / p.kb_per_plane, pb = kl % p.kb_per_plane;
-            tma_load_3d(st, second ? &tmA2 : &tmA, &full[s], pb * kBlockK, tile * kTileM, u);
-            bk = kb * kBlockK;
+            tma_load_3d(dst, second ? &tmA2 : &tmA, bar, pb * kBlockK, tile * kTileM, u);
           } else if (p.a_rows == AR_GATHER4) {
             const int u = kb / p.kb_per_plane, pb = kb % p.kb_per_plane;
             const int bB = tile % p.g_nb, aB = (tile / p.g_nb) % p.g_na, c = tile / (p.g_nb * p.g_na);
-            tma_load_5d(st, &tmA, &full[s], pb * kBlockK, c, bB * 32, aB * 4, u);
-            bk = kb * kBlockK;
+            tma_load_5d(dst, &tmA, bar, pb * kBlockK, c, bB * 32, aB * 4, u);
           } else if (p.a_rows == AR_PI) {
             const int mt = tile % p.pi_mtiles;
             const int kB = mt % p.pi_mk, iB = mt / p.pi_mk;
             const int qb = kb % p.pi_kq, rest = kb / p.pi_kq;
             const int pp = rest % N, u = rest / N;
-            tma_load_5d(st, &tmA, &full[s], qb * kBlockK, kB * 32, pp, iB * 4, u);
-            bk = kb * kBlockK;
+            tma_load_5d(dst, &tmA, bar, qb * kBlockK, kB * 32, pp, iB * 4, u);
           } else {
             const int u = tile / p.splits, split = tile % p.splits;
-            const int kglob = (split * p.kb_per_split + kb) * kBlockK;
-            tma_load_3d(st, &tmA, &full[s], kglob, 0, u);
-            bk = kglob;
+            tma_load_3d(dst, &tmA, bar, (split * p.kb_per_split + kb) * kBlockK, 0, u);
           }
-          const int brow = (p.a_rows == AR_PI) ? (tile / p.pi_mtiles) * p.nout : 0;
-          if (kSliced) {
-            tma_load_3d(st + kSlicedBOff, &tmBhi, &full[s], bk, brow, 0);  // all four slices
-          } else {
-            tma_load_3d(st + 2 * kABytes, &tmBhi, &full[s], bk, brow, 0);
-            tma_load_3d(st + 2 * kABytes + b_bytes, &tmBlo, &full[s], bk, brow, 0);
+          if (!kSliced) {
+            int bk, brow;
+            b_coords(p, tile, kb, bk, brow);
+            tma_load_3d(dst + 2 * kABytes, &tmBhi, bar, bk, brow, 0);
+            tma_load_3d(dst + 2 * kABytes + b_bytes, &tmBlo, bar, bk, brow, 0);
           }
-          if (++s == stages) { s = 0; ph ^= 1u; }
+          if (++s == (kSliced ? nf : stages)) { s = 0; ph ^= 1u; }
         }
       }
     }
@@ -228,11 +258,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kAccCols);
           const uint32_t first = p.kb_chunks ? (uint32_t)(kb % p.kb_chunks) : (uint32_t)kb;
           if (!mbar_wait(&conv[s], ph, p.err)) { ok = false; break; }
+          if (kSliced && !mbar_wait(&full[s], ph, p.err)) { ok = false; break; }   // B slices landed
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
+          const uint32_t sa = smem_u32(stg + (size_t)s * stage_bytes);
           if (kSliced) {
-            // slice s of A at sa + kABytes + s * kASliceBytes, of B at sa + kSlicedBOff + s * b_bytes
-            const uint32_t as0 = sa + kABytes, bs0 = sa + kSlicedBOff;
+            // slice q of A at sa + q * kASliceBytes, of B at sa + kSlicedBOff + q * b_bytes
+            const uint32_t as0 = sa, bs0 = sa + kSlicedBOff;
 #pragma unroll
             for (int k = 0; k < kBlockK / 16; ++k) {
               uint64_t ad[kSlices], bd[kSlices];
@@ -295,13 +326,29 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 #pragma unroll
       for (int q = 0; q < kSlices; ++q) cut2[q] = splat_f32x2(ldexpf(1.5f, 23 + E - Ld - 8 * q));
     }
+    int f = 0;
+    uint32_t fph = 0;
     for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
       const int nkb = tile_kblocks(p, tile);
       for (int kb = 0; kb < nkb; ++kb) {
-        if (!mbar_wait(&full[s], ph, p.err)) { ok = false; break; }
-        float4 *a = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes);
+        float4 *a;
         if (kSliced) {
-          uint8_t *sl = smem + (size_t)s * stage_bytes + kABytes;
+          // take the MMA stage, start its B load, then wait for the FP32 A tile
+          if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
+          if (ct == 0) {
+            int bk, brow;
+            b_coords(p, tile, kb, bk, brow);
+            mbar_arrive_expect_tx(&full[s], kSlices * b_bytes);
+            tma_load_3d(stg + (size_t)s * stage_bytes + kSlicedBOff, &tmBhi, &full[s], bk, brow, 0);
+          }
+          if (!mbar_wait(&ffull[f], fph, p.err)) { ok = false; break; }
+          a = reinterpret_cast<float4 *>(fring + (size_t)f * kABytes);
+        } else {
+          if (!mbar_wait(&full[s], ph, p.err)) { ok = false; break; }
+          a = reinterpret_cast<float4 *>(stg + (size_t)s * stage_bytes);
+        }
+        if (kSliced) {
+          uint8_t *sl = stg + (size_t)s * stage_bytes;
 #pragma unroll 2
           for (int i = ct; i < (int)(kABytes / 16); i += kConvThreads) {
             // 16-byte chunk i of the 128-byte-swizzled FP32 tile: row r, logical floats k0..k0+3
@@ -321,7 +368,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             }
           }
         } else {
-          float4 *lo = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes + kABytes);
+          float4 *lo = reinterpret_cast<float4 *>(stg + (size_t)s * stage_bytes + kABytes);
 #pragma unroll 4
           for (int i = ct; i < (int)(kABytes / 16); i += kConvThreads) {
             const float4 x = a[i];
@@ -337,6 +384,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         fence_proxy_async_smem();
         mbar_arrive(&conv[s]);
         if (++s == stages) { s = 0; ph ^= 1u; }
+        if (kSliced) {
+          mbar_arrive(&fempty[f]);   // the FP32 slot may be refilled
+          if (++f == nf) { f = 0; fph ^= 1u; }
+        }
       }
     }
   } else {
@@ -475,7 +526,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             if (j >= nv || cg >= p.rows) break;
             const long long jl = cg >> 1;
             const long long jj = jl / NN, ll = jl - jj * NN;
-            o[((i0 * NN + jj) * NN + ll) * NN + i2] = make_float2(v[j], v[j + 1]);
+            o[p.out_blk ? blk4(NN, i0, jj, ll, i2) : ((i0 * NN + jj) * NN + ll) * NN + i2] =
+                make_float2(v[j], v[j + 1]);
           }
         } else if (p.out_il) {
           // col_il columns (2 l, 2 l + 1) -> one interleaved complex value
@@ -484,7 +536,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           for (int j = 0; j < 32; j += 2) {
             if (j >= nv) break;
             const int l = (c0 + j) >> 1;
-            o[l * cs] = make_float2(v[j], v[j + 1]);
+            if (p.out_blk)
+              reinterpret_cast<float2 *>(p.out)[blk4(NN, i0, i1, l, i2)] = make_float2(v[j], v[j + 1]);
+            else
+              o[l * cs] = make_float2(v[j], v[j + 1]);
             if (kSliced) mx = fmaxf(mx, fmaxf(fabsf(v[j]), fabsf(v[j + 1])));
           }
         } else if (p.col_il) {

@@ -280,83 +280,83 @@ __global__ void realify_pi_kernel(int nb, int kpad, const float *__restrict__ Y1
   }
 }
 
-// Per-column maxima of the polarisation GEMM's B operand: colmax[j nb + l] = max over
-// (q, p) of the larger component of hcorr_qjpl = Y1_qjpl - Y2_plqj (FP32 bits, atomic max),
-// so that every column (j, l, v) of B gets its own slice exponent.  One CTA per (j, l)
-// and 32 x 32 tile of (p, q), read along p for Y1 and along q for Y2.
-__global__ void hcorr_colmax_kernel(int nb, const float *__restrict__ Y1s, const float *__restrict__ Y2s,
-                                    long long P, int *colmax) {
-  __shared__ float2 t1[32][33];
-  const long long N = nb;
-  const long long jl = blockIdx.y;
-  const long long j = jl / N, l = jl % N;
-  const int nt = (nb + 31) / 32;
-  const int p0 = (blockIdx.x / nt) * 32, q0 = (blockIdx.x % nt) * 32;
-  const int tx = threadIdx.x, ty0 = threadIdx.y;
-  for (int ty = ty0; ty < 32; ty += blockDim.y) {
-    const int q = q0 + ty, pp = p0 + tx;
-    float2 v = make_float2(0.f, 0.f);
-    if (q < nb && pp < nb) {
-      const long long g = ((q * N + j) * N + l) * N + pp;   // Y1_{q j p l} at [q][j][l][p]
-      v = make_float2(Y1s[g], Y1s[P + g]);
-    }
-    t1[ty][tx] = v;
-  }
-  __syncthreads();
-  float mx = 0.f;
-  for (int ty = ty0; ty < 32; ty += blockDim.y) {
-    const int pp = p0 + ty, q = q0 + tx;
-    if (pp < nb && q < nb) {
-      const long long g = ((pp * N + l) * N + j) * N + q;   // Y2_{p l q j} at [p][l][j][q]
-      const float2 a = t1[tx][ty];
-      mx = fmaxf(mx, fmaxf(fabsf(a.x - Y2s[g]), fabsf(a.y - Y2s[P + g])));
-    }
-  }
-  block_amax(mx, colmax + jl);
-}
-
 // B operand of the polarisation GEMM (tc_pi_gemm_kernel): rows (j, l, v) interleaved as
 // 2 (j nb + l) + v, K = (u, p, q) as (u nb + p) nb + q, value R(hcorr_qjpl)[u][v] (the
-// real 2 x 2 block [[Re, Im], [-Im, Re]] of the complex product), as three BF16 slices
-// [slice][row][K] with the exponent of the column's maximum colmax[j nb + l].  Same
-// tiling as hcorr_colmax_kernel.
-__global__ void realify_pi_slice3_kernel(int nb, const float *__restrict__ Y1s, const float *__restrict__ Y2s,
-                                         long long P, const int *__restrict__ colmax, __nv_bfloat16 *out,
-                                         long long slice_stride) {
+// real 2 x 2 block [[Re, Im], [-Im, Re]] of the complex product) with
+// hcorr_qjpl = Y1_qjpl - Y2_plqj (Y1 = w x_4 n, Y2 = w x_4 n^T in the swapped layout
+// [a][b][d][c]), as three BF16 slices [slice][row][K] with one exponent per column (j, l):
+// that of max over (p, q) of the larger component of hcorr_qjpl.  One CTA per (j, l):
+// a first sweep over the 32 x 32 tiles of (p, q) takes the maximum, a second one (its
+// reads served from L2) slices; Y1 is read along p and Y2 along q, transposed in shared
+// memory.
+__global__ void __launch_bounds__(256) realify_pi_slice3_kernel(int nb, const float *__restrict__ Y1s,
+                                                                const float *__restrict__ Y2s, long long P,
+                                                                __nv_bfloat16 *out, long long slice_stride) {
   __shared__ float2 t1[32][33];
+  __shared__ float red[8];
   const long long N = nb, K = 2 * N * N;
-  const long long jl = blockIdx.y;
+  const long long jl = blockIdx.x;
   const long long j = jl / N, l = jl % N;
   const int nt = (nb + 31) / 32;
-  const int p0 = (blockIdx.x / nt) * 32, q0 = (blockIdx.x % nt) * 32;
-  const int tx = threadIdx.x, ty0 = threadIdx.y;
-  const int E = slice_exponent(colmax[jl]);
-  for (int ty = ty0; ty < 32; ty += blockDim.y) {
-    const int q = q0 + ty, pp = p0 + tx;
-    float2 v = make_float2(0.f, 0.f);
-    if (q < nb && pp < nb) {
-      const long long g = ((q * N + j) * N + l) * N + pp;   // Y1_{q j p l} at [q][j][l][p]
-      v = make_float2(Y1s[g], Y1s[P + g]);
-    }
-    t1[ty][tx] = v;
-  }
-  __syncthreads();
-  for (int ty = ty0; ty < 32; ty += blockDim.y) {
-    const int pp = p0 + ty, q = q0 + tx;
-    if (pp >= nb || q >= nb) continue;
-    const long long g = ((pp * N + l) * N + j) * N + q;     // Y2_{p l q j} at [p][l][j][q]
-    const float2 a = t1[tx][ty];
-    const float2 h = make_float2(a.x - Y2s[g], a.y - Y2s[P + g]);
-    for (int u = 0; u < 2; ++u)
-      for (int v = 0; v < 2; ++v) {
-        const float x = (u == 0) ? (v ? h.y : h.x) : (v ? h.x : -h.y);
-        const long long row = 2 * jl + v;
-        const long long col = ((long long)u * N + pp) * N + q;
-        float sl[3];
-        slice3_lead8(x, E, sl);
-#pragma unroll
-        for (int z = 0; z < 3; ++z) out[z * slice_stride + row * K + col] = __float2bfloat16_rn(sl[z]);
+  const int tx = threadIdx.x & 31, ty0 = threadIdx.x >> 5;
+  auto load_tile = [&](int p0, int q0) {
+    for (int ty = ty0; ty < 32; ty += 8) {
+      const int q = q0 + ty, pp = p0 + tx;
+      float2 v = make_float2(0.f, 0.f);
+      if (q < nb && pp < nb) {
+        const long long g = ((q * N + j) * N + l) * N + pp;   // Y1_{q j p l} at [q][j][l][p]
+        v = make_float2(Y1s[g], Y1s[P + g]);
       }
+      t1[ty][tx] = v;
+    }
+  };
+  auto hval = [&](int pp, int q, int ty) {   // hcorr_qjpl (after load_tile and a barrier)
+    const long long g = ((pp * N + l) * N + j) * N + q;       // Y2_{p l q j} at [p][l][j][q]
+    const float2 a = t1[tx][ty];
+    return make_float2(a.x - Y2s[g], a.y - Y2s[P + g]);
+  };
+  float mx = 0.f;
+  for (int tile = 0; tile < nt * nt; ++tile) {
+    const int p0 = (tile / nt) * 32, q0 = (tile % nt) * 32;
+    __syncthreads();
+    load_tile(p0, q0);
+    __syncthreads();
+    for (int ty = ty0; ty < 32; ty += 8) {
+      const int pp = p0 + ty, q = q0 + tx;
+      if (pp < nb && q < nb) {
+        const float2 h = hval(pp, q, ty);
+        mx = fmaxf(mx, fmaxf(fabsf(h.x), fabsf(h.y)));
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (tx == 0) red[ty0] = mx;
+  __syncthreads();
+  mx = red[0];
+  for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
+  float cut[3];
+  cuts3_lead8(slice_exponent(__float_as_int(mx)), cut);
+  for (int tile = 0; tile < nt * nt; ++tile) {
+    const int p0 = (tile / nt) * 32, q0 = (tile % nt) * 32;
+    __syncthreads();
+    load_tile(p0, q0);
+    __syncthreads();
+    for (int ty = ty0; ty < 32; ty += 8) {
+      const int pp = p0 + ty, q = q0 + tx;
+      if (pp >= nb || q >= nb) continue;
+      const float2 h = hval(pp, q, ty);
+      for (int u = 0; u < 2; ++u)
+        for (int v = 0; v < 2; ++v) {
+          const float x = (u == 0) ? (v ? h.y : h.x) : (v ? h.x : -h.y);
+          const long long row = 2 * jl + v;
+          const long long col = ((long long)u * N + pp) * N + q;
+          float sl[3];
+          slice3(x, cut, sl);
+#pragma unroll
+          for (int z = 0; z < 3; ++z) out[z * slice_stride + row * K + col] = __float2bfloat16_rn(sl[z]);
+        }
+    }
   }
 }
 
@@ -371,14 +371,20 @@ __global__ void realify_lam_slice3_kernel(int nb, const float *__restrict__ P1s,
                                           long long P, const int *__restrict__ colmax, __nv_bfloat16 *out,
                                           long long slice_stride) {
   __shared__ float2 t1[32][33];
-  __shared__ int se[32];
+  __shared__ float sc[32][3];
   const long long N = nb, K = 2 * N * N;
   const long long pc = blockIdx.y;
   const long long p = pc / N, c = pc % N;
   const int ntd = (nb + 31) / 32;
   const int q0 = (blockIdx.x / ntd) * 32, d0 = (blockIdx.x % ntd) * 32;
   const int tx = threadIdx.x, ty0 = threadIdx.y;
-  if (ty0 == 0) se[tx] = (d0 + tx < nb) ? slice_exponent(colmax[c * N + d0 + tx]) : 0;
+  if (ty0 == 0) {
+    float cu[3];
+    cuts3_lead8((d0 + tx < nb) ? slice_exponent(colmax[c * N + d0 + tx]) : 0, cu);
+    sc[tx][0] = cu[0];
+    sc[tx][1] = cu[1];
+    sc[tx][2] = cu[2];
+  }
   for (int ty = ty0; ty < 32; ty += blockDim.y) {
     const int q = q0 + ty, d = d0 + tx;
     float2 v = make_float2(0.f, 0.f);
@@ -393,14 +399,14 @@ __global__ void realify_lam_slice3_kernel(int nb, const float *__restrict__ P1s,
     const int d = d0 + ty, q = q0 + tx;
     if (d >= nb || q >= nb) continue;
     const float2 h = t1[tx][ty];
-    const int E = se[ty];
+    const float cu[3] = {sc[ty][0], sc[ty][1], sc[ty][2]};
     for (int u = 0; u < 2; ++u)
       for (int v = 0; v < 2; ++v) {
         const float x = (u == 0) ? (v ? h.y : h.x) : (v ? h.x : -h.y);
         const long long row = 2 * (c * N + d) + v;
         const long long col = ((long long)u * N + p) * N + q;
         float sl[3];
-        slice3_lead8(x, E, sl);
+        slice3(x, cu, sl);
 #pragma unroll
         for (int z = 0; z < 3; ++z) out[z * slice_stride + row * K + col] = __float2bfloat16_rn(sl[z]);
       }
@@ -495,13 +501,14 @@ __global__ void a_rowmax_kernel(int nb, const float *__restrict__ G, long long P
 }
 
 // Three BF16 slices [slice][row][K] of the A operand (see AOperand) with the exponent of
-// each row's maximum rowmax[row] and a 9-bit leading slice (slice3_lead8).  One CTA
-// (32 x 8 threads) per (a, 32-row block of b) and (u, p): a 32 x 32 tile of (b, q) is read
-// along the contiguous index, kept in shared memory and written along q.
+// each row's maximum rowmax[row] and a 9-bit leading slice (slice3).  One CTA (32 x 8
+// threads) per (a, 32-row block of b) and (u, p): a 32 x 32 tile of (b, q) is read along
+// the contiguous index into shared memory; each thread then cuts two adjacent q of one row
+// and stores them as BF16 pairs.
 __global__ void a_slice3_kernel(int nb, const float *__restrict__ G, long long P, AOperand m,
                                 const int *__restrict__ rowmax, __nv_bfloat16 *out, long long slice_stride) {
-  __shared__ float t[32][33];
-  __shared__ int se[32];
+  __shared__ float t[32][34];
+  __shared__ float sc[32][3];
   const long long N = nb, K = 2 * N * N;
   const int nbt = (nb + 31) / 32;
   const long long a = blockIdx.x / nbt;
@@ -509,7 +516,14 @@ __global__ void a_slice3_kernel(int nb, const float *__restrict__ G, long long P
   const int u = blockIdx.y / nb, pp = blockIdx.y % nb;
   const bool b_fast = m.sB == 1;
   const float *base = G + u * P + a * m.sA + pp * m.sP;
-  if (threadIdx.y == 0) se[threadIdx.x] = (b0 + (int)threadIdx.x < nb) ? slice_exponent(rowmax[a * N + b0 + threadIdx.x]) : 0;
+  if (threadIdx.y == 0) {
+    float cu[3];
+    cuts3_lead8((b0 + (int)threadIdx.x < nb) ? slice_exponent(rowmax[a * N + b0 + threadIdx.x]) : 0, cu);
+    sc[threadIdx.x][0] = cu[0];
+    sc[threadIdx.x][1] = cu[1];
+    sc[threadIdx.x][2] = cu[2];
+  }
+  const int qp = threadIdx.x & 15, rsub = threadIdx.x >> 4;   // q pair, row within the warp's pair
   for (int q0 = 0; q0 < nb; q0 += 32) {
     __syncthreads();
     for (int ty = threadIdx.y; ty < 32; ty += 8) {
@@ -520,14 +534,17 @@ __global__ void a_slice3_kernel(int nb, const float *__restrict__ G, long long P
       else t[ty][threadIdx.x] = x;
     }
     __syncthreads();
-    for (int ty = threadIdx.y; ty < 32; ty += 8) {
-      const int b = b0 + ty, q = q0 + threadIdx.x;
-      if (b >= nb || q >= nb) continue;
-      float sl[3];
-      slice3_lead8(t[ty][threadIdx.x], se[ty], sl);
+    for (int rb = 2 * threadIdx.y + rsub; rb < 32; rb += 16) {
+      const int b = b0 + rb, q = q0 + 2 * qp;
+      if (b >= nb || q >= nb) continue;   // nb % 4 == 0: q and q + 1 are both in range
+      const float cu[3] = {sc[rb][0], sc[rb][1], sc[rb][2]};
+      float s0[3], s1[3];
+      slice3(t[rb][2 * qp], cu, s0);
+      slice3(t[rb][2 * qp + 1], cu, s1);
       const long long o = (a * N + b) * K + ((long long)u * N + pp) * N + q;
 #pragma unroll
-      for (int z = 0; z < 3; ++z) out[z * slice_stride + o] = __float2bfloat16_rn(sl[z]);
+      for (int z = 0; z < 3; ++z)
+        *reinterpret_cast<__nv_bfloat162 *>(out + z * slice_stride + o) = __floats2bfloat162_rn(s0[z], s1[z]);
     }
   }
 }
@@ -551,7 +568,7 @@ __global__ void sub_rot_kernel(int nb, const float2 *__restrict__ Lam, float2 *Q
   for (int ty = ty0; ty < 32; ty += blockDim.y) {
     const int c = c0 + ty, d = d0 + tx;
     if (c < nb && d < nb) {
-      float2 *o = Q + ((a * N + b) * N + c) * N + d;
+      float2 *o = Q + blk4(N, a, b, c, d);
       const float2 l = t1[tx][ty];
       *o = make_float2(o->x - l.x, o->y - l.y);
     }
@@ -577,7 +594,7 @@ __global__ void sub_swap13_kernel(int nb, const float2 *__restrict__ Lam, float2
   for (int ty = ty0; ty < 32; ty += blockDim.y) {
     const int b = b0 + ty, d = d0 + tx;
     if (b < nb && d < nb) {
-      float2 *o = Q + ((a * N + b) * N + c) * N + d;
+      float2 *o = Q + blk4(N, a, b, c, d);
       const float2 l = t1[tx][ty];
       *o = make_float2(o->x - l.x, o->y - l.y);
     }
@@ -587,10 +604,10 @@ __global__ void sub_swap13_kernel(int nb, const float2 *__restrict__ Lam, float2
 struct AsmParams {
   int nb, nblk;
   const int4 *blocks;
-  const float *Z, *Q, *Pi;     // interleaved complex FP32, swapped layout
+  const float *Z, *Q, *Pi;     // interleaved complex FP32, swapped layout in 4^4 blocks (blk4)
   long long P;                 // plane stride of ys and y32
   cplx *y;                     // FP64 state (interleaved)
-  float *acc;                  // interleaved complex FP32
+  float *acc;                  // interleaved complex FP32 in 4^4 blocks (blk4)
   float *ys;                   // planar FP32 stage input of the next stage
   float *y32;                  // planar FP32 copy of y (stage 3)
   cplx *kout;                  // write-k mode
@@ -653,9 +670,8 @@ __global__ void __launch_bounds__(ATHREADS, 4) orbit_assemble_kernel(const AsmPa
     for (int t = 0; t < APER; ++t) {
       int a, b, c, d;
       elem(threadIdx.x + ATHREADS * t, a, b, c, d);
-      // stored (swapped) element of block (X0, X1, X3, X2): natural in-block index (a, b, d, c)
-      const long long gs = (((X[m][0] * BSZ + a) * N + X[m][1] * BSZ + b) * N + X[m][3] * BSZ + c) * N +
-                           X[m][2] * BSZ + d;
+      // stored (swapped, 4^4-blocked) element of block (X0, X1, X3, X2): natural in-block index (a, b, d, c)
+      const long long gs = blk4(N, X[m][0] * BSZ + a, X[m][1] * BSZ + b, X[m][3] * BSZ + c, X[m][2] * BSZ + d);
       const float2 z = reinterpret_cast<const float2 *>(p.Z)[gs];
       const float2 q = reinterpret_cast<const float2 *>(p.Q)[gs];
       float2 v = make_float2(z.x - 0.5f * q.x, z.y - 0.5f * q.y);
@@ -668,7 +684,8 @@ __global__ void __launch_bounds__(ATHREADS, 4) orbit_assemble_kernel(const AsmPa
       const long long gn = (((X[m][0] * BSZ + a) * N + X[m][1] * BSZ + b) * N + X[m][2] * BSZ + c) * N +
                            X[m][3] * BSZ + d;
       y0[m][t] = rk && !dup[m] ? p.y[gn] : make_double2(0.0, 0.0);
-      ac[m][t] = acc_in && !dup[m] ? reinterpret_cast<const float2 *>(p.acc)[gn] : make_float2(0.f, 0.f);
+      const long long gb = blk4(N, X[m][0] * BSZ + a, X[m][1] * BSZ + b, X[m][2] * BSZ + c, X[m][3] * BSZ + d);
+      ac[m][t] = acc_in && !dup[m] ? reinterpret_cast<const float2 *>(p.acc)[gb] : make_float2(0.f, 0.f);
     }
   __syncthreads();
   float2 kx[APER], ky[APER];
@@ -717,7 +734,9 @@ __global__ void __launch_bounds__(ATHREADS, 4) orbit_assemble_kernel(const AsmPa
       } else if (p.stage < 3) {
         const double h = (p.stage == 2) ? dt : 0.5 * dt;
         const float w = (p.stage == 0) ? 1.f : 2.f;
-        reinterpret_cast<float2 *>(accv)[g] = make_float2(ac[m][t].x + w * k.x, ac[m][t].y + w * k.y);
+        reinterpret_cast<float2 *>(accv)[blk4(N, X[m][0] * BSZ + a, X[m][1] * BSZ + b, X[m][2] * BSZ + c,
+                                              X[m][3] * BSZ + d)] =
+            make_float2(ac[m][t].x + w * k.x, ac[m][t].y + w * k.y);
         const float sx = (float)(y0[m][t].x + h * k.x), sy = (float)(y0[m][t].y + h * k.y);
         ysv[g] = sx;
         ysv[P + g] = sy;
@@ -868,13 +887,21 @@ int talloc(TcPath *p, T **ptr, size_t count) {
   return G1G2_OK;
 }
 
-// dynamic shared memory of one GEMM CTA; acc64_bytes > 0 adds the FP64 split-K accumulator
-size_t gemm_smem(bool sliced, int nout, int *stages, size_t acc64_bytes = 0) {
+// dynamic shared memory of one GEMM CTA; acc64_bytes > 0 adds the FP64 split-K accumulator.
+// TF32 form: up to 4 stages.  Sliced form: 2 MMA stages and as many FP32 A slots (2..6)
+// as the rest of the budget holds.
+size_t gemm_smem(bool sliced, int nout, int *stages, int *fstages, size_t acc64_bytes = 0) {
   const size_t stage = stage_bytes_for(sliced, nout);
   const size_t budget = 224 * 1024 - acc64_bytes;
+  if (sliced) {
+    *stages = 2;
+    *fstages = (int)std::max<size_t>(2, std::min<size_t>(6, (budget - std::min(budget, 2 * stage)) / kABytes));
+    return 1024 + 2 * stage + (size_t)*fstages * kABytes + 256 + acc64_bytes;
+  }
   int s = (int)std::min<size_t>(4, budget / stage);
   if (s < 2) s = 2;
   *stages = s;
+  *fstages = 0;
   return 1024 + s * stage + 256 + acc64_bytes;
 }
 
@@ -882,15 +909,15 @@ size_t gemm_smem(bool sliced, int nout, int *stages, size_t acc64_bytes = 0) {
 void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, const CUtensorMap &Bh,
                  const CUtensorMap &Bl, GemmParams gp, bool sliced = false, const CUtensorMap *A2 = nullptr) {
   gp.err = t->err;
-  int stages = 0;
+  int stages = 0, fstages = 0;
   const size_t acc64 = gp.kb_chunks ? (size_t)gp.nb * (gp.n_valid + 1) * sizeof(float2) : 0;
-  const size_t smem = gemm_smem(sliced, gp.nout, &stages, acc64);
+  const size_t smem = gemm_smem(sliced, gp.nout, &stages, &fstages, acc64);
   const int grid = std::max(1, std::min(gp.tiles, t->sms));
   L.before(tag);
   if (sliced) {
-    tc_gemm_kernel<true><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
+    tc_gemm_kernel<true><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages, fstages);
   } else {
-    tc_gemm_kernel<false><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages);
+    tc_gemm_kernel<false><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages, fstages);
   }
   L.after_launch();
 }
@@ -1147,10 +1174,10 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
     set_error_detail("cuTensorMapEncodeTiled failed");
     return bail(rc);
   }
-  int st = 0;
+  int st = 0, fst = 0;
   const size_t acc64 = (size_t)nb * (nb + 1) * sizeof(float2);
-  size_t smax = std::max(gemm_smem(sliced, t->nout2, &st), gemm_smem(sliced, t->nout1, &st, acc64));
-  if (big) smax = std::max(smax, gemm_smem(sliced, t->pi_nout, &st));
+  size_t smax = std::max(gemm_smem(sliced, t->nout2, &st, &fst), gemm_smem(sliced, t->nout1, &st, &fst, acc64));
+  if (big && !sliced) smax = std::max(smax, gemm_smem(sliced, t->pi_nout, &st, &fst));
   if (smax > 227 * 1024) {
     set_error_detail("basis too large for the FP64 split-K accumulator of the tensor-core collision integral");
     return bail(G1G2_EUNSUPPORTED);
@@ -1244,8 +1271,9 @@ namespace {
 // out = A B^T for one nb^2 x nb^2 x nb^2 product of the sliced form: the A operand read from
 // the planar FP32 state G32 through m, its per-row maxima and three BF16 slices, then
 // tc_pi_gemm_kernel against the B slices already in pb_s (out in the layout
-// out[a][c][d][b], complex).
-void sliced_product(TcPath *t, Launcher &L, const float *G32, AOperand m, float *out, const char *tag) {
+// out[a][c][d][b], complex; in 4^4 blocks with out_blk).
+void sliced_product(TcPath *t, Launcher &L, const float *G32, AOperand m, float *out, const char *tag,
+                    bool out_blk = false) {
   const int nb = t->nb;
   const long long N = nb, K = 2 * N * N;
   const int nbt = (nb + 31) / 32;
@@ -1266,6 +1294,7 @@ void sliced_product(TcPath *t, Launcher &L, const float *G32, AOperand m, float 
   g.mtiles = (g.M + kPiTileM - 1) / kPiTileM;
   g.tiles = g.mtiles * ((g.ncols + kPiTileN - 1) / kPiTileN);
   g.out = reinterpret_cast<float2 *>(out);
+  g.out_blk = out_blk ? 1 : 0;
   g.err = t->err;
   const int grid = std::max(1, std::min(g.tiles, t->sms));
   L.before(tag);
@@ -1385,6 +1414,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   auto il = [](GemmParams g, bool out_il) {
     g.col_il = 1;
     g.out_il = out_il ? 1 : 0;
+    g.out_blk = out_il ? 1 : 0;   // the assembly's inputs Z and Q: 4^4 blocks
     return g;
   };
   launch_gemm(t, L, "tc_gemm_psi3", t->mBuf2Lin, sl ? t->mBnb_s : t->mBnb_hi, t->mBnb_lo,
@@ -1404,18 +1434,13 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
                 lp(N3, 1, EP_SWAP34, t->Y2, wh_slot, kAmaxH2), sl);
     if (sl) {
       // B = R(hcorr) as three BF16 slices with per-column exponents, then the product
-      const int nt = (nb + 31) / 32;
-      const dim3 bgrid((unsigned)(nt * nt), (unsigned)(N * N));
-      cudaMemsetAsync(t->colmax, 0, N * N * sizeof(int), L.stream);
-      L.before("tc_pi_b_colmax");
-      hcorr_colmax_kernel<<<bgrid, dim3(32, 8), 0, L.stream>>>(nb, t->Y1, t->Y2, t->N4, t->colmax);
-      L.after_launch();
       L.before("tc_pi_b_slices");
-      realify_pi_slice3_kernel<<<bgrid, dim3(32, 8), 0, L.stream>>>(nb, t->Y1, t->Y2, t->N4, t->colmax, t->pb_s,
-                                                                     4 * N * N * N * N);
+      realify_pi_slice3_kernel<<<(unsigned)(N * N), 256, 0, L.stream>>>(nb, t->Y1, t->Y2, t->N4, t->pb_s,
+                                                                         4 * N * N * N * N);
       L.after_launch();
       // a6: Pi_(ik),(jl) = sum_(pq) G_ipkq hcorr_qjpl, rows (i, k) of G_ipkq
-      sliced_product(t, L, from_y ? t->y32 : t->ys32, AOperand{N * N * N, N, N * N, 1}, t->Pi, "tc_gemm_pi");
+      sliced_product(t, L, from_y ? t->y32 : t->ys32, AOperand{N * N * N, N, N * N, 1}, t->Pi, "tc_gemm_pi",
+                     true);
     } else {
       const dim3 pgrid((unsigned)(((nb + 31) / 32) * (t->kpad / 32)), (unsigned)(N * N));
       L.before("tc_realify_pi");
@@ -1437,6 +1462,7 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
       g.rows = 2 * N * N;
       g.out = t->Pi;
       g.out_plane = t->N4;
+      g.out_blk = 1;
       launch_gemm(t, L, "tc_gemm_pi", from_y ? t->mPi_y32 : t->mPi_ys32, t->mBpi_hi, t->mBpi_lo, g, false);
     }
   }

@@ -51,6 +51,7 @@ struct PiGemmParams {
   int mtiles;    // row tiles of 128
   int tiles;     // mtiles x column tiles; tile = n_tile * mtiles + m_tile
   float2 *out;   // out[a][c][d][b], complex: (D[m][2cd], D[m][2cd + 1])
+  int out_blk;   // out in 4^4 blocks: blk4(nb, a, c, d, b)
   int *err;
 };
 
@@ -168,7 +169,8 @@ __global__ void __launch_bounds__(kPiThreads, 1)
           if (col >= p.ncols) break;
           const long long cd = col >> 1;
           const long long c = cd / N, d = cd - c * N;
-          p.out[((a * N + c) * N + d) * N + b] = make_float2(v[j] + w[j], v[j + 1] + w[j + 1]);
+          p.out[p.out_blk ? blk4(N, a, c, d, b) : ((a * N + c) * N + d) * N + b] =
+              make_float2(v[j] + w[j], v[j + 1] + w[j + 1]);
         }
       }
       tc_fence_before();

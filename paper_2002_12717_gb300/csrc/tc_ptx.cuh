@@ -24,6 +24,17 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
+// Index of element (i0, i1, i2, i3) of an nb^4 tensor (nb % 4 == 0) stored in 4^4 blocks:
+// block (i0/4, i1/4, i2/4, i3/4) in row-major order, 256 contiguous elements each, row-major
+// inside the block.  The layout of the tensor-core form's assembly inputs and accumulator,
+// so that the assembly reads and writes whole blocks.
+__host__ __device__ __forceinline__ long long blk4(long long N, long long i0, long long i1, long long i2,
+                                                   long long i3) {
+  const long long nB = N >> 2;
+  return ((((i0 >> 2) * nB + (i1 >> 2)) * nB + (i2 >> 2)) * nB + (i3 >> 2)) * 256 +
+         ((((i0 & 3) * 4 + (i1 & 3)) * 4 + (i2 & 3)) * 4 + (i3 & 3));
+}
+
 // ---------------------------------------------------------------- mbarrier
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -216,15 +227,18 @@ __device__ __forceinline__ void slice4(float x, float (&v)[4], const float (&c)[
 }
 
 // Three slices of x (|x| < 2^E) with a 9-bit leading slice (L = 8): the cuts of slice4
-// with c_q = 1.5 2^(15 + E - 8q); v_q is x's remainder rounded to nearest-even on the
-// grid 2^(E - 8 - 8q), |v_0| <= 2^E, |v_1|, |v_2| <= 2^(E - 9 - 8(q - 1)), each exact in
-// BF16.  The part of x below 2^(E - 25) is dropped.
-__device__ __forceinline__ void slice3_lead8(float x, int E, float (&v)[3]) {
+// with c_q = 1.5 2^(15 + E - 8q) (cuts3_lead8); v_q is x's remainder rounded to
+// nearest-even on the grid 2^(E - 8 - 8q), |v_0| <= 2^E, |v_1|, |v_2| <= 2^(E - 9 - 8(q - 1)),
+// each exact in BF16.  The part of x below 2^(E - 25) is dropped.
+__device__ __forceinline__ void cuts3_lead8(int E, float (&c)[3]) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q) c[q] = ldexpf(1.5f, 15 + E - 8 * q);
+}
+__device__ __forceinline__ void slice3(float x, const float (&c)[3], float (&v)[3]) {
   float r = x;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const float c = ldexpf(1.5f, 15 + E - 8 * q);
-    v[q] = __fsub_rn(__fadd_rn(r, c), c);
+    v[q] = __fsub_rn(__fadd_rn(r, c[q]), c[q]);
     r = __fsub_rn(r, v[q]);
   }
 }
