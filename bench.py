@@ -47,10 +47,10 @@ TF32_OVER_BF16 = 1.1 / 2.25
 # DRAM bytes (read + write) per launch of the dominant kernel, keyed by (kernel tag,
 # workload), from one ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum, profiles/); missing entries report null.
-TRAFFIC = {}
+TRAFFIC = {("tc_gemm_pi", "general-gw-nb64"): 1875060000 + 123198464}   # profiles/tc_pi_gemm_gw64.md
 # sm__pipe_tensor_cycles_active (percent of peak, sustained over active cycles) of the
 # dominant kernel from the same capture; missing entries report null.
-TENSOR_PIPE = {}
+TENSOR_PIPE = {("tc_gemm_pi", "general-gw-nb64"): 89.2}
 
 
 def load_peaks():
@@ -95,9 +95,11 @@ def kernel_work(tag, nb, se, precision="tf32x3"):
     realified problem (three TF32 products, or ten BF16 slice products in the nb^5
     passes and six in the nb^2 x nb^2 x nb^2 products, per real multiply-add, 2 flops
     each): issued / algorithmic is the cost of the emulated
-    FP32-class accuracy.  The assembly counts its algorithmic HBM bytes (FP32
-    intermediates, FP64 state, FP32 RK4 accumulator and stage input), averaged over
-    the four RK4 stages.
+    FP32-class accuracy.  The assembly counts its algorithmic HBM bytes averaged over
+    the four RK4 stages: the FP32 intermediates Z and Q (and Pi for GW), the FP32
+    state copy (stages 0-2) or the FP64 state (last stage), the FP32 accumulator
+    (read at stages 1-3), and the stores (accumulator and stage input at stages 0-2,
+    FP64 state and its FP32 copy at the last).
     """
     n = float(nb)
     split = SPLIT_PRODUCTS.get(precision, 3) * 2
@@ -110,7 +112,7 @@ def kernel_work(tag, nb, se, precision="tf32x3"):
     if tag == "tc_gemm_collision":
         return "tensor", 4 * n ** 5, split * (2 * n) * n * n ** 3
     if tag == "tc_orbit_assemble_rk4":
-        per_elem = 8 + 8 + 16 + 0.75 * 8 + 18 + (8 if se == "GW" else 0)
+        per_elem = 8 + 8 + (3 * 8 + 16) / 4 + 0.75 * 8 + (3 * 16 + 24) / 4 + (8 if se == "GW" else 0)
         return "hbm", per_elem * n ** 4, per_elem * n ** 4
     if tag in ("fp64_zgemm", "fp64_zgemm_splitk"):
         return "alu", None, None

@@ -302,6 +302,108 @@ __global__ void hf_build_kernel(int nb, const void *__restrict__ Wm_, const cplx
   }
 }
 
+// ---------------------------------------------------------------------------
+// Hartree-Fock build in double-single arithmetic (the tensor-core forms).
+//
+// The same matrix-vector product as hf_build_kernel with every FP64 number x held
+// as a pair of FP32 numbers x = x_hi + x_lo (x_hi = fl32(x), x_lo = fl32(x - x_hi)),
+// evaluated on the FP32 pipe: GB300 issues FP64 instructions at a small fraction of
+// its FP32 rate, and in FP64 this product takes longer than streaming Wm from HBM.
+// Per term w n = w_hi n_hi + (w_hi n_lo + w_lo n_hi) + w_lo n_lo: the first product
+// exactly (TwoProd with a fused multiply-add), the cross terms in FP32, the last one
+// dropped (2^-48 relative); the sum in a (S, C) pair, S updated by the error-free
+// TwoSum of Knuth (TAOCP vol. 2, 4.2.2) and C collecting the rounding errors.  The
+// result carries about 46 bits: the tensor-core forms evaluate G2's terms to
+// about 2^-24, so the mean field stays far more accurate than the rest of the step.
+// Intrinsics keep the compiler from contracting the error terms into other FMAs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ds_add(float &S, float &C, float p) {
+  const float s = __fadd_rn(S, p);
+  const float bp = __fsub_rn(s, S);
+  C = __fadd_rn(C, __fadd_rn(__fsub_rn(S, __fsub_rn(s, bp)), __fsub_rn(p, bp)));
+  S = s;
+}
+
+// (S, C) += (wh + wl)(nh + nl)
+__device__ __forceinline__ void ds_mac(float &S, float &C, float wh, float wl, float nh, float nl) {
+  const float p = __fmul_rn(wh, nh);
+  const float e = __fmaf_rn(wh, nh, -p);
+  const float cross = __fmaf_rn(wh, nl, __fmul_rn(wl, nh));
+  ds_add(S, C, p);
+  C = __fadd_rn(C, __fadd_rn(e, cross));
+}
+
+// ns[c] = (Re n_hi, Im n_hi, Re n_lo, Im n_lo)
+__global__ void n_split_kernel(int nb2, const cplx *__restrict__ n, float4 *__restrict__ ns) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nb2) return;
+  const cplx v = n[c];
+  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+  ns[c] = make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
+}
+
+constexpr int kHfRows = 8;   // rows of Wm per CTA: each n load serves eight rows
+
+// Wds: the real Wm as float2 (hi, lo) per entry (the tensor-core forms take a real w).
+// One CTA of 256 threads per kHfRows rows: thread t takes entries c = t, t + 256, ... of
+// each row; the partial pairs are reduced over the warp and the CTA in a fixed order.
+__global__ void __launch_bounds__(256) hf_build_ds_kernel(int nb, const float2 *__restrict__ Wds,
+                                                           const float4 *__restrict__ ns,
+                                                           const cplx *__restrict__ h, const cplx *__restrict__ D,
+                                                           double f, cplx *__restrict__ hhf) {
+  __shared__ float4 red[8][kHfRows];   // per warp and row: (S_re, C_re, S_im, C_im)
+  const int nb2 = nb * nb;
+  const int row0 = blockIdx.x * kHfRows;
+  const int nrow = min(kHfRows, nb2 - row0);
+  float Sr[kHfRows], Cr[kHfRows], Si[kHfRows], Ci[kHfRows];
+#pragma unroll
+  for (int r = 0; r < kHfRows; ++r) Sr[r] = Cr[r] = Si[r] = Ci[r] = 0.f;
+  // rows past the end (a ragged last CTA) repeat the last row and are not stored, so the
+  // eight loads of an iteration carry no branch and are all issued before the arithmetic
+  const float2 *wbase = Wds + (long long)row0 * nb2;
+  int woff[kHfRows];
+#pragma unroll
+  for (int r = 0; r < kHfRows; ++r) woff[r] = (min(row0 + r, nb2 - 1) - row0) * nb2;
+  for (int c = threadIdx.x; c < nb2; c += 256) {
+    const float4 nv = ns[c];
+    float2 w[kHfRows];
+#pragma unroll
+    for (int r = 0; r < kHfRows; ++r) w[r] = wbase[woff[r] + c];
+#pragma unroll
+    for (int r = 0; r < kHfRows; ++r) {
+      ds_mac(Sr[r], Cr[r], w[r].x, w[r].y, nv.x, nv.z);
+      ds_mac(Si[r], Ci[r], w[r].x, w[r].y, nv.y, nv.w);
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < kHfRows; ++r) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float sr = __shfl_xor_sync(0xffffffffu, Sr[r], o), cr = __shfl_xor_sync(0xffffffffu, Cr[r], o);
+      const float si = __shfl_xor_sync(0xffffffffu, Si[r], o), ci = __shfl_xor_sync(0xffffffffu, Ci[r], o);
+      ds_add(Sr[r], Cr[r], sr);
+      Cr[r] = __fadd_rn(Cr[r], cr);
+      ds_add(Si[r], Ci[r], si);
+      Ci[r] = __fadd_rn(Ci[r], ci);
+    }
+    if (lane == 0) red[warp][r] = make_float4(Sr[r], Cr[r], Si[r], Ci[r]);
+  }
+  __syncthreads();
+  if (threadIdx.x < nrow) {
+    const int r = threadIdx.x, row = row0 + r;
+    cplx acc = {0.0, 0.0};
+    for (int w = 0; w < 8; ++w) {
+      const float4 v = red[w][r];
+      acc.x += (double)v.x + (double)v.y;
+      acc.y += (double)v.z + (double)v.w;
+    }
+    cplx out = cadd(h[row], acc);
+    if (D) out = cadd(out, cscale(D[row], f));
+    hhf[row] = out;
+  }
+}
+
 __global__ void one_pm_kernel(int nb, const cplx *n, double eta, cplx *nbar) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nb * nb) return;
@@ -650,6 +752,18 @@ void hf_build(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *h, 
     hf_build_kernel<true><<<blocks, threads, 0, L.stream>>>(nb, Wm, h, D, f, n, hhf);
   else
     hf_build_kernel<false><<<blocks, threads, 0, L.stream>>>(nb, Wm, h, D, f, n, hhf);
+  L.after_launch();
+}
+
+void hf_build_ds(Launcher &L, int nb, const float2 *Wds, const cplx *h, const cplx *D, double f, const cplx *n,
+                 float4 *nsplit, cplx *hhf) {
+  const int nb2 = nb * nb;
+  L.before("hf_split_n");
+  n_split_kernel<<<(nb2 + 255) / 256, 256, 0, L.stream>>>(nb2, n, nsplit);
+  L.after_launch();
+  L.before("hf_build");
+  const int blocks = (nb2 + kHfRows - 1) / kHfRows;
+  hf_build_ds_kernel<<<blocks, 256, 0, L.stream>>>(nb, Wds, nsplit, h, D, f, hhf);
   L.after_launch();
 }
 

@@ -43,6 +43,8 @@ struct g1g2_ctx {
   // device memory (FP64 form)
   cplx *h = nullptr, *D = nullptr;
   void *Wm = nullptr;               // Hartree-Fock matrix [(ij),(lk)], real or complex
+  bool wm_ds = false;               // real Wm held as (hi, lo) FP32 pairs (tensor-core forms)
+  float4 *nsplit = nullptr;         // n as (hi, lo) FP32 pairs for the double-single build
   cplx *w = nullptr;                // w (complex), [(ij),(kl)]
   cplx *wsrc = nullptr;             // source-term interaction (w^- or w)
   bool src_pm = false;              // wsrc = w + eta w_ijlk (else wsrc = w)
@@ -225,6 +227,15 @@ void source_A(g1g2_ctx *c, Launcher &L, const cplx *n_in) {
   }
 }
 
+// h^HF (Eq. h_HF) into c->hhf from the density n: FP64 in the FP64 form, double-single
+// arithmetic in the tensor-core forms (where Wm is stored as FP32 pairs).
+void mean_field(g1g2_ctx *c, Launcher &L, const cplx *h, const cplx *D, double f, const cplx *n) {
+  if (c->wm_ds)
+    hf_build_ds(L, c->nb, static_cast<const float2 *>(c->Wm), h, D, f, n, c->nsplit, c->hhf);
+  else
+    hf_build(L, c->nb, c->Wm, c->w_real, h, D, f, n, c->hhf);
+}
+
 void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *G_in, Rk4Stage st,
               const StageOut &o, bool w_only = false) {
   const int nb = c->nb;
@@ -233,9 +244,9 @@ void rhs_fp64(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cplx *
   // a1: Eq. (h_HF); with w_only the one-body h(t) is left out (the part of the
   // right-hand side that is linear in w, used for the gradient by the scale of w)
   if (w_only)
-    hf_build(L, nb, c->Wm, c->w_real, c->zero_h, nullptr, 0.0, n_in, c->hhf);
+    mean_field(c, L, c->zero_h, nullptr, 0.0, n_in);
   else
-    hf_build(L, nb, c->Wm, c->w_real, c->h, c->hasD ? c->D : nullptr, f, n_in, c->hhf);
+    mean_field(c, L, c->h, c->hasD ? c->D : nullptr, f, n_in);
   if (c->se == G1G2_HF) {
     g1_update(L, nb, c->hhf, n_in, nullptr, st, o.ny, o.nys, o.nacc, o.nk);
     return;
@@ -391,7 +402,7 @@ void rhs_dispatch(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cp
     rhs_fp64(c, L, t, n_in, G_in, st, o);
   } else {
     const double f = drive_f(c, t);
-    hf_build(L, c->nb, c->Wm, c->w_real, c->h, c->hasD ? c->D : nullptr, f, n_in, c->hhf);
+    mean_field(c, L, c->h, c->hasD ? c->D : nullptr, f, n_in);
     tc_rhs(c->tc, L, n_in, G_in, c->hhf, st, o.ny, o.nys, o.nacc, o.nk, o.Gy, o.Gys, o.Gacc, o.Gk);
   }
 }
@@ -424,7 +435,7 @@ int observables_impl(g1g2_ctx *c, g1g2_obs *out, double *density, double *nonfin
   Launcher L = c->launcher();
   const int nb = c->nb;
   const double f = drive_f(c, c->t);
-  hf_build(L, nb, c->Wm, c->w_real, c->h, c->hasD ? c->D : nullptr, f, c->n, c->hhf);
+  mean_field(c, L, c->h, c->hasD ? c->D : nullptr, f, c->n);
   obs_one_body(L, nb, c->h, c->hasD ? c->D : nullptr, f, c->hhf, c->n, c->red);
   double zero2[2] = {0.0, 0.0};
   if (c->se != G1G2_HF) {
@@ -1144,6 +1155,23 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "sync"))) return bail(rc);
   if ((rc = up(c->n, G1_0, N2 * sizeof(cplx)))) return bail(rc);
   if ((rc = up(c->w, hw.data(), N4 * sizeof(cplx)))) return bail(rc);
+  if (correlated && c->prec != G1G2_FP64 && real) {
+    // tensor-core forms (real w only): Wm as (hi, lo) FP32 pairs for the double-single
+    // h^HF build, in place (entry e's pair takes the bytes of entry e)
+    c->wm_ds = true;
+    cplx *ns_buf = nullptr;
+    if ((rc = dalloc(c, &ns_buf, N2))) return bail(rc);
+    c->nsplit = reinterpret_cast<float4 *>(ns_buf);
+    auto split = [](double x, float *out) {
+      out[0] = (float)x;
+      out[1] = (float)(x - (double)out[0]);
+    };
+    for (size_t e = 0; e < N4; ++e) {
+      float v[2];
+      split(WmR[e], v);
+      std::memcpy(&WmR[e], v, sizeof(v));
+    }
+  }
   if (real) { if ((rc = up(c->Wm, WmR.data(), N4 * sizeof(double)))) return bail(rc); }
   else { if ((rc = up(c->Wm, WmC.data(), N4 * sizeof(cplx)))) return bail(rc); }
   if (G2_0) { if ((rc = up(c->G, G2_0, N4 * sizeof(cplx)))) return bail(rc); }

@@ -81,6 +81,10 @@ void permute4(Launcher &L, int nb, const cplx *in, cplx *out, const int p[4], cp
 // hHF = h + f D + Wm * vec(n), Wm[(ij),(lk)] (real or complex), Eq. (h_HF).
 void hf_build(Launcher &L, int nb, const void *Wm, bool wm_real, const cplx *h, const cplx *D, double f,
               const cplx *n, cplx *hhf);
+// The same product in double-single arithmetic on the FP32 pipe (tensor-core forms, real w):
+// Wds holds the real Wm as (hi, lo) FP32 pairs; nsplit is scratch of nb^2 float4.
+void hf_build_ds(Launcher &L, int nb, const float2 *Wds, const cplx *h, const cplx *D, double f, const cplx *n,
+                 float4 *nsplit, cplx *hhf);
 // nbar = 1 + eta n: 1 - n for fermions (eta = -1), 1 + n for bosons (eta = +1)
 void one_pm(Launcher &L, int nb, const cplx *n, double eta, cplx *nbar);
 inline void one_minus(Launcher &L, int nb, const cplx *n, cplx *nbar) { one_pm(L, nb, n, -1.0, nbar); }

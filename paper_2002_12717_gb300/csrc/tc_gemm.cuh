@@ -121,6 +121,124 @@ __device__ __forceinline__ int tile_kblocks(const GemmParams &p, int tile) {
   return p.kb_per_plane * p.a_planes * (p.kb_first ? 2 : 1);
 }
 
+// Epilogue of one tile of a pass that is not split-K: TMEM lane r (the tile row) of the
+// accumulators at tbase (the exact one) and tbase + d1_off (the lower-order one, sliced
+// form), summed and stored through the output map of p; mx collects max |stored|.
+template <bool kSliced>
+__device__ __forceinline__ void epi_store_tile(const GemmParams &p, int tile, int r, uint32_t tbase,
+                                               uint32_t d1_off, float &mx) {
+  const int N = p.nb;
+  const long long NN = N;
+  // the row this thread owns
+  bool valid = false;
+  long long i0 = 0, i1 = 0, i2 = 0, grow = 0;
+  int u = 0, split = 0;
+  if (p.a_rows == AR_LINEAR) {
+    grow = (long long)tile * kTileM + r;
+    valid = grow < p.rows;
+    i2 = grow % NN;
+    i1 = (grow / NN) % NN;
+    i0 = grow / (NN * NN);
+  } else if (p.a_rows == AR_GATHER4) {
+    const int bB = tile % p.g_nb, aB = (tile / p.g_nb) % p.g_na, c = tile / (p.g_nb * p.g_na);
+    i0 = aB * 4 + r / 32;   // a
+    i1 = bB * 32 + r % 32;  // b
+    i2 = c;
+    valid = i0 < NN && i1 < NN;
+  } else if (p.a_rows == AR_PI) {
+    const int mt = tile % p.pi_mtiles;
+    const int kB = mt % p.pi_mk, iB = mt / p.pi_mk;
+    i0 = iB * 4 + r / 32;   // i
+    i2 = kB * 32 + r % 32;  // k
+    grow = (long long)(tile / p.pi_mtiles) * p.nout;  // first global output column of the tile
+    valid = i0 < NN && i2 < NN;
+  } else {
+    u = tile / p.splits;
+    split = tile % p.splits;
+    valid = r < N;
+  }
+  // Store map of this row: out[base + l cs (+ plane for the imaginary part)],
+  // with (l, v) decoded from the column (v nb + l, or 2 l + v with col_il).
+  long long base = 0;
+  int cs = 0;
+  bool neg_im = false;
+  if (p.epi == EP_SWAP34) {          // out[v][i][j][l][k], row (i,j,k)
+    base = (i0 * NN + i1) * NN * NN + i2;
+    cs = N;
+  } else if (p.epi == EP_EXCH_T) {   // out[v][q][p][l][r], row (p,q,r)
+    base = (i1 * NN + i0) * NN * NN + i2;
+    cs = N;
+  } else if (p.epi == EP_GATHER_TCONJ) {  // out[v][c][d][a][b], row (a,b,c), imaginary negated
+    base = i2 * NN * NN * NN + i0 * NN + i1;
+    cs = N * N;
+    neg_im = true;
+  }
+  for (int c0 = 0; c0 < p.nout; c0 += 32) {
+    float v[32];
+    tmem_ld32(tbase + (uint32_t)c0, v);
+    if (kSliced) {
+      float vl[32];
+      tmem_ld32(tbase + d1_off + (uint32_t)c0, vl);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] += vl[j];
+    }
+    if (!valid) continue;
+    const int nv = min(32, p.n_valid - c0);  // columns of this chunk that are stored
+    if (p.epi == EP_PARTIAL) {
+      float *o = p.out + (((long long)split * 2 + u) * NN + r) * p.n_valid + c0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < nv) o[j] = v[j];
+    } else if (p.epi == EP_PI) {
+      // columns (j, l, v) interleaved from the even global column grow + c0: complex pairs
+      float2 *o = reinterpret_cast<float2 *>(p.out);
+      const long long cg0 = grow + c0;
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) {
+        const long long cg = cg0 + j;
+        if (j >= nv || cg >= p.rows) break;
+        const long long jl = cg >> 1;
+        const long long jj = jl / NN, ll = jl - jj * NN;
+        o[p.out_blk ? blk4(NN, i0, jj, ll, i2) : ((i0 * NN + jj) * NN + ll) * NN + i2] =
+            make_float2(v[j], v[j + 1]);
+      }
+    } else if (p.out_il) {
+      // col_il columns (2 l, 2 l + 1) -> one interleaved complex value
+      float2 *o = reinterpret_cast<float2 *>(p.out) + base;
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) {
+        if (j >= nv) break;
+        const int l = (c0 + j) >> 1;
+        if (p.out_blk)
+          reinterpret_cast<float2 *>(p.out)[blk4(NN, i0, i1, l, i2)] = make_float2(v[j], v[j + 1]);
+        else
+          o[l * cs] = make_float2(v[j], v[j + 1]);
+        if (kSliced) mx = fmaxf(mx, fmaxf(fabsf(v[j]), fabsf(v[j + 1])));
+      }
+    } else if (p.col_il) {
+      float *o = p.out + base;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (j >= nv) break;
+        const int col = c0 + j, vv = col & 1, l = col >> 1;
+        const float x = (neg_im && vv) ? -v[j] : v[j];
+        o[(long long)l * cs + (vv ? p.out_plane : 0)] = x;
+        if (kSliced) mx = fmaxf(mx, fabsf(x));
+      }
+    } else {
+      float *o = p.out + base;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (j >= nv) break;
+        const int col = c0 + j, vv = col >= N ? 1 : 0, l = col - (vv ? N : 0);
+        const float x = (neg_im && vv) ? -v[j] : v[j];
+        o[(long long)l * cs + (vv ? p.out_plane : 0)] = x;
+        if (kSliced) mx = fmaxf(mx, fabsf(x));
+      }
+    }
+  }
+}
+
 // tmBhi/tmBlo: TF32 hi and lo parts of B; in the sliced form tmBhi holds the
 // four BF16 slices of B as [slice][row][k] (tmBlo unused).
 //
@@ -455,115 +573,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       // warp-uniform: the TMEM loads below are .sync.aligned
       if (!__all_sync(0xffffffffu, mbar_wait(&tfull[acc], acc_ph, p.err))) break;
       tc_fence_after();
-      // the row this thread owns
-      bool valid = false;
-      long long i0 = 0, i1 = 0, i2 = 0, grow = 0;
-      int u = 0, split = 0;
-      if (p.a_rows == AR_LINEAR) {
-        grow = (long long)tile * kTileM + r;
-        valid = grow < p.rows;
-        i2 = grow % NN;
-        i1 = (grow / NN) % NN;
-        i0 = grow / (NN * NN);
-      } else if (p.a_rows == AR_GATHER4) {
-        const int bB = tile % p.g_nb, aB = (tile / p.g_nb) % p.g_na, c = tile / (p.g_nb * p.g_na);
-        i0 = aB * 4 + r / 32;   // a
-        i1 = bB * 32 + r % 32;  // b
-        i2 = c;
-        valid = i0 < NN && i1 < NN;
-      } else if (p.a_rows == AR_PI) {
-        const int mt = tile % p.pi_mtiles;
-        const int kB = mt % p.pi_mk, iB = mt / p.pi_mk;
-        i0 = iB * 4 + r / 32;   // i
-        i2 = kB * 32 + r % 32;  // k
-        grow = (long long)(tile / p.pi_mtiles) * p.nout;  // first global output column of the tile
-        valid = i0 < NN && i2 < NN;
-      } else {
-        u = tile / p.splits;
-        split = tile % p.splits;
-        valid = r < N;
-      }
-      // Store map of this row: out[base + l cs (+ plane for the imaginary part)],
-      // with (l, v) decoded from the column (v nb + l, or 2 l + v with col_il).
-      long long base = 0;
-      int cs = 0;
-      bool neg_im = false;
-      if (p.epi == EP_SWAP34) {          // out[v][i][j][l][k], row (i,j,k)
-        base = (i0 * NN + i1) * NN * NN + i2;
-        cs = N;
-      } else if (p.epi == EP_EXCH_T) {   // out[v][q][p][l][r], row (p,q,r)
-        base = (i1 * NN + i0) * NN * NN + i2;
-        cs = N;
-      } else if (p.epi == EP_GATHER_TCONJ) {  // out[v][c][d][a][b], row (a,b,c), imaginary negated
-        base = i2 * NN * NN * NN + i0 * NN + i1;
-        cs = N * N;
-        neg_im = true;
-      }
-      const uint32_t tbase = tmem_base + lane_base + (uint32_t)(acc * kAccCols);
-      for (int c0 = 0; c0 < p.nout; c0 += 32) {
-        float v[32];
-        tmem_ld32(tbase + (uint32_t)c0, v);
-        if (kSliced) {
-          float vl[32];
-          tmem_ld32(tbase + d1_off + (uint32_t)c0, vl);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] += vl[j];
-        }
-        if (!valid) continue;
-        const int nv = min(32, p.n_valid - c0);  // columns of this chunk that are stored
-        if (p.epi == EP_PARTIAL) {
-          float *o = p.out + (((long long)split * 2 + u) * NN + r) * p.n_valid + c0;
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j < nv) o[j] = v[j];
-        } else if (p.epi == EP_PI) {
-          // columns (j, l, v) interleaved from the even global column grow + c0: complex pairs
-          float2 *o = reinterpret_cast<float2 *>(p.out);
-          const long long cg0 = grow + c0;
-#pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            const long long cg = cg0 + j;
-            if (j >= nv || cg >= p.rows) break;
-            const long long jl = cg >> 1;
-            const long long jj = jl / NN, ll = jl - jj * NN;
-            o[p.out_blk ? blk4(NN, i0, jj, ll, i2) : ((i0 * NN + jj) * NN + ll) * NN + i2] =
-                make_float2(v[j], v[j + 1]);
-          }
-        } else if (p.out_il) {
-          // col_il columns (2 l, 2 l + 1) -> one interleaved complex value
-          float2 *o = reinterpret_cast<float2 *>(p.out) + base;
-#pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            if (j >= nv) break;
-            const int l = (c0 + j) >> 1;
-            if (p.out_blk)
-              reinterpret_cast<float2 *>(p.out)[blk4(NN, i0, i1, l, i2)] = make_float2(v[j], v[j + 1]);
-            else
-              o[l * cs] = make_float2(v[j], v[j + 1]);
-            if (kSliced) mx = fmaxf(mx, fmaxf(fabsf(v[j]), fabsf(v[j + 1])));
-          }
-        } else if (p.col_il) {
-          float *o = p.out + base;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (j >= nv) break;
-            const int col = c0 + j, vv = col & 1, l = col >> 1;
-            const float x = (neg_im && vv) ? -v[j] : v[j];
-            o[(long long)l * cs + (vv ? p.out_plane : 0)] = x;
-            if (kSliced) mx = fmaxf(mx, fabsf(x));
-          }
-        } else {
-          float *o = p.out + base;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (j >= nv) break;
-            const int col = c0 + j, vv = col >= N ? 1 : 0, l = col - (vv ? N : 0);
-            const float x = (neg_im && vv) ? -v[j] : v[j];
-            o[(long long)l * cs + (vv ? p.out_plane : 0)] = x;
-            if (kSliced) mx = fmaxf(mx, fabsf(x));
-          }
-        }
-      }
+      epi_store_tile<kSliced>(p, tile, r, tmem_base + lane_base + (uint32_t)(acc * kAccCols), d1_off, mx);
       tc_fence_before();
       mbar_arrive(&tempty[acc]);
       if (++acc == nbuf) { acc = 0; acc_ph ^= 1u; }

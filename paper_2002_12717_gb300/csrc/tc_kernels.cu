@@ -37,6 +37,7 @@
 #include "tc_path.h"
 #include "tc_gemm.cuh"
 #include "tc_pi_gemm.cuh"
+#include "tc_gemm_ts.cuh"
 
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -166,9 +167,25 @@ __device__ __forceinline__ void slice4_f64(double x, const double (&c)[4], __nv_
 // from its largest magnitude, written as slices [q][row][ld].  The realified
 // matrix holds +-Re and +-Im of the (shifted) entries of S, so every CTA takes
 // the maximum over the nb^2 entries of S itself and slices its share.
-__global__ void __launch_bounds__(256) slice_b_kernel(int nb, int nout, int kpad, int complex_a, int shift, int ld,
-                                                      int transpose, int il, const cplx *__restrict__ S,
-                                                      __nv_bfloat16 *out, long long slice_stride) {
+// One operand of slice_b_kernel: the matrix S and how it is realified (see realify_kernel).
+struct SliceBOp {
+  const cplx *S;
+  __nv_bfloat16 *out;
+  long long slice_stride;
+  int complex_a, shift, ld, transpose, il;
+};
+constexpr int kMaxSliceBOps = 8;
+struct SliceBBatch {
+  SliceBOp op[kMaxSliceBOps];
+};
+
+// The B operands of one right-hand side in one launch: grid row blockIdx.y slices op[y].
+__global__ void __launch_bounds__(256) slice_b_kernel(int nb, int nout, int kpad, const SliceBBatch batch) {
+  const SliceBOp &o = batch.op[blockIdx.y];
+  const cplx *__restrict__ S = o.S;
+  const int complex_a = o.complex_a, shift = o.shift, ld = o.ld, transpose = o.transpose, il = o.il;
+  __nv_bfloat16 *out = o.out;
+  const long long slice_stride = o.slice_stride;
   __shared__ double red[8];
   __shared__ double smu;
   const int kt = complex_a ? 2 * kpad : kpad;
@@ -337,24 +354,32 @@ __global__ void __launch_bounds__(256) realify_pi_slice3_kernel(int nb, const fl
   for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
   float cut[3];
   cuts3_lead8(slice_exponent(__float_as_int(mx)), cut);
+  // slicing sweep: each thread cuts two adjacent q of one p and stores BF16 pairs
+  const int qp = tx & 15, psub = tx >> 4;
   for (int tile = 0; tile < nt * nt; ++tile) {
     const int p0 = (tile / nt) * 32, q0 = (tile % nt) * 32;
     __syncthreads();
     load_tile(p0, q0);
     __syncthreads();
-    for (int ty = ty0; ty < 32; ty += 8) {
-      const int pp = p0 + ty, q = q0 + tx;
-      if (pp >= nb || q >= nb) continue;
-      const float2 h = hval(pp, q, ty);
+    for (int pr = 2 * ty0 + psub; pr < 32; pr += 16) {
+      const int pp = p0 + pr, q = q0 + 2 * qp;
+      if (pp >= nb || q >= nb) continue;   // nb % 4 == 0: q + 1 < nb as well
+      const long long g = ((pp * N + l) * N + j) * N + q;     // Y2_{p l q j}, Y2_{p l q+1 j}
+      const float2 y2r = *reinterpret_cast<const float2 *>(Y2s + g), y2i = *reinterpret_cast<const float2 *>(Y2s + P + g);
+      const float2 a0 = t1[2 * qp][pr], a1 = t1[2 * qp + 1][pr];
+      const float2 h0 = make_float2(a0.x - y2r.x, a0.y - y2i.x), h1 = make_float2(a1.x - y2r.y, a1.y - y2i.y);
       for (int u = 0; u < 2; ++u)
         for (int v = 0; v < 2; ++v) {
-          const float x = (u == 0) ? (v ? h.y : h.x) : (v ? h.x : -h.y);
+          const float x0 = (u == 0) ? (v ? h0.y : h0.x) : (v ? h0.x : -h0.y);
+          const float x1 = (u == 0) ? (v ? h1.y : h1.x) : (v ? h1.x : -h1.y);
           const long long row = 2 * jl + v;
           const long long col = ((long long)u * N + pp) * N + q;
-          float sl[3];
-          slice3(x, cut, sl);
+          float s0[3], s1[3];
+          slice3(x0, cut, s0);
+          slice3(x1, cut, s1);
 #pragma unroll
-          for (int z = 0; z < 3; ++z) out[z * slice_stride + row * K + col] = __float2bfloat16_rn(sl[z]);
+          for (int z = 0; z < 3; ++z)
+            *reinterpret_cast<__nv_bfloat162 *>(out + z * slice_stride + row * K + col) = __floats2bfloat162_rn(s0[z], s1[z]);
         }
     }
   }
@@ -606,21 +631,23 @@ struct AsmParams {
   const int4 *blocks;
   const float *Z, *Q, *Pi;     // interleaved complex FP32, swapped layout in 4^4 blocks (blk4)
   long long P;                 // plane stride of ys and y32
-  cplx *y;                     // FP64 state (interleaved)
+  cplx *y;                     // FP64 state (interleaved): read and written at the last stage
   float *acc;                  // interleaved complex FP32 in 4^4 blocks (blk4)
-  float *ys;                   // planar FP32 stage input of the next stage
-  float *y32;                  // planar FP32 copy of y (stage 3)
+  float *ys;                   // planar FP32 stage input of the next stage (stages 0-2)
+  float *y32;                  // planar FP32 copy of y: read at stages 0-2, rewritten at the last
   cplx *kout;                  // write-k mode
   int stage;
-  double dt;
+  float hs;                    // stages 0-2: the stage's step (dt / 2 or dt) in FP32
+  double dt6;                  // last stage: dt / 6
   int *amax;                   // optional: max |written ys or y32| (sliced form)
 };
 
-__device__ __forceinline__ int bidx(int a, int b, int c, int d) { return ((a * BSZ + b) * BSZ + c) * BSZ + d; }
-// Shared-memory slot of block element (a,b,c,d): the last coordinate is XOR-swizzled
-// with the other three so that the four orbit permutations hit (nearly) distinct banks.
+// Shared-memory slot of block element (a,b,c,d) (BSZ = 4): row (a,b) of 16 slots, and
+// within the row the slot (a ^ c, b ^ d).  A half-warp (16 lanes of fixed (a,b) in
+// thread order) then reads or writes 16 distinct slots mod 16 (one 128-byte wavefront
+// of float2) under each of the permutations of (a,b,c,d) the assembly uses.
 __device__ __forceinline__ int sidx(int a, int b, int c, int d) {
-  return bidx(a, b, c, d ^ ((a ^ b ^ c) & (BSZ - 1)));
+  return ((a * BSZ + b) << 4) | (((a ^ c) & (BSZ - 1)) << 2) | ((b ^ d) & (BSZ - 1));
 }
 
 // 4^4 blocks: 8 KB of shared memory and 256 threads per orbit CTA, so that eight CTAs
@@ -636,6 +663,45 @@ __device__ __forceinline__ float2 sval(const float2 *sm, int m, int a, int b, in
   return sm[m * BEL + (swap34 ? sidx(a, b, d, c) : sidx(a, b, c, d))];
 }
 
+// Conversions between IEEE-754 binary32 and binary64 done on the bit patterns with
+// integer instructions.  GB300 issues FP64 instructions (conversions included) at a
+// small fraction of its FP32 and integer rates, and the assembly would otherwise spend
+// more time on them than on its HBM traffic.  Both follow the formats' definitions:
+// binary32 = (s, 8-bit exponent biased by 127, 23-bit fraction), binary64 = (s, 11-bit
+// exponent biased by 1023, 52-bit fraction).
+//
+// f32 -> f64 is exact for normal numbers, zero, infinities and NaNs; a subnormal input
+// becomes a zero of the same sign.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  uint32_t hi = u & 0x80000000u, lo = 0u;
+  if (e != 0u) {
+    hi |= ((e == 0xffu ? 0x7ffu : e + 896u) << 20) | (m >> 3);   // 896 = 1023 - 127
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// f64 -> f32, round to nearest, ties to even, for results in the binary32 normal range;
+// magnitudes below 2^-126 become a zero of the same sign, magnitudes beyond the range
+// infinity, and a NaN stays a NaN.
+__device__ __forceinline__ float f64_to_f32_bits(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t E = (hi >> 20) & 0x7ffu;
+  // the upper 23 of the 52 fraction bits; the lower 29 decide the rounding
+  uint32_t mag = ((E - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t rest = lo & 0x1fffffffu;
+  mag += (rest > 0x10000000u || (rest == 0x10000000u && (mag & 1u))) ? 1u : 0u;   // may carry into the exponent
+  if (E < 897u) mag = 0u;
+  if (E >= 1151u) mag = (E == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
+  return __uint_as_float((hi & 0x80000000u) | mag);
+}
+
+// Stage kinds of the assembly: the plain right-hand side (k written in FP64), RK4 stages
+// 0-2 (next stage input and accumulator) and the last stage (the FP64 state update).
+enum AsmKind { kAsmK = 0, kAsmStage = 1, kAsmLast = 2 };
+
 // One CTA per orbit {X, exch X, trans X, exch trans X} of BSZ^4 blocks, each thread
 // APER element orbits.  Z, Q and Pi arrive in the swapped layout and enter only as
 // V = Z - Q/2 - Pi/2 per element: with P = U - (Q + exch Q)/2 and U = Z + exch Z,
@@ -646,6 +712,15 @@ __device__ __forceinline__ float2 sval(const float2 *sm, int m, int a, int b, in
 // shared-memory exchange forms the orbit sums, and the update stores.  The tensor-core
 // form requires nb % 4 == 0 (tc_create), so BSZ = 4 blocks tile the tensor exactly and
 // no element of a block lies outside it.
+//
+// RK4 (classical, k in FP32 from the tensor-core products):
+//   stages 0-2: ys = y32 + h k (FP32; y32 the FP32 rounding of the state y),
+//               acc = acc + w k (w = 1 at stage 0, else 2; FP32);
+//   last stage: y = y + dt/6 (acc + k) with one FP64 fused multiply-add per component,
+//               y32 = the FP32 rounding of the new y.
+// The stage inputs are FP32 operands of the next products in either case; only the
+// state update needs FP64, and it issues one FP64 instruction per real component.
+template <int KIND>
 __global__ void __launch_bounds__(ATHREADS, 4) orbit_assemble_kernel(const AsmParams p) {
   extern __shared__ float2 sm[];  // 4 * BEL
   const int4 base = p.blocks[blockIdx.x];
@@ -654,6 +729,7 @@ __global__ void __launch_bounds__(ATHREADS, 4) orbit_assemble_kernel(const AsmPa
                        {base.z, base.w, base.x, base.y},
                        {base.w, base.z, base.y, base.x}};
   const long long N = p.nb;
+  const long long P = p.P;
   bool dup[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -661,8 +737,9 @@ __global__ void __launch_bounds__(ATHREADS, 4) orbit_assemble_kernel(const AsmPa
     for (int q = 0; q < m; ++q)
       dup[m] |= (X[q][0] == X[m][0] && X[q][1] == X[m][1] && X[q][2] == X[m][2] && X[q][3] == X[m][3]);
   }
-  const bool rk = p.stage >= 0, acc_in = p.stage > 0;
-  cplx y0[4][APER];
+  const bool acc_in = KIND == kAsmLast || (KIND == kAsmStage && p.stage > 0);
+  float2 yf[4][APER];   // stages 0-2: the FP32 state
+  cplx y0[4][APER];     // last stage: the FP64 state
   float2 ac[4][APER];
 #pragma unroll
   for (int m = 0; m < 4; ++m)
@@ -683,7 +760,8 @@ __global__ void __launch_bounds__(ATHREADS, 4) orbit_assemble_kernel(const AsmPa
       // RK4 state of the natural element (a, b, c, d) of member m
       const long long gn = (((X[m][0] * BSZ + a) * N + X[m][1] * BSZ + b) * N + X[m][2] * BSZ + c) * N +
                            X[m][3] * BSZ + d;
-      y0[m][t] = rk && !dup[m] ? p.y[gn] : make_double2(0.0, 0.0);
+      if (KIND == kAsmStage) yf[m][t] = dup[m] ? make_float2(0.f, 0.f) : make_float2(p.y32[gn], p.y32[P + gn]);
+      if (KIND == kAsmLast) y0[m][t] = dup[m] ? make_double2(0.0, 0.0) : p.y[gn];
       const long long gb = blk4(N, X[m][0] * BSZ + a, X[m][1] * BSZ + b, X[m][2] * BSZ + c, X[m][3] * BSZ + d);
       ac[m][t] = acc_in && !dup[m] ? reinterpret_cast<const float2 *>(p.acc)[gb] : make_float2(0.f, 0.f);
     }
@@ -713,11 +791,7 @@ __global__ void __launch_bounds__(ATHREADS, 4) orbit_assemble_kernel(const AsmPa
   }
   __syncthreads();
   // RK4 update of each distinct member block, in natural (coalesced) order
-  float *__restrict__ accv = p.acc;
-  float *__restrict__ ysv = p.ys;
-  float *__restrict__ y32v = p.y32;
-  const long long P = p.P;
-  const double dt = p.dt;
+  const float w = p.stage == 0 ? 1.f : 2.f;
   float mx = 0.f;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -729,29 +803,28 @@ __global__ void __launch_bounds__(ATHREADS, 4) orbit_assemble_kernel(const AsmPa
       const long long g = (((X[m][0] * BSZ + a) * N + X[m][1] * BSZ + b) * N + X[m][2] * BSZ + c) * N +
                           X[m][3] * BSZ + d;
       const float2 k = sm[m * BEL + sidx(a, b, c, d)];
-      if (p.stage < 0) {
-        p.kout[g] = make_double2((double)k.x, (double)k.y);
-      } else if (p.stage < 3) {
-        const double h = (p.stage == 2) ? dt : 0.5 * dt;
-        const float w = (p.stage == 0) ? 1.f : 2.f;
-        reinterpret_cast<float2 *>(accv)[blk4(N, X[m][0] * BSZ + a, X[m][1] * BSZ + b, X[m][2] * BSZ + c,
-                                              X[m][3] * BSZ + d)] =
-            make_float2(ac[m][t].x + w * k.x, ac[m][t].y + w * k.y);
-        const float sx = (float)(y0[m][t].x + h * k.x), sy = (float)(y0[m][t].y + h * k.y);
-        ysv[g] = sx;
-        ysv[P + g] = sy;
+      if (KIND == kAsmK) {
+        p.kout[g] = make_double2(f32_to_f64_bits(k.x), f32_to_f64_bits(k.y));
+      } else if (KIND == kAsmStage) {
+        reinterpret_cast<float2 *>(p.acc)[blk4(N, X[m][0] * BSZ + a, X[m][1] * BSZ + b, X[m][2] * BSZ + c,
+                                               X[m][3] * BSZ + d)] =
+            make_float2(fmaf(w, k.x, ac[m][t].x), fmaf(w, k.y, ac[m][t].y));
+        const float sx = fmaf(p.hs, k.x, yf[m][t].x), sy = fmaf(p.hs, k.y, yf[m][t].y);
+        p.ys[g] = sx;
+        p.ys[P + g] = sy;
         mx = fmaxf(mx, fmaxf(fabsf(sx), fabsf(sy)));
       } else {
-        const double nx = y0[m][t].x + dt / 6.0 * ((double)ac[m][t].x + (double)k.x);
-        const double ny = y0[m][t].y + dt / 6.0 * ((double)ac[m][t].y + (double)k.y);
+        const double nx = fma(f32_to_f64_bits(ac[m][t].x + k.x), p.dt6, y0[m][t].x);
+        const double ny = fma(f32_to_f64_bits(ac[m][t].y + k.y), p.dt6, y0[m][t].y);
         p.y[g] = make_double2(nx, ny);
-        y32v[g] = (float)nx;
-        y32v[P + g] = (float)ny;
-        mx = fmaxf(mx, fmaxf(fabsf((float)nx), fabsf((float)ny)));
+        const float fx = f64_to_f32_bits(nx), fy = f64_to_f32_bits(ny);
+        p.y32[g] = fx;
+        p.y32[P + g] = fy;
+        mx = fmaxf(mx, fmaxf(fabsf(fx), fabsf(fy)));
       }
     }
   }
-  if (p.amax) block_amax(mx, p.amax);
+  if (KIND != kAsmK && p.amax) block_amax(mx, p.amax);
 }
 
 // ------------------------------------------------------------------ tensor maps
@@ -888,21 +961,28 @@ int talloc(TcPath *p, T **ptr, size_t count) {
 }
 
 // dynamic shared memory of one GEMM CTA; acc64_bytes > 0 adds the FP64 split-K accumulator.
-// TF32 form: up to 4 stages.  Sliced form: 2 MMA stages and as many FP32 A slots (2..6)
-// as the rest of the budget holds.
+// TF32 form: up to 4 stages.  Sliced form: 2 or 3 MMA stages and as many FP32 A slots
+// (2..6) as the rest of the budget holds.
 size_t gemm_smem(bool sliced, int nout, int *stages, int *fstages, size_t acc64_bytes = 0) {
   const size_t stage = stage_bytes_for(sliced, nout);
   const size_t budget = 224 * 1024 - acc64_bytes;
   if (sliced) {
-    *stages = 2;
-    *fstages = (int)std::max<size_t>(2, std::min<size_t>(6, (budget - std::min(budget, 2 * stage)) / kABytes));
-    return 1024 + 2 * stage + (size_t)*fstages * kABytes + 256 + acc64_bytes;
+    // a third MMA stage (more lookahead for the B loads) where it fits beside two FP32 slots
+    *stages = (3 * stage + 2 * (size_t)kABytes <= budget) ? 3 : 2;
+    *fstages = (int)std::max<size_t>(2, std::min<size_t>(6, (budget - std::min(budget, *stages * stage)) / kABytes));
+    return 1024 + *stages * stage + (size_t)*fstages * kABytes + 256 + acc64_bytes;
   }
   int s = (int)std::min<size_t>(4, budget / stage);
   if (s < 2) s = 2;
   *stages = s;
   *fstages = 0;
   return 1024 + s * stage + 256 + acc64_bytes;
+}
+
+// The sliced passes with output tiles wider than 128 columns (nb > 64) whose rows are
+// linear or gathered run on tc_gemm_ts_kernel (A slices in tensor memory).
+bool use_ts_gemm(const GemmParams &g) {
+  return g.nout > 128 && g.nout <= 192 && !g.kb_chunks && (g.a_rows == AR_LINEAR || g.a_rows == AR_GATHER4);
 }
 
 // sliced: the BF16-slice form (Bh = slices of B, Bl unused); otherwise TF32 hi/lo
@@ -914,7 +994,9 @@ void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, 
   const size_t smem = gemm_smem(sliced, gp.nout, &stages, &fstages, acc64);
   const int grid = std::max(1, std::min(gp.tiles, t->sms));
   L.before(tag);
-  if (sliced) {
+  if (sliced && use_ts_gemm(gp)) {
+    tc_gemm_ts_kernel<<<grid, kTsThreads, ts_smem_bytes(gp.nout), L.stream>>>(A, A2 ? *A2 : A, Bh, gp);
+  } else if (sliced) {
     tc_gemm_kernel<true><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages, fstages);
   } else {
     tc_gemm_kernel<false><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages, fstages);
@@ -1058,6 +1140,25 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
             }
             if (canon) blk.push_back(make_int4(a, b, c, d));
           }
+    // CTA order: the orbits of the 4^4 blocks that make up one orbit of 8^4 blocks run one
+    // after another.  The state copy and the stage input are planar FP32 in natural order,
+    // so a 4^4 block covers only half of each 32-byte sector along the last index; the
+    // other half lies in the neighbouring 4^4 block of the same 8^4 block, which belongs
+    // to one of these orbits for every member of the orbit.  Run together, the two halves
+    // meet in L2 instead of reaching HBM twice.
+    auto orbit_key = [](int a, int b, int c, int d, long long K) {
+      const int m[4][4] = {{a, b, c, d}, {b, a, d, c}, {c, d, a, b}, {d, c, b, a}};
+      long long best = -1;
+      for (int q = 0; q < 4; ++q) {
+        const long long k = ((m[q][0] * K + m[q][1]) * K + m[q][2]) * K + m[q][3];
+        if (best < 0 || k < best) best = k;
+      }
+      return best;
+    };
+    const long long K8 = (nB + 1) / 2;
+    std::stable_sort(blk.begin(), blk.end(), [&](const int4 &x, const int4 &y) {
+      return orbit_key(x.x >> 1, x.y >> 1, x.z >> 1, x.w >> 1, K8) < orbit_key(y.x >> 1, y.y >> 1, y.z >> 1, y.w >> 1, K8);
+    });
     t->nblocks = (int)blk.size();
     if ((rc = talloc(t, &t->blocks, blk.size()))) return bail(rc);
     if (cudaMemcpy(t->blocks, blk.data(), blk.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -1193,8 +1294,11 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
     return dyn >= (int)need && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess;
   };
   if (!raise_limit((const void *)tc_gemm_kernel<false>, smax) || !raise_limit((const void *)tc_gemm_kernel<true>, smax) ||
-      !raise_limit((const void *)orbit_assemble_kernel, 4 * BEL * sizeof(float2)) ||
-      (big && sliced && !raise_limit((const void *)tc_pi_gemm_kernel, kPiSmemBytes))) {
+      !raise_limit((const void *)orbit_assemble_kernel<kAsmK>, 4 * BEL * sizeof(float2)) ||
+      !raise_limit((const void *)orbit_assemble_kernel<kAsmStage>, 4 * BEL * sizeof(float2)) ||
+      !raise_limit((const void *)orbit_assemble_kernel<kAsmLast>, 4 * BEL * sizeof(float2)) ||
+      (big && sliced && !raise_limit((const void *)tc_pi_gemm_kernel, kPiSmemBytes)) ||
+      (sliced && t->nout2 > 128 && !raise_limit((const void *)tc_gemm_ts_kernel, ts_smem_bytes(t->nout2)))) {
     cudaGetLastError();
     set_error_detail("cannot raise the shared-memory limit of the tensor-core kernels");
     return bail(G1G2_ECUDA);
@@ -1341,13 +1445,14 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     if (t->has_pp) sel[nops++] = 5;
     if (t->has_pp || t->has_ph) sel[nops++] = 6;
     if (t->has_ph) sel[nops++] = 7;
+    SliceBBatch batch{};
     for (int qi = 0; qi < nops; ++qi) {
       const auto &o = ops[sel[qi]];
-      L.before("tc_slice_b");
-      slice_b_kernel<<<64, 256, 0, L.stream>>>(nb, t->nout2, t->kpad, o.complex_a, o.shift, o.ld, o.transpose, o.il,
-                                               o.S, o.out, (long long)t->nout2 * o.ld);
-      L.after_launch();
+      batch.op[qi] = SliceBOp{o.S, o.out, (long long)t->nout2 * o.ld, o.complex_a, o.shift, o.ld, o.transpose, o.il};
     }
+    L.before("tc_slice_b");
+    slice_b_kernel<<<dim3(64, (unsigned)nops), 256, 0, L.stream>>>(nb, t->nout2, t->kpad, batch);
+    L.after_launch();
   }
   {
     const int kc = 2 * t->kpad;
@@ -1532,14 +1637,21 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
   a.y32 = t->y32;
   a.kout = Gk;
   a.stage = st.stage;
-  a.dt = st.dt;
+  a.hs = (float)(st.stage == 2 ? st.dt : 0.5 * st.dt);
+  a.dt6 = st.dt / 6.0;
   if (sl && st.stage >= 0) {
     // the assembly writes the next stage input (ys) or, at the last stage, the new FP32 state (y32)
     a.amax = amax + (st.stage < 3 ? kAmaxYs : kAmaxY);
     cudaMemsetAsync(a.amax, 0, sizeof(int), L.stream);
   }
   L.before("tc_orbit_assemble_rk4");
-  orbit_assemble_kernel<<<t->nblocks, ATHREADS, 4 * BEL * sizeof(float2), L.stream>>>(a);
+  const size_t asm_smem = 4 * BEL * sizeof(float2);
+  if (st.stage < 0)
+    orbit_assemble_kernel<kAsmK><<<t->nblocks, ATHREADS, asm_smem, L.stream>>>(a);
+  else if (st.stage < 3)
+    orbit_assemble_kernel<kAsmStage><<<t->nblocks, ATHREADS, asm_smem, L.stream>>>(a);
+  else
+    orbit_assemble_kernel<kAsmLast><<<t->nblocks, ATHREADS, asm_smem, L.stream>>>(a);
   L.after_launch();
 }
 

@@ -253,6 +253,9 @@ def workload(name):
     elif name == "general-soa-nb48":
         d = general_basis(48, 96, 24, seed=7, pulse=True)
         d.update(dt=0.01, nsteps=1000)
+    elif name == "general-soa-nb80":
+        d = general_basis(80, 160, 40, seed=8, pulse=True)
+        d.update(dt=0.01, nsteps=500)
     elif name == "general-soa-nb64":
         d = general_basis(64, 128, 32, seed=6, pulse=True)
         d.update(dt=0.01, nsteps=500)
@@ -265,7 +268,7 @@ def workload(name):
 
 
 WORKLOADS = ("hubbard-chain-nb8", "general-soa-nb32", "general-gw-nb48", "hubbard-2d-4x4",
-             "general-soa-nb96", "general-gw-nb64", "general-soa-nb64")
+             "general-soa-nb96", "general-gw-nb64", "general-soa-nb64", "general-soa-nb80")
 
 
 def random_state(nb, rng, g2_scale=1e-2, soa=True):

@@ -54,7 +54,9 @@ def run_rhs(prop, t, n, g2):
 CASES = [("SOA", 4, False), ("SOA", 8, False), ("SOA", 12, False), ("SOA", 20, False), ("SOA", 32, False),
          ("SOA", 36, False), ("SOA", 48, False), ("SOA", 8, True), ("SOA", 12, True), ("GW", 4, False),
          ("GW", 8, False), ("GW", 12, False), ("GW", 20, False), ("GW", 32, False), ("GW", 36, False),
-         ("GWX", 12, False), ("GWX", 32, False)]
+         ("GWX", 12, False), ("GWX", 32, False),
+         # output tiles wider than 128 columns (nb > 64): the tensor-memory A path
+         ("SOA", 68, False), ("GW", 68, False), ("SOA", 80, True)]
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x4"])
@@ -71,6 +73,27 @@ def test_tc_rhs_parity(se, nb, restricted, prec):
     e1, e2 = rel_err(dn, dn_ref), rel_err(dg, dg_ref)
     print(f"{prec} {se} nb={nb} restricted={restricted}: dn {e1:.2e} dG2 {e2:.2e}")
     assert e1 < tol_rhs(se, nb, prec) and e2 < tol_rhs(se, nb, prec)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x4"])
+@pytest.mark.parametrize("se,nb,restricted", [("SOA", 16, False), ("GW", 20, False), ("GWX", 12, False),
+                                              ("SOA", 12, True), ("SOA", 36, False)])
+def test_tc_mean_field_is_double_single_accurate(se, nb, restricted, prec):
+    """The tensor-core forms build h^HF (Eq. h_HF) in double-single arithmetic on the FP32
+    pipe.  At G2 = 0 the collision integral vanishes exactly in every form, so dn/dt =
+    -i[h^HF, n] isolates the mean field: it must match the oracle to about 2^-46, far
+    below the FP32-level bar of the G2 terms (a plain FP32 build would miss by ~1e-7)."""
+    from paper_2002_12717_gb300.g1g2 import Propagator
+    h, w, n, _, D, drv = problem(nb, se, restricted, False, seed=300 + nb)
+    g0 = np.zeros((nb,) * 4, dtype=np.complex128)
+    prob = O.Problem(h, w, se, restricted, D, drv.f)
+    dn_ref, _ = O.rhs(prob, 0.9, n, g0)
+    with Propagator(h, w, n, None, se, prec, restricted) as p:
+        p.set_drive(D, drv)
+        dn, _ = run_rhs(p, 0.9, n, g0)
+    e = rel_err(dn, dn_ref)
+    print(f"{prec} {se} nb={nb} restricted={restricted}: mean-field dn {e:.2e}")
+    assert np.abs(dn_ref).max() > 0.1 and e < 1e-11
 
 
 LADDER_CASES = [("TPP", 4, False), ("TPP", 8, False), ("TPP", 12, False), ("TPP", 20, False), ("TPP", 32, False),
@@ -190,6 +213,31 @@ def test_tc_propagation_tracks_fp64_form(se, prec):
     de = max(abs(a["e_total"] - b["e_total"]) for a, b in zip(res[prec][0], res["fp64"][0]))
     print(f"{prec} {se}: max|dG1| {dn:.2e}  max|dG2| {dg:.2e}  max|dE| {de:.2e}")
     assert dn < 1e-6 and dg < 1e-6 and de < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x4"])
+@pytest.mark.parametrize("se", ["SOA", "GW"])
+def test_tc_fp32_state_copy_is_the_rounding_of_the_state(se, prec):
+    """The last RK4 stage writes the FP32 copy of the new state (the operand of the next
+    step's products, and at stages 0-2 the base of the stage input) with integer bit
+    operations; g1g2_set_state writes it with CUDA's double-to-float conversion.  Steps
+    taken from either copy agree bit for bit: the tensor-core form has no floating-point
+    atomics, so any difference would be a conversion that is not round-to-nearest-even."""
+    from paper_2002_12717_gb300.g1g2 import from_workload
+    d = inputs.general_basis(16, 32, 8, seed=11, selfenergy=se, pulse=True)
+    d["drive"] = inputs.GaussSine(A=0.5, omega=1.5, t0=0.5, sigma=0.3)
+    out = []
+    for reload in (False, True):
+        with from_workload(d, precision=prec) as p:
+            p.propagate(0.01, 6)
+            if reload:
+                t, n, g = p.get_state()
+                p.set_state(t, n, g)
+            p.propagate(0.01, 3)
+            out.append(p.get_state())
+    assert np.abs(out[0][2]).max() > 1e-4   # a correlated state, not a trivial one
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x4"])
