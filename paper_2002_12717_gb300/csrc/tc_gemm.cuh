@@ -123,10 +123,11 @@ __device__ __forceinline__ int tile_kblocks(const GemmParams &p, int tile) {
 
 // Epilogue of one tile of a pass that is not split-K: TMEM lane r (the tile row) of the
 // accumulators at tbase (the exact one) and tbase + d1_off (the lower-order one, sliced
-// form), summed and stored through the output map of p; mx collects max |stored|.
+// form), summed and stored through the output map of p; mx collects max |stored|.  The
+// accumulators hold output columns col0 .. col0 + ncols - 1 (ncols = 0: all p.nout).
 template <bool kSliced>
 __device__ __forceinline__ void epi_store_tile(const GemmParams &p, int tile, int r, uint32_t tbase,
-                                               uint32_t d1_off, float &mx) {
+                                               uint32_t d1_off, float &mx, int col0 = 0, int ncols = 0) {
   const int N = p.nb;
   const long long NN = N;
   // the row this thread owns
@@ -173,7 +174,8 @@ __device__ __forceinline__ void epi_store_tile(const GemmParams &p, int tile, in
     cs = N * N;
     neg_im = true;
   }
-  for (int c0 = 0; c0 < p.nout; c0 += 32) {
+  const int nc = ncols ? ncols : p.nout;
+  for (int c0 = 0; c0 < nc; c0 += 32) {
     float v[32];
     tmem_ld32(tbase + (uint32_t)c0, v);
     if (kSliced) {
@@ -183,16 +185,17 @@ __device__ __forceinline__ void epi_store_tile(const GemmParams &p, int tile, in
       for (int j = 0; j < 32; ++j) v[j] += vl[j];
     }
     if (!valid) continue;
-    const int nv = min(32, p.n_valid - c0);  // columns of this chunk that are stored
+    const int g0 = col0 + c0;                              // output column of the chunk's first
+    const int nv = min(min(32, nc - c0), p.n_valid - g0);  // columns of this chunk that are stored
     if (p.epi == EP_PARTIAL) {
-      float *o = p.out + (((long long)split * 2 + u) * NN + r) * p.n_valid + c0;
+      float *o = p.out + (((long long)split * 2 + u) * NN + r) * p.n_valid + g0;
 #pragma unroll
       for (int j = 0; j < 32; ++j)
         if (j < nv) o[j] = v[j];
     } else if (p.epi == EP_PI) {
-      // columns (j, l, v) interleaved from the even global column grow + c0: complex pairs
+      // columns (j, l, v) interleaved from the even global column grow + g0: complex pairs
       float2 *o = reinterpret_cast<float2 *>(p.out);
-      const long long cg0 = grow + c0;
+      const long long cg0 = grow + g0;
 #pragma unroll
       for (int j = 0; j < 32; j += 2) {
         const long long cg = cg0 + j;
@@ -208,7 +211,7 @@ __device__ __forceinline__ void epi_store_tile(const GemmParams &p, int tile, in
 #pragma unroll
       for (int j = 0; j < 32; j += 2) {
         if (j >= nv) break;
-        const int l = (c0 + j) >> 1;
+        const int l = (g0 + j) >> 1;
         if (p.out_blk)
           reinterpret_cast<float2 *>(p.out)[blk4(NN, i0, i1, l, i2)] = make_float2(v[j], v[j + 1]);
         else
@@ -220,7 +223,7 @@ __device__ __forceinline__ void epi_store_tile(const GemmParams &p, int tile, in
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         if (j >= nv) break;
-        const int col = c0 + j, vv = col & 1, l = col >> 1;
+        const int col = g0 + j, vv = col & 1, l = col >> 1;
         const float x = (neg_im && vv) ? -v[j] : v[j];
         o[(long long)l * cs + (vv ? p.out_plane : 0)] = x;
         if (kSliced) mx = fmaxf(mx, fabsf(x));
@@ -230,7 +233,7 @@ __device__ __forceinline__ void epi_store_tile(const GemmParams &p, int tile, in
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         if (j >= nv) break;
-        const int col = c0 + j, vv = col >= N ? 1 : 0, l = col - (vv ? N : 0);
+        const int col = g0 + j, vv = col >= N ? 1 : 0, l = col - (vv ? N : 0);
         const float x = (neg_im && vv) ? -v[j] : v[j];
         o[(long long)l * cs + (vv ? p.out_plane : 0)] = x;
         if (kSliced) mx = fmaxf(mx, fabsf(x));

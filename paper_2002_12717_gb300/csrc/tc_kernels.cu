@@ -1234,6 +1234,8 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
   if (cudaMemset(t->err, 0, sizeof(int)) != cudaSuccess) return bail(G1G2_ECUDA);
   // tensor maps
   const long long N3 = N * N * N;
+  // B boxes of the 2 nb-column passes: the whole output, or one sub-tile of the TMEM-A kernel
+  const int bbox = (sliced && t->nout2 > 128) ? ts_nt(t->nout2) : t->nout2;
   if ((rc = map_linear(&t->mZin_y32, t->y32, nb, N3, 2)) || (rc = map_linear(&t->mZin_ys32, t->ys32, nb, N3, 2)) ||
       (rc = map_linear(&t->mCol_y32, t->y32, (int)N3, N, 2)) ||
       (rc = map_linear(&t->mCol_ys32, t->ys32, (int)N3, N, 2)) || (rc = map_linear(&t->mW32, t->W32, nb, N3, 1)) ||
@@ -1257,20 +1259,20 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
        ((rc = map_gather(&t->mPi_y32, t->y32, nb, 32, 1, 4)) || (rc = map_gather(&t->mPi_ys32, t->ys32, nb, 32, 1, 4)) ||
         (rc = map_b(&t->mBpi_hi, t->bpi_hi, (int)t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)) ||
         (rc = map_b(&t->mBpi_lo, t->bpi_lo, (int)t->pi_ldb, t->pi_ntiles * t->pi_nout, t->pi_nout)))) ||
-      (sliced && ((rc = map_bs(&t->mBh_s, t->bh_s, kt_c, t->nout2, t->nout2)) ||
-                  (rc = map_bs(&t->mBnr_s, t->bnr_s, kt_r, t->nout2, t->nout2)) ||
-                  (rc = map_bs(&t->mBnc_s, t->bnc_s, kt_c, t->nout2, t->nout2)) ||
-                  (rc = map_bs(&t->mBnb_s, t->bnb_s, kt_c, t->nout2, t->nout2)) ||
-                  (rc = map_bs(&t->mBnt_s, t->bnt_s, kt_r, t->nout2, t->nout2)) ||
+      (sliced && ((rc = map_bs(&t->mBh_s, t->bh_s, kt_c, t->nout2, bbox)) ||
+                  (rc = map_bs(&t->mBnr_s, t->bnr_s, kt_r, t->nout2, bbox)) ||
+                  (rc = map_bs(&t->mBnc_s, t->bnc_s, kt_c, t->nout2, bbox)) ||
+                  (rc = map_bs(&t->mBnb_s, t->bnb_s, kt_c, t->nout2, bbox)) ||
+                  (rc = map_bs(&t->mBnt_s, t->bnt_s, kt_r, t->nout2, bbox)) ||
                   (rc = map_bs(&t->mW_s, t->w_s, N3, nb, t->nout1)) ||
                   (big &&
                    ((rc = map_bs(&t->mPa_s, t->pa_s, 2 * N * N, (int)(N * N), kPiTileM, kPiSlices, kPiSlices)) ||
                     (rc = map_bs(&t->mPb_s, t->pb_s, 2 * N * N, (int)(2 * N * N), kPiTileN, kPiSlices,
                                  kPiSlices)))) ||
                   ((has_pp || has_ph) &&
-                   ((rc = map_bs(&t->mBnbr_s, t->bnbr_s, kt_r, t->nout2, t->nout2)) ||
-                    (rc = map_bs(&t->mBnbc_s, t->bnbc_s, kt_c, t->nout2, t->nout2)) ||
-                    (rc = map_bs(&t->mBnbt_s, t->bnbt_s, kt_r, t->nout2, t->nout2)))) ||
+                   ((rc = map_bs(&t->mBnbr_s, t->bnbr_s, kt_r, t->nout2, bbox)) ||
+                    (rc = map_bs(&t->mBnbc_s, t->bnbc_s, kt_c, t->nout2, bbox)) ||
+                    (rc = map_bs(&t->mBnbt_s, t->bnbt_s, kt_r, t->nout2, bbox)))) ||
                   (has_ph && (rc = map_linear(&t->mWp32, t->Wp32, nb, N3, 1)))))) {
     set_error_detail("cuTensorMapEncodeTiled failed");
     return bail(rc);
