@@ -342,11 +342,13 @@ __global__ void n_split_kernel(int nb2, const cplx *__restrict__ n, float4 *__re
   ns[c] = make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
 }
 
-constexpr int kHfRows = 8;   // rows of Wm per CTA: each n load serves eight rows
+constexpr int kHfRows = 4;   // rows of Wm per CTA: each n load serves four rows
 
 // Wds: the real Wm as float2 (hi, lo) per entry (the tensor-core forms take a real w).
 // One CTA of 256 threads per kHfRows rows: thread t takes entries c = t, t + 256, ... of
-// each row; the partial pairs are reduced over the warp and the CTA in a fixed order.
+// each row, four of them per iteration with all sixteen row loads and four n loads
+// issued before the arithmetic (the product is bound by the bytes in flight); the partial
+// pairs are reduced over the warp and the CTA in a fixed order.
 __global__ void __launch_bounds__(256) hf_build_ds_kernel(int nb, const float2 *__restrict__ Wds,
                                                            const float4 *__restrict__ ns,
                                                            const cplx *__restrict__ h, const cplx *__restrict__ D,
@@ -359,12 +361,30 @@ __global__ void __launch_bounds__(256) hf_build_ds_kernel(int nb, const float2 *
 #pragma unroll
   for (int r = 0; r < kHfRows; ++r) Sr[r] = Cr[r] = Si[r] = Ci[r] = 0.f;
   // rows past the end (a ragged last CTA) repeat the last row and are not stored, so the
-  // eight loads of an iteration carry no branch and are all issued before the arithmetic
+  // loads carry no branch
   const float2 *wbase = Wds + (long long)row0 * nb2;
   int woff[kHfRows];
 #pragma unroll
   for (int r = 0; r < kHfRows; ++r) woff[r] = (min(row0 + r, nb2 - 1) - row0) * nb2;
-  for (int c = threadIdx.x; c < nb2; c += 256) {
+  int c = threadIdx.x;
+  for (; c + 768 < nb2; c += 1024) {
+    float4 nv[4];
+    float2 w[4][kHfRows];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      nv[u] = ns[c + 256 * u];
+#pragma unroll
+      for (int r = 0; r < kHfRows; ++r) w[u][r] = wbase[woff[r] + c + 256 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int r = 0; r < kHfRows; ++r) {
+        ds_mac(Sr[r], Cr[r], w[u][r].x, w[u][r].y, nv[u].x, nv[u].z);
+        ds_mac(Si[r], Ci[r], w[u][r].x, w[u][r].y, nv[u].y, nv[u].w);
+      }
+  }
+  for (; c < nb2; c += 256) {
     const float4 nv = ns[c];
     float2 w[kHfRows];
 #pragma unroll

@@ -56,7 +56,7 @@ __host__ __device__ constexpr uint32_t stage_bytes_for(bool sliced, int nout) {
 enum ARows : int {
   AR_LINEAR = 0,   // A viewed as [plane][row][k]; tile = 128 consecutive rows
   AR_GATHER4 = 1,  // A = T[plane][a][b][c][k]; tile = rows (a: 4, b: 32) at fixed c
-  AR_SPLITK = 2,   // A = G[plane][j][c]; tile = (plane, K split), rows j
+  AR_SPLITK = 2,   // A = G[plane][j][c]; tile = 2 (K split) + plane, rows j
   AR_PI = 3,       // TF32 form: A = G[plane][i][p][k][q]; tile rows (i: 4, k: 32), K blocks over (plane, p, q)
 };
 
@@ -104,15 +104,21 @@ struct GemmParams {
   int *out_amax;      // sliced form, optional: atomic max of |stored outputs| (FP32 bits)
 };
 
+// AR_SPLITK tiles: tile = 2 split + u, so the two planes of one K split are neighbouring
+// tiles, which run at the same time on two SMs and read the same B K blocks: one of the
+// two reads comes from L2 instead of HBM.
+__device__ __forceinline__ int splitk_plane(int tile) { return tile & 1; }
+__device__ __forceinline__ int splitk_split(int tile) { return tile >> 1; }
+
 // K coordinate (elements) and first row of the B tile of K block kb of a tile
 __device__ __forceinline__ void b_coords(const GemmParams &p, int tile, int kb, int &bk, int &brow) {
-  bk = (p.a_rows == AR_SPLITK) ? ((tile % p.splits) * p.kb_per_split + kb) * kBlockK : kb * kBlockK;
+  bk = (p.a_rows == AR_SPLITK) ? (splitk_split(tile) * p.kb_per_split + kb) * kBlockK : kb * kBlockK;
   brow = (p.a_rows == AR_PI) ? (tile / p.pi_mtiles) * p.nout : 0;
 }
 
 __device__ __forceinline__ int tile_kblocks(const GemmParams &p, int tile) {
   if (p.a_rows == AR_SPLITK) {
-    const int split = tile % p.splits;
+    const int split = splitk_split(tile);
     const int b0 = split * p.kb_per_split;
     const int n = p.kb_all - b0;
     return n < p.kb_per_split ? (n > 0 ? n : 0) : p.kb_per_split;
@@ -154,8 +160,8 @@ __device__ __forceinline__ void epi_store_tile(const GemmParams &p, int tile, in
     grow = (long long)(tile / p.pi_mtiles) * p.nout;  // first global output column of the tile
     valid = i0 < NN && i2 < NN;
   } else {
-    u = tile / p.splits;
-    split = tile % p.splits;
+    u = splitk_plane(tile);
+    split = splitk_split(tile);
     valid = r < N;
   }
   // Store map of this row: out[base + l cs (+ plane for the imaginary part)],
@@ -242,6 +248,128 @@ __device__ __forceinline__ void epi_store_tile(const GemmParams &p, int tile, in
   }
 }
 
+// Staging tile of one epilogue warp for epi_store_tile_t: 16 columns x 32 rows of FP32,
+// row pitch 36 floats (writes of one column by 32 lanes and 16-byte reads of 4 rows are
+// free of bank conflicts).
+constexpr int kStgCols = 16;
+constexpr int kStgPitch = 36;
+constexpr uint32_t kStgBytes = kStgCols * kStgPitch * 4;
+constexpr uint32_t kStgAll = 4 * kStgBytes;   // four epilogue warps
+
+// the passes epi_store_tile_t serves
+__host__ __device__ __forceinline__ bool epi_transposed(const GemmParams &p) {
+  return (p.a_rows == AR_LINEAR || p.a_rows == AR_GATHER4) &&
+         (p.epi == EP_SWAP34 || p.epi == EP_EXCH_T || p.epi == EP_GATHER_TCONJ);
+}
+
+// Epilogue of one row tile of the sliced form (rows r, output columns 0 .. p.nout - 1) for
+// the row maps AR_LINEAR, AR_GATHER4 and the stores EP_SWAP34, EP_EXCH_T, EP_GATHER_TCONJ
+// (planar, col_il, or out_il complex, optionally 4^4-blocked) -- every nb^5 pass but the
+// collision integral.  Planar outputs: each 32-column chunk read from TMEM goes through
+// the warp's staging tile in two rounds of 16 columns, so that a lane stores four
+// consecutive rows of one column as one 16-byte vector: with nb % 4 == 0 and row tiles
+// starting at multiples of 4, four consecutive rows of a warp are four consecutive output
+// elements under every one of these maps (and 16-byte aligned); one store per four rows
+// and column instead of one per row.  Interleaved complex outputs already fill a 32-byte
+// sector with the 8-byte pairs of four rows and are stored per row.  No branch per
+// element, and the address split into a per-row base and a per-column term.
+__device__ __forceinline__ void epi_store_tile_t(const GemmParams &p, int tile, int r, uint32_t tbase,
+                                                 uint32_t d1_off, float &mx, float *stg) {
+  const int N = p.nb;
+  const long long NN = N;
+  const int lane = threadIdx.x & 31;
+  // the row this lane owns
+  bool valid;
+  long long i0, i1, i2;
+  if (p.a_rows == AR_LINEAR) {
+    const long long grow = (long long)tile * kTileM + r;
+    valid = grow < p.rows;
+    i2 = grow % NN;
+    i1 = (grow / NN) % NN;
+    i0 = grow / (NN * NN);
+  } else {  // AR_GATHER4
+    const int bB = tile % p.g_nb, aB = (tile / p.g_nb) % p.g_na, c = tile / (p.g_nb * p.g_na);
+    i0 = aB * 4 + r / 32;
+    i1 = bB * 32 + r % 32;
+    i2 = c;
+    valid = i0 < NN && i1 < NN;
+  }
+  // per-row part of the output index: planar out[base + l cs (+ plane)], or for out_il the
+  // float2 index base + l cs, or blk4(i0, i1, l, i2) = blk4(i0, i1, 0, i2) + blk4(0, 0, l, 0)
+  long long base = 0;
+  int cs = 0;
+  bool neg_im = false;
+  if (p.epi == EP_SWAP34) {
+    base = (i0 * NN + i1) * NN * NN + i2;
+    cs = N;
+  } else if (p.epi == EP_EXCH_T) {
+    base = (i1 * NN + i0) * NN * NN + i2;
+    cs = N;
+  } else {  // EP_GATHER_TCONJ
+    base = i2 * NN * NN * NN + i0 * NN + i1;
+    cs = N * N;
+    neg_im = true;
+  }
+  if (p.out_il && p.out_blk) base = blk4(NN, i0, i1, 0, i2);
+  // this lane stores rows 4 q .. 4 q + 3 of the warp's 32, column group jq
+  const int q = lane & 7, jq = lane >> 3;
+  const long long qbase = __shfl_sync(0xffffffffu, base, 4 * q);
+  const bool qvalid = __shfl_sync(0xffffffffu, valid ? 1 : 0, 4 * q) != 0;
+  for (int c0 = 0; c0 < p.nout; c0 += 32) {
+    float v[32];
+    tmem_ld32(tbase + (uint32_t)c0, v);
+    {
+      float vl[32];
+      tmem_ld32(tbase + d1_off + (uint32_t)c0, vl);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] += vl[j];
+    }
+    if (p.out_il) {
+      // interleaved complex output: each lane stores its own row, one 8-byte pair per
+      // column pair (2 l, 2 l + 1); four rows of a warp fill a 32-byte sector
+      const int nv = min(32, p.n_valid - c0);
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) {
+        if (valid && j < nv) {
+          const int l = (c0 + j) >> 1;
+          const long long e = base + (p.out_blk ? blk4(NN, 0, 0, l, 0) : (long long)l * cs);
+          reinterpret_cast<float2 *>(p.out)[e] = make_float2(v[j], v[j + 1]);
+          mx = fmaxf(mx, fmaxf(fabsf(v[j]), fabsf(v[j + 1])));
+        }
+      }
+      continue;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g0 = c0 + kStgCols * h;                       // output column of the round's first
+      const int nv = min(kStgCols, p.n_valid - g0);           // columns of this round that are stored
+#pragma unroll
+      for (int j = 0; j < kStgCols; ++j) stg[j * kStgPitch + lane] = v[kStgCols * h + j];
+      __syncwarp();
+#pragma unroll
+      for (int it = 0; it < 4; ++it) {
+        const int jj = 4 * it + jq;
+        float4 x = *reinterpret_cast<const float4 *>(stg + jj * kStgPitch + 4 * q);
+        if (qvalid && jj < nv) {
+          const int col = g0 + jj;
+          int vv, l;
+          if (p.col_il) {
+            vv = col & 1;
+            l = col >> 1;
+          } else {
+            vv = col >= N ? 1 : 0;
+            l = col - (vv ? N : 0);
+          }
+          if (neg_im && vv) x = make_float4(-x.x, -x.y, -x.z, -x.w);
+          *reinterpret_cast<float4 *>(p.out + qbase + (long long)l * cs + (vv ? p.out_plane : 0)) = x;
+          mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+        }
+      }
+      __syncwarp();   // the staging tile is read before the next round overwrites it
+    }
+  }
+}
+
 // tmBhi/tmBlo: TF32 hi and lo parts of B; in the sliced form tmBhi holds the
 // four BF16 slices of B as [slice][row][k] (tmBlo unused).
 //
@@ -279,6 +407,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   uint64_t *fin = tempty + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
   float2 *acc2 = reinterpret_cast<float2 *>(bar_area + 256);  // (sum, error) pairs
+  float *stg_all = reinterpret_cast<float *>(bar_area + 256);  // or: epilogue staging (kStgAll bytes)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -343,7 +472,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const int pp = rest % N, u = rest / N;
             tma_load_5d(dst, &tmA, bar, qb * kBlockK, kB * 32, pp, iB * 4, u);
           } else {
-            const int u = tile / p.splits, split = tile % p.splits;
+            const int u = splitk_plane(tile), split = splitk_split(tile);
             tma_load_3d(dst, &tmA, bar, (split * p.kb_per_split + kb) * kBlockK, 0, u);
           }
           if (!kSliced) {
@@ -527,7 +656,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       bool ok = true;
       for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
         const int nkb = tile_kblocks(p, tile);
-        const int u = tile / p.splits, split = tile % p.splits;
+        const int u = splitk_plane(tile), split = splitk_split(tile);
         if (r < N)
           for (int col = 0; col < nv; ++col) acc2[r * ld + col] = make_float2(0.f, 0.f);
         const int nchunks = (nkb + p.kb_chunks - 1) / p.kb_chunks;
@@ -576,7 +705,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       // warp-uniform: the TMEM loads below are .sync.aligned
       if (!__all_sync(0xffffffffu, mbar_wait(&tfull[acc], acc_ph, p.err))) break;
       tc_fence_after();
-      epi_store_tile<kSliced>(p, tile, r, tmem_base + lane_base + (uint32_t)(acc * kAccCols), d1_off, mx);
+      if (kSliced && epi_transposed(p))
+        epi_store_tile_t(p, tile, r, tmem_base + lane_base + (uint32_t)(acc * kAccCols), d1_off, mx,
+                         stg_all + (warp - kEpiWarp0) * (kStgCols * kStgPitch));
+      else
+        epi_store_tile<kSliced>(p, tile, r, tmem_base + lane_base + (uint32_t)(acc * kAccCols), d1_off, mx);
       tc_fence_before();
       mbar_arrive(&tempty[acc]);
       if (++acc == nbuf) { acc = 0; acc_ph ^= 1u; }

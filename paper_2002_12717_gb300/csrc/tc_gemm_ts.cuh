@@ -7,20 +7,22 @@
 //    (tcgen05.st) and the MMAs read A from there, so the A slices never pass
 //    through shared memory (ten MMAs per 16-element K step would read them
 //    ten times);
-//  * each 128-row tile is computed as nsub = ceil(nout / 96) sub-tiles of nt <= 96
-//    output columns, one after the other, into two accumulator pairs used in
-//    turn: the epilogue drains one sub-tile while the MMAs of the next run.  (With
-//    one 192-column pair per tile the MMA thread spent 46% of its time waiting for
-//    the drain.)  The A K blocks are loaded and sliced once per sub-tile; the
-//    second load of a block comes from L2;
+//  * one MMA spans the whole output width (N = nout): wait-time counters put
+//    the tensor core near its nominal rate while it runs N = 192 MMAs, and at
+//    about 60% of that rate on the same work as N = 96 MMAs, so the two
+//    accumulators (2 x 192 columns) stay single-buffered and the epilogue is
+//    made short instead: each 16-column round goes from TMEM through a staging
+//    tile in shared memory, and every lane stores four consecutive rows of a
+//    column as one 16-byte vector (one store per row and column took 3-7 us a
+//    tile, as long as the MMAs);
 //  * B arrives in a ring of its own, three stages deep, filled by a producer
-//    warp of its own (nt rows per stage, rows past nout zero-filled by the TMA);
-//  * the FP32 A tiles land in a ring of up to six slots.
+//    warp of its own;
+//  * the FP32 A tiles land in a ring of their own slots.
 //
-// TMEM (512 columns): accumulator pair b (exact, lower-order) at columns 192 b
-// and 192 b + 96, nt columns each; two A-slice buffers of 64 columns at 384 and
-// 448: four slices of a 128 x 32 tile, two BF16 per 32-bit column, slice q at
-// +16 q, the 16-element K step k at +8 k.
+// TMEM (512 columns): exact accumulator at column 0, lower-order one at 192,
+// two A-slice buffers of 64 columns at 384 and 448: four slices of a 128 x 32
+// tile, two BF16 per 32-bit column, slice q at +16 q, the 16-element K step k
+// at +8 k.
 //
 // Warps (480 threads): 0 A producer, 1 TMEM owner and MMA issuer, 2 B
 // producer, 3-10 converters (two per TMEM lane quarter, one per half of the
@@ -38,26 +40,23 @@ constexpr int kTsConvWarp0 = 3;
 constexpr int kTsConvThreads = 256;
 constexpr int kTsEpiWarp0 = 11;
 constexpr int kTsBStages = 3;
-constexpr int kTsMaxNt = 96;
-// TMEM columns: accumulator pair b, lower-order accumulator offset, A-slice buffer a
-__host__ __device__ constexpr uint32_t ts_dcol(int b) { return 192u * (uint32_t)b; }
-constexpr uint32_t kTsD1Off = 96;
+// TMEM columns: exact accumulator, lower-order accumulator, A-slice buffer a
+constexpr uint32_t kTsD1Col = 192;
 __host__ __device__ constexpr uint32_t ts_abuf(int a) { return 384u + 64u * (uint32_t)a; }
 
-// sub-tiles per row tile and their width (a multiple of 16, at most 96)
-__host__ __device__ constexpr int ts_nsub(int nout) { return (nout + kTsMaxNt - 1) / kTsMaxNt; }
-__host__ __device__ constexpr int ts_nt(int nout) { return ((nout + ts_nsub(nout) - 1) / ts_nsub(nout) + 15) / 16 * 16; }
+// rows of the B box: the whole output width
+__host__ __device__ constexpr int ts_nt(int nout) { return nout; }
 
-__host__ __device__ constexpr uint32_t ts_bstage_bytes(int nout) { return (uint32_t)kSlices * ts_nt(nout) * kBlockK * 2; }
+__host__ __device__ constexpr uint32_t ts_bstage_bytes(int nout) { return (uint32_t)kSlices * nout * kBlockK * 2; }
 
 // dynamic shared memory and FP32 slots of tc_gemm_ts_kernel for an output of nout columns
 __host__ __device__ constexpr int ts_fstages(int nout) {
-  return (int)((224u * 1024u - kTsBStages * ts_bstage_bytes(nout)) / kABytes) > 6
+  return (int)((224u * 1024u - kTsBStages * ts_bstage_bytes(nout) - kStgAll) / kABytes) > 6
              ? 6
-             : (int)((224u * 1024u - kTsBStages * ts_bstage_bytes(nout)) / kABytes);
+             : (int)((224u * 1024u - kTsBStages * ts_bstage_bytes(nout) - kStgAll) / kABytes);
 }
 __host__ __device__ constexpr size_t ts_smem_bytes(int nout) {
-  return 1024 + (size_t)ts_fstages(nout) * kABytes + (size_t)kTsBStages * ts_bstage_bytes(nout) + 256;
+  return 1024 + (size_t)ts_fstages(nout) * kABytes + (size_t)kTsBStages * ts_bstage_bytes(nout) + kStgAll + 256;
 }
 
 __global__ void __launch_bounds__(kTsThreads, 1)
@@ -66,21 +65,21 @@ __global__ void __launch_bounds__(kTsThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int nf = ts_fstages(p.nout);
-  const int nsub = ts_nsub(p.nout), nt = ts_nt(p.nout);
-  const uint32_t b_bytes = (uint32_t)nt * kBlockK * 2;         // one slice of a B stage
+  const uint32_t b_bytes = (uint32_t)p.nout * kBlockK * 2;     // one slice of a B stage
   const uint32_t bstage = ts_bstage_bytes(p.nout);
   uint8_t *fring = smem;
   uint8_t *bring = smem + (size_t)nf * kABytes;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(bring + (size_t)kTsBStages * bstage);
+  float *stg_all = reinterpret_cast<float *>(bring + (size_t)kTsBStages * bstage);   // epilogue staging
+  uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(stg_all) + kStgAll);
   uint64_t *ffull = bars;                     // FP32 A tile landed in slot
   uint64_t *fempty = ffull + nf;              // slot read by the converters
   uint64_t *bfull = fempty + nf;              // B slices landed in stage
   uint64_t *bempty = bfull + kTsBStages;      // stage read by the MMAs
   uint64_t *aready = bempty + kTsBStages;     // A slices stored in TMEM buffer
   uint64_t *afree = aready + 2;               // TMEM buffer read by the MMAs
-  uint64_t *tfull = afree + 2;                // accumulator pair complete (two)
-  uint64_t *tempty = tfull + 2;               // accumulator pair drained (two)
-  uint64_t *fin = tempty + 2;
+  uint64_t *tfull = afree + 2;                // accumulators complete
+  uint64_t *tempty = tfull + 1;               // accumulators drained
+  uint64_t *fin = tempty + 1;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -96,9 +95,9 @@ __global__ void __launch_bounds__(kTsThreads, 1)
     for (int a = 0; a < 2; ++a) {
       mbar_init(&aready[a], kTsConvThreads);
       mbar_init(&afree[a], 1);
-      mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 128);
     }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 128);
     mbar_init(fin, 1);
     mbar_fence_init();
   }
@@ -115,23 +114,21 @@ __global__ void __launch_bounds__(kTsThreads, 1)
       bool ok = true;
       for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
         const int nkb = tile_kblocks(p, tile);
-        for (int sub = 0; sub < nsub && ok; ++sub) {
-          for (int kb = 0; kb < nkb; ++kb) {
-            if (!mbar_wait(&fempty[f], ph ^ 1u, p.err)) { ok = false; break; }
-            uint8_t *dst = fring + (size_t)f * kABytes;
-            mbar_arrive_expect_tx(&ffull[f], kABytes);
-            if (p.a_rows == AR_LINEAR) {
-              const bool second = p.kb_first && kb >= p.kb_first;
-              const int kl = second ? kb - p.kb_first : kb;
-              const int u = kl / p.kb_per_plane, pb = kl % p.kb_per_plane;
-              tma_load_3d(dst, second ? &tmA2 : &tmA, &ffull[f], pb * kBlockK, tile * kTileM, u);
-            } else {  // AR_GATHER4
-              const int u = kb / p.kb_per_plane, pb = kb % p.kb_per_plane;
-              const int bB = tile % p.g_nb, aB = (tile / p.g_nb) % p.g_na, c = tile / (p.g_nb * p.g_na);
-              tma_load_5d(dst, &tmA, &ffull[f], pb * kBlockK, c, bB * 32, aB * 4, u);
-            }
-            if (++f == nf) { f = 0; ph ^= 1u; }
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(&fempty[f], ph ^ 1u, p.err)) { ok = false; break; }
+          uint8_t *dst = fring + (size_t)f * kABytes;
+          mbar_arrive_expect_tx(&ffull[f], kABytes);
+          if (p.a_rows == AR_LINEAR) {
+            const bool second = p.kb_first && kb >= p.kb_first;
+            const int kl = second ? kb - p.kb_first : kb;
+            const int u = kl / p.kb_per_plane, pb = kl % p.kb_per_plane;
+            tma_load_3d(dst, second ? &tmA2 : &tmA, &ffull[f], pb * kBlockK, tile * kTileM, u);
+          } else {  // AR_GATHER4
+            const int u = kb / p.kb_per_plane, pb = kb % p.kb_per_plane;
+            const int bB = tile % p.g_nb, aB = (tile / p.g_nb) % p.g_na, c = tile / (p.g_nb * p.g_na);
+            tma_load_5d(dst, &tmA, &ffull[f], pb * kBlockK, c, bB * 32, aB * 4, u);
           }
+          if (++f == nf) { f = 0; ph ^= 1u; }
         }
       }
     }
@@ -143,68 +140,62 @@ __global__ void __launch_bounds__(kTsThreads, 1)
       bool ok = true;
       for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
         const int nkb = tile_kblocks(p, tile);
-        for (int sub = 0; sub < nsub && ok; ++sub) {
-          for (int kb = 0; kb < nkb; ++kb) {
-            if (!mbar_wait(&bempty[s], ph ^ 1u, p.err)) { ok = false; break; }
-            int bk, brow;
-            b_coords(p, tile, kb, bk, brow);
-            mbar_arrive_expect_tx(&bfull[s], kSlices * b_bytes);
-            // the nt B rows of this sub-tile, all four slices (rows past nout read as zero)
-            tma_load_3d(bring + (size_t)s * bstage, &tmB, &bfull[s], bk, brow + sub * nt, 0);
-            if (++s == kTsBStages) { s = 0; ph ^= 1u; }
-          }
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(&bempty[s], ph ^ 1u, p.err)) { ok = false; break; }
+          int bk, brow;
+          b_coords(p, tile, kb, bk, brow);
+          mbar_arrive_expect_tx(&bfull[s], kSlices * b_bytes);
+          tma_load_3d(bring + (size_t)s * bstage, &tmB, &bfull[s], bk, brow, 0);   // all four slices
+          if (++s == kTsBStages) { s = 0; ph ^= 1u; }
         }
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kTileM, nt);
-      int s = 0, a = 0, job = 0;
-      uint32_t ph = 0, aph = 0;
+      const uint32_t idesc = idesc_bf16(kTileM, p.nout);
+      const uint32_t d0 = tmem_base, d1 = tmem_base + kTsD1Col;
+      int s = 0, a = 0;
+      uint32_t ph = 0, aph = 0, acc_ph = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
         const int nkb = tile_kblocks(p, tile);
-        for (int sub = 0; sub < nsub && ok; ++sub, ++job) {
-          const int buf = job & 1;
-          // the epilogue has drained this accumulator pair's previous sub-tile
-          if (!mbar_wait(&tempty[buf], ((uint32_t)(job >> 1) & 1u) ^ 1u, p.err)) { ok = false; break; }
+        if (!mbar_wait(tempty, acc_ph ^ 1u, p.err)) break;   // the epilogue has drained the last tile
+        tc_fence_after();
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(&aready[a], aph, p.err) || !mbar_wait(&bfull[s], ph, p.err)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t d0 = tmem_base + ts_dcol(buf), d1 = d0 + kTsD1Off;
-          for (int kb = 0; kb < nkb; ++kb) {
-            if (!mbar_wait(&aready[a], aph, p.err) || !mbar_wait(&bfull[s], ph, p.err)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t ab = tmem_base + ts_abuf(a);
-            const uint32_t bs0 = smem_u32(bring + (size_t)s * bstage);
+          const uint32_t ab = tmem_base + ts_abuf(a);
+          const uint32_t bs0 = smem_u32(bring + (size_t)s * bstage);
 #pragma unroll
-            for (int k = 0; k < kBlockK / 16; ++k) {
-              uint32_t at[kSlices];
-              uint64_t bd[kSlices];
+          for (int k = 0; k < kBlockK / 16; ++k) {
+            uint32_t at[kSlices];
+            uint64_t bd[kSlices];
 #pragma unroll
-              for (int q = 0; q < kSlices; ++q) {
-                at[q] = ab + 16u * q + 8u * k;
-                bd[q] = smem_desc_sw64(bs0 + q * b_bytes + 32 * k);
-              }
-              const uint32_t acc_in = (kb | k) ? 1u : 0u;
-              mma_bf16_ts(d0, at[0], bd[0], idesc, acc_in);          // exact: integers < 2^24
-              mma_bf16_ts(d1, at[0], bd[1], idesc, acc_in);          // order 1 ...
-              mma_bf16_ts(d1, at[1], bd[0], idesc, 1u);
-              mma_bf16_ts(d1, at[0], bd[2], idesc, 1u);              // order 2
-              mma_bf16_ts(d1, at[1], bd[1], idesc, 1u);
-              mma_bf16_ts(d1, at[2], bd[0], idesc, 1u);
-              mma_bf16_ts(d1, at[0], bd[3], idesc, 1u);              // order 3
-              mma_bf16_ts(d1, at[1], bd[2], idesc, 1u);
-              mma_bf16_ts(d1, at[2], bd[1], idesc, 1u);
-              mma_bf16_ts(d1, at[3], bd[0], idesc, 1u);
+            for (int q = 0; q < kSlices; ++q) {
+              at[q] = ab + 16u * q + 8u * k;
+              bd[q] = smem_desc_sw64(bs0 + q * b_bytes + 32 * k);
             }
-            mma_commit(&bempty[s]);   // the B stage and the A buffer are free once these MMAs have read them
-            mma_commit(&afree[a]);
-            if (++s == kTsBStages) { s = 0; ph ^= 1u; }
-            if (++a == 2) { a = 0; aph ^= 1u; }
+            const uint32_t acc_in = (kb | k) ? 1u : 0u;
+            mma_bf16_ts(d0, at[0], bd[0], idesc, acc_in);          // exact: integers < 2^24
+            mma_bf16_ts(d1, at[0], bd[1], idesc, acc_in);          // order 1 ...
+            mma_bf16_ts(d1, at[1], bd[0], idesc, 1u);
+            mma_bf16_ts(d1, at[0], bd[2], idesc, 1u);              // order 2
+            mma_bf16_ts(d1, at[1], bd[1], idesc, 1u);
+            mma_bf16_ts(d1, at[2], bd[0], idesc, 1u);
+            mma_bf16_ts(d1, at[0], bd[3], idesc, 1u);              // order 3
+            mma_bf16_ts(d1, at[1], bd[2], idesc, 1u);
+            mma_bf16_ts(d1, at[2], bd[1], idesc, 1u);
+            mma_bf16_ts(d1, at[3], bd[0], idesc, 1u);
           }
-          if (!ok) break;
-          mma_commit(&tfull[buf]);
+          mma_commit(&bempty[s]);   // the B stage and the A buffer are free once these MMAs have read them
+          mma_commit(&afree[a]);
+          if (++s == kTsBStages) { s = 0; ph ^= 1u; }
+          if (++a == 2) { a = 0; aph ^= 1u; }
         }
+        if (!ok) break;
+        mma_commit(tfull);
+        acc_ph ^= 1u;
       }
       // every MMA issued by this thread has completed before TMEM is released
       mma_commit(fin);
@@ -227,63 +218,56 @@ __global__ void __launch_bounds__(kTsThreads, 1)
     bool ok = true;
     for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
       const int nkb = tile_kblocks(p, tile);
-      for (int sub = 0; sub < nsub && ok; ++sub) {
-        for (int kb = 0; kb < nkb; ++kb) {
-          // warp-uniform waits: the TMEM stores below are .sync.aligned
-          if (!__all_sync(0xffffffffu, mbar_wait(&afree[a], aph ^ 1u, p.err) && mbar_wait(&ffull[f], fph, p.err))) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          // this thread's half row: logical floats 16 half .. 16 half + 15 of row r, four
-          // 16-byte chunks of the 128-byte-swizzled FP32 tile
-          const uint8_t *rowp = fring + (size_t)f * kABytes + (size_t)r * 128;
-          uint32_t w[kSlices][8];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int chunk = 4 * half + c;
-            const float4 x = *reinterpret_cast<const float4 *>(rowp + ((chunk ^ (r & 7)) << 4));
-            float2 lo2[kSlices], hi2[kSlices];
-            slice4x2(make_float2(x.x, x.y), lo2, cut2);
-            slice4x2(make_float2(x.z, x.w), hi2, cut2);
-#pragma unroll
-            for (int q = 0; q < kSlices; ++q) {
-              w[q][2 * c] = pack_bf16(lo2[q].x, lo2[q].y);
-              w[q][2 * c + 1] = pack_bf16(hi2[q].x, hi2[q].y);
-            }
-          }
-          const uint32_t ab = tmem_base + lane_addr + ts_abuf(a) + 8u * half;
-#pragma unroll
-          for (int q = 0; q < kSlices; ++q) tmem_st8(ab + 16u * q, w[q]);
-          tmem_wait_st();
-          tc_fence_before();
-          fence_proxy_async_smem();   // the FP32 slot's reads precede its next TMA write
-          mbar_arrive(&aready[a]);
-          mbar_arrive(&fempty[f]);
-          if (++f == nf) { f = 0; fph ^= 1u; }
-          if (++a == 2) { a = 0; aph ^= 1u; }
+      for (int kb = 0; kb < nkb; ++kb) {
+        // warp-uniform waits: the TMEM stores below are .sync.aligned
+        if (!__all_sync(0xffffffffu, mbar_wait(&afree[a], aph ^ 1u, p.err) && mbar_wait(&ffull[f], fph, p.err))) {
+          ok = false;
+          break;
         }
+        tc_fence_after();
+        // this thread's half row: logical floats 16 half .. 16 half + 15 of row r, four
+        // 16-byte chunks of the 128-byte-swizzled FP32 tile
+        const uint8_t *rowp = fring + (size_t)f * kABytes + (size_t)r * 128;
+        uint32_t w[kSlices][8];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int chunk = 4 * half + c;
+          const float4 x = *reinterpret_cast<const float4 *>(rowp + ((chunk ^ (r & 7)) << 4));
+          float2 lo2[kSlices], hi2[kSlices];
+          slice4x2(make_float2(x.x, x.y), lo2, cut2);
+          slice4x2(make_float2(x.z, x.w), hi2, cut2);
+#pragma unroll
+          for (int q = 0; q < kSlices; ++q) {
+            w[q][2 * c] = pack_bf16(lo2[q].x, lo2[q].y);
+            w[q][2 * c + 1] = pack_bf16(hi2[q].x, hi2[q].y);
+          }
+        }
+        const uint32_t ab = tmem_base + lane_addr + ts_abuf(a) + 8u * half;
+#pragma unroll
+        for (int q = 0; q < kSlices; ++q) tmem_st8(ab + 16u * q, w[q]);
+        tmem_wait_st();
+        tc_fence_before();
+        fence_proxy_async_smem();   // the FP32 slot's reads precede its next TMA write
+        mbar_arrive(&aready[a]);
+        mbar_arrive(&fempty[f]);
+        if (++f == nf) { f = 0; fph ^= 1u; }
+        if (++a == 2) { a = 0; aph ^= 1u; }
       }
     }
   } else {
     // ------------------------------------------------------------ epilogue (warps 11-14)
     const int r = 32 * (warp & 3) + lane;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    float *stg = stg_all + (warp - kTsEpiWarp0) * (kStgCols * kStgPitch);
+    uint32_t acc_ph = 0;
     float mx = 0.f;
-    int job = 0;
-    bool ok = true;
-    for (int tile = blockIdx.x; tile < p.tiles && ok; tile += gridDim.x) {
-      for (int sub = 0; sub < nsub; ++sub, ++job) {
-        const int buf = job & 1;
-        if (!__all_sync(0xffffffffu, mbar_wait(&tfull[buf], (uint32_t)(job >> 1) & 1u, p.err))) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        epi_store_tile<true>(p, tile, r, tmem_base + lane_base + ts_dcol(buf), kTsD1Off, mx, sub * nt, nt);
-        tc_fence_before();
-        mbar_arrive(&tempty[buf]);
-      }
+    for (int tile = blockIdx.x; tile < p.tiles; tile += gridDim.x) {
+      if (!__all_sync(0xffffffffu, mbar_wait(tfull, acc_ph, p.err))) break;
+      tc_fence_after();
+      epi_store_tile_t(p, tile, r, tmem_base + lane_base, kTsD1Col, mx, stg);
+      tc_fence_before();
+      mbar_arrive(tempty);
+      acc_ph ^= 1u;
     }
     if (p.out_amax) {
 #pragma unroll

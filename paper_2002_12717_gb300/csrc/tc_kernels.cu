@@ -990,7 +990,9 @@ void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, 
                  const CUtensorMap &Bl, GemmParams gp, bool sliced = false, const CUtensorMap *A2 = nullptr) {
   gp.err = t->err;
   int stages = 0, fstages = 0;
-  const size_t acc64 = gp.kb_chunks ? (size_t)gp.nb * (gp.n_valid + 1) * sizeof(float2) : 0;
+  // the region after the barriers: split-K partial pairs, or the staging of the transposed epilogue
+  const size_t acc64 = gp.kb_chunks ? (size_t)gp.nb * (gp.n_valid + 1) * sizeof(float2)
+                                    : ((sliced && epi_transposed(gp)) ? kStgAll : 0);
   const size_t smem = gemm_smem(sliced, gp.nout, &stages, &fstages, acc64);
   const int grid = std::max(1, std::min(gp.tiles, t->sms));
   L.before(tag);
@@ -1279,7 +1281,8 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
   }
   int st = 0, fst = 0;
   const size_t acc64 = (size_t)nb * (nb + 1) * sizeof(float2);
-  size_t smax = std::max(gemm_smem(sliced, t->nout2, &st, &fst), gemm_smem(sliced, t->nout1, &st, &fst, acc64));
+  size_t smax = std::max(gemm_smem(sliced, t->nout2, &st, &fst, sliced ? kStgAll : 0),
+                         gemm_smem(sliced, t->nout1, &st, &fst, acc64));
   if (big && !sliced) smax = std::max(smax, gemm_smem(sliced, t->pi_nout, &st, &fst));
   if (smax > 227 * 1024) {
     set_error_detail("basis too large for the FP64 split-K accumulator of the tensor-core collision integral");
