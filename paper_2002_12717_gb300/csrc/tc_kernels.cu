@@ -38,6 +38,7 @@
 #include "tc_gemm.cuh"
 #include "tc_pi_gemm.cuh"
 #include "tc_gemm_ts.cuh"
+#include "tc_coll_ts.cuh"
 
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -985,6 +986,9 @@ bool use_ts_gemm(const GemmParams &g) {
   return g.nout > 128 && g.nout <= 192 && !g.kb_chunks && (g.a_rows == AR_LINEAR || g.a_rows == AR_GATHER4);
 }
 
+// The sliced collision integral (split-K over nb^3, N = nb <= 96) runs on tc_collision_ts_kernel.
+bool use_collision_ts(const GemmParams &g) { return g.a_rows == AR_SPLITK && g.kb_chunks && g.nout <= 96; }
+
 // sliced: the BF16-slice form (Bh = slices of B, Bl unused); otherwise TF32 hi/lo
 void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, const CUtensorMap &Bh,
                  const CUtensorMap &Bl, GemmParams gp, bool sliced = false, const CUtensorMap *A2 = nullptr) {
@@ -998,6 +1002,9 @@ void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, 
   L.before(tag);
   if (sliced && use_ts_gemm(gp)) {
     tc_gemm_ts_kernel<<<grid, kTsThreads, ts_smem_bytes(gp.nout), L.stream>>>(A, A2 ? *A2 : A, Bh, gp);
+  } else if (sliced && use_collision_ts(gp)) {
+    tc_collision_ts_kernel<<<grid, kTsThreads, ct_smem_bytes(gp.nout, ct_acc_bytes(gp.nb, gp.n_valid)), L.stream>>>(
+        A, Bh, gp);
   } else if (sliced) {
     tc_gemm_kernel<true><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages, fstages);
   } else {
@@ -1303,7 +1310,9 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
       !raise_limit((const void *)orbit_assemble_kernel<kAsmStage>, 4 * BEL * sizeof(float2)) ||
       !raise_limit((const void *)orbit_assemble_kernel<kAsmLast>, 4 * BEL * sizeof(float2)) ||
       (big && sliced && !raise_limit((const void *)tc_pi_gemm_kernel, kPiSmemBytes)) ||
-      (sliced && t->nout2 > 128 && !raise_limit((const void *)tc_gemm_ts_kernel, ts_smem_bytes(t->nout2)))) {
+      (sliced && t->nout2 > 128 && !raise_limit((const void *)tc_gemm_ts_kernel, ts_smem_bytes(t->nout2))) ||
+      (sliced && t->nout1 <= 96 &&
+       !raise_limit((const void *)tc_collision_ts_kernel, ct_smem_bytes(t->nout1, ct_acc_bytes(nb, nb))))) {
     cudaGetLastError();
     set_error_detail("cannot raise the shared-memory limit of the tensor-core kernels");
     return bail(G1G2_ECUDA);
