@@ -458,19 +458,28 @@ __device__ __forceinline__ void rk4_apply(long long e, cplx k, int stage, double
 }
 
 // dn = -i[hHF, n] - (I + I^dag): one thread per element, explicit sums over p.
-__global__ void g1_update_kernel(int nb, const cplx *__restrict__ hhf, const cplx *__restrict__ n,
-                                 const cplx *__restrict__ I, int stage, double dt, cplx *y, cplx *ys, cplx *acc,
-                                 cplx *kout) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+// dn/dt = -i [hHF, n] - (I + I^dag) (Eqs. eom_gone-2, eom_gone-I) and its RK4 stage update:
+// one warp per element (i, j), the lanes splitting the sum over p and reducing in a fixed
+// order, so that the nb^3 FP64 multiply-adds spread over every SM.
+__global__ void __launch_bounds__(256) g1_update_kernel(int nb, const cplx *__restrict__ hhf,
+                                                        const cplx *__restrict__ n, const cplx *__restrict__ I,
+                                                        int stage, double dt, cplx *y, cplx *ys, cplx *acc,
+                                                        cplx *kout) {
+  const int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (idx >= nb * nb) return;
   const int i = idx / nb, j = idx % nb;
   cplx comm = {0.0, 0.0};
-  for (int p = 0; p < nb; ++p) {
+  for (int p = lane; p < nb; p += 32) {
     comm = cfma(hhf[i * nb + p], n[p * nb + j], comm);
-    const cplx np_ = n[i * nb + p];
-    const cplx hp = hhf[p * nb + j];
-    comm = csub(comm, cmul(np_, hp));
+    comm = csub(comm, cmul(n[i * nb + p], hhf[p * nb + j]));
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    comm.x += __shfl_xor_sync(0xffffffffu, comm.x, o);
+    comm.y += __shfl_xor_sync(0xffffffffu, comm.y, o);
+  }
+  if (lane != 0) return;
   cplx k = mul_minus_i(comm);
   if (I) {
     const cplx a = I[i * nb + j];
@@ -631,8 +640,8 @@ __global__ void obs_two_body_kernel(int nb, const cplx *__restrict__ W, const cp
       const cplx w = W[r * M + c];
       const cplx g = tile[threadIdx.x][yy];   // G[(c),(r)]
       acc += w.x * g.x - w.y * g.y;
-      const cplx gd = G[r * M + c];
-      if (!isfinite(gd.x) || !isfinite(gd.y)) bad += 1.0;
+      // every element of G lands in exactly one transposed tile: count the non-finite ones there
+      if (!isfinite(g.x) || !isfinite(g.y)) bad += 1.0;
     }
   }
   s0[tid] = acc;
@@ -796,7 +805,7 @@ void one_pm(Launcher &L, int nb, const cplx *n, double eta, cplx *nbar) {
 void g1_update(Launcher &L, int nb, const cplx *hhf, const cplx *n, const cplx *I, Rk4Stage st, cplx *y, cplx *ys,
                cplx *acc, cplx *kout) {
   L.before("g1_update");
-  g1_update_kernel<<<(nb * nb + 127) / 128, 128, 0, L.stream>>>(nb, hhf, n, I, st.stage, st.dt, y, ys, acc, kout);
+  g1_update_kernel<<<(nb * nb + 7) / 8, 256, 0, L.stream>>>(nb, hhf, n, I, st.stage, st.dt, y, ys, acc, kout);
   L.after_launch();
 }
 
