@@ -1149,12 +1149,13 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
             }
             if (canon) blk.push_back(make_int4(a, b, c, d));
           }
-    // CTA order: the orbits of the 4^4 blocks that make up one orbit of 8^4 blocks run one
-    // after another.  The state copy and the stage input are planar FP32 in natural order,
-    // so a 4^4 block covers only half of each 32-byte sector along the last index; the
-    // other half lies in the neighbouring 4^4 block of the same 8^4 block, which belongs
-    // to one of these orbits for every member of the orbit.  Run together, the two halves
-    // meet in L2 instead of reaching HBM twice.
+    // CTA order: the orbits of the 4^4 blocks that make up one orbit of 16^4 blocks (at most
+    // 256 of them) run one after another.  The state copy and the stage input are planar
+    // FP32 in natural order, so a 4^4 block covers 16 bytes of each 64-byte DRAM access
+    // along the last index; the other 48 bytes lie in the neighbouring 4^4 blocks of the
+    // same 16^4 block, which belong to these orbits for every member of the orbit.  Run
+    // together (well within the CTAs resident at one time), they meet in L2 instead of
+    // reaching HBM once each.
     auto orbit_key = [](int a, int b, int c, int d, long long K) {
       const int m[4][4] = {{a, b, c, d}, {b, a, d, c}, {c, d, a, b}, {d, c, b, a}};
       long long best = -1;
@@ -1164,9 +1165,10 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
       }
       return best;
     };
-    const long long K8 = (nB + 1) / 2;
+    const long long K16 = (nB + 3) / 4;
     std::stable_sort(blk.begin(), blk.end(), [&](const int4 &x, const int4 &y) {
-      return orbit_key(x.x >> 1, x.y >> 1, x.z >> 1, x.w >> 1, K8) < orbit_key(y.x >> 1, y.y >> 1, y.z >> 1, y.w >> 1, K8);
+      return orbit_key(x.x >> 2, x.y >> 2, x.z >> 2, x.w >> 2, K16) <
+             orbit_key(y.x >> 2, y.y >> 2, y.z >> 2, y.w >> 2, K16);
     });
     t->nblocks = (int)blk.size();
     if ((rc = talloc(t, &t->blocks, blk.size()))) return bail(rc);
