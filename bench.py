@@ -704,9 +704,9 @@ def run_reference(args):
     }
 
 
-def accuracy_run(names, every, out_path):
+def accuracy_run(names, every, out_path, max_steps=0):
     """North-star accuracy over whole runs: each named workload propagated for its full
-    length in the BF16-slice tensor-core form and in the FP64 GPU form from the same
+    length (or its first max_steps steps) in the BF16-slice tensor-core form and in the FP64 GPU form from the same
     initial state, recorded every `every` steps: max|dG1| and max|dG2| between the two,
     each form's energy drift |E(t) - E(0) - W(t)| / |E(0)| (W the drive work), and the
     relative energy difference between the forms.  One JSON line per record, appended to
@@ -720,6 +720,8 @@ def accuracy_run(names, every, out_path):
     for name in names:
         d = inputs.workload(name)
         dt, nsteps = d["dt"], d["nsteps"]
+        if max_steps > 0:
+            nsteps = min(nsteps, max_steps)
         forms = {"bf16x4": from_workload(d, precision="bf16x4"), "fp64": from_workload(d, precision="fp64")}
         o0 = {k: p.observables() for k, p in forms.items()}
         secs = {k: 0.0 for k in forms}
@@ -787,6 +789,8 @@ def main():
                     help="comma-separated workloads: propagate each for its full length in the BF16-slice and "
                          "FP64 forms side by side, record the differences and energy drifts, and exit")
     ap.add_argument("--accuracy-every", type=int, default=50, help="record interval of --accuracy-run")
+    ap.add_argument("--accuracy-steps", type=int, default=0,
+                    help="--accuracy-run: stop after this many steps (0: the workload's full length)")
     ap.add_argument("--accuracy-out", default="gpurun_out/accuracy.jsonl", help="JSON-lines file of --accuracy-run")
     ap.add_argument("--oracle-rhs-times", default="", help=argparse.SUPPRESS)
     ap.add_argument("--adjoint-run", action="store_true",
@@ -814,7 +818,8 @@ def main():
     if args.accuracy_run:
         if rank == 0:
             os.makedirs(os.path.dirname(os.path.abspath(args.accuracy_out)), exist_ok=True)
-            summary = accuracy_run(args.accuracy_run.split(","), args.accuracy_every, args.accuracy_out)
+            summary = accuracy_run(args.accuracy_run.split(","), args.accuracy_every, args.accuracy_out,
+                                   args.accuracy_steps)
             print(json.dumps({"accuracy_run": summary}), flush=True)
         return
     if args.hubbard_scaling:

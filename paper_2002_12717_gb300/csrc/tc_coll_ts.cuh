@@ -11,8 +11,8 @@
 //
 //  * the operands stream from HBM once (both are nb^4 tensors) and the kernel is
 //    bound by keeping enough of them in flight: w's slices arrive in a ring of
-//    their own, three stages deep, filled by a producer warp ahead of the MMAs,
-//    and G's FP32 tiles in a ring of up to six slots (in tc_gemm_kernel the B
+//    their own (three to eight stages, as shared memory allows), filled by a
+//    producer warp ahead of the MMAs, and G's FP32 tiles in a ring of four slots (in tc_gemm_kernel the B
 //    load of a K block started only when an MMA stage came free, and the pass
 //    ran at a fifth of the HBM rate);
 //  * the converters write the A slices into tensor memory, the MMAs read A from
@@ -32,21 +32,24 @@
 namespace g1g2 {
 namespace tc {
 
-constexpr int kCtBStages = 3;
 constexpr uint32_t kCtD1Off = 96;
+constexpr int kCtFStages = 4;   // FP32 A slots
 __host__ __device__ constexpr uint32_t ct_dcol(int b) { return 192u * (uint32_t)b; }
 
 __host__ __device__ constexpr uint32_t ct_bstage_bytes(int nout) { return (uint32_t)kSlices * nout * kBlockK * 2; }
 // bytes of the (sum, error) pairs: nb rows of n_valid + 1 (odd row stride: no bank conflicts)
 __host__ __device__ constexpr size_t ct_acc_bytes(int nb, int n_valid) { return (size_t)nb * (n_valid + 1) * 8; }
-__host__ __device__ constexpr int ct_fstages(int nout, size_t acc_bytes) {
-  return (int)((224u * 1024u - kCtBStages * ct_bstage_bytes(nout) - acc_bytes) / kABytes) > 6
-             ? 6
-             : (int)((224u * 1024u - kCtBStages * ct_bstage_bytes(nout) - acc_bytes) / kABytes);
+// B stages: what shared memory holds beside four FP32 slots and the pairs, at most eight
+// (a K block's MMAs take 640 cycles at N = 64, so the B ring must cover the HBM latency
+// with several blocks)
+__host__ __device__ constexpr int ct_bstages(int nout, size_t acc_bytes) {
+  return (int)((224u * 1024u - kCtFStages * kABytes - acc_bytes) / ct_bstage_bytes(nout)) > 8
+             ? 8
+             : (int)((224u * 1024u - kCtFStages * kABytes - acc_bytes) / ct_bstage_bytes(nout));
 }
 __host__ __device__ constexpr size_t ct_smem_bytes(int nout, size_t acc_bytes) {
-  return 1024 + (size_t)ct_fstages(nout, acc_bytes) * kABytes + (size_t)kCtBStages * ct_bstage_bytes(nout) +
-         acc_bytes + 256;
+  return 1024 + (size_t)kCtFStages * kABytes + (size_t)ct_bstages(nout, acc_bytes) * ct_bstage_bytes(nout) +
+         acc_bytes + 512;   // barriers: up to 8 B stages
 }
 
 __global__ void __launch_bounds__(kTsThreads, 1)
@@ -58,19 +61,20 @@ __global__ void __launch_bounds__(kTsThreads, 1)
   const int nv = p.n_valid;
   const int ld = nv + 1;
   const size_t acc_bytes = ct_acc_bytes(N, nv);
-  const int nf = ct_fstages(p.nout, acc_bytes);
+  const int nf = kCtFStages;
+  const int nbs = ct_bstages(p.nout, acc_bytes);
   const uint32_t b_bytes = (uint32_t)p.nout * kBlockK * 2;     // one slice of a B stage
   const uint32_t bstage = ct_bstage_bytes(p.nout);
   const int C = p.kb_chunks;                                    // K blocks per TMEM accumulation
   uint8_t *fring = smem;
   uint8_t *bring = smem + (size_t)nf * kABytes;
-  float2 *acc2 = reinterpret_cast<float2 *>(bring + (size_t)kCtBStages * bstage);   // (sum, error) pairs
+  float2 *acc2 = reinterpret_cast<float2 *>(bring + (size_t)nbs * bstage);   // (sum, error) pairs
   uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(acc2) + acc_bytes);
   uint64_t *ffull = bars;                     // FP32 A tile landed in slot
   uint64_t *fempty = ffull + nf;              // slot read by the converters
   uint64_t *bfull = fempty + nf;              // B slices landed in stage
-  uint64_t *bempty = bfull + kCtBStages;      // stage read by the MMAs
-  uint64_t *aready = bempty + kCtBStages;     // A slices stored in TMEM buffer
+  uint64_t *bempty = bfull + nbs;      // stage read by the MMAs
+  uint64_t *aready = bempty + nbs;     // A slices stored in TMEM buffer
   uint64_t *afree = aready + 2;               // TMEM buffer read by the MMAs
   uint64_t *tfull = afree + 2;                // accumulator pair holds a finished chunk (two)
   uint64_t *tempty = tfull + 2;               // accumulator pair drained (two)
@@ -83,7 +87,7 @@ __global__ void __launch_bounds__(kTsThreads, 1)
       mbar_init(&ffull[f], 1);
       mbar_init(&fempty[f], kTsConvThreads);
     }
-    for (int b = 0; b < kCtBStages; ++b) {
+    for (int b = 0; b < nbs; ++b) {
       mbar_init(&bfull[b], 1);
       mbar_init(&bempty[b], 1);
     }
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(kTsThreads, 1)
           b_coords(p, tile, kb, bk, brow);
           mbar_arrive_expect_tx(&bfull[s], kSlices * b_bytes);
           tma_load_3d(bring + (size_t)s * bstage, &tmB, &bfull[s], bk, brow, 0);   // all four slices
-          if (++s == kCtBStages) { s = 0; ph ^= 1u; }
+          if (++s == nbs) { s = 0; ph ^= 1u; }
         }
       }
     }
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(kTsThreads, 1)
           }
           mma_commit(&bempty[s]);   // the B stage and the A buffer are free once these MMAs have read them
           mma_commit(&afree[a]);
-          if (++s == kCtBStages) { s = 0; ph ^= 1u; }
+          if (++s == nbs) { s = 0; ph ^= 1u; }
           if (++a == 2) { a = 0; aph ^= 1u; }
           if (kc == C - 1 || kb == nkb - 1) {
             mma_commit(&tfull[chunk & 1]);
