@@ -620,41 +620,53 @@ __global__ void obs_one_body_kernel(int nb, const cplx *h, const cplx *D, double
   if (threadIdx.x < 4) red[threadIdx.x] = s[threadIdx.x][0];
 }
 
-// per-block partial sums of Re W[(ij),(kl)] G[(kl),(ij)] and of the non-finite count
-__global__ void obs_two_body_kernel(int nb, const cplx *__restrict__ W, const cplx *__restrict__ G,
-                                    double *partials) {
+// per-block partial sums of Re W[(ij),(kl)] G[(kl),(ij)] and of the non-finite count: each
+// CTA walks the 32 x 32 tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... of the (ij),(kl)
+// matrix view (G's tile read transposed through shared memory) and reduces once at the end
+__global__ void __launch_bounds__(PT * 8) obs_two_body_kernel(int nb, const cplx *__restrict__ W,
+                                                              const cplx *__restrict__ G, double *partials) {
   __shared__ cplx tile[PT][PT + 1];
-  __shared__ double s0[PT * 8], s1[PT * 8];
+  __shared__ double s0[8], s1[8];
   const long long M = (long long)nb * nb;
-  const long long r0 = (long long)blockIdx.y * PT, c0 = (long long)blockIdx.x * PT;
-  const int tid = threadIdx.y * PT + threadIdx.x;
-  for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
-    const long long rr = c0 + yy, cc = r0 + threadIdx.x;
-    if (rr < M && cc < M) tile[yy][threadIdx.x] = G[rr * M + cc];
-  }
-  __syncthreads();
+  const long long nt = (M + PT - 1) / PT;
   double acc = 0.0, bad = 0.0;
-  for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
-    const long long r = r0 + yy, c = c0 + threadIdx.x;
-    if (r < M && c < M) {
-      const cplx w = W[r * M + c];
-      const cplx g = tile[threadIdx.x][yy];   // G[(c),(r)]
-      acc += w.x * g.x - w.y * g.y;
-      // every element of G lands in exactly one transposed tile: count the non-finite ones there
-      if (!isfinite(g.x) || !isfinite(g.y)) bad += 1.0;
+  for (long long t = blockIdx.x; t < nt * nt; t += gridDim.x) {
+    const long long r0 = (t / nt) * PT, c0 = (t % nt) * PT;
+    __syncthreads();   // the previous tile has been read
+    for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
+      const long long rr = c0 + yy, cc = r0 + threadIdx.x;
+      if (rr < M && cc < M) tile[yy][threadIdx.x] = G[rr * M + cc];
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < PT; yy += blockDim.y) {
+      const long long r = r0 + yy, c = c0 + threadIdx.x;
+      if (r < M && c < M) {
+        const cplx w = W[r * M + c];
+        const cplx g = tile[threadIdx.x][yy];   // G[(c),(r)]
+        acc += w.x * g.x - w.y * g.y;
+        // every element of G lands in exactly one transposed tile: count the non-finite ones there
+        if (!isfinite(g.x) || !isfinite(g.y)) bad += 1.0;
+      }
     }
   }
-  s0[tid] = acc;
-  s1[tid] = bad;
-  __syncthreads();
-  for (int o = (PT * 8) / 2; o > 0; o >>= 1) {
-    if (tid < o) { s0[tid] += s0[tid + o]; s1[tid] += s1[tid + o]; }
-    __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
   }
-  if (tid == 0) {
-    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-    partials[2 * b] = s0[0];
-    partials[2 * b + 1] = s1[0];
+  if (threadIdx.x == 0) {
+    s0[threadIdx.y] = acc;
+    s1[threadIdx.y] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      a += s0[w];
+      b += s1[w];
+    }
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
   }
 }
 
@@ -841,12 +853,14 @@ void obs_one_body(Launcher &L, int nb, const cplx *h, const cplx *D, double f, c
 
 void obs_two_body(Launcher &L, int nb, const cplx *W, const cplx *G, double *partials, double *red) {
   const long long M = (long long)nb * nb;
-  const unsigned t = (unsigned)((M + PT - 1) / PT);
+  const long long t = (M + PT - 1) / PT;
+  // eight CTAs of 256 threads per SM, each over several tiles (partials holds t^2 pairs)
+  const unsigned blocks = (unsigned)std::min<long long>(t * t, 152 * 8);
   L.before("obs_two_body");
-  obs_two_body_kernel<<<dim3(t, t), dim3(PT, 8), 0, L.stream>>>(nb, W, G, partials);
+  obs_two_body_kernel<<<blocks, dim3(PT, 8), 0, L.stream>>>(nb, W, G, partials);
   L.after_launch();
   L.before("obs_sum");
-  sum_pairs_kernel<<<1, 256, 0, L.stream>>>(partials, (long long)t * t, red);
+  sum_pairs_kernel<<<1, 256, 0, L.stream>>>(partials, (long long)blocks, red);
   L.after_launch();
 }
 
