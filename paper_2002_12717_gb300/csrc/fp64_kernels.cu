@@ -683,21 +683,26 @@ __global__ void sum_pairs_kernel(const double *partials, long long nblk, double 
   if (threadIdx.x == 0) { red[0] = s0[0]; red[1] = s1[0]; }
 }
 
-__global__ void accumulate_work_kernel(int nb, const cplx *D, const cplx *n, double coeff, double *W) {
-  __shared__ double s[256];
+// W += coeff Re sum_ij D_ij n_ji: one CTA of 1024 threads, reduced over the warps in a
+// fixed order (deterministic, no atomics)
+__global__ void __launch_bounds__(1024) accumulate_work_kernel(int nb, const cplx *D, const cplx *n, double coeff,
+                                                               double *W) {
+  __shared__ double s[32];
   double a = 0;
   for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
     const int i = idx / nb, j = idx % nb;
     const cplx nji = n[j * nb + i];
     a += D[idx].x * nji.x - D[idx].y * nji.y;
   }
-  s[threadIdx.x] = a;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = a;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    *W += coeff * t;
   }
-  if (threadIdx.x == 0) *W += coeff * s[0];
 }
 
 __global__ void double_occ_kernel(int nb, const cplx *n, const cplx *G, double eta, double *out) {
@@ -866,7 +871,7 @@ void obs_two_body(Launcher &L, int nb, const cplx *W, const cplx *G, double *par
 
 void accumulate_work(Launcher &L, int nb, const cplx *D, const cplx *n, double coeff, double *W_acc) {
   L.before("drive_work");
-  accumulate_work_kernel<<<1, 256, 0, L.stream>>>(nb, D, n, coeff, W_acc);
+  accumulate_work_kernel<<<1, 1024, 0, L.stream>>>(nb, D, n, coeff, W_acc);
   L.after_launch();
 }
 

@@ -89,8 +89,6 @@ struct GemmParams {
   double *out64;      //            FP64 partial sums [split][plane][row][col]
   float *out;
   long long out_plane;
-  int kb_first;       // AR_LINEAR with two A tensors: K blocks [0, kb_first) read tmA,
-                      // [kb_first, kb_total) read tmA2 (same rows); 0 = one A tensor
   int n_tiles;        // output column tiles of width nout (B rows n_tile*nout ...); 1 for most passes
   int pi_mk, pi_kq;   // AR_PI: number of k-blocks (32) per i-block; q-blocks (32) per p
   int pi_mtiles;      // AR_PI: row tiles; tile = n_tile * pi_mtiles + m_tile (column-tile outer,
@@ -124,7 +122,7 @@ __device__ __forceinline__ int tile_kblocks(const GemmParams &p, int tile) {
     return n < p.kb_per_split ? (n > 0 ? n : 0) : p.kb_per_split;
   }
   if (p.a_rows == AR_PI) return 2 * p.nb * p.pi_kq;
-  return p.kb_per_plane * p.a_planes * (p.kb_first ? 2 : 1);
+  return p.kb_per_plane * p.a_planes;
 }
 
 // Epilogue of one tile of a pass that is not split-K: TMEM lane r (the tile row) of the
@@ -381,7 +379,7 @@ __device__ __forceinline__ void epi_store_tile_t(const GemmParams &p, int tile, 
 // FP32 tile of the matching slot into the stage's A slices and release the slot.
 template <bool kSliced>
 __global__ void __launch_bounds__(kGemmThreads, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                    const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
                    const GemmParams p, const int stages, const int fstages) {
   extern __shared__ uint8_t smem_raw[];
@@ -457,10 +455,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             mbar_arrive_expect_tx(bar, kABytes + 2 * b_bytes);
           }
           if (p.a_rows == AR_LINEAR) {
-            const bool second = p.kb_first && kb >= p.kb_first;
-            const int kl = second ? kb - p.kb_first : kb;
-            const int u = kl / p.kb_per_plane, pb = kl % p.kb_per_plane;
-            tma_load_3d(dst, second ? &tmA2 : &tmA, bar, pb * kBlockK, tile * kTileM, u);
+            const int u = kb / p.kb_per_plane, pb = kb % p.kb_per_plane;
+            tma_load_3d(dst, &tmA, bar, pb * kBlockK, tile * kTileM, u);
           } else if (p.a_rows == AR_GATHER4) {
             const int u = kb / p.kb_per_plane, pb = kb % p.kb_per_plane;
             const int bB = tile % p.g_nb, aB = (tile / p.g_nb) % p.g_na, c = tile / (p.g_nb * p.g_na);

@@ -60,8 +60,8 @@ __host__ __device__ constexpr size_t ts_smem_bytes(int nout) {
 }
 
 __global__ void __launch_bounds__(kTsThreads, 1)
-    tc_gemm_ts_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
-                      const __grid_constant__ CUtensorMap tmB, const GemmParams p) {
+    tc_gemm_ts_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const GemmParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int nf = ts_fstages(p.nout);
@@ -119,10 +119,8 @@ __global__ void __launch_bounds__(kTsThreads, 1)
           uint8_t *dst = fring + (size_t)f * kABytes;
           mbar_arrive_expect_tx(&ffull[f], kABytes);
           if (p.a_rows == AR_LINEAR) {
-            const bool second = p.kb_first && kb >= p.kb_first;
-            const int kl = second ? kb - p.kb_first : kb;
-            const int u = kl / p.kb_per_plane, pb = kl % p.kb_per_plane;
-            tma_load_3d(dst, second ? &tmA2 : &tmA, &ffull[f], pb * kBlockK, tile * kTileM, u);
+            const int u = kb / p.kb_per_plane, pb = kb % p.kb_per_plane;
+            tma_load_3d(dst, &tmA, &ffull[f], pb * kBlockK, tile * kTileM, u);
           } else {  // AR_GATHER4
             const int u = kb / p.kb_per_plane, pb = kb % p.kb_per_plane;
             const int bB = tile % p.g_nb, aB = (tile / p.g_nb) % p.g_na, c = tile / (p.g_nb * p.g_na);

@@ -191,11 +191,14 @@ __global__ void __launch_bounds__(256) slice_b_kernel(int nb, int nout, int kpad
   __shared__ double smu;
   const int kt = complex_a ? 2 * kpad : kpad;
   const int total = nout * kt;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // mu = Re Tr S / nb over warp 0 (lane-strided, fixed-order shuffle reduction)
     double mu = 0.0;
     if (shift)
-      for (int i = 0; i < nb; ++i) mu += S[i * nb + i].x;
-    smu = mu / nb;
+      for (int i = threadIdx.x; i < nb; i += 32) mu += S[i * nb + i].x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mu += __shfl_xor_sync(0xffffffffu, mu, o);
+    if (threadIdx.x == 0) smu = mu / nb;
   }
   __syncthreads();
   const double mu = smu;
@@ -991,7 +994,7 @@ bool use_collision_ts(const GemmParams &g) { return g.a_rows == AR_SPLITK && g.k
 
 // sliced: the BF16-slice form (Bh = slices of B, Bl unused); otherwise TF32 hi/lo
 void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, const CUtensorMap &Bh,
-                 const CUtensorMap &Bl, GemmParams gp, bool sliced = false, const CUtensorMap *A2 = nullptr) {
+                 const CUtensorMap &Bl, GemmParams gp, bool sliced = false) {
   gp.err = t->err;
   int stages = 0, fstages = 0;
   // the region after the barriers: split-K partial pairs, or the staging of the transposed epilogue
@@ -1001,14 +1004,14 @@ void launch_gemm(TcPath *t, Launcher &L, const char *tag, const CUtensorMap &A, 
   const int grid = std::max(1, std::min(gp.tiles, t->sms));
   L.before(tag);
   if (sliced && use_ts_gemm(gp)) {
-    tc_gemm_ts_kernel<<<grid, kTsThreads, ts_smem_bytes(gp.nout), L.stream>>>(A, A2 ? *A2 : A, Bh, gp);
+    tc_gemm_ts_kernel<<<grid, kTsThreads, ts_smem_bytes(gp.nout), L.stream>>>(A, Bh, gp);
   } else if (sliced && use_collision_ts(gp)) {
     tc_collision_ts_kernel<<<grid, kTsThreads, ct_smem_bytes(gp.nout, ct_acc_bytes(gp.nb, gp.n_valid)), L.stream>>>(
         A, Bh, gp);
   } else if (sliced) {
-    tc_gemm_kernel<true><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages, fstages);
+    tc_gemm_kernel<true><<<grid, kGemmThreads, smem, L.stream>>>(A, Bh, Bl, gp, stages, fstages);
   } else {
-    tc_gemm_kernel<false><<<grid, kGemmThreads, smem, L.stream>>>(A, A2 ? *A2 : A, Bh, Bl, gp, stages, fstages);
+    tc_gemm_kernel<false><<<grid, kGemmThreads, smem, L.stream>>>(A, Bh, Bl, gp, stages, fstages);
   }
   L.after_launch();
 }
