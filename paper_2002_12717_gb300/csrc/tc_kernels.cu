@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(256) realify_pi_slice3_kernel(int nb, const fl
                                                                 __nv_bfloat16 *out, long long slice_stride) {
   __shared__ float2 t1[32][33];
   __shared__ float red[8];
+  extern __shared__ float4 hs_raw[];   // nb * nb float2 (dynamic)
   const long long N = nb, K = 2 * N * N;
   const long long jl = blockIdx.x;
   const long long j = jl / N, l = jl % N;
@@ -336,6 +337,9 @@ __global__ void __launch_bounds__(256) realify_pi_slice3_kernel(int nb, const fl
     const float2 a = t1[tx][ty];
     return make_float2(a.x - Y2s[g], a.y - Y2s[P + g]);
   };
+  // first sweep: hcorr of this (j, l) into shared memory (Hs[p nb + q]) and its largest
+  // magnitude; the slicing sweep then reads shared memory only, so Y1 and Y2 stream once
+  float2 *Hs = reinterpret_cast<float2 *>(hs_raw);
   float mx = 0.f;
   for (int tile = 0; tile < nt * nt; ++tile) {
     const int p0 = (tile / nt) * 32, q0 = (tile % nt) * 32;
@@ -346,6 +350,7 @@ __global__ void __launch_bounds__(256) realify_pi_slice3_kernel(int nb, const fl
       const int pp = p0 + ty, q = q0 + tx;
       if (pp < nb && q < nb) {
         const float2 h = hval(pp, q, ty);
+        Hs[pp * nb + q] = h;
         mx = fmaxf(mx, fmaxf(fabsf(h.x), fabsf(h.y)));
       }
     }
@@ -353,39 +358,30 @@ __global__ void __launch_bounds__(256) realify_pi_slice3_kernel(int nb, const fl
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (tx == 0) red[ty0] = mx;
-  __syncthreads();
+  __syncthreads();   // also orders the Hs writes before the reads below
   mx = red[0];
   for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
   float cut[3];
   cuts3_lead8(slice_exponent(__float_as_int(mx)), cut);
-  // slicing sweep: each thread cuts two adjacent q of one p and stores BF16 pairs
-  const int qp = tx & 15, psub = tx >> 4;
-  for (int tile = 0; tile < nt * nt; ++tile) {
-    const int p0 = (tile / nt) * 32, q0 = (tile % nt) * 32;
-    __syncthreads();
-    load_tile(p0, q0);
-    __syncthreads();
-    for (int pr = 2 * ty0 + psub; pr < 32; pr += 16) {
-      const int pp = p0 + pr, q = q0 + 2 * qp;
-      if (pp >= nb || q >= nb) continue;   // nb % 4 == 0: q + 1 < nb as well
-      const long long g = ((pp * N + l) * N + j) * N + q;     // Y2_{p l q j}, Y2_{p l q+1 j}
-      const float2 y2r = *reinterpret_cast<const float2 *>(Y2s + g), y2i = *reinterpret_cast<const float2 *>(Y2s + P + g);
-      const float2 a0 = t1[2 * qp][pr], a1 = t1[2 * qp + 1][pr];
-      const float2 h0 = make_float2(a0.x - y2r.x, a0.y - y2i.x), h1 = make_float2(a1.x - y2r.y, a1.y - y2i.y);
-      for (int u = 0; u < 2; ++u)
-        for (int v = 0; v < 2; ++v) {
-          const float x0 = (u == 0) ? (v ? h0.y : h0.x) : (v ? h0.x : -h0.y);
-          const float x1 = (u == 0) ? (v ? h1.y : h1.x) : (v ? h1.x : -h1.y);
-          const long long row = 2 * jl + v;
-          const long long col = ((long long)u * N + pp) * N + q;
-          float s0[3], s1[3];
-          slice3(x0, cut, s0);
-          slice3(x1, cut, s1);
+  // slicing sweep: thread e cuts the pair q = 2 e mod nb, q + 1 of row p = 2 e / nb (nb is
+  // even), so a warp stores 128 contiguous bytes per slice and output row
+  for (int e = threadIdx.x; e < nb * nb / 2; e += blockDim.x) {
+    const int pp = (2 * e) / nb, q = 2 * e - pp * nb;
+    const float4 hv = reinterpret_cast<const float4 *>(Hs)[e];
+    const float2 h0 = make_float2(hv.x, hv.y), h1 = make_float2(hv.z, hv.w);
+    for (int u = 0; u < 2; ++u)
+      for (int v = 0; v < 2; ++v) {
+        const float x0 = (u == 0) ? (v ? h0.y : h0.x) : (v ? h0.x : -h0.y);
+        const float x1 = (u == 0) ? (v ? h1.y : h1.x) : (v ? h1.x : -h1.y);
+        const long long row = 2 * jl + v;
+        const long long col = ((long long)u * N + pp) * N + q;
+        float s0[3], s1[3];
+        slice3(x0, cut, s0);
+        slice3(x1, cut, s1);
 #pragma unroll
-          for (int z = 0; z < 3; ++z)
-            *reinterpret_cast<__nv_bfloat162 *>(out + z * slice_stride + row * K + col) = __floats2bfloat162_rn(s0[z], s1[z]);
-        }
-    }
+        for (int z = 0; z < 3; ++z)
+          *reinterpret_cast<__nv_bfloat162 *>(out + z * slice_stride + row * K + col) = __floats2bfloat162_rn(s0[z], s1[z]);
+      }
   }
 }
 
@@ -1315,6 +1311,7 @@ int tc_create(TcPath **out, int nb, int se, bool restricted, bool sliced, bool b
       !raise_limit((const void *)orbit_assemble_kernel<kAsmStage>, 4 * BEL * sizeof(float2)) ||
       !raise_limit((const void *)orbit_assemble_kernel<kAsmLast>, 4 * BEL * sizeof(float2)) ||
       (big && sliced && !raise_limit((const void *)tc_pi_gemm_kernel, kPiSmemBytes)) ||
+      (has_pi && sliced && !raise_limit((const void *)realify_pi_slice3_kernel, (size_t)nb * nb * sizeof(float2))) ||
       (sliced && t->nout2 > 128 && !raise_limit((const void *)tc_gemm_ts_kernel, ts_smem_bytes(t->nout2))) ||
       (sliced && t->nout1 <= 96 &&
        !raise_limit((const void *)tc_collision_ts_kernel, ct_smem_bytes(t->nout1, ct_acc_bytes(nb, nb))))) {
@@ -1559,8 +1556,8 @@ void tc_rhs(TcPath *t, Launcher &L, const cplx *n_in, const cplx *G_in, const cp
     if (sl) {
       // B = R(hcorr) as three BF16 slices with per-column exponents, then the product
       L.before("tc_pi_b_slices");
-      realify_pi_slice3_kernel<<<(unsigned)(N * N), 256, 0, L.stream>>>(nb, t->Y1, t->Y2, t->N4, t->pb_s,
-                                                                         4 * N * N * N * N);
+      realify_pi_slice3_kernel<<<(unsigned)(N * N), 256, N * N * sizeof(float2), L.stream>>>(
+          nb, t->Y1, t->Y2, t->N4, t->pb_s, 4 * N * N * N * N);
       L.after_launch();
       // a6: Pi_(ik),(jl) = sum_(pq) G_ipkq hcorr_qjpl, rows (i, k) of G_ipkq
       sliced_product(t, L, from_y ? t->y32 : t->ys32, AOperand{N * N * N, N, N * N, 1}, t->Pi, "tc_gemm_pi",
