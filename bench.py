@@ -705,7 +705,7 @@ def run_reference(args):
 
 
 def accuracy_run(names, every, out_path, max_steps=0):
-    """North-star accuracy over whole runs: each named workload propagated for its full
+    """Accuracy over whole runs: each named workload propagated for its full
     length (or its first max_steps steps) in the BF16-slice tensor-core form and in the FP64 GPU form from the same
     initial state, recorded every `every` steps: max|dG1| and max|dG2| between the two,
     each form's energy drift |E(t) - E(0) - W(t)| / |E(0)| (W the drive work), and the
@@ -791,7 +791,7 @@ def main():
     ap.add_argument("--accuracy-every", type=int, default=50, help="record interval of --accuracy-run")
     ap.add_argument("--accuracy-steps", type=int, default=0,
                     help="--accuracy-run: stop after this many steps (0: the workload's full length)")
-    ap.add_argument("--accuracy-out", default="gpurun_out/accuracy.jsonl", help="JSON-lines file of --accuracy-run")
+    ap.add_argument("--accuracy-out", default="accuracy.jsonl", help="JSON-lines file of --accuracy-run")
     ap.add_argument("--oracle-rhs-times", default="", help=argparse.SUPPRESS)
     ap.add_argument("--adjoint-run", action="store_true",
                     help="the discrete adjoint over the whole 4x4 Hubbard workload with finite-difference checks, "

@@ -264,7 +264,7 @@ __host__ __device__ __forceinline__ bool epi_transposed(const GemmParams &p) {
 // the row maps AR_LINEAR, AR_GATHER4 and the stores EP_SWAP34, EP_EXCH_T, EP_GATHER_TCONJ
 // (planar, col_il, or out_il complex, optionally 4^4-blocked) -- every nb^5 pass but the
 // collision integral.  Planar outputs: each 32-column chunk read from TMEM goes through
-// the warp's staging tile in two rounds of 16 columns, so that a lane stores four
+// the warp's staging tile in two halves of 16 columns, so that a lane stores four
 // consecutive rows of one column as one 16-byte vector: with nb % 4 == 0 and row tiles
 // starting at multiples of 4, four consecutive rows of a warp are four consecutive output
 // elements under every one of these maps (and 16-byte aligned); one store per four rows
@@ -339,8 +339,8 @@ __device__ __forceinline__ void epi_store_tile_t(const GemmParams &p, int tile, 
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int g0 = c0 + kStgCols * h;                       // output column of the round's first
-      const int nv = min(kStgCols, p.n_valid - g0);           // columns of this round that are stored
+      const int g0 = c0 + kStgCols * h;                       // output column of the half-chunk's first
+      const int nv = min(kStgCols, p.n_valid - g0);           // columns of this half-chunk that are stored
 #pragma unroll
       for (int j = 0; j < kStgCols; ++j) stg[j * kStgPitch + lane] = v[kStgCols * h + j];
       __syncwarp();
@@ -363,7 +363,7 @@ __device__ __forceinline__ void epi_store_tile_t(const GemmParams &p, int tile, 
           mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
         }
       }
-      __syncwarp();   // the staging tile is read before the next round overwrites it
+      __syncwarp();   // the staging tile is read before the next half-chunk overwrites it
     }
   }
 }

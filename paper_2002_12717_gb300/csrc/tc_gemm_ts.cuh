@@ -11,10 +11,12 @@
 //    the tensor core near its nominal rate while it runs N = 192 MMAs, and at
 //    about 60% of that rate on the same work as N = 96 MMAs, so the two
 //    accumulators (2 x 192 columns) stay single-buffered and the epilogue is
-//    made short instead: each 16-column round goes from TMEM through a staging
-//    tile in shared memory, and every lane stores four consecutive rows of a
-//    column as one 16-byte vector (one store per row and column took 3-7 us a
-//    tile, as long as the MMAs);
+//    made short instead (epi_store_tile_t): planar outputs go from TMEM
+//    through a staging tile in shared memory, 16 columns at a time, and every
+//    lane stores four consecutive rows of a column as one 16-byte vector;
+//    interleaved complex outputs are stored per row without a branch per
+//    element (one 4-byte store per row and column took 3-7 us a tile, as long
+//    as the MMAs);
 //  * B arrives in a ring of its own, three stages deep, filled by a producer
 //    warp of its own;
 //  * the FP32 A tiles land in a ring of their own slots.
