@@ -9,7 +9,8 @@ right-hand side; this module is the specification of the exchange steps that a
 multi-GPU run needs and is exercised on CPU ranks (gloo) against the oracle.
 
 Where each term of the right-hand side (Eqs. eom_gone-2, result_eom_soa,
-g2-eq-gw-pi) needs data of other ranks, and the collective that supplies it:
+g2-eq-gw-pi, g2-eq-tpp-lambda, g2-eq-tph-lambda, g2-dsl-equation-pi-lambda) needs
+data of other ranks, and the collective that supplies it:
 
   h^HF (Eq. h_HF)       rows i in I_r from w[I_r]; all-reduce of the nb x nb matrix
   I (Eq. eom_gone-I)    partial sum over l in I_r with w_iklp = conj(w_lpik) taken
@@ -20,13 +21,22 @@ g2-eq-gw-pi) needs data of other ranks, and the collective that supplies it:
                         needs all p: one all-to-all (B re-sharded on index 2), after
                         which A's slab follows from its exchange symmetry
   A^dag                 conj(A_klij): one all-to-all (A re-sharded on index 3)
-  GW hcorr (Eq. gwhcorr) w x_4 n - n x_2 w on w[I_r] (local); the polarisation
-                        Pi_ijkl = sum_pq G2_ipkq hcorr_qjpl needs all of hcorr:
-                        all-gather (the one-dimensional form of the block GEMM)
+  GW hcorr (Eq. gwhcorr) w x_4 n - n x_2 w on w[I_r] (local)
+  Pi (Eq. gwpi)         Pi_ijkl = sum_pq G2_ipkq hcorr_qjpl, rows i in I_r: SUMMA
+                        over the 1-D row blocks, P broadcasts of one rank's hcorr
+                        slab (the K panel q in I_s) each; no rank holds all of hcorr
   conj(Pi_lkji)         one all-to-all (Pi re-sharded on index 4)
+  TPP hcorr (HTPPcorr)  Y = G x_2 w on w[I_r] (local); the sum over p: one all-to-all
+                        (Y re-sharded on index 2), the i-slab by hcorr's exchange symmetry
+  TPH hcorr (HTPHcorr)  Z = w x_4 G on w[I_r] (local); the sum over p: one all-to-all,
+                        and one more back to i-slabs
+  Lambda (lambdapp/ph)  rows i in I_r: SUMMA with G2's slabs as the K panels (p resp.
+                        q in I_s), P broadcasts
+  conj(Lambda_klij)     one all-to-all (Lambda re-sharded on index 3)
   E_corr                local partial sum, scalar all-reduce
 
-Selfenergies: HF, SOA, GW and GW with exchange (fermions, spin-orbital basis).
+Selfenergies: HF, SOA, GW, GW with exchange, the particle-particle and particle-hole T
+matrices and DSL (fermions, spin-orbital basis).
 """
 from __future__ import annotations
 
@@ -78,17 +88,86 @@ def reshard(x, part: Partition, axis: int, group=None):
     return torch.movedim(y, 1, axis)
 
 
-def allgather_slabs(x, part: Partition, group=None):
-    """The full tensor from the first-index slabs of all ranks."""
+def panel_broadcast(part: Partition, own, group=None):
+    """The panels of a SUMMA product: yields (lo, hi, panel) for every rank s in turn, panel being
+    rank s's first-index slab `own` (first index in I_s = [lo, hi)), broadcast from s to every
+    rank.  A rank holds its own slab and one panel at a time (at most ceil(nb/P) leading rows),
+    never the whole tensor."""
     P, b = part.world, part.block
-    xs = _pad0(x, b).contiguous()
-    outs = [torch.empty_like(xs) for _ in range(P)]
-    dist.all_gather(outs, xs, group=group)
-    return torch.cat([outs[s][: part.range(s)[1] - part.range(s)[0]] for s in range(P)], 0)
+    shape = (b,) + tuple(own.shape[1:])
+    for s in range(P):
+        lo, hi = part.range(s)
+        buf = _pad0(own, b).contiguous() if s == part.rank else torch.empty(shape, dtype=own.dtype, device=own.device)
+        src = s if group is None else dist.get_global_rank(group, s)
+        dist.broadcast(buf, src=src, group=group)
+        yield lo, hi, buf[: hi - lo]
 
 
-def _es(*a):
-    return torch.einsum(*a)
+def polarisation_sharded(part: Partition, hc_slab, G_slab, group=None):
+    """Pi_ijkl = sum_pq hcorr_qjpl G_ipkq (Eq. gwpi) for the rows i in I_r: the sum over (p, q)
+    split by q over the ranks, rank s's slab of hcorr (q in I_s) the panel of step s."""
+    Pi = torch.zeros_like(G_slab)
+    for lo, hi, H in panel_broadcast(part, hc_slab, group):
+        if hi > lo:
+            Pi = Pi + _es("qjpl,ipkq->ijkl", H, G_slab[:, :, :, lo:hi])
+    return Pi
+
+
+def tpp_hcorr_sharded(part: Partition, w_slab, gl, gg, group=None):
+    """hcorr_ijkl = (i hbar)^2 sum_pq (G>_ip G>_jq - G<_ip G<_jq) w_pqkl (Eq. HTPPcorr), rows i in
+    I_r: Y_pjkl = sum_q G_jq w_pqkl on w's slab (p in I_r), one re-shard to j-slabs for the sum
+    over p, and the exchange symmetry hcorr_ijkl = hcorr_jilk (inherited from w_ijkl = w_jilk)
+    for the i-slab."""
+    Y = torch.stack([_es("jq,pqkl->pjkl", gg, w_slab), _es("jq,pqkl->pjkl", gl, w_slab)], -1)
+    Yj = reshard(Y, part, 1, group)                       # [p (all)][j in I_r][k][l][>, <]
+    Hj = -(_es("ip,pjkl->ijkl", gg, Yj[..., 0]) - _es("ip,pjkl->ijkl", gl, Yj[..., 1]))
+    return Hj.permute(1, 0, 3, 2)                         # hcorr_jilk, first index in I_r
+
+
+def tph_hcorr_sharded(part: Partition, w_slab, gl, gg, group=None):
+    """hcorr_ijkl = (i hbar)^2 sum_pq (G>_ip G<_ql - G<_ip G>_ql) w_pjkq (Eq. HTPHcorr), rows i in
+    I_r: Z_pjkl = sum_q G_ql w_pjkq on w's slab, a re-shard to j-slabs for the sum over p and one
+    back to i-slabs."""
+    Z = torch.stack([_es("ql,pjkq->pjkl", gl, w_slab), _es("ql,pjkq->pjkl", gg, w_slab)], -1)
+    Zj = reshard(Z, part, 1, group)                       # [p (all)][j in I_r][k][l][<, >]
+    Hj = -(_es("ip,pjkl->ijkl", gg, Zj[..., 0]) - _es("ip,pjkl->ijkl", gl, Zj[..., 1]))
+    Hi = reshard(Hj.transpose(0, 1).contiguous(), part, 1, group)   # [j (all)][i in I_r][k][l]
+    return Hi.transpose(0, 1)
+
+
+def tpp_ladder_sharded(part: Partition, H_slab, G_slab, group=None):
+    """Lambda_ijkl = sum_pq hcorr_ijpq G_pqkl (Eq. lambdapp), rows i in I_r: the sum split by p,
+    rank s's slab of G2 (p in I_s) the panel of step s."""
+    L = torch.zeros_like(G_slab)
+    for lo, hi, Gp in panel_broadcast(part, G_slab, group):
+        if hi > lo:
+            L = L + _es("ijpq,pqkl->ijkl", H_slab[:, :, lo:hi, :], Gp)
+    return L
+
+
+def tph_ladder_sharded(part: Partition, H_slab, G_slab, group=None):
+    """Lambda_ijkl = sum_pq hcorr_ipql G_qjkp (Eq. lambdaph), rows i in I_r: the sum split by q,
+    rank s's slab of G2 (q in I_s) the panel of step s."""
+    L = torch.zeros_like(G_slab)
+    for lo, hi, Gq in panel_broadcast(part, G_slab, group):
+        if hi > lo:
+            L = L + _es("ipql,qjkp->ijkl", H_slab[:, :, lo:hi, :], Gq)
+    return L
+
+
+def _es(eq, *ops):
+    """torch.einsum, with an empty operand (a rank whose slab is empty) giving the zeros the
+    contraction defines (an empty sum, or an empty output axis) directly."""
+    if any(o.numel() == 0 for o in ops):
+        ins, out = eq.split("->")
+        sizes = {}
+        for spec, o in zip(ins.split(","), ops):
+            sizes.update(zip(spec, o.shape))
+        dtype = ops[0].dtype
+        for o in ops[1:]:
+            dtype = torch.promote_types(dtype, o.dtype)
+        return torch.zeros([sizes[c] for c in out], dtype=dtype, device=ops[0].device)
+    return torch.einsum(eq, *ops)
 
 
 def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=None):
@@ -127,13 +206,22 @@ def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=N
     A3 = reshard(A, part, 2, group)                       # A[a][b][c in I_r][d]
     A_dag = A3.permute(2, 3, 0, 1).conj()                 # conj(A_cdab), first index in I_r
     rhs2 = C - A + A_dag
-    if selfenergy in ("GW", "GWX"):
-        # Eq. (gwhcorr): hcorr = w x4 n - n x2 w (w's exchange symmetry), all of it for Pi
+    if selfenergy in ("GW", "GWX", "DSL"):
+        # Eq. (gwhcorr): hcorr = w x4 n - n x2 w (w's exchange symmetry), on w's slab
         hc = _es("ijks,sl->ijkl", w_slab, n) - _es("jq,iqkl->ijkl", n, w_slab)
-        hc_full = allgather_slabs(hc, part, group)
-        Pi = _es("ipkq,qjpl->ijkl", G_slab, hc_full)      # Eq. (gwpi), rows i in I_r
+        Pi = polarisation_sharded(part, hc, G_slab, group)   # Eq. (gwpi), rows i in I_r
         Pi4 = reshard(Pi, part, 3, group)                 # Pi[a][b][c][d in I_r]
         rhs2 = rhs2 + Pi - Pi4.permute(3, 2, 1, 0).conj()
+    if selfenergy in ("TPP", "TPH", "DSL"):
+        # the T-matrix ladder terms (Eqs. lambdapp, lambdaph; DSL takes both, each once)
+        gl, gg = 1j * n, -1j * nbar                       # G^< and G^> at equal times (fermions)
+        lam = torch.zeros_like(G_slab)
+        if selfenergy in ("TPP", "DSL"):
+            lam = lam + tpp_ladder_sharded(part, tpp_hcorr_sharded(part, w_slab, gl, gg, group), G_slab, group)
+        if selfenergy in ("TPH", "DSL"):
+            lam = lam + tph_ladder_sharded(part, tph_hcorr_sharded(part, w_slab, gl, gg, group), G_slab, group)
+        L3 = reshard(lam, part, 2, group)                 # Lambda[a][b][c in I_r][d]
+        rhs2 = rhs2 + lam - L3.permute(2, 3, 0, 1).conj()  # - conj(Lambda_klij)
     return dn, -1j * rhs2
 
 
