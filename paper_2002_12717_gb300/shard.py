@@ -37,6 +37,10 @@ data of other ranks, and the collective that supplies it:
 
 Selfenergies: HF, SOA, GW, GW with exchange, the particle-particle and particle-hole T
 matrices and DSL (fermions, spin-orbital basis).
+
+`summa_matmul` is the 2-D block-distributed form of the nb^2 x nb^2 x nb^2 products on a
+q x q process grid (panels of about N^4 / q elements broadcast along grid rows and
+columns), for a partition that keeps those operands in 2-D blocks.
 """
 from __future__ import annotations
 
@@ -231,3 +235,51 @@ def correlation_energy_sharded(part: Partition, w_slab, G_slab, group=None):
     e = torch.tensor([(w_slab * G_slab.conj()).sum().real.item()], dtype=torch.float64)
     dist.all_reduce(e, group=group)
     return -0.5 * e.item()
+
+
+# ---------------------------------------------------------------------------
+# The 2-D block-distributed form of the nb^2 x nb^2 x nb^2 products (SUMMA)
+# ---------------------------------------------------------------------------
+
+def _block(n, q, x):
+    """[lo, hi) of block x when n indices are cut into q blocks of ceil(n / q)."""
+    b = -(-n // q)
+    lo = min(n, x * b)
+    return lo, min(n, lo + b)
+
+
+class Grid:
+    """q x q process grid over P = q^2 ranks: rank a q + b holds block (a, b) of every matrix.
+    The row and column communicators are created collectively (every rank, the same order)."""
+
+    def __init__(self, world: int, rank: int):
+        q = int(round(world ** 0.5))
+        if q * q != world:
+            raise ValueError("the 2-D grid needs a square number of ranks")
+        self.q, self.a, self.b = q, rank // q, rank % q
+        self.rows = [dist.new_group([a * q + b for b in range(q)]) for a in range(q)]
+        self.cols = [dist.new_group([a * q + b for a in range(q)]) for b in range(q)]
+
+
+def summa_matmul(grid: Grid, A_blk, B_blk, M: int, K: int, N: int):
+    """C = A B for A (M x K), B (K x N) in q x q blocks (rows, columns and K cut into blocks of
+    ceil(n / q)): rank (a, b) holds A[block a, block b] and B[block a, block b] and returns
+    C[block a, block b].  Step c broadcasts A[a, c] along grid row a and B[c, b] along grid
+    column b (panels of about M K / q and K N / q elements), and every rank adds their product."""
+    q, a, b = grid.q, grid.a, grid.b
+    mb, kb, nbk = -(-M // q), -(-K // q), -(-N // q)
+    r0, r1 = _block(M, q, a)
+    c0, c1 = _block(N, q, b)
+    C = torch.zeros((r1 - r0, c1 - c0), dtype=torch.promote_types(A_blk.dtype, B_blk.dtype), device=A_blk.device)
+    for c in range(q):
+        k0, k1 = _block(K, q, c)
+        Abuf = torch.zeros((mb, kb), dtype=A_blk.dtype, device=A_blk.device)
+        if b == c:
+            Abuf[: A_blk.shape[0], : A_blk.shape[1]] = A_blk
+        dist.broadcast(Abuf, src=a * q + c, group=grid.rows[a])
+        Bbuf = torch.zeros((kb, nbk), dtype=B_blk.dtype, device=B_blk.device)
+        if a == c:
+            Bbuf[: B_blk.shape[0], : B_blk.shape[1]] = B_blk
+        dist.broadcast(Bbuf, src=c * q + b, group=grid.cols[b])
+        C = C + Abuf[: r1 - r0, : k1 - k0] @ Bbuf[: k1 - k0, : c1 - c0]
+    return C
