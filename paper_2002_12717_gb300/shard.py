@@ -36,7 +36,7 @@ data of other ranks, and the collective that supplies it:
   E_corr                local partial sum, scalar all-reduce
 
 Selfenergies: HF, SOA, GW, GW with exchange, the particle-particle and particle-hole T
-matrices and DSL (fermions, spin-orbital basis).
+matrices and DSL; fermions and bosons; spin-orbital basis.
 
 `summa_matmul` is the 2-D block-distributed form of the nb^2 x nb^2 x nb^2 products on a
 q x q process grid (panels of about N^4 / q elements broadcast along grid rows and
@@ -174,8 +174,10 @@ def _es(eq, *ops):
     return torch.einsum(eq, *ops)
 
 
-def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=None):
-    """(dn/dt, the slab of dG2/dt) at the state (n, G2) for fermions in a spin-orbital basis.
+def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=None, bosons=False):
+    """(dn/dt, the slab of dG2/dt) at the state (n, G2) in a spin-orbital basis, for fermions or
+    (bosons=True) bosons: eta = -1 or +1 in the +/- of the paper (G^< = -i eta n, G^> = -i nbar
+    with nbar = 1 + eta n, w^+/- = w + eta w_ijlk).
 
     h, n: replicated nb x nb; w_slab = w[I_r], G_slab = G2[I_r] (complex tensors).  dn is
     the same on every rank.  The arithmetic is that of the oracle's right-hand side with
@@ -183,26 +185,27 @@ def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=N
     nb, lo, hi = part.nb, part.lo, part.hi
     cd = n.dtype
     eye = torch.eye(nb, dtype=cd, device=n.device)
-    nbar = eye - n
-    # Eq. (h_HF): hHF_ij = h_ij + sum_kl (w_ikjl - w_iklj) n_lk, rows i in I_r
-    wm = w_slab - w_slab.permute(0, 1, 3, 2)
+    eta = 1.0 if bosons else -1.0
+    nbar = eye + eta * n
+    # Eq. (h_HF): hHF_ij = h_ij + sum_kl (w_ikjl +/- w_iklj) n_lk, rows i in I_r
+    wpm = w_slab + eta * w_slab.permute(0, 1, 3, 2)
     hhf = torch.zeros((nb, nb), dtype=cd, device=n.device)
-    hhf[lo:hi] = _es("ikjl,lk->ij", wm, n)
+    hhf[lo:hi] = _es("ikjl,lk->ij", wpm, n)
     dist.all_reduce(hhf, group=group)
     hhf = hhf + h
     if selfenergy == "HF":
         return -1j * (hhf @ n - n @ hhf), torch.zeros_like(G_slab)
-    # Eq. (eom_gone-I): I_ij = -i sum_klp w_iklp G_lpjk, the part l in I_r; w_iklp = conj(w_lpik)
+    # Eq. (eom_gone-I): I_ij = +/- i sum_klp w_iklp G_lpjk, the part l in I_r; w_iklp = conj(w_lpik)
     w_t = w_slab.conj().permute(2, 3, 0, 1)               # [i][k][l in I_r][p] = w_iklp
-    I = -1j * _es("iklp,lpjk->ij", w_t, G_slab)
+    I = eta * 1j * _es("iklp,lpjk->ij", w_t, G_slab)
     dist.all_reduce(I, group=group)
-    dn = -1j * (hhf @ n - n @ hhf) - (I + I.conj().T)
+    dn = -1j * (hhf @ n - n @ hhf) + eta * (I + I.conj().T)
     # two-particle commutator: [h2, G] = X + exch X, X = G x_2 h - G x_4 h
     X = _es("jp,ipkl->ijkl", hhf, G_slab) - _es("ijkp,pl->ijkl", G_slab, hhf)
     Xj = reshard(X, part, 1, group)                       # X[a][b in I_r][c][d]
     C = X + Xj.permute(1, 0, 3, 2)                        # exch X_abcd = X_badc, a in I_r
     # source term, Eq. (psi-pm-def): A = nbar x1 nbar x2 w~ x3 n x4 n, Psi = -A + A^dag
-    wsrc = w_slab if selfenergy == "GW" else wm           # plain w for standard GW, w^- otherwise
+    wsrc = w_slab if selfenergy == "GW" else wpm          # plain w for standard GW, w^+/- otherwise
     B = _es("jq,pqrs,rk,sl->pjkl", nbar, wsrc, n, n)      # p in I_r
     Bj = reshard(B, part, 1, group)                       # B[p (all)][j in I_r][k][l]
     Aj = _es("ip,pjkl->ijkl", nbar, Bj)                   # A[i (all)][j in I_r][k][l]
@@ -211,14 +214,15 @@ def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=N
     A_dag = A3.permute(2, 3, 0, 1).conj()                 # conj(A_cdab), first index in I_r
     rhs2 = C - A + A_dag
     if selfenergy in ("GW", "GWX", "DSL"):
-        # Eq. (gwhcorr): hcorr = w x4 n - n x2 w (w's exchange symmetry), on w's slab
+        # Eq. (gwhcorr): hcorr = w x4 n - n x2 w (w's exchange symmetry; the eta terms of
+        # nbar cancel, so the same for bosons), on w's slab
         hc = _es("ijks,sl->ijkl", w_slab, n) - _es("jq,iqkl->ijkl", n, w_slab)
         Pi = polarisation_sharded(part, hc, G_slab, group)   # Eq. (gwpi), rows i in I_r
         Pi4 = reshard(Pi, part, 3, group)                 # Pi[a][b][c][d in I_r]
         rhs2 = rhs2 + Pi - Pi4.permute(3, 2, 1, 0).conj()
     if selfenergy in ("TPP", "TPH", "DSL"):
         # the T-matrix ladder terms (Eqs. lambdapp, lambdaph; DSL takes both, each once)
-        gl, gg = 1j * n, -1j * nbar                       # G^< and G^> at equal times (fermions)
+        gl, gg = -1j * eta * n, -1j * nbar                # G^< and G^> at equal times
         lam = torch.zeros_like(G_slab)
         if selfenergy in ("TPP", "DSL"):
             lam = lam + tpp_ladder_sharded(part, tpp_hcorr_sharded(part, w_slab, gl, gg, group), G_slab, group)

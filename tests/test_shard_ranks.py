@@ -1,7 +1,8 @@
 """The partition of the right-hand side over ranks (G2 and w split along their first
 index, paper_2002_12717_gb300/shard.py) on CPU ranks with the gloo backend: every
 rank's slab of dG2/dt, the replicated dn/dt and the correlation energy against the
-oracle's full right-hand side, element by element, for every selfenergy on 2 ranks
+oracle's full right-hand side, element by element, for every selfenergy, fermions and
+bosons, on 2 ranks
 (nb = 6, and nb = 5 with a ragged last block), 3 ranks (nb = 5: blocks 2, 2, 1) and
 4 ranks (nb = 5: blocks 2, 2, 1, 0, an empty slab and an empty SUMMA panel)."""
 import os
@@ -17,8 +18,12 @@ from .helpers import problem
 
 torch = pytest.importorskip("torch")
 
-CASES = [("SOA", 6), ("SOA", 5), ("GW", 6), ("GW", 5), ("GWX", 5), ("HF", 5),
-         ("TPP", 6), ("TPP", 5), ("TPH", 6), ("TPH", 5), ("DSL", 6), ("DSL", 5)]
+# (selfenergy, nb, bosons)
+CASES = [("SOA", 6, False), ("SOA", 5, False), ("GW", 6, False), ("GW", 5, False), ("GWX", 5, False),
+         ("HF", 5, False), ("TPP", 6, False), ("TPP", 5, False), ("TPH", 6, False), ("TPH", 5, False),
+         ("DSL", 6, False), ("DSL", 5, False),
+         ("SOA", 5, True), ("GW", 5, True), ("GWX", 6, True), ("HF", 5, True), ("TPP", 5, True),
+         ("TPH", 6, True), ("DSL", 5, True)]
 
 
 def _free_port():
@@ -40,11 +45,11 @@ def _worker(rank, world, port, outdir, cases):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        for ci, (se, nb) in enumerate(cases):
+        for ci, (se, nb, bosons) in enumerate(cases):
             h, w, n, g2 = _state(nb, se, 60 + ci)
             part = shard.Partition(nb, world, rank)
             t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128))
-            dn, dg = shard.rhs_sharded(part, t(h), part.slab(t(w)), t(n), part.slab(t(g2)), se)
+            dn, dg = shard.rhs_sharded(part, t(h), part.slab(t(w)), t(n), part.slab(t(g2)), se, bosons=bosons)
             ec = shard.correlation_energy_sharded(part, part.slab(t(w)), part.slab(t(g2)))
             np.savez(os.path.join(outdir, f"r{rank}_c{ci}.npz"), dn=dn.numpy(), dg=dg.numpy(), ec=ec,
                      lo=part.lo, hi=part.hi)
@@ -58,9 +63,9 @@ def test_sharded_rhs_matches_oracle(world):
     cases = CASES if world == 2 else [c for c in CASES if c[1] == 5]
     with tempfile.TemporaryDirectory() as outdir:
         mp.spawn(_worker, args=(world, _free_port(), outdir, cases), nprocs=world, join=True)
-        for ci, (se, nb) in enumerate(cases):
+        for ci, (se, nb, bosons) in enumerate(cases):
             h, w, n, g2 = _state(nb, se, 60 + ci)
-            prob = O.Problem(h, w, se, False)
+            prob = O.Problem(h, w, se, False, bosons=bosons)
             dn_ref, dg_ref = O.rhs(prob, 0.0, n, g2)
             e_ref = -0.5 * np.real(np.einsum("ijkl,klij->", w, g2))
             covered = np.zeros(nb, dtype=bool)
