@@ -36,7 +36,7 @@ data of other ranks, and the collective that supplies it:
   E_corr                local partial sum, scalar all-reduce
 
 Selfenergies: HF, SOA, GW, GW with exchange, the particle-particle and particle-hole T
-matrices and DSL; fermions and bosons; spin-orbital basis.
+matrices and DSL; fermions and bosons; spin-orbital basis or (not GW) spin-restricted.
 
 `summa_matmul` is the 2-D block-distributed form of the nb^2 x nb^2 x nb^2 products on a
 q x q process grid (panels of about N^4 / q elements broadcast along grid rows and
@@ -174,10 +174,13 @@ def _es(eq, *ops):
     return torch.einsum(eq, *ops)
 
 
-def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=None, bosons=False):
-    """(dn/dt, the slab of dG2/dt) at the state (n, G2) in a spin-orbital basis, for fermions or
-    (bosons=True) bosons: eta = -1 or +1 in the +/- of the paper (G^< = -i eta n, G^> = -i nbar
-    with nbar = 1 + eta n, w^+/- = w + eta w_ijlk).
+def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=None, bosons=False,
+                restricted=False):
+    """(dn/dt, the slab of dG2/dt) at the state (n, G2), for fermions or (bosons=True) bosons:
+    eta = -1 or +1 in the +/- of the paper (G^< = -i eta n, G^> = -i nbar with nbar = 1 + eta n,
+    w^+/- = w + eta w_ijlk).  In a spin-orbital basis h^HF and the source term take w^+/-; in
+    the spin-restricted mode (restricted=True, one spin species of an opposite-spin
+    interaction; not GW) both take the plain w.
 
     h, n: replicated nb x nb; w_slab = w[I_r], G_slab = G2[I_r] (complex tensors).  dn is
     the same on every rank.  The arithmetic is that of the oracle's right-hand side with
@@ -188,7 +191,9 @@ def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=N
     eta = 1.0 if bosons else -1.0
     nbar = eye + eta * n
     # Eq. (h_HF): hHF_ij = h_ij + sum_kl (w_ikjl +/- w_iklj) n_lk, rows i in I_r
-    wpm = w_slab + eta * w_slab.permute(0, 1, 3, 2)
+    if restricted and selfenergy in ("GW", "GWX", "DSL"):
+        raise ValueError("GW couples same-spin components; no spin-restricted form")
+    wpm = w_slab if restricted else w_slab + eta * w_slab.permute(0, 1, 3, 2)
     hhf = torch.zeros((nb, nb), dtype=cd, device=n.device)
     hhf[lo:hi] = _es("ikjl,lk->ij", wpm, n)
     dist.all_reduce(hhf, group=group)
@@ -233,12 +238,13 @@ def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=N
     return dn, -1j * rhs2
 
 
-def correlation_energy_sharded(part: Partition, w_slab, G_slab, group=None):
-    """E_corr = -1/2 Re sum_ijkl w_ijkl G2_klij (spin-orbital basis), with
+def correlation_energy_sharded(part: Partition, w_slab, G_slab, group=None, restricted=False):
+    """E_corr = -1/2 Re sum_ijkl w_ijkl G2_klij in a spin-orbital basis (-Re sum in the
+    spin-restricted mode, both spin species of the opposite-spin interaction), with
     G2_klij = conj(G2_ijkl): a local partial sum and one scalar all-reduce."""
     e = torch.tensor([(w_slab * G_slab.conj()).sum().real.item()], dtype=torch.float64)
     dist.all_reduce(e, group=group)
-    return -0.5 * e.item()
+    return -(1.0 if restricted else 0.5) * e.item()
 
 
 # ---------------------------------------------------------------------------

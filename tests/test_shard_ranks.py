@@ -2,7 +2,7 @@
 index, paper_2002_12717_gb300/shard.py) on CPU ranks with the gloo backend: every
 rank's slab of dG2/dt, the replicated dn/dt and the correlation energy against the
 oracle's full right-hand side, element by element, for every selfenergy, fermions and
-bosons, on 2 ranks
+bosons, spin-orbital and (not GW) spin-restricted, on 2 ranks
 (nb = 6, and nb = 5 with a ragged last block), 3 ranks (nb = 5: blocks 2, 2, 1) and
 4 ranks (nb = 5: blocks 2, 2, 1, 0, an empty slab and an empty SUMMA panel)."""
 import os
@@ -18,12 +18,14 @@ from .helpers import problem
 
 torch = pytest.importorskip("torch")
 
-# (selfenergy, nb, bosons)
-CASES = [("SOA", 6, False), ("SOA", 5, False), ("GW", 6, False), ("GW", 5, False), ("GWX", 5, False),
-         ("HF", 5, False), ("TPP", 6, False), ("TPP", 5, False), ("TPH", 6, False), ("TPH", 5, False),
-         ("DSL", 6, False), ("DSL", 5, False),
-         ("SOA", 5, True), ("GW", 5, True), ("GWX", 6, True), ("HF", 5, True), ("TPP", 5, True),
-         ("TPH", 6, True), ("DSL", 5, True)]
+# (selfenergy, nb, bosons, spin-restricted)
+CASES = [("SOA", 6, False, False), ("SOA", 5, False, False), ("GW", 6, False, False), ("GW", 5, False, False),
+         ("GWX", 5, False, False), ("HF", 5, False, False), ("TPP", 6, False, False), ("TPP", 5, False, False),
+         ("TPH", 6, False, False), ("TPH", 5, False, False), ("DSL", 6, False, False), ("DSL", 5, False, False),
+         ("SOA", 5, True, False), ("GW", 5, True, False), ("GWX", 6, True, False), ("HF", 5, True, False),
+         ("TPP", 5, True, False), ("TPH", 6, True, False), ("DSL", 5, True, False),
+         ("SOA", 5, False, True), ("SOA", 6, False, True), ("HF", 5, False, True), ("TPP", 5, False, True),
+         ("TPH", 6, False, True)]
 
 
 def _free_port():
@@ -32,8 +34,12 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _state(nb, se, seed):
-    h, w, n, g2, _, _ = problem(nb, se if se != "HF" else "SOA", complex_w=True, seed=seed, drive=False)
+def _state(nb, se, seed, restricted=False):
+    se_ = se if se != "HF" else "SOA"
+    if restricted:
+        h, w, n, g2, _, _ = problem(nb, se_, restricted=True, seed=seed, drive=False)
+    else:
+        h, w, n, g2, _, _ = problem(nb, se_, complex_w=True, seed=seed, drive=False)
     return h, w, n, g2
 
 
@@ -45,12 +51,13 @@ def _worker(rank, world, port, outdir, cases):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        for ci, (se, nb, bosons) in enumerate(cases):
-            h, w, n, g2 = _state(nb, se, 60 + ci)
+        for ci, (se, nb, bosons, rs) in enumerate(cases):
+            h, w, n, g2 = _state(nb, se, 60 + ci, rs)
             part = shard.Partition(nb, world, rank)
             t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128))
-            dn, dg = shard.rhs_sharded(part, t(h), part.slab(t(w)), t(n), part.slab(t(g2)), se, bosons=bosons)
-            ec = shard.correlation_energy_sharded(part, part.slab(t(w)), part.slab(t(g2)))
+            dn, dg = shard.rhs_sharded(part, t(h), part.slab(t(w)), t(n), part.slab(t(g2)), se, bosons=bosons,
+                                       restricted=rs)
+            ec = shard.correlation_energy_sharded(part, part.slab(t(w)), part.slab(t(g2)), restricted=rs)
             np.savez(os.path.join(outdir, f"r{rank}_c{ci}.npz"), dn=dn.numpy(), dg=dg.numpy(), ec=ec,
                      lo=part.lo, hi=part.hi)
     finally:
@@ -63,11 +70,11 @@ def test_sharded_rhs_matches_oracle(world):
     cases = CASES if world == 2 else [c for c in CASES if c[1] == 5]
     with tempfile.TemporaryDirectory() as outdir:
         mp.spawn(_worker, args=(world, _free_port(), outdir, cases), nprocs=world, join=True)
-        for ci, (se, nb, bosons) in enumerate(cases):
-            h, w, n, g2 = _state(nb, se, 60 + ci)
-            prob = O.Problem(h, w, se, False, bosons=bosons)
+        for ci, (se, nb, bosons, rs) in enumerate(cases):
+            h, w, n, g2 = _state(nb, se, 60 + ci, rs)
+            prob = O.Problem(h, w, se, rs, bosons=bosons)
             dn_ref, dg_ref = O.rhs(prob, 0.0, n, g2)
-            e_ref = -0.5 * np.real(np.einsum("ijkl,klij->", w, g2))
+            e_ref = -(1.0 if rs else 0.5) * np.real(np.einsum("ijkl,klij->", w, g2))
             covered = np.zeros(nb, dtype=bool)
             for r in range(world):
                 z = np.load(os.path.join(outdir, f"r{r}_c{ci}.npz"))
