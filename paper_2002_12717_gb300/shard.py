@@ -38,6 +38,10 @@ data of other ranks, and the collective that supplies it:
 Selfenergies: HF, SOA, GW, GW with exchange, the particle-particle and particle-hole T
 matrices and DSL; fermions and bosons; spin-orbital basis or (not GW) spin-restricted.
 
+`rk4_step_sharded` takes one classical RK4 step on the slabs: four partitioned right-hand
+sides, the stage states formed locally (G2 on each rank's slab, n replicated), no
+exchange beyond those of the right-hand sides.
+
 `summa_matmul` is the 2-D block-distributed form of the nb^2 x nb^2 x nb^2 products on a
 q x q process grid (panels of about N^4 / q elements broadcast along grid rows and
 columns), for a partition that keeps those operands in 2-D blocks.
@@ -236,6 +240,23 @@ def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=N
         L3 = reshard(lam, part, 2, group)                 # Lambda[a][b][c in I_r][d]
         rhs2 = rhs2 + lam - L3.permute(2, 3, 0, 1).conj()  # - conj(Lambda_klij)
     return dn, -1j * rhs2
+
+
+def rk4_step_sharded(part: Partition, h_of_t, t, w_slab, n, G_slab, dt, selfenergy="SOA", group=None,
+                     bosons=False, restricted=False):
+    """One classical RK4 step of (n, G2) with G2 partitioned (the slab G2[i in I_r], n replicated):
+    four right-hand sides of rhs_sharded at t, t + dt/2, t + dt/2, t + dt (h_of_t(t) the
+    replicated one-body Hamiltonian at time t), the stage states formed on each rank's slab.
+    Returns (n, the slab of G2) at t + dt."""
+    def f(tt, nn, gg):
+        return rhs_sharded(part, h_of_t(tt), w_slab, nn, gg, selfenergy, group, bosons, restricted)
+    k1 = f(t, n, G_slab)
+    k2 = f(t + dt / 2, n + dt / 2 * k1[0], G_slab + dt / 2 * k1[1])
+    k3 = f(t + dt / 2, n + dt / 2 * k2[0], G_slab + dt / 2 * k2[1])
+    k4 = f(t + dt, n + dt * k3[0], G_slab + dt * k3[1])
+    n_new = n + dt / 6 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0])
+    G_new = G_slab + dt / 6 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1])
+    return n_new, G_new
 
 
 def correlation_energy_sharded(part: Partition, w_slab, G_slab, group=None, restricted=False):
