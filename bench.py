@@ -553,6 +553,38 @@ FP64_CMAC = {
 }
 
 
+def factorised_compare(sizes, steps=3, selfenergies=("SOA", "GWX")):
+    """ms per RK4 step of the FP64 form on the seeded general basis (rank 2 nb, nb/2 occupied,
+    gauss-sine pulse) with w given as the nb^4 tensor and as its 2 nb factors (the factorised
+    source term), and the largest difference of the two states after the timed steps."""
+    import torch
+
+    from paper_2002_12717_gb300.g1g2 import Propagator
+
+    out = []
+    for nb, se in ((nb, se) for nb in sizes for se in selfenergies):
+        d = inputs.general_basis(nb, 2 * nb, nb // 2, seed=nb, selfenergy=se, pulse=True)
+        row, states = {"nb": nb, "selfenergy": se, "nfac": 2 * nb}, []
+        for key in ("w", "factors"):
+            kw = {"factors": d["factors"]} if key == "factors" else {}
+            with Propagator(d["h"], d["w"] if key == "w" else None, d["n0"], None, se, "fp64", **kw) as p:
+                p.set_drive(d["D"], d["drive"])
+                p.step(0.01)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(steps):
+                    p.step(0.01)
+                e1.record()
+                torch.cuda.synchronize()
+                row[f"{key}_ms"] = round(e0.elapsed_time(e1) / steps, 3)
+                states.append(p.get_state()[1:])
+        row["max_dG1"] = float(np.abs(states[0][0] - states[1][0]).max())
+        row["max_dG2"] = float(np.abs(states[0][1] - states[1][1]).max())
+        out.append(row)
+    return out
+
+
 def selfenergy_sweep(sizes, precisions=("fp64",), steps=2):
     """ms per RK4 step of every selfenergy on the seeded general basis (rank 2 nb, nb/2
     occupied, gauss-sine pulse).  FP64 form: the algorithmic FLOP rate against the
@@ -785,6 +817,8 @@ def main():
     ap.add_argument("--selfenergy-sweep", default="",
                     help="comma-separated nb: time every selfenergy and exit (forms: --sweep-precisions)")
     ap.add_argument("--sweep-precisions", default="fp64", help="comma-separated forms of --selfenergy-sweep")
+    ap.add_argument("--factorised-compare", default="",
+                    help="comma-separated nb: time the FP64 form with w as a tensor and as its factors, and exit")
     ap.add_argument("--accuracy-run", default="",
                     help="comma-separated workloads: propagate each for its full length in the BF16-slice and "
                          "FP64 forms side by side, record the differences and energy drifts, and exit")
@@ -841,6 +875,11 @@ def main():
             sweep = selfenergy_sweep([int(x) for x in args.selfenergy_sweep.split(",")],
                                      args.sweep_precisions.split(","))
             print(json.dumps({"selfenergy_sweep": sweep}), flush=True)
+        return
+    if args.factorised_compare:
+        if rank == 0:
+            rows = factorised_compare([int(x) for x in args.factorised_compare.split(",")])
+            print(json.dumps({"factorised_compare": rows}), flush=True)
         return
     if args.nt_scaling:
         if rank == 0:

@@ -138,6 +138,25 @@ void g1g2_default_options(g1g2_options *opt);
 int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const double *G1_0,
               const double *G2_0, int se, const g1g2_options *opt);
 
+/* Create a context for a factorised interaction
+ *   w_ijkl = sum_{P<nfac} L^P_ik L^P_jl
+ * (the density-fitted / Cholesky form of a two-electron integral tensor; the
+ * paper's general-basis w of Eq. (h) in the pair order (ik),(jl)).
+ *   L      nfac*nb*nb, element (P, i, k) at P*nb*nb + i*nb + k: complex
+ *          interleaved, or real if opt->w_is_real (host, copied).  Each L^P is
+ *          Hermitian or i times Hermitian, so that w meets Eqs. (wsymm_a/b)
+ *   nfac   number of factors, 1 <= nfac <= nb*nb
+ * The other arguments and the error codes are those of g1g2_init, which runs on
+ * the w expanded on the device (one nb^2 x nb^2 x nfac product; nb^4 complex
+ * doubles of host memory for the duration of the call).  In the FP64 form the
+ * source term of Eq. (psi-pm-def) then runs in the factorised form: M^P = nbar
+ * L^P n (two batched nb^3 products per factor) and
+ *   A_ijkl = sum_P M^P_ik M^P_jl  (+ eta M^P_il M^P_jk for the source w^±),
+ * an nb^2 x nb^2 x nfac product in place of four nb^5 mode products.  The
+ * split-precision forms run on the expanded w. */
+int g1g2_init_factorised(g1g2_ctx **out, int nb, const double *h, const double *L, int nfac,
+                         const double *G1_0, const double *G2_0, int se, const g1g2_options *opt);
+
 /* Time-dependent one-body term h(t) = h + f(t) D (the excitations of the
  * workloads; the paper's Eq. (h) allows any h(t)).
  *   D       nb*nb complex Hermitian (host), copied

@@ -82,6 +82,13 @@ def w_antisym(w):
     return w_pm(w, -1)
 
 
+def w_from_factors(L):
+    """Factorised (density-fitted) interaction w_ijkl = Σ_P L^P_ik L^P_jl: the general-basis
+    w of Eq. (h) written through nfac factors L[P] (nb x nb), each Hermitian or i times
+    Hermitian so that w meets Eqs. (wsymm_a/b)."""
+    return einsum("pik,pjl->ijkl", L, L)
+
+
 def hf_hamiltonian(h, w, n, restricted=False, eta=-1):
     """Eq. (h_HF): h^HF_ij = h_ij ± iħ Σ_kl w^±_ikjl G^<_lk.
 

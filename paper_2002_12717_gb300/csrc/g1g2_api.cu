@@ -49,6 +49,10 @@ struct g1g2_ctx {
   cplx *wsrc = nullptr;             // source-term interaction (w^- or w)
   bool src_pm = false;              // wsrc = w + eta w_ijlk (else wsrc = w)
   cplx *wP = nullptr;               // collision layout [(lp)][i][k] = w_iklp
+  // factorised interaction w_ijkl = sum_P L^P_ik L^P_jl (FP64 form): factors [P][i][k] and
+  // the per-factor products L^P n and nbar L^P n
+  int nfac = 0;
+  cplx *Lf = nullptr, *LfN = nullptr, *Mf = nullptr;
   cplx *n = nullptr, *ns = nullptr, *ns2 = nullptr, *nacc = nullptr;
   cplx *G = nullptr, *Gs = nullptr, *Gacc = nullptr;
   cplx *hhf = nullptr, *nbar = nullptr, *I = nullptr, *ntr = nullptr;
@@ -189,10 +193,16 @@ void collision(g1g2_ctx *c, Launcher &L, const cplx *G_in) {
 
 // a4: A_ijkl = sum nbar_ip nbar_jq wt_pqrs n_rk n_sl (Eq. psi-pm-def) by successive
 // contractions into c->Ab (nbar into c->nbar); the source term is Psi = -A + A^dag
+void source_A_factorised(g1g2_ctx *c, Launcher &L, const cplx *n_in);
+
 void source_A(g1g2_ctx *c, Launcher &L, const cplx *n_in) {
   const int nb = c->nb;
   const long long N = nb, N2 = N * N, N3 = N2 * N;
   one_pm(L, nb, n_in, c->eta, c->nbar);
+  if (c->Lf) {
+    source_A_factorised(c, L, n_in);
+    return;
+  }
   {
     ZGemm g;  // T1_pqrl = sum_s wt_pqrs n_sl
     g.M = (int)N3; g.N = nb; g.K = nb;
@@ -224,6 +234,48 @@ void source_A(g1g2_ctx *c, Launcher &L, const cplx *n_in) {
     g.B = c->T1; g.sb_k = N3; g.sb_n = 1;
     g.C = c->Ab; g.sc_m = N3; g.sc_n = 1;
     zgemm(L, g);
+  }
+}
+
+// a4 for a factorised interaction w_pqrs = sum_P L^P_pr L^P_qs: the mode products act on
+// each factor, sum_pr nbar_ip L^P_pr n_rk = M^P_ik with M^P = nbar L^P n, so
+//   A_ijkl = sum_P M^P_ik M^P_jl            (plain w)
+//          + eta sum_P M^P_il M^P_jk        (the exchange part of w^± = w_pqrs + eta w_pqsr)
+// The pair product C_(ik),(jl) = sum_P M^P_ik M^P_jl is one nb^2 x nb^2 x nfac GEMM (into T1);
+// A follows by two index permutations of C.  c->nbar is set by the caller.
+void source_A_factorised(g1g2_ctx *c, Launcher &L, const cplx *n_in) {
+  const int nb = c->nb, P = c->nfac;
+  const long long N = nb, N2 = N * N;
+  {
+    ZGemm g;  // LfN^P_pk = sum_r L^P_pr n_rk  (batched over P)
+    g.M = nb; g.N = nb; g.K = nb; g.batch = P;
+    g.A = c->Lf; g.sa_b = N2; g.sa_m = N; g.sa_k = 1;
+    g.B = n_in; g.sb_k = N; g.sb_n = 1;
+    g.C = c->LfN; g.sc_b = N2; g.sc_m = N; g.sc_n = 1;
+    zgemm(L, g);
+  }
+  {
+    ZGemm g;  // M^P_ik = sum_p nbar_ip LfN^P_pk  (batched over P)
+    g.M = nb; g.N = nb; g.K = nb; g.batch = P;
+    g.A = c->nbar; g.sa_m = N; g.sa_k = 1;
+    g.B = c->LfN; g.sb_b = N2; g.sb_k = N; g.sb_n = 1;
+    g.C = c->Mf; g.sc_b = N2; g.sc_m = N; g.sc_n = 1;
+    zgemm(L, g);
+  }
+  {
+    ZGemm g;  // C_(ik),(jl) = sum_P M^P_(ik) M^P_(jl)
+    g.M = (int)N2; g.N = (int)N2; g.K = P;
+    g.A = c->Mf; g.sa_m = 1; g.sa_k = N2;
+    g.B = c->Mf; g.sb_k = N2; g.sb_n = 1;
+    g.C = c->T1; g.sc_m = N2; g.sc_n = 1;
+    zgemm(L, g);
+  }
+  // A_ijkl = C(i,k,j,l) [+ eta C(i,l,j,k)]
+  const int p_direct[4] = {0, 2, 1, 3};
+  permute4(L, nb, c->T1, c->Ab, p_direct, {1.0, 0.0}, 0.0, false);
+  if (c->src_pm) {
+    const int p_exch[4] = {0, 3, 1, 2};
+    permute4(L, nb, c->T1, c->Ab, p_exch, {c->eta, 0.0}, 1.0, false);
   }
 }
 
@@ -1216,6 +1268,95 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
   }
   if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "init sync"))) return bail(rc);
   *out = c;
+  return G1G2_OK;
+}
+
+// w_ijkl = sum_P L^P_ik L^P_jl expanded on the device (the pair product C_(ik),(jl) and one
+// index permutation), then the context of g1g2_init on that w; FP64 contexts with a correlated
+// selfenergy keep the factors for the factorised source term (source_A_factorised).
+int g1g2_init_factorised(g1g2_ctx **out, int nb, const double *h, const double *Lh, int nfac, const double *G1_0,
+                         const double *G2_0, int se, const g1g2_options *opt_in) {
+  if (!out) return fail(G1G2_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nb < 1 || nb > 128) return fail(G1G2_EINVAL, "nb must be in [1, 128]");
+  if (!h || !Lh || !G1_0) return fail(G1G2_EINVAL, "h, L and G1_0 must be non-NULL");
+  if (se < G1G2_HF || se > G1G2_DSL) return fail(G1G2_EINVAL, "bad selfenergy");
+  if (nfac < 1 || (long long)nfac > (long long)nb * nb) return fail(G1G2_EINVAL, "nfac must be in [1, nb^2]");
+  g1g2_options opt;
+  g1g2_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  const size_t N2 = (size_t)nb * nb, N4 = N2 * N2, NL = (size_t)nfac * N2;
+  std::vector<cplx> hL(NL);
+  for (size_t e = 0; e < NL; ++e) hL[e] = opt.w_is_real ? cplx{Lh[e], 0.0} : cplx{Lh[2 * e], Lh[2 * e + 1]};
+  cudaStream_t s = static_cast<cudaStream_t>(opt.cuda_stream);
+  cplx *dL = nullptr, *dC = nullptr, *dW = nullptr;
+  auto alloc = [](cplx **p, size_t count) -> int {
+    void *q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(cplx)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(G1G2_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(cplx)) + " bytes failed");
+    }
+    *p = static_cast<cplx *>(q);
+    return G1G2_OK;
+  };
+  auto release = [&]() {
+    if (dL) cudaFree(dL);
+    if (dC) cudaFree(dC);
+    if (dW) cudaFree(dW);
+    dL = dC = dW = nullptr;
+  };
+  int rc = G1G2_OK;
+  if ((rc = alloc(&dL, NL)) || (rc = alloc(&dC, N4)) || (rc = alloc(&dW, N4))) {
+    release();
+    return rc;
+  }
+  std::vector<double> hw;
+  rc = cuda_check(cudaMemcpyAsync(dL, hL.data(), NL * sizeof(cplx), cudaMemcpyHostToDevice, s), "factor upload");
+  if (!rc) {
+    Launcher L;
+    L.stream = s;
+    ZGemm g;  // C_(ik),(jl) = sum_P L^P_(ik) L^P_(jl)
+    g.M = (int)N2; g.N = (int)N2; g.K = nfac;
+    g.A = dL; g.sa_m = 1; g.sa_k = (long long)N2;
+    g.B = dL; g.sb_k = (long long)N2; g.sb_n = 1;
+    g.C = dC; g.sc_m = (long long)N2; g.sc_n = 1;
+    zgemm(L, g);
+    const int p[4] = {0, 2, 1, 3};  // w(i,j,k,l) = C(i,k,j,l)
+    permute4(L, nb, dC, dW, p, {1.0, 0.0}, 0.0, false);
+    rc = launch_status(L, "factorised interaction");
+  }
+  if (!rc) {
+    hw.resize(2 * N4);
+    rc = cuda_check(cudaMemcpyAsync(hw.data(), dW, N4 * sizeof(cplx), cudaMemcpyDeviceToHost, s), "w download");
+  }
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "factorised interaction sync");
+  cudaFree(dC);
+  cudaFree(dW);
+  dC = dW = nullptr;
+  if (rc) {
+    release();
+    return rc;
+  }
+  g1g2_options o2 = opt;
+  o2.w_is_real = 0;
+  rc = g1g2_init(out, nb, h, hw.data(), G1_0, G2_0, se, &o2);
+  if (rc) {
+    release();
+    return rc;
+  }
+  g1g2_ctx *c = *out;
+  if (c->T1 && c->Ab) {  // FP64 form with a source term
+    c->allocs.push_back(dL);
+    c->Lf = dL;
+    dL = nullptr;
+    c->nfac = nfac;
+    if ((rc = dalloc(c, &c->LfN, NL)) || (rc = dalloc(c, &c->Mf, NL))) {
+      g1g2_destroy(c);
+      *out = nullptr;
+      return rc;
+    }
+  }
+  release();
   return G1G2_OK;
 }
 

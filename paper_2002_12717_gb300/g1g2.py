@@ -61,6 +61,8 @@ def load():
         "g1g2_default_options": (None, [ctypes.POINTER(Options)]),
         "g1g2_init": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int,
                                      ctypes.POINTER(Options)]),
+        "g1g2_init_factorised": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp,
+                                                ctypes.c_int, ctypes.POINTER(Options)]),
         "g1g2_set_drive": (ctypes.c_int, [vp, _dp, ctypes.c_int, _dp, ctypes.c_int]),
         "g1g2_rhs": (ctypes.c_int, [vp, ctypes.c_double, vp, vp, vp, vp]),
         "g1g2_step": (ctypes.c_int, [vp, ctypes.c_double]),
@@ -167,7 +169,10 @@ class Propagator:
     """One g1g2_ctx: state (G1 = n, G2), RK4 stepping, observables."""
 
     def __init__(self, h, w, n0, G2_0=None, selfenergy="SOA", precision="fp64", restricted=False,
-                 sym_tol=1e-10, stream=None, bosons=False):
+                 sym_tol=1e-10, stream=None, bosons=False, factors=None):
+        """w: the nb^4 interaction, or None with `factors` = L of shape (nfac, nb, nb), each L^P
+        Hermitian or i times Hermitian, for the factorised w_ijkl = sum_P L^P_ik L^P_jl
+        (g1g2_init_factorised)."""
         lib = load()
         self.nb = int(np.asarray(h).shape[0])
         self.restricted = restricted
@@ -179,17 +184,26 @@ class Propagator:
         opt.sym_tol = sym_tol
         opt.cuda_stream = stream
         opt.statistics = 1 if bosons else 0
-        w = np.asarray(w)
-        if np.isrealobj(w):
-            wbuf = np.ascontiguousarray(w, dtype=np.float64)
+        if (w is None) == (factors is None):
+            raise ValueError("give exactly one of w and factors")
+        x = np.asarray(w if factors is None else factors)
+        if factors is not None and (x.ndim != 3 or x.shape[1:] != (self.nb, self.nb)):
+            raise ValueError(f"factors must have shape (nfac, {self.nb}, {self.nb}), got {x.shape}")
+        if np.isrealobj(x):
+            wbuf = np.ascontiguousarray(x, dtype=np.float64)
             opt.w_is_real = 1
         else:
-            wbuf = _c128(w)
+            wbuf = _c128(x)
         hb, nbuf = _c128(h), _c128(n0)
         gbuf = None if G2_0 is None else _c128(G2_0)
+        gptr = None if gbuf is None else _cptr(gbuf)
         ctx = ctypes.c_void_p()
-        rc = lib.g1g2_init(ctypes.byref(ctx), self.nb, _cptr(hb), _cptr(wbuf), _cptr(nbuf),
-                           None if gbuf is None else _cptr(gbuf), SELFENERGY[selfenergy], ctypes.byref(opt))
+        if factors is None:
+            rc = lib.g1g2_init(ctypes.byref(ctx), self.nb, _cptr(hb), _cptr(wbuf), _cptr(nbuf), gptr,
+                               SELFENERGY[selfenergy], ctypes.byref(opt))
+        else:
+            rc = lib.g1g2_init_factorised(ctypes.byref(ctx), self.nb, _cptr(hb), _cptr(wbuf), int(x.shape[0]),
+                                          _cptr(nbuf), gptr, SELFENERGY[selfenergy], ctypes.byref(opt))
         _check(rc)
         self._ctx = ctx
         self._lib = lib

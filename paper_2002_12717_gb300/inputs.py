@@ -112,10 +112,20 @@ def random_hermitian(nb, rng):
     return (a + a.conj().T) / 2
 
 
-def factor_w(nb, rank, rng, sigma=0.1):
-    """w_ijkl = Σ_P L^P_ik L^P_jl, L^P = (B + B^T)/2 with B ~ N(0, sigma^2). Real, nb^4."""
+def factors(nb, rank, rng, sigma=0.1):
+    """The factors L^P = (B + B^T)/2, B ~ N(0, sigma^2), P < rank: real, shape (rank, nb, nb)."""
     b = rng.standard_normal((rank, nb, nb)) * sigma
-    lp = (b + b.transpose(0, 2, 1)) / 2
+    return (b + b.transpose(0, 2, 1)) / 2
+
+
+def factor_w(nb, rank, rng, sigma=0.1):
+    """w_ijkl = Σ_P L^P_ik L^P_jl with the factors of `factors`. Real, nb^4."""
+    return expand_factors(factors(nb, rank, rng, sigma))
+
+
+def expand_factors(lp):
+    """The nb^4 tensor Σ_P L^P_ik L^P_jl of factors lp[P] (the workloads' w)."""
+    rank, nb = lp.shape[0], lp.shape[1]
     flat = lp.reshape(rank, nb * nb)                  # [P, (i,k)]
     wik_jl = flat.T @ flat                            # [(i,k), (j,l)]
     return np.ascontiguousarray(wik_jl.reshape(nb, nb, nb, nb).transpose(0, 2, 1, 3))
@@ -204,13 +214,14 @@ def general_basis(nb, rank, n_occ, seed, selfenergy="SOA", pulse=False):
     """Seeded general basis, optional gauss-sine pulse with a random real diagonal dipole."""
     rng = np.random.default_rng(seed)
     h = random_hermitian(nb, rng)
-    w = factor_w(nb, rank, rng)
+    lp = factors(nb, rank, rng)
+    w = expand_factors(lp)
     n0 = lowest_projector(h, n_occ)
     D = drive = None
     if pulse:
         D = np.diag(rng.standard_normal(nb)).astype(np.complex128)
         drive = GaussSine()
-    return dict(name=f"general-{selfenergy.lower()}-nb{nb}", nb=nb, h=h, w=w, n0=n0, G2_0=None,
+    return dict(name=f"general-{selfenergy.lower()}-nb{nb}", nb=nb, h=h, w=w, factors=lp, n0=n0, G2_0=None,
                 selfenergy=selfenergy, restricted=False, D=D, drive=drive)
 
 

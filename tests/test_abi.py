@@ -86,6 +86,35 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert _init(lib, 3, h, w, n0, opt={"statistics": 1, "basis": 1}) == g1g2.EINVAL   # bosons: spin-orbital only
 
 
+def test_factorised_arguments_rejected_on_host(lib):
+    """g1g2_init_factorised checks its arguments before any device work."""
+    h, _, n0 = _valid(3)
+    L = np.zeros((2, 3, 3))
+    ctx = ctypes.c_void_p()
+    o = g1g2.Options()
+    lib.g1g2_default_options(ctypes.byref(o))
+    o.w_is_real = 1
+    ptr = lambda a: None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    def init(nb, hh, LL, nfac, nn, se=1):
+        return lib.g1g2_init_factorised(ctypes.byref(ctx), nb, ptr(hh), ptr(LL), nfac, ptr(nn), None, se,
+                                        ctypes.byref(o))
+    assert init(0, h, L, 2, n0) == g1g2.EINVAL
+    assert init(129, h, L, 2, n0) == g1g2.EINVAL
+    assert init(3, h, None, 2, n0) == g1g2.EINVAL
+    assert init(3, None, L, 2, n0) == g1g2.EINVAL
+    assert init(3, h, L, 2, None) == g1g2.EINVAL
+    assert init(3, h, L, 0, n0) == g1g2.EINVAL
+    assert init(3, h, L, 10, n0) == g1g2.EINVAL           # more than nb^2 factors
+    assert b"nfac" in lib.g1g2_last_error_detail()
+    assert init(3, h, L, 2, n0, se=9) == g1g2.EINVAL
+    assert not ctx.value
+    with pytest.raises(ValueError):
+        g1g2.Propagator(h, None, n0)                        # neither w nor factors
+    with pytest.raises(ValueError):
+        g1g2.Propagator(h, None, n0, factors=np.zeros((2, 3, 4)))
+
+
 def test_symmetry_violations_rejected_on_host(lib):
     h, w, n0 = _valid(3)
     bad = w.copy()

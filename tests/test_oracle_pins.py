@@ -179,6 +179,70 @@ def test_psi_successive_contractions_equal_literal_phi_sum(nb):
         assert np.abs(O.psi_source(wt, n) - literal).max() < 1e-12
 
 
+def test_factorised_w_reproduces_the_hubbard_interactions():
+    """w_from_factors against the paper's Hubbard interactions built element by element:
+    the on-site opposite-spin w = U δ_ij δ_ik δ_il from the factors sqrt(U) e_a e_a^T, and
+    the spin-orbital w of Eq. (wmatrix-hubbard) from two factors per site, the Hermitian
+    sqrt(U/2) (E_up + E_dn) and i sqrt(U/2) (E_up - E_dn) (their same-spin parts cancel)."""
+    L, U = 4, 1.7
+    f = np.zeros((L, L, L), dtype=np.complex128)
+    for a in range(L):
+        f[a, a, a] = math.sqrt(U)
+    assert np.abs(O.w_from_factors(f) - inputs.onsite_w_restricted(L, U)).max() < 1e-15
+    nb = 2 * L
+    f = np.zeros((2 * L, nb, nb), dtype=np.complex128)
+    for s_ in range(L):
+        up, dn = 2 * s_, 2 * s_ + 1
+        f[2 * s_, up, up] = f[2 * s_, dn, dn] = math.sqrt(U / 2)
+        f[2 * s_ + 1, up, up] = 1j * math.sqrt(U / 2)
+        f[2 * s_ + 1, dn, dn] = -1j * math.sqrt(U / 2)
+    assert np.abs(O.w_from_factors(f) - inputs.spin_orbital_hubbard_w(L, U)).max() < 1e-15
+
+
+def test_factorised_w_symmetries_and_rank():
+    """Hermitian and i-Hermitian factors give Eqs. (wsymm_a/b); real symmetric factors give a
+    positive semidefinite (ik),(jl) matrix of rank nfac (a Coulomb-like integral tensor)."""
+    rng = np.random.default_rng(3)
+    nb, P = 5, 4
+    a = rng.standard_normal((P, nb, nb)) + 1j * rng.standard_normal((P, nb, nb))
+    herm = (a + a.conj().transpose(0, 2, 1)) / 2
+    herm[1::2] *= 1j
+    w = O.w_from_factors(herm)
+    assert np.abs(w - w.transpose(1, 0, 3, 2)).max() < 1e-14
+    assert np.abs(w - w.transpose(2, 3, 0, 1).conj()).max() < 1e-14
+    b = rng.standard_normal((P, nb, nb))
+    w = O.w_from_factors((b + b.transpose(0, 2, 1)) / 2)
+    m = w.transpose(0, 2, 1, 3).reshape(nb * nb, nb * nb)
+    ev = np.linalg.eigvalsh(m)
+    assert ev.min() > -1e-13 * ev.max()
+    assert int((ev > 1e-10 * ev.max()).sum()) == P
+
+
+@pytest.mark.parametrize("eta", [-1, 1])
+def test_psi_for_factorised_w_equals_factor_products(eta):
+    """For w = Σ_P L^P ⊗ L^P each sum of the successive contractions of Eq. (soa-skalierung)
+    acts on one factor: Σ_pqrs a_ip b_jq w_pqrs c_rk d_sl = Σ_P (a L^P c)_ik (b L^P d)_jl, and
+    the exchange part of w^± pairs (a L^P d)_il with (b L^P c)_jk.  psi_source (plain w and
+    w^±, fermions and bosons) against these nb^3 factor products."""
+    rng = np.random.default_rng(11)
+    nb, P = 5, 6
+    b = rng.standard_normal((P, nb, nb))
+    L = (b + b.transpose(0, 2, 1)) / 2
+    w = O.w_from_factors(L)
+    n, _ = inputs.random_state(nb, rng, soa=False)
+    gl, gg = O.g_less(n, eta), O.g_greater(n, eta)
+
+    def chain(a, b_, c, d, pm):
+        x = sum(np.einsum("ik,jl->ijkl", a @ Lp @ c, b_ @ Lp @ d) for Lp in L)
+        if pm:
+            x = x + eta * sum(np.einsum("il,jk->ijkl", a @ Lp @ d, b_ @ Lp @ c) for Lp in L)
+        return x
+    for pm in (False, True):
+        ref = -(chain(gg, gg, gl, gl, pm) - chain(gl, gl, gg, gg, pm))
+        got = O.psi_source(O.w_pm(w, eta) if pm else w, n, eta)
+        assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+
+
 def test_commutator_equals_kronecker_matrix_commutator():
     """Eq. (twopart_hamiltonian): h2 = 1⊗h + h⊗1 as an nb^2 x nb^2 matrix."""
     rng = np.random.default_rng(30)
