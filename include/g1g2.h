@@ -46,7 +46,7 @@ extern "C" {
 #define G1G2_ESYMM        -2  /* w, G1_0 or G2_0 violates the symmetries of Sec. II (Eqs. Gsymm, wsymm) */
 #define G1G2_ENOMEM       -3  /* device allocation failed */
 #define G1G2_ECUDA        -4  /* a CUDA runtime call or kernel launch failed */
-#define G1G2_ENONFINITE   -5  /* the state contains NaN or Inf */
+#define G1G2_ENONFINITE   -5  /* the state or a host input contains NaN or Inf */
 #define G1G2_ETIMEOUT     -6  /* a bounded device wait gave up */
 #define G1G2_EUNSUPPORTED -7  /* valid request that this build does not implement */
 
@@ -134,7 +134,9 @@ void g1g2_default_options(g1g2_options *opt);
  *   opt        options, or NULL for the defaults
  * Returns G1G2_EINVAL for nb out of range, NULL arrays, bad enums, or GW in
  * the spin-restricted basis; G1G2_ESYMM when a symmetry is violated beyond
- * sym_tol; G1G2_ENOMEM / G1G2_ECUDA on device failure. t starts at 0. */
+ * sym_tol; G1G2_ENONFINITE when h, w, G1_0 or G2_0 holds a NaN or an Inf
+ * (checked on the host before any device work); G1G2_ENOMEM / G1G2_ECUDA on
+ * device failure. t starts at 0. */
 int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const double *G1_0,
               const double *G2_0, int se, const g1g2_options *opt);
 
@@ -146,6 +148,7 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
  *          interleaved, or real if opt->w_is_real (host, copied).  Each L^P is
  *          Hermitian or i times Hermitian, so that w meets Eqs. (wsymm_a/b)
  *   nfac   number of factors, 1 <= nfac <= nb*nb
+ * A NaN or an Inf in L returns G1G2_ENONFINITE before any device work.
  * The other arguments and the error codes are those of g1g2_init, which runs on
  * the w expanded on the device (one nb^2 x nb^2 x nfac product; nb^4 complex
  * doubles of host memory for the duration of the call).  In the FP64 form the

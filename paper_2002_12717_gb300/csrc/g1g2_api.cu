@@ -124,6 +124,12 @@ int launch_status(Launcher &L, const char *what) {
 
 using zc = std::complex<double>;
 
+bool all_finite(const double *p, size_t len) {
+  for (size_t e = 0; e < len; ++e)
+    if (!std::isfinite(p[e])) return false;
+  return true;
+}
+
 inline zc hz(const double *a, size_t idx) { return zc(a[2 * idx], a[2 * idx + 1]); }
 
 double drive_f(const g1g2_ctx *c, double t) {
@@ -974,7 +980,7 @@ const char *g1g2_strerror(int code) {
     case G1G2_ESYMM: return "input violates the symmetries of w, G1 or G2";
     case G1G2_ENOMEM: return "device allocation failed";
     case G1G2_ECUDA: return "CUDA error";
-    case G1G2_ENONFINITE: return "state contains NaN or Inf";
+    case G1G2_ENONFINITE: return "state or input contains NaN or Inf";
     case G1G2_ETIMEOUT: return "bounded device wait timed out";
     case G1G2_EUNSUPPORTED: return "not supported by this build";
     default: return "unknown error code";
@@ -1077,6 +1083,14 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
 
   const size_t N = nb, N2 = N * N, N4 = N2 * N2;
   const bool restricted = opt.basis == G1G2_SPIN_RESTRICTED;
+  // non-finite host inputs are refused before they reach the device
+  {
+    struct In { const double *p; size_t len; const char *name; };
+    const In ins[4] = {{h, 2 * N2, "h"}, {w, (opt.w_is_real ? 1 : 2) * N4, "w"}, {G1_0, 2 * N2, "G1_0"},
+                       {G2_0, G2_0 ? 2 * N4 : 0, "G2_0"}};
+    for (const In &x : ins)
+      if (!all_finite(x.p, x.len)) return fail(G1G2_ENONFINITE, std::string(x.name) + " contains NaN or Inf");
+  }
   auto wv = [&](size_t idx) -> zc { return opt.w_is_real ? zc(w[idx], 0.0) : hz(w, idx); };
   auto at4 = [&](size_t i, size_t j, size_t k, size_t l) { return ((i * N + j) * N + k) * N + l; };
 
@@ -1286,6 +1300,7 @@ int g1g2_init_factorised(g1g2_ctx **out, int nb, const double *h, const double *
   g1g2_default_options(&opt);
   if (opt_in) opt = *opt_in;
   const size_t N2 = (size_t)nb * nb, N4 = N2 * N2, NL = (size_t)nfac * N2;
+  if (!all_finite(Lh, (opt.w_is_real ? 1 : 2) * NL)) return fail(G1G2_ENONFINITE, "L contains NaN or Inf");
   std::vector<cplx> hL(NL);
   for (size_t e = 0; e < NL; ++e) hL[e] = opt.w_is_real ? cplx{Lh[e], 0.0} : cplx{Lh[2 * e], Lh[2 * e + 1]};
   cudaStream_t s = static_cast<cudaStream_t>(opt.cuda_stream);
@@ -1374,6 +1389,8 @@ int g1g2_set_drive(g1g2_ctx *c, const double *D, int kind, const double *params,
   if (kind != 1 && kind != 2) return fail(G1G2_EINVAL, "bad drive kind");
   if (kind == 1 && params[3] == 0.0) return fail(G1G2_EINVAL, "sigma must be nonzero");
   const size_t N2 = (size_t)c->nb * c->nb;
+  if (!all_finite(D, 2 * N2) || !all_finite(params, (size_t)nparams))
+    return fail(G1G2_ENONFINITE, "D or the drive parameters contain NaN or Inf");
   int rc = cuda_check(cudaMemcpyAsync(c->D, D, N2 * sizeof(cplx), cudaMemcpyHostToDevice, c->stream), "drive upload");
   if (rc) return rc;
   if ((rc = cuda_check(cudaStreamSynchronize(c->stream), "drive sync"))) return rc;

@@ -115,6 +115,54 @@ def test_factorised_arguments_rejected_on_host(lib):
         g1g2.Propagator(h, None, n0, factors=np.zeros((2, 3, 4)))
 
 
+def test_non_finite_inputs_rejected_on_host(lib):
+    """A NaN or an Inf in any host input of g1g2_init / g1g2_init_factorised is refused
+    (G1G2_ENONFINITE) before any device work."""
+    h, w, n0 = _valid(3)
+    g2 = np.zeros((3,) * 4, dtype=np.complex128)
+    for name in ("h", "w", "n0", "g2"):
+        args = dict(h=h.copy(), w=w.copy(), n0=n0.copy(), g2=g2.copy())
+        args[name].flat[4] = np.nan if name != "w" else complex(0.0, np.inf)
+        assert _init(lib, 3, args["h"], args["w"], args["n0"], g2=args["g2"]) == g1g2.ENONFINITE, name
+        assert name.replace("n0", "G1_0").replace("g2", "G2_0").encode() in lib.g1g2_last_error_detail()
+    wr = w.real.copy()
+    wr[1, 2, 1, 2] = -np.inf
+    assert _init(lib, 3, h, wr, n0, opt={"w_is_real": 1}) == g1g2.ENONFINITE
+    L = np.zeros((2, 3, 3))
+    L[1, 0, 0] = np.nan
+    ctx = ctypes.c_void_p()
+    o = g1g2.Options()
+    lib.g1g2_default_options(ctypes.byref(o))
+    o.w_is_real = 1
+    ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.g1g2_init_factorised(ctypes.byref(ctx), 3, ptr(h), ptr(L), 2, ptr(n0), None, 1,
+                                    ctypes.byref(o)) == g1g2.ENONFINITE
+    assert b"L contains" in lib.g1g2_last_error_detail()
+
+
+def test_device_allocation_failure_is_an_error_code(lib):
+    """Where no device memory can be had (here: a host without a GPU), init and
+    init_factorised return G1G2_ENOMEM with the failed size in the detail and leave the
+    context NULL; a repeated call fails the same way (nothing half-built is kept)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: cudaMalloc succeeds")
+    h, w, n0 = _valid(3)
+    ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    o = g1g2.Options()
+    lib.g1g2_default_options(ctypes.byref(o))
+    for _ in range(2):
+        ctx = ctypes.c_void_p()
+        assert lib.g1g2_init(ctypes.byref(ctx), 3, ptr(h), ptr(w), ptr(n0), None, 1, ctypes.byref(o)) == g1g2.ENOMEM
+        assert ctx.value is None and b"cudaMalloc" in lib.g1g2_last_error_detail()
+    o.w_is_real = 1
+    L = inputs.factors(3, 2, np.random.default_rng(1))
+    ctx = ctypes.c_void_p()
+    assert lib.g1g2_init_factorised(ctypes.byref(ctx), 3, ptr(h), ptr(L), 2, ptr(n0), None, 1,
+                                    ctypes.byref(o)) == g1g2.ENOMEM
+    assert ctx.value is None
+
+
 def test_symmetry_violations_rejected_on_host(lib):
     h, w, n0 = _valid(3)
     bad = w.copy()

@@ -222,3 +222,26 @@ def test_boson_rejections():
         Propagator(h, w, n, g2, "SOA", bosons=True, restricted=True)
     with Propagator(h, w, n, None, "SOA", bosons=True) as p, pytest.raises(G1G2Error):
         p.adjoint(0.01, 2, objective=0, ckpt_every=1, n_drive_params=0)
+
+
+def test_non_finite_state_and_drive_are_reported():
+    """A NaN planted in the state through g1g2_set_state (which does not scan its input) is
+    caught at the next observable record of g1g2_propagate (G1G2_ENONFINITE); a drive with an
+    Inf is refused by g1g2_set_drive; the context stays usable afterwards."""
+    from paper_2002_12717_gb300.g1g2 import ENONFINITE, G1G2Error, Propagator
+    h, w, n, g2, D, drv = problem(6, "SOA", seed=21)
+    with Propagator(h, w, n, None, "SOA") as p:
+        bad = n.copy()
+        bad[1, 2] = bad[2, 1] = np.nan
+        p.set_state(0.0, bad)
+        with pytest.raises(G1G2Error) as e:
+            p.propagate(0.01, 3, 1)
+        assert e.value.code == ENONFINITE
+        Dbad = D.copy()
+        Dbad[0, 0] = np.inf
+        with pytest.raises(G1G2Error) as e:
+            p.set_drive(Dbad, drv)
+        assert e.value.code == ENONFINITE
+        p.set_state(0.0, n)
+        obs, _ = p.propagate(0.01, 3, 1)
+        assert np.isfinite(obs[-1]["e_total"])
