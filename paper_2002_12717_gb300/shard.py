@@ -21,6 +21,9 @@ data of other ranks, and the collective that supplies it:
                         needs all p: one all-to-all (B re-sharded on index 2), after
                         which A's slab follows from its exchange symmetry
   A^dag                 conj(A_klij): one all-to-all (A re-sharded on index 3)
+  A, A^dag (factorised) with w = sum_P L^P (x) L^P and L replicated: from M^P = nbar L^P n,
+                        A_ijkl = sum_P M^P_ik M^P_jl (+ eta M^P_il M^P_jk) for any
+                        index range: no exchange (w's slab is formed from L as well)
   GW hcorr (Eq. gwhcorr) w x_4 n - n x_2 w on w[I_r] (local)
   Pi (Eq. gwpi)         Pi_ijkl = sum_pq G2_ipkq hcorr_qjpl, rows i in I_r: SUMMA
                         over the 1-D row blocks, P broadcasts of one rank's hcorr
@@ -179,7 +182,7 @@ def _es(eq, *ops):
 
 
 def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=None, bosons=False,
-                restricted=False):
+                restricted=False, factors=None):
     """(dn/dt, the slab of dG2/dt) at the state (n, G2), for fermions or (bosons=True) bosons:
     eta = -1 or +1 in the +/- of the paper (G^< = -i eta n, G^> = -i nbar with nbar = 1 + eta n,
     w^+/- = w + eta w_ijlk).  In a spin-orbital basis h^HF and the source term take w^+/-; in
@@ -188,9 +191,17 @@ def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=N
 
     h, n: replicated nb x nb; w_slab = w[I_r], G_slab = G2[I_r] (complex tensors).  dn is
     the same on every rank.  The arithmetic is that of the oracle's right-hand side with
-    the index ranges of the partition; the collectives are listed in the module header."""
+    the index ranges of the partition; the collectives are listed in the module header.
+
+    factors: the replicated factors L (nfac x nb x nb) of w_ijkl = sum_P L^P_ik L^P_jl, or
+    None.  With factors, w_slab may be None (each rank forms w[I_r] from L), and the source
+    term and its conjugate transpose come from the replicated M^P = nbar L^P n with no
+    exchange: A_ijkl = sum_P M^P_ik M^P_jl (+ eta M^P_il M^P_jk for w^+/-) for any index
+    range."""
     nb, lo, hi = part.nb, part.lo, part.hi
     cd = n.dtype
+    if factors is not None and w_slab is None:
+        w_slab = _es("pik,pjl->ijkl", factors[:, lo:hi], factors)
     eye = torch.eye(nb, dtype=cd, device=n.device)
     eta = 1.0 if bosons else -1.0
     nbar = eye + eta * n
@@ -214,13 +225,23 @@ def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=N
     Xj = reshard(X, part, 1, group)                       # X[a][b in I_r][c][d]
     C = X + Xj.permute(1, 0, 3, 2)                        # exch X_abcd = X_badc, a in I_r
     # source term, Eq. (psi-pm-def): A = nbar x1 nbar x2 w~ x3 n x4 n, Psi = -A + A^dag
-    wsrc = w_slab if selfenergy == "GW" else wpm          # plain w for standard GW, w^+/- otherwise
-    B = _es("jq,pqrs,rk,sl->pjkl", nbar, wsrc, n, n)      # p in I_r
-    Bj = reshard(B, part, 1, group)                       # B[p (all)][j in I_r][k][l]
-    Aj = _es("ip,pjkl->ijkl", nbar, Bj)                   # A[i (all)][j in I_r][k][l]
-    A = Aj.permute(1, 0, 3, 2)                            # A_abcd = A_badc (exchange symmetry), a in I_r
-    A3 = reshard(A, part, 2, group)                       # A[a][b][c in I_r][d]
-    A_dag = A3.permute(2, 3, 0, 1).conj()                 # conj(A_cdab), first index in I_r
+    if factors is not None:
+        pm = selfenergy != "GW" and not restricted        # w~ = w^+/- (else the plain w)
+        M = nbar @ factors @ n                            # M^P = nbar L^P n, replicated
+        Mr, Mc = M[:, lo:hi], M[:, :, lo:hi]              # rows / columns in I_r
+        A = _es("pik,pjl->ijkl", Mr, M)                   # i in I_r
+        A_dag = _es("pki,plj->ijkl", Mc, M).conj()        # conj(A_klij): sum_P M^P_ki M^P_lj
+        if pm:
+            A = A + eta * _es("pil,pjk->ijkl", Mr, M)
+            A_dag = A_dag + eta * _es("pli,pkj->ijkl", Mc, M).conj()   # eta M^P_kj M^P_li
+    else:
+        wsrc = w_slab if selfenergy == "GW" else wpm      # plain w for standard GW, w^+/- otherwise
+        B = _es("jq,pqrs,rk,sl->pjkl", nbar, wsrc, n, n)  # p in I_r
+        Bj = reshard(B, part, 1, group)                   # B[p (all)][j in I_r][k][l]
+        Aj = _es("ip,pjkl->ijkl", nbar, Bj)               # A[i (all)][j in I_r][k][l]
+        A = Aj.permute(1, 0, 3, 2)                        # A_abcd = A_badc (exchange symmetry), a in I_r
+        A3 = reshard(A, part, 2, group)                   # A[a][b][c in I_r][d]
+        A_dag = A3.permute(2, 3, 0, 1).conj()             # conj(A_cdab), first index in I_r
     rhs2 = C - A + A_dag
     if selfenergy in ("GW", "GWX", "DSL"):
         # Eq. (gwhcorr): hcorr = w x4 n - n x2 w (w's exchange symmetry; the eta terms of

@@ -15,6 +15,8 @@ import pytest
 
 from oracle import g1g2_oracle as O
 
+from paper_2002_12717_gb300 import inputs
+
 from .helpers import problem
 
 torch = pytest.importorskip("torch")
@@ -88,6 +90,80 @@ def test_sharded_rhs_matches_oracle(world):
                 assert np.abs(z["dn"] - dn_ref).max() <= 1e-12 * np.abs(dn_ref).max(), (se, nb, r)
                 assert abs(float(z["ec"]) - e_ref) <= 1e-12 * max(abs(e_ref), 1e-12)
             assert covered.all()
+
+
+# (selfenergy, nb, bosons, spin-restricted, complex factors)
+FACTOR_CASES = [("SOA", 5, False, False, False), ("SOA", 6, False, False, True), ("GW", 5, False, False, True),
+                ("GWX", 5, False, False, False), ("TPP", 5, False, False, True), ("TPH", 5, False, False, False),
+                ("DSL", 5, True, False, True), ("SOA", 5, True, False, False), ("SOA", 5, False, True, False)]
+
+
+def _factor_state(nb, seed, complex_l):
+    rng = np.random.default_rng(seed)
+    h = inputs.random_hermitian(nb, rng)
+    if complex_l:
+        a = (rng.standard_normal((4, nb, nb)) + 1j * rng.standard_normal((4, nb, nb))) * 0.1
+        L = (a + a.conj().transpose(0, 2, 1)) / 2
+        L[1::2] *= 1j                                   # Hermitian and i-Hermitian factors
+    else:
+        L = inputs.factors(nb, 4, rng)
+    n, g2 = inputs.random_state(nb, rng, soa=False)
+    return h, L, n, g2
+
+
+def _factor_worker(rank, world, port, outdir):
+    import torch.distributed as dist
+
+    from paper_2002_12717_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    calls = {"n": 0}
+    a2a = shard.dist.all_to_all_single
+
+    def counted(*args, **kw):
+        calls["n"] += 1
+        return a2a(*args, **kw)
+    shard.dist.all_to_all_single = counted
+    try:
+        for ci, (se, nb, bosons, rs, cl) in enumerate(FACTOR_CASES):
+            h, L, n, g2 = _factor_state(nb, 120 + ci, cl)
+            part = shard.Partition(nb, world, rank)
+            t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128))
+            counts = []
+            for use_factors in (True, False):
+                calls["n"] = 0
+                w_slab = None if use_factors else part.slab(t(np.einsum("pik,pjl->ijkl", L, L)))
+                dn, dg = shard.rhs_sharded(part, t(h), w_slab, t(n), part.slab(t(g2)), se, bosons=bosons,
+                                           restricted=rs, factors=t(L) if use_factors else None)
+                counts.append(calls["n"])
+                if use_factors:
+                    out = dict(dn=dn.numpy(), dg=dg.numpy())
+            np.savez(os.path.join(outdir, f"f{rank}_c{ci}.npz"), counts=counts, lo=part.lo, hi=part.hi, **out)
+    finally:
+        shard.dist.all_to_all_single = a2a
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_rhs_with_factors_matches_oracle(world):
+    """w given as replicated factors (each rank forms w[I_r] itself): every rank's slab of
+    dG2/dt and dn/dt against the oracle's right-hand side on w = w_from_factors(L), and the
+    source term's two all-to-alls gone (counted on every rank)."""
+    import torch.multiprocessing as mp
+    with tempfile.TemporaryDirectory() as outdir:
+        mp.spawn(_factor_worker, args=(world, _free_port(), outdir), nprocs=world, join=True)
+        for ci, (se, nb, bosons, rs, cl) in enumerate(FACTOR_CASES):
+            h, L, n, g2 = _factor_state(nb, 120 + ci, cl)
+            prob = O.Problem(h, O.w_from_factors(L), se, rs, bosons=bosons)
+            dn_ref, dg_ref = O.rhs(prob, 0.0, n, g2)
+            for r in range(world):
+                z = np.load(os.path.join(outdir, f"f{r}_c{ci}.npz"))
+                lo, hi = int(z["lo"]), int(z["hi"])
+                assert np.abs(z["dg"] - dg_ref[lo:hi]).max() <= 1e-12 * np.abs(dg_ref).max(), (se, r)
+                assert np.abs(z["dn"] - dn_ref).max() <= 1e-12 * np.abs(dn_ref).max(), (se, r)
+                with_f, without = z["counts"]
+                assert with_f == without - 2, (se, r, with_f, without)
 
 
 STEP_CASES = [("SOA", 5, False), ("GW", 5, False), ("DSL", 5, True)]
