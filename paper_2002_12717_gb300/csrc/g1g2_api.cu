@@ -7,6 +7,8 @@
 #include "g1g2_internal.h"
 #include "tc_path.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -123,6 +125,16 @@ int launch_status(Launcher &L, const char *what) {
 }
 
 using zc = std::complex<double>;
+
+// NVTX range for the lifetime of the object: RK4 steps and stages, observables, the
+// propagation loops and the adjoint sweeps show up by name on a profiler's timeline
+// (without a tool attached the calls return at once).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 bool all_finite(const double *p, size_t len) {
   for (size_t e = 0; e < len; ++e)
@@ -466,6 +478,9 @@ void rhs_dispatch(g1g2_ctx *c, Launcher &L, double t, const cplx *n_in, const cp
 }
 
 int rk4_step(g1g2_ctx *c, double dt) {
+  NvtxRange step_range("g1g2 rk4 step");
+  static const char *const stage_name[4] = {"g1g2 rk4 stage 1", "g1g2 rk4 stage 2", "g1g2 rk4 stage 3",
+                                            "g1g2 rk4 stage 4"};
   Launcher L = c->launcher();
   const double t = c->t;
   const double cs[4] = {0.0, 0.5, 0.5, 1.0};
@@ -482,6 +497,7 @@ int rk4_step(g1g2_ctx *c, double dt) {
       const double coeff = dt / 6.0 * wgt[s] * drive_dfdt(c, t + cs[s] * dt);
       accumulate_work(L, c->nb, c->D, n_in, coeff * (c->basis == G1G2_SPIN_RESTRICTED ? 2.0 : 1.0), c->W_dev);
     }
+    NvtxRange stage_range(stage_name[s]);
     Rk4Stage st{s, dt};
     rhs_dispatch(c, L, t + cs[s] * dt, n_in, G_in, st, o);
   }
@@ -490,6 +506,7 @@ int rk4_step(g1g2_ctx *c, double dt) {
 }
 
 int observables_impl(g1g2_ctx *c, g1g2_obs *out, double *density, double *nonfinite) {
+  NvtxRange range("g1g2 observables");
   Launcher L = c->launcher();
   const int nb = c->nb;
   const double f = drive_f(c, c->t);
@@ -1449,6 +1466,7 @@ int g1g2_observables(g1g2_ctx *c, g1g2_obs *out, double *density, double *dbl) {
 int g1g2_propagate(g1g2_ctx *c, double dt, int nsteps, int obs_every, g1g2_obs *obs, double *density) {
   if (!c || nsteps < 0) return fail(G1G2_EINVAL, "bad argument");
   if ((obs || density) && obs_every <= 0) return fail(G1G2_EINVAL, "obs_every must be positive");
+  NvtxRange range("g1g2 propagate");
   int rec = 0, rc;
   auto record = [&]() -> int {
     g1g2_obs o;
@@ -1483,6 +1501,7 @@ int g1g2_propagate_hfgkba(g1g2_ctx *c, double dt, int nsteps, double *G1_history
   if (!c || nsteps < 0 || !std::isfinite(dt)) return fail(G1G2_EINVAL, "bad argument");
   if (c->se != G1G2_SOA || c->prec != G1G2_FP64)
     return fail(G1G2_EUNSUPPORTED, "the memory-integral HF-GKBA covers SOA in the FP64 form");
+  NvtxRange range("g1g2 hf-gkba propagate");
   if (c->hasD) return fail(G1G2_EUNSUPPORTED, "the memory-integral HF-GKBA runs without a drive");
   if (c->nb > mode_rotate_max_nb())
     return fail(G1G2_EUNSUPPORTED, "the memory-integral HF-GKBA keeps nb^4 per time step; nb <= " +
@@ -1668,6 +1687,7 @@ int g1g2_adjoint(g1g2_ctx *c, double dt, int nsteps, int ckpt_every, int objecti
                  double *grad_drive, double *grad_wscale, double *grad_h, double *grad_w) {
   if (!c || nsteps < 1 || !J_out) return fail(G1G2_EINVAL, "bad adjoint argument");
   if (c->prec != G1G2_FP64) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint runs on the FP64 form");
+  NvtxRange range("g1g2 adjoint");
   if (c->hub_gw) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers the general basis");
   if (c->eta > 0) return fail(G1G2_EUNSUPPORTED, "the discrete adjoint covers fermions");
   if (objective < 0 || objective > 2) return fail(G1G2_EINVAL, "objective must be 0, 1 or 2");
