@@ -264,13 +264,17 @@ def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=N
 
 
 def rk4_step_sharded(part: Partition, h_of_t, t, w_slab, n, G_slab, dt, selfenergy="SOA", group=None,
-                     bosons=False, restricted=False):
+                     bosons=False, restricted=False, factors=None):
     """One classical RK4 step of (n, G2) with G2 partitioned (the slab G2[i in I_r], n replicated):
     four right-hand sides of rhs_sharded at t, t + dt/2, t + dt/2, t + dt (h_of_t(t) the
     replicated one-body Hamiltonian at time t), the stage states formed on each rank's slab.
+    With factors (and w_slab None) w's slab is formed once from them for the whole step.
     Returns (n, the slab of G2) at t + dt."""
+    if factors is not None and w_slab is None:
+        w_slab = _es("pik,pjl->ijkl", factors[:, part.lo:part.hi], factors)
+
     def f(tt, nn, gg):
-        return rhs_sharded(part, h_of_t(tt), w_slab, nn, gg, selfenergy, group, bosons, restricted)
+        return rhs_sharded(part, h_of_t(tt), w_slab, nn, gg, selfenergy, group, bosons, restricted, factors)
     k1 = f(t, n, G_slab)
     k2 = f(t + dt / 2, n + dt / 2 * k1[0], G_slab + dt / 2 * k1[1])
     k3 = f(t + dt / 2, n + dt / 2 * k2[0], G_slab + dt / 2 * k2[1])

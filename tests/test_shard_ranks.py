@@ -166,7 +166,7 @@ def test_sharded_rhs_with_factors_matches_oracle(world):
                 assert with_f == without - 2, (se, r, with_f, without)
 
 
-STEP_CASES = [("SOA", 5, False), ("GW", 5, False), ("DSL", 5, True)]
+STEP_CASES = [("SOA", 5, False), ("GW", 5, False), ("DSL", 5, True), ("GWX", 5, False)]
 
 
 def _step_worker(rank, world, port, outdir, nsteps, dt):
@@ -183,9 +183,12 @@ def _step_worker(rank, world, port, outdir, nsteps, dt):
             t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128))
             h_of_t = lambda tt: t(h + drv.f(tt) * D)
             nn, gg = t(n), part.slab(t(g2))
+            L = None
+            if ci == len(STEP_CASES) - 1:       # the last case: w given as factors
+                L = t(inputs.factors(nb, 3, np.random.default_rng(91)))
             for m in range(nsteps):
-                nn, gg = shard.rk4_step_sharded(part, h_of_t, m * dt, part.slab(t(w)), nn, gg, dt, se,
-                                                bosons=bosons)
+                nn, gg = shard.rk4_step_sharded(part, h_of_t, m * dt, None if L is not None else part.slab(t(w)),
+                                                nn, gg, dt, se, bosons=bosons, factors=L)
             np.savez(os.path.join(outdir, f"s{rank}_c{ci}.npz"), n=nn.numpy(), g=gg.numpy(), lo=part.lo,
                      hi=part.hi)
     finally:
@@ -194,13 +197,16 @@ def _step_worker(rank, world, port, outdir, nsteps, dt):
 
 def test_sharded_rk4_steps_match_oracle():
     """Three driven RK4 steps with G2 partitioned over 3 ranks (nb = 5: blocks 2, 2, 1) against
-    the oracle's steps on the whole state: SOA, GW, and DSL for bosons."""
+    the oracle's steps on the whole state: SOA, GW, DSL for bosons, and GWX with w given as
+    three factors."""
     import torch.multiprocessing as mp
     world, nsteps, dt = 3, 3, 0.02
     with tempfile.TemporaryDirectory() as outdir:
         mp.spawn(_step_worker, args=(world, _free_port(), outdir, nsteps, dt), nprocs=world, join=True)
         for ci, (se, nb, bosons) in enumerate(STEP_CASES):
             h, w, n, g2, D, drv = problem(nb, se, complex_w=True, seed=90 + ci)
+            if ci == len(STEP_CASES) - 1:
+                w = O.w_from_factors(inputs.factors(nb, 3, np.random.default_rng(91)))
             prob = O.Problem(h, w, se, False, D, drv.f, bosons=bosons)
             for m in range(nsteps):
                 n, g2, _ = O.rk4_step(prob, m * dt, n, g2, dt)
