@@ -1,7 +1,8 @@
 """The 2-D block-distributed product of the partition module (shard.summa_matmul: SUMMA on a
 q x q process grid, gloo CPU ranks): a ragged complex product against numpy, and the GW
-polarisation (Eq. gwpi) in its nb^2 x nb^2 matrix view against the oracle, on 2 x 2 and
-3 x 3 grids."""
+polarisation (Eq. gwpi) and the particle-particle and particle-hole ladder terms
+(Eqs. lambdapp, lambdaph) in their nb^2 x nb^2 matrix views against the oracle, on 2 x 2
+and 3 x 3 grids."""
 import os
 import socket
 import tempfile
@@ -32,7 +33,15 @@ def _matrices(nb):
     hc = O.gw_hcorr(w, n)
     A2 = g2.transpose(0, 2, 1, 3).reshape(nb * nb, nb * nb)
     B2 = hc.transpose(2, 0, 1, 3).reshape(nb * nb, nb * nb)
-    return [(A1, B1), (A2, B2)], O.gw_polarisation(hc, g2)
+    # Eq. (lambdapp): Lambda_(ij),(kl) = sum_(pq) hpp_(ij),(pq) G_(pq),(kl)
+    hpp = O.tpp_hcorr(w, n)
+    A3, B3 = hpp.reshape(nb * nb, nb * nb), g2.reshape(nb * nb, nb * nb)
+    # Eq. (lambdaph): Lambda_ijkl = sum_pq hph_ipql G_qjkp, rows (i,l), K (p,q), columns (j,k)
+    hph = O.tph_hcorr(w, n)
+    A4 = hph.transpose(0, 3, 1, 2).reshape(nb * nb, nb * nb)
+    B4 = g2.transpose(3, 0, 1, 2).reshape(nb * nb, nb * nb)
+    refs = {1: O.gw_polarisation(hc, g2), 2: O.tpp_ladder(hpp, g2), 3: O.tph_ladder(hph, g2)}
+    return [(A1, B1), (A2, B2), (A3, B3), (A4, B4)], refs
 
 
 def _worker(rank, world, port, outdir, nb):
@@ -66,7 +75,7 @@ def test_summa_matches_dense_product(world):
     nb = 5
     with tempfile.TemporaryDirectory() as outdir:
         mp.spawn(_worker, args=(world, _free_port(), outdir, nb), nprocs=world, join=True)
-        pairs, pi_ref = _matrices(nb)
+        pairs, refs = _matrices(nb)
         for ci, (A, B) in enumerate(pairs):
             ref = A @ B
             got = np.full(ref.shape, np.nan, dtype=np.complex128)
@@ -76,7 +85,9 @@ def test_summa_matches_dense_product(world):
                 got[r0:r1, c0:c1] = z["C"]
             assert np.isfinite(got).all()                      # every block written
             assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
-            if ci == 1:
-                # the matrix view of Eq. (gwpi): C_(ik),(jl) = Pi_ijkl
-                pi = got.reshape(nb, nb, nb, nb).transpose(0, 2, 1, 3)
-                assert np.abs(pi - pi_ref).max() <= 1e-12 * np.abs(pi_ref).max()
+            if ci:
+                g4 = got.reshape(nb, nb, nb, nb)
+                # the matrix views: Pi_ijkl = C_(ik),(jl) (Eq. gwpi), Lambda^pp_ijkl = C_(ij),(kl)
+                # (Eq. lambdapp), Lambda^ph_ijkl = C_(il),(jk) (Eq. lambdaph)
+                got4 = {1: g4.transpose(0, 2, 1, 3), 2: g4, 3: g4.transpose(0, 2, 3, 1)}[ci]
+                assert np.abs(got4 - refs[ci]).max() <= 1e-12 * np.abs(refs[ci]).max(), ci
