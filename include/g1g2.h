@@ -148,7 +148,8 @@ int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const do
  *          interleaved, or real if opt->w_is_real (host, copied).  Each L^P is
  *          Hermitian or i times Hermitian, so that w meets Eqs. (wsymm_a/b)
  *   nfac   number of factors, 1 <= nfac <= nb*nb
- * A NaN or an Inf in L returns G1G2_ENONFINITE before any device work.
+ * A NaN or an Inf in L returns G1G2_ENONFINITE, a factor that is neither Hermitian
+ * nor i times Hermitian (beyond opt->sym_tol) G1G2_ESYMM, both before any device work.
  * The other arguments and the error codes are those of g1g2_init, which runs on
  * the w expanded on the device (one nb^2 x nb^2 x nfac product; nb^4 complex
  * doubles of host memory for the duration of the call).  In the FP64 form the

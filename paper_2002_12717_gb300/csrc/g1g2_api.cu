@@ -1320,6 +1320,22 @@ int g1g2_init_factorised(g1g2_ctx **out, int nb, const double *h, const double *
   if (!all_finite(Lh, (opt.w_is_real ? 1 : 2) * NL)) return fail(G1G2_ENONFINITE, "L contains NaN or Inf");
   std::vector<cplx> hL(NL);
   for (size_t e = 0; e < NL; ++e) hL[e] = opt.w_is_real ? cplx{Lh[e], 0.0} : cplx{Lh[2 * e], Lh[2 * e + 1]};
+  // each factor Hermitian or i times Hermitian (then w meets Eqs. wsymm_a/b), checked on the host
+  if (opt.sym_tol >= 0) {
+    for (int P = 0; P < nfac; ++P) {
+      const cplx *f = hL.data() + (size_t)P * N2;
+      double fmax = 0, eh = 0, ea = 0;
+      for (int i = 0; i < nb; ++i)
+        for (int k = 0; k < nb; ++k) {
+          const cplx a = f[(size_t)i * nb + k], b = f[(size_t)k * nb + i];  // b = L_ki
+          fmax = std::max(fmax, std::hypot(a.x, a.y));
+          eh = std::max(eh, std::hypot(a.x - b.x, a.y + b.y));   // |L_ik - conj(L_ki)|
+          ea = std::max(ea, std::hypot(a.x + b.x, a.y - b.y));   // |L_ik + conj(L_ki)|
+        }
+      if (std::min(eh, ea) > opt.sym_tol * std::max(1.0, fmax))
+        return fail(G1G2_ESYMM, "factor " + std::to_string(P) + " is neither Hermitian nor i times Hermitian");
+    }
+  }
   cudaStream_t s = static_cast<cudaStream_t>(opt.cuda_stream);
   cplx *dL = nullptr, *dC = nullptr, *dW = nullptr;
   auto alloc = [](cplx **p, size_t count) -> int {

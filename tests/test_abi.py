@@ -54,6 +54,10 @@ def _init(lib, nb, h, w, n0, se=1, opt=None, g2=None):
     return lib.g1g2_init(ctypes.byref(ctx), nb, ptr(h), ptr(w), ptr(n0), ptr(g2), se, ctypes.byref(o))
 
 
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
 def _valid(nb):
     rng = np.random.default_rng(0)
     h = inputs.random_hermitian(nb, rng)
@@ -113,6 +117,53 @@ def test_factorised_arguments_rejected_on_host(lib):
         g1g2.Propagator(h, None, n0)                        # neither w nor factors
     with pytest.raises(ValueError):
         g1g2.Propagator(h, None, n0, factors=np.zeros((2, 3, 4)))
+
+
+def test_factor_symmetry_checked_on_host(lib):
+    """g1g2_init_factorised accepts Hermitian and i-Hermitian factors (the ones whose w meets
+    Eqs. wsymm_a/b) and refuses others with G1G2_ESYMM before any device work; the factors of
+    the GPU parity tests pass the check."""
+    from .test_gpu_factorised import CASES, complex_factors, state
+    nb = 4
+    h, _, n0 = _valid(nb)
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((2, nb, nb)) + 1j * rng.standard_normal((2, nb, nb))
+    herm = (a + a.conj().transpose(0, 2, 1)) / 2
+    b = rng.standard_normal((2, nb, nb))
+    ptr = lambda x: x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    def init(L):
+        o = g1g2.Options()
+        lib.g1g2_default_options(ctypes.byref(o))
+        real = np.isrealobj(L)
+        o.w_is_real = int(real)
+        buf = np.ascontiguousarray(L, dtype=np.float64 if real else np.complex128)
+        ctx = ctypes.c_void_p()
+        rc = lib.g1g2_init_factorised(ctypes.byref(ctx), nb, ptr(h), ptr(buf), L.shape[0], ptr(n0), None, 1,
+                                      ctypes.byref(o))
+        if ctx.value:
+            lib.g1g2_destroy(ctx)
+        return rc
+    valid = [herm, 1j * herm, inputs.factors(nb, 3, rng), b - b.transpose(0, 2, 1), np.zeros((1, nb, nb)),
+             np.concatenate([herm, 1j * herm]), complex_factors(nb, 5, rng)]
+    for L in valid:
+        assert init(L) in (g1g2.OK, g1g2.ENOMEM)
+    for se, nb_, nfac, complex_l, _, restricted in CASES:   # the inputs of the GPU parity tests
+        hh, L, nn, _ = state(nb_, nfac, se, 100 + nb_, complex_l, restricted)
+        o = g1g2.Options()
+        lib.g1g2_default_options(ctypes.byref(o))
+        o.w_is_real = int(np.isrealobj(L))
+        buf = np.ascontiguousarray(L, dtype=np.float64 if np.isrealobj(L) else np.complex128)
+        ctx = ctypes.c_void_p()
+        rc = lib.g1g2_init_factorised(ctypes.byref(ctx), nb_, ptr(_c(hh)), ptr(buf), nfac, ptr(_c(nn)), None, 1,
+                                      ctypes.byref(o))
+        if ctx.value:
+            lib.g1g2_destroy(ctx)
+        assert rc in (g1g2.OK, g1g2.ENOMEM), (se, nb_, rc)
+    sym = a + a.transpose(0, 2, 1)                        # complex symmetric, not Hermitian
+    for L in (sym, b, (1 + 1j) * herm, np.concatenate([herm, sym[:1]])):
+        assert init(L) == g1g2.ESYMM
+        assert b"Hermitian" in lib.g1g2_last_error_detail()
 
 
 def test_non_finite_inputs_rejected_on_host(lib):
