@@ -200,6 +200,8 @@ def rhs_sharded(part: Partition, h, w_slab, n, G_slab, selfenergy="SOA", group=N
     range."""
     nb, lo, hi = part.nb, part.lo, part.hi
     cd = n.dtype
+    if factors is not None:
+        factors = factors.to(cd)
     if factors is not None and w_slab is None:
         w_slab = _es("pik,pjl->ijkl", factors[:, lo:hi], factors)
     eye = torch.eye(nb, dtype=cd, device=n.device)
@@ -270,6 +272,8 @@ def rk4_step_sharded(part: Partition, h_of_t, t, w_slab, n, G_slab, dt, selfener
     replicated one-body Hamiltonian at time t), the stage states formed on each rank's slab.
     With factors (and w_slab None) w's slab is formed once from them for the whole step.
     Returns (n, the slab of G2) at t + dt."""
+    if factors is not None:
+        factors = factors.to(n.dtype)
     if factors is not None and w_slab is None:
         w_slab = _es("pik,pjl->ijkl", factors[:, part.lo:part.hi], factors)
 

@@ -134,8 +134,9 @@ def _factor_worker(rank, world, port, outdir):
             for use_factors in (True, False):
                 calls["n"] = 0
                 w_slab = None if use_factors else part.slab(t(np.einsum("pik,pjl->ijkl", L, L)))
+                Lt = (torch.from_numpy(L) if np.isrealobj(L) else t(L)) if use_factors else None  # real stays real
                 dn, dg = shard.rhs_sharded(part, t(h), w_slab, t(n), part.slab(t(g2)), se, bosons=bosons,
-                                           restricted=rs, factors=t(L) if use_factors else None)
+                                           restricted=rs, factors=Lt)
                 counts.append(calls["n"])
                 if use_factors:
                     out = dict(dn=dn.numpy(), dg=dg.numpy())
