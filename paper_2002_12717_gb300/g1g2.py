@@ -350,6 +350,30 @@ class Propagator:
         return int(self._lib.g1g2_launch_count(self._ctx))
 
 
+def save_checkpoint(prop, path):
+    """Write the propagated state of `prop` (t, G1 = n, G2; the paper's initial-value data of
+    Sec. III.F at time t) to `path` as a numpy .npz archive, with nb, the selfenergy and the
+    basis for the check on resume.  The accumulated pulse work is an observable, not state:
+    it restarts from zero after load_checkpoint (as after g1g2_set_state)."""
+    t, n, g = prop.get_state()
+    np.savez(path, t=np.float64(t), G1=n, G2=g, nb=np.int64(prop.nb), selfenergy=str(prop.selfenergy),
+             restricted=bool(prop.restricted))
+
+
+def load_checkpoint(prop, path):
+    """Resume `prop` from a save_checkpoint archive (g1g2_set_state); returns t.  Refuses an
+    archive of another nb, selfenergy or basis (ValueError).  Spin-restricted Hubbard GW keeps
+    a same-spin block inside the context that set_state zeroes, so its resume is not exact."""
+    with np.load(path) as z:
+        for key, want in (("nb", prop.nb), ("selfenergy", str(prop.selfenergy)), ("restricted", bool(prop.restricted))):
+            got = z[key].item()
+            if got != want:
+                raise ValueError(f"checkpoint has {key} = {got!r}, the propagator {want!r}")
+        t, n, g = float(z["t"]), z["G1"], z["G2"]
+    prop.set_state(t, n, g)
+    return t
+
+
 def from_workload(d, precision="fp64", stream=None):
     """Propagator for a workload dict of paper_2002_12717_gb300.inputs."""
     p = Propagator(d["h"], d["w"], d["n0"], d.get("G2_0"), selfenergy=d["selfenergy"], precision=precision,
