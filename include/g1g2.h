@@ -88,7 +88,8 @@ typedef enum {
 /* Basis. SPIN_RESTRICTED: the index runs over spatial orbitals, w is an
  * opposite-spin interaction and n_up = n_down (the Hubbard equations of
  * Sec. III.D: no exchange term in h^HF and Psi, spin factors in the energies).
- * Only SOA and HF are defined in this basis. */
+ * HF, SOA and the two T matrices run in this basis for any such w; GW only in
+ * the Hubbard form (an on-site w); GW with exchange and DSL not at all. */
 typedef enum { G1G2_SPIN_ORBITAL = 0, G1G2_SPIN_RESTRICTED = 1 } g1g2_basis;
 
 typedef struct {
@@ -132,9 +133,11 @@ void g1g2_default_options(g1g2_options *opt);
  *   G2_0       nb^4 complex with Eqs. (Gsymm_a/b) (host), or NULL for G2_0 = 0
  *   se         g1g2_selfenergy
  *   opt        options, or NULL for the defaults
- * Returns G1G2_EINVAL for nb out of range, NULL arrays, bad enums, or GW in
- * the spin-restricted basis; G1G2_ESYMM when a symmetry is violated beyond
- * sym_tol; G1G2_ENONFINITE when h, w, G1_0 or G2_0 holds a NaN or an Inf
+ * Returns G1G2_EINVAL for nb out of range, NULL arrays, bad enums, GW with
+ * exchange or DSL in the spin-restricted basis, or GW there with a w that is
+ * not on-site (the Hubbard form); G1G2_EUNSUPPORTED for a combination this
+ * build does not run (see g1g2_selfenergy and g1g2_precision); G1G2_ESYMM
+ * when a symmetry is violated beyond sym_tol; G1G2_ENONFINITE when h, w, G1_0 or G2_0 holds a NaN or an Inf
  * (checked on the host before any device work); G1G2_ENOMEM / G1G2_ECUDA on
  * device failure. t starts at 0. */
 int g1g2_init(g1g2_ctx **out, int nb, const double *h, const double *w, const double *G1_0,
